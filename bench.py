@@ -1,0 +1,343 @@
+"""Throughput of one RBM-VMC + SR iteration on the 20x20 J1-J2 workload
+(N = 400 sites, complex RBM alpha = 4: M = 1600, 642,000 complex parameters,
+16384 chains x 4 samples = 65,536 samples per iteration, exchange moves,
+SR by lazy CG with 50 iterations), on synthetic seeded inputs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--prec fp32|bf16x2] [--workload c5|c3|c2|c1]
+
+One JSON line on rank 0.  `value` = samples per second of whole iterations
+(Metropolis sweeps incl. burn-in, ln psi, local energies, SR step), device
+timed with CUDA events, max over ranks; several GPUs run independent replicas
+(weak scaling).  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RBM-VMC samples/s and SR steps/s at N=400 vs plain FP32 GPU path; % roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x2"])
+    ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c3", "c5"])
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fp32-arm", action="store_true", help="skip the plain FP32 comparison")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(workload: str, n_chains: int, spc: int, n_cg: int) -> dict:
+    """One oracle VMC + SR iteration on a bounded sample (n_chains chains, spc
+    samples per chain, 1 burn-in sweep); returns seconds and samples."""
+    import numpy as np
+    from oracle import local_energy, rbm, sampler, sr
+    from paper_1904_00031_gb300 import workloads as W
+    w = W.workload(workload)
+    p = W.init_params(w.n, w.m, w.is_complex, 0.01, w.seed)
+    s0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed)[:n_chains]
+    t0 = time.perf_counter()
+    samples, fin, cnt, nacc = sampler.metropolis(p, s0, w.move, w.sampler_bonds, w.group_size,
+                                                 w.seed, 0, 1, spc)
+    e = local_energy.local_energy_rbm(p, w.op, samples)
+    mean, var, err = sr.stats(e, n_chains)
+    sig, t = rbm.logderiv_factored(p, samples)
+    real = not p.is_complex
+    f = sr.force_lazy(sig, t, e, p.n, p.m, None, real)
+    delta, it, res = sr.cg(lambda x: sr.sr_matvec_lazy(sig, t, x, p.n, p.m, None, real), f,
+                           w.diag_shift, n_cg, 1e-12)
+    sr.sgd_update(p.flat(), delta, w.lr)
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "samples": int(len(samples)), "energy": float(mean.real)}
+
+
+def run_oracle_subprocess(workload: str, n_chains: int, spc: int, n_cg: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    spec = json.dumps({"workload": workload, "n_chains": n_chains, "spc": spc, "n_cg": n_cg})
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", spec],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+ORACLE_SAMPLE = {"c5": (16, 2, 50), "c3": (64, 1, 50), "c2": (128, 4, 50), "c1": (16, 63, 120)}
+
+
+# ---------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.f.read().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------- GPU arm
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    # 152 SMs x 128 FP32 lanes x 2 flop per FMA x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def metropolis_flops(w) -> float:
+    """Algorithmic FP32 work of one nk_metropolis_sweep call: per proposal and
+    hidden unit one complex ratio factor r = C - t S (complex multiply and
+    subtract, 8 flop), its squared modulus (3) and the running product (1):
+    12 flop complex, 4 flop real (r = C - t S, product)."""
+    per = 12 if w.is_complex else 4
+    return float(w.n_chains) * (w.n_discard + w.samples_per_chain) * w.n * w.m * per
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1904_00031_gb300 import nk
+    from paper_1904_00031_gb300 import workloads as W
+    from paper_1904_00031_gb300.vmc import VmcSr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    nk.load_library()
+    w = W.workload(args.workload)
+    params = W.init_params(w.n, w.m, w.is_complex, 0.01, w.seed)
+    prec_name = args.prec if args.prec != "auto" else "fp32"
+    prec = nk.NK_PREC_FP32 if prec_name == "fp32" else nk.NK_PREC_BF16X2
+    # each rank samples its own chains (independent replicas)
+    sigma0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed + 7919 * rank)
+    v = VmcSr(w, params, sigma0, prec)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        v.step()
+    barrier()
+    stages = ["sample", "amplitudes", "energies", "sr"]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        for si, name in enumerate(stages):
+            getattr(v, name)()
+            ev[k][si + 1].record(stream)
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    stage_ms = {name: float(np.mean([ev[k][si].elapsed_time(ev[k][si + 1])
+                                     for k in range(args.steps)]))
+                for si, name in enumerate(stages)}
+    info = v.info()
+    t = torch.tensor([total_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * w.n_samples / (ms_per_step / 1e3)
+
+    # end to end through the public API: parameters H2D from pinned memory,
+    # one iteration, the FP64 status block D2H, every step
+    pa = v.rbm.a.cpu().pin_memory()
+    pb = v.rbm.b.cpu().pin_memory()
+    pw = v.rbm.w.cpu().pin_memory()
+    host_info = torch.empty(nk.NK_INFO_LEN, dtype=torch.float64).pin_memory()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        v.rbm.a.copy_(pa, non_blocking=True)
+        v.rbm.b.copy_(pb, non_blocking=True)
+        v.rbm.w.copy_(pw, non_blocking=True)
+        nk.nk_rbm_prepare(v.rbm)
+        v.step()
+        host_info.copy_(v.info_buf, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([e2e_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(t.item())
+    h2d = (pa.numel() + pb.numel() + pw.numel()) * 8
+
+    # the plain FP32 path on the same workload (for the mixed-precision ratio)
+    fp32_arm = None
+    if prec != nk.NK_PREC_FP32 and not args.no_fp32_arm:
+        v32 = VmcSr(w, params, sigma0, nk.NK_PREC_FP32)
+        for _ in range(max(1, args.warmup)):
+            v32.step()
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            v32.step()
+        a1.record(stream)
+        barrier()
+        fp32_arm = w.n_samples / (a0.elapsed_time(a1) / args.steps / 1e3)
+
+    pk, pk_kind = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    dom = max(stage_ms, key=stage_ms.get)
+    roof = None
+    if dom == "sample":
+        peak = fp32_peak_tflops(sm_max)
+        ach = metropolis_flops(w) / (stage_ms["sample"] / 1e3) / 1e12
+        roof = {"kernel": "metropolis_kernel", "bound": "alu", "achieved": round(ach, 3),
+                "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                "traffic": None,
+                "peak_source": f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (max clock of "
+                               f"{pk_kind} peaks file)"}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None}
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded RBM parameters N(0,0.01^2), random S^z=0 chain starts)",
+        "config": {"workload": w.name, "n": w.n, "m": w.m, "complex": w.is_complex,
+                   "chains": w.n_chains, "samples_per_chain": w.samples_per_chain,
+                   "burn_in_sweeps": w.n_discard, "samples_per_iter": w.n_samples,
+                   "moves": w.move, "n_cg": w.n_cg, "diag_shift": w.diag_shift, "lr": w.lr,
+                   "prec": prec_name, "l2": "inputs larger than L2 (T = tanh theta is 839 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "sr_steps_per_s": round(1e3 / ms_per_step, 4),
+        "stage_ms": {k: round(x, 3) for k, x in stage_ms.items()},
+        "fp32_path_samples_per_s": None if fp32_arm is None else round(fp32_arm, 2),
+        "acceptance": round(info["acceptance"], 4), "energy": info["energy"],
+        "roofline": roof,
+        "e2e": {"value": round(world * w.n_samples / (e2e_ms / 1e3), 2), "unit": "samples/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nk.NK_INFO_LEN * 8},
+        "gpu_launches": v.launches_per_step() * args.steps,
+        "clocks": clk,
+    }
+    return rank, out
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        spec = json.loads(args.oracle_sample)
+        print(json.dumps(oracle_sample(spec["workload"], spec["n_chains"], spec["spc"],
+                                       spec["n_cg"])))
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    nc, spc, ncg = ORACLE_SAMPLE[args.workload]
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from paper_1904_00031_gb300 import workloads as W
+        w = W.workload(args.workload)
+        tot_s, tot_n = 0.0, 0
+        for k in range(args.warmup + args.steps):
+            r = run_oracle_subprocess(args.workload, nc, spc, ncg)
+            if k >= args.warmup:
+                tot_s += r["seconds"]
+                tot_n += r["samples"]
+        val = tot_n / tot_s
+        sample = (f"{nc} chains x ({spc} samples + 1 burn-in sweep) of the {w.name} workload, "
+                  f"full oracle iteration incl. {ncg} CG iterations, per step")
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "samples/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * tot_s / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "oracle_sample": sample},
+            "cpu_baseline": {"value": round(val, 4), "unit": "samples/s", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(val, 4), "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }))
+        return
+    base = None
+    if rank == 0 and world == 1 and not args.no_baseline:
+        # before any CUDA call: the oracle runs in a fresh single-threaded process
+        r = run_oracle_subprocess(args.workload, nc, spc, ncg)
+        base = {"value": round(r["samples"] / r["seconds"], 4), "unit": "samples/s", "cores": 1,
+                "kind": "oracle",
+                "sample": f"{nc} chains x ({spc} samples + 1 burn-in sweep), one full oracle "
+                          f"VMC+SR iteration ({ncg} CG iterations), {r['seconds']:.1f} s"}
+    rank, out = run_gpu(args)
+    out["cpu_baseline"] = base
+    if rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

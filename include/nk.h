@@ -1,0 +1,235 @@
+/*
+ * nk.h -- C ABI of the GB300 (sm_103a) RBM variational Monte Carlo + stochastic
+ * reconfiguration hot path, after NetKet (Carleo et al., arXiv:1904.00031).
+ *
+ * Conventions (apply to every entry point unless stated otherwise)
+ * ---------------------------------------------------------------
+ * - Pointers are DEVICE pointers, allocated and owned by the caller.  The
+ *   library never allocates or frees device memory and never synchronises the
+ *   stream inside a call (nk_operator_upload is the one exception and says so).
+ * - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *   stream).  Argument errors are detected on the host and returned
+ *   synchronously, with nothing enqueued.  A kernel launch failure returns
+ *   NK_ERR_CUDA.  nk_last_error() gives a message for the calling thread.
+ * - Spin configurations sigma in {+1,-1}^N are int8, row-major [rows][n].
+ *   +1 is spin up.  The local basis index of a spin is idx(+1)=0, idx(-1)=1.
+ * - Complex numbers are interleaved (re, im): "c128" = 2 doubles, "c64" = 2
+ *   floats.  "F32" below means float for a real RBM and c64 for a complex one;
+ *   "F64" means double / c128 likewise.
+ * - RBM (Sec. 2.2.2, RbmSpin): ln psi(sigma) = sum_i a_i sigma_i
+ *   + sum_j ln cosh(theta_j), theta = W sigma + b, W row-major [m][n].  No
+ *   constant M ln 2 is added.
+ * - Parameter vectors (gradients, SR directions) are ordered (a, b, W
+ *   row-major), length P = n + m + n*m, F64.
+ */
+#ifndef NK_H
+#define NK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t nk_status;
+#define NK_OK 0
+#define NK_ERR_INVALID_ARG 1   /* NULL pointer, negative size, unknown enum   */
+#define NK_ERR_SHAPE 2         /* sizes outside the supported range            */
+#define NK_ERR_CUDA 3          /* a CUDA runtime call or launch failed         */
+#define NK_ERR_NOT_CONVERGED 4 /* (info flag) CG stopped at n_cg above cg_rtol */
+#define NK_ERR_NONFINITE 5     /* (info flag) NaN/Inf met in E_loc or CG       */
+#define NK_ERR_TIMEOUT 6       /* a bounded device-side wait gave up           */
+#define NK_ERR_UNSUPPORTED 7   /* valid request this build does not implement  */
+
+/* Arithmetic of the dense contractions (theta GEMM, SR matvec, backward). */
+#define NK_PREC_FP32 0   /* FP32 FMA on the CUDA cores ("plain FP32 path")          */
+#define NK_PREC_BF16X2 1 /* tensor cores (tcgen05), operand split into BF16 hi + lo,
+                            sigma exact in BF16, FP32 accumulation in TMEM        */
+
+#define NK_MOVE_FLIP 0     /* single-spin flip at a uniformly random site          */
+#define NK_MOVE_EXCHANGE 1 /* swap of the two spins of a uniformly random bond     */
+
+#define NK_LAYOUT_FACTORED 0 /* O as T = tanh(theta) F32 [ns][m]; O_a = sigma,
+                                O_W = T (x) sigma are implied                       */
+#define NK_LAYOUT_DENSE 1    /* O as F32 [ns][P]                                    */
+
+/* Size limits of this build. */
+#define NK_MAX_N 4096      /* sites                                               */
+#define NK_MAX_M 8192      /* hidden units (kernels hold tanh(theta) in registers) */
+#define NK_MAX_GROUP 32    /* chains sharing one proposal stream (one CTA)         */
+
+/* An RBM: FP64 master parameters plus the FP32 planes derived from them. */
+typedef struct nk_rbm {
+  int32_t n;          /* visible units (sites), 1..NK_MAX_N                         */
+  int32_t m;          /* hidden units, 1..NK_MAX_M                                  */
+  int32_t is_complex; /* 0: parameters in R, 1: in C                                */
+  int32_t reserved;
+  double* a;          /* F64 [n]    (device)                                        */
+  double* b;          /* F64 [m]    (device)                                        */
+  double* w;          /* F64 [m][n] (device, row-major)                             */
+  void* ws;           /* derived planes, nk_rbm_workspace_bytes() bytes, 256-B
+                         aligned (device); filled by nk_rbm_prepare              */
+  size_t ws_bytes;
+} nk_rbm;
+
+/* Persistent Markov chains. */
+typedef struct nk_chains {
+  int32_t nc;         /* number of chains                                           */
+  int32_t group_size; /* chains per proposal group, 1..NK_MAX_GROUP                 */
+  int8_t* sigma;      /* int8 [nc][n] current states (device, updated in place)     */
+  uint64_t seed;      /* Philox4x32-10 key                                          */
+  uint64_t counter;   /* proposals made so far by each chain (host; advanced by
+                         nk_metropolis_sweep)                                      */
+} nk_chains;
+
+/* A Hamiltonian as 1-local site terms and 2-local bond terms (GraphOperator,
+ * Sec. 2.2.1).  HOST memory.  Site term t acts on site_idx[t] with the 2x2 c128
+ * matrix site_mat[t][idx(s)][idx(s')] = <s|O|s'>; bond term t acts on
+ * (bond_i[t], bond_k[t]) with the 4x4 c128 matrix bond_mat[t][r][c], r,c =
+ * 2*idx(s_i) + idx(s_k). */
+typedef struct nk_operator {
+  int32_t n;
+  int32_t n_site_terms;
+  const int32_t* site_idx; /* [n_site_terms]          */
+  const double* site_mat;  /* [n_site_terms][2][2][2] */
+  int32_t n_bond_terms;
+  int32_t reserved;
+  const int32_t* bond_i;   /* [n_bond_terms]          */
+  const int32_t* bond_k;   /* [n_bond_terms]          */
+  const double* bond_mat;  /* [n_bond_terms][4][4][2] */
+} nk_operator;
+
+/* Layout of the nk_sr_step info block (device, NK_INFO_LEN doubles). */
+#define NK_INFO_E_RE 0     /* Re <E_loc>                                     */
+#define NK_INFO_E_IM 1     /* Im <E_loc>                                     */
+#define NK_INFO_VAR 2      /* <|E_loc - <E_loc>|^2>                          */
+#define NK_INFO_ERR 3      /* error bar from chain means (0 with weights)    */
+#define NK_INFO_CG_ITERS 4 /* CG iterations run                              */
+#define NK_INFO_CG_RESID 5 /* final ||r|| / ||F||                            */
+#define NK_INFO_F_NORM 6   /* ||F||                                          */
+#define NK_INFO_FLAGS 7    /* bit (1<<NK_ERR_NOT_CONVERGED), (1<<NK_ERR_NONFINITE) */
+#define NK_INFO_LEN 8
+
+/* ---------------------------------------------------------------- library */
+
+/* Human-readable name of a status code (static string). */
+const char* nk_status_string(nk_status s);
+/* Message describing the last error returned to the calling thread. */
+const char* nk_last_error(void);
+/* 1 if the library was compiled for sm_103a and a device of that kind is
+ * current; 0 otherwise (no error is raised). */
+int32_t nk_device_supported(void);
+
+/* ---------------------------------------------------------------- RBM */
+
+/* Bytes of the derived-plane workspace of an (n, m, is_complex) RBM. */
+size_t nk_rbm_workspace_bytes(int32_t n, int32_t m, int32_t is_complex);
+
+/* Refresh the derived planes from the FP64 master (a, b, W): FP32 copies of
+ * a, b and W^T, the tables cosh(2 W), sinh(2 W) used by the amplitude-ratio
+ * kernels, and the BF16 hi/lo planes of the tensor-core path.  Must be called
+ * after any change of the master parameters (nk_sr_step calls it itself). */
+nk_status nk_rbm_prepare(const nk_rbm* rbm, void* stream);
+
+/* ln psi(sigma) for ns configurations (Sec. 2.2.2).
+ *   sigma      int8 [ns][n]
+ *   prec       NK_PREC_FP32 or NK_PREC_BF16X2 (theta = W sigma + b contraction)
+ *   logpsi_out c128 [ns]
+ *   theta_out  F32 [ns][m] theta of every configuration, or NULL
+ * ns = 0 is a no-op. */
+nk_status nk_rbm_logpsi(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int32_t prec,
+                        double* logpsi_out, void* theta_out, void* stream);
+
+/* ---------------------------------------------------------------- sampling */
+
+/* Metropolis sampling of |psi|^2 (Eq. 4; Sec. 2.2.5), single-spin-flip or
+ * nearest-neighbour exchange moves (the MetropolisExchange of the VMC listing,
+ * Sec. 3.1).  Every chain runs n_discard + n_samples_per_chain sweeps of n
+ * proposals and records its state after each of the last n_samples_per_chain
+ * sweeps.  The proposal of step t for the chains of group g = c / group_size is
+ * drawn from Philox4x32-10 stream (g, t, "SITE"); the accept uniform of chain c
+ * from (c, t, "ACCP") (key = seed).  An exchange of two equal spins is a null
+ * move and is rejected.  Accept iff U < exp(2 Re(ln psi' - ln psi)) (FP64 test).
+ *   bond_i, bond_k  int32 [n_bonds] exchange bonds (ignored for FLIP; may be NULL)
+ *   samples_out     int8 [nc * n_samples_per_chain][n], chain-major
+ *                   (row c * n_samples_per_chain + s)
+ *   n_accept_out    uint64 [nc] accepted proposals per chain in this call, or NULL
+ * chains->sigma is updated in place and chains->counter advanced by
+ * (n_discard + n_samples_per_chain) * n on success. */
+nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move,
+                              const int32_t* bond_i, const int32_t* bond_k, int32_t n_bonds,
+                              int32_t n_discard, int32_t n_samples_per_chain,
+                              int8_t* samples_out, uint64_t* n_accept_out, void* stream);
+
+/* ---------------------------------------------------------------- operators */
+
+/* Bytes of the compiled device form of a host operator description. */
+size_t nk_operator_bytes(const nk_operator* op);
+/* Compile the operator (merge terms into diagonal tables and a list of
+ * distinct one- and two-spin moves with sigma-dependent matrix elements) and
+ * copy it to `dev` (nk_operator_bytes(op) bytes).  Unlike the other calls this
+ * one SYNCHRONISES `stream` before returning (it stages through host memory). */
+nk_status nk_operator_upload(const nk_operator* op, void* dev, size_t bytes, void* stream);
+
+/* ---------------------------------------------------------------- estimators */
+
+/* Local energies E_loc(sigma) = sum_sigma' <sigma|H|sigma'> psi(sigma')/psi(sigma)
+ * (Eq. 5, Sec. 2.2.5), with every psi ratio from the exact theta update.
+ *   op_dev   compiled operator (nk_operator_upload)
+ *   sigma    int8 [ns][n];   theta F32 [ns][m] (from nk_rbm_logpsi)
+ *   eloc_out c128 [ns]
+ *   t_out    F32 [ns][m] tanh(theta) (the factored log-derivatives), or NULL */
+nk_status nk_local_energy(const nk_rbm* rbm, const void* op_dev, const int8_t* sigma,
+                          const void* theta, int64_t ns, double* eloc_out, void* t_out,
+                          void* stream);
+
+/* Log-derivatives O_k = d ln psi / d alpha_k (Sec. 2.2.5, analytic for the RBM):
+ * O_a = sigma, O_b = tanh(theta), O_W = tanh(theta) (x) sigma.
+ *   layout NK_LAYOUT_FACTORED: o_out = T F32 [ns][m]
+ *          NK_LAYOUT_DENSE:    o_out = O F32 [ns][P] */
+nk_status nk_logderiv(const nk_rbm* rbm, const int8_t* sigma, const void* theta, int64_t ns,
+                      int32_t layout, void* o_out, void* stream);
+
+/* ---------------------------------------------------------------- SR */
+
+/* Scratch bytes nk_sr_step / nk_rbm_logpsi_backward need for ns samples. */
+size_t nk_sr_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns);
+
+/* One stochastic-reconfiguration step (Sec. 2.2.5; SGD rule Eq. 2):
+ *   <X> = sum_s w_s X_s, w = weights (double [ns]) or 1/ns when NULL,
+ *   F = <O^* E_loc> - <O^*><E_loc>,
+ *   (S + diag_shift I) delta = F with S x = <O^* (O x)> - <O^*>(<O> x), S never
+ *   formed: conjugate gradient from x0 = 0, n_cg iterations unless
+ *   ||r|| <= cg_rtol ||F|| first (decided on the device, no host sync),
+ *   then alpha <- alpha - lr delta in the FP64 master and nk_rbm_prepare.
+ * Real RBMs use Re S and Re F.  Samples are chain-major over n_chains chains
+ * (for the error bar).  CG vectors and all reductions are FP64; the O and O^H
+ * contractions run at `prec`.
+ *   t        F32 [ns][m] tanh(theta) (nk_local_energy t_out or nk_logderiv)
+ *   eloc     c128 [ns]
+ *   info_out double [NK_INFO_LEN] (device)
+ *   scratch  nk_sr_scratch_bytes(n, m, is_complex, ns) bytes, 256-B aligned */
+nk_status nk_sr_step(nk_rbm* rbm, const int8_t* sigma, const void* t, const double* eloc,
+                     const double* weights, int64_t ns, int32_t n_chains, double diag_shift,
+                     double lr, int32_t n_cg, double cg_rtol, int32_t prec, void* scratch,
+                     size_t scratch_bytes, double* info_out, void* stream);
+
+/* Scratch bytes nk_rbm_logpsi_backward needs for ns samples. */
+size_t nk_backward_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns);
+
+/* Backward of ln psi (the analytic derivatives of Sec. 2.2.5 contracted with
+ * an upstream gradient): grad_k = sum_s conj(O_sk) g_s (PyTorch's convention
+ * for a holomorphic function), theta recomputed from sigma.
+ *   g           c128 [ns]
+ *   grad_out    F64 [P]
+ *   scratch     nk_backward_scratch_bytes(n, m, is_complex, ns) bytes, 256-B
+ *               aligned (holds theta and tanh(theta) of the ns configurations) */
+nk_status nk_rbm_logpsi_backward(const nk_rbm* rbm, const int8_t* sigma, int64_t ns,
+                                 const double* g, double* grad_out, int32_t prec, void* scratch,
+                                 size_t scratch_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NK_H */

@@ -1,0 +1,330 @@
+// The C ABI (include/nk.h): argument validation, operator compilation and
+// dispatch to the kernels.  No device memory is allocated here.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "opdev.h"
+
+namespace nk {
+
+static thread_local char g_err[512] = "";
+
+nk_status fail(nk_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+nk_status check_launch(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(NK_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+  return NK_OK;
+}
+
+static nk_status check_rbm(const nk_rbm* r, const char* who) {
+  if (!r) return fail(NK_ERR_INVALID_ARG, "%s: rbm is NULL", who);
+  if (r->n < 1 || r->n > NK_MAX_N || r->m < 1 || r->m > NK_MAX_M)
+    return fail(NK_ERR_SHAPE, "%s: n = %d, m = %d outside [1, %d] x [1, %d]", who, r->n, r->m,
+                NK_MAX_N, NK_MAX_M);
+  if (r->is_complex != 0 && r->is_complex != 1)
+    return fail(NK_ERR_INVALID_ARG, "%s: is_complex must be 0 or 1", who);
+  if (!r->a || !r->b || !r->w || !r->ws)
+    return fail(NK_ERR_INVALID_ARG, "%s: NULL parameter or workspace pointer", who);
+  size_t need = WsLayout(r->n, r->m, r->is_complex).total;
+  if (r->ws_bytes < need)
+    return fail(NK_ERR_SHAPE, "%s: workspace of %zu B, need %zu B", who, r->ws_bytes, need);
+  if (((uintptr_t)r->ws) & 255)
+    return fail(NK_ERR_INVALID_ARG, "%s: workspace not 256-byte aligned", who);
+  return NK_OK;
+}
+
+// ------------------------------------------------------------------ operator compilation
+
+struct Compiled {
+  std::vector<OpDSite> ds;
+  std::vector<OpDBond> db;
+  std::vector<OpMove> mv;
+};
+
+static bool nz(const double* c) { return c[0] != 0.0 || c[1] != 0.0; }
+
+static nk_status compile_op(const nk_operator* op, Compiled& out) {
+  if (!op) return fail(NK_ERR_INVALID_ARG, "operator is NULL");
+  if (op->n < 1 || op->n > NK_MAX_N || op->n_site_terms < 0 || op->n_bond_terms < 0)
+    return fail(NK_ERR_SHAPE, "operator: bad sizes");
+  if ((op->n_site_terms && (!op->site_idx || !op->site_mat)) ||
+      (op->n_bond_terms && (!op->bond_i || !op->bond_k || !op->bond_mat)))
+    return fail(NK_ERR_INVALID_ARG, "operator: NULL table");
+  // moves keyed by (i, k, two); mel indexed 2 idx(s_i) + idx(s_k)
+  std::map<std::tuple<int, int, int>, OpMove> moves;
+  auto add = [&](int i, int k, int two, int x, const double* v) {
+    auto key = std::make_tuple(i, k, two);
+    auto it = moves.find(key);
+    if (it == moves.end()) {
+      OpMove mvv;
+      memset(&mvv, 0, sizeof(mvv));
+      mvv.i = i;
+      mvv.k = k;
+      mvv.two = two;
+      it = moves.emplace(key, mvv).first;
+    }
+    it->second.mel[x][0] += v[0];
+    it->second.mel[x][1] += v[1];
+  };
+  for (int t = 0; t < op->n_site_terms; ++t) {
+    int i = op->site_idx[t];
+    if (i < 0 || i >= op->n) return fail(NK_ERR_SHAPE, "operator: site index %d out of range", i);
+    const double* M = op->site_mat + 8 * t;  // [2][2][2]
+    OpDSite d;
+    memset(&d, 0, sizeof(d));
+    d.i = i;
+    for (int x = 0; x < 2; ++x) {
+      d.d[x][0] = M[(x * 2 + x) * 2];
+      d.d[x][1] = M[(x * 2 + x) * 2 + 1];
+    }
+    out.ds.push_back(d);
+    // flip of site i: from idx 0 (up) -> element M[0][1]; from idx 1 -> M[1][0]
+    if (nz(M + (0 * 2 + 1) * 2)) add(i, i, 0, 0, M + (0 * 2 + 1) * 2);
+    if (nz(M + (1 * 2 + 0) * 2)) add(i, i, 0, 3, M + (1 * 2 + 0) * 2);
+  }
+  for (int t = 0; t < op->n_bond_terms; ++t) {
+    int i = op->bond_i[t], k = op->bond_k[t];
+    if (i < 0 || i >= op->n || k < 0 || k >= op->n || i == k)
+      return fail(NK_ERR_SHAPE, "operator: bond (%d, %d) invalid", i, k);
+    const double* M = op->bond_mat + 32 * t;  // [4][4][2]
+    OpDBond d;
+    memset(&d, 0, sizeof(d));
+    d.i = i;
+    d.k = k;
+    for (int x = 0; x < 4; ++x) {
+      d.d[x][0] = M[(x * 4 + x) * 2];
+      d.d[x][1] = M[(x * 4 + x) * 2 + 1];
+    }
+    out.db.push_back(d);
+    for (int row = 0; row < 4; ++row) {
+      for (int col = 0; col < 4; ++col) {
+        if (row == col) continue;
+        const double* v = M + (row * 4 + col) * 2;
+        if (!nz(v)) continue;
+        int ri = row >> 1, rk = row & 1, ci = col >> 1, ck = col & 1;
+        if (ri != ci && rk != ck) add(i, k, 1, row, v);
+        else if (ri != ci) add(i, k, 0, 2 * ri + rk, v);      // flip i, context k
+        else add(k, i, 0, 2 * rk + ri, v);                     // flip k, context i
+      }
+    }
+  }
+  for (auto& kv : moves) {
+    const OpMove& m = kv.second;
+    bool any = false;
+    for (int x = 0; x < 4; ++x) any |= nz(m.mel[x]);
+    if (any) out.mv.push_back(m);
+  }
+  return NK_OK;
+}
+
+static size_t layout_sizes(const Compiled& c, int32_t* off_ds, int32_t* off_db, int32_t* off_mv) {
+  size_t off = round_up(sizeof(OpDevHeader), 16);
+  *off_ds = (int32_t)off;
+  off += round_up(c.ds.size() * sizeof(OpDSite), 16);
+  *off_db = (int32_t)off;
+  off += round_up(c.db.size() * sizeof(OpDBond), 16);
+  *off_mv = (int32_t)off;
+  off += round_up(c.mv.size() * sizeof(OpMove), 16);
+  return off;
+}
+
+}  // namespace nk
+
+using namespace nk;
+
+extern "C" {
+
+const char* nk_status_string(nk_status s) {
+  switch (s) {
+    case NK_OK: return "ok";
+    case NK_ERR_INVALID_ARG: return "invalid argument";
+    case NK_ERR_SHAPE: return "unsupported shape";
+    case NK_ERR_CUDA: return "CUDA error";
+    case NK_ERR_NOT_CONVERGED: return "not converged";
+    case NK_ERR_NONFINITE: return "non-finite value";
+    case NK_ERR_TIMEOUT: return "device wait timed out";
+    case NK_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* nk_last_error(void) { return g_err; }
+
+int32_t nk_device_supported(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (p.major == 10 && p.minor == 3) ? 1 : 0;
+}
+
+size_t nk_rbm_workspace_bytes(int32_t n, int32_t m, int32_t is_complex) {
+  if (n < 1 || m < 1) return 0;
+  return WsLayout(n, m, is_complex ? 1 : 0).total;
+}
+
+nk_status nk_rbm_prepare(const nk_rbm* rbm, void* stream) {
+  if (nk_status e = check_rbm(rbm, "nk_rbm_prepare")) return e;
+  return launch_prepare(rbm, (cudaStream_t)stream);
+}
+
+nk_status nk_rbm_logpsi(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int32_t prec,
+                        double* logpsi_out, void* theta_out, void* stream) {
+  if (nk_status e = check_rbm(rbm, "nk_rbm_logpsi")) return e;
+  if (ns < 0) return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi: ns < 0");
+  if (ns == 0) return NK_OK;
+  if (!sigma || !logpsi_out) return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi: NULL pointer");
+  if (prec == NK_PREC_FP32)
+    return launch_logpsi_fp32(rbm, sigma, ns, logpsi_out, theta_out, (cudaStream_t)stream);
+  if (prec == NK_PREC_BF16X2)
+    return launch_logpsi_bf16(rbm, sigma, ns, logpsi_out, theta_out, (cudaStream_t)stream);
+  return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi: unknown precision %d", prec);
+}
+
+nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move,
+                              const int32_t* bond_i, const int32_t* bond_k, int32_t n_bonds,
+                              int32_t n_discard, int32_t n_samples_per_chain,
+                              int8_t* samples_out, uint64_t* n_accept_out, void* stream) {
+  if (nk_status e = check_rbm(rbm, "nk_metropolis_sweep")) return e;
+  if (!chains || !chains->sigma)
+    return fail(NK_ERR_INVALID_ARG, "nk_metropolis_sweep: NULL chains");
+  if (chains->nc < 0 || n_discard < 0 || n_samples_per_chain < 0)
+    return fail(NK_ERR_INVALID_ARG, "nk_metropolis_sweep: negative size");
+  if (chains->group_size < 1 || chains->group_size > NK_MAX_GROUP)
+    return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: group_size %d outside [1, %d]",
+                chains->group_size, NK_MAX_GROUP);
+  if (move != NK_MOVE_FLIP && move != NK_MOVE_EXCHANGE)
+    return fail(NK_ERR_INVALID_ARG, "nk_metropolis_sweep: unknown move %d", move);
+  if (move == NK_MOVE_EXCHANGE && (n_bonds < 1 || !bond_i || !bond_k))
+    return fail(NK_ERR_INVALID_ARG, "nk_metropolis_sweep: exchange moves need a bond list");
+  if (n_samples_per_chain > 0 && !samples_out)
+    return fail(NK_ERR_INVALID_ARG, "nk_metropolis_sweep: NULL samples_out");
+  if (chains->nc == 0 || n_discard + n_samples_per_chain == 0) return NK_OK;
+  nk_status e = launch_metropolis(rbm, chains, move, bond_i, bond_k, n_bonds, n_discard,
+                                  n_samples_per_chain, samples_out, n_accept_out,
+                                  (cudaStream_t)stream);
+  if (e == NK_OK) chains->counter += (uint64_t)(n_discard + n_samples_per_chain) * rbm->n;
+  return e;
+}
+
+size_t nk_operator_bytes(const nk_operator* op) {
+  Compiled c;
+  if (compile_op(op, c) != NK_OK) return 0;
+  int32_t a, b, d;
+  return layout_sizes(c, &a, &b, &d);
+}
+
+nk_status nk_operator_upload(const nk_operator* op, void* dev, size_t bytes, void* stream) {
+  Compiled c;
+  if (nk_status e = compile_op(op, c)) return e;
+  if (!dev) return fail(NK_ERR_INVALID_ARG, "nk_operator_upload: NULL destination");
+  OpDevHeader h;
+  memset(&h, 0, sizeof(h));
+  h.n = op->n;
+  h.n_dsite = (int32_t)c.ds.size();
+  h.n_dbond = (int32_t)c.db.size();
+  h.n_moves = (int32_t)c.mv.size();
+  size_t total = layout_sizes(c, &h.off_dsite, &h.off_dbond, &h.off_moves);
+  if (bytes < total)
+    return fail(NK_ERR_SHAPE, "nk_operator_upload: %zu B given, %zu B needed", bytes, total);
+  std::vector<char> buf(total, 0);
+  memcpy(buf.data(), &h, sizeof(h));
+  if (!c.ds.empty()) memcpy(buf.data() + h.off_dsite, c.ds.data(), c.ds.size() * sizeof(OpDSite));
+  if (!c.db.empty()) memcpy(buf.data() + h.off_dbond, c.db.data(), c.db.size() * sizeof(OpDBond));
+  if (!c.mv.empty()) memcpy(buf.data() + h.off_moves, c.mv.data(), c.mv.size() * sizeof(OpMove));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(dev, buf.data(), total, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(NK_ERR_CUDA, "nk_operator_upload: %s", cudaGetErrorString(cudaGetLastError()));
+  return NK_OK;
+}
+
+nk_status nk_local_energy(const nk_rbm* rbm, const void* op_dev, const int8_t* sigma,
+                          const void* theta, int64_t ns, double* eloc_out, void* t_out,
+                          void* stream) {
+  if (nk_status e = check_rbm(rbm, "nk_local_energy")) return e;
+  if (ns < 0) return fail(NK_ERR_INVALID_ARG, "nk_local_energy: ns < 0");
+  if (ns == 0) return NK_OK;
+  if (!op_dev || !sigma || !theta || !eloc_out)
+    return fail(NK_ERR_INVALID_ARG, "nk_local_energy: NULL pointer");
+  return launch_local_energy(rbm, op_dev, sigma, theta, ns, eloc_out, t_out, (cudaStream_t)stream);
+}
+
+nk_status nk_logderiv(const nk_rbm* rbm, const int8_t* sigma, const void* theta, int64_t ns,
+                      int32_t layout, void* o_out, void* stream) {
+  if (nk_status e = check_rbm(rbm, "nk_logderiv")) return e;
+  if (ns < 0) return fail(NK_ERR_INVALID_ARG, "nk_logderiv: ns < 0");
+  if (layout != NK_LAYOUT_FACTORED && layout != NK_LAYOUT_DENSE)
+    return fail(NK_ERR_INVALID_ARG, "nk_logderiv: unknown layout %d", layout);
+  if (ns == 0) return NK_OK;
+  if (!sigma || !theta || !o_out) return fail(NK_ERR_INVALID_ARG, "nk_logderiv: NULL pointer");
+  return launch_logderiv(rbm, sigma, theta, ns, layout, o_out, (cudaStream_t)stream);
+}
+
+size_t nk_sr_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns) {
+  if (n < 1 || m < 1 || ns < 0) return 0;
+  return sr_scratch_bytes(n, m, is_complex ? 1 : 0, ns);
+}
+
+size_t nk_backward_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns) {
+  if (n < 1 || m < 1 || ns < 0) return 0;
+  return backward_scratch_bytes(n, m, is_complex ? 1 : 0, ns);
+}
+
+nk_status nk_sr_step(nk_rbm* rbm, const int8_t* sigma, const void* t, const double* eloc,
+                     const double* weights, int64_t ns, int32_t n_chains, double diag_shift,
+                     double lr, int32_t n_cg, double cg_rtol, int32_t prec, void* scratch,
+                     size_t scratch_bytes, double* info_out, void* stream) {
+  if (nk_status e = check_rbm(rbm, "nk_sr_step")) return e;
+  if (ns < 1) return fail(NK_ERR_INVALID_ARG, "nk_sr_step: ns < 1");
+  if (!sigma || !t || !eloc || !scratch || !info_out)
+    return fail(NK_ERR_INVALID_ARG, "nk_sr_step: NULL pointer");
+  if (n_cg < 0 || !(diag_shift >= 0.0) || !(cg_rtol >= 0.0))
+    return fail(NK_ERR_INVALID_ARG, "nk_sr_step: negative n_cg, diag_shift or cg_rtol");
+  if (n_chains < 0 || (n_chains > 0 && ns % n_chains))
+    return fail(NK_ERR_SHAPE, "nk_sr_step: ns = %lld not a multiple of n_chains = %d",
+                (long long)ns, n_chains);
+  if (((uintptr_t)scratch) & 255)
+    return fail(NK_ERR_INVALID_ARG, "nk_sr_step: scratch not 256-byte aligned");
+  if (prec != NK_PREC_FP32 && prec != NK_PREC_BF16X2)
+    return fail(NK_ERR_INVALID_ARG, "nk_sr_step: unknown precision %d", prec);
+  return run_sr_step(rbm, sigma, t, eloc, weights, ns, n_chains, diag_shift, lr, n_cg, cg_rtol,
+                     prec, scratch, scratch_bytes, info_out, (cudaStream_t)stream);
+}
+
+nk_status nk_rbm_logpsi_backward(const nk_rbm* rbm, const int8_t* sigma, int64_t ns,
+                                 const double* g, double* grad_out, int32_t prec, void* scratch,
+                                 size_t scratch_bytes, void* stream) {
+  if (nk_status e = check_rbm(rbm, "nk_rbm_logpsi_backward")) return e;
+  if (ns < 1) return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi_backward: ns < 1");
+  if (!sigma || !g || !grad_out || !scratch)
+    return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi_backward: NULL pointer");
+  if (((uintptr_t)scratch) & 255)
+    return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi_backward: scratch not 256-byte aligned");
+  if (prec != NK_PREC_FP32 && prec != NK_PREC_BF16X2)
+    return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi_backward: unknown precision %d", prec);
+  return run_backward(rbm, sigma, ns, g, grad_out, prec, scratch, scratch_bytes,
+                      (cudaStream_t)stream);
+}
+
+}  // extern "C"

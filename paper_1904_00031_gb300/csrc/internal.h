@@ -1,0 +1,62 @@
+// Internal declarations shared by the nk library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "nk.h"
+
+namespace nk {
+
+// Record an error message for nk_last_error() and return `s`.
+nk_status fail(nk_status s, const char* fmt, ...);
+// NK_ERR_CUDA with the pending launch error, or NK_OK.
+nk_status check_launch(const char* where);
+
+nk_status launch_prepare(const nk_rbm* r, cudaStream_t st);
+
+// theta = W sigma + b and ln psi; theta_out may be null.
+nk_status launch_logpsi_fp32(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,
+                             void* theta_out, cudaStream_t st);
+nk_status launch_logpsi_bf16(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,
+                             void* theta_out, cudaStream_t st);
+
+nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int32_t* bi,
+                            const int32_t* bk, int nb, int n_discard, int n_samples,
+                            int8_t* samples, uint64_t* n_acc, cudaStream_t st);
+
+nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, const int8_t* sigma,
+                              const void* theta, int64_t ns, double* eloc, void* t_out,
+                              cudaStream_t st);
+nk_status launch_logderiv(const nk_rbm* r, const int8_t* sigma, const void* theta, int64_t ns,
+                          int layout, void* o_out, cudaStream_t st);
+
+// ------------------------------------------------------------------ SR
+// The SR algebra runs on "augmented" matrices: T' = [T | 1] (ns x (m+1)) and
+// sigma' = [sigma | 1] (ns x (n+1)); a parameter-space vector is held as an
+// (m+1) x (n+1) row-major array X' with X'[j][i] = x_W[j][i], X'[j][n] = x_b[j],
+// X'[m][i] = x_a[i], X'[m][n] = 0.  Then O_s . x = sum_j T'_sj (X' sigma'_s)_j and
+// sum_s conj(O_s) v_s = T'^H diag(v) sigma'.
+struct SrLayout {
+  int n, m, cplx;
+  int64_t ns;
+  int ma, na;        // m + 1, n + 1
+  int64_t pa;        // ma * na
+  int splits;        // split-K factor of the adjoint contraction
+  size_t x, r, p, ap, xf, part, y, v, red, scal, total;
+  SrLayout(int n_, int m_, int cplx_, int64_t ns_);
+};
+
+size_t sr_scratch_bytes(int n, int m, int cplx, int64_t ns);
+size_t backward_scratch_bytes(int n, int m, int cplx, int64_t ns);
+nk_status run_sr_step(nk_rbm* r, const int8_t* sigma, const void* t, const double* eloc,
+                      const double* weights, int64_t ns, int n_chains, double diag_shift,
+                      double lr, int n_cg, double cg_rtol, int prec, void* scratch,
+                      size_t scratch_bytes, double* info, cudaStream_t st);
+nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const double* g,
+                       double* grad, int prec, void* scratch, size_t scratch_bytes,
+                       cudaStream_t st);
+
+}  // namespace nk

@@ -1,0 +1,96 @@
+// K1 (FP32 path): ln psi(sigma) = a . sigma + sum_j ln cosh(theta_j),
+// theta = W sigma + b (Sec. 2.2.2: RbmSpin; an RBM is a one-layer FFNN with
+// ln cosh activation).  theta is computed as the augmented contraction
+// [W | b] [sigma; 1] on the CUDA cores, ln cosh is fused into the epilogue and
+// summed per sample in FP64; a . sigma is added in FP64 from the master a.
+#include "common.cuh"
+#include "internal.h"
+#include "sgemm.cuh"
+
+namespace nk {
+
+template <bool CPLX>
+struct LogpsiEpi {
+  using F = typename SgTypes<CPLX>::F;
+  int m, n;
+  int64_t ns;
+  F* theta_out;            // [ns][m] or null
+  const double* a;         // master a (F64)
+  const int8_t* sigma;
+  double* logpsi;          // c128 [ns]
+
+  __device__ __forceinline__ void tile(float (&ar)[4][4], float (&ai)[4][4], int64_t sb, int jb,
+                                       double2 (&part)[4]) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      int64_t s = sb + p;
+      if (s >= ns) continue;
+      float lr = 0.f, li = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int j = jb + 16 * q;
+        if (j >= m) continue;
+        if constexpr (CPLX) {
+          cf l = lncosh_c(cf{ar[p][q], ai[p][q]});
+          lr += l.x;
+          li += l.y;
+          if (theta_out) theta_out[s * m + j] = make_float2(ar[p][q], ai[p][q]);
+        } else {
+          lr += lncosh_f(ar[p][q]);
+          if (theta_out) theta_out[s * m + j] = ar[p][q];
+        }
+      }
+      part[p].x += (double)lr;
+      part[p].y += (double)li;
+    }
+  }
+
+  __device__ __forceinline__ void finish(int64_t s, double2 v) {
+    double vr = 0.0, vi = 0.0;
+    const int8_t* sg = sigma + s * n;
+    for (int i = 0; i < n; ++i) {
+      double si = (double)sg[i];
+      if (CPLX) {
+        vr += a[2 * i] * si;
+        vi += a[2 * i + 1] * si;
+      } else {
+        vr += a[i] * si;
+      }
+    }
+    logpsi[2 * s] = v.x + vr;
+    logpsi[2 * s + 1] = v.y + vi;
+  }
+};
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kSgThreads) logpsi_fp32_kernel(const int8_t* __restrict__ sigma,
+                                                                 int64_t ns, int n, int m,
+                                                                 const void* __restrict__ xw,
+                                                                 int rows, const double* a,
+                                                                 double* logpsi, void* theta_out) {
+  LogpsiEpi<CPLX> epi;
+  epi.m = m;
+  epi.n = n;
+  epi.ns = ns;
+  epi.theta_out = reinterpret_cast<typename SgTypes<CPLX>::F*>(theta_out);
+  epi.a = a;
+  epi.sigma = sigma;
+  epi.logpsi = logpsi;
+  sgemm_rowreduce<CPLX>(sigma, ns, n, xw, rows, n + 1, epi);
+}
+
+nk_status launch_logpsi_fp32(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,
+                             void* theta_out, cudaStream_t st) {
+  WsLayout L(r->n, r->m, r->is_complex);
+  const char* ws = (const char*)r->ws;
+  int64_t blocks = (ns + kSgBS - 1) / kSgBS;
+  if (r->is_complex)
+    logpsi_fp32_kernel<true><<<(unsigned)blocks, kSgThreads, 0, st>>>(
+        sigma, ns, r->n, r->m, ws + L.xw, r->m, r->a, logpsi, theta_out);
+  else
+    logpsi_fp32_kernel<false><<<(unsigned)blocks, kSgThreads, 0, st>>>(
+        sigma, ns, r->n, r->m, ws + L.xw, r->m, r->a, logpsi, theta_out);
+  return check_launch("nk_rbm_logpsi");
+}
+
+}  // namespace nk

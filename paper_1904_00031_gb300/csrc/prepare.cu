@@ -1,0 +1,103 @@
+// K9: derived planes of an RBM from its FP64 master parameters.
+//
+// The ratio of amplitudes for flipping spin i (Sec. 2.2.5; RBM of Sec. 2.2.2) is
+//   psi(sigma')/psi(sigma) = exp(-2 a_i s) prod_j cosh(theta_j - 2 s W_ji)/cosh(theta_j)
+// with s = sigma_i, and cosh(theta - c)/cosh(theta) = cosh c - tanh(theta) sinh c.
+// The tables cosh(2 W_ji), sinh(2 W_ji) let the sampling and local-energy
+// kernels evaluate every factor with complex multiply-adds only.  They are
+// computed in FP64 and rounded once.
+#include "common.cuh"
+#include "internal.h"
+
+namespace nk {
+
+template <bool CPLX>
+__global__ void prepare_kernel(int n, int m, int mp, const double* __restrict__ a,
+                               const double* __restrict__ b, const double* __restrict__ w,
+                               char* __restrict__ ws, WsLayout L) {
+  const int64_t total = (int64_t)n * mp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / mp), j = (int)(e % mp);
+    double wr = 0.0, wi = 0.0;
+    if (j < m) {
+      if (CPLX) {
+        wr = w[2 * ((int64_t)j * n + i)];
+        wi = w[2 * ((int64_t)j * n + i) + 1];
+      } else {
+        wr = w[(int64_t)j * n + i];
+      }
+    }
+    double c2 = cosh(2.0 * wr), s2 = sinh(2.0 * wr);
+    if (CPLX) {
+      double cy = cos(2.0 * wi), sy = sin(2.0 * wi);
+      reinterpret_cast<float2*>(ws + L.wt)[e] = make_float2((float)wr, (float)wi);
+      // cosh(2w) = cosh 2x cos 2y + i sinh 2x sin 2y; sinh(2w) = sinh 2x cos 2y + i cosh 2x sin 2y
+      reinterpret_cast<float4*>(ws + L.tab)[e] =
+          make_float4((float)(c2 * cy), (float)(s2 * sy), (float)(s2 * cy), (float)(c2 * sy));
+    } else {
+      reinterpret_cast<float*>(ws + L.wt)[e] = (float)wr;
+      reinterpret_cast<float2*>(ws + L.tab)[e] = make_float2((float)c2, (float)s2);
+    }
+  }
+  // augmented row-major W | b, rows j < mp, columns i <= n (column n = b)
+  const int64_t total2 = (int64_t)mp * (n + 1);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total2;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int j = (int)(e / (n + 1)), i = (int)(e % (n + 1));
+    double vr = 0.0, vi = 0.0;
+    if (j < m) {
+      if (i < n) {
+        if (CPLX) {
+          vr = w[2 * ((int64_t)j * n + i)];
+          vi = w[2 * ((int64_t)j * n + i) + 1];
+        } else {
+          vr = w[(int64_t)j * n + i];
+        }
+      } else {
+        vr = CPLX ? b[2 * j] : b[j];
+        vi = CPLX ? b[2 * j + 1] : 0.0;
+      }
+    }
+    if (CPLX)
+      reinterpret_cast<float2*>(ws + L.xw)[e] = make_float2((float)vr, (float)vi);
+    else
+      reinterpret_cast<float*>(ws + L.xw)[e] = (float)vr;
+  }
+  const int64_t t3 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t3 < n) {
+    if (CPLX)
+      reinterpret_cast<float2*>(ws + L.a32)[t3] = make_float2((float)a[2 * t3], (float)a[2 * t3 + 1]);
+    else
+      reinterpret_cast<float*>(ws + L.a32)[t3] = (float)a[t3];
+  }
+  if (t3 < mp) {
+    double br = 0.0, bi = 0.0;
+    if (t3 < m) {
+      br = CPLX ? b[2 * t3] : b[t3];
+      bi = CPLX ? b[2 * t3 + 1] : 0.0;
+    }
+    if (CPLX)
+      reinterpret_cast<float2*>(ws + L.b32)[t3] = make_float2((float)br, (float)bi);
+    else
+      reinterpret_cast<float*>(ws + L.b32)[t3] = (float)br;
+  }
+}
+
+nk_status launch_prepare(const nk_rbm* r, cudaStream_t st) {
+  WsLayout L(r->n, r->m, r->is_complex);
+  int64_t work = (int64_t)L.mp * (r->n + 1);
+  int threads = 256;
+  int64_t blocks = (work + threads - 1) / threads;
+  int64_t minb = (std::max(L.mp, r->n) + threads - 1) / threads;
+  blocks = std::max<int64_t>(std::min<int64_t>(blocks, 152 * 8), minb);
+  if (r->is_complex)
+    prepare_kernel<true><<<(unsigned)blocks, threads, 0, st>>>(r->n, r->m, L.mp, r->a, r->b, r->w,
+                                                              (char*)r->ws, L);
+  else
+    prepare_kernel<false><<<(unsigned)blocks, threads, 0, st>>>(r->n, r->m, L.mp, r->a, r->b, r->w,
+                                                               (char*)r->ws, L);
+  return check_launch("nk_rbm_prepare");
+}
+
+}  // namespace nk

@@ -1,0 +1,683 @@
+// K5-K7: energy statistics and stochastic reconfiguration (Sec. 2.2.5; update
+// rule Eq. 2), and K8: the backward of ln psi.
+//
+// The SR system (S + eps I) delta = F is solved by conjugate gradient with S
+// never formed.  All algebra runs on "augmented" operands: T' = [T | 1],
+// sigma' = [sigma | 1], and a parameter vector as an (m+1) x (n+1) array X'
+// (X'[j][i] = x_W[j][i], X'[j][n] = x_b[j], X'[m][i] = x_a[i], X'[m][n] = 0):
+//   (O x)_s         = sum_j T'_sj (X' sigma'_s)_j           (forward contraction)
+//   sum_s conj(O_s) v_s = T'^H diag(v) sigma'               (adjoint contraction)
+//   S x             = adjoint(w o (O x - <O x>)),  <y> = sum_s w_s y_s.
+// The two contractions run at the requested precision (this file: FP32 CUDA
+// cores); CG vectors, inner products and every reduction are FP64, and every
+// reduction has a fixed order (no atomics), so a step is bitwise reproducible.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "sgemm.cuh"
+
+namespace nk {
+
+constexpr int kVecBlocks = 256;   // fixed grid of the CG vector kernels
+constexpr int kVecThreads = 256;
+constexpr int kAdjBK = 16;
+
+// scalars in the scratch `scal` block
+enum {
+  SC_RS0 = 0, SC_RS1 = 1,   // r^H r, double-buffered by iteration parity
+  SC_DONE = 2,              // converged flag
+  SC_ITERS = 3,             // completed iterations
+  SC_FNORM = 4,             // ||F||
+  SC_EBAR_RE = 5, SC_EBAR_IM = 6,
+  SC_NONFINITE = 7,
+  SC_LEN = 16
+};
+
+SrLayout::SrLayout(int n_, int m_, int cplx_, int64_t ns_) : n(n_), m(m_), cplx(cplx_), ns(ns_) {
+  ma = m + 1;
+  na = n + 1;
+  pa = (int64_t)ma * na;
+  int tiles = ceil_div(na, 64) * ceil_div(ma, 64);
+  int64_t sp = (2 * 152 + tiles - 1) / tiles;
+  sp = std::min<int64_t>(sp, std::max<int64_t>(1, ns / 256));
+  splits = (int)std::max<int64_t>(1, std::min<int64_t>(sp, 64));
+  size_t d = cplx ? 16 : 8;  // F64 element
+  size_t f = cplx ? 8 : 4;   // F32 element
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (size_t)round_up((int64_t)bytes, 256);
+    return o;
+  };
+  x = take(pa * d);
+  r = take(pa * d);
+  p = take(pa * d);
+  ap = take(pa * d);
+  xf = take(pa * f);
+  part = take((size_t)splits * pa * f);
+  y = take((size_t)std::max<int64_t>(ns, 1) * 16);
+  v = take((size_t)std::max<int64_t>(ns, 1) * 16);
+  red = take(4 * kVecBlocks * sizeof(double));
+  scal = take(SC_LEN * sizeof(double));
+  total = off;
+}
+
+size_t sr_scratch_bytes(int n, int m, int cplx, int64_t ns) {
+  return SrLayout(n, m, cplx, ns).total;
+}
+
+// ------------------------------------------------------------------ helpers
+
+template <bool CPLX>
+struct D;  // F64 element
+template <>
+struct D<true> {
+  using T = double2;
+  static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
+};
+template <>
+struct D<false> {
+  using T = double;
+  static __device__ __forceinline__ double zero() { return 0.0; }
+};
+
+__device__ __forceinline__ double re(double x) { return x; }
+__device__ __forceinline__ double re(double2 x) { return x.x; }
+__device__ __forceinline__ double norm2(double x) { return x * x; }
+__device__ __forceinline__ double norm2(double2 x) { return x.x * x.x + x.y * x.y; }
+__device__ __forceinline__ double cdot_re(double a, double b) { return a * b; }
+__device__ __forceinline__ double cdot_re(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
+__device__ __forceinline__ double axpy(double a, double x, double y) { return fma(a, x, y); }
+__device__ __forceinline__ double2 axpy(double a, double2 x, double2 y) {
+  return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
+}
+
+// Deterministic block reduction of one double (all threads get the result).
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[32];
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int u = 0; u < nw; ++u) t += sh[u];
+  return t;
+}
+
+// Sum of kVecBlocks partials in a fixed order (every block gets the same value).
+__device__ __forceinline__ double sum_partials(const double* red) {
+  __shared__ double tot;
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int u = threadIdx.x; u < kVecBlocks; u += 32) v += red[u];
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0) tot = v;
+  }
+  __syncthreads();
+  return tot;
+}
+
+// ------------------------------------------------------------------ K7 statistics
+
+// One CTA.  E = sum w E_s, var = sum w |E_s - E|^2, error from chain means;
+// writes v_s = w_s (E_s - E) (the vector whose adjoint contraction is F).
+template <bool CPLX>
+__global__ void __launch_bounds__(1024) stats_kernel(const double* __restrict__ eloc,
+                                                     const double* __restrict__ weights,
+                                                     int64_t ns, int n_chains, double* info,
+                                                     double* scal, void* vout) {
+  const double invn = 1.0 / (double)ns;
+  double sr = 0.0, si = 0.0;
+  for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) {
+    double w = weights ? weights[s] : invn;
+    sr += w * eloc[2 * s];
+    si += w * eloc[2 * s + 1];
+  }
+  const double er = block_sum(sr), ei = block_sum(si);
+  double vv = 0.0;
+  for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) {
+    double w = weights ? weights[s] : invn;
+    double dr = eloc[2 * s] - er, di = eloc[2 * s + 1] - ei;
+    vv += w * (dr * dr + di * di);
+    if (CPLX)
+      reinterpret_cast<double2*>(vout)[s] = make_double2(w * dr, w * di);
+    else
+      reinterpret_cast<double*>(vout)[s] = w * dr;
+  }
+  const double var = block_sum(vv);
+  double ce = 0.0;
+  const int64_t spc = n_chains > 0 ? ns / n_chains : 0;
+  if (!weights && n_chains > 1 && spc > 0) {
+    for (int c = threadIdx.x; c < n_chains; c += blockDim.x) {
+      double mc = 0.0;
+      for (int64_t u = 0; u < spc; ++u) mc += eloc[2 * (c * spc + u)];
+      mc /= (double)spc;
+      ce += (mc - er) * (mc - er);
+    }
+  }
+  ce = block_sum(ce);
+  if (threadIdx.x == 0) {
+    info[NK_INFO_E_RE] = er;
+    info[NK_INFO_E_IM] = ei;
+    info[NK_INFO_VAR] = var;
+    info[NK_INFO_ERR] =
+        (!weights && n_chains > 1 && spc > 0) ? sqrt(ce / ((double)n_chains * (n_chains - 1))) : 0.0;
+    scal[SC_EBAR_RE] = er;
+    scal[SC_EBAR_IM] = ei;
+    scal[SC_NONFINITE] = (isfinite(er) && isfinite(ei) && isfinite(var)) ? 0.0 : 1.0;
+  }
+}
+
+// ------------------------------------------------------------------ adjoint contraction
+// part[z][j][i] = sum_{s in split z} conj(T'_sj) v_s sigma'_si   (FP32 CUDA cores)
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256) adjoint_fp32_kernel(const int8_t* __restrict__ sigma,
+                                                           const void* __restrict__ Tv,
+                                                           const void* __restrict__ vv,
+                                                           int64_t ns, int n, int m, int64_t chunk,
+                                                           void* partv, const double* scal) {
+  if (scal && scal[SC_DONE] != 0.0) return;
+  using F = typename SgTypes<CPLX>::F;
+  const F* T = reinterpret_cast<const F*>(Tv);
+  const int ma = m + 1, na = n + 1;
+  __shared__ __align__(16) F Zs[kAdjBK][64];
+  __shared__ __align__(16) float Ss[kAdjBK][64];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+  const int64_t sb = (int64_t)blockIdx.z * chunk;
+  const int64_t se = std::min<int64_t>(ns, sb + chunk);
+  float ar[4][4], ai[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ar[p][q] = ai[p][q] = 0.f;
+  for (int64_t k0 = sb; k0 < se; k0 += kAdjBK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int e = tid + u * 256;
+      int kk = e >> 6, jj = e & 63;
+      int64_t s = k0 + kk;
+      int j = j0 + jj;
+      F z;
+      if constexpr (CPLX) {
+        z = make_float2(0.f, 0.f);
+        if (s < se && j <= m) {
+          float2 t = j < m ? T[s * m + j] : make_float2(1.f, 0.f);
+          double2 vs = reinterpret_cast<const double2*>(vv)[s];
+          float vr = (float)vs.x, vi = (float)vs.y;
+          // conj(t) * v
+          z = make_float2(t.x * vr + t.y * vi, t.x * vi - t.y * vr);
+        }
+      } else {
+        z = 0.f;
+        if (s < se && j <= m) {
+          float t = j < m ? T[s * m + j] : 1.f;
+          z = t * (float)reinterpret_cast<const double*>(vv)[s];
+        }
+      }
+      Zs[kk][jj] = z;
+      int ii = jj, i = i0 + ii;
+      float sv = 0.f;
+      if (s < se) sv = i < n ? (float)sigma[s * n + i] : (i == n ? 1.f : 0.f);
+      Ss[kk][ii] = sv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kAdjBK; ++kk) {
+      F z[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) z[p] = Zs[kk][ty * 4 + p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float sv = Ss[kk][tx + 16 * q];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          if constexpr (CPLX) {
+            ar[p][q] = fmaf(z[p].x, sv, ar[p][q]);
+            ai[p][q] = fmaf(z[p].y, sv, ai[p][q]);
+          } else {
+            ar[p][q] = fmaf(z[p], sv, ar[p][q]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  F* part = reinterpret_cast<F*>(partv) + (int64_t)blockIdx.z * ma * na;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    int j = j0 + ty * 4 + p;
+    if (j >= ma) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int i = i0 + tx + 16 * q;
+      if (i >= na) continue;
+      if constexpr (CPLX) part[(int64_t)j * na + i] = make_float2(ar[p][q], ai[p][q]);
+      else part[(int64_t)j * na + i] = ar[p][q];
+    }
+  }
+}
+
+template <bool CPLX>
+static void launch_adjoint_fp32(const int8_t* sigma, const void* T, const void* v, int64_t ns,
+                                int n, int m, int splits, void* part, const double* scal,
+                                cudaStream_t st) {
+  int64_t chunk = (ns + splits - 1) / splits;
+  chunk = round_up(chunk, kAdjBK);
+  dim3 grid(ceil_div(n + 1, 64), ceil_div(m + 1, 64), splits);
+  adjoint_fp32_kernel<CPLX><<<grid, 256, 0, st>>>(sigma, T, v, ns, n, m, chunk, part, scal);
+}
+
+// ------------------------------------------------------------------ forward contraction
+// y_s = sum_j T'_sj (X' sigma'_s)_j   (FP32 CUDA cores, FP64 row sums)
+
+template <bool CPLX>
+struct FwdEpi {
+  using F = typename SgTypes<CPLX>::F;
+  int m;
+  int64_t ns;
+  const F* T;
+  void* y;
+  __device__ __forceinline__ void tile(float (&ar)[4][4], float (&ai)[4][4], int64_t sb, int jb,
+                                       double2 (&part)[4]) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      int64_t s = sb + p;
+      if (s >= ns) continue;
+      float pr = 0.f, pi = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int j = jb + 16 * q;
+        if (j > m) continue;
+        if constexpr (CPLX) {
+          float2 t = j < m ? T[s * m + j] : make_float2(1.f, 0.f);
+          pr += t.x * ar[p][q] - t.y * ai[p][q];
+          pi += t.x * ai[p][q] + t.y * ar[p][q];
+        } else {
+          float t = j < m ? T[s * m + j] : 1.f;
+          pr += t * ar[p][q];
+        }
+      }
+      part[p].x += (double)pr;
+      part[p].y += (double)pi;
+    }
+  }
+  __device__ __forceinline__ void finish(int64_t s, double2 v) {
+    if (CPLX) reinterpret_cast<double2*>(y)[s] = v;
+    else reinterpret_cast<double*>(y)[s] = v.x;
+  }
+};
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kSgThreads) forward_fp32_kernel(const int8_t* __restrict__ sigma,
+                                                                  int64_t ns, int n, int m,
+                                                                  const void* __restrict__ xf,
+                                                                  const void* __restrict__ T,
+                                                                  void* y, const double* scal) {
+  if (scal && scal[SC_DONE] != 0.0) return;
+  FwdEpi<CPLX> epi;
+  epi.m = m;
+  epi.ns = ns;
+  epi.T = reinterpret_cast<const typename SgTypes<CPLX>::F*>(T);
+  epi.y = y;
+  sgemm_rowreduce<CPLX>(sigma, ns, n, xf, m + 1, n + 1, epi);
+}
+
+// ------------------------------------------------------------------ CG vector kernels
+
+// X' (FP64) -> FP32 copy for the forward contraction
+template <bool CPLX>
+__global__ void to_f32_kernel(const void* __restrict__ src, void* dst, int64_t pa,
+                              const double* scal) {
+  if (scal[SC_DONE] != 0.0) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pa;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (CPLX) {
+      double2 v = reinterpret_cast<const double2*>(src)[e];
+      reinterpret_cast<float2*>(dst)[e] = make_float2((float)v.x, (float)v.y);
+    } else {
+      reinterpret_cast<float*>(dst)[e] = (float)reinterpret_cast<const double*>(src)[e];
+    }
+  }
+}
+
+// y~ = w o (y - <y>) in place (one CTA; fixed-order sums)
+template <bool CPLX>
+__global__ void __launch_bounds__(1024) center_kernel(void* yv, void* vout,
+                                                      const double* __restrict__ weights,
+                                                      int64_t ns, const double* scal) {
+  if (scal[SC_DONE] != 0.0) return;
+  const double invn = 1.0 / (double)ns;
+  double sr = 0.0, si = 0.0;
+  for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) {
+    double w = weights ? weights[s] : invn;
+    if (CPLX) {
+      double2 y = reinterpret_cast<double2*>(yv)[s];
+      sr += w * y.x;
+      si += w * y.y;
+    } else {
+      sr += w * reinterpret_cast<double*>(yv)[s];
+    }
+  }
+  const double mr = block_sum(sr), mi = block_sum(si);
+  for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) {
+    double w = weights ? weights[s] : invn;
+    if (CPLX) {
+      double2 y = reinterpret_cast<double2*>(yv)[s];
+      reinterpret_cast<double2*>(vout)[s] = make_double2(w * (y.x - mr), w * (y.y - mi));
+    } else {
+      reinterpret_cast<double*>(vout)[s] = w * (reinterpret_cast<double*>(yv)[s] - mr);
+    }
+  }
+}
+
+// out = sum_z part[z] (+ eps * p);  red[b] = sum conj(p) . out (if p given).
+// The element X'[m][n] (no parameter) is forced to 0.
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) reduce_parts_kernel(
+    const void* __restrict__ partv, int splits, int64_t pa, int64_t corner, void* outv,
+    const void* __restrict__ pv, double eps, double* red, const double* scal) {
+  if (scal && scal[SC_DONE] != 0.0) return;
+  using DT = typename D<CPLX>::T;
+  DT* out = reinterpret_cast<DT*>(outv);
+  const DT* p = reinterpret_cast<const DT*>(pv);
+  double dot = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pa;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    DT acc = D<CPLX>::zero();
+    for (int z = 0; z < splits; ++z) {
+      if constexpr (CPLX) {
+        float2 v = reinterpret_cast<const float2*>(partv)[(int64_t)z * pa + e];
+        acc.x += (double)v.x;
+        acc.y += (double)v.y;
+      } else {
+        acc += (double)reinterpret_cast<const float*>(partv)[(int64_t)z * pa + e];
+      }
+    }
+    if (p) acc = axpy(eps, p[e], acc);
+    if (e == corner) acc = D<CPLX>::zero();
+    out[e] = acc;
+    if (p) dot += cdot_re(p[e], acc);
+  }
+  if (red) {
+    double b = block_sum(dot);
+    if (threadIdx.x == 0) red[blockIdx.x] = b;
+  }
+}
+
+// x = 0, r = p = F, rs = ||F||^2 (run after F was reduced into r)
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) cg_init_kernel(void* xv, void* rv, void* pv,
+                                                              int64_t pa, double* red) {
+  using DT = typename D<CPLX>::T;
+  DT* x = reinterpret_cast<DT*>(xv);
+  DT* r = reinterpret_cast<DT*>(rv);
+  DT* p = reinterpret_cast<DT*>(pv);
+  double nn = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pa;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    x[e] = D<CPLX>::zero();
+    p[e] = r[e];
+    nn += norm2(r[e]);
+  }
+  double b = block_sum(nn);
+  if (threadIdx.x == 0) red[kVecBlocks + blockIdx.x] = b;
+}
+
+__global__ void cg_init_scalars_kernel(const double* red, double* scal, double rtol) {
+  double rs = sum_partials(red + kVecBlocks);
+  if (threadIdx.x == 0) {
+    scal[SC_RS0] = rs;
+    scal[SC_RS1] = rs;
+    scal[SC_FNORM] = sqrt(rs);
+    scal[SC_ITERS] = 0.0;
+    scal[SC_DONE] = (rs == 0.0) ? 1.0 : 0.0;
+    if (!isfinite(rs)) {
+      scal[SC_NONFINITE] = 1.0;
+      scal[SC_DONE] = 1.0;
+    }
+  }
+}
+
+// alpha = rs / p^H A p; x += alpha p; r -= alpha A p; red2 = ||r||^2 partials
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) cg_step_x_kernel(void* xv, void* rv,
+                                                                const void* pv, const void* apv,
+                                                                int64_t pa, double* red,
+                                                                double* scal, int it) {
+  if (scal[SC_DONE] != 0.0) return;
+  using DT = typename D<CPLX>::T;
+  DT* x = reinterpret_cast<DT*>(xv);
+  DT* r = reinterpret_cast<DT*>(rv);
+  const DT* p = reinterpret_cast<const DT*>(pv);
+  const DT* ap = reinterpret_cast<const DT*>(apv);
+  const double pap = sum_partials(red);
+  const double rs = scal[(it & 1) ? SC_RS1 : SC_RS0];
+  const double alpha = rs / pap;
+  double nn = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pa;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    x[e] = axpy(alpha, p[e], x[e]);
+    DT rr = axpy(-alpha, ap[e], r[e]);
+    r[e] = rr;
+    nn += norm2(rr);
+  }
+  double b = block_sum(nn);
+  if (threadIdx.x == 0) red[kVecBlocks + blockIdx.x] = b;
+}
+
+// beta = rs_new / rs; p = r + beta p; convergence test on ||r|| <= rtol ||F||
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) cg_step_p_kernel(const void* rv, void* pv,
+                                                                int64_t pa, const double* red,
+                                                                double* scal, int it,
+                                                                double rtol) {
+  if (scal[SC_DONE] != 0.0) return;
+  using DT = typename D<CPLX>::T;
+  const DT* r = reinterpret_cast<const DT*>(rv);
+  DT* p = reinterpret_cast<DT*>(pv);
+  const double rs_new = sum_partials(red + kVecBlocks);
+  const double rs = scal[(it & 1) ? SC_RS1 : SC_RS0];
+  const double fn = scal[SC_FNORM];
+  const bool conv = sqrt(rs_new) <= rtol * fn;
+  const bool bad = !isfinite(rs_new);
+  if (!conv && !bad) {
+    const double beta = rs_new / rs;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pa;
+         e += (int64_t)gridDim.x * blockDim.x)
+      p[e] = axpy(beta, p[e], r[e]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    scal[(it & 1) ? SC_RS0 : SC_RS1] = rs_new;
+    scal[SC_ITERS] = (double)(it + 1);
+    if (conv || bad) scal[SC_DONE] = 1.0;
+    if (bad) scal[SC_NONFINITE] = 1.0;
+  }
+}
+
+// alpha <- alpha - lr delta (FP64 master), delta in the augmented layout; info.
+template <bool CPLX>
+__global__ void sr_update_kernel(double* a, double* b, double* w, int n, int m,
+                                 const void* __restrict__ xv, double lr, const double* scal,
+                                 double* info, int n_iter_final, double rtol) {
+  using DT = typename D<CPLX>::T;
+  const DT* x = reinterpret_cast<const DT*>(xv);
+  const int na = n + 1;
+  const int64_t tot = (int64_t)(m + 1) * na;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int j = (int)(e / na), i = (int)(e % na);
+    double* dst;
+    if (j < m && i < n) dst = w + (CPLX ? 2 : 1) * ((int64_t)j * n + i);
+    else if (j < m) dst = b + (CPLX ? 2 : 1) * j;
+    else if (i < n) dst = a + (CPLX ? 2 : 1) * i;
+    else continue;
+    if constexpr (CPLX) {
+      dst[0] -= lr * x[e].x;
+      dst[1] -= lr * x[e].y;
+    } else {
+      dst[0] -= lr * x[e];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double iters = scal[SC_ITERS];
+    const double fn = scal[SC_FNORM];
+    const double rs = scal[((int)iters & 1) ? SC_RS1 : SC_RS0];
+    const double res = fn > 0.0 ? sqrt(rs) / fn : 0.0;
+    info[NK_INFO_CG_ITERS] = iters;
+    info[NK_INFO_CG_RESID] = res;
+    info[NK_INFO_F_NORM] = fn;
+    int flags = 0;
+    if (res > rtol) flags |= 1 << NK_ERR_NOT_CONVERGED;
+    if (scal[SC_NONFINITE] != 0.0 || !isfinite(res)) flags |= 1 << NK_ERR_NONFINITE;
+    info[NK_INFO_FLAGS] = (double)flags;
+  }
+}
+
+// grad (a, b, W order) from the augmented adjoint result
+template <bool CPLX>
+__global__ void scatter_grad_kernel(const void* __restrict__ gv, int n, int m, double* grad) {
+  using DT = typename D<CPLX>::T;
+  const DT* g = reinterpret_cast<const DT*>(gv);
+  const int na = n + 1;
+  const int64_t tot = (int64_t)(m + 1) * na;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int j = (int)(e / na), i = (int)(e % na);
+    int64_t k;
+    if (j < m && i < n) k = (int64_t)n + m + (int64_t)j * n + i;
+    else if (j < m) k = n + j;
+    else if (i < n) k = i;
+    else continue;
+    if constexpr (CPLX) {
+      grad[2 * k] = g[e].x;
+      grad[2 * k + 1] = g[e].y;
+    } else {
+      grad[k] = g[e];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ drivers
+
+template <bool CPLX>
+static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const double* eloc,
+                           const double* weights, int64_t ns, int n_chains, double eps,
+                           double lr, int n_cg, double rtol, int prec, char* sc,
+                           double* info, cudaStream_t st) {
+  (void)prec;
+  SrLayout L(r->n, r->m, CPLX, ns);
+  double* scal = (double*)(sc + L.scal);
+  double* red = (double*)(sc + L.red);
+  const int n = r->n, m = r->m;
+  const int64_t corner = (int64_t)m * L.na + n;
+  stats_kernel<CPLX><<<1, 1024, 0, st>>>(eloc, weights, ns, n_chains, info, scal, sc + L.v);
+  if (nk_status e = check_launch("nk_sr_step(stats)")) return e;
+  cudaMemsetAsync(scal + SC_DONE, 0, sizeof(double), st);
+  // F = adjoint(w o (E - <E>)) -> r
+  launch_adjoint_fp32<CPLX>(sigma, T, sc + L.v, ns, n, m, L.splits, sc + L.part, nullptr, st);
+  reduce_parts_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.part, L.splits, L.pa,
+                                                                corner, sc + L.r, nullptr, 0.0,
+                                                                nullptr, nullptr);
+  cg_init_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, sc + L.r, sc + L.p, L.pa,
+                                                           red);
+  cg_init_scalars_kernel<<<1, 32, 0, st>>>(red, scal, rtol);
+  if (nk_status e = check_launch("nk_sr_step(force)")) return e;
+  const int64_t sg_blocks = (ns + kSgBS - 1) / kSgBS;
+  for (int it = 0; it < n_cg; ++it) {
+    to_f32_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.p, sc + L.xf, L.pa, scal);
+    forward_fp32_kernel<CPLX><<<(unsigned)sg_blocks, kSgThreads, 0, st>>>(
+        sigma, ns, n, m, sc + L.xf, T, sc + L.y, scal);
+    center_kernel<CPLX><<<1, 1024, 0, st>>>(sc + L.y, sc + L.v, weights, ns, scal);
+    launch_adjoint_fp32<CPLX>(sigma, T, sc + L.v, ns, n, m, L.splits, sc + L.part, scal, st);
+    reduce_parts_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(
+        sc + L.part, L.splits, L.pa, corner, sc + L.ap, sc + L.p, eps, red, scal);
+    cg_step_x_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, sc + L.r, sc + L.p,
+                                                               sc + L.ap, L.pa, red, scal, it);
+    cg_step_p_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.r, sc + L.p, L.pa, red,
+                                                               scal, it, rtol);
+    if (nk_status e = check_launch("nk_sr_step(cg)")) return e;
+  }
+  sr_update_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(r->a, r->b, r->w, n, m, sc + L.x, lr,
+                                                             scal, info, n_cg, rtol);
+  if (nk_status e = check_launch("nk_sr_step(update)")) return e;
+  return launch_prepare(r, st);
+}
+
+nk_status run_sr_step(nk_rbm* r, const int8_t* sigma, const void* t, const double* eloc,
+                      const double* weights, int64_t ns, int n_chains, double diag_shift,
+                      double lr, int n_cg, double cg_rtol, int prec, void* scratch,
+                      size_t scratch_bytes, double* info, cudaStream_t st) {
+  size_t need = sr_scratch_bytes(r->n, r->m, r->is_complex, ns);
+  if (scratch_bytes < need)
+    return fail(NK_ERR_SHAPE, "nk_sr_step: scratch of %zu B, need %zu B", scratch_bytes, need);
+  if (r->is_complex)
+    return sr_step_t<true>(r, sigma, t, eloc, weights, ns, n_chains, diag_shift, lr, n_cg, cg_rtol,
+                           prec, (char*)scratch, info, st);
+  return sr_step_t<false>(r, sigma, t, eloc, weights, ns, n_chains, diag_shift, lr, n_cg, cg_rtol,
+                          prec, (char*)scratch, info, st);
+}
+
+// ------------------------------------------------------------------ K8 backward
+
+size_t backward_scratch_bytes(int n, int m, int cplx, int64_t ns) {
+  SrLayout L(n, m, cplx, ns);
+  size_t f = cplx ? 8 : 4;
+  return L.total + 2 * (size_t)round_up(std::max<int64_t>(ns, 1) * m * f, 256) +
+         (size_t)round_up(std::max<int64_t>(ns, 1) * 16, 256);
+}
+
+template <bool CPLX>
+__global__ void copy_g_kernel(const double* g, void* v, int64_t ns) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    if (CPLX) reinterpret_cast<double2*>(v)[s] = make_double2(g[2 * s], g[2 * s + 1]);
+    else reinterpret_cast<double*>(v)[s] = g[2 * s];
+  }
+}
+
+nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const double* g,
+                       double* grad, int prec, void* scratch, size_t scratch_bytes,
+                       cudaStream_t st) {
+  size_t need = backward_scratch_bytes(r->n, r->m, r->is_complex, ns);
+  if (scratch_bytes < need)
+    return fail(NK_ERR_SHAPE, "nk_rbm_logpsi_backward: scratch of %zu B, need %zu B",
+                scratch_bytes, need);
+  SrLayout L(r->n, r->m, r->is_complex, ns);
+  char* sc = (char*)scratch;
+  size_t f = r->is_complex ? 8 : 4;
+  char* theta = sc + L.total;
+  char* T = theta + round_up(std::max<int64_t>(ns, 1) * r->m * f, 256);
+  char* lp = T + round_up(std::max<int64_t>(ns, 1) * r->m * f, 256);
+  nk_status e = prec == NK_PREC_BF16X2
+                    ? launch_logpsi_bf16(r, sigma, ns, (double*)lp, theta, st)
+                    : launch_logpsi_fp32(r, sigma, ns, (double*)lp, theta, st);
+  if (e) return e;
+  if ((e = launch_logderiv(r, sigma, theta, ns, NK_LAYOUT_FACTORED, T, st))) return e;
+  int64_t blocks = std::min<int64_t>((ns + 255) / 256, 1024);
+  if (blocks < 1) blocks = 1;
+  if (r->is_complex) {
+    copy_g_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(g, sc + L.v, ns);
+    launch_adjoint_fp32<true>(sigma, T, sc + L.v, ns, r->n, r->m, L.splits, sc + L.part, nullptr,
+                              st);
+    reduce_parts_kernel<true><<<kVecBlocks, kVecThreads, 0, st>>>(
+        sc + L.part, L.splits, L.pa, (int64_t)r->m * L.na + r->n, sc + L.x, nullptr, 0.0, nullptr,
+        nullptr);
+    scatter_grad_kernel<true><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, r->n, r->m, grad);
+  } else {
+    copy_g_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(g, sc + L.v, ns);
+    launch_adjoint_fp32<false>(sigma, T, sc + L.v, ns, r->n, r->m, L.splits, sc + L.part, nullptr,
+                               st);
+    reduce_parts_kernel<false><<<kVecBlocks, kVecThreads, 0, st>>>(
+        sc + L.part, L.splits, L.pa, (int64_t)r->m * L.na + r->n, sc + L.x, nullptr, 0.0, nullptr,
+        nullptr);
+    scatter_grad_kernel<false><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, r->n, r->m, grad);
+  }
+  return check_launch("nk_rbm_logpsi_backward");
+}
+
+}  // namespace nk

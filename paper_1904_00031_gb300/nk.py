@@ -1,0 +1,323 @@
+"""Thin Python binding of the nk C ABI (include/nk.h): argument marshalling only.
+
+Every function here calls the entry point of the same name in ``libnk.so``
+with device pointers of torch tensors.  PyTorch provides device memory and
+streams; every step of the computation runs in the library's CUDA kernels.
+There is no CPU fallback: if the library is missing or the device is not an
+sm_103a GPU, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnk.so")
+
+NK_OK = 0
+NK_PREC_FP32 = 0
+NK_PREC_BF16X2 = 1
+NK_MOVE_FLIP = 0
+NK_MOVE_EXCHANGE = 1
+NK_LAYOUT_FACTORED = 0
+NK_LAYOUT_DENSE = 1
+NK_INFO_LEN = 8
+INFO_KEYS = ("energy", "energy_imag", "variance", "error", "cg_iters", "cg_resid", "f_norm",
+             "flags")
+
+EXPORTS = (
+    "nk_status_string", "nk_last_error", "nk_device_supported", "nk_rbm_workspace_bytes",
+    "nk_rbm_prepare", "nk_rbm_logpsi", "nk_metropolis_sweep", "nk_operator_bytes",
+    "nk_operator_upload", "nk_local_energy", "nk_logderiv", "nk_sr_scratch_bytes", "nk_sr_step",
+    "nk_backward_scratch_bytes", "nk_rbm_logpsi_backward",
+)
+
+
+class NkError(RuntimeError):
+    pass
+
+
+class _Rbm(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("is_complex", C.c_int32),
+                ("reserved", C.c_int32), ("a", C.c_void_p), ("b", C.c_void_p), ("w", C.c_void_p),
+                ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
+
+
+class _Chains(C.Structure):
+    _fields_ = [("nc", C.c_int32), ("group_size", C.c_int32), ("sigma", C.c_void_p),
+                ("seed", C.c_uint64), ("counter", C.c_uint64)]
+
+
+class _Operator(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_site_terms", C.c_int32), ("site_idx", C.c_void_p),
+                ("site_mat", C.c_void_p), ("n_bond_terms", C.c_int32), ("reserved", C.c_int32),
+                ("bond_i", C.c_void_p), ("bond_k", C.c_void_p), ("bond_mat", C.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libnk.so (building nothing); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise NkError(f"{path} not found: build it with paper_1904_00031_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, I32, I64, SZ, D = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t, C.c_double
+    sig = {
+        "nk_status_string": (C.c_char_p, [I32]),
+        "nk_last_error": (C.c_char_p, []),
+        "nk_device_supported": (I32, []),
+        "nk_rbm_workspace_bytes": (SZ, [I32, I32, I32]),
+        "nk_rbm_prepare": (I32, [P, P]),
+        "nk_rbm_logpsi": (I32, [P, P, I64, I32, P, P, P]),
+        "nk_metropolis_sweep": (I32, [P, P, I32, P, P, I32, I32, I32, P, P, P]),
+        "nk_operator_bytes": (SZ, [P]),
+        "nk_operator_upload": (I32, [P, P, SZ, P]),
+        "nk_local_energy": (I32, [P, P, P, P, I64, P, P, P]),
+        "nk_logderiv": (I32, [P, P, P, I64, I32, P, P]),
+        "nk_sr_scratch_bytes": (SZ, [I32, I32, I32, I64]),
+        "nk_sr_step": (I32, [P, P, P, P, P, I64, I32, D, D, I32, D, I32, P, SZ, P, P]),
+        "nk_backward_scratch_bytes": (SZ, [I32, I32, I32, I64]),
+        "nk_rbm_logpsi_backward": (I32, [P, P, I64, P, P, I32, P, SZ, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != NK_OK:
+        lib = load_library()
+        raise NkError(f"{what}: {lib.nk_status_string(status).decode()} "
+                      f"({lib.nk_last_error().decode()})")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _require_gpu(*tensors):
+    for t in tensors:
+        if t is not None and not t.is_cuda:
+            raise NkError("nk: every tensor argument must live on the CUDA device")
+
+
+# ---------------------------------------------------------------------- RBM
+
+class Rbm:
+    """FP64 master parameters on the device plus the library's derived planes."""
+
+    def __init__(self, n: int, m: int, is_complex: bool, device="cuda"):
+        lib = load_library()
+        self.n, self.m, self.is_complex = int(n), int(m), bool(is_complex)
+        dt = torch.float64
+        k = 2 if is_complex else 1
+        self.a = torch.zeros(n * k, dtype=dt, device=device)
+        self.b = torch.zeros(m * k, dtype=dt, device=device)
+        self.w = torch.zeros(m * n * k, dtype=dt, device=device)
+        nb = lib.nk_rbm_workspace_bytes(n, m, int(is_complex))
+        self.ws = torch.empty(nb + 256, dtype=torch.uint8, device=device)
+        off = (-self.ws.data_ptr()) % 256
+        self._ws_ptr = self.ws.data_ptr() + off
+        self._ws_bytes = nb
+        self._s = _Rbm(self.n, self.m, int(is_complex), 0, self.a.data_ptr(), self.b.data_ptr(),
+                       self.w.data_ptr(), self._ws_ptr, nb)
+
+    @property
+    def n_params(self) -> int:
+        return self.n + self.m + self.n * self.m
+
+    def struct(self):
+        return C.byref(self._s)
+
+    def load(self, a, b, w, stream=None):
+        """Copy FP64 parameters (numpy; complex allowed) in and refresh the planes."""
+        def flat(x):
+            x = np.asarray(x)
+            if self.is_complex:
+                x = x.astype(np.complex128).reshape(-1)
+                return torch.from_numpy(np.stack([x.real, x.imag], axis=1).reshape(-1).copy())
+            return torch.from_numpy(np.asarray(x, dtype=np.float64).reshape(-1).copy())
+        self.a.copy_(flat(a))
+        self.b.copy_(flat(b))
+        self.w.copy_(flat(w))
+        nk_rbm_prepare(self, stream)
+
+    def params_numpy(self):
+        def un(t, shape):
+            x = t.detach().cpu().numpy()
+            if self.is_complex:
+                x = x[0::2] + 1j * x[1::2]
+            return x.reshape(shape)
+        return un(self.a, (self.n,)), un(self.b, (self.m,)), un(self.w, (self.m, self.n))
+
+    def f32_dtype(self):
+        return torch.complex64 if self.is_complex else torch.float32
+
+
+def nk_rbm_prepare(rbm: Rbm, stream=None):
+    _check(load_library().nk_rbm_prepare(rbm.struct(), _stream(stream)), "nk_rbm_prepare")
+
+
+def nk_rbm_logpsi(rbm: Rbm, sigma, prec=NK_PREC_FP32, logpsi_out=None, theta_out=None,
+                  stream=None):
+    """ln psi (complex128 [ns]); optionally theta into ``theta_out`` ([ns, m] F32)."""
+    _require_gpu(sigma, theta_out)
+    ns = sigma.shape[0]
+    if logpsi_out is None:
+        logpsi_out = torch.empty(ns, dtype=torch.complex128, device=sigma.device)
+    _check(load_library().nk_rbm_logpsi(rbm.struct(), _ptr(sigma), ns, prec, _ptr(logpsi_out),
+                                        _ptr(theta_out), _stream(stream)), "nk_rbm_logpsi")
+    return logpsi_out
+
+
+class Chains:
+    """Persistent Markov chains: device states plus the Philox seed and counter."""
+
+    def __init__(self, sigma0, group_size: int, seed: int, device="cuda"):
+        s = torch.as_tensor(np.asarray(sigma0, dtype=np.int8))
+        self.sigma = s.to(device).contiguous()
+        self.nc, self.n = self.sigma.shape
+        self._s = _Chains(self.nc, int(group_size), self.sigma.data_ptr(), int(seed), 0)
+
+    @property
+    def counter(self) -> int:
+        return int(self._s.counter)
+
+    @counter.setter
+    def counter(self, v: int):
+        self._s.counter = int(v)
+
+    @property
+    def group_size(self) -> int:
+        return int(self._s.group_size)
+
+    @property
+    def seed(self) -> int:
+        return int(self._s.seed)
+
+
+def nk_metropolis_sweep(rbm: Rbm, chains: Chains, move: int, bond_i=None, bond_k=None,
+                        n_discard: int = 1, n_samples_per_chain: int = 1, samples_out=None,
+                        n_accept_out=None, stream=None):
+    _require_gpu(bond_i, bond_k, samples_out, n_accept_out)
+    nb = 0 if bond_i is None else int(bond_i.shape[0])
+    if samples_out is None:
+        samples_out = torch.empty(chains.nc * n_samples_per_chain, rbm.n, dtype=torch.int8,
+                                  device=chains.sigma.device)
+    _check(load_library().nk_metropolis_sweep(
+        rbm.struct(), C.byref(chains._s), move, _ptr(bond_i), _ptr(bond_k), nb, n_discard,
+        n_samples_per_chain, _ptr(samples_out), _ptr(n_accept_out), _stream(stream)),
+        "nk_metropolis_sweep")
+    return samples_out
+
+
+class Operator:
+    """A Hamiltonian (workloads.Operator) compiled into device memory."""
+
+    def __init__(self, op, device="cuda", stream=None):
+        lib = load_library()
+        self.n = op.n
+        self._site_idx = np.ascontiguousarray(op.site_idx, dtype=np.int32)
+        self._site_mat = np.ascontiguousarray(
+            np.stack([op.site_mat.real, op.site_mat.imag], axis=-1), dtype=np.float64)
+        self._bond_i = np.ascontiguousarray(op.bond_i, dtype=np.int32)
+        self._bond_k = np.ascontiguousarray(op.bond_k, dtype=np.int32)
+        self._bond_mat = np.ascontiguousarray(
+            np.stack([op.bond_mat.real, op.bond_mat.imag], axis=-1), dtype=np.float64)
+        self._s = _Operator(op.n, op.n_site_terms, self._site_idx.ctypes.data,
+                            self._site_mat.ctypes.data, op.n_bond_terms, 0,
+                            self._bond_i.ctypes.data, self._bond_k.ctypes.data,
+                            self._bond_mat.ctypes.data)
+        nb = lib.nk_operator_bytes(C.byref(self._s))
+        if nb == 0:
+            raise NkError("nk_operator_bytes: invalid operator " + lib.nk_last_error().decode())
+        self.dev = torch.empty(nb, dtype=torch.uint8, device=device)
+        _check(lib.nk_operator_upload(C.byref(self._s), _ptr(self.dev), nb, _stream(stream)),
+               "nk_operator_upload")
+
+
+def nk_local_energy(rbm: Rbm, op: Operator, sigma, theta, eloc_out=None, t_out=None, stream=None):
+    _require_gpu(sigma, theta, t_out)
+    ns = sigma.shape[0]
+    if eloc_out is None:
+        eloc_out = torch.empty(ns, dtype=torch.complex128, device=sigma.device)
+    _check(load_library().nk_local_energy(rbm.struct(), _ptr(op.dev), _ptr(sigma), _ptr(theta), ns,
+                                          _ptr(eloc_out), _ptr(t_out), _stream(stream)),
+           "nk_local_energy")
+    return eloc_out
+
+
+def nk_logderiv(rbm: Rbm, sigma, theta, layout=NK_LAYOUT_FACTORED, o_out=None, stream=None):
+    _require_gpu(sigma, theta, o_out)
+    ns = sigma.shape[0]
+    if o_out is None:
+        cols = rbm.m if layout == NK_LAYOUT_FACTORED else rbm.n_params
+        o_out = torch.empty(ns, cols, dtype=rbm.f32_dtype(), device=sigma.device)
+    _check(load_library().nk_logderiv(rbm.struct(), _ptr(sigma), _ptr(theta), ns, layout,
+                                      _ptr(o_out), _stream(stream)), "nk_logderiv")
+    return o_out
+
+
+def sr_scratch(rbm: Rbm, ns: int, device="cuda"):
+    nb = load_library().nk_sr_scratch_bytes(rbm.n, rbm.m, int(rbm.is_complex), ns)
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def nk_sr_step(rbm: Rbm, sigma, t, eloc, n_chains: int, diag_shift: float, lr: float, n_cg: int,
+               cg_rtol: float = 1e-12, prec=NK_PREC_FP32, weights=None, scratch=None,
+               info_out=None, stream=None):
+    _require_gpu(sigma, t, eloc, weights, scratch, info_out)
+    ns = sigma.shape[0]
+    if scratch is None:
+        scratch = sr_scratch(rbm, ns, sigma.device)
+    if info_out is None:
+        info_out = torch.zeros(NK_INFO_LEN, dtype=torch.float64, device=sigma.device)
+    _check(load_library().nk_sr_step(
+        rbm.struct(), _ptr(sigma), _ptr(t), _ptr(eloc), _ptr(weights), ns, n_chains,
+        float(diag_shift), float(lr), int(n_cg), float(cg_rtol), prec, _ptr(scratch),
+        scratch.numel(), _ptr(info_out), _stream(stream)), "nk_sr_step")
+    return info_out
+
+
+def info_dict(info) -> dict:
+    v = info.detach().cpu().numpy()
+    return {k: float(x) for k, x in zip(INFO_KEYS, v)}
+
+
+def backward_scratch(rbm: Rbm, ns: int, device="cuda"):
+    nb = load_library().nk_backward_scratch_bytes(rbm.n, rbm.m, int(rbm.is_complex), ns)
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def nk_rbm_logpsi_backward(rbm: Rbm, sigma, g, prec=NK_PREC_FP32, grad_out=None, scratch=None,
+                           stream=None):
+    """grad_k = sum_s conj(O_sk) g_s, F64 [P] (complex128 for a complex RBM)."""
+    _require_gpu(sigma, g, grad_out, scratch)
+    ns = sigma.shape[0]
+    if scratch is None:
+        scratch = backward_scratch(rbm, ns, sigma.device)
+    if grad_out is None:
+        grad_out = torch.empty(rbm.n_params,
+                               dtype=torch.complex128 if rbm.is_complex else torch.float64,
+                               device=sigma.device)
+    g = g.to(torch.complex128).contiguous()
+    _check(load_library().nk_rbm_logpsi_backward(rbm.struct(), _ptr(sigma), ns, _ptr(g),
+                                                 _ptr(grad_out), prec, _ptr(scratch),
+                                                 scratch.numel(), _stream(stream)),
+           "nk_rbm_logpsi_backward")
+    return grad_out

@@ -1,0 +1,76 @@
+"""One VMC + SR iteration (Sec. 2.2.5) driven through the C ABI:
+
+    nk_metropolis_sweep -> nk_rbm_logpsi (theta, ln psi) -> nk_local_energy
+    (E_loc and T = tanh theta) -> nk_sr_step (statistics, force, lazy CG, update)
+
+All buffers are allocated once; a step launches only library kernels and does
+not synchronise the host (``info()`` reads the small FP64 status block).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import nk
+from . import workloads as W
+
+
+class VmcSr:
+    def __init__(self, w: W.Workload, params: W.RbmParams, sigma0=None,
+                 prec: int = nk.NK_PREC_FP32, device="cuda"):
+        self.w = w
+        self.prec = prec
+        self.rbm = nk.Rbm(w.n, w.m, w.is_complex, device)
+        self.rbm.load(params.a, params.b, params.w)
+        if sigma0 is None:
+            sigma0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed)
+        self.chains = nk.Chains(sigma0, w.group_size, w.seed, device)
+        self.op = nk.Operator(w.op, device)
+        b = np.ascontiguousarray(w.sampler_bonds, dtype=np.int32)
+        self.bond_i = torch.from_numpy(b[:, 0].copy()).to(device)
+        self.bond_k = torch.from_numpy(b[:, 1].copy()).to(device)
+        ns = w.n_samples
+        self.ns = ns
+        self.samples = torch.empty(ns, w.n, dtype=torch.int8, device=device)
+        f32 = self.rbm.f32_dtype()
+        self.theta = torch.empty(ns, w.m, dtype=f32, device=device)
+        self.t = torch.empty(ns, w.m, dtype=f32, device=device)
+        self.logpsi = torch.empty(ns, dtype=torch.complex128, device=device)
+        self.eloc = torch.empty(ns, dtype=torch.complex128, device=device)
+        self.n_acc = torch.zeros(w.n_chains, dtype=torch.int64, device=device)
+        self.scratch = nk.sr_scratch(self.rbm, ns, device)
+        self.info_buf = torch.zeros(nk.NK_INFO_LEN, dtype=torch.float64, device=device)
+        self.move = nk.NK_MOVE_FLIP if w.move == "flip" else nk.NK_MOVE_EXCHANGE
+
+    # stages ---------------------------------------------------------------
+    def sample(self):
+        nk.nk_metropolis_sweep(self.rbm, self.chains, self.move, self.bond_i, self.bond_k,
+                               self.w.n_discard, self.w.samples_per_chain, self.samples,
+                               self.n_acc)
+
+    def amplitudes(self):
+        nk.nk_rbm_logpsi(self.rbm, self.samples, self.prec, self.logpsi, self.theta)
+
+    def energies(self):
+        nk.nk_local_energy(self.rbm, self.op, self.samples, self.theta, self.eloc, self.t)
+
+    def sr(self):
+        nk.nk_sr_step(self.rbm, self.samples, self.t, self.eloc, self.w.n_chains,
+                      self.w.diag_shift, self.w.lr, self.w.n_cg, 1e-12, self.prec,
+                      scratch=self.scratch, info_out=self.info_buf)
+
+    def step(self):
+        self.sample()
+        self.amplitudes()
+        self.energies()
+        self.sr()
+
+    def info(self) -> dict:
+        d = nk.info_dict(self.info_buf)
+        sweeps = self.w.n_discard + self.w.samples_per_chain
+        d["acceptance"] = float(self.n_acc.sum().item()) / (self.w.n_chains * sweeps * self.w.n)
+        return d
+
+    # kernel launches per step (for reporting)
+    def launches_per_step(self) -> int:
+        return 3 + 8 + 7 * self.w.n_cg

@@ -1,0 +1,99 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/nk.h declares, and rejects bad arguments on the
+host before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1904_00031_gb300 import build as nkbuild
+from paper_1904_00031_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = nkbuild.build()
+    from paper_1904_00031_gb300 import nk
+    return nk.load_library(path)
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "nk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nk_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_five_entry_points():
+    names = declared_functions()
+    for f in ("nk_rbm_logpsi", "nk_metropolis_sweep", "nk_local_energy", "nk_logderiv",
+              "nk_sr_step"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [f for f in declared_functions() if not hasattr(lib, f)]
+    assert not missing, missing
+    from paper_1904_00031_gb300 import nk
+    assert set(nk.EXPORTS) <= set(declared_functions())
+
+
+def test_status_strings_and_sizes(lib):
+    assert lib.nk_status_string(0) == b"ok"
+    assert lib.nk_status_string(2) == b"unsupported shape"
+    assert lib.nk_rbm_workspace_bytes(0, 5, 0) == 0
+    a = lib.nk_rbm_workspace_bytes(400, 1600, 1)
+    b = lib.nk_rbm_workspace_bytes(400, 1600, 0)
+    assert a > b > 400 * 1600 * 4
+    assert lib.nk_sr_scratch_bytes(40, 80, 1, 16384) > 41 * 81 * 16 * 4
+    assert lib.nk_backward_scratch_bytes(40, 80, 1, 16384) > 16384 * 80 * 8 * 2
+
+
+def test_host_argument_validation(lib):
+    from paper_1904_00031_gb300 import nk
+    assert lib.nk_rbm_logpsi(None, None, 4, 0, None, None, None) == 1
+    assert b"rbm is NULL" in lib.nk_last_error()
+    r = nk._Rbm(0, 10, 0, 0, 8, 8, 8, 256, 1 << 20)
+    assert lib.nk_rbm_logpsi(C.byref(r), None, 4, 0, None, None, None) == 2
+    r = nk._Rbm(10, 10, 0, 0, 8, 8, 8, 256, 16)
+    assert lib.nk_rbm_prepare(C.byref(r), None) == 2
+    assert b"workspace" in lib.nk_last_error()
+    r = nk._Rbm(10, 10, 0, 0, 8, 8, 8, 256, 1 << 20)
+    ch = nk._Chains(4, 64, 8, 1, 0)
+    assert lib.nk_metropolis_sweep(C.byref(r), C.byref(ch), 0, None, None, 0, 1, 1, 8, None,
+                                   None) == 2
+    ch = nk._Chains(4, 4, 8, 1, 0)
+    assert lib.nk_metropolis_sweep(C.byref(r), C.byref(ch), 1, None, None, 0, 1, 1, 8, None,
+                                   None) == 1
+    assert lib.nk_sr_step(C.byref(r), 8, 8, 8, None, 10, 3, 0.01, 0.01, 5, 0.0, 0, 256, 1 << 20,
+                          8, None) == 2  # 10 samples do not split into 3 chains
+    assert ch.counter == 0
+
+
+def test_operator_compilation_sizes(lib):
+    from paper_1904_00031_gb300 import nk
+    ops = [W.ising(10, W.chain_bonds(10), h=1.0),
+           W.heisenberg(40, W.chain_bonds(40), 1.0, True, W.sublattice(40)),
+           W.j1j2(4, 1.0, 0.5, True)]
+    sizes = []
+    for op in ops:
+        o = object.__new__(nk.Operator)
+        o._site_idx = np.ascontiguousarray(op.site_idx, dtype=np.int32)
+        o._site_mat = np.ascontiguousarray(np.stack([op.site_mat.real, op.site_mat.imag], -1))
+        o._bond_i = np.ascontiguousarray(op.bond_i, dtype=np.int32)
+        o._bond_k = np.ascontiguousarray(op.bond_k, dtype=np.int32)
+        o._bond_mat = np.ascontiguousarray(np.stack([op.bond_mat.real, op.bond_mat.imag], -1))
+        s = nk._Operator(op.n, op.n_site_terms, o._site_idx.ctypes.data, o._site_mat.ctypes.data,
+                         op.n_bond_terms, 0, o._bond_i.ctypes.data, o._bond_k.ctypes.data,
+                         o._bond_mat.ctypes.data)
+        sizes.append(lib.nk_operator_bytes(C.byref(s)))
+    # header 32 B; site 40 B, bond 72 B, move 80 B records (16-B padded blocks)
+    assert sizes[0] == 32 + 400 + 720 + 800      # TFIM: 10 diag sites, 10 diag bonds, 10 flips
+    assert sizes[1] == 32 + 0 + 2880 + 3200      # Heisenberg: 40 diag bonds, 40 pair moves
+    assert sizes[2] == 32 + 0 + 64 * 72 + 64 * 80
+    bad = nk._Operator(3, 0, None, None, 1, 0, np.array([0], np.int32).ctypes.data,
+                       np.array([7], np.int32).ctypes.data, np.zeros(32).ctypes.data)
+    assert lib.nk_operator_bytes(C.byref(bad)) == 0

@@ -1,0 +1,285 @@
+"""Parity of every CUDA entry point with the FP64 oracle, called through the C ABI
+on the same seeded inputs.  Tolerances (FP32 kernels):
+  ln psi       |d Re| <= 1e-5 max(1, |ref|), Im compared mod 2 pi likewise
+  theta, tanh  |d| <= 2e-5 max(1, |ref|)
+  E_loc        |d| <= 1e-4 max(1, |ref|) per sample, mean rel 1e-5
+  adjoint (O^H v), SR force       rel 1e-5 (norm-wise)
+  SR direction (converged CG)     rel 1e-3 (norm-wise; FP32 matvec, cond(S+eps) ~ 1e2)
+  Metropolis   bit-exact trajectories for chains whose decisions never came
+               within 1e-3 of a tie (in 2 Re Delta) in the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import local_energy as ole
+from oracle import rbm as orbm
+from oracle import sampler as osam
+from oracle import sr as osr
+from oracle import hamiltonian as oham
+from paper_1904_00031_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nk():
+    from paper_1904_00031_gb300 import build, nk as nkmod
+    build.build()
+    lib = nkmod.load_library()
+    assert lib.nk_device_supported() == 1
+    return nkmod
+
+
+def make_rbm(nk, p):
+    r = nk.Rbm(p.n, p.m, p.is_complex)
+    r.load(p.a, p.b, p.w)
+    return r
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def wrap(d):
+    return np.angle(np.exp(1j * d))
+
+
+def check_logpsi(got, ref, tol=1e-5):
+    scale = np.maximum(1.0, np.abs(ref))
+    assert np.all(np.abs(got.real - ref.real) <= tol * scale), np.abs(got.real - ref.real).max()
+    assert np.all(np.abs(wrap(got.imag - ref.imag)) <= tol * scale)
+
+
+SHAPES = [(10, 10, False), (7, 3, False), (40, 80, True), (37, 75, True), (100, 400, False),
+          (16, 64, True), (50, 200, True)]
+
+
+@pytest.mark.parametrize("n,m,cplx", SHAPES)
+@pytest.mark.parametrize("scale", [0.01, 0.3])
+def test_logpsi_and_theta(nk, n, m, cplx, scale):
+    p = W.init_params(n, m, cplx, 0.01, 1000 + n)
+    if scale > 0.01:
+        p = W.perturb_params(p, scale / np.sqrt(n), 7)
+    ns = 333
+    s = W.random_configs(ns, n, 3)
+    r = make_rbm(nk, p)
+    th = torch.empty(ns, m, dtype=r.f32_dtype(), device="cuda")
+    lp = nk.nk_rbm_logpsi(r, dev(s), theta_out=th).cpu().numpy()
+    check_logpsi(lp, orbm.logpsi(p, s))
+    tref = orbm.theta(p, s)
+    tg = th.cpu().numpy()
+    assert np.all(np.abs(tg - tref) <= 2e-5 * np.maximum(1.0, np.abs(tref)))
+
+
+def test_logpsi_full_size_sampled(nk):
+    # 20x20 J1-J2 workload shape: n = 400, m = 1600, complex; 4096 configurations,
+    # a sample of 64 checked against the oracle
+    p = W.perturb_params(W.init_params(400, 1600, True, 0.01, 1237), 0.02, 5)
+    s = W.random_configs(4096, 400, 11, True)
+    r = make_rbm(nk, p)
+    lp = nk.nk_rbm_logpsi(r, dev(s)).cpu().numpy()
+    idx = np.random.default_rng(0).choice(4096, 64, replace=False)
+    check_logpsi(lp[idx], orbm.logpsi(p, s[idx]))
+
+
+def test_logpsi_empty_and_errors(nk):
+    p = W.init_params(6, 4, False, 0.1, 1)
+    r = make_rbm(nk, p)
+    out = torch.empty(0, dtype=torch.complex128, device="cuda")
+    nk.nk_rbm_logpsi(r, torch.empty(0, 6, dtype=torch.int8, device="cuda"), logpsi_out=out)
+    with pytest.raises(nk.NkError):
+        nk.nk_rbm_logpsi(r, dev(W.random_configs(3, 6, 1)), prec=7)
+
+
+OPS = {
+    "tfim": (lambda: W.ising(12, W.chain_bonds(12), h=1.3), 12, False),
+    "heis": (lambda: W.heisenberg(16, W.chain_bonds(16), 1.0, True, W.sublattice(16)), 16, True),
+    "j1j2": (lambda: W.j1j2(4, 1.0, 0.5, True), 16, True),
+    "tfim2d": (lambda: W.ising(36, W.square_bonds(6), h=3.04), 36, False),
+}
+
+
+@pytest.mark.parametrize("which", list(OPS))
+@pytest.mark.parametrize("cplx", [False, True])
+def test_local_energy_and_tanh(nk, which, cplx):
+    mk, n, sz = OPS[which]
+    op = mk()
+    m = 2 * n + 3
+    p = W.perturb_params(W.init_params(n, m, cplx, 0.01, 5), 0.3 / np.sqrt(n), 9)
+    ns = 257
+    s = W.random_configs(ns, n, 21, sz)
+    r = make_rbm(nk, p)
+    gop = nk.Operator(op)
+    th = torch.empty(ns, m, dtype=r.f32_dtype(), device="cuda")
+    sg = dev(s)
+    nk.nk_rbm_logpsi(r, sg, theta_out=th)
+    t = torch.empty_like(th)
+    e = nk.nk_local_energy(r, gop, sg, th, t_out=t).cpu().numpy()
+    ref = ole.local_energy_rbm(p, op, s)
+    assert np.all(np.abs(e - ref) <= 1e-4 * np.maximum(1.0, np.abs(ref))), np.abs(e - ref).max()
+    assert abs(e.mean() - ref.mean()) <= 1e-5 * max(1.0, abs(ref.mean()))
+    tref = np.tanh(orbm.theta(p, s))
+    assert np.all(np.abs(t.cpu().numpy() - tref) <= 2e-5 * np.maximum(1.0, np.abs(tref)))
+
+
+def test_local_energy_full_size_sampled(nk):
+    w = W.workload("c5")
+    p = W.perturb_params(W.init_params(w.n, w.m, True, 0.01, w.seed), 0.02, 5)
+    ns = 512
+    s = W.random_configs(ns, w.n, 13, True)
+    r = make_rbm(nk, p)
+    gop = nk.Operator(w.op)
+    th = torch.empty(ns, w.m, dtype=torch.complex64, device="cuda")
+    sg = dev(s)
+    nk.nk_rbm_logpsi(r, sg, theta_out=th)
+    e = nk.nk_local_energy(r, gop, sg, th).cpu().numpy()
+    idx = np.random.default_rng(1).choice(ns, 8, replace=False)
+    ref = ole.local_energy_rbm(p, w.op, s[idx])
+    assert np.all(np.abs(e[idx] - ref) <= 1e-4 * np.maximum(1.0, np.abs(ref)))
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_logderiv_dense(nk, cplx):
+    n, m, ns = 9, 13, 70
+    p = W.perturb_params(W.init_params(n, m, cplx, 0.01, 3), 0.2, 4)
+    s = W.random_configs(ns, n, 5)
+    r = make_rbm(nk, p)
+    th = torch.empty(ns, m, dtype=r.f32_dtype(), device="cuda")
+    sg = dev(s)
+    nk.nk_rbm_logpsi(r, sg, theta_out=th)
+    o = nk.nk_logderiv(r, sg, th, layout=nk.NK_LAYOUT_DENSE).cpu().numpy()
+    oref = orbm.logderiv_dense(p, s)
+    assert np.all(np.abs(o - oref) <= 2e-5 * np.maximum(1.0, np.abs(oref)))
+    t = nk.nk_logderiv(r, sg, th).cpu().numpy()
+    tref = np.tanh(orbm.theta(p, s))
+    assert np.all(np.abs(t - tref) <= 2e-5 * np.maximum(1.0, np.abs(tref)))
+
+
+# ---------------------------------------------------------------- sampling
+
+@pytest.mark.parametrize("move,n,m,cplx,G", [("flip", 10, 10, False, 8), ("flip", 24, 40, True, 4),
+                                             ("exchange", 12, 24, True, 8),
+                                             ("exchange", 20, 20, False, 1)])
+def test_metropolis_trajectories(nk, move, n, m, cplx, G):
+    p = W.perturb_params(W.init_params(n, m, cplx, 0.01, 77), 0.5 / np.sqrt(n), 3)
+    nc = 40
+    sz = move == "exchange"
+    s0 = W.init_chains(nc, n, sz, 8)
+    bonds = W.chain_bonds(n)
+    seed, counter, nd, nsamp = 0xC0FFEE1234, 5 * n, 2, 3
+    samp, fin, cnt, nacc, marg = osam.metropolis(p, s0, move, bonds, G, seed, counter, nd, nsamp,
+                                                 return_margin=True)
+    r = make_rbm(nk, p)
+    ch = nk.Chains(s0, G, seed)
+    ch.counter = counter
+    acc = torch.zeros(nc, dtype=torch.int64, device="cuda")
+    out = nk.nk_metropolis_sweep(r, ch, nk.NK_MOVE_FLIP if move == "flip" else nk.NK_MOVE_EXCHANGE,
+                                 dev(bonds[:, 0].copy()), dev(bonds[:, 1].copy()), nd, nsamp,
+                                 n_accept_out=acc)
+    assert ch.counter == cnt
+    got = out.cpu().numpy().reshape(nc, nsamp, n)
+    ref = samp.reshape(nc, nsamp, n)
+    ok = marg > 1e-3
+    assert ok.sum() >= nc // 2
+    assert np.array_equal(got[ok], ref[ok])
+    assert np.array_equal(ch.sigma.cpu().numpy()[ok], fin[ok])
+    assert np.array_equal(acc.cpu().numpy()[ok], nacc[ok])
+    if sz:
+        assert np.all(out.cpu().numpy().astype(int).sum(axis=1) == 0)
+
+
+@pytest.mark.parametrize("move", ["flip", "exchange"])
+def test_metropolis_samples_psi_squared(nk, move):
+    n = 8
+    sz = move == "exchange"
+    p = W.init_params(n, 8, True, 0.25, 31)
+    xs = oham.basis(n, sz)
+    pi = osam.exact_distribution(p, oham.configs(xs, n))
+    nc = 16384
+    r = make_rbm(nk, p)
+    ch = nk.Chains(W.init_chains(nc, n, sz, 12), 8, 2024)
+    bonds = W.chain_bonds(n)
+    out = nk.nk_metropolis_sweep(r, ch, nk.NK_MOVE_FLIP if move == "flip" else nk.NK_MOVE_EXCHANGE,
+                                 dev(bonds[:, 0].copy()), dev(bonds[:, 1].copy()), 400, 1)
+    ints = ((1 - out.cpu().numpy().astype(np.int64)) // 2) @ (1 << np.arange(n))
+    c = np.bincount(np.searchsorted(xs, ints), minlength=len(xs)).astype(np.float64)
+    exp = pi * nc
+    keep = exp >= 5
+    chi2 = np.sum((c[keep] - exp[keep]) ** 2 / exp[keep])
+    dof = keep.sum() - 1
+    assert chi2 < dof + 5 * np.sqrt(2 * dof)
+
+
+# ---------------------------------------------------------------- SR and backward
+
+def _sr_inputs(nk, n, m, cplx, ns, op, sz, seed=3):
+    p = W.perturb_params(W.init_params(n, m, cplx, 0.01, seed), 0.2 / np.sqrt(n), seed + 1)
+    s = W.random_configs(ns, n, seed + 2, sz)
+    r = make_rbm(nk, p)
+    gop = nk.Operator(op)
+    sg = dev(s)
+    th = torch.empty(ns, m, dtype=r.f32_dtype(), device="cuda")
+    nk.nk_rbm_logpsi(r, sg, theta_out=th)
+    t = torch.empty_like(th)
+    e = nk.nk_local_energy(r, gop, sg, th, t_out=t)
+    return p, s, r, sg, t, e
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_backward_is_the_adjoint(nk, cplx):
+    n, m, ns = 21, 45, 1000
+    p = W.perturb_params(W.init_params(n, m, cplx, 0.01, 2), 0.2, 3)
+    s = W.random_configs(ns, n, 4)
+    g = np.random.default_rng(5).normal(size=ns) + (1j * np.random.default_rng(6).normal(size=ns)
+                                                      if cplx else 0.0)
+    r = make_rbm(nk, p)
+    got = nk.nk_rbm_logpsi_backward(r, dev(s), dev(np.asarray(g, np.complex128))).cpu().numpy()
+    o = orbm.logderiv_dense(p, s)
+    ref = o.conj().T @ g
+    if not cplx:
+        ref = ref.real
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_sr_step_matches_oracle(nk, cplx):
+    n = 12
+    op = W.heisenberg(n, W.chain_bonds(n), 1.0, True, W.sublattice(n)) if cplx else \
+        W.ising(n, W.chain_bonds(n), h=1.0)
+    m, ns, nc = 2 * n, 2048, 64
+    p, s, r, sg, t, e = _sr_inputs(nk, n, m, cplx, ns, op, cplx)
+    eref = ole.local_energy_rbm(p, op, s)
+    sig, tref = orbm.logderiv_factored(p, s)
+    f = osr.force_lazy(sig, tref, eref, n, m, None, not cplx)
+    mean, var, err = osr.stats(eref, nc)
+    o = orbm.logderiv_dense(p, s)
+    smat, _ = osr.sr_matrices(o, eref, None, not cplx)
+    delta = osr.solve_dense(smat, f, 0.01)
+    P = p.n_params
+    info = nk.info_dict(nk.nk_sr_step(r, sg, t, e, nc, 0.01, 0.05, n_cg=4 * P, cg_rtol=1e-10))
+    assert abs(info["energy"] - mean.real) <= 1e-5 * abs(mean.real)
+    assert abs(info["variance"] - var) <= 1e-4 * var
+    assert abs(info["error"] - err) <= 1e-4 * err
+    assert abs(info["f_norm"] - np.linalg.norm(f)) <= 1e-5 * np.linalg.norm(f)
+    assert info["cg_resid"] <= 1e-6
+    a, b, w = r.params_numpy()
+    newp = np.concatenate([a, b, w.reshape(-1)])
+    d_gpu = (p.flat() - newp) / 0.05
+    assert np.linalg.norm(d_gpu - delta) <= 1e-3 * np.linalg.norm(delta)
+
+
+def test_sr_fixed_iterations_and_flags(nk):
+    n, m, ns = 10, 10, 1008
+    op = W.ising(n, W.chain_bonds(n), h=1.0)
+    p, s, r, sg, t, e = _sr_inputs(nk, n, m, False, ns, op, False)
+    eref = ole.local_energy_rbm(p, op, s)
+    sig, tref = orbm.logderiv_factored(p, s)
+    f = osr.force_lazy(sig, tref, eref, n, m, None, True)
+    x, it, res = osr.cg(lambda v: osr.sr_matvec_lazy(sig, tref, v, n, m, None, True), f, 0.01, 5,
+                        1e-12)
+    info = nk.info_dict(nk.nk_sr_step(r, sg, t, e, 16, 0.01, 0.1, n_cg=5, cg_rtol=1e-12))
+    assert info["cg_iters"] == 5 and int(info["flags"]) & (1 << 4)
+    a, b, w = r.params_numpy()
+    d_gpu = (p.flat() - np.concatenate([a, b, w.reshape(-1)])) / 0.1
+    assert np.linalg.norm(d_gpu - x) <= 1e-3 * np.linalg.norm(x)
+    assert abs(info["cg_resid"] - res) <= 1e-2 * res
