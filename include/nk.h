@@ -215,6 +215,28 @@ nk_status nk_sr_step(nk_rbm* rbm, const int8_t* sigma, const void* t, const doub
                      double lr, int32_t n_cg, double cg_rtol, int32_t prec, void* scratch,
                      size_t scratch_bytes, double* info_out, void* stream);
 
+/* Size of the built-in scratch array used by nk_sr_step_noalloc (16 MiB). */
+#define NK_SR_NOALLOC_MAX_BYTES (16u << 20)
+
+/* nk_sr_step for callers that cannot allocate device memory (a framework that
+ * owns the allocator and forbids raw cudaMalloc, a plugin handed only a stream
+ * and its tensors, a loop that must not block on allocation).  The paper has
+ * no counterpart: this is a deployment variant of the SR step above, with the
+ * same arguments minus the scratch, and the same results.
+ *   Scratch comes from one static device array of NK_SR_NOALLOC_MAX_BYTES in
+ *   the library image, present on every GPU that loads the library until exit.
+ *   Problems needing more (nk_sr_scratch_bytes(n, m, is_complex, ns) above the
+ *   limit) return NK_ERR_SHAPE with nothing enqueued.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make it before any
+ *   stream capture.  All calls share the array: calls that overlap on the GPU
+ *   race and must be serialised by the caller.  No memory is allocated or
+ *   freed. */
+nk_status nk_sr_step_noalloc(nk_rbm* rbm, const int8_t* sigma, const void* t, const double* eloc,
+                             const double* weights, int64_t ns, int32_t n_chains,
+                             double diag_shift, double lr, int32_t n_cg, double cg_rtol,
+                             int32_t prec, double* info_out, void* stream);
+
 /* Scratch bytes nk_rbm_logpsi_backward needs for ns samples. */
 size_t nk_backward_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns);
 

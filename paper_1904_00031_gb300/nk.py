@@ -32,8 +32,9 @@ EXPORTS = (
     "nk_status_string", "nk_last_error", "nk_device_supported", "nk_rbm_workspace_bytes",
     "nk_rbm_prepare", "nk_rbm_logpsi", "nk_metropolis_sweep", "nk_operator_bytes",
     "nk_operator_upload", "nk_local_energy", "nk_logderiv", "nk_sr_scratch_bytes", "nk_sr_step",
-    "nk_backward_scratch_bytes", "nk_rbm_logpsi_backward",
+    "nk_backward_scratch_bytes", "nk_rbm_logpsi_backward", "nk_sr_step_noalloc",
 )
+NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
 
 class NkError(RuntimeError):
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         "nk_sr_step": (I32, [P, P, P, P, P, I64, I32, D, D, I32, D, I32, P, SZ, P, P]),
         "nk_backward_scratch_bytes": (SZ, [I32, I32, I32, I64]),
         "nk_rbm_logpsi_backward": (I32, [P, P, I64, P, P, I32, P, SZ, P]),
+        "nk_sr_step_noalloc": (I32, [P, P, P, P, P, I64, I32, D, D, I32, D, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -321,3 +323,19 @@ def nk_rbm_logpsi_backward(rbm: Rbm, sigma, g, prec=NK_PREC_FP32, grad_out=None,
                                                  scratch.numel(), _stream(stream)),
            "nk_rbm_logpsi_backward")
     return grad_out
+
+
+def nk_sr_step_noalloc(rbm: Rbm, sigma, t, eloc, n_chains: int, diag_shift: float, lr: float,
+                       n_cg: int, cg_rtol: float = 1e-12, prec=NK_PREC_FP32, weights=None,
+                       info_out=None, stream=None):
+    """nk_sr_step with the library's built-in scratch array (no scratch argument);
+    for callers that cannot allocate device memory.  Calls must not overlap."""
+    _require_gpu(sigma, t, eloc, weights, info_out)
+    ns = sigma.shape[0]
+    if info_out is None:
+        info_out = torch.zeros(NK_INFO_LEN, dtype=torch.float64, device=sigma.device)
+    _check(load_library().nk_sr_step_noalloc(
+        rbm.struct(), _ptr(sigma), _ptr(t), _ptr(eloc), _ptr(weights), ns, n_chains,
+        float(diag_shift), float(lr), int(n_cg), float(cg_rtol), prec, _ptr(info_out),
+        _stream(stream)), "nk_sr_step_noalloc")
+    return info_out
