@@ -143,6 +143,10 @@ nk_status nk_rbm_logpsi(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int3
 
 /* ---------------------------------------------------------------- sampling */
 
+/* Scratch bytes nk_metropolis_sweep needs (0 for flips: NULL scratch is fine). */
+size_t nk_metropolis_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int32_t move,
+                                   int32_t n_bonds);
+
 /* Metropolis sampling of |psi|^2 (Eq. 4; Sec. 2.2.5), single-spin-flip or
  * nearest-neighbour exchange moves (the MetropolisExchange of the VMC listing,
  * Sec. 3.1).  Every chain runs n_discard + n_samples_per_chain sweeps of n
@@ -154,13 +158,18 @@ nk_status nk_rbm_logpsi(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int3
  *   bond_i, bond_k  int32 [n_bonds] exchange bonds (ignored for FLIP; may be NULL)
  *   samples_out     int8 [nc * n_samples_per_chain][n], chain-major
  *                   (row c * n_samples_per_chain + s)
- *   n_accept_out    uint64 [nc] accepted proposals per chain in this call, or NULL
+ *   n_accept_out    uint64 [nc] accepted proposals per chain in this call, or NULL.
+ *                   UINT64_MAX marks a chain whose CTA gave up waiting for a
+ *                   table copy (bounded wait; the call's results are then invalid)
+ *   scratch         nk_metropolis_scratch_bytes(...) bytes, 256-B aligned
+ *                   (per-bond tables of exchange moves); may be NULL for FLIP
  * chains->sigma is updated in place and chains->counter advanced by
  * (n_discard + n_samples_per_chain) * n on success. */
 nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move,
                               const int32_t* bond_i, const int32_t* bond_k, int32_t n_bonds,
                               int32_t n_discard, int32_t n_samples_per_chain,
-                              int8_t* samples_out, uint64_t* n_accept_out, void* stream);
+                              int8_t* samples_out, uint64_t* n_accept_out, void* scratch,
+                              size_t scratch_bytes, void* stream);
 
 /* ---------------------------------------------------------------- operators */
 

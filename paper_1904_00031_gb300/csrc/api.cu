@@ -124,9 +124,25 @@ static nk_status compile_op(const nk_operator* op, Compiled& out) {
   }
   for (auto& kv : moves) {
     const OpMove& m = kv.second;
-    bool any = false;
-    for (int x = 0; x < 4; ++x) any |= nz(m.mel[x]);
-    if (any) out.mv.push_back(m);
+    if (!m.two) {
+      bool any = false;
+      for (int x = 0; x < 4; ++x) any |= nz(m.mel[x]);
+      if (any) out.mv.push_back(m);
+      continue;
+    }
+    // split a two-spin move into its aligned (x = 0, 3) and anti-aligned
+    // (x = 1, 2) parts: the ratio kernels use one (cosh c, sinh c) table per move
+    for (int align = 1; align >= -1; align -= 2) {
+      OpMove v = m;
+      v.align = align;
+      bool any = false;
+      for (int x = 0; x < 4; ++x) {
+        bool aligned = (x == 0 || x == 3);
+        if (aligned != (align == 1)) v.mel[x][0] = v.mel[x][1] = 0.0;
+        any |= nz(v.mel[x]);
+      }
+      if (any) out.mv.push_back(v);
+    }
   }
   return NK_OK;
 }
@@ -201,10 +217,17 @@ nk_status nk_rbm_logpsi(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int3
   return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi: unknown precision %d", prec);
 }
 
+size_t nk_metropolis_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int32_t move,
+                                   int32_t n_bonds) {
+  if (n < 1 || m < 1 || n_bonds < 0 || move != NK_MOVE_EXCHANGE) return 0;
+  return metropolis_scratch_bytes(n, m, is_complex ? 1 : 0, n_bonds);
+}
+
 nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move,
                               const int32_t* bond_i, const int32_t* bond_k, int32_t n_bonds,
                               int32_t n_discard, int32_t n_samples_per_chain,
-                              int8_t* samples_out, uint64_t* n_accept_out, void* stream) {
+                              int8_t* samples_out, uint64_t* n_accept_out, void* scratch,
+                              size_t scratch_bytes, void* stream) {
   if (nk_status e = check_rbm(rbm, "nk_metropolis_sweep")) return e;
   if (!chains || !chains->sigma)
     return fail(NK_ERR_INVALID_ARG, "nk_metropolis_sweep: NULL chains");
@@ -219,10 +242,12 @@ nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move
     return fail(NK_ERR_INVALID_ARG, "nk_metropolis_sweep: exchange moves need a bond list");
   if (n_samples_per_chain > 0 && !samples_out)
     return fail(NK_ERR_INVALID_ARG, "nk_metropolis_sweep: NULL samples_out");
+  if (scratch && (((uintptr_t)scratch) & 255))
+    return fail(NK_ERR_INVALID_ARG, "nk_metropolis_sweep: scratch not 256-byte aligned");
   if (chains->nc == 0 || n_discard + n_samples_per_chain == 0) return NK_OK;
   nk_status e = launch_metropolis(rbm, chains, move, bond_i, bond_k, n_bonds, n_discard,
-                                  n_samples_per_chain, samples_out, n_accept_out,
-                                  (cudaStream_t)stream);
+                                  n_samples_per_chain, samples_out, n_accept_out, scratch,
+                                  scratch_bytes, (cudaStream_t)stream);
   if (e == NK_OK) chains->counter += (uint64_t)(n_discard + n_samples_per_chain) * rbm->n;
   return e;
 }

@@ -25,7 +25,9 @@ nk_status launch_logpsi_bf16(const nk_rbm* r, const int8_t* sigma, int64_t ns, d
 
 nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int32_t* bi,
                             const int32_t* bk, int nb, int n_discard, int n_samples,
-                            int8_t* samples, uint64_t* n_acc, cudaStream_t st);
+                            int8_t* samples, uint64_t* n_acc, void* scratch, size_t scratch_bytes,
+                            cudaStream_t st);
+size_t metropolis_scratch_bytes(int n, int m, int cplx, int nb);
 
 nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, const int8_t* sigma,
                               const void* theta, int64_t ns, double* eloc, void* t_out,

@@ -3,12 +3,10 @@
 // the factored log-derivatives T = tanh(theta) (Sec. 2.2.5: O_b = tanh theta,
 // O_W = tanh theta (x) sigma, O_a = sigma).
 //
-// One warp per configuration.  The warp loads theta, keeps t = tanh(theta) in
-// registers (writing T out as a side product) and walks the compiled move
-// list; every move's psi ratio is exp(visible) * prod_j (cosh c_j - t_j sinh c_j)
-// from the cosh/sinh(2W) tables, with the product kept as mantissa * 2^e.  All
-// warps of a CTA walk the same list, so the table columns of a move are read
-// from L2 once per CTA.  Sums are FP64.
+// Every move's psi ratio is exp(visible) * prod_j (cosh c_j - t_j sinh c_j)
+// (c = 2 s_i W_i (+ 2 s_k W_k), t = tanh theta) from the cosh/sinh(2W) tables,
+// with each running product kept as mantissa * 2^e; matrix elements, visible
+// factors and the sums over moves are FP64.
 #include "common.cuh"
 #include "internal.h"
 #include "opdev.h"
@@ -30,172 +28,294 @@ struct ElocArgs {
 
 __device__ __forceinline__ int idx_of(int8_t s) { return s > 0 ? 0 : 1; }
 
-template <bool CPLX, int E>
-__global__ void __launch_bounds__(256) local_energy_kernel(ElocArgs A) {
+// Tiled form: a CTA owns 64 configurations and walks the move list in tiles of
+// 64 moves; per chunk of 16 hidden units it stages t = tanh(theta) of its
+// configurations and (cosh c, sinh c / s_i) of the tile's moves in shared
+// memory, and every thread advances a 4 x 4 block of running products
+// prod_j (cosh c_j - s_i t_j sinh c_j / s_i) held in registers: each staged value
+// is reused by 16 threads, so the kernel is bound by the FP32 pipe rather
+// than by the memory system.  A two-spin move with cosh c = A_i A_k +/- B_i B_k,
+// sinh c / s_i = B_i A_k +/- A_i B_k is built in the staging step from the
+// site tables; the sign is fixed per move (alignment split at compilation).
+constexpr int kEBS = 64;   // configurations per CTA
+constexpr int kEBM = 64;   // moves per tile
+constexpr int kEBK = 16;   // hidden units per chunk
+constexpr int kERenorm = 8;
+
+template <bool CPLX>
+struct EScaled;
+template <>
+struct EScaled<true> {
+  using S = ScaledComplex;
+};
+template <>
+struct EScaled<false> {
+  using S = ScaledReal;
+};
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256) local_energy_tiled(ElocArgs A) {
   using F = typename RatioTypes<CPLX>::F;
   using T2 = typename RatioTypes<CPLX>::T2;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + w;
-  if (s >= A.ns) return;
-  const int n = A.n, m = A.m, mp = A.mp, e = mp >> 5;
-  const int8_t* sg = A.sigma + s * n;
-  const F* th = reinterpret_cast<const F*>(A.theta) + s * m;
-  F* tout = reinterpret_cast<F*>(A.t_out);
-  F t[E];
-#pragma unroll
-  for (int q = 0; q < E; ++q) {
-    if (q < e) {
-      const int j = lane + 32 * q;
-      if constexpr (CPLX) {
-        t[q] = make_float2(0.f, 0.f);
-        if (j < m) {
-          F v = th[j];
-          cf tt = tanh_c(cf{v.x, v.y});
-          t[q] = make_float2(tt.x, tt.y);
-          if (tout) tout[s * m + j] = t[q];
-        }
-      } else {
-        t[q] = 0.f;
-        if (j < m) {
-          t[q] = tanh_f(th[j]);
-          if (tout) tout[s * m + j] = t[q];
-        }
-      }
-    }
-  }
+  __shared__ __align__(16) F tS[kEBK][kEBS];
+  __shared__ __align__(16) F Cs[kEBK][kEBM];
+  __shared__ __align__(16) F Ds[kEBK][kEBM];
+  __shared__ int mvi[kEBM], mvk[kEBM], mvtwo[kEBM], mval[kEBM];
+  __shared__ double2 cvs[kEBM][4];  // mel(x) * exp(visible(x)) per sign pattern x
+
+  const int tid = threadIdx.x, ts = tid >> 4, tm = tid & 15;
+  const int64_t s0 = (int64_t)blockIdx.x * kEBS;
+  const int n = A.n, m = A.m, mp = A.mp;
   const OpDevHeader* H = reinterpret_cast<const OpDevHeader*>(A.op);
   const OpDSite* ds = reinterpret_cast<const OpDSite*>(A.op + H->off_dsite);
   const OpDBond* db = reinterpret_cast<const OpDBond*>(A.op + H->off_dbond);
-  const OpMove* mv = reinterpret_cast<const OpMove*>(A.op + H->off_moves);
-  // diagonal part, lanes split the terms
-  double er = 0.0, ei = 0.0;
-  for (int u = lane; u < H->n_dsite; u += 32) {
-    int x = idx_of(sg[ds[u].i]);
-    er += ds[u].d[x][0];
-    ei += ds[u].d[x][1];
-  }
-  for (int u = lane; u < H->n_dbond; u += 32) {
-    int x = 2 * idx_of(sg[db[u].i]) + idx_of(sg[db[u].k]);
-    er += db[u].d[x][0];
-    ei += db[u].d[x][1];
-  }
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    er += __shfl_xor_sync(0xffffffffu, er, off);
-    ei += __shfl_xor_sync(0xffffffffu, ei, off);
-  }
+  const OpMove* mvs = reinterpret_cast<const OpMove*>(A.op + H->off_moves);
   const T2* tab = reinterpret_cast<const T2*>(A.tab);
+  const F* th = reinterpret_cast<const F*>(A.theta);
+  F* tout = reinterpret_cast<F*>(A.t_out);
+
+  // diagonal part: the 16 threads of a configuration split the terms
+  double er[4], ei[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    er[p] = ei[p] = 0.0;
+    const int64_t s = s0 + ts * 4 + p;
+    if (s >= A.ns) continue;
+    const int8_t* sg = A.sigma + s * n;
+    for (int u = tm; u < H->n_dsite; u += 16) {
+      int x = idx_of(sg[ds[u].i]);
+      er[p] += ds[u].d[x][0];
+      ei[p] += ds[u].d[x][1];
+    }
+    for (int u = tm; u < H->n_dbond; u += 16) {
+      int x = 2 * idx_of(sg[db[u].i]) + idx_of(sg[db[u].k]);
+      er[p] += db[u].d[x][0];
+      ei[p] += db[u].d[x][1];
+    }
+  }
+
   const int nm = H->n_moves;
-  for (int u = 0; u < nm; ++u) {
-    const int i = mv[u].i, k = mv[u].k, two = mv[u].two;
-    const int8_t sik = sg[i], skk = sg[k];
-    const int x = 2 * idx_of(sik) + idx_of(skk);
-    const double mr = mv[u].mel[x][0], mi = mv[u].mel[x][1];
-    if (mr == 0.0 && mi == 0.0) continue;  // warp-uniform
-    const float si = (float)sik, sk = (float)skk;
-    const T2* ti = tab + (int64_t)i * mp;
-    const T2* tk = tab + (int64_t)k * mp;
-    double pr, pi;  // prod_j r_j (complex double after the warp reduction)
-    if constexpr (CPLX) {
-      ScaledComplex P;
-      P.init();
-#pragma unroll
-      for (int q = 0; q < E; ++q) {
-        if (q < e) {
-          const int j = lane + 32 * q;
-          cf C, S;
-          if (!two) move_coef(ti[j], si, C, S);
-          else move_coef2(ti[j], tk[j], si, sk, C, S);
-          P.v = P.v * (C - cf{t[q].x, t[q].y} * S);
-          if ((q & 3) == 3) P.renorm();
+  for (int mt0 = 0; mt0 < nm; mt0 += kEBM) {
+    __syncthreads();
+    if (tid < kEBM) {
+      const int mv = mt0 + tid;
+      if (mv < nm) {
+        mvi[tid] = mvs[mv].i;
+        mvk[tid] = mvs[mv].k;
+        mvtwo[tid] = mvs[mv].two;
+        mval[tid] = mvs[mv].align;
+      } else {
+        mvi[tid] = 0;
+        mvk[tid] = 0;
+        mvtwo[tid] = -1;  // padding move: ratio 1, coefficient 0
+        mval[tid] = 1;
+      }
+    }
+    {
+      const int mm = tid >> 2, x = tid & 3, mv = mt0 + mm;
+      double cr = 0.0, ci = 0.0;
+      if (mv < nm) {
+        const double mr = mvs[mv].mel[x][0], mi = mvs[mv].mel[x][1];
+        if (mr != 0.0 || mi != 0.0) {
+          const double si = (x >> 1) ? -1.0 : 1.0, sk = (x & 1) ? -1.0 : 1.0;
+          const int i = mvs[mv].i, k = mvs[mv].k;
+          double vr, vi;
+          if (CPLX) {
+            vr = -2.0 * si * A.a[2 * i];
+            vi = -2.0 * si * A.a[2 * i + 1];
+            if (mvs[mv].two) {
+              vr += -2.0 * sk * A.a[2 * k];
+              vi += -2.0 * sk * A.a[2 * k + 1];
+            }
+          } else {
+            vr = -2.0 * si * A.a[i];
+            vi = 0.0;
+            if (mvs[mv].two) vr += -2.0 * sk * A.a[k];
+          }
+          const double ev = exp(vr), fr = ev * cos(vi), fi = ev * sin(vi);
+          cr = mr * fr - mi * fi;
+          ci = mr * fi + mi * fr;
         }
       }
-      P.renorm();
+      cvs[mm][x] = make_double2(cr, ci);
+    }
+    __syncthreads();
+    float sgn[4][4];
 #pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) {
-        ScaledComplex o;
-        o.v.x = __shfl_xor_sync(0xffffffffu, P.v.x, off);
-        o.v.y = __shfl_xor_sync(0xffffffffu, P.v.y, off);
-        o.e = __shfl_xor_sync(0xffffffffu, P.e, off);
-        mul_scaled(P, o);
+    for (int p = 0; p < 4; ++p) {
+      const int64_t s = s0 + ts * 4 + p;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int mm = tm + 16 * q;
+        sgn[p][q] = (s < A.ns) ? (float)A.sigma[s * n + mvi[mm]] : 1.f;
       }
-      pr = ldexp((double)P.v.x, P.e);
-      pi = ldexp((double)P.v.y, P.e);
-    } else {
-      ScaledReal P;
-      P.init();
+    }
+    typename EScaled<CPLX>::S P[4][4];
 #pragma unroll
-      for (int q = 0; q < E; ++q) {
-        if (q < e) {
-          const int j = lane + 32 * q;
-          float C, S;
-          if (!two) move_coef(ti[j], si, C, S);
-          else move_coef2(ti[j], tk[j], si, sk, C, S);
-          P.v *= fmaf(-t[q], S, C);
-          if ((q & 3) == 3) P.renorm();
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) P[p][q].init();
+
+    for (int k0 = 0; k0 < mp; k0 += kEBK) {
+      __syncthreads();
+      // stage t = tanh(theta): 64 configurations x 16 hidden units
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = tid + u * 256, ss = e >> 4, kk = e & 15;
+        const int64_t s = s0 + ss;
+        const int j = k0 + kk;
+        F tv;
+        if constexpr (CPLX) {
+          tv = make_float2(0.f, 0.f);
+          if (s < A.ns && j < m) {
+            F x = th[s * m + j];
+            cf c = tanh_c(cf{x.x, x.y});
+            tv = make_float2(c.x, c.y);
+            if (tout && mt0 == 0) tout[s * m + j] = tv;
+          }
+        } else {
+          tv = 0.f;
+          if (s < A.ns && j < m) {
+            tv = tanh_f(th[s * m + j]);
+            if (tout && mt0 == 0) tout[s * m + j] = tv;
+          }
+        }
+        tS[kk][ss] = tv;
+      }
+      // stage (cosh c, sinh c / s_i) of 64 moves x 16 hidden units
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = tid + u * 256, mm = e >> 4, kk = e & 15;
+        const int j = k0 + kk;
+        const int two = mvtwo[mm];
+        F C, D;
+        if constexpr (CPLX) {
+          if (two < 0) {
+            C = make_float2(1.f, 0.f);
+            D = make_float2(0.f, 0.f);
+          } else {
+            const float4 ai = tab[(int64_t)mvi[mm] * mp + j];
+            if (!two) {
+              C = make_float2(ai.x, ai.y);
+              D = make_float2(ai.z, ai.w);
+            } else {
+              const float4 ak = tab[(int64_t)mvk[mm] * mp + j];
+              const float al = (float)mval[mm];
+              cf Ai{ai.x, ai.y}, Bi{ai.z, ai.w}, Ak{ak.x, ak.y}, Bk{ak.z, ak.w};
+              cf c = Ai * Ak + al * (Bi * Bk);
+              cf d = Bi * Ak + al * (Ai * Bk);
+              C = make_float2(c.x, c.y);
+              D = make_float2(d.x, d.y);
+            }
+          }
+        } else {
+          if (two < 0) {
+            C = 1.f;
+            D = 0.f;
+          } else {
+            const float2 ai = tab[(int64_t)mvi[mm] * mp + j];
+            if (!two) {
+              C = ai.x;
+              D = ai.y;
+            } else {
+              const float2 ak = tab[(int64_t)mvk[mm] * mp + j];
+              const float al = (float)mval[mm];
+              C = fmaf(al * ai.y, ak.y, ai.x * ak.x);
+              D = fmaf(al * ai.x, ak.y, ai.y * ak.x);
+            }
+          }
+        }
+        Cs[kk][mm] = C;
+        Ds[kk][mm] = D;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < kEBK; ++kk) {
+        F t[4], C[4], D[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) t[p] = tS[kk][ts * 4 + p];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          C[q] = Cs[kk][tm + 16 * q];
+          D[q] = Ds[kk][tm + 16 * q];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if constexpr (CPLX) {
+              const float tdx = fmaf(t[p].x, D[q].x, -t[p].y * D[q].y);
+              const float tdy = fmaf(t[p].x, D[q].y, t[p].y * D[q].x);
+              const float rx = fmaf(-sgn[p][q], tdx, C[q].x);
+              const float ry = fmaf(-sgn[p][q], tdy, C[q].y);
+              P[p][q].v = P[p][q].v * cf{rx, ry};
+            } else {
+              P[p][q].v *= fmaf(-sgn[p][q] * t[p], D[q], C[q]);
+            }
+          }
+        }
+        if ((kk % kERenorm) == kERenorm - 1) {
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) P[p][q].renorm();
         }
       }
-      P.renorm();
+    }
+    // fold the tile's ratios into the local energies (FP64)
 #pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) {
-        float ov = __shfl_xor_sync(0xffffffffu, P.v, off);
-        int oe = __shfl_xor_sync(0xffffffffu, P.e, off);
-        P.v *= ov;
-        P.e += oe;
-        P.renorm();
+    for (int p = 0; p < 4; ++p) {
+      const int64_t s = s0 + ts * 4 + p;
+      if (s >= A.ns) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int mm = tm + 16 * q;
+        if (mvtwo[mm] < 0) continue;
+        const int x = 2 * idx_of(A.sigma[s * n + mvi[mm]]) + idx_of(A.sigma[s * n + mvk[mm]]);
+        const double2 cv = cvs[mm][x];
+        if (cv.x == 0.0 && cv.y == 0.0) continue;
+        double pr, pi;
+        if constexpr (CPLX) {
+          pr = ldexp((double)P[p][q].v.x, P[p][q].e);
+          pi = ldexp((double)P[p][q].v.y, P[p][q].e);
+        } else {
+          pr = ldexp((double)P[p][q].v, P[p][q].e);
+          pi = 0.0;
+        }
+        er[p] += cv.x * pr - cv.y * pi;
+        ei[p] += cv.x * pi + cv.y * pr;
       }
-      pr = ldexp((double)P.v, P.e);
-      pi = 0.0;
     }
-    // visible factor exp(-2 s_i a_i (- 2 s_k a_k)), FP64
-    double vr, vi;
-    if constexpr (CPLX) {
-      vr = -2.0 * si * A.a[2 * i];
-      vi = -2.0 * si * A.a[2 * i + 1];
-      if (two) {
-        vr += -2.0 * sk * A.a[2 * k];
-        vi += -2.0 * sk * A.a[2 * k + 1];
+  }
+  // the 16 threads of a configuration are lanes tid ^ 1, 2, 4, 8 of one warp
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+#pragma unroll
+    for (int off = 8; off >= 1; off >>= 1) {
+      er[p] += __shfl_xor_sync(0xffffffffu, er[p], off);
+      ei[p] += __shfl_xor_sync(0xffffffffu, ei[p], off);
+    }
+    const int64_t s = s0 + ts * 4 + p;
+    if (tm == 0 && s < A.ns) {
+      A.eloc[2 * s] = er[p];
+      A.eloc[2 * s + 1] = ei[p];
+    }
+  }
+  // with no moves at all, t = tanh(theta) is still written
+  if (nm == 0 && tout) {
+    for (int e = tid; e < kEBS * m; e += blockDim.x) {
+      const int64_t s = s0 + e / m;
+      const int j = e % m;
+      if (s >= A.ns) continue;
+      if constexpr (CPLX) {
+        F x = th[s * m + j];
+        cf c = tanh_c(cf{x.x, x.y});
+        tout[s * m + j] = make_float2(c.x, c.y);
+      } else {
+        tout[s * m + j] = tanh_f(th[s * m + j]);
       }
-    } else {
-      vr = -2.0 * si * A.a[i];
-      vi = 0.0;
-      if (two) vr += -2.0 * sk * A.a[k];
     }
-    double ev = exp(vr), c = cos(vi), sn = sin(vi);
-    double fr = ev * c, fi = ev * sn;                   // exp(visible)
-    double qr = fr * pr - fi * pi, qi = fr * pi + fi * pr;  // ratio psi'/psi
-    er += mr * qr - mi * qi;
-    ei += mr * qi + mi * qr;
   }
-  if (lane == 0) {
-    A.eloc[2 * s] = er;
-    A.eloc[2 * s + 1] = ei;
-  }
-}
-
-template <bool CPLX, int E>
-static nk_status launch_e(const ElocArgs& A, cudaStream_t st) {
-  const int warps = 8;
-  int64_t blocks = (A.ns + warps - 1) / warps;
-  local_energy_kernel<CPLX, E><<<(unsigned)blocks, 32 * warps, 0, st>>>(A);
-  return check_launch("nk_local_energy");
-}
-
-template <bool CPLX>
-static nk_status launch_c(const ElocArgs& A, cudaStream_t st) {
-  int e = A.mp / 32;
-  if (e <= 1) return launch_e<CPLX, 1>(A, st);
-  if (e <= 2) return launch_e<CPLX, 2>(A, st);
-  if (e <= 4) return launch_e<CPLX, 4>(A, st);
-  if (e <= 8) return launch_e<CPLX, 8>(A, st);
-  if (e <= 13) return launch_e<CPLX, 13>(A, st);
-  if (e <= 16) return launch_e<CPLX, 16>(A, st);
-  if (e <= 25) return launch_e<CPLX, 25>(A, st);
-  if (e <= 32) return launch_e<CPLX, 32>(A, st);
-  if (e <= 50) return launch_e<CPLX, 50>(A, st);
-  if (e <= 64) return launch_e<CPLX, 64>(A, st);
-  return fail(NK_ERR_SHAPE, "nk_local_energy: m = %d exceeds the register-resident limit 2048",
-              A.m);
 }
 
 nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, const int8_t* sigma,
@@ -214,7 +334,12 @@ nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, const int8_t*
   A.tab = (const char*)r->ws + L.tab;
   A.eloc = eloc;
   A.t_out = t_out;
-  return r->is_complex ? launch_c<true>(A, st) : launch_c<false>(A, st);
+  const int64_t blocks = (ns + kEBS - 1) / kEBS;
+  if (r->is_complex)
+    local_energy_tiled<true><<<(unsigned)blocks, 256, 0, st>>>(A);
+  else
+    local_energy_tiled<false><<<(unsigned)blocks, 256, 0, st>>>(A);
+  return check_launch("nk_local_energy");
 }
 
 // ------------------------------------------------------------------ K4 logderiv

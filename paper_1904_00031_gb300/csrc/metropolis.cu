@@ -1,18 +1,27 @@
 // K2: Metropolis sampling of |psi|^2 (Eq. 4; Sec. 2.2.5), single-spin flips or
 // nearest-neighbour exchanges (MetropolisExchange of the VMC listing, Sec. 3.1).
 //
-// One warp runs one chain; a CTA runs one proposal group (all its chains draw
-// the same site or bond at a step, so their table reads hit the same L1 lines).
+// One warp runs one chain; a CTA runs one proposal group, whose chains all
+// propose the same site (bond) at a step.  Per proposal the ratio needs, for
+// every hidden unit j, the column (cosh c_j, sinh c_j / s_i) of the move and,
+// on acceptance, its theta increment W_i (- W_k): flips read them from the
+// site tables of the RBM workspace, exchanges from per-bond tables built at
+// the start of the call in the caller's scratch.  One thread streams each
+// step's columns into shared memory with 1-D TMA bulk copies, double-buffered
+// and issued two steps ahead, so the warps read every table value from shared
+// memory once per chain.
+//
 // Per chain: sigma and theta live in shared memory, t = tanh(theta) in
-// registers (lane l owns j = l + 32 q).  A proposal costs, per hidden unit, one
-// table read and ~6 (real) / ~12 (complex) FMAs: |r_j|^2 with
-// r_j = cosh c_j - t_j sinh c_j; the product over j is kept as mantissa * 2^e.
-// Accepted moves update theta additively (theta -= 2 s W_i) and refresh
-// t = tanh(theta) for the chain.  Philox draws are made 32 steps at a time, one
-// step per lane, and broadcast by shuffles.
+// registers (lane l owns j = l + 32 q).  A proposal costs per hidden unit
+// r_j = cosh c_j - s_i t_j (sinh c_j / s_i), |r_j|^2 and a running product
+// (mantissa * 2^e).  An accepted move updates theta += -2 s_i W_i (- 2 s_k W_k)
+// and t by the tanh addition formula t' = (t cosh c - sinh c) / r; t is
+// recomputed exactly from theta after every sweep.  Philox draws are made 32
+// steps at a time, one step per lane, and broadcast by shuffles.
 #include "common.cuh"
 #include "internal.h"
 #include "ratio.cuh"
+#include "tma.cuh"
 
 namespace nk {
 
@@ -25,8 +34,9 @@ struct MetroArgs {
   int8_t* samples;      // [nc * n_samples][n]
   uint64_t* n_acc;      // [nc] or null
   const double* a;      // master a (F64)
-  const void* tab;      // [n][mp] T2
-  const void* wt;       // [n][mp] F
+  const void* cd;       // [rows][mp] T2: (cosh c, sinh c / s_i) per site (flip) or bond
+  const void* wd;       // [rows][mp] F : W_i (flip) or W_i - W_k (bond)
+  const void* wt;       // [n][mp] F    : W transposed (initial theta)
   const void* b32;      // [mp] F
 };
 
@@ -41,60 +51,114 @@ __device__ __forceinline__ bool accept_test(double U, float two_re) {
   return U < exp((double)two_re);
 }
 
+__device__ __forceinline__ int move_row(const MetroArgs& A, uint32_t g, int step) {
+  u4 us = philox_stream(g, A.counter + (uint64_t)step, kTagSite, A.seed);
+  return uniform_index(us.x, A.move == NK_MOVE_FLIP ? A.n : A.nb);
+}
+
 template <bool CPLX, int E>
-__global__ void __launch_bounds__(256) metropolis_kernel(MetroArgs A) {
+__global__ void __launch_bounds__(256, 1) metropolis_kernel(MetroArgs A) {
   using F = typename RatioTypes<CPLX>::F;
   using T2 = typename RatioTypes<CPLX>::T2;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int c = blockIdx.x * A.G + w;
-  if (w >= A.G || c >= A.nc) return;
-  const int n = A.n, mp = A.mp, e = mp >> 5;
-  F* th = reinterpret_cast<F*>(smem) + (size_t)w * mp;
-  int8_t* sg = reinterpret_cast<int8_t*>(smem + (size_t)A.G * mp * sizeof(F)) +
-               (size_t)w * round_up(n, 16);
-  const T2* tab = reinterpret_cast<const T2*>(A.tab);
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int mp = A.mp, n = A.n, e = mp >> 5, G = A.G;
+  T2* colCD = reinterpret_cast<T2*>(smem);                                  // [2][mp]
+  F* colW = reinterpret_cast<F*>(smem + 2 * (size_t)mp * sizeof(T2));       // [2][mp]
+  F* thall = reinterpret_cast<F*>(reinterpret_cast<char*>(colW) + 2 * (size_t)mp * sizeof(F));
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(thall) +
+                                               (size_t)G * mp * sizeof(F));
+  int8_t* sgall = reinterpret_cast<int8_t*>(mbar + 2);
+  const int n16 = (int)round_up(n, 16);
+
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int c = blockIdx.x * G + w;
+  const bool active = (w < G) && (c < A.nc);
+  const uint32_t g = (uint32_t)blockIdx.x;
+  F* th = thall + (size_t)(active ? w : 0) * mp;
+  int8_t* sg = sgall + (size_t)(active ? w : 0) * n16;
+  const T2* cdg = reinterpret_cast<const T2*>(A.cd);
+  const F* wdg = reinterpret_cast<const F*>(A.wd);
   const F* wt = reinterpret_cast<const F*>(A.wt);
   const F* b32 = reinterpret_cast<const F*>(A.b32);
 
-  for (int i = lane; i < n; i += 32) sg[i] = A.sigma[(int64_t)c * n + i];
-  __syncwarp();
-  // theta = W sigma + b (FP32), t = tanh(theta)
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    mbar_fence_init();
+  }
+  if (active)
+    for (int i = lane; i < n; i += 32) sg[i] = A.sigma[(int64_t)c * n + i];
+  __syncthreads();
+
+  // theta = W sigma + b: rows of W^T staged through the (not yet used) column
+  // buffers, KC sites at a time, shared by the CTA's chains
   F t[E];
+  {
+    F* stg = reinterpret_cast<F*>(smem);
+    const int KC = (int)((2 * (size_t)mp * (sizeof(T2) + sizeof(F))) / ((size_t)mp * sizeof(F)));
+    F acc[E];
 #pragma unroll
-  for (int q = 0; q < E; ++q) {
-    if (q < e) {
-      int j = lane + 32 * q;
-      F acc = b32[j];
-      for (int i = 0; i < n; ++i) {
-        float si = (float)sg[i];
-        F wv = wt[(int64_t)i * mp + j];
-        if constexpr (CPLX) {
-          acc.x = fmaf(si, wv.x, acc.x);
-          acc.y = fmaf(si, wv.y, acc.y);
-        } else {
-          acc = fmaf(si, wv, acc);
+    for (int q = 0; q < E; ++q) {
+      if constexpr (CPLX) acc[q] = make_float2(0.f, 0.f); else acc[q] = 0.f;
+      if (q < e) acc[q] = b32[lane + 32 * q];
+    }
+    for (int i0 = 0; i0 < n; i0 += KC) {
+      const int kc = min(KC, n - i0);
+      for (int x = tid; x < kc * mp; x += blockDim.x) stg[x] = wt[(int64_t)i0 * mp + x];
+      __syncthreads();
+      if (active) {
+        for (int kk = 0; kk < kc; ++kk) {
+          const float si = (float)sg[i0 + kk];
+#pragma unroll
+          for (int q = 0; q < E; ++q) {
+            if (q < e) {
+              F wv = stg[kk * mp + lane + 32 * q];
+              if constexpr (CPLX) {
+                acc[q].x = fmaf(si, wv.x, acc[q].x);
+                acc[q].y = fmaf(si, wv.y, acc[q].y);
+              } else {
+                acc[q] = fmaf(si, wv, acc[q]);
+              }
+            }
+          }
         }
       }
-      th[j] = acc;
-      if constexpr (CPLX) {
-        cf tt = tanh_c(cf{acc.x, acc.y});
-        t[q] = make_float2(tt.x, tt.y);
-      } else {
-        t[q] = tanh_f(acc);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      if (q < e) {
+        if (active) th[lane + 32 * q] = acc[q];
+        if constexpr (CPLX) {
+          cf tt = tanh_c(cf{acc[q].x, acc[q].y});
+          t[q] = make_float2(tt.x, tt.y);
+        } else {
+          t[q] = tanh_f(acc[q]);
+        }
       }
     }
   }
+  __syncthreads();
 
   const int total = (A.n_discard + A.n_samples) * n;
-  const uint32_t g = (uint32_t)blockIdx.x;
+  const uint32_t cd_bytes = (uint32_t)(mp * sizeof(T2)), wd_bytes = (uint32_t)(mp * sizeof(F));
+  if (tid == 0) {
+    for (int s = 0; s < 2 && s < total; ++s) {
+      const int row = move_row(A, g, s);
+      mbar_arrive_expect_tx(&mbar[s], cd_bytes + wd_bytes);
+      bulk_g2s(colCD + (size_t)s * mp, cdg + (int64_t)row * mp, cd_bytes, &mbar[s]);
+      bulk_g2s(colW + (size_t)s * mp, wdg + (int64_t)row * mp, wd_bytes, &mbar[s]);
+    }
+  }
+
   uint64_t nacc = 0;
+  bool timed_out = false;
   int my_idx = 0;
   double my_u = 0.0;
   for (int step = 0; step < total; ++step) {
     const int q32 = step & 31;
     if (q32 == 0) {  // draws for steps step .. step + 31, one per lane
-      uint64_t gs = A.counter + (uint64_t)(step + lane);
+      const uint64_t gs = A.counter + (uint64_t)(step + lane);
       u4 us = philox_stream(g, gs, kTagSite, A.seed);
       my_idx = uniform_index(us.x, A.move == NK_MOVE_FLIP ? n : A.nb);
       u4 ua = philox_stream((uint32_t)c, gs, kTagAccept, A.seed);
@@ -102,98 +166,159 @@ __global__ void __launch_bounds__(256) metropolis_kernel(MetroArgs A) {
     }
     const int idx = __shfl_sync(0xffffffffu, my_idx, q32);
     const double U = __shfl_sync(0xffffffffu, my_u, q32);
-    int i, k = -1;
-    float si, sk = 0.f;
-    if (A.move == NK_MOVE_FLIP) {
-      i = idx;
-      si = (float)sg[i];
-    } else {
-      i = A.bond_i[idx];
-      k = A.bond_k[idx];
-      si = (float)sg[i];
-      sk = (float)sg[k];
-      if (si == sk) goto next;  // null move: rejected
-    }
-    {
-      // log2 of prod_j |r_j|^2 (complex) or prod_j r_j (real), per lane
-      const T2* ti = tab + (int64_t)i * mp;
-      const T2* tk = tab + (int64_t)(k < 0 ? 0 : k) * mp;
-      ScaledReal P;
-      P.init();
-#pragma unroll
-      for (int q = 0; q < E; ++q) {
-        if (q < e) {
-          const int j = lane + 32 * q;
-          if constexpr (CPLX) {
-            cf C, S;
-            if (k < 0) move_coef(ti[j], si, C, S);
-            else move_coef2(ti[j], tk[j], si, sk, C, S);
-            cf r = C - cf{t[q].x, t[q].y} * S;
-            P.v *= fmaf(r.x, r.x, r.y * r.y);
-          } else {
-            float C, S;
-            if (k < 0) move_coef(ti[j], si, C, S);
-            else move_coef2(ti[j], tk[j], si, sk, C, S);
-            P.v *= fmaf(-t[q], S, C);
-          }
-          if ((q & 3) == 3) P.renorm();
-        }
+    const int b = step & 1;
+    const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((step >> 1) & 1));
+    if (active && ok) {
+      int i, k = -1;
+      if (A.move == NK_MOVE_FLIP) {
+        i = idx;
+      } else {
+        i = A.bond_i[idx];
+        k = A.bond_k[idx];
       }
-      float l2 = P.log2v();
-#pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, off);
-      // visible term: -2 s_i a_i - 2 s_k a_k (real part)
-      double av = CPLX ? A.a[2 * i] : A.a[i];
-      double vis = -2.0 * (double)si * av;
-      if (k >= 0) vis += -2.0 * (double)sk * (CPLX ? A.a[2 * k] : A.a[k]);
-      const float two_re = (CPLX ? 1.f : 2.f) * 0.69314718055994531f * l2 + 2.f * (float)vis;
-      if (accept_test(U, two_re)) {
-        ++nacc;
-        const F* wi = wt + (int64_t)i * mp;
-        const F* wk = wt + (int64_t)(k < 0 ? 0 : k) * mp;
+      const float si = (float)sg[i];
+      const bool null_move = (k >= 0) && (sg[k] == sg[i]);
+      if (!null_move) {
+        const T2* cd = colCD + (size_t)b * mp;
+        ScaledReal P;
+        P.init();
 #pragma unroll
         for (int q = 0; q < E; ++q) {
           if (q < e) {
-            const int j = lane + 32 * q;
-            F v = th[j];
+            const T2 v = cd[lane + 32 * q];
             if constexpr (CPLX) {
-              F d = wi[j];
-              v.x = fmaf(-2.f * si, d.x, v.x);
-              v.y = fmaf(-2.f * si, d.y, v.y);
-              if (k >= 0) {
-                F d2 = wk[j];
-                v.x = fmaf(-2.f * sk, d2.x, v.x);
-                v.y = fmaf(-2.f * sk, d2.y, v.y);
-              }
-              cf tt = tanh_c(cf{v.x, v.y});
-              t[q] = make_float2(tt.x, tt.y);
+              // r = C - s_i t D
+              const float ux = si * t[q].x, uy = si * t[q].y;
+              const float rx = v.x - fmaf(ux, v.z, -uy * v.w);
+              const float ry = v.y - fmaf(ux, v.w, uy * v.z);
+              P.v *= fmaf(rx, rx, ry * ry);
             } else {
-              v = fmaf(-2.f * si, wi[j], v);
-              if (k >= 0) v = fmaf(-2.f * sk, wk[j], v);
-              t[q] = tanh_f(v);
+              P.v *= fmaf(-si * t[q], v.y, v.x);
             }
-            th[j] = v;
+            if ((q & 7) == 7) P.renorm();
           }
         }
-        __syncwarp();
-        if (lane == 0) {
-          sg[i] = (int8_t)(-sg[i]);
-          if (k >= 0) sg[k] = (int8_t)(-sg[k]);
+        float l2 = P.log2v();
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, off);
+        double vis = -2.0 * (double)si * (CPLX ? A.a[2 * i] : A.a[i]);
+        if (k >= 0) vis += 2.0 * (double)si * (CPLX ? A.a[2 * k] : A.a[k]);  // s_k = -s_i
+        const float two_re = (CPLX ? 1.f : 2.f) * 0.69314718055994531f * l2 + 2.f * (float)vis;
+        if (accept_test(U, two_re)) {
+          ++nacc;
+          const F* wdc = colW + (size_t)b * mp;
+#pragma unroll
+          for (int q = 0; q < E; ++q) {
+            if (q < e) {
+              const int j = lane + 32 * q;
+              const T2 v = cd[j];
+              F x = th[j];
+              const F dw = wdc[j];
+              if constexpr (CPLX) {
+                // t' = (t C - s_i D) / (C - s_i t D)
+                const float ux = si * t[q].x, uy = si * t[q].y;
+                const float rx = v.x - fmaf(ux, v.z, -uy * v.w);
+                const float ry = v.y - fmaf(ux, v.w, uy * v.z);
+                const float nx = fmaf(t[q].x, v.x, -t[q].y * v.y) - si * v.z;
+                const float ny = fmaf(t[q].x, v.y, t[q].y * v.x) - si * v.w;
+                const float inv = __frcp_rn(fmaf(rx, rx, ry * ry));
+                t[q] = make_float2(fmaf(nx, rx, ny * ry) * inv, fmaf(ny, rx, -nx * ry) * inv);
+                x.x = fmaf(-2.f * si, dw.x, x.x);
+                x.y = fmaf(-2.f * si, dw.y, x.y);
+              } else {
+                const float r = fmaf(-si * t[q], v.y, v.x);
+                t[q] = fmaf(t[q], v.x, -si * v.y) / r;
+                x = fmaf(-2.f * si, dw, x);
+              }
+              th[j] = x;
+            }
+          }
+          __syncwarp();
+          if (lane == 0) {
+            sg[i] = (int8_t)(-sg[i]);
+            if (k >= 0) sg[k] = (int8_t)(-sg[k]);
+          }
+          __syncwarp();
         }
-        __syncwarp();
       }
     }
-  next:
-    if ((step + 1) % n == 0) {
+    // every warp is done with buffer b: refill it for step + 2
+    timed_out = __syncthreads_or(!ok) != 0;
+    if (timed_out) break;
+    if (tid == 0 && step + 2 < total) {
+      const int row = move_row(A, g, step + 2);
+      mbar_arrive_expect_tx(&mbar[b], cd_bytes + wd_bytes);
+      bulk_g2s(colCD + (size_t)b * mp, cdg + (int64_t)row * mp, cd_bytes, &mbar[b]);
+      bulk_g2s(colW + (size_t)b * mp, wdg + (int64_t)row * mp, wd_bytes, &mbar[b]);
+    }
+    if ((step + 1) % n == 0 && active) {
       const int sweep = (step + 1) / n - 1;
       if (sweep >= A.n_discard) {
         int8_t* out = A.samples + ((int64_t)c * A.n_samples + (sweep - A.n_discard)) * n;
         for (int ii = lane; ii < n; ii += 32) out[ii] = sg[ii];
       }
+      // exact refresh of t from theta
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        if (q < e) {
+          const F x = th[lane + 32 * q];
+          if constexpr (CPLX) {
+            cf tt = tanh_c(cf{x.x, x.y});
+            t[q] = make_float2(tt.x, tt.y);
+          } else {
+            t[q] = tanh_f(x);
+          }
+        }
+      }
     }
   }
-  for (int ii = lane; ii < n; ii += 32) A.sigma[(int64_t)c * n + ii] = sg[ii];
-  if (A.n_acc && lane == 0) A.n_acc[c] = nacc;
+  if (timed_out && tid == 0) {
+    // let the copy into the other buffer land before the CTA exits
+    mbar_wait_bounded(&mbar[0], 0, 1u << 20);
+    mbar_wait_bounded(&mbar[1], 0, 1u << 20);
+  }
+  if (active) {
+    for (int ii = lane; ii < n; ii += 32) A.sigma[(int64_t)c * n + ii] = sg[ii];
+    if (A.n_acc && lane == 0) A.n_acc[c] = timed_out ? ~0ull : nacc;
+  }
+}
+
+// Per-bond tables of an exchange move (s_k = -s_i): cosh c = A_i A_k - B_i B_k,
+// sinh c / s_i = B_i A_k - A_i B_k, increment W_i - W_k.
+template <bool CPLX>
+__global__ void pair_tables_kernel(const void* __restrict__ tabv, const void* __restrict__ wtv,
+                                   const int32_t* __restrict__ bi, const int32_t* __restrict__ bk,
+                                   int nb, int mp, void* cdv, void* wdv) {
+  using F = typename RatioTypes<CPLX>::F;
+  using T2 = typename RatioTypes<CPLX>::T2;
+  const T2* tab = reinterpret_cast<const T2*>(tabv);
+  const F* wt = reinterpret_cast<const F*>(wtv);
+  T2* cd = reinterpret_cast<T2*>(cdv);
+  F* wd = reinterpret_cast<F*>(wdv);
+  const int64_t total = (int64_t)nb * mp;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(x / mp), j = (int)(x % mp);
+    const int i = bi[b], k = bk[b];
+    const T2 ti = tab[(int64_t)i * mp + j], tk = tab[(int64_t)k * mp + j];
+    const F wi = wt[(int64_t)i * mp + j], wk = wt[(int64_t)k * mp + j];
+    if constexpr (CPLX) {
+      cf Ai{ti.x, ti.y}, Bi{ti.z, ti.w}, Ak{tk.x, tk.y}, Bk{tk.z, tk.w};
+      cf C = Ai * Ak - Bi * Bk, D = Bi * Ak - Ai * Bk;
+      cd[x] = make_float4(C.x, C.y, D.x, D.y);
+      wd[x] = make_float2(wi.x - wk.x, wi.y - wk.y);
+    } else {
+      cd[x] = make_float2(fmaf(-ti.y, tk.y, ti.x * tk.x), fmaf(-ti.x, tk.y, ti.y * tk.x));
+      wd[x] = wi - wk;
+    }
+  }
+}
+
+size_t metropolis_scratch_bytes(int n, int m, int cplx, int nb) {
+  (void)n;
+  const int mp = padded_m(m);
+  const size_t f = cplx ? 8 : 4;
+  return (size_t)round_up((int64_t)nb * mp * 2 * f, 256) + (size_t)round_up((int64_t)nb * mp * f, 256);
 }
 
 // ------------------------------------------------------------------ dispatch
@@ -201,11 +326,9 @@ __global__ void __launch_bounds__(256) metropolis_kernel(MetroArgs A) {
 template <bool CPLX, int E>
 static nk_status launch_e(const MetroArgs& A, size_t smem, cudaStream_t st) {
   auto kern = metropolis_kernel<CPLX, E>;
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return fail(NK_ERR_CUDA, "nk_metropolis_sweep: cannot reserve %zu B shared memory", smem);
-  }
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return fail(NK_ERR_CUDA, "nk_metropolis_sweep: cannot reserve %zu B shared memory", smem);
   int blocks = (A.nc + A.G - 1) / A.G;
   kern<<<blocks, 32 * A.G, smem, st>>>(A);
   return check_launch("nk_metropolis_sweep");
@@ -230,7 +353,8 @@ static nk_status launch_c(const MetroArgs& A, size_t smem, cudaStream_t st) {
 
 nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int32_t* bi,
                             const int32_t* bk, int nb, int n_discard, int n_samples,
-                            int8_t* samples, uint64_t* n_acc, cudaStream_t st) {
+                            int8_t* samples, uint64_t* n_acc, void* scratch, size_t scratch_bytes,
+                            cudaStream_t st) {
   WsLayout L(r->n, r->m, r->is_complex);
   MetroArgs A;
   A.n = r->n;
@@ -251,15 +375,37 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
   A.n_acc = n_acc;
   A.a = r->a;
   const char* ws = (const char*)r->ws;
-  A.tab = ws + L.tab;
   A.wt = ws + L.wt;
   A.b32 = ws + L.b32;
-  size_t f = r->is_complex ? 8 : 4;
-  size_t smem = (size_t)A.G * (L.mp * f + round_up(r->n, 16));
+  const size_t f = r->is_complex ? 8 : 4;
+  if (move == NK_MOVE_FLIP) {
+    A.cd = ws + L.tab;
+    A.wd = ws + L.wt;
+  } else {
+    const size_t need = metropolis_scratch_bytes(r->n, r->m, r->is_complex, nb);
+    if (!scratch || scratch_bytes < need)
+      return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: exchange moves need %zu B of scratch", need);
+    char* sc = (char*)scratch;
+    A.cd = sc;
+    A.wd = sc + round_up((int64_t)nb * L.mp * 2 * f, 256);
+    const int64_t tot = (int64_t)nb * L.mp;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
+    if (r->is_complex)
+      pair_tables_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(ws + L.tab, ws + L.wt, bi, bk, nb,
+                                                                 L.mp, (void*)A.cd, (void*)A.wd);
+    else
+      pair_tables_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(ws + L.tab, ws + L.wt, bi, bk,
+                                                                  nb, L.mp, (void*)A.cd,
+                                                                  (void*)A.wd);
+    if (nk_status e = check_launch("nk_metropolis_sweep(pair tables)")) return e;
+  }
+  const size_t smem = 2 * (size_t)L.mp * 3 * f + (size_t)A.G * L.mp * f + 16 +
+                      (size_t)A.G * round_up(r->n, 16);
   if (smem > 227 * 1024)
     return fail(NK_ERR_SHAPE,
-                "nk_metropolis_sweep: group_size * (padded m * %zu + n) = %zu B exceeds 227 KB",
-                f, smem);
+                "nk_metropolis_sweep: group_size %d with padded m %d needs %zu B of shared "
+                "memory (> 227 KB)",
+                A.G, L.mp, smem);
   if ((int64_t)(n_discard + n_samples) * r->n > 0x7fffffff)
     return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: too many proposals in one call");
   return r->is_complex ? launch_c<true>(A, smem, st) : launch_c<false>(A, smem, st);

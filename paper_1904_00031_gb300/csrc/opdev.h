@@ -33,7 +33,8 @@ struct OpDBond {  // diagonal of a bond term: d[2 idx(s_i) + idx(s_k)]
 struct OpMove {
   int32_t i, k;      // flipped spin i; context (or second flipped) spin k
   int32_t two;       // 1: spins i and k both flip
-  int32_t reserved;
+  int32_t align;     // two-spin moves: +1 if mel is nonzero only for s_i = s_k,
+                     // -1 if only for s_i = -s_k (terms are split so that one holds)
   double mel[4][2];  // complex matrix element by 2 idx(s_i) + idx(s_k)
 };
 

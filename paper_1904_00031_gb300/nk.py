@@ -33,6 +33,7 @@ EXPORTS = (
     "nk_rbm_prepare", "nk_rbm_logpsi", "nk_metropolis_sweep", "nk_operator_bytes",
     "nk_operator_upload", "nk_local_energy", "nk_logderiv", "nk_sr_scratch_bytes", "nk_sr_step",
     "nk_backward_scratch_bytes", "nk_rbm_logpsi_backward", "nk_sr_step_noalloc",
+    "nk_metropolis_scratch_bytes",
 )
 NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
@@ -77,7 +78,8 @@ def load_library(path: str = LIB_PATH):
         "nk_rbm_workspace_bytes": (SZ, [I32, I32, I32]),
         "nk_rbm_prepare": (I32, [P, P]),
         "nk_rbm_logpsi": (I32, [P, P, I64, I32, P, P, P]),
-        "nk_metropolis_sweep": (I32, [P, P, I32, P, P, I32, I32, I32, P, P, P]),
+        "nk_metropolis_scratch_bytes": (SZ, [I32, I32, I32, I32, I32]),
+        "nk_metropolis_sweep": (I32, [P, P, I32, P, P, I32, I32, I32, P, P, P, SZ, P]),
         "nk_operator_bytes": (SZ, [P]),
         "nk_operator_upload": (I32, [P, P, SZ, P]),
         "nk_local_energy": (I32, [P, P, P, P, I64, P, P, P]),
@@ -213,18 +215,26 @@ class Chains:
         return int(self._s.seed)
 
 
+def metropolis_scratch(rbm: Rbm, move: int, n_bonds: int, device="cuda"):
+    nb = load_library().nk_metropolis_scratch_bytes(rbm.n, rbm.m, int(rbm.is_complex), move,
+                                                     n_bonds)
+    return torch.empty(max(nb, 1), dtype=torch.uint8, device=device)
+
+
 def nk_metropolis_sweep(rbm: Rbm, chains: Chains, move: int, bond_i=None, bond_k=None,
                         n_discard: int = 1, n_samples_per_chain: int = 1, samples_out=None,
-                        n_accept_out=None, stream=None):
-    _require_gpu(bond_i, bond_k, samples_out, n_accept_out)
+                        n_accept_out=None, scratch=None, stream=None):
+    _require_gpu(bond_i, bond_k, samples_out, n_accept_out, scratch)
     nb = 0 if bond_i is None else int(bond_i.shape[0])
     if samples_out is None:
         samples_out = torch.empty(chains.nc * n_samples_per_chain, rbm.n, dtype=torch.int8,
                                   device=chains.sigma.device)
+    if scratch is None and move == NK_MOVE_EXCHANGE:
+        scratch = metropolis_scratch(rbm, move, nb, chains.sigma.device)
     _check(load_library().nk_metropolis_sweep(
         rbm.struct(), C.byref(chains._s), move, _ptr(bond_i), _ptr(bond_k), nb, n_discard,
-        n_samples_per_chain, _ptr(samples_out), _ptr(n_accept_out), _stream(stream)),
-        "nk_metropolis_sweep")
+        n_samples_per_chain, _ptr(samples_out), _ptr(n_accept_out), _ptr(scratch),
+        0 if scratch is None else scratch.numel(), _stream(stream)), "nk_metropolis_sweep")
     return samples_out
 
 

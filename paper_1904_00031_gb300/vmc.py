@@ -41,12 +41,13 @@ class VmcSr:
         self.scratch = nk.sr_scratch(self.rbm, ns, device)
         self.info_buf = torch.zeros(nk.NK_INFO_LEN, dtype=torch.float64, device=device)
         self.move = nk.NK_MOVE_FLIP if w.move == "flip" else nk.NK_MOVE_EXCHANGE
+        self.metro_scratch = nk.metropolis_scratch(self.rbm, self.move, len(b), device)
 
     # stages ---------------------------------------------------------------
     def sample(self):
         nk.nk_metropolis_sweep(self.rbm, self.chains, self.move, self.bond_i, self.bond_k,
                                self.w.n_discard, self.w.samples_per_chain, self.samples,
-                               self.n_acc)
+                               self.n_acc, self.metro_scratch)
 
     def amplitudes(self):
         nk.nk_rbm_logpsi(self.rbm, self.samples, self.prec, self.logpsi, self.theta)
@@ -73,4 +74,4 @@ class VmcSr:
 
     # kernel launches per step (for reporting)
     def launches_per_step(self) -> int:
-        return 3 + 8 + 7 * self.w.n_cg
+        return 3 + 8 + 7 * self.w.n_cg + (1 if self.move == nk.NK_MOVE_EXCHANGE else 0)

@@ -64,10 +64,12 @@ def test_host_argument_validation(lib):
     r = nk._Rbm(10, 10, 0, 0, 8, 8, 8, 256, 1 << 20)
     ch = nk._Chains(4, 64, 8, 1, 0)
     assert lib.nk_metropolis_sweep(C.byref(r), C.byref(ch), 0, None, None, 0, 1, 1, 8, None,
-                                   None) == 2
+                                   None, 0, None) == 2
     ch = nk._Chains(4, 4, 8, 1, 0)
     assert lib.nk_metropolis_sweep(C.byref(r), C.byref(ch), 1, None, None, 0, 1, 1, 8, None,
-                                   None) == 1
+                                   None, 0, None) == 1
+    assert lib.nk_metropolis_scratch_bytes(400, 1600, 1, 0, 800) == 0
+    assert lib.nk_metropolis_scratch_bytes(400, 1600, 1, 1, 800) == 800 * 1600 * 24
     assert lib.nk_sr_step(C.byref(r), 8, 8, 8, None, 10, 3, 0.01, 0.01, 5, 0.0, 0, 256, 1 << 20,
                           8, None) == 2  # 10 samples do not split into 3 chains
     assert ch.counter == 0
