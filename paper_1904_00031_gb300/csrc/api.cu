@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "opdev.h"
+#include "tc.cuh"
 
 namespace nk {
 
@@ -333,6 +334,8 @@ nk_status nk_sr_step(nk_rbm* rbm, const int8_t* sigma, const void* t, const doub
     return fail(NK_ERR_INVALID_ARG, "nk_sr_step: scratch not 256-byte aligned");
   if (prec != NK_PREC_FP32 && prec != NK_PREC_BF16X2)
     return fail(NK_ERR_INVALID_ARG, "nk_sr_step: unknown precision %d", prec);
+  if (prec == NK_PREC_BF16X2 && !tc_supported_shape(rbm->n, rbm->m))
+    return fail(NK_ERR_UNSUPPORTED, "nk_sr_step: the tensor-core path supports n + 1 <= 448");
   return run_sr_step(rbm, sigma, t, eloc, weights, ns, n_chains, diag_shift, lr, n_cg, cg_rtol,
                      prec, scratch, scratch_bytes, info_out, (cudaStream_t)stream);
 }

@@ -27,11 +27,15 @@ __host__ __device__ inline int padded_m(int m) { return (int)round_up(m, kWarp);
 //   tab  T2  [n][mp]       (cosh 2W_ji, sinh 2W_ji); T2 = float2 (real) or
 //                          float4 (re A, im A, re B, im B) (complex)
 //   xw   F32 [mp][n+1]     W | b row-major ("augmented" W, FP32), rows >= m zero
+//   wbf  BF16 [2][mt*128][na64]  tensor-core operand planes of W | b (hi, lo),
+//                          see tc_rows_per_tile below
 struct WsLayout {
-  int n, m, mp, cplx;
-  size_t a32, b32, wt, tab, xw, total;
+  int n, m, mp, cplx, na64, mt;
+  size_t a32, b32, wt, tab, xw, wbf, total;
   __host__ __device__ WsLayout(int n_, int m_, int cplx_) : n(n_), m(m_), cplx(cplx_) {
     mp = padded_m(m);
+    na64 = (int)round_up(n + 1, 64);
+    mt = (m + (cplx ? 64 : 128) - 1) / (cplx ? 64 : 128);
     size_t f = cplx ? 8 : 4;  // bytes of one F32 element
     size_t off = 0;
     a32 = off;  off += round_up((int64_t)n * f, 256);
@@ -39,9 +43,17 @@ struct WsLayout {
     wt = off;   off += round_up((int64_t)n * mp * f, 256);
     tab = off;  off += round_up((int64_t)n * mp * 2 * f, 256);
     xw = off;   off += round_up((int64_t)mp * (n + 1) * f, 256);
+    wbf = off;  off += round_up((int64_t)2 * mt * 128 * na64 * 2, 256);
     total = off;
   }
 };
+
+// Tensor-core operand planes of a complex (or real) matrix X [rows][n+1]
+// ("B planes"): BF16 [2][mt*128][na64], plane 0 = hi = bf16(X), plane 1 =
+// lo = bf16(X - hi).  Tile jt covers 128 plane rows: for a complex X, rows
+// 0..63 hold Re X[jt*64 + r] and rows 64..127 Im X[jt*64 + r]; for a real X,
+// rows 0..127 hold X[jt*128 + r].  Entries beyond X are zero.
+__host__ __device__ inline int tc_hidden_per_tile(int cplx) { return cplx ? 64 : 128; }
 
 // ------------------------------------------------------------------ complex
 

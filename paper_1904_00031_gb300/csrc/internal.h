@@ -47,7 +47,9 @@ struct SrLayout {
   int ma, na;        // m + 1, n + 1
   int64_t pa;        // ma * na
   int splits;        // split-K factor of the adjoint contraction
-  size_t x, r, p, ap, xf, part, y, v, red, scal, total;
+  int na64, mt1;      // tensor-core path: n + 1 padded to 64; tiles of the m + 1 rows
+  int64_t ns8;        // ns rounded up to 8
+  size_t x, r, p, ap, xf, part, y, v, red, scal, sigt, xbf, total;
   SrLayout(int n_, int m_, int cplx_, int64_t ns_);
 };
 

@@ -1,13 +1,28 @@
-// K1 (tensor-core path): placeholder until the tcgen05 kernel lands.
-#include "common.cuh"
-#include "internal.h"
+// K1 (tensor-core path): theta = [W | b] [sigma; 1] on the tensor cores (W | b
+// split into BF16 hi + lo planes by nk_rbm_prepare, sigma exact in BF16, FP32
+// accumulation in TMEM), ln cosh fused into the epilogue and summed per
+// configuration in FP64, a . sigma added in FP64 (Sec. 2.2.2, RbmSpin).
+#include "tc.cuh"
 
 namespace nk {
 
 nk_status launch_logpsi_bf16(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,
                              void* theta_out, cudaStream_t st) {
-  (void)r; (void)sigma; (void)ns; (void)logpsi; (void)theta_out; (void)st;
-  return fail(NK_ERR_UNSUPPORTED, "nk_rbm_logpsi: NK_PREC_BF16X2 not built yet");
+  WsLayout L(r->n, r->m, r->is_complex);
+  FwdTcArgs A{};
+  A.sigma = sigma;
+  A.ns = ns;
+  A.n = r->n;
+  A.m = r->m;
+  A.cplx = r->is_complex;
+  A.mode = 1;
+  A.mt = L.mt;
+  A.na64 = L.na64;
+  A.rows = r->m;
+  A.a = r->a;
+  A.logpsi = logpsi;
+  A.theta_out = theta_out;
+  return launch_fwd_tc(A, (const char*)r->ws + L.wbf, st);
 }
 
 }  // namespace nk

@@ -8,6 +8,7 @@
 // computed in FP64 and rounded once.
 #include "common.cuh"
 #include "internal.h"
+#include "tc.cuh"
 
 namespace nk {
 
@@ -97,7 +98,8 @@ nk_status launch_prepare(const nk_rbm* r, cudaStream_t st) {
   else
     prepare_kernel<false><<<(unsigned)blocks, threads, 0, st>>>(r->n, r->m, L.mp, r->a, r->b, r->w,
                                                                (char*)r->ws, L);
-  return check_launch("nk_rbm_prepare");
+  if (nk_status e = check_launch("nk_rbm_prepare")) return e;
+  return launch_bplanes_from_rbm(r, st);
 }
 
 }  // namespace nk

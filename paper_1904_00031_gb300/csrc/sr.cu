@@ -8,14 +8,16 @@
 //   (O x)_s         = sum_j T'_sj (X' sigma'_s)_j           (forward contraction)
 //   sum_s conj(O_s) v_s = T'^H diag(v) sigma'               (adjoint contraction)
 //   S x             = adjoint(w o (O x - <O x>)),  <y> = sum_s w_s y_s.
-// The two contractions run at the requested precision (this file: FP32 CUDA
-// cores); CG vectors, inner products and every reduction are FP64, and every
-// reduction has a fixed order (no atomics), so a step is bitwise reproducible.
+// The two contractions run at the requested precision: FP32 CUDA-core kernels
+// here, or the tensor-core kernels of tc.cu (BF16 hi + lo split); CG vectors,
+// inner products and every reduction are FP64, and every reduction has a fixed
+// order (no atomics), so a step is bitwise reproducible.
 #include <math.h>
 
 #include "common.cuh"
 #include "internal.h"
 #include "sgemm.cuh"
+#include "tc.cuh"
 
 namespace nk {
 
@@ -31,6 +33,7 @@ enum {
   SC_FNORM = 4,             // ||F||
   SC_EBAR_RE = 5, SC_EBAR_IM = 6,
   SC_NONFINITE = 7,
+  SC_ERR = 8,               // int: a tensor-core kernel gave up a bounded wait
   SC_LEN = 16
 };
 
@@ -42,6 +45,10 @@ SrLayout::SrLayout(int n_, int m_, int cplx_, int64_t ns_) : n(n_), m(m_), cplx(
   int64_t sp = (2 * 152 + tiles - 1) / tiles;
   sp = std::min<int64_t>(sp, std::max<int64_t>(1, ns / 256));
   splits = (int)std::max<int64_t>(1, std::min<int64_t>(sp, 64));
+  splits = std::max(splits, adj_tc_splits(n, m, cplx, ns));
+  na64 = (int)round_up(n + 1, 64);
+  mt1 = (m + 1 + tc_hidden_per_tile(cplx) - 1) / tc_hidden_per_tile(cplx);
+  ns8 = round_up(std::max<int64_t>(ns, 1), 8);
   size_t d = cplx ? 16 : 8;  // F64 element
   size_t f = cplx ? 8 : 4;   // F32 element
   size_t off = 0;
@@ -60,6 +67,8 @@ SrLayout::SrLayout(int n_, int m_, int cplx_, int64_t ns_) : n(n_), m(m_), cplx(
   v = take((size_t)std::max<int64_t>(ns, 1) * 16);
   red = take(4 * kVecBlocks * sizeof(double));
   scal = take(SC_LEN * sizeof(double));
+  sigt = take((size_t)na64 * ns8 * 2);
+  xbf = take((size_t)2 * mt1 * 128 * na64 * 2);
   total = off;
 }
 
@@ -534,6 +543,7 @@ __global__ void sr_update_kernel(double* a, double* b, double* w, int n, int m,
     int flags = 0;
     if (res > rtol) flags |= 1 << NK_ERR_NOT_CONVERGED;
     if (scal[SC_NONFINITE] != 0.0 || !isfinite(res)) flags |= 1 << NK_ERR_NONFINITE;
+    if (*reinterpret_cast<const int*>(scal + SC_ERR) != 0) flags |= 1 << NK_ERR_TIMEOUT;
     info[NK_INFO_FLAGS] = (double)flags;
   }
 }
@@ -569,18 +579,54 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
                            const double* weights, int64_t ns, int n_chains, double eps,
                            double lr, int n_cg, double rtol, int prec, char* sc,
                            double* info, cudaStream_t st) {
-  (void)prec;
   SrLayout L(r->n, r->m, CPLX, ns);
   double* scal = (double*)(sc + L.scal);
   double* red = (double*)(sc + L.red);
   const int n = r->n, m = r->m;
   const int64_t corner = (int64_t)m * L.na + n;
+  const bool tc = prec == NK_PREC_BF16X2;
+  int* err = reinterpret_cast<int*>(scal + SC_ERR);
+  const int splits = tc ? adj_tc_splits(n, m, CPLX, ns) : L.splits;
+  AdjTcArgs aa{};
+  FwdTcArgs fa{};
+  if (tc) {
+    aa.T = T;
+    aa.ns = ns;
+    aa.n = n;
+    aa.m = m;
+    aa.cplx = CPLX;
+    aa.na64 = L.na64;
+    aa.splits = splits;
+    aa.part = sc + L.part;
+    aa.err = err;
+    fa.sigma = sigma;
+    fa.ns = ns;
+    fa.n = n;
+    fa.m = m;
+    fa.cplx = CPLX;
+    fa.mode = 0;
+    fa.mt = L.mt1;
+    fa.na64 = L.na64;
+    fa.rows = m + 1;
+    fa.T = T;
+    fa.y = sc + L.y;
+    fa.skip = scal + SC_DONE;
+    fa.err = err;
+  }
   stats_kernel<CPLX><<<1, 1024, 0, st>>>(eloc, weights, ns, n_chains, info, scal, sc + L.v);
   if (nk_status e = check_launch("nk_sr_step(stats)")) return e;
   cudaMemsetAsync(scal + SC_DONE, 0, sizeof(double), st);
+  cudaMemsetAsync(scal + SC_ERR, 0, sizeof(double), st);
   // F = adjoint(w o (E - <E>)) -> r
-  launch_adjoint_fp32<CPLX>(sigma, T, sc + L.v, ns, n, m, L.splits, sc + L.part, nullptr, st);
-  reduce_parts_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.part, L.splits, L.pa,
+  if (tc) {
+    if (nk_status e = launch_sigma_t(sigma, ns, n, L.na64, sc + L.sigt, st)) return e;
+    aa.v = sc + L.v;
+    aa.skip = nullptr;
+    if (nk_status e = launch_adj_tc(aa, sc + L.sigt, st)) return e;
+  } else {
+    launch_adjoint_fp32<CPLX>(sigma, T, sc + L.v, ns, n, m, splits, sc + L.part, nullptr, st);
+  }
+  reduce_parts_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.part, splits, L.pa,
                                                                 corner, sc + L.r, nullptr, 0.0,
                                                                 nullptr, nullptr);
   cg_init_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, sc + L.r, sc + L.p, L.pa,
@@ -588,14 +634,27 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
   cg_init_scalars_kernel<<<1, 32, 0, st>>>(red, scal, rtol);
   if (nk_status e = check_launch("nk_sr_step(force)")) return e;
   const int64_t sg_blocks = (ns + kSgBS - 1) / kSgBS;
+  aa.v = sc + L.v;
+  aa.skip = scal + SC_DONE;
   for (int it = 0; it < n_cg; ++it) {
-    to_f32_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.p, sc + L.xf, L.pa, scal);
-    forward_fp32_kernel<CPLX><<<(unsigned)sg_blocks, kSgThreads, 0, st>>>(
-        sigma, ns, n, m, sc + L.xf, T, sc + L.y, scal);
+    if (tc) {
+      if (nk_status e = launch_bplanes_from_f64(sc + L.p, m + 1, n + 1, L.na, CPLX, L.mt1, L.na64,
+                                                sc + L.xbf, scal + SC_DONE, st))
+        return e;
+      if (nk_status e = launch_fwd_tc(fa, sc + L.xbf, st)) return e;
+    } else {
+      to_f32_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.p, sc + L.xf, L.pa, scal);
+      forward_fp32_kernel<CPLX><<<(unsigned)sg_blocks, kSgThreads, 0, st>>>(
+          sigma, ns, n, m, sc + L.xf, T, sc + L.y, scal);
+    }
     center_kernel<CPLX><<<1, 1024, 0, st>>>(sc + L.y, sc + L.v, weights, ns, scal);
-    launch_adjoint_fp32<CPLX>(sigma, T, sc + L.v, ns, n, m, L.splits, sc + L.part, scal, st);
+    if (tc) {
+      if (nk_status e = launch_adj_tc(aa, sc + L.sigt, st)) return e;
+    } else {
+      launch_adjoint_fp32<CPLX>(sigma, T, sc + L.v, ns, n, m, splits, sc + L.part, scal, st);
+    }
     reduce_parts_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(
-        sc + L.part, L.splits, L.pa, corner, sc + L.ap, sc + L.p, eps, red, scal);
+        sc + L.part, splits, L.pa, corner, sc + L.ap, sc + L.p, eps, red, scal);
     cg_step_x_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, sc + L.r, sc + L.p,
                                                                sc + L.ap, L.pa, red, scal, it);
     cg_step_p_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.r, sc + L.p, L.pa, red,
@@ -660,21 +719,43 @@ nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const d
   if ((e = launch_logderiv(r, sigma, theta, ns, NK_LAYOUT_FACTORED, T, st))) return e;
   int64_t blocks = std::min<int64_t>((ns + 255) / 256, 1024);
   if (blocks < 1) blocks = 1;
+  const bool tc = prec == NK_PREC_BF16X2;
+  const int splits = tc ? adj_tc_splits(r->n, r->m, r->is_complex, ns) : L.splits;
+  if (tc) {
+    if ((e = launch_sigma_t(sigma, ns, r->n, L.na64, sc + L.sigt, st))) return e;
+  }
+  AdjTcArgs aa{};
+  aa.T = T;
+  aa.v = sc + L.v;
+  aa.ns = ns;
+  aa.n = r->n;
+  aa.m = r->m;
+  aa.cplx = r->is_complex;
+  aa.na64 = L.na64;
+  aa.splits = splits;
+  aa.part = sc + L.part;
+  const int64_t corner = (int64_t)r->m * L.na + r->n;
   if (r->is_complex) {
     copy_g_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(g, sc + L.v, ns);
-    launch_adjoint_fp32<true>(sigma, T, sc + L.v, ns, r->n, r->m, L.splits, sc + L.part, nullptr,
-                              st);
+    if (tc) {
+      if ((e = launch_adj_tc(aa, sc + L.sigt, st))) return e;
+    } else {
+      launch_adjoint_fp32<true>(sigma, T, sc + L.v, ns, r->n, r->m, splits, sc + L.part, nullptr,
+                                st);
+    }
     reduce_parts_kernel<true><<<kVecBlocks, kVecThreads, 0, st>>>(
-        sc + L.part, L.splits, L.pa, (int64_t)r->m * L.na + r->n, sc + L.x, nullptr, 0.0, nullptr,
-        nullptr);
+        sc + L.part, splits, L.pa, corner, sc + L.x, nullptr, 0.0, nullptr, nullptr);
     scatter_grad_kernel<true><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, r->n, r->m, grad);
   } else {
     copy_g_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(g, sc + L.v, ns);
-    launch_adjoint_fp32<false>(sigma, T, sc + L.v, ns, r->n, r->m, L.splits, sc + L.part, nullptr,
-                               st);
+    if (tc) {
+      if ((e = launch_adj_tc(aa, sc + L.sigt, st))) return e;
+    } else {
+      launch_adjoint_fp32<false>(sigma, T, sc + L.v, ns, r->n, r->m, splits, sc + L.part, nullptr,
+                                 st);
+    }
     reduce_parts_kernel<false><<<kVecBlocks, kVecThreads, 0, st>>>(
-        sc + L.part, L.splits, L.pa, (int64_t)r->m * L.na + r->n, sc + L.x, nullptr, 0.0, nullptr,
-        nullptr);
+        sc + L.part, splits, L.pa, corner, sc + L.x, nullptr, 0.0, nullptr, nullptr);
     scatter_grad_kernel<false><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, r->n, r->m, grad);
   }
   return check_launch("nk_rbm_logpsi_backward");

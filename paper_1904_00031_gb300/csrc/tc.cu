@@ -1,0 +1,654 @@
+// Tensor-core contractions of the RBM path (tcgen05, BF16 hi + lo, FP32 in TMEM).
+//
+// sigma' = [sigma | 1] is exact in BF16.  The other operand X (W | b, or an SR
+// direction) is split as X = hi + lo with hi = bf16(X), lo = bf16(X - hi), and
+// every product is accumulated from both halves in FP32 (relative error of the
+// split ~2^-17 per element).
+//
+// Forward (theta and the O x half of the SR matvec): one CTA owns 128
+// configurations; their sigma' rows stay resident in shared memory as K-major
+// 128-byte-swizzled tiles written by the CTA itself, the B planes of X stream
+// in by TMA through a 3-stage ring, one thread issues the MMAs (M = 128
+// configurations, N = 128 plane rows, K = n + 1 padded to 64) into one of two
+// TMEM accumulators, and four epilogue warps fold each finished 128 x 128 tile
+// (tcgen05.ld) into per-configuration FP64 sums while the next tile is built.
+//
+// Adjoint (the O^H v half): one CTA owns 64 complex (128 real) parameter rows
+// j and a range of samples (split-K).  Four producer warps compute
+// Z = conj(T'_sj) v_s for 64 samples at a time, split it into BF16 hi/lo and
+// write it, swizzled, as the A operand; sigma'^T tiles (a BF16 plane built once
+// per SR step) arrive by TMA; MMAs accumulate G[j][0..n] in TMEM (two halves of
+// N <= 224); the epilogue writes FP32 partials that a fixed-order FP64
+// reduction sums over the splits.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "tc.cuh"
+#include "umma.cuh"
+
+namespace nk {
+
+// ------------------------------------------------------------------ tensor maps
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
+                 int64_t row_stride_elems, int box_rows) {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    else
+      cudaGetLastError();
+  });
+  if (!g_encode) {
+    fail(NK_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
+    return false;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)row_stride_elems * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return false;
+  }
+  return true;
+}
+
+bool tc_supported_shape(int n, int m) { return n + 1 <= 448 && m >= 1; }
+
+// ------------------------------------------------------------------ BF16 helpers
+
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float bf16_val(uint32_t b) {
+  return __bfloat162float(__ushort_as_bfloat16((unsigned short)b));
+}
+// hi = bf16(x), lo = bf16(x - hi)
+__device__ __forceinline__ void split_bf16(float x, uint32_t& hi, uint32_t& lo) {
+  hi = bf16_bits(x);
+  lo = bf16_bits(x - bf16_val(hi));
+}
+__device__ __forceinline__ void split_bf16(double x, uint32_t& hi, uint32_t& lo) {
+  hi = bf16_bits((float)x);
+  lo = bf16_bits((float)(x - (double)bf16_val(hi)));
+}
+
+// ------------------------------------------------------------------ B planes
+
+template <bool CPLX, bool FROM_RBM>
+__global__ void bplanes_kernel(const double* __restrict__ src, int src_rows, int ncols, int ld,
+                               const double* __restrict__ w, const double* __restrict__ b, int n,
+                               int mt, int na64, uint16_t* __restrict__ planes,
+                               const double* skip) {
+  if (skip && *skip != 0.0) return;
+  const int HJ = CPLX ? 64 : 128;
+  const int64_t plane = (int64_t)mt * 128 * na64;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int row = (int)(e / na64), i = (int)(e % na64);
+    const int jt = row >> 7, rr = row & 127;
+    const int j = CPLX ? jt * HJ + (rr & 63) : jt * HJ + rr;
+    const int comp = CPLX ? (rr >> 6) : 0;
+    double x = 0.0;
+    if (j < src_rows && i < ncols) {
+      if (FROM_RBM) {
+        const int k = CPLX ? 2 : 1;
+        x = i < n ? w[((int64_t)j * n + i) * k + comp] : b[(int64_t)j * k + comp];
+      } else {
+        x = CPLX ? src[((int64_t)j * ld + i) * 2 + comp] : src[(int64_t)j * ld + i];
+      }
+    }
+    uint32_t hi, lo;
+    split_bf16(x, hi, lo);
+    planes[e] = (uint16_t)hi;
+    planes[plane + e] = (uint16_t)lo;
+  }
+}
+
+nk_status launch_bplanes_from_f64(const void* src, int src_rows, int ncols, int ld, int cplx,
+                                  int mt, int na64, void* planes, const double* skip,
+                                  cudaStream_t st) {
+  const int64_t tot = (int64_t)mt * 128 * na64;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 8));
+  if (cplx)
+    bplanes_kernel<true, false><<<(unsigned)blocks, 256, 0, st>>>(
+        (const double*)src, src_rows, ncols, ld, nullptr, nullptr, 0, mt, na64,
+        (uint16_t*)planes, skip);
+  else
+    bplanes_kernel<false, false><<<(unsigned)blocks, 256, 0, st>>>(
+        (const double*)src, src_rows, ncols, ld, nullptr, nullptr, 0, mt, na64,
+        (uint16_t*)planes, skip);
+  return check_launch("bplanes");
+}
+
+nk_status launch_bplanes_from_rbm(const nk_rbm* r, cudaStream_t st) {
+  WsLayout L(r->n, r->m, r->is_complex);
+  const int64_t tot = (int64_t)L.mt * 128 * L.na64;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 8));
+  uint16_t* planes = (uint16_t*)((char*)r->ws + L.wbf);
+  if (r->is_complex)
+    bplanes_kernel<true, true><<<(unsigned)blocks, 256, 0, st>>>(
+        nullptr, r->m, r->n + 1, 0, r->w, r->b, r->n, L.mt, L.na64, planes, nullptr);
+  else
+    bplanes_kernel<false, true><<<(unsigned)blocks, 256, 0, st>>>(
+        nullptr, r->m, r->n + 1, 0, r->w, r->b, r->n, L.mt, L.na64, planes, nullptr);
+  return check_launch("nk_rbm_prepare(bf16 planes)");
+}
+
+// ------------------------------------------------------------------ sigma'^T
+
+__global__ void sigma_t_kernel(const int8_t* __restrict__ sigma, int64_t ns, int n, int na64,
+                               int64_t ns8, uint16_t* __restrict__ out) {
+  const int i = blockIdx.y;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns8;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    uint16_t v = 0;
+    if (s < ns) {
+      if (i < n) v = sigma[s * n + i] > 0 ? 0x3F80 : 0xBF80;
+      else if (i == n) v = 0x3F80;
+    }
+    out[(int64_t)i * ns8 + s] = v;
+  }
+}
+
+nk_status launch_sigma_t(const int8_t* sigma, int64_t ns, int n, int na64, void* out,
+                         cudaStream_t st) {
+  const int64_t ns8 = round_up(ns, 8);
+  dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((ns8 + 255) / 256, 64)), na64);
+  sigma_t_kernel<<<grid, 256, 0, st>>>(sigma, ns, n, na64, ns8, (uint16_t*)out);
+  return check_launch("sigma_t");
+}
+
+// ------------------------------------------------------------------ forward
+
+constexpr int kFwdStages = 3;
+constexpr int kFwdThreads = 192;
+constexpr uint32_t kStageB = 32768;  // hi + lo tiles of 128 rows x 128 B
+
+__device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
+  return (unsigned char*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+}
+
+__device__ __forceinline__ uint32_t sig_bits(const int8_t* sigma, int64_t s, int64_t ns, int n,
+                                             int i) {
+  if (s >= ns) return 0;
+  if (i < n) return sigma[s * n + i] > 0 ? 0x3F80u : 0xBF80u;
+  return i == n ? 0x3F80u : 0u;
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kFwdThreads, 1)
+    fwd_tc_kernel(const __grid_constant__ CUtensorMap tb, FwdTcArgs A) {
+  if (A.skip && *A.skip != 0.0) return;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = align1024(smraw);
+  const int KC = A.na64 / 64;
+  unsigned char* sA = sm;
+  unsigned char* sB = sm + (size_t)KC * 16384;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kFwdStages * kStageB);
+  uint64_t* empty = full + kFwdStages;
+  uint64_t* tfull = empty + kFwdStages;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int64_t s0 = (int64_t)blockIdx.x * 128;
+
+  if (tid == 0) {
+    for (int st = 0; st < kFwdStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&tfull[k], 1);
+      mbar_init(&tempty[k], 4);
+    }
+    mbar_fence_init();
+  }
+  if (w == 1) tmem_alloc(slot, 256);
+  // resident sigma' tile: 128 rows x KC * 64 columns, 16-B chunks of 8 BF16
+  for (int x = tid; x < 128 * KC * 8; x += blockDim.x) {
+    const int r = x / (KC * 8), rem = x % (KC * 8), kc = rem >> 3, c = rem & 7;
+    const int64_t s = s0 + r;
+    const int i0 = kc * 64 + c * 8;
+    uint32_t pk[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      pk[q] = sig_bits(A.sigma, s, A.ns, A.n, i0 + 2 * q) |
+              (sig_bits(A.sigma, s, A.ns, A.n, i0 + 2 * q + 1) << 16);
+    *reinterpret_cast<uint4*>(sA + (size_t)kc * 16384 + sw128_offset(r, c * 8)) =
+        make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = *slot;
+  const int total_it = A.mt * KC;
+  bool bad = false;
+
+  if (w == 0) {
+    if (lane == 0) {
+      for (int it = 0; it < total_it; ++it) {
+        const int st = it % kFwdStages, u = it / kFwdStages, jt = it / KC, kc = it % KC;
+        if (u > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((u - 1) & 1))) {
+          bad = true;
+          break;
+        }
+        mbar_arrive_expect_tx(&full[st], kStageB);
+        tma_load_2d(sB + (size_t)st * kStageB, &tb, kc * 64, jt * 128, &full[st]);
+        tma_load_2d(sB + (size_t)st * kStageB + 16384, &tb, kc * 64, (A.mt + jt) * 128,
+                    &full[st]);
+      }
+    }
+  } else if (w == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, 128);
+      int it = 0;
+      for (int jt = 0; jt < A.mt && !bad; ++jt) {
+        const int acc = jt & 1, ua = jt >> 1;
+        if (ua > 0 && !mbar_wait_bounded(&tempty[acc], (uint32_t)((ua - 1) & 1))) {
+          bad = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = taddr + (uint32_t)(acc * 128);
+        for (int kc = 0; kc < KC; ++kc, ++it) {
+          const int st = it % kFwdStages, u = it / kFwdStages;
+          if (!mbar_wait_bounded(&full[st], (uint32_t)(u & 1))) {
+            bad = true;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = sdesc_sw128(smem_addr(sA + (size_t)kc * 16384 + kk * 32));
+            const uint64_t bh = sdesc_sw128(smem_addr(sB + (size_t)st * kStageB + kk * 32));
+            const uint64_t bl =
+                sdesc_sw128(smem_addr(sB + (size_t)st * kStageB + 16384 + kk * 32));
+            umma_bf16(d, ad, bh, idesc, (kc | kk) != 0);
+            umma_bf16(d, ad, bl, idesc, 1u);
+          }
+          umma_commit(&empty[st]);
+        }
+        if (!bad) umma_commit(&tfull[acc]);
+      }
+    }
+  } else {
+    // epilogue warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. + 31
+    const int q = w & 3;
+    const int row = 32 * q + lane;
+    const int64_t s = s0 + row;
+    const bool live = s < A.ns;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const int HJ = CPLX ? 64 : 128;
+    double sr = 0.0, si = 0.0;
+    for (int jt = 0; jt < A.mt; ++jt) {
+      const int acc = jt & 1;
+      if (!mbar_wait_bounded(&tfull[acc], (uint32_t)((jt >> 1) & 1))) {
+        bad = true;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t tb0 = taddr + lane_base + (uint32_t)(acc * 128);
+      const int j0 = jt * HJ;
+      float pr = 0.f, pi = 0.f;
+      if constexpr (CPLX) {
+        const float2* T = reinterpret_cast<const float2*>(A.T);
+        float2* th = reinterpret_cast<float2*>(A.theta_out);
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+          float ur[16], ui[16];
+          tmem_ld16(tb0 + c * 16, ur);
+          tmem_ld16(tb0 + 64 + c * 16, ui);
+          tmem_ld_wait();
+          if (live) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int j = j0 + c * 16 + e;
+              if (A.mode == 0) {
+                if (j <= A.m) {
+                  const float2 t = j < A.m ? T[s * A.m + j] : make_float2(1.f, 0.f);
+                  pr += t.x * ur[e] - t.y * ui[e];
+                  pi += t.x * ui[e] + t.y * ur[e];
+                }
+              } else if (j < A.m) {
+                cf l = lncosh_c(cf{ur[e], ui[e]});
+                pr += l.x;
+                pi += l.y;
+                if (th) th[s * A.m + j] = make_float2(ur[e], ui[e]);
+              }
+            }
+          }
+        }
+      } else {
+        const float* T = reinterpret_cast<const float*>(A.T);
+        float* th = reinterpret_cast<float*>(A.theta_out);
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+          float u[16];
+          tmem_ld16(tb0 + c * 16, u);
+          tmem_ld_wait();
+          if (live) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int j = j0 + c * 16 + e;
+              if (A.mode == 0) {
+                if (j <= A.m) pr += (j < A.m ? T[s * A.m + j] : 1.f) * u[e];
+              } else if (j < A.m) {
+                pr += lncosh_f(u[e]);
+                if (th) th[s * A.m + j] = u[e];
+              }
+            }
+          }
+        }
+      }
+      sr += (double)pr;
+      si += (double)pi;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+    }
+    if (live) {
+      if (bad) sr = si = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a timeout
+      if (A.mode == 0) {
+        if (CPLX) reinterpret_cast<double2*>(A.y)[s] = make_double2(sr, si);
+        else reinterpret_cast<double*>(A.y)[s] = sr;
+      } else {
+        double vr = 0.0, vi = 0.0;
+        const int8_t* sg = A.sigma + s * A.n;
+        for (int i = 0; i < A.n; ++i) {
+          const double sv = (double)sg[i];
+          if (CPLX) {
+            vr += A.a[2 * i] * sv;
+            vi += A.a[2 * i + 1] * sv;
+          } else {
+            vr += A.a[i] * sv;
+          }
+        }
+        A.logpsi[2 * s] = sr + vr;
+        A.logpsi[2 * s + 1] = si + vi;
+      }
+    }
+  }
+  if (bad && A.err) atomicOr(A.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (w == 1) {
+    tc_fence_after();
+    tmem_dealloc(taddr, 256);
+  }
+}
+
+static size_t fwd_smem_bytes(int na64) {
+  return 1024 + (size_t)(na64 / 64) * 16384 + kFwdStages * kStageB + 128;
+}
+
+nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st) {
+  if (!tc_supported_shape(A.n, A.m))
+    return fail(NK_ERR_UNSUPPORTED, "tensor-core path supports n + 1 <= 448 (n = %d)", A.n);
+  CUtensorMap map;
+  if (!tc_make_map(&map, planes, 2LL * A.mt * 128, A.na64, A.na64, 128)) return NK_ERR_CUDA;
+  const size_t smem = fwd_smem_bytes(A.na64);
+  const int64_t blocks = (A.ns + 127) / 128;
+  if (A.cplx) {
+    if (cudaFuncSetAttribute(fwd_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return fail(NK_ERR_CUDA, "fwd_tc: shared memory attribute");
+    fwd_tc_kernel<true><<<(unsigned)blocks, kFwdThreads, smem, st>>>(map, A);
+  } else {
+    if (cudaFuncSetAttribute(fwd_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return fail(NK_ERR_CUDA, "fwd_tc: shared memory attribute");
+    fwd_tc_kernel<false><<<(unsigned)blocks, kFwdThreads, smem, st>>>(map, A);
+  }
+  return check_launch("fwd_tc");
+}
+
+// ------------------------------------------------------------------ adjoint
+
+constexpr int kAdjThreads = 192;
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kAdjThreads, 1)
+    adj_tc_kernel(const __grid_constant__ CUtensorMap ts_map, AdjTcArgs A, int64_t chunk) {
+  if (A.skip && *A.skip != 0.0) return;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = align1024(smraw);
+  const int NB = A.na64, NH = NB / 2;
+  const uint32_t stage_bytes = 32768u + (uint32_t)NB * 128u;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + 2 * (size_t)stage_bytes);
+  uint64_t* empty = full + 2;
+  uint64_t* done = empty + 2;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(done + 1);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int HJ = CPLX ? 64 : 128;
+  const int j0 = blockIdx.x * HJ;
+  const int z = blockIdx.y;
+  const int64_t sb = (int64_t)z * chunk;
+  const int64_t se = std::min<int64_t>(A.ns, sb + chunk);
+  const int nit = se > sb ? (int)((se - sb + 63) / 64) : 0;
+  const uint32_t ncols = NB <= 32 ? 32 : (NB <= 64 ? 64 : (NB <= 128 ? 128 : (NB <= 256 ? 256 : 512)));
+
+  if (tid == 0) {
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&full[k], 1 + 4);
+      mbar_init(&empty[k], 1);
+    }
+    mbar_init(done, 1);
+    mbar_fence_init();
+  }
+  if (w == 1) tmem_alloc(slot, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = *slot;
+  bool bad = false;
+
+  if (w == 0) {
+    if (lane == 0) {
+      for (int it = 0; it < nit; ++it) {
+        const int st = it & 1, u = it >> 1;
+        if (u > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((u - 1) & 1))) {
+          bad = true;
+          break;
+        }
+        unsigned char* B = sm + (size_t)st * stage_bytes + 32768;
+        mbar_arrive_expect_tx(&full[st], (uint32_t)NB * 128u);
+        tma_load_2d(B, &ts_map, (int)(sb + (int64_t)it * 64), 0, &full[st]);
+        tma_load_2d(B + (size_t)NH * 128, &ts_map, (int)(sb + (int64_t)it * 64), NH, &full[st]);
+      }
+    }
+  } else if (w == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, NH);
+      for (int it = 0; it < nit; ++it) {
+        const int st = it & 1;
+        if (!mbar_wait_bounded(&full[st], (uint32_t)((it >> 1) & 1))) {
+          bad = true;
+          break;
+        }
+        tc_fence_after();
+        unsigned char* S = sm + (size_t)st * stage_bytes;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t ah = sdesc_sw128(smem_addr(S + kk * 32));
+          const uint64_t al = sdesc_sw128(smem_addr(S + 16384 + kk * 32));
+          const uint64_t b0 = sdesc_sw128(smem_addr(S + 32768 + kk * 32));
+          const uint64_t b1 = sdesc_sw128(smem_addr(S + 32768 + (size_t)NH * 128 + kk * 32));
+          const uint32_t first = (it | kk) == 0;
+          umma_bf16(taddr, ah, b0, idesc, !first);
+          umma_bf16(taddr, al, b0, idesc, 1u);
+          umma_bf16(taddr + (uint32_t)NH, ah, b1, idesc, !first);
+          umma_bf16(taddr + (uint32_t)NH, al, b1, idesc, 1u);
+        }
+        umma_commit(&empty[st]);
+      }
+      umma_commit(done);
+    }
+  } else {
+    // producers: Z = conj(T'_sj) v_s as BF16 hi/lo, K-major swizzled A tiles
+    const int pt = tid - 64;
+    for (int it = 0; it < nit && !bad; ++it) {
+      const int st = it & 1, u = it >> 1;
+      if (u > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((u - 1) & 1))) {
+        bad = true;
+        break;
+      }
+      unsigned char* Ahi = sm + (size_t)st * stage_bytes;
+      unsigned char* Alo = Ahi + 16384;
+      const int64_t k0 = sb + (int64_t)it * 64;
+      if constexpr (CPLX) {
+        const float2* T = reinterpret_cast<const float2*>(A.T);
+        const double2* v = reinterpret_cast<const double2*>(A.v);
+        const int jl = pt & 63, half = pt >> 6, j = j0 + jl;
+#pragma unroll 1
+        for (int cc = 0; cc < 4; ++cc) {
+          const int kl = half * 32 + cc * 8;
+          uint32_t hr[4], lr[4], hi_[4], li[4];
+#pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) {
+            float zr[2], zi[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int64_t s = k0 + kl + 2 * e2 + h;
+              zr[h] = zi[h] = 0.f;
+              if (s < se && j <= A.m) {
+                const float2 t = j < A.m ? T[s * A.m + j] : make_float2(1.f, 0.f);
+                const double2 vd = v[s];
+                const float vr = (float)vd.x, vi = (float)vd.y;
+                zr[h] = t.x * vr + t.y * vi;
+                zi[h] = t.x * vi - t.y * vr;
+              }
+            }
+            uint32_t a0, b0, a1, b1;
+            split_bf16(zr[0], a0, b0);
+            split_bf16(zr[1], a1, b1);
+            hr[e2] = a0 | (a1 << 16);
+            lr[e2] = b0 | (b1 << 16);
+            split_bf16(zi[0], a0, b0);
+            split_bf16(zi[1], a1, b1);
+            hi_[e2] = a0 | (a1 << 16);
+            li[e2] = b0 | (b1 << 16);
+          }
+          *reinterpret_cast<uint4*>(Ahi + sw128_offset(jl, kl)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+          *reinterpret_cast<uint4*>(Alo + sw128_offset(jl, kl)) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+          *reinterpret_cast<uint4*>(Ahi + sw128_offset(64 + jl, kl)) =
+              make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
+          *reinterpret_cast<uint4*>(Alo + sw128_offset(64 + jl, kl)) =
+              make_uint4(li[0], li[1], li[2], li[3]);
+        }
+      } else {
+        const float* T = reinterpret_cast<const float*>(A.T);
+        const double* v = reinterpret_cast<const double*>(A.v);
+        const int jl = pt, j = j0 + jl;
+#pragma unroll 1
+        for (int cc = 0; cc < 8; ++cc) {
+          const int kl = cc * 8;
+          uint32_t hr[4], lr[4];
+#pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) {
+            float zz[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int64_t s = k0 + kl + 2 * e2 + h;
+              zz[h] = 0.f;
+              if (s < se && j <= A.m) zz[h] = (j < A.m ? T[s * A.m + j] : 1.f) * (float)v[s];
+            }
+            uint32_t a0, b0, a1, b1;
+            split_bf16(zz[0], a0, b0);
+            split_bf16(zz[1], a1, b1);
+            hr[e2] = a0 | (a1 << 16);
+            lr[e2] = b0 | (b1 << 16);
+          }
+          *reinterpret_cast<uint4*>(Ahi + sw128_offset(jl, kl)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+          *reinterpret_cast<uint4*>(Alo + sw128_offset(jl, kl)) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+        }
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[st]);
+    }
+    // epilogue: partial sums of this split
+    if (!bad && !mbar_wait_bounded(done, 0u)) bad = true;
+    tc_fence_after();
+    const int q = w & 3, row = 32 * q + lane;
+    const int j = CPLX ? j0 + (row & 63) : j0 + row;
+    const int comp = CPLX ? (row >> 6) : 0;
+    const int ma = A.m + 1, na = A.n + 1;
+    float* part = reinterpret_cast<float*>(A.part);
+    for (int col = 0; col < NB; col += 16) {
+      float v[16];
+      tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
+      tmem_ld_wait();
+      if (j < ma) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int i = col + e;
+          if (i < na) {
+            const float x = (nit > 0 && !bad) ? v[e] : (bad ? __int_as_float(0x7fc00000) : 0.f);
+            const int64_t idx = ((int64_t)z * ma + j) * na + i;
+            if (CPLX) part[2 * idx + comp] = x;
+            else part[idx] = x;
+          }
+        }
+      }
+    }
+  }
+  if (bad && A.err) atomicOr(A.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (w == 1) {
+    tc_fence_after();
+    tmem_dealloc(taddr, ncols);
+  }
+}
+
+int adj_tc_splits(int n, int m, int cplx, int64_t ns) {
+  (void)n;
+  const int HJ = cplx ? 64 : 128;
+  const int tiles = (m + 1 + HJ - 1) / HJ;
+  int64_t sp = (2 * 152 + tiles - 1) / tiles;
+  sp = std::min<int64_t>(sp, std::max<int64_t>(1, (ns + 63) / 64));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 64));
+}
+
+nk_status launch_adj_tc(const AdjTcArgs& A, const void* sigma_t, cudaStream_t st) {
+  if (!tc_supported_shape(A.n, A.m))
+    return fail(NK_ERR_UNSUPPORTED, "tensor-core path supports n + 1 <= 448 (n = %d)", A.n);
+  const int64_t ns8 = round_up(A.ns, 8);
+  CUtensorMap map;
+  if (!tc_make_map(&map, sigma_t, A.na64, ns8, ns8, A.na64 / 2)) return NK_ERR_CUDA;
+  const int HJ = A.cplx ? 64 : 128;
+  const int tiles = (A.m + 1 + HJ - 1) / HJ;
+  int64_t chunk = (A.ns + A.splits - 1) / A.splits;
+  chunk = round_up(std::max<int64_t>(chunk, 1), 64);
+  const size_t smem = 1024 + 2 * (32768 + (size_t)A.na64 * 128) + 64;
+  dim3 grid(tiles, A.splits);
+  if (A.cplx) {
+    if (cudaFuncSetAttribute(adj_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return fail(NK_ERR_CUDA, "adj_tc: shared memory attribute");
+    adj_tc_kernel<true><<<grid, kAdjThreads, smem, st>>>(map, A, chunk);
+  } else {
+    if (cudaFuncSetAttribute(adj_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return fail(NK_ERR_CUDA, "adj_tc: shared memory attribute");
+    adj_tc_kernel<false><<<grid, kAdjThreads, smem, st>>>(map, A, chunk);
+  }
+  return check_launch("adj_tc");
+}
+
+}  // namespace nk

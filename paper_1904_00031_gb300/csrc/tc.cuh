@@ -1,0 +1,66 @@
+// Tensor-core (tcgen05, BF16 hi + lo split, FP32 accumulation in TMEM)
+// contractions of the RBM path.  Declarations shared by logpsi, SR and backward.
+#pragma once
+
+#include <cuda.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace nk {
+
+// Encode a 2-D BF16 tensor map (row-major [rows][cols], 128-byte swizzle,
+// box = 64 columns x box_rows rows).  Returns false (and sets the error
+// message) if the driver entry point is unavailable or rejects the map.
+bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
+                 int64_t row_stride_elems, int box_rows);
+
+// Build B planes (see WsLayout) from an FP64 augmented matrix src [src_rows][ld]
+// (double or interleaved complex), only columns < ncols used.
+nk_status launch_bplanes_from_f64(const void* src, int src_rows, int ncols, int ld, int cplx,
+                                  int mt, int na64, void* planes, const double* skip_flag,
+                                  cudaStream_t st);
+// Build the B planes of W | b from the master parameters.
+nk_status launch_bplanes_from_rbm(const nk_rbm* r, cudaStream_t st);
+
+// sigma' transposed, BF16 [na64][ns8]: sigma'[s][i] = sigma (i < n), 1 (i = n),
+// 0 beyond; ns8 = ns rounded up to 8.
+nk_status launch_sigma_t(const int8_t* sigma, int64_t ns, int n, int na64, void* out,
+                         cudaStream_t st);
+
+// Forward contraction with a fused epilogue, for 128 configurations per CTA:
+//   U[s][j] = sum_i sigma'[s][i] X[j][i]  (X given as B planes)
+// mode 0 (SR):     y_s = sum_j T'_sj U_sj,  T' = [T | 1]    -> y (F64 [ns])
+// mode 1 (logpsi): ln psi_s = a . sigma_s + sum_j ln cosh U_sj -> logpsi (c128),
+//                  theta_out[s][j] = U_sj (optional)
+struct FwdTcArgs {
+  const int8_t* sigma;
+  int64_t ns;
+  int n, m, cplx, mode, mt, na64, rows;  // rows = hidden rows of X (m or m + 1)
+  const void* T;          // mode 0
+  void* y;                // mode 0: F64 [ns]
+  const double* a;        // mode 1: master a
+  double* logpsi;         // mode 1
+  void* theta_out;        // mode 1 (may be null)
+  const double* skip;     // if non-null and *skip != 0, the kernel returns at once
+  int* err;               // set on a timed-out wait (may be null)
+};
+nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st);
+
+// Adjoint contraction: part[z][j][i] = sum_{s in split z} conj(T'_sj) v_s sigma'_si
+// (FP32 partials, complex interleaved for a complex RBM), j < m + 1, i < n + 1.
+struct AdjTcArgs {
+  const void* T;
+  const void* v;          // F64 [ns]
+  int64_t ns;
+  int n, m, cplx, na64, splits;
+  void* part;
+  const double* skip;
+  int* err;
+};
+nk_status launch_adj_tc(const AdjTcArgs& A, const void* sigma_t, cudaStream_t st);
+
+int adj_tc_splits(int n, int m, int cplx, int64_t ns);
+bool tc_supported_shape(int n, int m);
+
+}  // namespace nk
