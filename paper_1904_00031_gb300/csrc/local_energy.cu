@@ -165,19 +165,29 @@ __global__ void __launch_bounds__(256) local_energy_tiled(ElocArgs A) {
         const int64_t s = s0 + ss;
         const int j = k0 + kk;
         F tv;
+        // after the first move tile, t is reread from this CTA's own output
+        const bool reuse = tout && mt0 > 0;
         if constexpr (CPLX) {
           tv = make_float2(0.f, 0.f);
           if (s < A.ns && j < m) {
-            F x = th[s * m + j];
-            cf c = tanh_c(cf{x.x, x.y});
-            tv = make_float2(c.x, c.y);
-            if (tout && mt0 == 0) tout[s * m + j] = tv;
+            if (reuse) {
+              tv = tout[s * m + j];
+            } else {
+              F x = th[s * m + j];
+              cf c = tanh_c(cf{x.x, x.y});
+              tv = make_float2(c.x, c.y);
+              if (tout) tout[s * m + j] = tv;
+            }
           }
         } else {
           tv = 0.f;
           if (s < A.ns && j < m) {
-            tv = tanh_f(th[s * m + j]);
-            if (tout && mt0 == 0) tout[s * m + j] = tv;
+            if (reuse) {
+              tv = tout[s * m + j];
+            } else {
+              tv = tanh_f(th[s * m + j]);
+              if (tout) tout[s * m + j] = tv;
+            }
           }
         }
         tS[kk][ss] = tv;

@@ -1,18 +1,18 @@
 // K2: Metropolis sampling of |psi|^2 (Eq. 4; Sec. 2.2.5), single-spin flips or
 // nearest-neighbour exchanges (MetropolisExchange of the VMC listing, Sec. 3.1).
 //
-// One warp runs one chain; a CTA runs one proposal group, whose chains all
-// propose the same site (bond) at a step.  Per proposal the ratio needs, for
+// One or two warps run one chain; a CTA runs one proposal group, whose chains
+// all propose the same site (bond) at a step.  Per proposal the ratio needs, for
 // every hidden unit j, the column (cosh c_j, sinh c_j / s_i) of the move and,
 // on acceptance, its theta increment W_i (- W_k): flips read them from the
 // site tables of the RBM workspace, exchanges from per-bond tables built at
 // the start of the call in the caller's scratch.  One thread streams each
-// step's columns into shared memory with 1-D TMA bulk copies, double-buffered
-// and issued two steps ahead, so the warps read every table value from shared
-// memory once per chain.
+// step's columns into shared memory with 1-D TMA bulk copies through a
+// three-slot ring, issued two steps ahead, so the warps read every table value
+// from shared memory once per chain.
 //
 // Per chain: sigma and theta live in shared memory, t = tanh(theta) in
-// registers (lane l owns j = l + 32 q).  A proposal costs per hidden unit
+// registers.  A proposal costs per hidden unit
 // r_j = cosh c_j - s_i t_j (sinh c_j / s_i), |r_j|^2 and a running product
 // (mantissa * 2^e).  An accepted move updates theta += -2 s_i W_i (- 2 s_k W_k)
 // and t by the tanh addition formula t' = (t cosh c - sinh c) / r; t is
@@ -56,51 +56,60 @@ __device__ __forceinline__ int move_row(const MetroArgs& A, uint32_t g, int step
   return uniform_index(us.x, A.move == NK_MOVE_FLIP ? A.n : A.nb);
 }
 
-template <bool CPLX, int E>
-__global__ void __launch_bounds__(256, 1) metropolis_kernel(MetroArgs A) {
+// Thread (chain cw, half h, lane l) of a CTA owns hidden units
+// j = 32 (h + WPC q) + l, q < E: WPC warps share a chain and split its hidden
+// units; their partial log-products meet in shared memory across the one
+// barrier of each step.  The column of step t sits in ring slot t % 3: the slot
+// refilled after the barrier of step t (for step t + 2) was last read before
+// that barrier, during step t - 1.
+constexpr int kRing = 3;
+
+template <bool CPLX, int E, int WPC>
+__global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   using F = typename RatioTypes<CPLX>::F;
   using T2 = typename RatioTypes<CPLX>::T2;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int mp = A.mp, n = A.n, e = mp >> 5, G = A.G;
-  T2* colCD = reinterpret_cast<T2*>(smem);                                  // [2][mp]
-  F* colW = reinterpret_cast<F*>(smem + 2 * (size_t)mp * sizeof(T2));       // [2][mp]
-  F* thall = reinterpret_cast<F*>(reinterpret_cast<char*>(colW) + 2 * (size_t)mp * sizeof(F));
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(thall) +
-                                               (size_t)G * mp * sizeof(F));
-  int8_t* sgall = reinterpret_cast<int8_t*>(mbar + 2);
+  const int mp = A.mp, n = A.n, G = A.G;
+  const size_t slot_bytes = (size_t)mp * (sizeof(T2) + sizeof(F));
+  // ring slot k: CD [mp] T2, then WD [mp] F
+  F* thall = reinterpret_cast<F*>(smem + kRing * slot_bytes);                       // [G][mp]
+  float* part = reinterpret_cast<float*>(reinterpret_cast<char*>(thall) +
+                                         (size_t)G * mp * sizeof(F));               // [2][G][WPC]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(part + round_up(2 * G * WPC, 2));    // [kRing]
+  int8_t* sgall = reinterpret_cast<int8_t*>(mbar + kRing);                           // [G*WPC][n16]
   const int n16 = (int)round_up(n, 16);
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int c = blockIdx.x * G + w;
-  const bool active = (w < G) && (c < A.nc);
+  const int cw = w / WPC, h = w % WPC;
+  const int c = blockIdx.x * G + cw;
+  const bool active = (cw < G) && (c < A.nc);
   const uint32_t g = (uint32_t)blockIdx.x;
-  F* th = thall + (size_t)(active ? w : 0) * mp;
-  int8_t* sg = sgall + (size_t)(active ? w : 0) * n16;
+  F* th = thall + (size_t)(active ? cw : 0) * mp;
+  int8_t* sg = sgall + (size_t)(active ? w : 0) * n16;  // one copy per warp
   const T2* cdg = reinterpret_cast<const T2*>(A.cd);
   const F* wdg = reinterpret_cast<const F*>(A.wd);
   const F* wt = reinterpret_cast<const F*>(A.wt);
   const F* b32 = reinterpret_cast<const F*>(A.b32);
+  auto jof = [&](int q) { return 32 * (h + WPC * q) + lane; };
 
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int k = 0; k < kRing; ++k) mbar_init(&mbar[k], 1);
     mbar_fence_init();
   }
   if (active)
     for (int i = lane; i < n; i += 32) sg[i] = A.sigma[(int64_t)c * n + i];
   __syncthreads();
 
-  // theta = W sigma + b: rows of W^T staged through the (not yet used) column
-  // buffers, KC sites at a time, shared by the CTA's chains
+  // theta = W sigma + b: rows of W^T staged through the (not yet used) ring
   F t[E];
   {
     F* stg = reinterpret_cast<F*>(smem);
-    const int KC = (int)((2 * (size_t)mp * (sizeof(T2) + sizeof(F))) / ((size_t)mp * sizeof(F)));
+    const int KC = (int)((kRing * slot_bytes) / ((size_t)mp * sizeof(F)));
     F acc[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       if constexpr (CPLX) acc[q] = make_float2(0.f, 0.f); else acc[q] = 0.f;
-      if (q < e) acc[q] = b32[lane + 32 * q];
+      if (jof(q) < mp) acc[q] = b32[jof(q)];
     }
     for (int i0 = 0; i0 < n; i0 += KC) {
       const int kc = min(KC, n - i0);
@@ -111,8 +120,8 @@ __global__ void __launch_bounds__(256, 1) metropolis_kernel(MetroArgs A) {
           const float si = (float)sg[i0 + kk];
 #pragma unroll
           for (int q = 0; q < E; ++q) {
-            if (q < e) {
-              F wv = stg[kk * mp + lane + 32 * q];
+            if (jof(q) < mp) {
+              F wv = stg[kk * mp + jof(q)];
               if constexpr (CPLX) {
                 acc[q].x = fmaf(si, wv.x, acc[q].x);
                 acc[q].y = fmaf(si, wv.y, acc[q].y);
@@ -127,8 +136,9 @@ __global__ void __launch_bounds__(256, 1) metropolis_kernel(MetroArgs A) {
     }
 #pragma unroll
     for (int q = 0; q < E; ++q) {
-      if (q < e) {
-        if (active) th[lane + 32 * q] = acc[q];
+      if constexpr (CPLX) t[q] = make_float2(0.f, 0.f); else t[q] = 0.f;
+      if (jof(q) < mp) {
+        if (active) th[jof(q)] = acc[q];
         if constexpr (CPLX) {
           cf tt = tanh_c(cf{acc[q].x, acc[q].y});
           t[q] = make_float2(tt.x, tt.y);
@@ -142,13 +152,15 @@ __global__ void __launch_bounds__(256, 1) metropolis_kernel(MetroArgs A) {
 
   const int total = (A.n_discard + A.n_samples) * n;
   const uint32_t cd_bytes = (uint32_t)(mp * sizeof(T2)), wd_bytes = (uint32_t)(mp * sizeof(F));
+  auto issue = [&](int step, int row) {
+    const int k = step % kRing;
+    unsigned char* sl = smem + (size_t)k * slot_bytes;
+    mbar_arrive_expect_tx(&mbar[k], cd_bytes + wd_bytes);
+    bulk_g2s(sl, cdg + (int64_t)row * mp, cd_bytes, &mbar[k]);
+    bulk_g2s(sl + cd_bytes, wdg + (int64_t)row * mp, wd_bytes, &mbar[k]);
+  };
   if (tid == 0) {
-    for (int s = 0; s < 2 && s < total; ++s) {
-      const int row = move_row(A, g, s);
-      mbar_arrive_expect_tx(&mbar[s], cd_bytes + wd_bytes);
-      bulk_g2s(colCD + (size_t)s * mp, cdg + (int64_t)row * mp, cd_bytes, &mbar[s]);
-      bulk_g2s(colW + (size_t)s * mp, wdg + (int64_t)row * mp, wd_bytes, &mbar[s]);
-    }
+    for (int s2 = 0; s2 < 2 && s2 < total; ++s2) issue(s2, move_row(A, g, s2));
   }
 
   uint64_t nacc = 0;
@@ -166,102 +178,114 @@ __global__ void __launch_bounds__(256, 1) metropolis_kernel(MetroArgs A) {
     }
     const int idx = __shfl_sync(0xffffffffu, my_idx, q32);
     const double U = __shfl_sync(0xffffffffu, my_u, q32);
-    const int b = step & 1;
-    const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((step >> 1) & 1));
-    if (active && ok) {
-      int i, k = -1;
-      if (A.move == NK_MOVE_FLIP) {
-        i = idx;
-      } else {
-        i = A.bond_i[idx];
-        k = A.bond_k[idx];
-      }
-      const float si = (float)sg[i];
-      const bool null_move = (k >= 0) && (sg[k] == sg[i]);
-      if (!null_move) {
-        const T2* cd = colCD + (size_t)b * mp;
-        ScaledReal P;
-        P.init();
-#pragma unroll
-        for (int q = 0; q < E; ++q) {
-          if (q < e) {
-            const T2 v = cd[lane + 32 * q];
-            if constexpr (CPLX) {
-              // r = C - s_i t D
-              const float ux = si * t[q].x, uy = si * t[q].y;
-              const float rx = v.x - fmaf(ux, v.z, -uy * v.w);
-              const float ry = v.y - fmaf(ux, v.w, uy * v.z);
-              P.v *= fmaf(rx, rx, ry * ry);
-            } else {
-              P.v *= fmaf(-si * t[q], v.y, v.x);
-            }
-            if ((q & 7) == 7) P.renorm();
-          }
-        }
-        float l2 = P.log2v();
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, off);
-        double vis = -2.0 * (double)si * (CPLX ? A.a[2 * i] : A.a[i]);
-        if (k >= 0) vis += 2.0 * (double)si * (CPLX ? A.a[2 * k] : A.a[k]);  // s_k = -s_i
-        const float two_re = (CPLX ? 1.f : 2.f) * 0.69314718055994531f * l2 + 2.f * (float)vis;
-        if (accept_test(U, two_re)) {
-          ++nacc;
-          const F* wdc = colW + (size_t)b * mp;
-#pragma unroll
-          for (int q = 0; q < E; ++q) {
-            if (q < e) {
-              const int j = lane + 32 * q;
-              const T2 v = cd[j];
-              F x = th[j];
-              const F dw = wdc[j];
-              if constexpr (CPLX) {
-                // t' = (t C - s_i D) / (C - s_i t D)
-                const float ux = si * t[q].x, uy = si * t[q].y;
-                const float rx = v.x - fmaf(ux, v.z, -uy * v.w);
-                const float ry = v.y - fmaf(ux, v.w, uy * v.z);
-                const float nx = fmaf(t[q].x, v.x, -t[q].y * v.y) - si * v.z;
-                const float ny = fmaf(t[q].x, v.y, t[q].y * v.x) - si * v.w;
-                const float inv = __frcp_rn(fmaf(rx, rx, ry * ry));
-                t[q] = make_float2(fmaf(nx, rx, ny * ry) * inv, fmaf(ny, rx, -nx * ry) * inv);
-                x.x = fmaf(-2.f * si, dw.x, x.x);
-                x.y = fmaf(-2.f * si, dw.y, x.y);
-              } else {
-                const float r = fmaf(-si * t[q], v.y, v.x);
-                t[q] = fmaf(t[q], v.x, -si * v.y) / r;
-                x = fmaf(-2.f * si, dw, x);
-              }
-              th[j] = x;
-            }
-          }
-          __syncwarp();
-          if (lane == 0) {
-            sg[i] = (int8_t)(-sg[i]);
-            if (k >= 0) sg[k] = (int8_t)(-sg[k]);
-          }
-          __syncwarp();
-        }
-      }
+    // index of step + 2 for the copy issued after this step's barrier
+    const int idx2 = __shfl_sync(0xffffffffu, my_idx, (q32 + 2) & 31);
+    const int k = step % kRing;
+    const T2* cd = reinterpret_cast<const T2*>(smem + (size_t)k * slot_bytes);
+    const F* wdc = reinterpret_cast<const F*>(smem + (size_t)k * slot_bytes + cd_bytes);
+    const bool ok = mbar_wait_bounded(&mbar[k], (uint32_t)((step / kRing) & 1));
+    int i = idx, kk2 = -1;
+    if (A.move != NK_MOVE_FLIP) {
+      i = A.bond_i[idx];
+      kk2 = A.bond_k[idx];
     }
-    // every warp is done with buffer b: refill it for step + 2
+    const float si = (float)sg[i];
+    const bool null_move = (kk2 >= 0) && (sg[kk2] == sg[i]);
+    float* pslot = part + (step & 1) * G * WPC;
+    if (active && ok && !null_move) {
+      // four independent running products, renormalised every 8 factors each
+      ScaledReal P[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) P[u].init();
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        if (jof(q) < mp) {
+          const T2 v = cd[jof(q)];
+          if constexpr (CPLX) {
+            const float tdx = fmaf(t[q].x, v.z, -t[q].y * v.w);
+            const float tdy = fmaf(t[q].x, v.w, t[q].y * v.z);
+            const float rx = fmaf(-si, tdx, v.x);
+            const float ry = fmaf(-si, tdy, v.y);
+            P[q & 3].v *= fmaf(rx, rx, ry * ry);
+          } else {
+            P[q & 3].v *= fmaf(-si * t[q], v.y, v.x);
+          }
+        }
+        if ((q & 31) == 31) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) P[u].renorm();
+        }
+      }
+      float l2 = P[0].log2v() + P[1].log2v() + P[2].log2v() + P[3].log2v();
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, off);
+      if (lane == 0) pslot[cw * WPC + h] = l2;
+    }
+    // the one barrier of the step: partial products meet; ring slot (step - 1) % 3 is free
     timed_out = __syncthreads_or(!ok) != 0;
     if (timed_out) break;
     if (tid == 0 && step + 2 < total) {
-      const int row = move_row(A, g, step + 2);
-      mbar_arrive_expect_tx(&mbar[b], cd_bytes + wd_bytes);
-      bulk_g2s(colCD + (size_t)b * mp, cdg + (int64_t)row * mp, cd_bytes, &mbar[b]);
-      bulk_g2s(colW + (size_t)b * mp, wdg + (int64_t)row * mp, wd_bytes, &mbar[b]);
+      int row2 = idx2;
+      if (q32 + 2 >= 32) {  // step + 2 lies in the next block of draws
+        row2 = move_row(A, g, step + 2);
+      }
+      issue(step + 2, row2);
+    }
+    if (active && !null_move) {
+      float l2 = 0.f;
+#pragma unroll
+      for (int hh = 0; hh < WPC; ++hh) l2 += pslot[cw * WPC + hh];
+      double vis = -2.0 * (double)si * (CPLX ? A.a[2 * i] : A.a[i]);
+      if (kk2 >= 0) vis += 2.0 * (double)si * (CPLX ? A.a[2 * kk2] : A.a[kk2]);  // s_k = -s_i
+      const float two_re = (CPLX ? 1.f : 2.f) * 0.69314718055994531f * l2 + 2.f * (float)vis;
+      if (accept_test(U, two_re)) {
+        ++nacc;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const int j = jof(q);
+          if (j < mp) {
+            const T2 v = cd[j];
+            F x = th[j];
+            const F dw = wdc[j];
+            if constexpr (CPLX) {
+              // t' = (t C - s_i D) / (C - s_i t D)
+              const float tdx = fmaf(t[q].x, v.z, -t[q].y * v.w);
+              const float tdy = fmaf(t[q].x, v.w, t[q].y * v.z);
+              const float rx = fmaf(-si, tdx, v.x);
+              const float ry = fmaf(-si, tdy, v.y);
+              const float nx = fmaf(-si, v.z, fmaf(t[q].x, v.x, -t[q].y * v.y));
+              const float ny = fmaf(-si, v.w, fmaf(t[q].x, v.y, t[q].y * v.x));
+              const float inv = __fdividef(1.f, fmaf(rx, rx, ry * ry));
+              t[q] = make_float2(fmaf(nx, rx, ny * ry) * inv, fmaf(ny, rx, -nx * ry) * inv);
+              x.x = fmaf(-2.f * si, dw.x, x.x);
+              x.y = fmaf(-2.f * si, dw.y, x.y);
+            } else {
+              const float r = fmaf(-si * t[q], v.y, v.x);
+              t[q] = __fdividef(fmaf(t[q], v.x, -si * v.y), r);
+              x = fmaf(-2.f * si, dw, x);
+            }
+            th[j] = x;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          sg[i] = (int8_t)(-sg[i]);
+          if (kk2 >= 0) sg[kk2] = (int8_t)(-sg[kk2]);
+        }
+        __syncwarp();
+      }
     }
     if ((step + 1) % n == 0 && active) {
       const int sweep = (step + 1) / n - 1;
-      if (sweep >= A.n_discard) {
+      if (sweep >= A.n_discard && h == 0) {
         int8_t* out = A.samples + ((int64_t)c * A.n_samples + (sweep - A.n_discard)) * n;
         for (int ii = lane; ii < n; ii += 32) out[ii] = sg[ii];
       }
-      // exact refresh of t from theta
+      // exact refresh of t from theta (this thread's own entries)
 #pragma unroll
       for (int q = 0; q < E; ++q) {
-        if (q < e) {
-          const F x = th[lane + 32 * q];
+        if (jof(q) < mp) {
+          const F x = th[jof(q)];
           if constexpr (CPLX) {
             cf tt = tanh_c(cf{x.x, x.y});
             t[q] = make_float2(tt.x, tt.y);
@@ -273,11 +297,10 @@ __global__ void __launch_bounds__(256, 1) metropolis_kernel(MetroArgs A) {
     }
   }
   if (timed_out && tid == 0) {
-    // let the copy into the other buffer land before the CTA exits
-    mbar_wait_bounded(&mbar[0], 0, 1u << 20);
-    mbar_wait_bounded(&mbar[1], 0, 1u << 20);
+    // let copies still in flight land before the CTA exits
+    for (int k = 0; k < kRing; ++k) mbar_wait_bounded(&mbar[k], 0, 1u << 20);
   }
-  if (active) {
+  if (active && h == 0) {
     for (int ii = lane; ii < n; ii += 32) A.sigma[(int64_t)c * n + ii] = sg[ii];
     if (A.n_acc && lane == 0) A.n_acc[c] = timed_out ? ~0ull : nacc;
   }
@@ -323,30 +346,39 @@ size_t metropolis_scratch_bytes(int n, int m, int cplx, int nb) {
 
 // ------------------------------------------------------------------ dispatch
 
-template <bool CPLX, int E>
+template <bool CPLX, int E, int WPC>
 static nk_status launch_e(const MetroArgs& A, size_t smem, cudaStream_t st) {
-  auto kern = metropolis_kernel<CPLX, E>;
+  auto kern = metropolis_kernel<CPLX, E, WPC>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return fail(NK_ERR_CUDA, "nk_metropolis_sweep: cannot reserve %zu B shared memory", smem);
-  int blocks = (A.nc + A.G - 1) / A.G;
-  kern<<<blocks, 32 * A.G, smem, st>>>(A);
+  const int blocks = (A.nc + A.G - 1) / A.G;
+  kern<<<blocks, 32 * A.G * WPC, smem, st>>>(A);
   return check_launch("nk_metropolis_sweep");
 }
 
+// hidden units per thread E = mp / (32 WPC), rounded up to an instantiated size;
+// two warps per chain from mp = 512 on
 template <bool CPLX>
-static nk_status launch_c(const MetroArgs& A, size_t smem, cudaStream_t st) {
-  int e = A.mp / 32;
-  if (e <= 1) return launch_e<CPLX, 1>(A, smem, st);
-  if (e <= 2) return launch_e<CPLX, 2>(A, smem, st);
-  if (e <= 4) return launch_e<CPLX, 4>(A, smem, st);
-  if (e <= 8) return launch_e<CPLX, 8>(A, smem, st);
-  if (e <= 13) return launch_e<CPLX, 13>(A, smem, st);
-  if (e <= 16) return launch_e<CPLX, 16>(A, smem, st);
-  if (e <= 25) return launch_e<CPLX, 25>(A, smem, st);
-  if (e <= 32) return launch_e<CPLX, 32>(A, smem, st);
-  if (e <= 50) return launch_e<CPLX, 50>(A, smem, st);
-  if (e <= 64) return launch_e<CPLX, 64>(A, smem, st);
+static nk_status launch_c(const MetroArgs& A, size_t smem1, size_t smem2, cudaStream_t st) {
+  const int mp = A.mp;
+  if (mp < 512 || A.G * 64 > 512) {
+    const int e = mp / 32;
+    if (e <= 1) return launch_e<CPLX, 1, 1>(A, smem1, st);
+    if (e <= 2) return launch_e<CPLX, 2, 1>(A, smem1, st);
+    if (e <= 4) return launch_e<CPLX, 4, 1>(A, smem1, st);
+    if (e <= 8) return launch_e<CPLX, 8, 1>(A, smem1, st);
+    if (e <= 16) return launch_e<CPLX, 16, 1>(A, smem1, st);
+    if (e <= 32) return launch_e<CPLX, 32, 1>(A, smem1, st);
+    if (e <= 64) return launch_e<CPLX, 64, 1>(A, smem1, st);
+  } else {
+    const int e = (mp + 63) / 64;
+    if (e <= 8) return launch_e<CPLX, 8, 2>(A, smem2, st);
+    if (e <= 13) return launch_e<CPLX, 13, 2>(A, smem2, st);
+    if (e <= 16) return launch_e<CPLX, 16, 2>(A, smem2, st);
+    if (e <= 25) return launch_e<CPLX, 25, 2>(A, smem2, st);
+    if (e <= 32) return launch_e<CPLX, 32, 2>(A, smem2, st);
+  }
   return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: m = %d exceeds the register-resident limit 2048",
               A.m);
 }
@@ -399,8 +431,14 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
                                                                   (void*)A.wd);
     if (nk_status e = check_launch("nk_metropolis_sweep(pair tables)")) return e;
   }
-  const size_t smem = 2 * (size_t)L.mp * 3 * f + (size_t)A.G * L.mp * f + 16 +
-                      (size_t)A.G * round_up(r->n, 16);
+  auto smem_for = [&](int wpc) {
+    return (size_t)kRing * L.mp * 3 * f + (size_t)A.G * L.mp * f +
+           (size_t)round_up(2 * A.G * wpc, 2) * 4 + kRing * 8 +
+           (size_t)A.G * wpc * round_up(r->n, 16);
+  };
+  const size_t smem1 = smem_for(1), smem2 = smem_for(2);
+  const bool two = L.mp >= 512 && A.G * 64 <= 512;
+  const size_t smem = two ? smem2 : smem1;
   if (smem > 227 * 1024)
     return fail(NK_ERR_SHAPE,
                 "nk_metropolis_sweep: group_size %d with padded m %d needs %zu B of shared "
@@ -408,7 +446,7 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
                 A.G, L.mp, smem);
   if ((int64_t)(n_discard + n_samples) * r->n > 0x7fffffff)
     return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: too many proposals in one call");
-  return r->is_complex ? launch_c<true>(A, smem, st) : launch_c<false>(A, smem, st);
+  return r->is_complex ? launch_c<true>(A, smem1, smem2, st) : launch_c<false>(A, smem1, smem2, st);
 }
 
 }  // namespace nk

@@ -354,32 +354,51 @@ __global__ void to_f32_kernel(const void* __restrict__ src, void* dst, int64_t p
   }
 }
 
-// y~ = w o (y - <y>) in place (one CTA; fixed-order sums)
+// y~ = w o (y - <y>): pass 1 writes per-block partial sums of w y (fixed grid),
+// pass 2 adds them in a fixed order (every block gets the same mean) and
+// writes y~.
 template <bool CPLX>
-__global__ void __launch_bounds__(1024) center_kernel(void* yv, void* vout,
-                                                      const double* __restrict__ weights,
-                                                      int64_t ns, const double* scal) {
+__global__ void __launch_bounds__(kVecThreads) center_partial_kernel(
+    const void* __restrict__ yv, const double* __restrict__ weights, int64_t ns, double* red,
+    const double* scal) {
   if (scal[SC_DONE] != 0.0) return;
   const double invn = 1.0 / (double)ns;
   double sr = 0.0, si = 0.0;
-  for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) {
-    double w = weights ? weights[s] : invn;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const double w = weights ? weights[s] : invn;
     if (CPLX) {
-      double2 y = reinterpret_cast<double2*>(yv)[s];
+      const double2 y = reinterpret_cast<const double2*>(yv)[s];
       sr += w * y.x;
       si += w * y.y;
     } else {
-      sr += w * reinterpret_cast<double*>(yv)[s];
+      sr += w * reinterpret_cast<const double*>(yv)[s];
     }
   }
-  const double mr = block_sum(sr), mi = block_sum(si);
-  for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) {
-    double w = weights ? weights[s] : invn;
+  const double br = block_sum(sr);
+  const double bi = block_sum(si);
+  if (threadIdx.x == 0) {
+    red[2 * kVecBlocks + blockIdx.x] = br;
+    red[3 * kVecBlocks + blockIdx.x] = bi;
+  }
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) center_apply_kernel(
+    const void* __restrict__ yv, void* vout, const double* __restrict__ weights, int64_t ns,
+    const double* red, const double* scal) {
+  if (scal[SC_DONE] != 0.0) return;
+  const double mr = sum_partials(red + 2 * kVecBlocks);
+  const double mi = sum_partials(red + 3 * kVecBlocks);
+  const double invn = 1.0 / (double)ns;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const double w = weights ? weights[s] : invn;
     if (CPLX) {
-      double2 y = reinterpret_cast<double2*>(yv)[s];
+      const double2 y = reinterpret_cast<const double2*>(yv)[s];
       reinterpret_cast<double2*>(vout)[s] = make_double2(w * (y.x - mr), w * (y.y - mi));
     } else {
-      reinterpret_cast<double*>(vout)[s] = w * (reinterpret_cast<double*>(yv)[s] - mr);
+      reinterpret_cast<double*>(vout)[s] = w * (reinterpret_cast<const double*>(yv)[s] - mr);
     }
   }
 }
@@ -647,7 +666,10 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
       forward_fp32_kernel<CPLX><<<(unsigned)sg_blocks, kSgThreads, 0, st>>>(
           sigma, ns, n, m, sc + L.xf, T, sc + L.y, scal);
     }
-    center_kernel<CPLX><<<1, 1024, 0, st>>>(sc + L.y, sc + L.v, weights, ns, scal);
+    center_partial_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.y, weights, ns, red,
+                                                                    scal);
+    center_apply_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.y, sc + L.v, weights,
+                                                                  ns, red, scal);
     if (tc) {
       if (nk_status e = launch_adj_tc(aa, sc + L.sigt, st)) return e;
     } else {

@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "tc.cuh"
 #include "umma.cuh"
@@ -287,13 +288,34 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
       }
     }
   } else {
-    // epilogue warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. + 31
+    // epilogue warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. + 31.  In SR
+    // mode the T' values of the next tile are loaded into registers while the
+    // MMAs of that tile run (all loads in flight at once).
     const int q = w & 3;
     const int row = 32 * q + lane;
     const int64_t s = s0 + row;
     const bool live = s < A.ns;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    const int HJ = CPLX ? 64 : 128;
+    constexpr int HJ = CPLX ? 64 : 128;
+    using F = typename std::conditional<CPLX, float2, float>::type;
+    const F* T = reinterpret_cast<const F*>(A.T);
+    F tp[HJ];
+    auto load_t = [&](int jt) {
+#pragma unroll
+      for (int e = 0; e < HJ; ++e) {
+        const int j = jt * HJ + e;
+        if constexpr (CPLX) {
+          tp[e] = make_float2(0.f, 0.f);
+          if (live && j < A.m) tp[e] = T[s * A.m + j];
+          else if (j == A.m) tp[e] = make_float2(1.f, 0.f);
+        } else {
+          tp[e] = 0.f;
+          if (live && j < A.m) tp[e] = T[s * A.m + j];
+          else if (j == A.m) tp[e] = 1.f;
+        }
+      }
+    };
+    if (A.mode == 0 && A.mt > 0) load_t(0);
     double sr = 0.0, si = 0.0;
     for (int jt = 0; jt < A.mt; ++jt) {
       const int acc = jt & 1;
@@ -306,25 +328,25 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
       const int j0 = jt * HJ;
       float pr = 0.f, pi = 0.f;
       if constexpr (CPLX) {
-        const float2* T = reinterpret_cast<const float2*>(A.T);
         float2* th = reinterpret_cast<float2*>(A.theta_out);
-#pragma unroll 1
+#pragma unroll
         for (int c = 0; c < 4; ++c) {
           float ur[16], ui[16];
           tmem_ld16(tb0 + c * 16, ur);
           tmem_ld16(tb0 + 64 + c * 16, ui);
           tmem_ld_wait();
-          if (live) {
+          if (A.mode == 0) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const float2 t = tp[c * 16 + e];
+              pr += t.x * ur[e] - t.y * ui[e];
+              pi += t.x * ui[e] + t.y * ur[e];
+            }
+          } else if (live) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
               const int j = j0 + c * 16 + e;
-              if (A.mode == 0) {
-                if (j <= A.m) {
-                  const float2 t = j < A.m ? T[s * A.m + j] : make_float2(1.f, 0.f);
-                  pr += t.x * ur[e] - t.y * ui[e];
-                  pi += t.x * ui[e] + t.y * ur[e];
-                }
-              } else if (j < A.m) {
+              if (j < A.m) {
                 cf l = lncosh_c(cf{ur[e], ui[e]});
                 pr += l.x;
                 pi += l.y;
@@ -334,20 +356,20 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           }
         }
       } else {
-        const float* T = reinterpret_cast<const float*>(A.T);
         float* th = reinterpret_cast<float*>(A.theta_out);
-#pragma unroll 1
+#pragma unroll
         for (int c = 0; c < 8; ++c) {
           float u[16];
           tmem_ld16(tb0 + c * 16, u);
           tmem_ld_wait();
-          if (live) {
+          if (A.mode == 0) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) pr += tp[c * 16 + e] * u[e];
+          } else if (live) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
               const int j = j0 + c * 16 + e;
-              if (A.mode == 0) {
-                if (j <= A.m) pr += (j < A.m ? T[s * A.m + j] : 1.f) * u[e];
-              } else if (j < A.m) {
+              if (j < A.m) {
                 pr += lncosh_f(u[e]);
                 if (th) th[s * A.m + j] = u[e];
               }
@@ -360,6 +382,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
+      if (A.mode == 0 && jt + 1 < A.mt) load_t(jt + 1);
     }
     if (live) {
       if (bad) sr = si = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a timeout
@@ -499,8 +522,48 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
       umma_commit(done);
     }
   } else {
-    // producers: Z = conj(T'_sj) v_s as BF16 hi/lo, K-major swizzled A tiles
+    // producers: Z = conj(T'_sj) v_s as BF16 hi/lo, K-major swizzled A tiles.
+    // Thread (jl, half) owns parameter row j = j0 + jl and 32 samples of each
+    // 64-sample stage (complex); the T' values of the next stage are loaded
+    // into registers before the thread waits for its buffer, and v_s reaches
+    // the warp by shuffles from the lane that loaded it.
     const int pt = tid - 64;
+    constexpr int NSMP = CPLX ? 32 : 64;  // samples per thread and stage
+    const int jl = CPLX ? (pt & 63) : pt;
+    const int half = CPLX ? (pt >> 6) : 0;
+    const int j = j0 + jl;
+    using F = typename std::conditional<CPLX, float2, float>::type;
+    const F* T = reinterpret_cast<const F*>(A.T);
+    F tq[NSMP];
+    float vq0 = 0.f, vq1 = 0.f, vq2 = 0.f, vq3 = 0.f;  // v of this lane's sample(s)
+    auto load_stage = [&](int it) {
+      const int64_t kb = sb + (int64_t)it * 64 + half * 32;
+#pragma unroll
+      for (int e = 0; e < NSMP; ++e) {
+        const int64_t smp = kb + e;
+        if constexpr (CPLX) {
+          tq[e] = make_float2(0.f, 0.f);
+          if (smp < se && j < A.m) tq[e] = T[smp * A.m + j];
+          else if (smp < se && j == A.m) tq[e] = make_float2(1.f, 0.f);
+        } else {
+          tq[e] = 0.f;
+          if (smp < se && j < A.m) tq[e] = T[smp * A.m + j];
+          else if (smp < se && j == A.m) tq[e] = 1.f;
+        }
+      }
+      if constexpr (CPLX) {
+        const int64_t smp = kb + lane;
+        const double2 vd = smp < se ? reinterpret_cast<const double2*>(A.v)[smp]
+                                    : make_double2(0.0, 0.0);
+        vq0 = (float)vd.x;
+        vq1 = (float)vd.y;
+      } else {
+        const int64_t s1 = kb + lane, s2 = kb + 32 + lane;
+        vq0 = s1 < se ? (float)reinterpret_cast<const double*>(A.v)[s1] : 0.f;
+        vq2 = s2 < se ? (float)reinterpret_cast<const double*>(A.v)[s2] : 0.f;
+      }
+    };
+    if (nit > 0) load_stage(0);
     for (int it = 0; it < nit && !bad; ++it) {
       const int st = it & 1, u = it >> 1;
       if (u > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((u - 1) & 1))) {
@@ -509,83 +572,60 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
       }
       unsigned char* Ahi = sm + (size_t)st * stage_bytes;
       unsigned char* Alo = Ahi + 16384;
-      const int64_t k0 = sb + (int64_t)it * 64;
-      if constexpr (CPLX) {
-        const float2* T = reinterpret_cast<const float2*>(A.T);
-        const double2* v = reinterpret_cast<const double2*>(A.v);
-        const int jl = pt & 63, half = pt >> 6, j = j0 + jl;
-#pragma unroll 1
-        for (int cc = 0; cc < 4; ++cc) {
-          const int kl = half * 32 + cc * 8;
-          uint32_t hr[4], lr[4], hi_[4], li[4];
 #pragma unroll
-          for (int e2 = 0; e2 < 4; ++e2) {
-            float zr[2], zi[2];
+      for (int cc = 0; cc < NSMP / 8; ++cc) {
+        const int kl = half * 32 + cc * 8;
+        uint32_t hr[4], lr[4], hi_[4], li[4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int64_t s = k0 + kl + 2 * e2 + h;
-              zr[h] = zi[h] = 0.f;
-              if (s < se && j <= A.m) {
-                const float2 t = j < A.m ? T[s * A.m + j] : make_float2(1.f, 0.f);
-                const double2 vd = v[s];
-                const float vr = (float)vd.x, vi = (float)vd.y;
-                zr[h] = t.x * vr + t.y * vi;
-                zi[h] = t.x * vi - t.y * vr;
-              }
+        for (int e2 = 0; e2 < 4; ++e2) {
+          float zr[2], zi[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int e = cc * 8 + 2 * e2 + h;
+            if constexpr (CPLX) {
+              const float vr = __shfl_sync(0xffffffffu, vq0, e);
+              const float vi = __shfl_sync(0xffffffffu, vq1, e);
+              const float2 t = tq[e];
+              zr[h] = t.x * vr + t.y * vi;  // conj(t) v
+              zi[h] = t.x * vi - t.y * vr;
+            } else {
+              const float vv = e < 32 ? __shfl_sync(0xffffffffu, vq0, e & 31)
+                                      : __shfl_sync(0xffffffffu, vq2, e & 31);
+              zr[h] = tq[e] * vv;
+              zi[h] = 0.f;
             }
-            uint32_t a0, b0, a1, b1;
-            split_bf16(zr[0], a0, b0);
-            split_bf16(zr[1], a1, b1);
-            hr[e2] = a0 | (a1 << 16);
-            lr[e2] = b0 | (b1 << 16);
+          }
+          uint32_t a0, b0, a1, b1;
+          split_bf16(zr[0], a0, b0);
+          split_bf16(zr[1], a1, b1);
+          hr[e2] = a0 | (a1 << 16);
+          lr[e2] = b0 | (b1 << 16);
+          if constexpr (CPLX) {
             split_bf16(zi[0], a0, b0);
             split_bf16(zi[1], a1, b1);
             hi_[e2] = a0 | (a1 << 16);
             li[e2] = b0 | (b1 << 16);
           }
-          *reinterpret_cast<uint4*>(Ahi + sw128_offset(jl, kl)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-          *reinterpret_cast<uint4*>(Alo + sw128_offset(jl, kl)) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+        }
+        *reinterpret_cast<uint4*>(Ahi + sw128_offset(jl, kl)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+        *reinterpret_cast<uint4*>(Alo + sw128_offset(jl, kl)) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+        if constexpr (CPLX) {
           *reinterpret_cast<uint4*>(Ahi + sw128_offset(64 + jl, kl)) =
               make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
           *reinterpret_cast<uint4*>(Alo + sw128_offset(64 + jl, kl)) =
               make_uint4(li[0], li[1], li[2], li[3]);
         }
-      } else {
-        const float* T = reinterpret_cast<const float*>(A.T);
-        const double* v = reinterpret_cast<const double*>(A.v);
-        const int jl = pt, j = j0 + jl;
-#pragma unroll 1
-        for (int cc = 0; cc < 8; ++cc) {
-          const int kl = cc * 8;
-          uint32_t hr[4], lr[4];
-#pragma unroll
-          for (int e2 = 0; e2 < 4; ++e2) {
-            float zz[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int64_t s = k0 + kl + 2 * e2 + h;
-              zz[h] = 0.f;
-              if (s < se && j <= A.m) zz[h] = (j < A.m ? T[s * A.m + j] : 1.f) * (float)v[s];
-            }
-            uint32_t a0, b0, a1, b1;
-            split_bf16(zz[0], a0, b0);
-            split_bf16(zz[1], a1, b1);
-            hr[e2] = a0 | (a1 << 16);
-            lr[e2] = b0 | (b1 << 16);
-          }
-          *reinterpret_cast<uint4*>(Ahi + sw128_offset(jl, kl)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-          *reinterpret_cast<uint4*>(Alo + sw128_offset(jl, kl)) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-        }
       }
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&full[st]);
+      if (it + 1 < nit) load_stage(it + 1);
     }
     // epilogue: partial sums of this split
     if (!bad && !mbar_wait_bounded(done, 0u)) bad = true;
     tc_fence_after();
     const int q = w & 3, row = 32 * q + lane;
-    const int j = CPLX ? j0 + (row & 63) : j0 + row;
+    const int jo = CPLX ? j0 + (row & 63) : j0 + row;
     const int comp = CPLX ? (row >> 6) : 0;
     const int ma = A.m + 1, na = A.n + 1;
     float* part = reinterpret_cast<float*>(A.part);
@@ -593,13 +633,13 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
       float v[16];
       tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
       tmem_ld_wait();
-      if (j < ma) {
+      if (jo < ma) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int i = col + e;
           if (i < na) {
             const float x = (nit > 0 && !bad) ? v[e] : (bad ? __int_as_float(0x7fc00000) : 0.f);
-            const int64_t idx = ((int64_t)z * ma + j) * na + i;
+            const int64_t idx = ((int64_t)z * ma + jo) * na + i;
             if (CPLX) part[2 * idx + comp] = x;
             else part[idx] = x;
           }

@@ -74,4 +74,11 @@ class VmcSr:
 
     # kernel launches per step (for reporting)
     def launches_per_step(self) -> int:
-        return 3 + 8 + 7 * self.w.n_cg + (1 if self.move == nk.NK_MOVE_EXCHANGE else 0)
+        # metropolis (+ pair tables), logpsi, local energy; SR: stats, force (adjoint,
+        # reduce, cg init x2), 8 per CG iteration, update, prepare (2); the tensor-core
+        # path adds sigma^T once
+        n = 3 + (1 if self.move == nk.NK_MOVE_EXCHANGE else 0)
+        n += 5 + 8 * self.w.n_cg + 3
+        if self.prec == nk.NK_PREC_BF16X2:
+            n += 1
+        return n
