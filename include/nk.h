@@ -183,15 +183,24 @@ nk_status nk_operator_upload(const nk_operator* op, void* dev, size_t bytes, voi
 
 /* ---------------------------------------------------------------- estimators */
 
+/* Number of distinct moves (one- and two-spin flips with nonzero elements)
+ * of the compiled operator; host only. */
+int32_t nk_operator_moves(const nk_operator* op);
+
+/* Scratch bytes nk_local_energy needs for an operator with n_moves moves. */
+size_t nk_local_energy_scratch_bytes(int32_t m, int32_t is_complex, int32_t n_moves);
+
 /* Local energies E_loc(sigma) = sum_sigma' <sigma|H|sigma'> psi(sigma')/psi(sigma)
  * (Eq. 5, Sec. 2.2.5), with every psi ratio from the exact theta update.
- *   op_dev   compiled operator (nk_operator_upload)
+ *   op_dev   compiled operator (nk_operator_upload); n_moves = nk_operator_moves(op)
  *   sigma    int8 [ns][n];   theta F32 [ns][m] (from nk_rbm_logpsi)
  *   eloc_out c128 [ns]
- *   t_out    F32 [ns][m] tanh(theta) (the factored log-derivatives), or NULL */
-nk_status nk_local_energy(const nk_rbm* rbm, const void* op_dev, const int8_t* sigma,
-                          const void* theta, int64_t ns, double* eloc_out, void* t_out,
-                          void* stream);
+ *   t_out    F32 [ns][m] tanh(theta) (the factored log-derivatives), or NULL
+ *   scratch  nk_local_energy_scratch_bytes(m, is_complex, n_moves) bytes, 256-B
+ *            aligned (per-move ratio tables built by the call) */
+nk_status nk_local_energy(const nk_rbm* rbm, const void* op_dev, int32_t n_moves,
+                          const int8_t* sigma, const void* theta, int64_t ns, double* eloc_out,
+                          void* t_out, void* scratch, size_t scratch_bytes, void* stream);
 
 /* Log-derivatives O_k = d ln psi / d alpha_k (Sec. 2.2.5, analytic for the RBM):
  * O_a = sigma, O_b = tanh(theta), O_W = tanh(theta) (x) sigma.

@@ -285,15 +285,29 @@ nk_status nk_operator_upload(const nk_operator* op, void* dev, size_t bytes, voi
   return NK_OK;
 }
 
-nk_status nk_local_energy(const nk_rbm* rbm, const void* op_dev, const int8_t* sigma,
-                          const void* theta, int64_t ns, double* eloc_out, void* t_out,
-                          void* stream) {
+int32_t nk_operator_moves(const nk_operator* op) {
+  Compiled c;
+  if (compile_op(op, c) != NK_OK) return -1;
+  return (int32_t)c.mv.size();
+}
+
+size_t nk_local_energy_scratch_bytes(int32_t m, int32_t is_complex, int32_t n_moves) {
+  if (m < 1 || n_moves < 0) return 0;
+  return local_energy_scratch_bytes(m, is_complex ? 1 : 0, n_moves);
+}
+
+nk_status nk_local_energy(const nk_rbm* rbm, const void* op_dev, int32_t n_moves,
+                          const int8_t* sigma, const void* theta, int64_t ns, double* eloc_out,
+                          void* t_out, void* scratch, size_t scratch_bytes, void* stream) {
   if (nk_status e = check_rbm(rbm, "nk_local_energy")) return e;
-  if (ns < 0) return fail(NK_ERR_INVALID_ARG, "nk_local_energy: ns < 0");
+  if (ns < 0 || n_moves < 0) return fail(NK_ERR_INVALID_ARG, "nk_local_energy: negative size");
   if (ns == 0) return NK_OK;
   if (!op_dev || !sigma || !theta || !eloc_out)
     return fail(NK_ERR_INVALID_ARG, "nk_local_energy: NULL pointer");
-  return launch_local_energy(rbm, op_dev, sigma, theta, ns, eloc_out, t_out, (cudaStream_t)stream);
+  if (scratch && (((uintptr_t)scratch) & 255))
+    return fail(NK_ERR_INVALID_ARG, "nk_local_energy: scratch not 256-byte aligned");
+  return launch_local_energy(rbm, op_dev, n_moves, sigma, theta, ns, eloc_out, t_out, scratch,
+                             scratch_bytes, (cudaStream_t)stream);
 }
 
 nk_status nk_logderiv(const nk_rbm* rbm, const int8_t* sigma, const void* theta, int64_t ns,

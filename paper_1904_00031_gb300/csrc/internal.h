@@ -29,9 +29,10 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
                             cudaStream_t st);
 size_t metropolis_scratch_bytes(int n, int m, int cplx, int nb);
 
-nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, const int8_t* sigma,
-                              const void* theta, int64_t ns, double* eloc, void* t_out,
-                              cudaStream_t st);
+nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
+                              const int8_t* sigma, const void* theta, int64_t ns, double* eloc,
+                              void* t_out, void* scratch, size_t scratch_bytes, cudaStream_t st);
+size_t local_energy_scratch_bytes(int m, int cplx, int n_moves);
 nk_status launch_logderiv(const nk_rbm* r, const int8_t* sigma, const void* theta, int64_t ns,
                           int layout, void* o_out, cudaStream_t st);
 

@@ -11,11 +11,15 @@
 #include "internal.h"
 #include "opdev.h"
 #include "ratio.cuh"
+#include "tc.cuh"
+#include "umma.cuh"
+
+#include <string.h>
 
 namespace nk {
 
 struct ElocArgs {
-  int n, m, mp;
+  int n, m, mp, n_moves;
   int64_t ns;
   const int8_t* sigma;
   const void* theta;   // [ns][m] F
@@ -29,18 +33,18 @@ struct ElocArgs {
 __device__ __forceinline__ int idx_of(int8_t s) { return s > 0 ? 0 : 1; }
 
 // Tiled form: a CTA owns 64 configurations and walks the move list in tiles of
-// 64 moves; per chunk of 16 hidden units it stages t = tanh(theta) of its
-// configurations and (cosh c, sinh c / s_i) of the tile's moves in shared
-// memory, and every thread advances a 4 x 4 block of running products
-// prod_j (cosh c_j - s_i t_j sinh c_j / s_i) held in registers: each staged value
-// is reused by 16 threads, so the kernel is bound by the FP32 pipe rather
-// than by the memory system.  A two-spin move with cosh c = A_i A_k +/- B_i B_k,
-// sinh c / s_i = B_i A_k +/- A_i B_k is built in the staging step from the
-// site tables; the sign is fixed per move (alignment split at compilation).
+// 64 moves; every thread advances a 4 x 4 block of running products
+// prod_j (cosh c_j - s_i t_j sinh c_j / s_i) held in registers, so each staged
+// value is reused by 16 threads and the kernel is bound by the FP32 pipe.  The
+// (cosh c, sinh c / s_i) columns of all moves are built once per call in the
+// caller's scratch as a [m][moves] table (a two-spin move has cosh c =
+// A_i A_k +/- B_i B_k, sinh c / s_i = B_i A_k +/- A_i B_k from the site tables;
+// the sign is fixed per move by the alignment split at compilation); 16 x 64
+// tiles of it arrive by 2-D TMA into a double buffer, one chunk ahead, while
+// the t = tanh(theta) tile of the next chunk is loaded into registers.
 constexpr int kEBS = 64;   // configurations per CTA
 constexpr int kEBM = 64;   // moves per tile
 constexpr int kEBK = 16;   // hidden units per chunk
-constexpr int kERenorm = 8;
 
 template <bool CPLX>
 struct EScaled;
@@ -53,15 +57,55 @@ struct EScaled<false> {
   using S = ScaledReal;
 };
 
+// table[j][mv] = (cosh c_j, sinh c_j / s_i) of move mv
 template <bool CPLX>
-__global__ void __launch_bounds__(256) local_energy_tiled(ElocArgs A) {
+__global__ void move_tables_kernel(const char* __restrict__ op, const void* __restrict__ tabv,
+                                   int mp, int nm, int nm_pad, void* outv) {
+  using T2 = typename RatioTypes<CPLX>::T2;
+  const OpDevHeader* H = reinterpret_cast<const OpDevHeader*>(op);
+  const OpMove* mvs = reinterpret_cast<const OpMove*>(op + H->off_moves);
+  const T2* tab = reinterpret_cast<const T2*>(tabv);
+  T2* out = reinterpret_cast<T2*>(outv);
+  const int64_t total = (int64_t)mp * nm_pad;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(x / nm_pad), mv = (int)(x % nm_pad);
+    if (mv >= nm) {
+      if constexpr (CPLX) out[x] = make_float4(0.f, 0.f, 0.f, 0.f); else out[x] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const OpMove& M = mvs[mv];
+    const T2 ai = tab[(int64_t)M.i * mp + j];
+    if (!M.two) {
+      out[x] = ai;
+      continue;
+    }
+    const T2 ak = tab[(int64_t)M.k * mp + j];
+    const float al = (float)M.align;
+    if constexpr (CPLX) {
+      cf Ai{ai.x, ai.y}, Bi{ai.z, ai.w}, Ak{ak.x, ak.y}, Bk{ak.z, ak.w};
+      cf c = Ai * Ak + al * (Bi * Bk);
+      cf d = Bi * Ak + al * (Ai * Bk);
+      out[x] = make_float4(c.x, c.y, d.x, d.y);
+    } else {
+      out[x] = make_float2(fmaf(al * ai.y, ak.y, ai.x * ak.x), fmaf(al * ai.x, ak.y, ai.y * ak.x));
+    }
+  }
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256) local_energy_tiled(const __grid_constant__ CUtensorMap mtab,
+                                                          ElocArgs A) {
   using F = typename RatioTypes<CPLX>::F;
   using T2 = typename RatioTypes<CPLX>::T2;
-  __shared__ __align__(16) F tS[kEBK][kEBS];
-  __shared__ __align__(16) F Cs[kEBK][kEBM];
-  __shared__ __align__(16) F Ds[kEBK][kEBM];
-  __shared__ int mvi[kEBM], mvk[kEBM], mvtwo[kEBM], mval[kEBM];
-  __shared__ double2 cvs[kEBM][4];  // mel(x) * exp(visible(x)) per sign pattern x
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T2* mvt = reinterpret_cast<T2*>(smraw);                                    // [2][BK][BM]
+  F* tS = reinterpret_cast<F*>(smraw + 2 * kEBK * kEBM * sizeof(T2));        // [2][BK][BS]
+  int* mvi = reinterpret_cast<int*>(reinterpret_cast<char*>(tS) + 2 * kEBK * kEBS * sizeof(F));
+  int* mvk = mvi + kEBM;
+  int* mvtwo = mvk + kEBM;
+  double2* cvs = reinterpret_cast<double2*>(mvtwo + kEBM);                   // [BM][4]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(cvs + 4 * kEBM);              // [2]
 
   const int tid = threadIdx.x, ts = tid >> 4, tm = tid & 15;
   const int64_t s0 = (int64_t)blockIdx.x * kEBS;
@@ -70,9 +114,18 @@ __global__ void __launch_bounds__(256) local_energy_tiled(ElocArgs A) {
   const OpDSite* ds = reinterpret_cast<const OpDSite*>(A.op + H->off_dsite);
   const OpDBond* db = reinterpret_cast<const OpDBond*>(A.op + H->off_dbond);
   const OpMove* mvs = reinterpret_cast<const OpMove*>(A.op + H->off_moves);
-  const T2* tab = reinterpret_cast<const T2*>(A.tab);
   const F* th = reinterpret_cast<const F*>(A.theta);
   F* tout = reinterpret_cast<F*>(A.t_out);
+  const int nm = A.n_moves;
+  const int ntile = (nm + kEBM - 1) / kEBM, nchunk = mp / kEBK;
+  const int total = ntile * nchunk;
+  const uint32_t tile_bytes = kEBK * kEBM * sizeof(T2);
+
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    mbar_fence_init();
+  }
 
   // diagonal part: the 16 threads of a configuration split the terms
   double er[4], ei[4];
@@ -94,206 +147,169 @@ __global__ void __launch_bounds__(256) local_energy_tiled(ElocArgs A) {
     }
   }
 
-  const int nm = H->n_moves;
-  for (int mt0 = 0; mt0 < nm; mt0 += kEBM) {
-    __syncthreads();
-    if (tid < kEBM) {
-      const int mv = mt0 + tid;
-      if (mv < nm) {
-        mvi[tid] = mvs[mv].i;
-        mvk[tid] = mvs[mv].k;
-        mvtwo[tid] = mvs[mv].two;
-        mval[tid] = mvs[mv].align;
-      } else {
-        mvi[tid] = 0;
-        mvk[tid] = 0;
-        mvtwo[tid] = -1;  // padding move: ratio 1, coefficient 0
-        mval[tid] = 1;
-      }
+  // t tile of a chunk: thread covers (ss, kk) = (e >> 4, e & 15), e = tid + 256 u
+  F tv[4];
+  auto load_t = [&](int it) {
+    const int kc = it % nchunk, mt = it / nchunk;
+    const bool reuse = tout && mt > 0;  // t was written by this CTA at mt = 0
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + u * 256, ss = e >> 4, kk = e & 15;
+      const int64_t s = s0 + ss;
+      const int j = kc * kEBK + kk;
+      if constexpr (CPLX) tv[u] = make_float2(0.f, 0.f); else tv[u] = 0.f;
+      if (s < A.ns && j < m) tv[u] = reuse ? tout[s * m + j] : th[s * m + j];
     }
-    {
-      const int mm = tid >> 2, x = tid & 3, mv = mt0 + mm;
-      double cr = 0.0, ci = 0.0;
-      if (mv < nm) {
-        const double mr = mvs[mv].mel[x][0], mi = mvs[mv].mel[x][1];
-        if (mr != 0.0 || mi != 0.0) {
-          const double si = (x >> 1) ? -1.0 : 1.0, sk = (x & 1) ? -1.0 : 1.0;
-          const int i = mvs[mv].i, k = mvs[mv].k;
-          double vr, vi;
-          if (CPLX) {
-            vr = -2.0 * si * A.a[2 * i];
-            vi = -2.0 * si * A.a[2 * i + 1];
-            if (mvs[mv].two) {
-              vr += -2.0 * sk * A.a[2 * k];
-              vi += -2.0 * sk * A.a[2 * k + 1];
-            }
-          } else {
-            vr = -2.0 * si * A.a[i];
-            vi = 0.0;
-            if (mvs[mv].two) vr += -2.0 * sk * A.a[k];
-          }
-          const double ev = exp(vr), fr = ev * cos(vi), fi = ev * sin(vi);
-          cr = mr * fr - mi * fi;
-          ci = mr * fi + mi * fr;
+  };
+  auto store_t = [&](int it, int buf) {
+    const int kc = it % nchunk, mt = it / nchunk;
+    const bool reuse = tout && mt > 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + u * 256, ss = e >> 4, kk = e & 15;
+      const int64_t s = s0 + ss;
+      const int j = kc * kEBK + kk;
+      F v = tv[u];
+      if (!reuse && s < A.ns && j < m) {
+        if constexpr (CPLX) {
+          cf c = tanh_c(cf{v.x, v.y});
+          v = make_float2(c.x, c.y);
+        } else {
+          v = tanh_f(v);
         }
+        if (tout) tout[s * m + j] = v;
       }
-      cvs[mm][x] = make_double2(cr, ci);
+      tS[(buf * kEBK + kk) * kEBS + ss] = v;
     }
-    __syncthreads();
-    float sgn[4][4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const int64_t s = s0 + ts * 4 + p;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int mm = tm + 16 * q;
-        sgn[p][q] = (s < A.ns) ? (float)A.sigma[s * n + mvi[mm]] : 1.f;
-      }
-    }
-    typename EScaled<CPLX>::S P[4][4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) P[p][q].init();
+  };
 
-    for (int k0 = 0; k0 < mp; k0 += kEBK) {
-      __syncthreads();
-      // stage t = tanh(theta): 64 configurations x 16 hidden units
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = tid + u * 256, ss = e >> 4, kk = e & 15;
-        const int64_t s = s0 + ss;
-        const int j = k0 + kk;
-        F tv;
-        // after the first move tile, t is reread from this CTA's own output
-        const bool reuse = tout && mt0 > 0;
-        if constexpr (CPLX) {
-          tv = make_float2(0.f, 0.f);
-          if (s < A.ns && j < m) {
-            if (reuse) {
-              tv = tout[s * m + j];
-            } else {
-              F x = th[s * m + j];
-              cf c = tanh_c(cf{x.x, x.y});
-              tv = make_float2(c.x, c.y);
-              if (tout) tout[s * m + j] = tv;
-            }
-          }
-        } else {
-          tv = 0.f;
-          if (s < A.ns && j < m) {
-            if (reuse) {
-              tv = tout[s * m + j];
-            } else {
-              tv = tanh_f(th[s * m + j]);
-              if (tout) tout[s * m + j] = tv;
-            }
-          }
-        }
-        tS[kk][ss] = tv;
+  __syncthreads();
+  if (total > 0) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&mbar[0], tile_bytes);
+      tma_load_2d(mvt, &mtab, 0, 0, &mbar[0]);
+    }
+    load_t(0);
+    store_t(0, 0);
+  }
+
+  typename EScaled<CPLX>::S P[4][4];
+  float sgn[4][4];
+  for (int it = 0; it < total; ++it) {
+    const int b = it & 1, kc = it % nchunk, mt = it / nchunk, mt0 = mt * kEBM;
+    __syncthreads();  // chunk it-1 fully consumed; t tile of chunk it stored
+    if (kc == 0) {
+      // new tile of moves: metadata and mel * exp(visible) per sign pattern
+      if (tid < kEBM) {
+        const int mv = mt0 + tid;
+        mvi[tid] = mv < nm ? mvs[mv].i : 0;
+        mvk[tid] = mv < nm ? mvs[mv].k : 0;
+        mvtwo[tid] = mv < nm ? mvs[mv].two : -1;  // -1: padding move
       }
-      // stage (cosh c, sinh c / s_i) of 64 moves x 16 hidden units
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = tid + u * 256, mm = e >> 4, kk = e & 15;
-        const int j = k0 + kk;
-        const int two = mvtwo[mm];
-        F C, D;
-        if constexpr (CPLX) {
-          if (two < 0) {
-            C = make_float2(1.f, 0.f);
-            D = make_float2(0.f, 0.f);
-          } else {
-            const float4 ai = tab[(int64_t)mvi[mm] * mp + j];
-            if (!two) {
-              C = make_float2(ai.x, ai.y);
-              D = make_float2(ai.z, ai.w);
+      {
+        const int mm = tid >> 2, x = tid & 3, mv = mt0 + mm;
+        double cr = 0.0, ci = 0.0;
+        if (mv < nm) {
+          const double mr = mvs[mv].mel[x][0], mi = mvs[mv].mel[x][1];
+          if (mr != 0.0 || mi != 0.0) {
+            const double si = (x >> 1) ? -1.0 : 1.0, sk = (x & 1) ? -1.0 : 1.0;
+            const int i = mvs[mv].i, k = mvs[mv].k;
+            double vr, vi;
+            if (CPLX) {
+              vr = -2.0 * si * A.a[2 * i];
+              vi = -2.0 * si * A.a[2 * i + 1];
+              if (mvs[mv].two) {
+                vr += -2.0 * sk * A.a[2 * k];
+                vi += -2.0 * sk * A.a[2 * k + 1];
+              }
             } else {
-              const float4 ak = tab[(int64_t)mvk[mm] * mp + j];
-              const float al = (float)mval[mm];
-              cf Ai{ai.x, ai.y}, Bi{ai.z, ai.w}, Ak{ak.x, ak.y}, Bk{ak.z, ak.w};
-              cf c = Ai * Ak + al * (Bi * Bk);
-              cf d = Bi * Ak + al * (Ai * Bk);
-              C = make_float2(c.x, c.y);
-              D = make_float2(d.x, d.y);
+              vr = -2.0 * si * A.a[i];
+              vi = 0.0;
+              if (mvs[mv].two) vr += -2.0 * sk * A.a[k];
             }
-          }
-        } else {
-          if (two < 0) {
-            C = 1.f;
-            D = 0.f;
-          } else {
-            const float2 ai = tab[(int64_t)mvi[mm] * mp + j];
-            if (!two) {
-              C = ai.x;
-              D = ai.y;
-            } else {
-              const float2 ak = tab[(int64_t)mvk[mm] * mp + j];
-              const float al = (float)mval[mm];
-              C = fmaf(al * ai.y, ak.y, ai.x * ak.x);
-              D = fmaf(al * ai.x, ak.y, ai.y * ak.x);
-            }
+            const double ev = exp(vr), fr = ev * cos(vi), fi = ev * sin(vi);
+            cr = mr * fr - mi * fi;
+            ci = mr * fi + mi * fr;
           }
         }
-        Cs[kk][mm] = C;
-        Ds[kk][mm] = D;
+        cvs[mm * 4 + x] = make_double2(cr, ci);
       }
       __syncthreads();
 #pragma unroll
-      for (int kk = 0; kk < kEBK; ++kk) {
-        F t[4], C[4], D[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) t[p] = tS[kk][ts * 4 + p];
+      for (int p = 0; p < 4; ++p) {
+        const int64_t s = s0 + ts * 4 + p;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          C[q] = Cs[kk][tm + 16 * q];
-          D[q] = Ds[kk][tm + 16 * q];
-        }
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if constexpr (CPLX) {
-              const float tdx = fmaf(t[p].x, D[q].x, -t[p].y * D[q].y);
-              const float tdy = fmaf(t[p].x, D[q].y, t[p].y * D[q].x);
-              const float rx = fmaf(-sgn[p][q], tdx, C[q].x);
-              const float ry = fmaf(-sgn[p][q], tdy, C[q].y);
-              P[p][q].v = P[p][q].v * cf{rx, ry};
-            } else {
-              P[p][q].v *= fmaf(-sgn[p][q] * t[p], D[q], C[q]);
-            }
-          }
-        }
-        if ((kk % kERenorm) == kERenorm - 1) {
-#pragma unroll
-          for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) P[p][q].renorm();
+          sgn[p][q] = (s < A.ns) ? (float)A.sigma[s * n + mvi[tm + 16 * q]] : 1.f;
+          P[p][q].init();
         }
       }
     }
-    // fold the tile's ratios into the local energies (FP64)
+    if (tid == 0 && it + 1 < total) {
+      const int it1 = it + 1;
+      mbar_arrive_expect_tx(&mbar[b ^ 1], tile_bytes);
+      tma_load_2d(mvt + (size_t)(b ^ 1) * kEBK * kEBM, &mtab,
+                      (it1 / nchunk) * kEBM * (CPLX ? 4 : 2), (it1 % nchunk) * kEBK, &mbar[b ^ 1]);
+    }
+    if (it + 1 < total) load_t(it + 1);
+    mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1));
+    const T2* mv_b = mvt + (size_t)b * kEBK * kEBM;
+    const F* t_b = tS + (size_t)b * kEBK * kEBS;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const int64_t s = s0 + ts * 4 + p;
-      if (s >= A.ns) continue;
+    for (int kk = 0; kk < kEBK; ++kk) {
+      F t[4];
+      T2 v[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int mm = tm + 16 * q;
-        if (mvtwo[mm] < 0) continue;
-        const int x = 2 * idx_of(A.sigma[s * n + mvi[mm]]) + idx_of(A.sigma[s * n + mvk[mm]]);
-        const double2 cv = cvs[mm][x];
-        if (cv.x == 0.0 && cv.y == 0.0) continue;
-        double pr, pi;
-        if constexpr (CPLX) {
-          pr = ldexp((double)P[p][q].v.x, P[p][q].e);
-          pi = ldexp((double)P[p][q].v.y, P[p][q].e);
-        } else {
-          pr = ldexp((double)P[p][q].v, P[p][q].e);
-          pi = 0.0;
+      for (int p = 0; p < 4; ++p) t[p] = t_b[kk * kEBS + ts * 4 + p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = mv_b[kk * kEBM + tm + 16 * q];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if constexpr (CPLX) {
+            const float tdx = fmaf(t[p].x, v[q].z, -t[p].y * v[q].w);
+            const float tdy = fmaf(t[p].x, v[q].w, t[p].y * v[q].z);
+            const float rx = fmaf(-sgn[p][q], tdx, v[q].x);
+            const float ry = fmaf(-sgn[p][q], tdy, v[q].y);
+            P[p][q].v = P[p][q].v * cf{rx, ry};
+          } else {
+            P[p][q].v *= fmaf(-sgn[p][q] * t[p], v[q].y, v[q].x);
+          }
         }
-        er[p] += cv.x * pr - cv.y * pi;
-        ei[p] += cv.x * pi + cv.y * pr;
+      }
+      if ((kk & 7) == 7) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) P[p][q].renorm();
+      }
+    }
+    if (it + 1 < total) store_t(it + 1, b ^ 1);
+    if (kc == nchunk - 1) {
+      // fold the tile's ratios into the local energies (FP64)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int64_t s = s0 + ts * 4 + p;
+        if (s >= A.ns) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int mm = tm + 16 * q;
+          if (mvtwo[mm] < 0) continue;
+          const int x = 2 * idx_of(A.sigma[s * n + mvi[mm]]) + idx_of(A.sigma[s * n + mvk[mm]]);
+          const double2 cv = cvs[mm * 4 + x];
+          if (cv.x == 0.0 && cv.y == 0.0) continue;
+          double pr, pi;
+          if constexpr (CPLX) {
+            pr = ldexp((double)P[p][q].v.x, P[p][q].e);
+            pi = ldexp((double)P[p][q].v.y, P[p][q].e);
+          } else {
+            pr = ldexp((double)P[p][q].v, P[p][q].e);
+            pi = 0.0;
+          }
+          er[p] += cv.x * pr - cv.y * pi;
+          ei[p] += cv.x * pi + cv.y * pr;
+        }
       }
     }
   }
@@ -328,15 +344,25 @@ __global__ void __launch_bounds__(256) local_energy_tiled(ElocArgs A) {
   }
 }
 
-nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, const int8_t* sigma,
-                              const void* theta, int64_t ns, double* eloc, void* t_out,
-                              cudaStream_t st) {
+size_t local_energy_scratch_bytes(int m, int cplx, int n_moves) {
+  const int64_t nm_pad = round_up(std::max(n_moves, 1), kEBM);
+  return (size_t)round_up((int64_t)padded_m(m) * nm_pad * (cplx ? 16 : 8), 256);
+}
+
+nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
+                              const int8_t* sigma, const void* theta, int64_t ns, double* eloc,
+                              void* t_out, void* scratch, size_t scratch_bytes, cudaStream_t st) {
   WsLayout L(r->n, r->m, r->is_complex);
+  const bool cplx = r->is_complex != 0;
+  const size_t need = local_energy_scratch_bytes(r->m, cplx, n_moves);
+  if (n_moves > 0 && (!scratch || scratch_bytes < need))
+    return fail(NK_ERR_SHAPE, "nk_local_energy: scratch of %zu B, need %zu B", scratch_bytes, need);
   ElocArgs A;
   A.n = r->n;
   A.m = r->m;
   A.mp = L.mp;
   A.ns = ns;
+  A.n_moves = n_moves;
   A.sigma = sigma;
   A.theta = theta;
   A.op = (const char*)op_dev;
@@ -344,11 +370,38 @@ nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, const int8_t*
   A.tab = (const char*)r->ws + L.tab;
   A.eloc = eloc;
   A.t_out = t_out;
+  const int nm_pad = (int)round_up(std::max(n_moves, 1), kEBM);
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  if (n_moves > 0) {
+    const int64_t tot = (int64_t)L.mp * nm_pad;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 8));
+    if (cplx)
+      move_tables_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(A.op, A.tab, L.mp, n_moves,
+                                                                 nm_pad, scratch);
+    else
+      move_tables_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(A.op, A.tab, L.mp, n_moves,
+                                                                  nm_pad, scratch);
+    if (nk_status e = check_launch("nk_local_energy(move tables)")) return e;
+    const int fl = cplx ? 4 : 2;  // floats per table entry
+    if (!make_map_f32(&map, scratch, L.mp, (int64_t)nm_pad * fl, (int64_t)nm_pad * fl * 4,
+                      kEBM * fl, kEBK))
+      return NK_ERR_CUDA;
+  }
+  const size_t t2 = cplx ? 16 : 8, f = cplx ? 8 : 4;
+  const size_t smem = 2 * kEBK * kEBM * t2 + 2 * kEBK * kEBS * f + 3 * kEBM * 4 + kEBM * 4 * 16 + 16;
   const int64_t blocks = (ns + kEBS - 1) / kEBS;
-  if (r->is_complex)
-    local_energy_tiled<true><<<(unsigned)blocks, 256, 0, st>>>(A);
-  else
-    local_energy_tiled<false><<<(unsigned)blocks, 256, 0, st>>>(A);
+  if (cplx) {
+    if (cudaFuncSetAttribute(local_energy_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return fail(NK_ERR_CUDA, "nk_local_energy: shared memory attribute");
+    local_energy_tiled<true><<<(unsigned)blocks, 256, smem, st>>>(map, A);
+  } else {
+    if (cudaFuncSetAttribute(local_energy_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return fail(NK_ERR_CUDA, "nk_local_energy: shared memory attribute");
+    local_energy_tiled<false><<<(unsigned)blocks, 256, smem, st>>>(map, A);
+  }
   return check_launch("nk_local_energy");
 }
 

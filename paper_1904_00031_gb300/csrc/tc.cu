@@ -36,8 +36,7 @@ namespace nk {
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 static std::once_flag g_encode_once;
 
-bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
-                 int64_t row_stride_elems, int box_rows) {
+static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   std::call_once(g_encode_once, [] {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -48,7 +47,12 @@ bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
     else
       cudaGetLastError();
   });
-  if (!g_encode) {
+  return g_encode;
+}
+
+bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
+                 int64_t row_stride_elems, int box_rows) {
+  if (!encoder()) {
     fail(NK_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
     return false;
   }
@@ -62,6 +66,26 @@ bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return false;
+  }
+  return true;
+}
+
+bool make_map_f32(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
+                  int64_t stride_bytes, int box_cols, int box_rows) {
+  if (!encoder()) {
+    fail(NK_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
+    return false;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)stride_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled (FP32) failed (%d)", (int)r);
     return false;
   }
   return true;

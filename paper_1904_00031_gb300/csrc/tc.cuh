@@ -15,6 +15,11 @@ namespace nk {
 bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
                  int64_t row_stride_elems, int box_rows);
 
+// Encode a 2-D FP32 tensor map without swizzle: row-major [rows][cols] with a
+// row stride of stride_bytes, box = box_cols x box_rows.
+bool make_map_f32(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
+                  int64_t stride_bytes, int box_cols, int box_rows);
+
 // Build B planes (see WsLayout) from an FP64 augmented matrix src [src_rows][ld]
 // (double or interleaved complex), only columns < ncols used.
 nk_status launch_bplanes_from_f64(const void* src, int src_rows, int ncols, int ld, int cplx,

@@ -33,7 +33,7 @@ EXPORTS = (
     "nk_rbm_prepare", "nk_rbm_logpsi", "nk_metropolis_sweep", "nk_operator_bytes",
     "nk_operator_upload", "nk_local_energy", "nk_logderiv", "nk_sr_scratch_bytes", "nk_sr_step",
     "nk_backward_scratch_bytes", "nk_rbm_logpsi_backward", "nk_sr_step_noalloc",
-    "nk_metropolis_scratch_bytes",
+    "nk_metropolis_scratch_bytes", "nk_operator_moves", "nk_local_energy_scratch_bytes",
 )
 NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
@@ -82,7 +82,9 @@ def load_library(path: str = LIB_PATH):
         "nk_metropolis_sweep": (I32, [P, P, I32, P, P, I32, I32, I32, P, P, P, SZ, P]),
         "nk_operator_bytes": (SZ, [P]),
         "nk_operator_upload": (I32, [P, P, SZ, P]),
-        "nk_local_energy": (I32, [P, P, P, P, I64, P, P, P]),
+        "nk_operator_moves": (I32, [P]),
+        "nk_local_energy_scratch_bytes": (SZ, [I32, I32, I32]),
+        "nk_local_energy": (I32, [P, P, I32, P, P, I64, P, P, P, SZ, P]),
         "nk_logderiv": (I32, [P, P, P, I64, I32, P, P]),
         "nk_sr_scratch_bytes": (SZ, [I32, I32, I32, I64]),
         "nk_sr_step": (I32, [P, P, P, P, P, I64, I32, D, D, I32, D, I32, P, SZ, P, P]),
@@ -258,18 +260,28 @@ class Operator:
         nb = lib.nk_operator_bytes(C.byref(self._s))
         if nb == 0:
             raise NkError("nk_operator_bytes: invalid operator " + lib.nk_last_error().decode())
+        self.n_moves = int(lib.nk_operator_moves(C.byref(self._s)))
         self.dev = torch.empty(nb, dtype=torch.uint8, device=device)
         _check(lib.nk_operator_upload(C.byref(self._s), _ptr(self.dev), nb, _stream(stream)),
                "nk_operator_upload")
 
 
-def nk_local_energy(rbm: Rbm, op: Operator, sigma, theta, eloc_out=None, t_out=None, stream=None):
-    _require_gpu(sigma, theta, t_out)
+def local_energy_scratch(rbm: Rbm, op: Operator, device="cuda"):
+    nb = load_library().nk_local_energy_scratch_bytes(rbm.m, int(rbm.is_complex), op.n_moves)
+    return torch.empty(max(nb, 1), dtype=torch.uint8, device=device)
+
+
+def nk_local_energy(rbm: Rbm, op: Operator, sigma, theta, eloc_out=None, t_out=None,
+                    scratch=None, stream=None):
+    _require_gpu(sigma, theta, t_out, scratch)
     ns = sigma.shape[0]
     if eloc_out is None:
         eloc_out = torch.empty(ns, dtype=torch.complex128, device=sigma.device)
-    _check(load_library().nk_local_energy(rbm.struct(), _ptr(op.dev), _ptr(sigma), _ptr(theta), ns,
-                                          _ptr(eloc_out), _ptr(t_out), _stream(stream)),
+    if scratch is None:
+        scratch = local_energy_scratch(rbm, op, sigma.device)
+    _check(load_library().nk_local_energy(rbm.struct(), _ptr(op.dev), op.n_moves, _ptr(sigma),
+                                          _ptr(theta), ns, _ptr(eloc_out), _ptr(t_out),
+                                          _ptr(scratch), scratch.numel(), _stream(stream)),
            "nk_local_energy")
     return eloc_out
 

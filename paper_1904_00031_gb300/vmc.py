@@ -42,6 +42,7 @@ class VmcSr:
         self.info_buf = torch.zeros(nk.NK_INFO_LEN, dtype=torch.float64, device=device)
         self.move = nk.NK_MOVE_FLIP if w.move == "flip" else nk.NK_MOVE_EXCHANGE
         self.metro_scratch = nk.metropolis_scratch(self.rbm, self.move, len(b), device)
+        self.eloc_scratch = nk.local_energy_scratch(self.rbm, self.op, device)
 
     # stages ---------------------------------------------------------------
     def sample(self):
@@ -53,7 +54,8 @@ class VmcSr:
         nk.nk_rbm_logpsi(self.rbm, self.samples, self.prec, self.logpsi, self.theta)
 
     def energies(self):
-        nk.nk_local_energy(self.rbm, self.op, self.samples, self.theta, self.eloc, self.t)
+        nk.nk_local_energy(self.rbm, self.op, self.samples, self.theta, self.eloc, self.t,
+                           self.eloc_scratch)
 
     def sr(self):
         nk.nk_sr_step(self.rbm, self.samples, self.t, self.eloc, self.w.n_chains,
@@ -77,7 +79,7 @@ class VmcSr:
         # metropolis (+ pair tables), logpsi, local energy; SR: stats, force (adjoint,
         # reduce, cg init x2), 8 per CG iteration, update, prepare (2); the tensor-core
         # path adds sigma^T once
-        n = 3 + (1 if self.move == nk.NK_MOVE_EXCHANGE else 0)
+        n = 4 + (1 if self.move == nk.NK_MOVE_EXCHANGE else 0)
         n += 5 + 8 * self.w.n_cg + 3
         if self.prec == nk.NK_PREC_BF16X2:
             n += 1
