@@ -35,7 +35,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x2"])
-    ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c3", "c5"])
+    ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--graph", type=int, default=1, help="replay iterations as CUDA graphs")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp32-arm", action="store_true", help="skip the plain FP32 comparison")
@@ -50,7 +51,7 @@ def oracle_sample(workload: str, n_chains: int, spc: int, n_cg: int) -> dict:
     import numpy as np
     from oracle import local_energy, rbm, sampler, sr
     from paper_1904_00031_gb300 import workloads as W
-    w = W.workload(workload)
+    w = W.workload(workload) if workload != "c4" else W.batched_instances(64, 4242, 1024)[0]
     p = W.init_params(w.n, w.m, w.is_complex, 0.01, w.seed)
     s0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed)[:n_chains]
     t0 = time.perf_counter()
@@ -80,7 +81,8 @@ def run_oracle_subprocess(workload: str, n_chains: int, spc: int, n_cg: int) -> 
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-ORACLE_SAMPLE = {"c5": (16, 2, 50), "c3": (64, 1, 50), "c2": (128, 4, 50), "c1": (16, 63, 120)}
+ORACLE_SAMPLE = {"c5": (16, 2, 50), "c3": (64, 1, 50), "c2": (128, 4, 50), "c1": (16, 63, 120),
+                 "c4": (64, 4, 50)}
 
 
 # ---------------------------------------------------------------------- clocks
@@ -139,13 +141,25 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def metropolis_flops(w) -> float:
-    """Algorithmic FP32 work of one nk_metropolis_sweep call: per proposal and
-    hidden unit one complex ratio factor r = C - t S (complex multiply and
-    subtract, 8 flop), its squared modulus (3) and the running product (1):
-    12 flop complex, 4 flop real (r = C - t S, product)."""
-    per = 12 if w.is_complex else 4
-    return float(w.n_chains) * (w.n_discard + w.samples_per_chain) * w.n * w.m * per
+# Algorithmic FLOPs per stage (counted from the formulas, not from the kernels'
+# instruction streams; FMA = 2 flop; complex multiply = 6, complex add = 2):
+#  sampling, per hidden unit: a non-null proposal evaluates r = C - s t D and
+#    accumulates |r|^2 (complex 12, real 4); an accepted one also updates
+#    t' = (t C - s D) / r and theta (complex 32, real 8).
+#  local energy, per (configuration, move, hidden unit): r = C - s t D and the
+#    running product (complex 14, real 4).
+#  ln psi: theta = W sigma' (complex W: 4 n m per configuration).
+#  SR: per CG iteration the forward and adjoint contractions, 4 n m each per
+#    sample (complex), 2 n m (real); plus the force (one adjoint).
+def stage_flops(w, n_nonnull: float, n_accept: float, n_moves: int) -> dict:
+    c = w.is_complex
+    m, n, ns = w.m, w.n, w.n_samples
+    return {
+        "sample": m * ((12 if c else 4) * n_nonnull + (32 if c else 8) * n_accept),
+        "energies": float(ns) * n_moves * m * (14 if c else 4),
+        "amplitudes": float(ns) * (4 if c else 2) * n * m,
+        "sr": float(ns) * (4 if c else 2) * n * m * (2 * w.n_cg + 1),
+    }
 
 
 def run_gpu(args):
@@ -166,11 +180,11 @@ def run_gpu(args):
     nk.load_library()
     w = W.workload(args.workload)
     params = W.init_params(w.n, w.m, w.is_complex, 0.01, w.seed)
-    prec_name = args.prec if args.prec != "auto" else "fp32"
+    prec_name = args.prec if args.prec != "auto" else "bf16x2"
     prec = nk.NK_PREC_FP32 if prec_name == "fp32" else nk.NK_PREC_BF16X2
     # each rank samples its own chains (independent replicas)
     sigma0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed + 7919 * rank)
-    v = VmcSr(w, params, sigma0, prec)
+    v = VmcSr(w, params, sigma0, prec, graph=bool(args.graph))
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -181,22 +195,27 @@ def run_gpu(args):
     for _ in range(args.warmup):
         v.step()
     barrier()
-    stages = ["sample", "amplitudes", "energies", "sr"]
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    # timed region: K whole iterations (CUDA-graph replays unless --graph 0)
     clocks = ClockSampler(local)
     barrier()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
+    for _ in range(args.steps):
+        v.step()
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    # per-stage breakdown (eager launches, CUDA events between the stages)
+    stages = ["sample", "amplitudes", "energies", "sr"]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     for k in range(args.steps):
         ev[k][0].record(stream)
         for si, name in enumerate(stages):
             getattr(v, name)()
             ev[k][si + 1].record(stream)
-    t_end.record(stream)
     barrier()
-    clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
     stage_ms = {name: float(np.mean([ev[k][si].elapsed_time(ev[k][si + 1])
                                      for k in range(args.steps)]))
                 for si, name in enumerate(stages)}
@@ -252,19 +271,37 @@ def run_gpu(args):
 
     pk, pk_kind = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
-    dom = max(stage_ms, key=stage_ms.get)
-    roof = None
-    if dom == "sample":
-        peak = fp32_peak_tflops(sm_max)
-        ach = metropolis_flops(w) / (stage_ms["sample"] / 1e3) / 1e12
-        roof = {"kernel": "metropolis_kernel", "bound": "alu", "achieved": round(ach, 3),
-                "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
-                "traffic": None,
-                "peak_source": f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (max clock of "
-                               f"{pk_kind} peaks file)"}
+    # proposals that needed a ratio: every flip; exchanges of two unequal spins
+    # (fraction measured on the recorded samples)
+    sweeps = w.n_discard + w.samples_per_chain
+    n_prop = float(w.n_chains) * sweeps * w.n
+    if w.move == "flip":
+        nonnull_frac = 1.0
     else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None}
+        sm = v.samples.to(torch.int16)
+        bi = v.bond_i.long()
+        bk = v.bond_k.long()
+        nonnull_frac = float((sm[:, bi] != sm[:, bk]).float().mean().item())
+    n_accept = float(v.n_acc.sum().item())
+    fl = stage_flops(w, n_prop * nonnull_frac, n_accept, v.op.n_moves)
+    alu_peak = fp32_peak_tflops(sm_max)
+    tc_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0))
+    rl = {}
+    for st_name, ms in stage_ms.items():
+        tensor = st_name in ("sr", "amplitudes") and prec_name == "bf16x2"
+        peak = tc_peak if tensor else alu_peak
+        ach = fl[st_name] / (ms / 1e3) / 1e12
+        rl[st_name] = {"bound": "tensor" if tensor else "alu", "achieved": round(ach, 3),
+                       "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 4)}
+    dom = max(stage_ms, key=stage_ms.get)
+    kern = {"sample": "metropolis_kernel", "energies": "local_energy_tiled",
+            "amplitudes": "fwd_tc_kernel (ln psi)" if prec_name == "bf16x2" else "logpsi_fp32_kernel",
+            "sr": "SR step (fwd_tc + adj_tc + CG vector kernels)" if prec_name == "bf16x2"
+                  else "SR step (forward/adjoint FP32 + CG vector kernels)"}[dom]
+    roof = dict(rl[dom])
+    roof.update({"kernel": kern, "traffic": None,
+                 "peak_source": (f"{pk_kind} bf16 dense TFLOP/s (sustained)" if roof["bound"] == "tensor"
+                                 else f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz")})
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
@@ -280,13 +317,73 @@ def run_gpu(args):
         "stage_ms": {k: round(x, 3) for k, x in stage_ms.items()},
         "fp32_path_samples_per_s": None if fp32_arm is None else round(fp32_arm, 2),
         "acceptance": round(info["acceptance"], 4), "energy": info["energy"],
-        "roofline": roof,
+        "nonnull_proposal_fraction": round(nonnull_frac, 4),
+        "roofline": roof, "stage_roofline": rl,
         "e2e": {"value": round(world * w.n_samples / (e2e_ms / 1e3), 2), "unit": "samples/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nk.NK_INFO_LEN * 8},
         "gpu_launches": v.launches_per_step() * args.steps,
+        "graph": bool(args.graph),
         "clocks": clk,
     }
     return rank, out
+
+
+def run_gpu_batched(args):
+    """64 uneven independent instances, one CUDA graph launch per iteration."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1904_00031_gb300 import nk
+    from paper_1904_00031_gb300 import workloads as W
+    from paper_1904_00031_gb300.batch import BatchedVmc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    nk.load_library()
+    prec_name = args.prec if args.prec != "auto" else "bf16x2"
+    prec = nk.NK_PREC_FP32 if prec_name == "fp32" else nk.NK_PREC_BF16X2
+    insts = W.batched_instances(64, 4242 + 1000 * rank, 1024)
+    b = BatchedVmc(insts, prec=prec, graph=bool(args.graph))
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 2)):
+        b.step()
+    barrier()
+    clocks = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    t = torch.tensor([e0.elapsed_time(e1)], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item()) / args.steps
+    ns = b.n_samples
+    return rank, {
+        "metric": METRIC, "value": round(world * ns / (ms / 1e3), 2), "unit": "samples/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (64 seeded uneven 1D TFIM / Heisenberg instances)",
+        "config": {"workload": "batched_64_uneven_1d", "instances": len(insts),
+                   "n_range": [min(w.n for w in insts), max(w.n for w in insts)],
+                   "samples_per_iter": ns, "n_cg": 50, "prec": prec_name,
+                   "graph": bool(args.graph), "parallelism": f"replicas x{world}"},
+        "sr_steps_per_s": round(1e3 / ms, 4), "roofline": None,
+        "gpu_launches": b.launches_per_step() * args.steps, "clocks": clk,
+    }
 
 
 def main():
@@ -333,7 +430,7 @@ def main():
                 "kind": "oracle",
                 "sample": f"{nc} chains x ({spc} samples + 1 burn-in sweep), one full oracle "
                           f"VMC+SR iteration ({ncg} CG iterations), {r['seconds']:.1f} s"}
-    rank, out = run_gpu(args)
+    rank, out = run_gpu_batched(args) if args.workload == "c4" else run_gpu(args)
     out["cpu_baseline"] = base
     if rank == 0:
         print(json.dumps(out))

@@ -81,6 +81,10 @@ typedef struct nk_chains {
   uint64_t seed;      /* Philox4x32-10 key                                          */
   uint64_t counter;   /* proposals made so far by each chain (host; advanced by
                          nk_metropolis_sweep)                                      */
+  uint64_t* counter_dev; /* optional device copy of the counter: if not NULL the
+                         sweep reads the counter from it and advances it on the
+                         device, so that replays of a captured CUDA graph draw
+                         fresh random numbers; `counter` is then not used       */
 } nk_chains;
 
 /* A Hamiltonian as 1-local site terms and 2-local bond terms (GraphOperator,

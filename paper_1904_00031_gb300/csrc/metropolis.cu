@@ -28,6 +28,7 @@ namespace nk {
 struct MetroArgs {
   int n, m, mp, nc, G, move, nb, n_discard, n_samples;
   uint64_t seed, counter;
+  const uint64_t* counter_dev;  // if set, the counter is read from here
   const int32_t* bond_i;
   const int32_t* bond_k;
   int8_t* sigma;        // [nc][n]
@@ -51,8 +52,8 @@ __device__ __forceinline__ bool accept_test(double U, float two_re) {
   return U < exp((double)two_re);
 }
 
-__device__ __forceinline__ int move_row(const MetroArgs& A, uint32_t g, int step) {
-  u4 us = philox_stream(g, A.counter + (uint64_t)step, kTagSite, A.seed);
+__device__ __forceinline__ int move_row(const MetroArgs& A, uint64_t ctr, uint32_t g, int step) {
+  u4 us = philox_stream(g, ctr + (uint64_t)step, kTagSite, A.seed);
   return uniform_index(us.x, A.move == NK_MOVE_FLIP ? A.n : A.nb);
 }
 
@@ -78,6 +79,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   uint64_t* mbar = reinterpret_cast<uint64_t*>(part + round_up(2 * G * WPC, 2));    // [kRing]
   int8_t* sgall = reinterpret_cast<int8_t*>(mbar + kRing);                           // [G*WPC][n16]
   const int n16 = (int)round_up(n, 16);
+  const uint64_t ctr = A.counter_dev ? *A.counter_dev : A.counter;
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int cw = w / WPC, h = w % WPC;
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     bulk_g2s(sl + cd_bytes, wdg + (int64_t)row * mp, wd_bytes, &mbar[k]);
   };
   if (tid == 0) {
-    for (int s2 = 0; s2 < 2 && s2 < total; ++s2) issue(s2, move_row(A, g, s2));
+    for (int s2 = 0; s2 < 2 && s2 < total; ++s2) issue(s2, move_row(A, ctr, g, s2));
   }
 
   uint64_t nacc = 0;
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   for (int step = 0; step < total; ++step) {
     const int q32 = step & 31;
     if (q32 == 0) {  // draws for steps step .. step + 31, one per lane
-      const uint64_t gs = A.counter + (uint64_t)(step + lane);
+      const uint64_t gs = ctr + (uint64_t)(step + lane);
       u4 us = philox_stream(g, gs, kTagSite, A.seed);
       my_idx = uniform_index(us.x, A.move == NK_MOVE_FLIP ? n : A.nb);
       u4 ua = philox_stream((uint32_t)c, gs, kTagAccept, A.seed);
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     if (tid == 0 && step + 2 < total) {
       int row2 = idx2;
       if (q32 + 2 >= 32) {  // step + 2 lies in the next block of draws
-        row2 = move_row(A, g, step + 2);
+        row2 = move_row(A, ctr, g, step + 2);
       }
       issue(step + 2, row2);
     }
@@ -337,6 +339,8 @@ __global__ void pair_tables_kernel(const void* __restrict__ tabv, const void* __
   }
 }
 
+__global__ void advance_counter_kernel(uint64_t* ctr, uint64_t delta) { *ctr += delta; }
+
 size_t metropolis_scratch_bytes(int n, int m, int cplx, int nb) {
   (void)n;
   const int mp = padded_m(m);
@@ -400,6 +404,7 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
   A.n_samples = n_samples;
   A.seed = ch->seed;
   A.counter = ch->counter;
+  A.counter_dev = ch->counter_dev;
   A.bond_i = bi;
   A.bond_k = bk;
   A.sigma = ch->sigma;
@@ -446,7 +451,14 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
                 A.G, L.mp, smem);
   if ((int64_t)(n_discard + n_samples) * r->n > 0x7fffffff)
     return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: too many proposals in one call");
-  return r->is_complex ? launch_c<true>(A, smem1, smem2, st) : launch_c<false>(A, smem1, smem2, st);
+  nk_status e = r->is_complex ? launch_c<true>(A, smem1, smem2, st)
+                              : launch_c<false>(A, smem1, smem2, st);
+  if (e == NK_OK && ch->counter_dev) {
+    advance_counter_kernel<<<1, 1, 0, st>>>(ch->counter_dev,
+                                           (uint64_t)(n_discard + n_samples) * r->n);
+    e = check_launch("nk_metropolis_sweep(counter)");
+  }
+  return e;
 }
 
 }  // namespace nk

@@ -50,7 +50,7 @@ class _Rbm(C.Structure):
 
 class _Chains(C.Structure):
     _fields_ = [("nc", C.c_int32), ("group_size", C.c_int32), ("sigma", C.c_void_p),
-                ("seed", C.c_uint64), ("counter", C.c_uint64)]
+                ("seed", C.c_uint64), ("counter", C.c_uint64), ("counter_dev", C.c_void_p)]
 
 
 class _Operator(C.Structure):
@@ -194,18 +194,29 @@ def nk_rbm_logpsi(rbm: Rbm, sigma, prec=NK_PREC_FP32, logpsi_out=None, theta_out
 class Chains:
     """Persistent Markov chains: device states plus the Philox seed and counter."""
 
-    def __init__(self, sigma0, group_size: int, seed: int, device="cuda"):
+    def __init__(self, sigma0, group_size: int, seed: int, device="cuda",
+                 device_counter: bool = False):
         s = torch.as_tensor(np.asarray(sigma0, dtype=np.int8))
         self.sigma = s.to(device).contiguous()
         self.nc, self.n = self.sigma.shape
-        self._s = _Chains(self.nc, int(group_size), self.sigma.data_ptr(), int(seed), 0)
+        self.counter_dev = None
+        cptr = None
+        if device_counter:
+            # uint64 counter on the device (held in an int64 tensor)
+            self.counter_dev = torch.zeros(1, dtype=torch.int64, device=device)
+            cptr = self.counter_dev.data_ptr()
+        self._s = _Chains(self.nc, int(group_size), self.sigma.data_ptr(), int(seed), 0, cptr)
 
     @property
     def counter(self) -> int:
+        if self.counter_dev is not None:
+            return int(self.counter_dev.item()) & 0xFFFFFFFFFFFFFFFF
         return int(self._s.counter)
 
     @counter.setter
     def counter(self, v: int):
+        if self.counter_dev is not None:
+            self.counter_dev.fill_(int(v))
         self._s.counter = int(v)
 
     @property

@@ -17,14 +17,16 @@ from . import workloads as W
 
 class VmcSr:
     def __init__(self, w: W.Workload, params: W.RbmParams, sigma0=None,
-                 prec: int = nk.NK_PREC_FP32, device="cuda"):
+                 prec: int = nk.NK_PREC_FP32, device="cuda", graph: bool = False):
         self.w = w
         self.prec = prec
         self.rbm = nk.Rbm(w.n, w.m, w.is_complex, device)
         self.rbm.load(params.a, params.b, params.w)
         if sigma0 is None:
             sigma0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed)
-        self.chains = nk.Chains(sigma0, w.group_size, w.seed, device)
+        self.chains = nk.Chains(sigma0, w.group_size, w.seed, device, device_counter=graph)
+        self.use_graph = graph
+        self.graph = None
         self.op = nk.Operator(w.op, device)
         b = np.ascontiguousarray(w.sampler_bonds, dtype=np.int32)
         self.bond_i = torch.from_numpy(b[:, 0].copy()).to(device)
@@ -62,11 +64,32 @@ class VmcSr:
                       self.w.diag_shift, self.w.lr, self.w.n_cg, 1e-12, self.prec,
                       scratch=self.scratch, info_out=self.info_buf)
 
-    def step(self):
+    def _eager_step(self):
         self.sample()
         self.amplitudes()
         self.energies()
         self.sr()
+
+    def capture(self):
+        """Capture one whole iteration in a CUDA graph (nothing runs during the
+        capture; the Philox counter lives on the device, so every replay draws
+        fresh random numbers).  Call after at least one eager step."""
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._eager_step()
+
+    def step(self):
+        """One iteration.  In graph mode the first call runs eagerly and captures
+        the graph; later calls replay it."""
+        if self.use_graph:
+            if self.graph is None:
+                self._eager_step()
+                self.capture()
+            else:
+                self.graph.replay()
+        else:
+            self._eager_step()
 
     def info(self) -> dict:
         d = nk.info_dict(self.info_buf)
@@ -76,11 +99,10 @@ class VmcSr:
 
     # kernel launches per step (for reporting)
     def launches_per_step(self) -> int:
-        # metropolis (+ pair tables), logpsi, local energy; SR: stats, force (adjoint,
-        # reduce, cg init x2), 8 per CG iteration, update, prepare (2); the tensor-core
-        # path adds sigma^T once
-        n = 4 + (1 if self.move == nk.NK_MOVE_EXCHANGE else 0)
-        n += 5 + 8 * self.w.n_cg + 3
+        n = 1 + (1 if self.move == nk.NK_MOVE_EXCHANGE else 0)   # pair tables, sweep
+        n += 1                                                  # ln psi / theta
+        n += 2                                                  # move tables, local energy
+        n += 5 + 8 * self.w.n_cg + 3                            # SR: stats, force, CG, update
         if self.prec == nk.NK_PREC_BF16X2:
-            n += 1
+            n += 1                                              # sigma^T plane
         return n
