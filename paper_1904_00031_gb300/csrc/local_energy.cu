@@ -45,6 +45,7 @@ __device__ __forceinline__ int idx_of(int8_t s) { return s > 0 ? 0 : 1; }
 constexpr int kEBS = 64;   // configurations per CTA
 constexpr int kEBM = 64;   // moves per tile
 constexpr int kEBK = 16;   // hidden units per chunk
+constexpr int kETS = kEBS + 1;  // padded row of the t tile (conflict-free transposed stores)
 
 template <bool CPLX>
 struct EScaled;
@@ -94,14 +95,15 @@ __global__ void move_tables_kernel(const char* __restrict__ op, const void* __re
 }
 
 template <bool CPLX>
-__global__ void __launch_bounds__(256) local_energy_tiled(const __grid_constant__ CUtensorMap mtab,
+__global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_constant__ CUtensorMap mtab,
                                                           ElocArgs A) {
   using F = typename RatioTypes<CPLX>::F;
   using T2 = typename RatioTypes<CPLX>::T2;
   extern __shared__ __align__(128) unsigned char smraw[];
   T2* mvt = reinterpret_cast<T2*>(smraw);                                    // [2][BK][BM]
-  F* tS = reinterpret_cast<F*>(smraw + 2 * kEBK * kEBM * sizeof(T2));        // [2][BK][BS]
-  int* mvi = reinterpret_cast<int*>(reinterpret_cast<char*>(tS) + 2 * kEBK * kEBS * sizeof(F));
+  F* tS = reinterpret_cast<F*>(smraw + 2 * kEBK * kEBM * sizeof(T2));        // [2][BK][BS+1]
+  int* mvi = reinterpret_cast<int*>(reinterpret_cast<char*>(tS) +
+                                    round_up(2 * kEBK * kETS * sizeof(F), 16));
   int* mvk = mvi + kEBM;
   int* mvtwo = mvk + kEBM;
   double2* cvs = reinterpret_cast<double2*>(mvtwo + kEBM);                   // [BM][4]
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(256) local_energy_tiled(const __grid_constant_
         }
         if (tout) tout[s * m + j] = v;
       }
-      tS[(buf * kEBK + kk) * kEBS + ss] = v;
+      tS[(buf * kEBK + kk) * kETS + ss] = v;
     }
   };
 
@@ -254,13 +256,13 @@ __global__ void __launch_bounds__(256) local_energy_tiled(const __grid_constant_
     if (it + 1 < total) load_t(it + 1);
     mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1));
     const T2* mv_b = mvt + (size_t)b * kEBK * kEBM;
-    const F* t_b = tS + (size_t)b * kEBK * kEBS;
+    const F* t_b = tS + (size_t)b * kEBK * kETS;
 #pragma unroll
     for (int kk = 0; kk < kEBK; ++kk) {
       F t[4];
       T2 v[4];
 #pragma unroll
-      for (int p = 0; p < 4; ++p) t[p] = t_b[kk * kEBS + ts * 4 + p];
+      for (int p = 0; p < 4; ++p) t[p] = t_b[kk * kETS + ts * 4 + p];
 #pragma unroll
       for (int q = 0; q < 4; ++q) v[q] = mv_b[kk * kEBM + tm + 16 * q];
 #pragma unroll
@@ -389,7 +391,8 @@ nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
       return NK_ERR_CUDA;
   }
   const size_t t2 = cplx ? 16 : 8, f = cplx ? 8 : 4;
-  const size_t smem = 2 * kEBK * kEBM * t2 + 2 * kEBK * kEBS * f + 3 * kEBM * 4 + kEBM * 4 * 16 + 16;
+  const size_t smem = 2 * kEBK * kEBM * t2 + round_up(2 * kEBK * kETS * f, 16) + 3 * kEBM * 4 +
+                      kEBM * 4 * 16 + 16;
   const int64_t blocks = (ns + kEBS - 1) / kEBS;
   if (cplx) {
     if (cudaFuncSetAttribute(local_energy_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

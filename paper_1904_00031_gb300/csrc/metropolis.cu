@@ -59,11 +59,18 @@ __device__ __forceinline__ int move_row(const MetroArgs& A, uint64_t ctr, uint32
 
 // Thread (chain cw, half h, lane l) of a CTA owns hidden units
 // j = 32 (h + WPC q) + l, q < E: WPC warps share a chain and split its hidden
-// units; their partial log-products meet in shared memory across the one
-// barrier of each step.  The column of step t sits in ring slot t % 3: the slot
-// refilled after the barrier of step t (for step t + 2) was last read before
-// that barrier, during step t - 1.
+// units; their partial log-products meet in shared memory across a named
+// barrier of the pair.  The columns of step t sit in ring slot t % kRing.  The
+// warps are not in lockstep: each waits for its slot to be filled (full
+// barrier) and releases it when done (empty barrier, one arrival per warp), and
+// the copy into a slot is issued once every warp has released the slot's
+// previous step, so chains may run up to kRing - 1 steps apart and absorb the
+// uneven work of accepted, rejected and null proposals.
 constexpr int kRing = 3;
+
+__device__ __forceinline__ void pair_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
 template <bool CPLX, int E, int WPC>
 __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
@@ -76,14 +83,16 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   F* thall = reinterpret_cast<F*>(smem + kRing * slot_bytes);                       // [G][mp]
   float* part = reinterpret_cast<float*>(reinterpret_cast<char*>(thall) +
                                          (size_t)G * mp * sizeof(F));               // [2][G][WPC]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(part + round_up(2 * G * WPC, 2));    // [kRing]
-  int8_t* sgall = reinterpret_cast<int8_t*>(mbar + kRing);                           // [G*WPC][n16]
+  uint64_t* full = reinterpret_cast<uint64_t*>(part + round_up(2 * G * WPC, 2));    // [kRing]
+  uint64_t* empty = full + kRing;                                                    // [kRing]
+  int8_t* sgall = reinterpret_cast<int8_t*>(empty + kRing);                          // [G*WPC][n16]
   const int n16 = (int)round_up(n, 16);
   const uint64_t ctr = A.counter_dev ? *A.counter_dev : A.counter;
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int cw = w / WPC, h = w % WPC;
   const int c = blockIdx.x * G + cw;
+  const int chains_here = min(G, A.nc - (int)blockIdx.x * G);
   const bool active = (cw < G) && (c < A.nc);
   const uint32_t g = (uint32_t)blockIdx.x;
   F* th = thall + (size_t)(active ? cw : 0) * mp;
@@ -95,7 +104,10 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   auto jof = [&](int q) { return 32 * (h + WPC * q) + lane; };
 
   if (tid == 0) {
-    for (int k = 0; k < kRing; ++k) mbar_init(&mbar[k], 1);
+    for (int k = 0; k < kRing; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], (uint32_t)(chains_here * WPC));
+    }
     mbar_fence_init();
   }
   if (active)
@@ -151,22 +163,27 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     }
   }
   __syncthreads();
+  if (!active) return;  // no CTA-wide barrier from here on
 
   const int total = (A.n_discard + A.n_samples) * n;
   const uint32_t cd_bytes = (uint32_t)(mp * sizeof(T2)), wd_bytes = (uint32_t)(mp * sizeof(F));
-  auto issue = [&](int step, int row) {
+  auto issue = [&](int step) {
     const int k = step % kRing;
+    const int row = move_row(A, ctr, g, step);
     unsigned char* sl = smem + (size_t)k * slot_bytes;
-    mbar_arrive_expect_tx(&mbar[k], cd_bytes + wd_bytes);
-    bulk_g2s(sl, cdg + (int64_t)row * mp, cd_bytes, &mbar[k]);
-    bulk_g2s(sl + cd_bytes, wdg + (int64_t)row * mp, wd_bytes, &mbar[k]);
+    mbar_arrive_expect_tx(&full[k], cd_bytes + wd_bytes);
+    bulk_g2s(sl, cdg + (int64_t)row * mp, cd_bytes, &full[k]);
+    bulk_g2s(sl + cd_bytes, wdg + (int64_t)row * mp, wd_bytes, &full[k]);
   };
-  if (tid == 0) {
-    for (int s2 = 0; s2 < 2 && s2 < total; ++s2) issue(s2, move_row(A, ctr, g, s2));
+  const bool producer = (tid == 0);
+  int issued = 0;  // steps whose columns have been requested (producer only)
+  if (producer) {
+    for (; issued < kRing && issued < total; ++issued) issue(issued);
   }
 
   uint64_t nacc = 0;
-  bool timed_out = false;
+  bool timed_out = false;  // a bounded wait gave up: finish the loop without work
+  int nn = 0;              // non-null steps so far (identical in the warps of a chain)
   int my_idx = 0;
   double my_u = 0.0;
   for (int step = 0; step < total; ++step) {
@@ -180,12 +197,9 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     }
     const int idx = __shfl_sync(0xffffffffu, my_idx, q32);
     const double U = __shfl_sync(0xffffffffu, my_u, q32);
-    // index of step + 2 for the copy issued after this step's barrier
-    const int idx2 = __shfl_sync(0xffffffffu, my_idx, (q32 + 2) & 31);
     const int k = step % kRing;
     const T2* cd = reinterpret_cast<const T2*>(smem + (size_t)k * slot_bytes);
     const F* wdc = reinterpret_cast<const F*>(smem + (size_t)k * slot_bytes + cd_bytes);
-    const bool ok = mbar_wait_bounded(&mbar[k], (uint32_t)((step / kRing) & 1));
     int i = idx, kk2 = -1;
     if (A.move != NK_MOVE_FLIP) {
       i = A.bond_i[idx];
@@ -193,54 +207,60 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     }
     const float si = (float)sg[i];
     const bool null_move = (kk2 >= 0) && (sg[kk2] == sg[i]);
-    float* pslot = part + (step & 1) * G * WPC;
-    if (active && ok && !null_move) {
-      // four independent running products, renormalised every 8 factors each
-      ScaledReal P[4];
+    // every warp observes every phase of the slot's barrier, in order, so that
+    // no barrier is ever more than one phase ahead of a waiting warp
+    if (!timed_out) {
+      const bool ok = mbar_wait_bounded(&full[k], (uint32_t)((step / kRing) & 1));
+      timed_out = __any_sync(0xffffffffu, !ok);  // warp-uniform
+    }
+    if (!null_move) {
+      float l2 = 0.f;
+      if (!timed_out) {
+        // four independent running products, renormalised every 8 factors each
+        ScaledReal P[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) P[u].init();
+        for (int u = 0; u < 4; ++u) P[u].init();
 #pragma unroll
-      for (int q = 0; q < E; ++q) {
-        if (jof(q) < mp) {
-          const T2 v = cd[jof(q)];
-          if constexpr (CPLX) {
-            const float tdx = fmaf(t[q].x, v.z, -t[q].y * v.w);
-            const float tdy = fmaf(t[q].x, v.w, t[q].y * v.z);
-            const float rx = fmaf(-si, tdx, v.x);
-            const float ry = fmaf(-si, tdy, v.y);
-            P[q & 3].v *= fmaf(rx, rx, ry * ry);
-          } else {
-            P[q & 3].v *= fmaf(-si * t[q], v.y, v.x);
+        for (int q = 0; q < E; ++q) {
+          if (jof(q) < mp) {
+            const T2 v = cd[jof(q)];
+            if constexpr (CPLX) {
+              const float tdx = fmaf(t[q].x, v.z, -t[q].y * v.w);
+              const float tdy = fmaf(t[q].x, v.w, t[q].y * v.z);
+              const float rx = fmaf(-si, tdx, v.x);
+              const float ry = fmaf(-si, tdy, v.y);
+              P[q & 3].v *= fmaf(rx, rx, ry * ry);
+            } else {
+              P[q & 3].v *= fmaf(-si * t[q], v.y, v.x);
+            }
+          }
+          if ((q & 31) == 31) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) P[u].renorm();
           }
         }
-        if ((q & 31) == 31) {
+        l2 = P[0].log2v() + P[1].log2v() + P[2].log2v() + P[3].log2v();
 #pragma unroll
-          for (int u = 0; u < 4; ++u) P[u].renorm();
-        }
+        for (int off = 16; off >= 1; off >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, off);
       }
-      float l2 = P[0].log2v() + P[1].log2v() + P[2].log2v() + P[3].log2v();
+      if (WPC > 1) {
+        // partial buffer indexed by the non-null step count: a warp's next write
+        // to it comes after the partner has passed the next pair barrier.  A
+        // timed-out warp contributes NaN, so both warps of the chain see it and
+        // take the same (no-op) decision, keeping their sigma copies identical.
+        float* pslot = part + (nn & 1) * G * WPC;
+        if (lane == 0) pslot[cw * WPC + h] = timed_out ? __int_as_float(0x7fc00000) : l2;
+        pair_sync(1 + cw, 32 * WPC);
+        l2 = 0.f;
 #pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, off);
-      if (lane == 0) pslot[cw * WPC + h] = l2;
-    }
-    // the one barrier of the step: partial products meet; ring slot (step - 1) % 3 is free
-    timed_out = __syncthreads_or(!ok) != 0;
-    if (timed_out) break;
-    if (tid == 0 && step + 2 < total) {
-      int row2 = idx2;
-      if (q32 + 2 >= 32) {  // step + 2 lies in the next block of draws
-        row2 = move_row(A, ctr, g, step + 2);
+        for (int hh = 0; hh < WPC; ++hh) l2 += pslot[cw * WPC + hh];
+        if (isnan(l2)) timed_out = true;
       }
-      issue(step + 2, row2);
-    }
-    if (active && !null_move) {
-      float l2 = 0.f;
-#pragma unroll
-      for (int hh = 0; hh < WPC; ++hh) l2 += pslot[cw * WPC + hh];
+      ++nn;
       double vis = -2.0 * (double)si * (CPLX ? A.a[2 * i] : A.a[i]);
       if (kk2 >= 0) vis += 2.0 * (double)si * (CPLX ? A.a[2 * kk2] : A.a[kk2]);  // s_k = -s_i
       const float two_re = (CPLX ? 1.f : 2.f) * 0.69314718055994531f * l2 + 2.f * (float)vis;
-      if (accept_test(U, two_re)) {
+      if (!timed_out && accept_test(U, two_re)) {
         ++nacc;
 #pragma unroll
         for (int q = 0; q < E; ++q) {
@@ -274,10 +294,29 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
           sg[i] = (int8_t)(-sg[i]);
           if (kk2 >= 0) sg[kk2] = (int8_t)(-sg[kk2]);
         }
-        __syncwarp();
       }
     }
-    if ((step + 1) % n == 0 && active) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[k]);  // this warp is done with slot k
+    if (producer && !timed_out) {
+      // refill slots whose previous step every warp has released; block only
+      // when this warp's own next step would otherwise have no data
+      while (issued < total && issued <= step + kRing) {
+        const int prev = issued - kRing;  // last step that used the slot
+        const uint32_t par = (uint32_t)((prev / kRing) & 1);
+        if (!mbar_try_wait(&empty[prev % kRing], par)) {
+          if (issued > step + 1) break;
+          if (!mbar_wait_bounded(&empty[prev % kRing], par)) {
+            timed_out = true;
+            break;
+          }
+        }
+        issue(issued);
+        ++issued;
+      }
+    }
+    if (w == 0) timed_out = __shfl_sync(0xffffffffu, (int)timed_out, 0) != 0;
+    if ((step + 1) % n == 0) {
       const int sweep = (step + 1) / n - 1;
       if (sweep >= A.n_discard && h == 0) {
         int8_t* out = A.samples + ((int64_t)c * A.n_samples + (sweep - A.n_discard)) * n;
@@ -298,11 +337,11 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
       }
     }
   }
-  if (timed_out && tid == 0) {
+  if (timed_out && producer) {
     // let copies still in flight land before the CTA exits
-    for (int k = 0; k < kRing; ++k) mbar_wait_bounded(&mbar[k], 0, 1u << 20);
+    for (int k = 0; k < kRing; ++k) mbar_wait_bounded(&full[k], 0, 1u << 20);
   }
-  if (active && h == 0) {
+  if (h == 0) {
     for (int ii = lane; ii < n; ii += 32) A.sigma[(int64_t)c * n + ii] = sg[ii];
     if (A.n_acc && lane == 0) A.n_acc[c] = timed_out ? ~0ull : nacc;
   }
@@ -438,7 +477,7 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
   }
   auto smem_for = [&](int wpc) {
     return (size_t)kRing * L.mp * 3 * f + (size_t)A.G * L.mp * f +
-           (size_t)round_up(2 * A.G * wpc, 2) * 4 + kRing * 8 +
+           (size_t)round_up(2 * A.G * wpc, 2) * 4 + 2 * kRing * 8 +
            (size_t)A.G * wpc * round_up(r->n, 16);
   };
   const size_t smem1 = smem_for(1), smem2 = smem_for(2);
