@@ -324,10 +324,32 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     using F = typename std::conditional<CPLX, float2, float>::type;
     const F* T = reinterpret_cast<const F*>(A.T);
     F tp[HJ];
+    // 16-byte loads when every row of T starts 16-B aligned (m even for complex,
+    // m a multiple of 4 for real); the tile's tail and j = m are handled per element
+    const bool vec = CPLX ? (A.m % 2 == 0) : (A.m % 4 == 0);
     auto load_t = [&](int jt) {
+      const int j0 = jt * HJ;
+      if (vec && live && j0 + HJ <= A.m) {
+        const float4* src = reinterpret_cast<const float4*>(T + s * A.m + j0);
+        constexpr int NV = CPLX ? HJ / 2 : HJ / 4;
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+          const float4 x = src[e];
+          if constexpr (CPLX) {
+            tp[2 * e] = make_float2(x.x, x.y);
+            tp[2 * e + 1] = make_float2(x.z, x.w);
+          } else {
+            tp[4 * e] = x.x;
+            tp[4 * e + 1] = x.y;
+            tp[4 * e + 2] = x.z;
+            tp[4 * e + 3] = x.w;
+          }
+        }
+        return;
+      }
 #pragma unroll
       for (int e = 0; e < HJ; ++e) {
-        const int j = jt * HJ + e;
+        const int j = j0 + e;
         if constexpr (CPLX) {
           tp[e] = make_float2(0.f, 0.f);
           if (live && j < A.m) tp[e] = T[s * A.m + j];
@@ -547,44 +569,62 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     }
   } else {
     // producers: Z = conj(T'_sj) v_s as BF16 hi/lo, K-major swizzled A tiles.
-    // Thread (jl, half) owns parameter row j = j0 + jl and 32 samples of each
-    // 64-sample stage (complex); the T' values of the next stage are loaded
-    // into registers before the thread waits for its buffer, and v_s reaches
-    // the warp by shuffles from the lane that loaded it.
+    // Complex: thread (jp, qs) owns parameter rows j0 + 2 jp, j0 + 2 jp + 1 and
+    // samples 16 qs .. 16 qs + 15 of each 64-sample stage, loading both T values
+    // of a sample with one 16-byte load (a warp reads 512 contiguous bytes per
+    // sample); real: thread (jq, qs) owns rows j0 + 4 jq .. + 3 and samples
+    // 16 qs ..  The next stage's T values are loaded into registers before the
+    // thread waits for its buffer; v_s reaches the warp by shuffles.
     const int pt = tid - 64;
-    constexpr int NSMP = CPLX ? 32 : 64;  // samples per thread and stage
-    const int jl = CPLX ? (pt & 63) : pt;
-    const int half = CPLX ? (pt >> 6) : 0;
-    const int j = j0 + jl;
+    constexpr int JPT = CPLX ? 2 : 4;        // parameter rows per thread
+    const int jb = (pt & 31) * JPT;          // first local row
+    const int qs = pt >> 5;                  // sample quarter of the stage
+    const bool vec = (A.m % JPT) == 0;
     using F = typename std::conditional<CPLX, float2, float>::type;
     const F* T = reinterpret_cast<const F*>(A.T);
-    F tq[NSMP];
-    float vq0 = 0.f, vq1 = 0.f, vq2 = 0.f, vq3 = 0.f;  // v of this lane's sample(s)
+    F tq[16][JPT];
+    float vq0 = 0.f, vq1 = 0.f;  // v of sample (lane & 15) of this thread's quarter
     auto load_stage = [&](int it) {
-      const int64_t kb = sb + (int64_t)it * 64 + half * 32;
+      const int64_t kb = sb + (int64_t)it * 64 + qs * 16;
 #pragma unroll
-      for (int e = 0; e < NSMP; ++e) {
+      for (int e = 0; e < 16; ++e) {
         const int64_t smp = kb + e;
-        if constexpr (CPLX) {
-          tq[e] = make_float2(0.f, 0.f);
-          if (smp < se && j < A.m) tq[e] = T[smp * A.m + j];
-          else if (smp < se && j == A.m) tq[e] = make_float2(1.f, 0.f);
+        const int j = j0 + jb;
+        if (vec && smp < se && j + JPT <= A.m) {
+          const float4 x = *reinterpret_cast<const float4*>(T + smp * A.m + j);
+          if constexpr (CPLX) {
+            tq[e][0] = make_float2(x.x, x.y);
+            tq[e][1] = make_float2(x.z, x.w);
+          } else {
+            tq[e][0] = x.x;
+            tq[e][1] = x.y;
+            tq[e][2] = x.z;
+            tq[e][3] = x.w;
+          }
         } else {
-          tq[e] = 0.f;
-          if (smp < se && j < A.m) tq[e] = T[smp * A.m + j];
-          else if (smp < se && j == A.m) tq[e] = 1.f;
+#pragma unroll
+          for (int u = 0; u < JPT; ++u) {
+            const int jj = j + u;
+            if constexpr (CPLX) {
+              tq[e][u] = make_float2(0.f, 0.f);
+              if (smp < se && jj < A.m) tq[e][u] = T[smp * A.m + jj];
+              else if (smp < se && jj == A.m) tq[e][u] = make_float2(1.f, 0.f);
+            } else {
+              tq[e][u] = 0.f;
+              if (smp < se && jj < A.m) tq[e][u] = T[smp * A.m + jj];
+              else if (smp < se && jj == A.m) tq[e][u] = 1.f;
+            }
+          }
         }
       }
+      const int64_t smp = kb + (lane & 15);
       if constexpr (CPLX) {
-        const int64_t smp = kb + lane;
         const double2 vd = smp < se ? reinterpret_cast<const double2*>(A.v)[smp]
                                     : make_double2(0.0, 0.0);
         vq0 = (float)vd.x;
         vq1 = (float)vd.y;
       } else {
-        const int64_t s1 = kb + lane, s2 = kb + 32 + lane;
-        vq0 = s1 < se ? (float)reinterpret_cast<const double*>(A.v)[s1] : 0.f;
-        vq2 = s2 < se ? (float)reinterpret_cast<const double*>(A.v)[s2] : 0.f;
+        vq0 = smp < se ? (float)reinterpret_cast<const double*>(A.v)[smp] : 0.f;
       }
     };
     if (nit > 0) load_stage(0);
@@ -597,47 +637,49 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
       unsigned char* Ahi = sm + (size_t)st * stage_bytes;
       unsigned char* Alo = Ahi + 16384;
 #pragma unroll
-      for (int cc = 0; cc < NSMP / 8; ++cc) {
-        const int kl = half * 32 + cc * 8;
-        uint32_t hr[4], lr[4], hi_[4], li[4];
+      for (int cc = 0; cc < 2; ++cc) {
+        const int kl = qs * 16 + cc * 8;
 #pragma unroll
-        for (int e2 = 0; e2 < 4; ++e2) {
-          float zr[2], zi[2];
+        for (int u2 = 0; u2 < JPT; ++u2) {
+          uint32_t hr[4], lr[4], hi_[4], li[4];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int e = cc * 8 + 2 * e2 + h;
+          for (int e2 = 0; e2 < 4; ++e2) {
+            float zr[2], zi[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int e = cc * 8 + 2 * e2 + h;
+              if constexpr (CPLX) {
+                const float vr = __shfl_sync(0xffffffffu, vq0, e);
+                const float vi = __shfl_sync(0xffffffffu, vq1, e);
+                const float2 t = tq[e][u2];
+                zr[h] = t.x * vr + t.y * vi;  // conj(t) v
+                zi[h] = t.x * vi - t.y * vr;
+              } else {
+                zr[h] = tq[e][u2] * __shfl_sync(0xffffffffu, vq0, e);
+                zi[h] = 0.f;
+              }
+            }
+            uint32_t a0, b0, a1, b1;
+            split_bf16(zr[0], a0, b0);
+            split_bf16(zr[1], a1, b1);
+            hr[e2] = a0 | (a1 << 16);
+            lr[e2] = b0 | (b1 << 16);
             if constexpr (CPLX) {
-              const float vr = __shfl_sync(0xffffffffu, vq0, e);
-              const float vi = __shfl_sync(0xffffffffu, vq1, e);
-              const float2 t = tq[e];
-              zr[h] = t.x * vr + t.y * vi;  // conj(t) v
-              zi[h] = t.x * vi - t.y * vr;
-            } else {
-              const float vv = e < 32 ? __shfl_sync(0xffffffffu, vq0, e & 31)
-                                      : __shfl_sync(0xffffffffu, vq2, e & 31);
-              zr[h] = tq[e] * vv;
-              zi[h] = 0.f;
+              split_bf16(zi[0], a0, b0);
+              split_bf16(zi[1], a1, b1);
+              hi_[e2] = a0 | (a1 << 16);
+              li[e2] = b0 | (b1 << 16);
             }
           }
-          uint32_t a0, b0, a1, b1;
-          split_bf16(zr[0], a0, b0);
-          split_bf16(zr[1], a1, b1);
-          hr[e2] = a0 | (a1 << 16);
-          lr[e2] = b0 | (b1 << 16);
+          const int row = jb + u2;
+          *reinterpret_cast<uint4*>(Ahi + sw128_offset(row, kl)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+          *reinterpret_cast<uint4*>(Alo + sw128_offset(row, kl)) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
           if constexpr (CPLX) {
-            split_bf16(zi[0], a0, b0);
-            split_bf16(zi[1], a1, b1);
-            hi_[e2] = a0 | (a1 << 16);
-            li[e2] = b0 | (b1 << 16);
+            *reinterpret_cast<uint4*>(Ahi + sw128_offset(64 + row, kl)) =
+                make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
+            *reinterpret_cast<uint4*>(Alo + sw128_offset(64 + row, kl)) =
+                make_uint4(li[0], li[1], li[2], li[3]);
           }
-        }
-        *reinterpret_cast<uint4*>(Ahi + sw128_offset(jl, kl)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-        *reinterpret_cast<uint4*>(Alo + sw128_offset(jl, kl)) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-        if constexpr (CPLX) {
-          *reinterpret_cast<uint4*>(Ahi + sw128_offset(64 + jl, kl)) =
-              make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
-          *reinterpret_cast<uint4*>(Alo + sw128_offset(64 + jl, kl)) =
-              make_uint4(li[0], li[1], li[2], li[3]);
         }
       }
       fence_async_smem();
