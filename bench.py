@@ -184,7 +184,7 @@ def run_gpu(args):
     prec = nk.NK_PREC_FP32 if prec_name == "fp32" else nk.NK_PREC_BF16X2
     # each rank samples its own chains (independent replicas)
     sigma0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed + 7919 * rank)
-    v = VmcSr(w, params, sigma0, prec, graph=bool(args.graph))
+    v = VmcSr(w, params, sigma0, prec, graph=bool(args.graph), autotune=True)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -322,7 +322,7 @@ def run_gpu(args):
         "e2e": {"value": round(world * w.n_samples / (e2e_ms / 1e3), 2), "unit": "samples/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nk.NK_INFO_LEN * 8},
         "gpu_launches": v.launches_per_step() * args.steps,
-        "graph": bool(args.graph),
+        "graph": bool(args.graph), "sr_split_k": getattr(v, "split_k", None),
         "clocks": clk,
     }
     return rank, out
@@ -380,7 +380,7 @@ def run_gpu_batched(args):
         "config": {"workload": "batched_64_uneven_1d", "instances": len(insts),
                    "n_range": [min(w.n for w in insts), max(w.n for w in insts)],
                    "samples_per_iter": ns, "n_cg": 50, "prec": prec_name,
-                   "graph": bool(args.graph), "parallelism": f"replicas x{world}"},
+                   "graph": bool(args.graph), "sr_split_k": getattr(v, "split_k", None), "parallelism": f"replicas x{world}"},
         "sr_steps_per_s": round(1e3 / ms, 4), "roofline": None,
         "gpu_launches": b.launches_per_step() * args.steps, "clocks": clk,
     }

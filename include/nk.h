@@ -64,7 +64,9 @@ typedef struct nk_rbm {
   int32_t n;          /* visible units (sites), 1..NK_MAX_N                         */
   int32_t m;          /* hidden units, 1..NK_MAX_M                                  */
   int32_t is_complex; /* 0: parameters in R, 1: in C                                */
-  int32_t reserved;
+  int32_t sr_splits;  /* split-K count of the adjoint contraction of nk_sr_step and
+                         nk_rbm_logpsi_backward; 0 = built-in heuristic.  Set by
+                         nk_sr_tune (or by hand); clamped to the scratch capacity */
   double* a;          /* F64 [n]    (device)                                        */
   double* b;          /* F64 [m]    (device)                                        */
   double* w;          /* F64 [m][n] (device, row-major)                             */
@@ -258,6 +260,14 @@ nk_status nk_sr_step_noalloc(nk_rbm* rbm, const int8_t* sigma, const void* t, co
                              const double* weights, int64_t ns, int32_t n_chains,
                              double diag_shift, double lr, int32_t n_cg, double cg_rtol,
                              int32_t prec, double* info_out, void* stream);
+
+/* Autotuner of the SR contractions: times the adjoint contraction (the O^H
+ * half of every CG iteration) for a few split-K counts on the given samples
+ * and stores the fastest in rbm->sr_splits.  Arguments as for nk_sr_step.
+ * Unlike the other calls this one SYNCHRONISES `stream` (it measures with
+ * CUDA events) and must not be called while a stream is being captured. */
+nk_status nk_sr_tune(nk_rbm* rbm, const int8_t* sigma, const void* t, int64_t ns, int32_t prec,
+                     void* scratch, size_t scratch_bytes, void* stream);
 
 /* Scratch bytes nk_rbm_logpsi_backward needs for ns samples. */
 size_t nk_backward_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns);

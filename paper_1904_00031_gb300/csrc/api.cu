@@ -354,6 +354,20 @@ nk_status nk_sr_step(nk_rbm* rbm, const int8_t* sigma, const void* t, const doub
                      prec, scratch, scratch_bytes, info_out, (cudaStream_t)stream);
 }
 
+nk_status nk_sr_tune(nk_rbm* rbm, const int8_t* sigma, const void* t, int64_t ns, int32_t prec,
+                     void* scratch, size_t scratch_bytes, void* stream) {
+  if (nk_status e = check_rbm(rbm, "nk_sr_tune")) return e;
+  if (ns < 1 || !sigma || !t || !scratch)
+    return fail(NK_ERR_INVALID_ARG, "nk_sr_tune: bad arguments");
+  if (((uintptr_t)scratch) & 255)
+    return fail(NK_ERR_INVALID_ARG, "nk_sr_tune: scratch not 256-byte aligned");
+  if (prec != NK_PREC_FP32 && prec != NK_PREC_BF16X2)
+    return fail(NK_ERR_INVALID_ARG, "nk_sr_tune: unknown precision %d", prec);
+  if (prec == NK_PREC_BF16X2 && !tc_supported_shape(rbm->n, rbm->m))
+    return fail(NK_ERR_UNSUPPORTED, "nk_sr_tune: the tensor-core path supports n + 1 <= 448");
+  return run_sr_tune(rbm, sigma, t, ns, prec, scratch, scratch_bytes, (cudaStream_t)stream);
+}
+
 nk_status nk_rbm_logpsi_backward(const nk_rbm* rbm, const int8_t* sigma, int64_t ns,
                                  const double* g, double* grad_out, int32_t prec, void* scratch,
                                  size_t scratch_bytes, void* stream) {

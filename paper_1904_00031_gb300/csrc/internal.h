@@ -47,7 +47,8 @@ struct SrLayout {
   int64_t ns;
   int ma, na;        // m + 1, n + 1
   int64_t pa;        // ma * na
-  int splits;        // split-K factor of the adjoint contraction
+  int splits;        // split-K capacity of the partial buffer (2 x the heuristics)
+  int splits_fp32, splits_tc;  // heuristic split-K counts
   int na64, mt1;      // tensor-core path: n + 1 padded to 64; tiles of the m + 1 rows
   int64_t ns8;        // ns rounded up to 8
   size_t x, r, p, ap, xf, part, y, v, red, scal, sigt, xbf, total;
@@ -60,6 +61,9 @@ nk_status run_sr_step(nk_rbm* r, const int8_t* sigma, const void* t, const doubl
                       const double* weights, int64_t ns, int n_chains, double diag_shift,
                       double lr, int n_cg, double cg_rtol, int prec, void* scratch,
                       size_t scratch_bytes, double* info, cudaStream_t st);
+int sr_choose_splits(const SrLayout& L, int prec, int requested);
+nk_status run_sr_tune(nk_rbm* r, const int8_t* sigma, const void* t, int64_t ns, int prec,
+                      void* scratch, size_t scratch_bytes, cudaStream_t st);
 nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const double* g,
                        double* grad, int prec, void* scratch, size_t scratch_bytes,
                        cudaStream_t st);

@@ -44,8 +44,9 @@ SrLayout::SrLayout(int n_, int m_, int cplx_, int64_t ns_) : n(n_), m(m_), cplx(
   int tiles = ceil_div(na, 64) * ceil_div(ma, 64);
   int64_t sp = (2 * 152 + tiles - 1) / tiles;
   sp = std::min<int64_t>(sp, std::max<int64_t>(1, ns / 256));
-  splits = (int)std::max<int64_t>(1, std::min<int64_t>(sp, 64));
-  splits = std::max(splits, adj_tc_splits(n, m, cplx, ns));
+  splits_fp32 = (int)std::max<int64_t>(1, std::min<int64_t>(sp, 64));
+  splits_tc = adj_tc_splits(n, m, cplx, ns);
+  splits = std::min(64, 2 * std::max(splits_fp32, splits_tc));
   na64 = (int)round_up(n + 1, 64);
   mt1 = (m + 1 + tc_hidden_per_tile(cplx) - 1) / tc_hidden_per_tile(cplx);
   ns8 = round_up(std::max<int64_t>(ns, 1), 8);
@@ -74,6 +75,14 @@ SrLayout::SrLayout(int n_, int m_, int cplx_, int64_t ns_) : n(n_), m(m_), cplx(
 
 size_t sr_scratch_bytes(int n, int m, int cplx, int64_t ns) {
   return SrLayout(n, m, cplx, ns).total;
+}
+
+int sr_choose_splits(const SrLayout& L, int prec, int requested) {
+  const int h = prec == NK_PREC_BF16X2 ? L.splits_tc : L.splits_fp32;
+  int s = requested > 0 ? requested : h;
+  const int64_t max_useful = std::max<int64_t>(1, (L.ns + 63) / 64);
+  s = (int)std::min<int64_t>(s, max_useful);
+  return std::max(1, std::min(s, L.splits));
 }
 
 // ------------------------------------------------------------------ helpers
@@ -605,7 +614,7 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
   const int64_t corner = (int64_t)m * L.na + n;
   const bool tc = prec == NK_PREC_BF16X2;
   int* err = reinterpret_cast<int*>(scal + SC_ERR);
-  const int splits = tc ? adj_tc_splits(n, m, CPLX, ns) : L.splits;
+  const int splits = sr_choose_splits(L, prec, r->sr_splits);
   AdjTcArgs aa{};
   FwdTcArgs fa{};
   if (tc) {
@@ -703,6 +712,85 @@ nk_status run_sr_step(nk_rbm* r, const int8_t* sigma, const void* t, const doubl
                           prec, (char*)scratch, info, st);
 }
 
+// ------------------------------------------------------------------ autotuner
+
+template <bool CPLX>
+static nk_status time_adjoint(const nk_rbm* r, const int8_t* sigma, const void* T, int64_t ns,
+                              int prec, char* sc, const SrLayout& L, int splits,
+                              cudaStream_t st, float* ms) {
+  const int64_t corner = (int64_t)r->m * L.na + r->n;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(NK_ERR_CUDA, "nk_sr_tune: cannot create events");
+  AdjTcArgs aa{};
+  aa.T = T;
+  aa.v = sc + L.v;
+  aa.ns = ns;
+  aa.n = r->n;
+  aa.m = r->m;
+  aa.cplx = CPLX;
+  aa.na64 = L.na64;
+  aa.splits = splits;
+  aa.part = sc + L.part;
+  nk_status e = NK_OK;
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == NK_OK; ++rep) {
+    cudaEventRecord(e0, st);
+    if (prec == NK_PREC_BF16X2)
+      e = launch_adj_tc(aa, sc + L.sigt, st);
+    else
+      launch_adjoint_fp32<CPLX>(sigma, T, sc + L.v, ns, r->n, r->m, splits, sc + L.part, nullptr,
+                                st);
+    reduce_parts_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(
+        sc + L.part, splits, L.pa, corner, sc + L.ap, nullptr, 0.0, nullptr, nullptr);
+    cudaEventRecord(e1, st);
+    if (e == NK_OK) e = check_launch("nk_sr_tune");
+    if (cudaEventSynchronize(e1) != cudaSuccess) e = fail(NK_ERR_CUDA, "nk_sr_tune: sync");
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (rep > 0) best = std::min(best, t);  // first repetition is a warm-up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = best;
+  return e;
+}
+
+nk_status run_sr_tune(nk_rbm* r, const int8_t* sigma, const void* t, int64_t ns, int prec,
+                      void* scratch, size_t scratch_bytes, cudaStream_t st) {
+  SrLayout L(r->n, r->m, r->is_complex, ns);
+  if (scratch_bytes < L.total)
+    return fail(NK_ERR_SHAPE, "nk_sr_tune: scratch of %zu B, need %zu B", scratch_bytes, L.total);
+  char* sc = (char*)scratch;
+  // any finite v: only the timing matters
+  if (cudaMemsetAsync(sc + L.v, 0, (size_t)ns * (r->is_complex ? 16 : 8), st) != cudaSuccess)
+    return fail(NK_ERR_CUDA, "nk_sr_tune: memset");
+  if (prec == NK_PREC_BF16X2) {
+    if (nk_status e = launch_sigma_t(sigma, ns, r->n, L.na64, sc + L.sigt, st)) return e;
+  }
+  const int h = prec == NK_PREC_BF16X2 ? L.splits_tc : L.splits_fp32;
+  int cand[6] = {h / 4, h / 2, h, (3 * h) / 2, 2 * h, 0};
+  int best_s = sr_choose_splits(L, prec, h);
+  float best_t = 1e30f;
+  int last = -1;
+  for (int k = 0; k < 5; ++k) {
+    const int sp = sr_choose_splits(L, prec, std::max(1, cand[k]));
+    if (sp == last) continue;
+    last = sp;
+    float ms = 0.f;
+    nk_status e = r->is_complex
+                      ? time_adjoint<true>(r, sigma, t, ns, prec, sc, L, sp, st, &ms)
+                      : time_adjoint<false>(r, sigma, t, ns, prec, sc, L, sp, st, &ms);
+    if (e) return e;
+    if (ms < best_t) {
+      best_t = ms;
+      best_s = sp;
+    }
+  }
+  r->sr_splits = best_s;
+  return NK_OK;
+}
+
 // ------------------------------------------------------------------ K8 backward
 
 size_t backward_scratch_bytes(int n, int m, int cplx, int64_t ns) {
@@ -742,7 +830,7 @@ nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const d
   int64_t blocks = std::min<int64_t>((ns + 255) / 256, 1024);
   if (blocks < 1) blocks = 1;
   const bool tc = prec == NK_PREC_BF16X2;
-  const int splits = tc ? adj_tc_splits(r->n, r->m, r->is_complex, ns) : L.splits;
+  const int splits = sr_choose_splits(L, prec, r->sr_splits);
   if (tc) {
     if ((e = launch_sigma_t(sigma, ns, r->n, L.na64, sc + L.sigt, st))) return e;
   }

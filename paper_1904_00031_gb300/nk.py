@@ -34,6 +34,7 @@ EXPORTS = (
     "nk_operator_upload", "nk_local_energy", "nk_logderiv", "nk_sr_scratch_bytes", "nk_sr_step",
     "nk_backward_scratch_bytes", "nk_rbm_logpsi_backward", "nk_sr_step_noalloc",
     "nk_metropolis_scratch_bytes", "nk_operator_moves", "nk_local_energy_scratch_bytes",
+    "nk_sr_tune",
 )
 NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
@@ -44,7 +45,7 @@ class NkError(RuntimeError):
 
 class _Rbm(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("is_complex", C.c_int32),
-                ("reserved", C.c_int32), ("a", C.c_void_p), ("b", C.c_void_p), ("w", C.c_void_p),
+                ("sr_splits", C.c_int32), ("a", C.c_void_p), ("b", C.c_void_p), ("w", C.c_void_p),
                 ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
 
 
@@ -91,6 +92,7 @@ def load_library(path: str = LIB_PATH):
         "nk_backward_scratch_bytes": (SZ, [I32, I32, I32, I64]),
         "nk_rbm_logpsi_backward": (I32, [P, P, I64, P, P, I32, P, SZ, P]),
         "nk_sr_step_noalloc": (I32, [P, P, P, P, P, I64, I32, D, D, I32, D, I32, P, P]),
+        "nk_sr_tune": (I32, [P, P, P, I64, I32, P, SZ, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -327,6 +329,18 @@ def nk_sr_step(rbm: Rbm, sigma, t, eloc, n_chains: int, diag_shift: float, lr: f
         float(diag_shift), float(lr), int(n_cg), float(cg_rtol), prec, _ptr(scratch),
         scratch.numel(), _ptr(info_out), _stream(stream)), "nk_sr_step")
     return info_out
+
+
+def nk_sr_tune(rbm: Rbm, sigma, t, prec=NK_PREC_FP32, scratch=None, stream=None) -> int:
+    """Autotune the split-K count of the SR contractions (synchronises); returns it
+    and stores it in the RBM for later nk_sr_step calls."""
+    _require_gpu(sigma, t, scratch)
+    ns = sigma.shape[0]
+    if scratch is None:
+        scratch = sr_scratch(rbm, ns, sigma.device)
+    _check(load_library().nk_sr_tune(rbm.struct(), _ptr(sigma), _ptr(t), ns, prec, _ptr(scratch),
+                                     scratch.numel(), _stream(stream)), "nk_sr_tune")
+    return int(rbm._s.sr_splits)
 
 
 def info_dict(info) -> dict:

@@ -17,7 +17,8 @@ from . import workloads as W
 
 class VmcSr:
     def __init__(self, w: W.Workload, params: W.RbmParams, sigma0=None,
-                 prec: int = nk.NK_PREC_FP32, device="cuda", graph: bool = False):
+                 prec: int = nk.NK_PREC_FP32, device="cuda", graph: bool = False,
+                 autotune: bool = False):
         self.w = w
         self.prec = prec
         self.rbm = nk.Rbm(w.n, w.m, w.is_complex, device)
@@ -27,6 +28,8 @@ class VmcSr:
         self.chains = nk.Chains(sigma0, w.group_size, w.seed, device, device_counter=graph)
         self.use_graph = graph
         self.graph = None
+        self.autotune = autotune
+        self.tuned = False
         self.op = nk.Operator(w.op, device)
         b = np.ascontiguousarray(w.sampler_bonds, dtype=np.int32)
         self.bond_i = torch.from_numpy(b[:, 0].copy()).to(device)
@@ -79,17 +82,22 @@ class VmcSr:
         with torch.cuda.graph(self.graph):
             self._eager_step()
 
+    def tune(self):
+        """Autotune the SR contractions on the current samples (synchronises)."""
+        self.split_k = nk.nk_sr_tune(self.rbm, self.samples, self.t, self.prec, self.scratch)
+        self.tuned = True
+
     def step(self):
-        """One iteration.  In graph mode the first call runs eagerly and captures
-        the graph; later calls replay it."""
+        """One iteration.  The first call also autotunes (if asked) and, in graph
+        mode, captures the graph; later graph-mode calls replay it."""
+        if self.use_graph and self.graph is not None:
+            self.graph.replay()
+            return
+        self._eager_step()
+        if self.autotune and not self.tuned:
+            self.tune()
         if self.use_graph:
-            if self.graph is None:
-                self._eager_step()
-                self.capture()
-            else:
-                self.graph.replay()
-        else:
-            self._eager_step()
+            self.capture()
 
     def info(self) -> dict:
         d = nk.info_dict(self.info_buf)

@@ -362,3 +362,23 @@ def test_sr_step_bf16x2_matches_oracle(nk, cplx):
     a, b, w = r.params_numpy()
     d_gpu = (p.flat() - np.concatenate([a, b, w.reshape(-1)])) / 0.05
     assert np.linalg.norm(d_gpu - delta) <= 5e-3 * np.linalg.norm(delta)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sr_autotune_keeps_results(nk, prec):
+    """The split-K autotuner only changes how the adjoint sum is split: the SR
+    direction after tuning agrees with the untuned one to FP32 summation noise."""
+    n = 12
+    op = W.heisenberg(n, W.chain_bonds(n), 1.0, True, W.sublattice(n))
+    m, ns, nc = 2 * n, 4096, 64
+    p, s, r, sg, t, e = _sr_inputs(nk, n, m, True, ns, op, True)
+    r2 = make_rbm(nk, p)
+    sp = nk.nk_sr_tune(r2, sg, t, prec=prec)
+    assert sp >= 1 and r2._s.sr_splits == sp
+    nk.nk_sr_step(r, sg, t, e, nc, 0.01, 0.05, n_cg=20, prec=prec)
+    nk.nk_sr_step(r2, sg, t, e, nc, 0.01, 0.05, n_cg=20, prec=prec)
+    a = np.concatenate([x.reshape(-1) for x in r.params_numpy()])
+    b = np.concatenate([x.reshape(-1) for x in r2.params_numpy()])
+    d = (p.flat() - a) / 0.05
+    d2 = (p.flat() - b) / 0.05
+    assert np.linalg.norm(d - d2) <= 1e-4 * np.linalg.norm(d)
