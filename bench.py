@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x2"])
     ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--graph", type=int, default=1, help="replay iterations as CUDA graphs")
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="small 20x20 J1-J2 case for ncu captures: one CTA per SM per kernel")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp32-arm", action="store_true", help="skip the plain FP32 comparison")
@@ -198,15 +200,19 @@ def run_gpu(args):
     # timed region: K whole iterations (CUDA-graph replays unless --graph 0)
     clocks = ClockSampler(local)
     barrier()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for _ in range(args.steps):
+    small = w.n_samples * w.m * (8 if w.is_complex else 4) <= 129e6
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if small else None
+    ev_it = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps)]
+    for k in range(args.steps):
+        if flush is not None:
+            flush.zero_()  # evict the working set from the 129 MB L2 (outside the timing)
+        ev_it[k][0].record(stream)
         v.step()
-    t_end.record(stream)
+        ev_it[k][1].record(stream)
     barrier()
     clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev_it)
     # per-stage breakdown (eager launches, CUDA events between the stages)
     stages = ["sample", "amplitudes", "energies", "sr"]
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
@@ -269,6 +275,10 @@ def run_gpu(args):
         barrier()
         fp32_arm = w.n_samples / (a0.elapsed_time(a1) / args.steps / 1e3)
 
+    t_bytes = w.n_samples * w.m * (8 if w.is_complex else 4)
+    l2_note = (f"inputs larger than L2 (T = tanh theta is {t_bytes / 1e6:.0f} MB)" if t_bytes > 129e6
+               else f"inputs smaller than L2 (T is {t_bytes / 1e6:.1f} MB); L2 flushed before each "
+                    "timed iteration")
     pk, pk_kind = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
     # proposals that needed a ratio: every flip; exchanges of two unequal spins
@@ -311,7 +321,7 @@ def run_gpu(args):
                    "chains": w.n_chains, "samples_per_chain": w.samples_per_chain,
                    "burn_in_sweeps": w.n_discard, "samples_per_iter": w.n_samples,
                    "moves": w.move, "n_cg": w.n_cg, "diag_shift": w.diag_shift, "lr": w.lr,
-                   "prec": prec_name, "l2": "inputs larger than L2 (T = tanh theta is 839 MB)",
+                   "prec": prec_name, "l2": l2_note,
                    "parallelism": f"replicas x{world}"},
         "sr_steps_per_s": round(1e3 / ms_per_step, 4),
         "stage_ms": {k: round(x, 3) for k, x in stage_ms.items()},
@@ -326,6 +336,31 @@ def run_gpu(args):
         "clocks": clk,
     }
     return rank, out
+
+
+def profile_kernels():
+    """Small case of the 20x20 J1-J2 shapes for profiler captures: Metropolis on
+    1216 chains (one CTA per SM) for 16 sweeps, ln psi and local energies on their
+    19,456 samples, one SR step with 2 CG iterations; every stage runs twice."""
+    import torch
+
+    from paper_1904_00031_gb300 import nk
+    from paper_1904_00031_gb300 import workloads as W
+    from paper_1904_00031_gb300.vmc import VmcSr
+    w = W.workload("c5", n_chains=1216, samples_per_chain=16)
+    w.n_discard = 0
+    w.n_cg = 2
+    v = VmcSr(w, W.init_params(w.n, w.m, True, 0.01, w.seed), prec=nk.NK_PREC_BF16X2)
+    for _ in range(2):
+        for name in ("sample", "amplitudes", "energies", "sr"):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            getattr(v, name)()
+            b.record()
+            torch.cuda.synchronize()
+            print(f"{name}: {a.elapsed_time(b):.3f} ms")
+    print("acceptance", v.info()["acceptance"])
 
 
 def run_gpu_batched(args):
@@ -392,6 +427,9 @@ def main():
         spec = json.loads(args.oracle_sample)
         print(json.dumps(oracle_sample(spec["workload"], spec["n_chains"], spec["spc"],
                                        spec["n_cg"])))
+        return
+    if args.profile_kernels:
+        profile_kernels()
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

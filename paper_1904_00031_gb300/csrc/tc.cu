@@ -488,7 +488,8 @@ nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st)
 
 // ------------------------------------------------------------------ adjoint
 
-constexpr int kAdjThreads = 192;
+constexpr int kAdjProducerWarps = 8;
+constexpr int kAdjThreads = 64 + 32 * kAdjProducerWarps;
 
 template <bool CPLX>
 __global__ void __launch_bounds__(kAdjThreads, 1)
@@ -513,7 +514,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
 
   if (tid == 0) {
     for (int k = 0; k < 2; ++k) {
-      mbar_init(&full[k], 1 + 4);
+      mbar_init(&full[k], 1 + kAdjProducerWarps);
       mbar_init(&empty[k], 1);
     }
     mbar_init(done, 1);
@@ -569,12 +570,12 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     }
   } else {
     // producers: Z = conj(T'_sj) v_s as BF16 hi/lo, K-major swizzled A tiles.
-    // Complex: thread (jp, qs) owns parameter rows j0 + 2 jp, j0 + 2 jp + 1 and
-    // samples 16 qs .. 16 qs + 15 of each 64-sample stage, loading both T values
-    // of a sample with one 16-byte load (a warp reads 512 contiguous bytes per
-    // sample); real: thread (jq, qs) owns rows j0 + 4 jq .. + 3 and samples
-    // 16 qs ..  The next stage's T values are loaded into registers before the
-    // thread waits for its buffer; v_s reaches the warp by shuffles.
+    // Complex: thread (jp, qs) of the eight producer warps owns parameter rows
+    // j0 + 2 jp, j0 + 2 jp + 1 and samples 8 qs .. 8 qs + 7 of each 64-sample
+    // stage, loading both T values of a sample with one 16-byte load (a warp
+    // reads 512 contiguous bytes per sample); real: thread (jq, qs) owns rows
+    // j0 + 4 jq .. + 3.  The next stage's T values are loaded into registers
+    // before the thread waits for its buffer; v_s reaches the warp by shuffles.
     const int pt = tid - 64;
     constexpr int JPT = CPLX ? 2 : 4;        // parameter rows per thread
     const int jb = (pt & 31) * JPT;          // first local row
@@ -582,12 +583,13 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     const bool vec = (A.m % JPT) == 0;
     using F = typename std::conditional<CPLX, float2, float>::type;
     const F* T = reinterpret_cast<const F*>(A.T);
-    F tq[16][JPT];
-    float vq0 = 0.f, vq1 = 0.f;  // v of sample (lane & 15) of this thread's quarter
+    constexpr int SPT = 64 / kAdjProducerWarps;  // samples per thread and stage
+    F tq[SPT][JPT];
+    float vq0 = 0.f, vq1 = 0.f;  // v of sample (lane % SPT) of this thread's slice
     auto load_stage = [&](int it) {
-      const int64_t kb = sb + (int64_t)it * 64 + qs * 16;
+      const int64_t kb = sb + (int64_t)it * 64 + qs * SPT;
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
+      for (int e = 0; e < SPT; ++e) {
         const int64_t smp = kb + e;
         const int j = j0 + jb;
         if (vec && smp < se && j + JPT <= A.m) {
@@ -617,7 +619,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
           }
         }
       }
-      const int64_t smp = kb + (lane & 15);
+      const int64_t smp = kb + (lane % SPT);
       if constexpr (CPLX) {
         const double2 vd = smp < se ? reinterpret_cast<const double2*>(A.v)[smp]
                                     : make_double2(0.0, 0.0);
@@ -637,8 +639,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
       unsigned char* Ahi = sm + (size_t)st * stage_bytes;
       unsigned char* Alo = Ahi + 16384;
 #pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const int kl = qs * 16 + cc * 8;
+      for (int cc = 0; cc < SPT / 8; ++cc) {
+        const int kl = qs * SPT + cc * 8;
 #pragma unroll
         for (int u2 = 0; u2 < JPT; ++u2) {
           uint32_t hr[4], lr[4], hi_[4], li[4];
@@ -687,7 +689,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
       if (lane == 0) mbar_arrive(&full[st]);
       if (it + 1 < nit) load_stage(it + 1);
     }
-    // epilogue: partial sums of this split
+    // epilogue (warps 2..5, one per TMEM lane quarter): partial sums of this split
     if (!bad && !mbar_wait_bounded(done, 0u)) bad = true;
     tc_fence_after();
     const int q = w & 3, row = 32 * q + lane;
@@ -695,7 +697,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
     const int comp = CPLX ? (row >> 6) : 0;
     const int ma = A.m + 1, na = A.n + 1;
     float* part = reinterpret_cast<float*>(A.part);
-    for (int col = 0; col < NB; col += 16) {
+    for (int col = 0; col < (w < 6 ? NB : 0); col += 16) {
       float v[16];
       tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
       tmem_ld_wait();
