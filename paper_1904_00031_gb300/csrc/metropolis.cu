@@ -184,27 +184,35 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   uint64_t nacc = 0;
   bool timed_out = false;  // a bounded wait gave up: finish the loop without work
   int nn = 0;              // non-null steps so far (identical in the warps of a chain)
-  int my_idx = 0;
-  double my_u = 0.0;
+  // per lane: the draws of step (block start + lane): proposed sites, accept
+  // uniform and a_i - a_k, fetched once per 32 steps and broadcast by shuffles
+  int my_i = 0, my_k = -1;
+  double my_u = 0.0, my_da = 0.0;
   for (int step = 0; step < total; ++step) {
     const int q32 = step & 31;
-    if (q32 == 0) {  // draws for steps step .. step + 31, one per lane
+    if (q32 == 0) {
       const uint64_t gs = ctr + (uint64_t)(step + lane);
       u4 us = philox_stream(g, gs, kTagSite, A.seed);
-      my_idx = uniform_index(us.x, A.move == NK_MOVE_FLIP ? n : A.nb);
+      const int idx = uniform_index(us.x, A.move == NK_MOVE_FLIP ? n : A.nb);
       u4 ua = philox_stream((uint32_t)c, gs, kTagAccept, A.seed);
       my_u = uniform53(ua.x, ua.y);
+      if (A.move == NK_MOVE_FLIP) {
+        my_i = idx;
+        my_k = -1;
+        my_da = CPLX ? A.a[2 * idx] : A.a[idx];
+      } else {
+        my_i = A.bond_i[idx];
+        my_k = A.bond_k[idx];
+        my_da = CPLX ? A.a[2 * my_i] - A.a[2 * my_k] : A.a[my_i] - A.a[my_k];
+      }
     }
-    const int idx = __shfl_sync(0xffffffffu, my_idx, q32);
+    const int i = __shfl_sync(0xffffffffu, my_i, q32);
+    const int kk2 = __shfl_sync(0xffffffffu, my_k, q32);
     const double U = __shfl_sync(0xffffffffu, my_u, q32);
+    const double da = __shfl_sync(0xffffffffu, my_da, q32);
     const int k = step % kRing;
     const T2* cd = reinterpret_cast<const T2*>(smem + (size_t)k * slot_bytes);
     const F* wdc = reinterpret_cast<const F*>(smem + (size_t)k * slot_bytes + cd_bytes);
-    int i = idx, kk2 = -1;
-    if (A.move != NK_MOVE_FLIP) {
-      i = A.bond_i[idx];
-      kk2 = A.bond_k[idx];
-    }
     const float si = (float)sg[i];
     const bool null_move = (kk2 >= 0) && (sg[kk2] == sg[i]);
     // every warp observes every phase of the slot's barrier, in order, so that
@@ -257,8 +265,8 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
         if (isnan(l2)) timed_out = true;
       }
       ++nn;
-      double vis = -2.0 * (double)si * (CPLX ? A.a[2 * i] : A.a[i]);
-      if (kk2 >= 0) vis += 2.0 * (double)si * (CPLX ? A.a[2 * kk2] : A.a[kk2]);  // s_k = -s_i
+      // visible term -2 s_i a_i (- 2 s_k a_k) = -2 s_i (a_i - a_k), s_k = -s_i
+      const double vis = -2.0 * (double)si * da;
       const float two_re = (CPLX ? 1.f : 2.f) * 0.69314718055994531f * l2 + 2.f * (float)vis;
       if (!timed_out && accept_test(U, two_re)) {
         ++nacc;
