@@ -83,7 +83,7 @@ def run_oracle_subprocess(workload: str, n_chains: int, spc: int, n_cg: int) -> 
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-ORACLE_SAMPLE = {"c5": (16, 2, 50), "c3": (64, 1, 50), "c2": (128, 4, 50), "c1": (16, 63, 120),
+ORACLE_SAMPLE = {"c5": (24, 2, 50), "c3": (64, 1, 50), "c2": (128, 4, 50), "c1": (16, 63, 120),
                  "c4": (64, 4, 50)}
 
 
