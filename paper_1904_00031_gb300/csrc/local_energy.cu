@@ -16,6 +16,8 @@
 
 #include <string.h>
 
+#include <type_traits>
+
 namespace nk {
 
 struct ElocArgs {
@@ -47,51 +49,79 @@ constexpr int kEBM = 64;   // moves per tile
 constexpr int kEBK = 16;   // hidden units per chunk
 constexpr int kETS = kEBS + 1;  // padded row of the t tile (conflict-free transposed stores)
 
+// (cosh c_j, sinh c_j / s_i) of move mv: the two-spin form from the site tables
 template <bool CPLX>
-struct EScaled;
-template <>
-struct EScaled<true> {
-  using S = ScaledComplex;
-};
-template <>
-struct EScaled<false> {
-  using S = ScaledReal;
-};
+__device__ __forceinline__ typename RatioTypes<CPLX>::T2 move_column(const OpMove& M,
+                                                                     const void* tabv, int mp,
+                                                                     int j) {
+  using T2 = typename RatioTypes<CPLX>::T2;
+  const T2* tab = reinterpret_cast<const T2*>(tabv);
+  const T2 ai = tab[(int64_t)M.i * mp + j];
+  if (!M.two) return ai;
+  const T2 ak = tab[(int64_t)M.k * mp + j];
+  const float al = (float)M.align;
+  if constexpr (CPLX) {
+    cf Ai{ai.x, ai.y}, Bi{ai.z, ai.w}, Ak{ak.x, ak.y}, Bk{ak.z, ak.w};
+    cf c = Ai * Ak + al * (Bi * Bk);
+    cf d = Bi * Ak + al * (Ai * Bk);
+    return make_float4(c.x, c.y, d.x, d.y);
+  } else {
+    return make_float2(fmaf(al * ai.y, ak.y, ai.x * ak.x), fmaf(al * ai.x, ak.y, ai.y * ak.x));
+  }
+}
 
-// table[j][mv] = (cosh c_j, sinh c_j / s_i) of move mv
+// Real RBMs: table[j][mv] = (cosh c_j, sinh c_j / s_i) of move mv.
+// Complex RBMs: row j holds, per tile of 64 moves, 32 slots for move pairs
+// (a, b = a + 16) with a = (s mod 16) + 32 (s div 16): first the C plane,
+// slot s = (Re C_a, Re C_b, Im C_a, Im C_b), then the D plane (same for
+// D = sinh c / s_i), so that one 16-byte load gives a thread the operands of
+// two moves as packed FP32 pairs.
 template <bool CPLX>
 __global__ void move_tables_kernel(const char* __restrict__ op, const void* __restrict__ tabv,
                                    int mp, int nm, int nm_pad, void* outv) {
-  using T2 = typename RatioTypes<CPLX>::T2;
   const OpDevHeader* H = reinterpret_cast<const OpDevHeader*>(op);
   const OpMove* mvs = reinterpret_cast<const OpMove*>(op + H->off_moves);
-  const T2* tab = reinterpret_cast<const T2*>(tabv);
-  T2* out = reinterpret_cast<T2*>(outv);
-  const int64_t total = (int64_t)mp * nm_pad;
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(x / nm_pad), mv = (int)(x % nm_pad);
-    if (mv >= nm) {
-      if constexpr (CPLX) out[x] = make_float4(0.f, 0.f, 0.f, 0.f); else out[x] = make_float2(0.f, 0.f);
-      continue;
+  if constexpr (CPLX) {
+    float4* out = reinterpret_cast<float4*>(outv);
+    const int ntile = nm_pad / kEBM;
+    const int64_t total = (int64_t)mp * ntile * 32;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+      const int slot = (int)(x & 31);
+      const int64_t jt = x >> 5;
+      const int j = (int)(jt / ntile), mt = (int)(jt % ntile);
+      const int a = mt * kEBM + (slot & 15) + 32 * (slot >> 4), b = a + 16;
+      const float4 za = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 va = a < nm ? move_column<true>(mvs[a], tabv, mp, j) : za;
+      const float4 vb = b < nm ? move_column<true>(mvs[b], tabv, mp, j) : za;
+      float4* row = out + ((int64_t)j * ntile + mt) * 64;
+      row[slot] = make_float4(va.x, vb.x, va.y, vb.y);
+      row[32 + slot] = make_float4(va.z, vb.z, va.w, vb.w);
     }
-    const OpMove& M = mvs[mv];
-    const T2 ai = tab[(int64_t)M.i * mp + j];
-    if (!M.two) {
-      out[x] = ai;
-      continue;
-    }
-    const T2 ak = tab[(int64_t)M.k * mp + j];
-    const float al = (float)M.align;
-    if constexpr (CPLX) {
-      cf Ai{ai.x, ai.y}, Bi{ai.z, ai.w}, Ak{ak.x, ak.y}, Bk{ak.z, ak.w};
-      cf c = Ai * Ak + al * (Bi * Bk);
-      cf d = Bi * Ak + al * (Ai * Bk);
-      out[x] = make_float4(c.x, c.y, d.x, d.y);
-    } else {
-      out[x] = make_float2(fmaf(al * ai.y, ak.y, ai.x * ak.x), fmaf(al * ai.x, ak.y, ai.y * ak.x));
+  } else {
+    float2* out = reinterpret_cast<float2*>(outv);
+    const int64_t total = (int64_t)mp * nm_pad;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+      const int j = (int)(x / nm_pad), mv = (int)(x % nm_pad);
+      out[x] = mv < nm ? move_column<false>(mvs[mv], tabv, mp, j) : make_float2(0.f, 0.f);
     }
   }
+}
+
+// Packed FP32 pair arithmetic (two independent lanes per instruction).
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// One running product kept as mantissa * 2^e, renormalised from a packed lane.
+__device__ __forceinline__ void renorm_lane(float& x, float& y, int& e) {
+  const float mx = fmaxf(fabsf(x), fabsf(y));
+  int ex = ((__float_as_int(mx) >> 23) & 0xff) - 127;
+  if (mx == 0.f) ex = 0;
+  const float sc = __int_as_float((127 - ex) << 23);
+  x *= sc;
+  y *= sc;
+  e += ex;
 }
 
 template <bool CPLX>
@@ -100,14 +130,17 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   using F = typename RatioTypes<CPLX>::F;
   using T2 = typename RatioTypes<CPLX>::T2;
   extern __shared__ __align__(128) unsigned char smraw[];
+  // t tile entry: real t, or (Re t, Re t, Im t, Im t) as two packed pairs
+  using TS = typename std::conditional<CPLX, float4, float>::type;
   T2* mvt = reinterpret_cast<T2*>(smraw);                                    // [2][BK][BM]
-  F* tS = reinterpret_cast<F*>(smraw + 2 * kEBK * kEBM * sizeof(T2));        // [2][BK][BS+1]
+  TS* tS = reinterpret_cast<TS*>(smraw + 2 * kEBK * kEBM * sizeof(T2));      // [2][BK][BS+1]
   int* mvi = reinterpret_cast<int*>(reinterpret_cast<char*>(tS) +
-                                    round_up(2 * kEBK * kETS * sizeof(F), 16));
+                                    round_up(2 * kEBK * kETS * sizeof(TS), 16));
   int* mvk = mvi + kEBM;
   int* mvtwo = mvk + kEBM;
   double2* cvs = reinterpret_cast<double2*>(mvtwo + kEBM);                   // [BM][4]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(cvs + 4 * kEBM);              // [2]
+  double2* eacc = cvs + 4 * kEBM;  // [4][256] per-thread partial E_loc (kept out of registers)
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(eacc + 4 * 256);              // [2]
 
   const int tid = threadIdx.x, ts = tid >> 4, tm = tid & 15;
   const int64_t s0 = (int64_t)blockIdx.x * kEBS;
@@ -135,18 +168,20 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   for (int p = 0; p < 4; ++p) {
     er[p] = ei[p] = 0.0;
     const int64_t s = s0 + ts * 4 + p;
-    if (s >= A.ns) continue;
-    const int8_t* sg = A.sigma + s * n;
-    for (int u = tm; u < H->n_dsite; u += 16) {
-      int x = idx_of(sg[ds[u].i]);
-      er[p] += ds[u].d[x][0];
-      ei[p] += ds[u].d[x][1];
+    if (s < A.ns) {
+      const int8_t* sg = A.sigma + s * n;
+      for (int u = tm; u < H->n_dsite; u += 16) {
+        int x = idx_of(sg[ds[u].i]);
+        er[p] += ds[u].d[x][0];
+        ei[p] += ds[u].d[x][1];
+      }
+      for (int u = tm; u < H->n_dbond; u += 16) {
+        int x = 2 * idx_of(sg[db[u].i]) + idx_of(sg[db[u].k]);
+        er[p] += db[u].d[x][0];
+        ei[p] += db[u].d[x][1];
+      }
     }
-    for (int u = tm; u < H->n_dbond; u += 16) {
-      int x = 2 * idx_of(sg[db[u].i]) + idx_of(sg[db[u].k]);
-      er[p] += db[u].d[x][0];
-      ei[p] += db[u].d[x][1];
-    }
+    eacc[p * 256 + tid] = make_double2(er[p], ei[p]);
   }
 
   // t tile of a chunk: thread covers (ss, kk) = (e >> 4, e & 15), e = tid + 256 u
@@ -181,7 +216,10 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
         }
         if (tout) tout[s * m + j] = v;
       }
-      tS[(buf * kEBK + kk) * kETS + ss] = v;
+      if constexpr (CPLX)
+        tS[(buf * kEBK + kk) * kETS + ss] = make_float4(v.x, v.x, v.y, v.y);
+      else
+        tS[(buf * kEBK + kk) * kETS + ss] = v;
     }
   };
 
@@ -195,8 +233,13 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
     store_t(0, 0);
   }
 
-  typename EScaled<CPLX>::S P[4][4];
-  float sgn[4][4];
+  // running products: real, P[p][q]; complex, packed over the move pairs
+  // (q = 2 qp, 2 qp + 1): Px/Py[p][qp] = (Re, Im) parts, exponents Pe[p][q]
+  ScaledReal P[4][4];
+  float2 Px[4][2], Py[4][2];
+  int Pe[4][4];
+  float sgn[4][4];      // real: sigma_i of the configuration for each move
+  float2 ns2[4][2];     // complex: -sigma_i packed over the move pairs
   for (int it = 0; it < total; ++it) {
     const int b = it & 1, kc = it % nchunk, mt = it / nchunk, mt0 = mt * kEBM;
     __syncthreads();  // chunk it-1 fully consumed; t tile of chunk it stored
@@ -242,8 +285,21 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
         const int64_t s = s0 + ts * 4 + p;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          sgn[p][q] = (s < A.ns) ? (float)A.sigma[s * n + mvi[tm + 16 * q]] : 1.f;
-          P[p][q].init();
+          const float sv = (s < A.ns) ? (float)A.sigma[s * n + mvi[tm + 16 * q]] : 1.f;
+          if constexpr (CPLX) {
+            Pe[p][q] = 0;
+            if (q & 1) ns2[p][q >> 1].y = -sv; else ns2[p][q >> 1].x = -sv;
+          } else {
+            sgn[p][q] = sv;
+            P[p][q].init();
+          }
+        }
+        if constexpr (CPLX) {
+#pragma unroll
+          for (int qp = 0; qp < 2; ++qp) {
+            Px[p][qp] = make_float2(1.f, 1.f);
+            Py[p][qp] = make_float2(0.f, 0.f);
+          }
         }
       }
     }
@@ -256,35 +312,69 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
     if (it + 1 < total) load_t(it + 1);
     mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1));
     const T2* mv_b = mvt + (size_t)b * kEBK * kEBM;
-    const F* t_b = tS + (size_t)b * kEBK * kETS;
+    const TS* t_b = tS + (size_t)b * kEBK * kETS;
+    if constexpr (CPLX) {
+      // r = C - s t D for two moves at once: with ns = -s,
+      // Re r = Re C + ns (Re t Re D - Im t Im D), Im r = Im C + ns (Re t Im D + Im t Re D),
+      // then P *= r.
+      const float4* mvc = reinterpret_cast<const float4*>(mv_b);
 #pragma unroll
-    for (int kk = 0; kk < kEBK; ++kk) {
-      F t[4];
-      T2 v[4];
+      for (int kk = 0; kk < kEBK; ++kk) {
+        float4 t4[4], c4[2], d4[2];
 #pragma unroll
-      for (int p = 0; p < 4; ++p) t[p] = t_b[kk * kETS + ts * 4 + p];
+        for (int p = 0; p < 4; ++p) t4[p] = t_b[kk * kETS + ts * 4 + p];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = mv_b[kk * kEBM + tm + 16 * q];
+        for (int qp = 0; qp < 2; ++qp) {
+          c4[qp] = mvc[kk * kEBM + tm + 16 * qp];
+          d4[qp] = mvc[kk * kEBM + 32 + tm + 16 * qp];
+        }
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < 4; ++p) {
+          const float2 tx = make_float2(t4[p].x, t4[p].y), ty = make_float2(t4[p].z, t4[p].w);
+          const float2 nty = make_float2(-t4[p].z, -t4[p].w);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if constexpr (CPLX) {
-            const float tdx = fmaf(t[p].x, v[q].z, -t[p].y * v[q].w);
-            const float tdy = fmaf(t[p].x, v[q].w, t[p].y * v[q].z);
-            const float rx = fmaf(-sgn[p][q], tdx, v[q].x);
-            const float ry = fmaf(-sgn[p][q], tdy, v[q].y);
-            P[p][q].v = P[p][q].v * cf{rx, ry};
-          } else {
-            P[p][q].v *= fmaf(-sgn[p][q] * t[p], v[q].y, v[q].x);
+          for (int qp = 0; qp < 2; ++qp) {
+            const float2 cx = make_float2(c4[qp].x, c4[qp].y), cy = make_float2(c4[qp].z, c4[qp].w);
+            const float2 dx = make_float2(d4[qp].x, d4[qp].y), dy = make_float2(d4[qp].z, d4[qp].w);
+            const float2 tdx = f2fma(tx, dx, f2mul(nty, dy));
+            const float2 tdy = f2fma(tx, dy, f2mul(ty, dx));
+            const float2 rx = f2fma(ns2[p][qp], tdx, cx);
+            const float2 ry = f2fma(ns2[p][qp], tdy, cy);
+            const float2 nry = f2mul(ry, make_float2(-1.f, -1.f));
+            const float2 px = Px[p][qp], py = Py[p][qp];
+            Px[p][qp] = f2fma(py, nry, f2mul(px, rx));
+            Py[p][qp] = f2fma(py, rx, f2mul(px, ry));
           }
         }
+        if ((kk & 7) == 7) {
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int qp = 0; qp < 2; ++qp) {
+              renorm_lane(Px[p][qp].x, Py[p][qp].x, Pe[p][2 * qp]);
+              renorm_lane(Px[p][qp].y, Py[p][qp].y, Pe[p][2 * qp + 1]);
+            }
+        }
       }
-      if ((kk & 7) == 7) {
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < kEBK; ++kk) {
+        F t[4];
+        T2 v[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) t[p] = t_b[kk * kETS + ts * 4 + p];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = mv_b[kk * kEBM + tm + 16 * q];
 #pragma unroll
         for (int p = 0; p < 4; ++p)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) P[p][q].renorm();
+          for (int q = 0; q < 4; ++q) P[p][q].v *= fmaf(-sgn[p][q] * t[p], v[q].y, v[q].x);
+        if ((kk & 7) == 7) {
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) P[p][q].renorm();
+        }
       }
     }
     if (it + 1 < total) store_t(it + 1, b ^ 1);
@@ -294,6 +384,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
       for (int p = 0; p < 4; ++p) {
         const int64_t s = s0 + ts * 4 + p;
         if (s >= A.ns) continue;
+        double2 acc = eacc[p * 256 + tid];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int mm = tm + 16 * q;
@@ -303,21 +394,25 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
           if (cv.x == 0.0 && cv.y == 0.0) continue;
           double pr, pi;
           if constexpr (CPLX) {
-            pr = ldexp((double)P[p][q].v.x, P[p][q].e);
-            pi = ldexp((double)P[p][q].v.y, P[p][q].e);
+            const float2 px = Px[p][q >> 1], py = Py[p][q >> 1];
+            pr = ldexp((double)((q & 1) ? px.y : px.x), Pe[p][q]);
+            pi = ldexp((double)((q & 1) ? py.y : py.x), Pe[p][q]);
           } else {
             pr = ldexp((double)P[p][q].v, P[p][q].e);
             pi = 0.0;
           }
-          er[p] += cv.x * pr - cv.y * pi;
-          ei[p] += cv.x * pi + cv.y * pr;
+          acc.x += cv.x * pr - cv.y * pi;
+          acc.y += cv.x * pi + cv.y * pr;
         }
+        eacc[p * 256 + tid] = acc;
       }
     }
   }
   // the 16 threads of a configuration are lanes tid ^ 1, 2, 4, 8 of one warp
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
+    er[p] = eacc[p * 256 + tid].x;
+    ei[p] = eacc[p * 256 + tid].y;
 #pragma unroll
     for (int off = 8; off >= 1; off >>= 1) {
       er[p] += __shfl_xor_sync(0xffffffffu, er[p], off);
@@ -376,7 +471,7 @@ nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
   CUtensorMap map;
   memset(&map, 0, sizeof(map));
   if (n_moves > 0) {
-    const int64_t tot = (int64_t)L.mp * nm_pad;
+    const int64_t tot = (int64_t)L.mp * nm_pad / (cplx ? 2 : 1);  // complex: a move pair per thread
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 8));
     if (cplx)
       move_tables_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(A.op, A.tab, L.mp, n_moves,
@@ -390,9 +485,9 @@ nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
                       kEBM * fl, kEBK))
       return NK_ERR_CUDA;
   }
-  const size_t t2 = cplx ? 16 : 8, f = cplx ? 8 : 4;
+  const size_t t2 = cplx ? 16 : 8, f = cplx ? 16 : 4;  // table entry, t tile entry
   const size_t smem = 2 * kEBK * kEBM * t2 + round_up(2 * kEBK * kETS * f, 16) + 3 * kEBM * 4 +
-                      kEBM * 4 * 16 + 16;
+                      kEBM * 4 * 16 + 4 * 256 * 16 + 16;
   const int64_t blocks = (ns + kEBS - 1) / kEBS;
   if (cplx) {
     if (cudaFuncSetAttribute(local_energy_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

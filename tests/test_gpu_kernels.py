@@ -96,6 +96,8 @@ OPS = {
     "heis": (lambda: W.heisenberg(16, W.chain_bonds(16), 1.0, True, W.sublattice(16)), 16, True),
     "j1j2": (lambda: W.j1j2(4, 1.0, 0.5, True), 16, True),
     "tfim2d": (lambda: W.ising(36, W.square_bonds(6), h=3.04), 36, False),
+    # 72 exchange moves: two move tiles, the second ragged
+    "j1j2_6x6": (lambda: W.j1j2(6, 1.0, 0.5, True), 36, True),
 }
 
 
