@@ -149,7 +149,9 @@ nk_status nk_rbm_logpsi(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int3
 
 /* ---------------------------------------------------------------- sampling */
 
-/* Scratch bytes nk_metropolis_sweep needs (0 for flips: NULL scratch is fine). */
+/* Scratch bytes nk_metropolis_sweep needs: per-bond tables of exchange moves;
+ * for complex RBMs also per-site tables of flips.  0 for flips of a real RBM
+ * (NULL scratch is then fine). */
 size_t nk_metropolis_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int32_t move,
                                    int32_t n_bonds);
 
@@ -168,7 +170,8 @@ size_t nk_metropolis_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int
  *                   UINT64_MAX marks a chain whose CTA gave up waiting for a
  *                   table copy (bounded wait; the call's results are then invalid)
  *   scratch         nk_metropolis_scratch_bytes(...) bytes, 256-B aligned
- *                   (per-bond tables of exchange moves); may be NULL for FLIP
+ *                   (move tables built at the start of the call); may be NULL
+ *                   when that size is 0
  * chains->sigma is updated in place and chains->counter advanced by
  * (n_discard + n_samples_per_chain) * n on success. */
 nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move,

@@ -220,8 +220,9 @@ nk_status nk_rbm_logpsi(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int3
 
 size_t nk_metropolis_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int32_t move,
                                    int32_t n_bonds) {
-  if (n < 1 || m < 1 || n_bonds < 0 || move != NK_MOVE_EXCHANGE) return 0;
-  return metropolis_scratch_bytes(n, m, is_complex ? 1 : 0, n_bonds);
+  if (n < 1 || m < 1 || n_bonds < 0 || (move != NK_MOVE_EXCHANGE && move != NK_MOVE_FLIP))
+    return 0;
+  return metropolis_scratch_bytes(n, m, is_complex ? 1 : 0, move, n_bonds);
 }
 
 nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move,

@@ -27,7 +27,7 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
                             const int32_t* bk, int nb, int n_discard, int n_samples,
                             int8_t* samples, uint64_t* n_acc, void* scratch, size_t scratch_bytes,
                             cudaStream_t st);
-size_t metropolis_scratch_bytes(int n, int m, int cplx, int nb);
+size_t metropolis_scratch_bytes(int n, int m, int cplx, int move, int nb);
 
 nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
                               const int8_t* sigma, const void* theta, int64_t ns, double* eloc,

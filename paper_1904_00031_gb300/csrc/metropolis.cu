@@ -3,21 +3,25 @@
 //
 // One or two warps run one chain; a CTA runs one proposal group, whose chains
 // all propose the same site (bond) at a step.  Per proposal the ratio needs, for
-// every hidden unit j, the column (cosh c_j, sinh c_j / s_i) of the move and,
-// on acceptance, its theta increment W_i (- W_k): flips read them from the
-// site tables of the RBM workspace, exchanges from per-bond tables built at
-// the start of the call in the caller's scratch.  One thread streams each
+// every hidden unit j, the table column (cosh c_j, sinh c_j / s_i) of the move
+// and, on acceptance, its theta increment W_i (- W_k).  One thread streams each
 // step's columns into shared memory with 1-D TMA bulk copies through a
-// three-slot ring, issued two steps ahead, so the warps read every table value
-// from shared memory once per chain.
+// three-slot ring, so the warps read every table value from shared memory once
+// per chain.
 //
 // Per chain: sigma and theta live in shared memory, t = tanh(theta) in
-// registers.  A proposal costs per hidden unit
-// r_j = cosh c_j - s_i t_j (sinh c_j / s_i), |r_j|^2 and a running product
-// (mantissa * 2^e).  An accepted move updates theta += -2 s_i W_i (- 2 s_k W_k)
-// and t by the tanh addition formula t' = (t cosh c - sinh c) / r; t is
-// recomputed exactly from theta after every sweep.  Philox draws are made 32
-// steps at a time, one step per lane, and broadcast by shuffles.
+// registers.  With C = cosh c, D = sinh c / s_i, the factor of hidden unit j is
+// r_j = C_j - s_i t_j D_j.  Real RBMs read (C, D) and multiply r_j.  Complex RBMs
+// need only |r_j|^2 for the accept test and read, per unit, the expanded form
+//   |r|^2 = |C|^2 + |t|^2 |D|^2 - 2 s_i Re(t conj(C) D),
+// from per-call tables (|C|^2, |D|^2, conj(C) D) laid out so that one 16-byte
+// load gives a thread two of its units, evaluated with packed FP32 pair
+// instructions.  An accepted move updates theta += -2 s_i W_i (- 2 s_k W_k) and
+// t by the tanh addition formula t' = (t C - s_i D) / r, for complex RBMs from
+// the same tables: t' = (t |C|^2 + conj(t) |D|^2 - s_i (|t|^2 conj(E) + E)) / |r|^2
+// with E = conj(C) D.  t is recomputed exactly from theta after every sweep.
+// Philox draws are made 32 steps at a time, one step per lane, and broadcast by
+// shuffles.
 #include "common.cuh"
 #include "internal.h"
 #include "ratio.cuh"
@@ -35,7 +39,8 @@ struct MetroArgs {
   int8_t* samples;      // [nc * n_samples][n]
   uint64_t* n_acc;      // [nc] or null
   const double* a;      // master a (F64)
-  const void* cd;       // [rows][mp] T2: (cosh c, sinh c / s_i) per site (flip) or bond
+  const void* cd;       // real: [rows][mp] T2 (cosh c, sinh c / s_i) per site (flip) or bond;
+                        // complex: [rows] pair rows of cplx_row_bytes(NU, WPC)
   const void* wd;       // [rows][mp] F : W_i (flip) or W_i - W_k (bond)
   const void* wt;       // [n][mp] F    : W transposed (initial theta)
   const void* b32;      // [mp] F
@@ -68,18 +73,35 @@ __device__ __forceinline__ int move_row(const MetroArgs& A, uint64_t ctr, uint32
 // uneven work of accepted, rejected and null proposals.
 constexpr int kRing = 3;
 
+// Complex tables: a thread (half h, lane l) owns units j = 32 (h + WPC q) + l,
+// q < NU, taken in pairs (2 qp, 2 qp + 1).  A row holds one 1024-byte block per
+// (qp, h), in the order qp * WPC + h: 32 float4 (|C|^2 of the pair, |D|^2 of
+// the pair), then 32 float4 (Re E of the pair, -Im E of the pair), E = conj(C) D.
+// Units beyond m hold C = 1, D = 0 (a factor of exactly 1).
+__host__ __device__ constexpr size_t cplx_row_bytes(int nu, int wpc) {
+  return (size_t)512 * nu * wpc;
+}
+
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
 __device__ __forceinline__ void pair_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <bool CPLX, int E, int WPC>
+// NU hidden units per thread (even for complex RBMs), WPC warps per chain.
+template <bool CPLX, int NU, int WPC>
 __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   using F = typename RatioTypes<CPLX>::F;
   using T2 = typename RatioTypes<CPLX>::T2;
+  constexpr int E = NU;
+  constexpr int EP = (NU + 1) / 2;
   extern __shared__ __align__(128) unsigned char smem[];
   const int mp = A.mp, n = A.n, G = A.G;
-  const size_t slot_bytes = (size_t)mp * (sizeof(T2) + sizeof(F));
-  // ring slot k: CD [mp] T2, then WD [mp] F
+  const size_t cd_row = CPLX ? cplx_row_bytes(NU, WPC) : (size_t)mp * sizeof(T2);
+  const size_t slot_bytes = cd_row + (size_t)mp * sizeof(F);
+  // ring slot k: the move's table row (cd_row bytes), then WD [mp] F
   F* thall = reinterpret_cast<F*>(smem + kRing * slot_bytes);                       // [G][mp]
   float* part = reinterpret_cast<float*>(reinterpret_cast<char*>(thall) +
                                          (size_t)G * mp * sizeof(F));               // [2][G][WPC]
@@ -97,7 +119,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   const uint32_t g = (uint32_t)blockIdx.x;
   F* th = thall + (size_t)(active ? cw : 0) * mp;
   int8_t* sg = sgall + (size_t)(active ? w : 0) * n16;  // one copy per warp
-  const T2* cdg = reinterpret_cast<const T2*>(A.cd);
+  const unsigned char* cdg = reinterpret_cast<const unsigned char*>(A.cd);
   const F* wdg = reinterpret_cast<const F*>(A.wd);
   const F* wt = reinterpret_cast<const F*>(A.wt);
   const F* b32 = reinterpret_cast<const F*>(A.b32);
@@ -115,7 +137,22 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   __syncthreads();
 
   // theta = W sigma + b: rows of W^T staged through the (not yet used) ring
-  F t[E];
+  float t[CPLX ? 1 : E];             // real: t of unit q
+  float2 tx[CPLX ? EP : 1], ty[CPLX ? EP : 1];  // complex: Re t, Im t of units (2 qp, 2 qp + 1)
+  auto set_t = [&](int q, F x, bool valid) {
+    if constexpr (CPLX) {
+      cf tt = valid ? tanh_c(cf{x.x, x.y}) : cf{0.f, 0.f};
+      if (q & 1) {
+        tx[q >> 1].y = tt.x;
+        ty[q >> 1].y = tt.y;
+      } else {
+        tx[q >> 1].x = tt.x;
+        ty[q >> 1].x = tt.y;
+      }
+    } else {
+      t[q] = valid ? tanh_f(x) : 0.f;
+    }
+  };
   {
     F* stg = reinterpret_cast<F*>(smem);
     const int KC = (int)((kRing * slot_bytes) / ((size_t)mp * sizeof(F)));
@@ -150,29 +187,22 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     }
 #pragma unroll
     for (int q = 0; q < E; ++q) {
-      if constexpr (CPLX) t[q] = make_float2(0.f, 0.f); else t[q] = 0.f;
-      if (jof(q) < mp) {
-        if (active) th[jof(q)] = acc[q];
-        if constexpr (CPLX) {
-          cf tt = tanh_c(cf{acc[q].x, acc[q].y});
-          t[q] = make_float2(tt.x, tt.y);
-        } else {
-          t[q] = tanh_f(acc[q]);
-        }
-      }
+      const bool valid = jof(q) < mp;
+      if (valid && active) th[jof(q)] = acc[q];
+      set_t(q, acc[q], valid);
     }
   }
   __syncthreads();
   if (!active) return;  // no CTA-wide barrier from here on
 
   const int total = (A.n_discard + A.n_samples) * n;
-  const uint32_t cd_bytes = (uint32_t)(mp * sizeof(T2)), wd_bytes = (uint32_t)(mp * sizeof(F));
+  const uint32_t cd_bytes = (uint32_t)cd_row, wd_bytes = (uint32_t)(mp * sizeof(F));
   auto issue = [&](int step) {
     const int k = step % kRing;
     const int row = move_row(A, ctr, g, step);
     unsigned char* sl = smem + (size_t)k * slot_bytes;
     mbar_arrive_expect_tx(&full[k], cd_bytes + wd_bytes);
-    bulk_g2s(sl, cdg + (int64_t)row * mp, cd_bytes, &full[k]);
+    bulk_g2s(sl, cdg + (int64_t)row * cd_row, cd_bytes, &full[k]);
     bulk_g2s(sl + cd_bytes, wdg + (int64_t)row * mp, wd_bytes, &full[k]);
   };
   const bool producer = (tid == 0);
@@ -224,6 +254,29 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     if (!null_move) {
       float l2 = 0.f;
       if (!timed_out) {
+        if constexpr (CPLX) {
+          // four packed running products of |r|^2; with at most 16 pairs each
+          // lane collects at most 4 factors, so no renormalisation is needed
+          // for factors in (2^-31, 2^31)
+          const float4* row4 = reinterpret_cast<const float4*>(smem + (size_t)k * slot_bytes);
+          const float2 m2s = make_float2(-2.f * si, -2.f * si);
+          float2 Pp[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) Pp[u] = make_float2(1.f, 1.f);
+#pragma unroll
+          for (int qp = 0; qp < EP; ++qp) {
+            const float4 q0 = row4[(qp * WPC + h) * 64 + lane];
+            const float4 q1 = row4[(qp * WPC + h) * 64 + 32 + lane];
+            const float2 c2 = make_float2(q0.x, q0.y), d2 = make_float2(q0.z, q0.w);
+            const float2 ex = make_float2(q1.x, q1.y), ney = make_float2(q1.z, q1.w);
+            const float2 tt = f2fma(tx[qp], tx[qp], f2mul(ty[qp], ty[qp]));
+            const float2 e = f2fma(tx[qp], ex, f2mul(ty[qp], ney));  // Re(t E)
+            Pp[qp & 3] = f2mul(Pp[qp & 3], f2fma(m2s, e, f2fma(tt, d2, c2)));
+          }
+          l2 = 0.f;
+#pragma unroll
+          for (int u = 0; u < (EP < 4 ? EP : 4); ++u) l2 += __log2f(Pp[u].x) + __log2f(Pp[u].y);
+        } else {
         // four independent running products, renormalised every 8 factors each
         ScaledReal P[4];
 #pragma unroll
@@ -232,15 +285,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
         for (int q = 0; q < E; ++q) {
           if (jof(q) < mp) {
             const T2 v = cd[jof(q)];
-            if constexpr (CPLX) {
-              const float tdx = fmaf(t[q].x, v.z, -t[q].y * v.w);
-              const float tdy = fmaf(t[q].x, v.w, t[q].y * v.z);
-              const float rx = fmaf(-si, tdx, v.x);
-              const float ry = fmaf(-si, tdy, v.y);
-              P[q & 3].v *= fmaf(rx, rx, ry * ry);
-            } else {
-              P[q & 3].v *= fmaf(-si * t[q], v.y, v.x);
-            }
+            P[q & 3].v *= fmaf(-si * t[q], v.y, v.x);
           }
           if ((q & 31) == 31) {
 #pragma unroll
@@ -248,6 +293,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
           }
         }
         l2 = P[0].log2v() + P[1].log2v() + P[2].log2v() + P[3].log2v();
+        }
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, off);
       }
@@ -270,31 +316,51 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
       const float two_re = (CPLX ? 1.f : 2.f) * 0.69314718055994531f * l2 + 2.f * (float)vis;
       if (!timed_out && accept_test(U, two_re)) {
         ++nacc;
+        if constexpr (CPLX) {
+          const float4* row4 = reinterpret_cast<const float4*>(smem + (size_t)k * slot_bytes);
+          const float2 m2s = make_float2(-2.f * si, -2.f * si);
+          const float2 ns2 = make_float2(-si, -si), s2 = make_float2(si, si);
+          const float2 one = make_float2(1.f, 1.f), mone = make_float2(-1.f, -1.f);
 #pragma unroll
-        for (int q = 0; q < E; ++q) {
-          const int j = jof(q);
-          if (j < mp) {
-            const T2 v = cd[j];
-            F x = th[j];
-            const F dw = wdc[j];
-            if constexpr (CPLX) {
-              // t' = (t C - s_i D) / (C - s_i t D)
-              const float tdx = fmaf(t[q].x, v.z, -t[q].y * v.w);
-              const float tdy = fmaf(t[q].x, v.w, t[q].y * v.z);
-              const float rx = fmaf(-si, tdx, v.x);
-              const float ry = fmaf(-si, tdy, v.y);
-              const float nx = fmaf(-si, v.z, fmaf(t[q].x, v.x, -t[q].y * v.y));
-              const float ny = fmaf(-si, v.w, fmaf(t[q].x, v.y, t[q].y * v.x));
-              const float inv = __fdividef(1.f, fmaf(rx, rx, ry * ry));
-              t[q] = make_float2(fmaf(nx, rx, ny * ry) * inv, fmaf(ny, rx, -nx * ry) * inv);
+          for (int qp = 0; qp < EP; ++qp) {
+            const float4 q0 = row4[(qp * WPC + h) * 64 + lane];
+            const float4 q1 = row4[(qp * WPC + h) * 64 + 32 + lane];
+            const float2 c2 = make_float2(q0.x, q0.y), d2 = make_float2(q0.z, q0.w);
+            const float2 ex = make_float2(q1.x, q1.y), ney = make_float2(q1.z, q1.w);
+            const float2 tt = f2fma(tx[qp], tx[qp], f2mul(ty[qp], ty[qp]));
+            const float2 e = f2fma(tx[qp], ex, f2mul(ty[qp], ney));
+            const float2 r2 = f2fma(m2s, e, f2fma(tt, d2, c2));
+            const float2 inv = make_float2(__fdividef(1.f, r2.x), __fdividef(1.f, r2.y));
+            // Re: t_x (|C|^2 + |D|^2) - s Re E (|t|^2 + 1)
+            // Im: t_y (|C|^2 - |D|^2) - s Im E (1 - |t|^2)
+            const float2 nx = f2fma(ns2, f2mul(ex, f2add(tt, one)), f2mul(tx[qp], f2add(c2, d2)));
+            const float2 ny = f2fma(s2, f2mul(ney, f2fma(tt, mone, one)),
+                                    f2mul(ty[qp], f2fma(d2, mone, c2)));
+            tx[qp] = f2mul(nx, inv);
+            ty[qp] = f2mul(ny, inv);
+          }
+#pragma unroll
+          for (int q = 0; q < E; ++q) {
+            const int j = jof(q);
+            if (j < mp) {
+              F x = th[j];
+              const F dw = wdc[j];
               x.x = fmaf(-2.f * si, dw.x, x.x);
               x.y = fmaf(-2.f * si, dw.y, x.y);
-            } else {
+              th[j] = x;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < E; ++q) {
+            const int j = jof(q);
+            if (j < mp) {
+              const T2 v = cd[j];
+              const F dw = wdc[j];
               const float r = fmaf(-si * t[q], v.y, v.x);
               t[q] = __fdividef(fmaf(t[q], v.x, -si * v.y), r);
-              x = fmaf(-2.f * si, dw, x);
+              th[j] = fmaf(-2.f * si, dw, th[j]);
             }
-            th[j] = x;
           }
         }
         __syncwarp();
@@ -332,17 +398,8 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
       }
       // exact refresh of t from theta (this thread's own entries)
 #pragma unroll
-      for (int q = 0; q < E; ++q) {
-        if (jof(q) < mp) {
-          const F x = th[jof(q)];
-          if constexpr (CPLX) {
-            cf tt = tanh_c(cf{x.x, x.y});
-            t[q] = make_float2(tt.x, tt.y);
-          } else {
-            t[q] = tanh_f(x);
-          }
-        }
-      }
+      for (int q = 0; q < E; ++q)
+        if (jof(q) < mp) set_t(q, th[jof(q)], true);
     }
   }
   if (timed_out && producer) {
@@ -355,51 +412,116 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   }
 }
 
-// Per-bond tables of an exchange move (s_k = -s_i): cosh c = A_i A_k - B_i B_k,
-// sinh c / s_i = B_i A_k - A_i B_k, increment W_i - W_k.
-template <bool CPLX>
-__global__ void pair_tables_kernel(const void* __restrict__ tabv, const void* __restrict__ wtv,
-                                   const int32_t* __restrict__ bi, const int32_t* __restrict__ bk,
-                                   int nb, int mp, void* cdv, void* wdv) {
-  using F = typename RatioTypes<CPLX>::F;
-  using T2 = typename RatioTypes<CPLX>::T2;
-  const T2* tab = reinterpret_cast<const T2*>(tabv);
-  const F* wt = reinterpret_cast<const F*>(wtv);
-  T2* cd = reinterpret_cast<T2*>(cdv);
-  F* wd = reinterpret_cast<F*>(wdv);
+// Per-bond tables of an exchange move of a real RBM (s_k = -s_i):
+// cosh c = A_i A_k - B_i B_k, sinh c / s_i = B_i A_k - A_i B_k, increment W_i - W_k.
+__global__ void pair_tables_real_kernel(const float2* __restrict__ tab, const float* __restrict__ wt,
+                                        const int32_t* __restrict__ bi,
+                                        const int32_t* __restrict__ bk, int nb, int mp,
+                                        float2* __restrict__ cd, float* __restrict__ wd) {
   const int64_t total = (int64_t)nb * mp;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
        x += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(x / mp), j = (int)(x % mp);
     const int i = bi[b], k = bk[b];
-    const T2 ti = tab[(int64_t)i * mp + j], tk = tab[(int64_t)k * mp + j];
-    const F wi = wt[(int64_t)i * mp + j], wk = wt[(int64_t)k * mp + j];
-    if constexpr (CPLX) {
-      cf Ai{ti.x, ti.y}, Bi{ti.z, ti.w}, Ak{tk.x, tk.y}, Bk{tk.z, tk.w};
-      cf C = Ai * Ak - Bi * Bk, D = Bi * Ak - Ai * Bk;
-      cd[x] = make_float4(C.x, C.y, D.x, D.y);
-      wd[x] = make_float2(wi.x - wk.x, wi.y - wk.y);
-    } else {
-      cd[x] = make_float2(fmaf(-ti.y, tk.y, ti.x * tk.x), fmaf(-ti.x, tk.y, ti.y * tk.x));
-      wd[x] = wi - wk;
+    const float2 ti = tab[(int64_t)i * mp + j], tk = tab[(int64_t)k * mp + j];
+    cd[x] = make_float2(fmaf(-ti.y, tk.y, ti.x * tk.x), fmaf(-ti.x, tk.y, ti.y * tk.x));
+    wd[x] = wt[(int64_t)i * mp + j] - wt[(int64_t)k * mp + j];
+  }
+}
+
+// Pair rows of a complex RBM (layout of cplx_row_bytes): one per site (flips,
+// C = A_i, D = B_i) or per bond (exchanges, s_k = -s_i: C = A_i A_k - B_i B_k,
+// D = B_i A_k - A_i B_k, and the increments W_i - W_k into wd).
+template <bool PAIR>
+__global__ void cplx_rows_kernel(const float4* __restrict__ tab, const float2* __restrict__ wt,
+                                 const int32_t* __restrict__ bi, const int32_t* __restrict__ bk,
+                                 int rows, int mp, int nu, int wpc, float4* __restrict__ qout,
+                                 float2* __restrict__ wd) {
+  const int nblk = (nu / 2) * wpc;
+  const int64_t total = (int64_t)rows * nblk * 32;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = (int)(x & 31);
+    const int64_t rb = x >> 5;
+    const int blk = (int)(rb % nblk), r = (int)(rb / nblk);
+    const int qp = blk / wpc, h = blk % wpc;
+    float v[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int j = 32 * (h + wpc * (2 * qp + u)) + lane;
+      cf C{1.f, 0.f}, D{0.f, 0.f};
+      if (j < mp) {
+        const int i = PAIR ? bi[r] : r;
+        const float4 ti = tab[(int64_t)i * mp + j];
+        const cf Ai{ti.x, ti.y}, Bi{ti.z, ti.w};
+        if (PAIR) {
+          const int k = bk[r];
+          const float4 tk = tab[(int64_t)k * mp + j];
+          const cf Ak{tk.x, tk.y}, Bk{tk.z, tk.w};
+          C = Ai * Ak - Bi * Bk;
+          D = Bi * Ak - Ai * Bk;
+          const float2 wi = wt[(int64_t)i * mp + j], wk = wt[(int64_t)k * mp + j];
+          wd[(int64_t)r * mp + j] = make_float2(wi.x - wk.x, wi.y - wk.y);
+        } else {
+          C = Ai;
+          D = Bi;
+        }
+      }
+      const cf E = conj(C) * D;
+      v[u][0] = fmaf(C.x, C.x, C.y * C.y);
+      v[u][1] = fmaf(D.x, D.x, D.y * D.y);
+      v[u][2] = E.x;
+      v[u][3] = -E.y;
     }
+    float4* row = qout + rb * 64;
+    row[lane] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+    row[32 + lane] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
   }
 }
 
 __global__ void advance_counter_kernel(uint64_t* ctr, uint64_t delta) { *ctr += delta; }
 
-size_t metropolis_scratch_bytes(int n, int m, int cplx, int nb) {
-  (void)n;
-  const int mp = padded_m(m);
-  const size_t f = cplx ? 8 : 4;
-  return (size_t)round_up((int64_t)nb * mp * 2 * f, 256) + (size_t)round_up((int64_t)nb * mp * f, 256);
-}
-
 // ------------------------------------------------------------------ dispatch
 
-template <bool CPLX, int E, int WPC>
+// Hidden units per thread NU for WPC warps per chain: the smallest instantiated
+// size >= mp / (32 WPC); complex RBMs need an even NU.  0 if m is too large.
+static int metro_nu(int mp, int cplx, int wpc) {
+  const int e = (mp + 32 * wpc - 1) / (32 * wpc);
+  static const int real1[] = {1, 2, 4, 8, 16, 32, 64}, real2[] = {8, 13, 16, 25, 32};
+  static const int cplx1[] = {2, 4, 8, 16, 32, 64}, cplx2[] = {8, 14, 16, 26, 32};
+  const int* L = cplx ? (wpc == 1 ? cplx1 : cplx2) : (wpc == 1 ? real1 : real2);
+  const int nl = cplx ? (wpc == 1 ? 6 : 5) : (wpc == 1 ? 7 : 5);
+  for (int x = 0; x < nl; ++x)
+    if (L[x] >= e) return L[x];
+  return 0;
+}
+
+// two warps per chain from mp = 512 on, when the group fits in 512 threads
+static int metro_wpc(int mp, int G) { return (mp >= 512 && G * 64 <= 512) ? 2 : 1; }
+
+size_t metropolis_scratch_bytes(int n, int m, int cplx, int move, int nb) {
+  const int mp = padded_m(m);
+  const size_t f = cplx ? 8 : 4;
+  if (!cplx) {
+    if (move == NK_MOVE_FLIP) return 0;
+    return (size_t)round_up((int64_t)nb * mp * 2 * f, 256) + (size_t)round_up((int64_t)nb * mp * f, 256);
+  }
+  // the row layout depends on the warps per chain (group size): take the larger
+  size_t row = 0;
+  for (int wpc = 1; wpc <= 2; ++wpc) {
+    if (wpc == 2 && mp < 512) continue;
+    const int nu = metro_nu(mp, 1, wpc);
+    if (nu) row = std::max(row, cplx_row_bytes(nu, wpc));
+  }
+  const int64_t rows = move == NK_MOVE_FLIP ? n : nb;
+  size_t bytes = (size_t)round_up((int64_t)(rows * row), 256);
+  if (move != NK_MOVE_FLIP) bytes += (size_t)round_up((int64_t)nb * mp * f, 256);
+  return bytes;
+}
+
+template <bool CPLX, int NU, int WPC>
 static nk_status launch_e(const MetroArgs& A, size_t smem, cudaStream_t st) {
-  auto kern = metropolis_kernel<CPLX, E, WPC>;
+  auto kern = metropolis_kernel<CPLX, NU, WPC>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return fail(NK_ERR_CUDA, "nk_metropolis_sweep: cannot reserve %zu B shared memory", smem);
@@ -408,27 +530,47 @@ static nk_status launch_e(const MetroArgs& A, size_t smem, cudaStream_t st) {
   return check_launch("nk_metropolis_sweep");
 }
 
-// hidden units per thread E = mp / (32 WPC), rounded up to an instantiated size;
-// two warps per chain from mp = 512 on
 template <bool CPLX>
-static nk_status launch_c(const MetroArgs& A, size_t smem1, size_t smem2, cudaStream_t st) {
-  const int mp = A.mp;
-  if (mp < 512 || A.G * 64 > 512) {
-    const int e = mp / 32;
-    if (e <= 1) return launch_e<CPLX, 1, 1>(A, smem1, st);
-    if (e <= 2) return launch_e<CPLX, 2, 1>(A, smem1, st);
-    if (e <= 4) return launch_e<CPLX, 4, 1>(A, smem1, st);
-    if (e <= 8) return launch_e<CPLX, 8, 1>(A, smem1, st);
-    if (e <= 16) return launch_e<CPLX, 16, 1>(A, smem1, st);
-    if (e <= 32) return launch_e<CPLX, 32, 1>(A, smem1, st);
-    if (e <= 64) return launch_e<CPLX, 64, 1>(A, smem1, st);
+static nk_status launch_c(const MetroArgs& A, int nu, int wpc, size_t smem, cudaStream_t st) {
+  if (wpc == 1) {
+    if constexpr (CPLX) {
+      switch (nu) {
+        case 2: return launch_e<true, 2, 1>(A, smem, st);
+        case 4: return launch_e<true, 4, 1>(A, smem, st);
+        case 8: return launch_e<true, 8, 1>(A, smem, st);
+        case 16: return launch_e<true, 16, 1>(A, smem, st);
+        case 32: return launch_e<true, 32, 1>(A, smem, st);
+        case 64: return launch_e<true, 64, 1>(A, smem, st);
+      }
+    } else {
+      switch (nu) {
+        case 1: return launch_e<false, 1, 1>(A, smem, st);
+        case 2: return launch_e<false, 2, 1>(A, smem, st);
+        case 4: return launch_e<false, 4, 1>(A, smem, st);
+        case 8: return launch_e<false, 8, 1>(A, smem, st);
+        case 16: return launch_e<false, 16, 1>(A, smem, st);
+        case 32: return launch_e<false, 32, 1>(A, smem, st);
+        case 64: return launch_e<false, 64, 1>(A, smem, st);
+      }
+    }
   } else {
-    const int e = (mp + 63) / 64;
-    if (e <= 8) return launch_e<CPLX, 8, 2>(A, smem2, st);
-    if (e <= 13) return launch_e<CPLX, 13, 2>(A, smem2, st);
-    if (e <= 16) return launch_e<CPLX, 16, 2>(A, smem2, st);
-    if (e <= 25) return launch_e<CPLX, 25, 2>(A, smem2, st);
-    if (e <= 32) return launch_e<CPLX, 32, 2>(A, smem2, st);
+    if constexpr (CPLX) {
+      switch (nu) {
+        case 8: return launch_e<true, 8, 2>(A, smem, st);
+        case 14: return launch_e<true, 14, 2>(A, smem, st);
+        case 16: return launch_e<true, 16, 2>(A, smem, st);
+        case 26: return launch_e<true, 26, 2>(A, smem, st);
+        case 32: return launch_e<true, 32, 2>(A, smem, st);
+      }
+    } else {
+      switch (nu) {
+        case 8: return launch_e<false, 8, 2>(A, smem, st);
+        case 13: return launch_e<false, 13, 2>(A, smem, st);
+        case 16: return launch_e<false, 16, 2>(A, smem, st);
+        case 25: return launch_e<false, 25, 2>(A, smem, st);
+        case 32: return launch_e<false, 32, 2>(A, smem, st);
+      }
+    }
   }
   return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: m = %d exceeds the register-resident limit 2048",
               A.m);
@@ -461,36 +603,53 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
   const char* ws = (const char*)r->ws;
   A.wt = ws + L.wt;
   A.b32 = ws + L.b32;
-  const size_t f = r->is_complex ? 8 : 4;
-  if (move == NK_MOVE_FLIP) {
-    A.cd = ws + L.tab;
-    A.wd = ws + L.wt;
+  const bool cplx = r->is_complex != 0;
+  const size_t f = cplx ? 8 : 4;
+  const int wpc = metro_wpc(L.mp, A.G);
+  const int nu = metro_nu(L.mp, cplx, wpc);
+  if (!nu)
+    return fail(NK_ERR_SHAPE,
+                "nk_metropolis_sweep: m = %d exceeds the register-resident limit 2048", r->m);
+  const size_t cd_row = cplx ? cplx_row_bytes(nu, wpc) : (size_t)L.mp * 2 * f;
+  const size_t need = metropolis_scratch_bytes(r->n, r->m, cplx, move, nb);
+  if (need && (!scratch || scratch_bytes < need))
+    return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: scratch of %zu B, need %zu B", scratch_bytes,
+                need);
+  char* sc = (char*)scratch;
+  const int rows = move == NK_MOVE_FLIP ? r->n : nb;
+  const int64_t qbytes = round_up((int64_t)rows * (int64_t)cd_row, 256);
+  if (!cplx) {
+    if (move == NK_MOVE_FLIP) {
+      A.cd = ws + L.tab;
+      A.wd = ws + L.wt;
+    } else {
+      A.cd = sc;
+      A.wd = sc + round_up((int64_t)nb * L.mp * 2 * f, 256);
+      const int64_t tot = (int64_t)nb * L.mp;
+      const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
+      pair_tables_real_kernel<<<(unsigned)blocks, 256, 0, st>>>(
+          (const float2*)(ws + L.tab), (const float*)(ws + L.wt), bi, bk, nb, L.mp, (float2*)A.cd,
+          (float*)A.wd);
+      if (nk_status e = check_launch("nk_metropolis_sweep(pair tables)")) return e;
+    }
   } else {
-    const size_t need = metropolis_scratch_bytes(r->n, r->m, r->is_complex, nb);
-    if (!scratch || scratch_bytes < need)
-      return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: exchange moves need %zu B of scratch", need);
-    char* sc = (char*)scratch;
     A.cd = sc;
-    A.wd = sc + round_up((int64_t)nb * L.mp * 2 * f, 256);
-    const int64_t tot = (int64_t)nb * L.mp;
+    A.wd = move == NK_MOVE_FLIP ? (const void*)(ws + L.wt) : (const void*)(sc + qbytes);
+    const int64_t tot = (int64_t)rows * (nu / 2) * wpc * 32;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
-    if (r->is_complex)
-      pair_tables_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(ws + L.tab, ws + L.wt, bi, bk, nb,
-                                                                 L.mp, (void*)A.cd, (void*)A.wd);
+    if (move == NK_MOVE_FLIP)
+      cplx_rows_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(
+          (const float4*)(ws + L.tab), (const float2*)(ws + L.wt), bi, bk, rows, L.mp, nu, wpc,
+          (float4*)sc, nullptr);
     else
-      pair_tables_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(ws + L.tab, ws + L.wt, bi, bk,
-                                                                  nb, L.mp, (void*)A.cd,
-                                                                  (void*)A.wd);
-    if (nk_status e = check_launch("nk_metropolis_sweep(pair tables)")) return e;
+      cplx_rows_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(
+          (const float4*)(ws + L.tab), (const float2*)(ws + L.wt), bi, bk, rows, L.mp, nu, wpc,
+          (float4*)sc, (float2*)(sc + qbytes));
+    if (nk_status e = check_launch("nk_metropolis_sweep(tables)")) return e;
   }
-  auto smem_for = [&](int wpc) {
-    return (size_t)kRing * L.mp * 3 * f + (size_t)A.G * L.mp * f +
-           (size_t)round_up(2 * A.G * wpc, 2) * 4 + 2 * kRing * 8 +
-           (size_t)A.G * wpc * round_up(r->n, 16);
-  };
-  const size_t smem1 = smem_for(1), smem2 = smem_for(2);
-  const bool two = L.mp >= 512 && A.G * 64 <= 512;
-  const size_t smem = two ? smem2 : smem1;
+  const size_t smem = (size_t)kRing * (cd_row + (size_t)L.mp * f) + (size_t)A.G * L.mp * f +
+                      (size_t)round_up(2 * A.G * wpc, 2) * 4 + 2 * kRing * 8 +
+                      (size_t)A.G * wpc * round_up(r->n, 16);
   if (smem > 227 * 1024)
     return fail(NK_ERR_SHAPE,
                 "nk_metropolis_sweep: group_size %d with padded m %d needs %zu B of shared "
@@ -498,8 +657,7 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
                 A.G, L.mp, smem);
   if ((int64_t)(n_discard + n_samples) * r->n > 0x7fffffff)
     return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: too many proposals in one call");
-  nk_status e = r->is_complex ? launch_c<true>(A, smem1, smem2, st)
-                              : launch_c<false>(A, smem1, smem2, st);
+  nk_status e = cplx ? launch_c<true>(A, nu, wpc, smem, st) : launch_c<false>(A, nu, wpc, smem, st);
   if (e == NK_OK && ch->counter_dev) {
     advance_counter_kernel<<<1, 1, 0, st>>>(ch->counter_dev,
                                            (uint64_t)(n_discard + n_samples) * r->n);

@@ -244,7 +244,8 @@ def nk_metropolis_sweep(rbm: Rbm, chains: Chains, move: int, bond_i=None, bond_k
     if samples_out is None:
         samples_out = torch.empty(chains.nc * n_samples_per_chain, rbm.n, dtype=torch.int8,
                                   device=chains.sigma.device)
-    if scratch is None and move == NK_MOVE_EXCHANGE:
+    if scratch is None and load_library().nk_metropolis_scratch_bytes(
+            rbm.n, rbm.m, int(rbm.is_complex), move, nb) > 0:
         scratch = metropolis_scratch(rbm, move, nb, chains.sigma.device)
     _check(load_library().nk_metropolis_sweep(
         rbm.struct(), C.byref(chains._s), move, _ptr(bond_i), _ptr(bond_k), nb, n_discard,
