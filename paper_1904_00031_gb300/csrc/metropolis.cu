@@ -46,14 +46,17 @@ struct MetroArgs {
   const void* b32;      // [mp] F
 };
 
-// FP64 accept test U < exp(two_re).  A float pre-test with a 1e-5 relative
-// margin settles all but near-ties; those get the double comparison.
-__device__ __forceinline__ bool accept_test(double U, float two_re) {
+// Accept test U < exp(two_re), decided in FP64.  A float pre-test on
+// u32 = (float) U with a 1e-5 relative margin settles all but near-ties (the
+// per-step path then has no FP64 instruction, which is slow on this GPU); a
+// near-tie fetches the double U of the step from its lane and compares in FP64.
+// Warp-uniform: every lane holds the same two_re and u32.
+__device__ __forceinline__ bool accept_test(float u32, float two_re, double my_u, int src_lane) {
   if (two_re >= 0.f) return true;
   float e32 = __expf(two_re);
-  float u32 = (float)U;
   if (u32 < e32 * (1.f - 1e-5f) - 1e-37f) return true;
   if (u32 > e32 * (1.f + 1e-5f) + 1e-37f) return false;
+  const double U = __shfl_sync(0xffffffffu, my_u, src_lane);
   return U < exp((double)two_re);
 }
 
@@ -217,7 +220,8 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   // per lane: the draws of step (block start + lane): proposed sites, accept
   // uniform and a_i - a_k, fetched once per 32 steps and broadcast by shuffles
   int my_i = 0, my_k = -1;
-  double my_u = 0.0, my_da = 0.0;
+  double my_u = 0.0;          // FP64 uniform (near-ties only)
+  float my_u32 = 0.f, my_da = 0.f;
   for (int step = 0; step < total; ++step) {
     const int q32 = step & 31;
     if (q32 == 0) {
@@ -226,20 +230,21 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
       const int idx = uniform_index(us.x, A.move == NK_MOVE_FLIP ? n : A.nb);
       u4 ua = philox_stream((uint32_t)c, gs, kTagAccept, A.seed);
       my_u = uniform53(ua.x, ua.y);
+      my_u32 = (float)my_u;
       if (A.move == NK_MOVE_FLIP) {
         my_i = idx;
         my_k = -1;
-        my_da = CPLX ? A.a[2 * idx] : A.a[idx];
+        my_da = (float)(CPLX ? A.a[2 * idx] : A.a[idx]);
       } else {
         my_i = A.bond_i[idx];
         my_k = A.bond_k[idx];
-        my_da = CPLX ? A.a[2 * my_i] - A.a[2 * my_k] : A.a[my_i] - A.a[my_k];
+        my_da = (float)(CPLX ? A.a[2 * my_i] - A.a[2 * my_k] : A.a[my_i] - A.a[my_k]);
       }
     }
     const int i = __shfl_sync(0xffffffffu, my_i, q32);
     const int kk2 = __shfl_sync(0xffffffffu, my_k, q32);
-    const double U = __shfl_sync(0xffffffffu, my_u, q32);
-    const double da = __shfl_sync(0xffffffffu, my_da, q32);
+    const float u32 = __shfl_sync(0xffffffffu, my_u32, q32);
+    const float da = __shfl_sync(0xffffffffu, my_da, q32);
     const int k = step % kRing;
     const T2* cd = reinterpret_cast<const T2*>(smem + (size_t)k * slot_bytes);
     const F* wdc = reinterpret_cast<const F*>(smem + (size_t)k * slot_bytes + cd_bytes);
@@ -311,10 +316,10 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
         if (isnan(l2)) timed_out = true;
       }
       ++nn;
-      // visible term -2 s_i a_i (- 2 s_k a_k) = -2 s_i (a_i - a_k), s_k = -s_i
-      const double vis = -2.0 * (double)si * da;
-      const float two_re = (CPLX ? 1.f : 2.f) * 0.69314718055994531f * l2 + 2.f * (float)vis;
-      if (!timed_out && accept_test(U, two_re)) {
+      // visible term -2 s_i a_i (- 2 s_k a_k) = -2 s_i (a_i - a_k) (s_k = -s_i),
+      // in FP32 like the hidden-unit product
+      const float two_re = (CPLX ? 1.f : 2.f) * 0.69314718055994531f * l2 - 4.f * si * da;
+      if (!timed_out && accept_test(u32, two_re, my_u, q32)) {
         ++nacc;
         if constexpr (CPLX) {
           const float4* row4 = reinterpret_cast<const float4*>(smem + (size_t)k * slot_bytes);
