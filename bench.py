@@ -153,12 +153,36 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 #  ln psi: theta = W sigma' (complex W: 4 n m per configuration).
 #  SR: per CG iteration the forward and adjoint contractions, 4 n m each per
 #    sample (complex), 2 n m (real); plus the force (one adjoint).
-def stage_flops(w, n_nonnull: float, n_accept: float, n_moves: int) -> dict:
+def connected_per_config(op, sm) -> float:
+    """Mean number of connected configurations sigma' != sigma (nonzero
+    <sigma'|H|sigma>) of the configurations sm (int8 [S][n]): the local-energy
+    terms the method evaluates.  Terms producing the same sigma' count once."""
+    import numpy as np
+    idx = (sm < 0).astype(np.int64)
+    active = {}
+
+    def add(key, mask):
+        active[key] = active[key] | mask if key in active else mask.copy()
+
+    for t in range(op.n_site_terms):
+        i, M = int(op.site_idx[t]), op.site_mat[t]
+        add((i,), np.array([M[1, 0] != 0, M[0, 1] != 0])[idx[:, i]])
+    for t in range(op.n_bond_terms):
+        i, k, M = int(op.bond_i[t]), int(op.bond_k[t]), op.bond_mat[t]
+        x = 2 * idx[:, i] + idx[:, k]
+        for flip, key in ((2, (i,)), (1, (k,)), (3, (min(i, k), max(i, k)))):
+            add(key, np.array([M[xx ^ flip, xx] != 0 for xx in range(4)])[x])
+    return float(sum(v.mean() for v in active.values()))
+
+
+def stage_flops(w, n_nonnull: float, n_accept: float, n_connected: float) -> dict:
+    """Algorithmic FLOPs per stage; n_connected = mean connected configurations
+    per sample (the local-energy terms)."""
     c = w.is_complex
     m, n, ns = w.m, w.n, w.n_samples
     return {
         "sample": m * ((12 if c else 4) * n_nonnull + (32 if c else 8) * n_accept),
-        "energies": float(ns) * n_moves * m * (14 if c else 4),
+        "energies": float(ns) * n_connected * m * (14 if c else 4),
         "amplitudes": float(ns) * (4 if c else 2) * n * m,
         "sr": float(ns) * (4 if c else 2) * n * m * (2 * w.n_cg + 1),
     }
@@ -293,7 +317,8 @@ def run_gpu(args):
         bk = v.bond_k.long()
         nonnull_frac = float((sm[:, bi] != sm[:, bk]).float().mean().item())
     n_accept = float(v.n_acc.sum().item())
-    fl = stage_flops(w, n_prop * nonnull_frac, n_accept, v.op.n_moves)
+    n_conn = connected_per_config(w.op, v.samples[:4096].cpu().numpy())
+    fl = stage_flops(w, n_prop * nonnull_frac, n_accept, n_conn)
     alu_peak = fp32_peak_tflops(sm_max)
     tc_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0))
     rl = {}
@@ -328,6 +353,7 @@ def run_gpu(args):
         "fp32_path_samples_per_s": None if fp32_arm is None else round(fp32_arm, 2),
         "acceptance": round(info["acceptance"], 4), "energy": info["energy"],
         "nonnull_proposal_fraction": round(nonnull_frac, 4),
+        "connected_per_sample": round(n_conn, 2), "moves": v.op.n_moves,
         "roofline": roof, "stage_roofline": rl,
         "e2e": {"value": round(world * w.n_samples / (e2e_ms / 1e3), 2), "unit": "samples/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nk.NK_INFO_LEN * 8},

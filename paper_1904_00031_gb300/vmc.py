@@ -107,7 +107,8 @@ class VmcSr:
 
     # kernel launches per step (for reporting)
     def launches_per_step(self) -> int:
-        n = 1 + (1 if self.move == nk.NK_MOVE_EXCHANGE else 0)   # pair tables, sweep
+        # move tables (exchanges; flips of complex RBMs), sweep
+        n = 1 + (1 if self.move == nk.NK_MOVE_EXCHANGE or self.w.is_complex else 0)
         n += 1                                                  # ln psi / theta
         n += 2                                                  # move tables, local energy
         n += 5 + 8 * self.w.n_cg + 3                            # SR: stats, force, CG, update
