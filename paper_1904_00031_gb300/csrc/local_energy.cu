@@ -30,6 +30,8 @@ struct ElocArgs {
   const void* tab;     // [n][mp] T2
   double* eloc;        // c128 [ns]
   void* t_out;         // [ns][m] F or null
+  int nseg;            // 1, or 2: blockIdx.y takes half of the move tiles and the
+                       // two halves are added into eloc (zeroed first) atomically
 };
 
 __device__ __forceinline__ int idx_of(int8_t s) { return s > 0 ? 0 : 1; }
@@ -153,7 +155,9 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   F* tout = reinterpret_cast<F*>(A.t_out);
   const int nm = A.n_moves;
   const int ntile = (nm + kEBM - 1) / kEBM, nchunk = mp / kEBK;
-  const int total = ntile * nchunk;
+  const int seg = blockIdx.y;
+  const int tile_begin = ntile * seg / A.nseg, tile_end = ntile * (seg + 1) / A.nseg;
+  const int it_begin = tile_begin * nchunk, it_end = tile_end * nchunk;
   const uint32_t tile_bytes = kEBK * kEBM * sizeof(T2);
 
   if (tid == 0) {
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   for (int p = 0; p < 4; ++p) {
     er[p] = ei[p] = 0.0;
     const int64_t s = s0 + ts * 4 + p;
-    if (s < A.ns) {
+    if (s < A.ns && seg == 0) {  // the diagonal belongs to the first segment
       const int8_t* sg = A.sigma + s * n;
       for (int u = tm; u < H->n_dsite; u += 16) {
         int x = idx_of(sg[ds[u].i]);
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   F tv[4];
   auto load_t = [&](int it) {
     const int kc = it % nchunk, mt = it / nchunk;
-    const bool reuse = tout && mt > 0;  // t was written by this CTA at mt = 0
+    const bool reuse = tout && mt > tile_begin;  // t was written by this CTA at its first tile
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int e = tid + u * 256, ss = e >> 4, kk = e & 15;
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   };
   auto store_t = [&](int it, int buf) {
     const int kc = it % nchunk, mt = it / nchunk;
-    const bool reuse = tout && mt > 0;
+    const bool reuse = tout && mt > tile_begin;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int e = tid + u * 256, ss = e >> 4, kk = e & 15;
@@ -224,13 +228,13 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   };
 
   __syncthreads();
-  if (total > 0) {
+  if (it_end > it_begin) {
     if (tid == 0) {
       mbar_arrive_expect_tx(&mbar[0], tile_bytes);
-      tma_load_2d(mvt, &mtab, 0, 0, &mbar[0]);
+      tma_load_2d(mvt, &mtab, tile_begin * kEBM * (CPLX ? 4 : 2), 0, &mbar[0]);
     }
-    load_t(0);
-    store_t(0, 0);
+    load_t(it_begin);
+    store_t(it_begin, 0);
   }
 
   // running products: real, P[p][q]; complex, packed over the move pairs
@@ -240,8 +244,8 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   int Pe[4][4];
   float sgn[4][4];      // real: sigma_i of the configuration for each move
   float2 ns2[4][2];     // complex: -sigma_i packed over the move pairs
-  for (int it = 0; it < total; ++it) {
-    const int b = it & 1, kc = it % nchunk, mt = it / nchunk, mt0 = mt * kEBM;
+  for (int it = it_begin; it < it_end; ++it) {
+    const int b = (it - it_begin) & 1, kc = it % nchunk, mt = it / nchunk, mt0 = mt * kEBM;
     __syncthreads();  // chunk it-1 fully consumed; t tile of chunk it stored
     if (kc == 0) {
       // new tile of moves: metadata and mel * exp(visible) per sign pattern
@@ -303,14 +307,14 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
         }
       }
     }
-    if (tid == 0 && it + 1 < total) {
+    if (tid == 0 && it + 1 < it_end) {
       const int it1 = it + 1;
       mbar_arrive_expect_tx(&mbar[b ^ 1], tile_bytes);
       tma_load_2d(mvt + (size_t)(b ^ 1) * kEBK * kEBM, &mtab,
                       (it1 / nchunk) * kEBM * (CPLX ? 4 : 2), (it1 % nchunk) * kEBK, &mbar[b ^ 1]);
     }
-    if (it + 1 < total) load_t(it + 1);
-    mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1));
+    if (it + 1 < it_end) load_t(it + 1);
+    mbar_wait_bounded(&mbar[b], (uint32_t)(((it - it_begin) >> 1) & 1));
     const T2* mv_b = mvt + (size_t)b * kEBK * kEBM;
     const TS* t_b = tS + (size_t)b * kEBK * kETS;
     if constexpr (CPLX) {
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
         }
       }
     }
-    if (it + 1 < total) store_t(it + 1, b ^ 1);
+    if (it + 1 < it_end) store_t(it + 1, b ^ 1);
     if (kc == nchunk - 1) {
       // fold the tile's ratios into the local energies (FP64)
 #pragma unroll
@@ -420,12 +424,19 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
     }
     const int64_t s = s0 + ts * 4 + p;
     if (tm == 0 && s < A.ns) {
-      A.eloc[2 * s] = er[p];
-      A.eloc[2 * s + 1] = ei[p];
+      if (A.nseg == 1) {
+        A.eloc[2 * s] = er[p];
+        A.eloc[2 * s + 1] = ei[p];
+      } else {
+        // two addends onto an exact zero: 0 + x + y = 0 + y + x in IEEE
+        // arithmetic, so the result does not depend on the order
+        atomicAdd(&A.eloc[2 * s], er[p]);
+        atomicAdd(&A.eloc[2 * s + 1], ei[p]);
+      }
     }
   }
   // with no moves at all, t = tanh(theta) is still written
-  if (nm == 0 && tout) {
+  if (nm == 0 && tout && seg == 0) {
     for (int e = tid; e < kEBS * m; e += blockDim.x) {
       const int64_t s = s0 + e / m;
       const int j = e % m;
@@ -489,16 +500,28 @@ nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
   const size_t smem = 2 * kEBK * kEBM * t2 + round_up(2 * kEBK * kETS * f, 16) + 3 * kEBM * 4 +
                       kEBM * 4 * 16 + 4 * 256 * 16 + 16;
   const int64_t blocks = (ns + kEBS - 1) / kEBS;
+  // two CTAs per SM: when the last wave of CTAs would be far from full, split
+  // the move tiles into two halves (twice the CTAs) to even out the waves
+  const int ntile = (n_moves + kEBM - 1) / kEBM;
+  auto wave_eff = [&](int64_t b) {
+    const int64_t slots = 2 * 152;
+    return (double)b / (double)(((b + slots - 1) / slots) * slots);
+  };
+  A.nseg = (ntile >= 2 && wave_eff(2 * blocks) > wave_eff(blocks)) ? 2 : 1;
+  if (A.nseg == 2 &&
+      cudaMemsetAsync(eloc, 0, (size_t)ns * 2 * sizeof(double), st) != cudaSuccess)
+    return fail(NK_ERR_CUDA, "nk_local_energy: cudaMemsetAsync failed");
+  const dim3 grid((unsigned)blocks, (unsigned)A.nseg);
   if (cplx) {
     if (cudaFuncSetAttribute(local_energy_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return fail(NK_ERR_CUDA, "nk_local_energy: shared memory attribute");
-    local_energy_tiled<true><<<(unsigned)blocks, 256, smem, st>>>(map, A);
+    local_energy_tiled<true><<<grid, 256, smem, st>>>(map, A);
   } else {
     if (cudaFuncSetAttribute(local_energy_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return fail(NK_ERR_CUDA, "nk_local_energy: shared memory attribute");
-    local_energy_tiled<false><<<(unsigned)blocks, 256, smem, st>>>(map, A);
+    local_energy_tiled<false><<<grid, 256, smem, st>>>(map, A);
   }
   return check_launch("nk_local_energy");
 }

@@ -26,11 +26,13 @@
 #include "internal.h"
 #include "ratio.cuh"
 #include "tma.cuh"
+#include "umma.cuh"
 
 namespace nk {
 
 struct MetroArgs {
   int n, m, mp, nc, G, move, nb, n_discard, n_samples;
+  int ring;             // slots of the shared-memory table ring (2 .. kMaxRing)
   uint64_t seed, counter;
   const uint64_t* counter_dev;  // if set, the counter is read from here
   const int32_t* bond_i;
@@ -68,13 +70,16 @@ __device__ __forceinline__ int move_row(const MetroArgs& A, uint64_t ctr, uint32
 // Thread (chain cw, half h, lane l) of a CTA owns hidden units
 // j = 32 (h + WPC q) + l, q < E: WPC warps share a chain and split its hidden
 // units; their partial log-products meet in shared memory across a named
-// barrier of the pair.  The columns of step t sit in ring slot t % kRing.  The
-// warps are not in lockstep: each waits for its slot to be filled (full
-// barrier) and releases it when done (empty barrier, one arrival per warp), and
-// the copy into a slot is issued once every warp has released the slot's
-// previous step, so chains may run up to kRing - 1 steps apart and absorb the
-// uneven work of accepted, rejected and null proposals.
-constexpr int kRing = 3;
+// barrier of the pair.  The columns of step t sit in ring slot t % R (R up to
+// kMaxRing, as many as shared memory holds).  The warps are not in lockstep:
+// each waits for its slot to be filled (full barrier) and releases it when done
+// (empty barrier, one arrival per warp), and the copy into a slot is issued
+// once every warp has released the slot's previous step, so chains may run up
+// to R - 1 steps apart and absorb the uneven work of accepted, rejected and
+// null proposals.  theta is kept in tensor memory (per-thread TMEM columns,
+// loaded and stored with tcgen05.ld / tcgen05.st), which leaves shared memory
+// to the ring.
+constexpr int kMaxRing = 8;
 
 // Complex tables: a thread (half h, lane l) owns units j = 32 (h + WPC q) + l,
 // q < NU, taken in pairs (2 qp, 2 qp + 1).  A row holds one 1024-byte block per
@@ -93,6 +98,53 @@ __device__ __forceinline__ void pair_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// theta += m2s * increment for this thread's units, in chunks of 8 TMEM
+// columns (complex: column 2 q + 0/1 = Re/Im theta of unit q; real: column q).
+template <bool CPLX, int WPC, int TC, int C0>
+__device__ __forceinline__ void theta_add(uint32_t tm, const typename RatioTypes<CPLX>::F* wdc,
+                                          float m2s, int h, int lane, int mp) {
+  if constexpr (C0 < TC) {
+    constexpr int N = (TC - C0) < 8 ? (TC - C0) : 8;
+    float v[N];
+    tmem_ld_cols<N>(tm + C0, v);
+    tmem_ld_wait();
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      const int col = C0 + e;
+      const int q = CPLX ? col / 2 : col;
+      const int j = 32 * (h + WPC * q) + lane;
+      if (j < mp) {
+        if constexpr (CPLX)
+          v[e] = fmaf(m2s, (col & 1) ? wdc[j].y : wdc[j].x, v[e]);
+        else
+          v[e] = fmaf(m2s, wdc[j], v[e]);
+      }
+    }
+    tmem_st_cols<N>(tm + C0, v);
+    theta_add<CPLX, WPC, TC, C0 + 8>(tm, wdc, m2s, h, lane, mp);
+  }
+}
+
+// Read this thread's theta from TMEM in chunks of 16 columns and hand each unit
+// (index q, value) to f.
+template <bool CPLX, int TC, int C0, typename Fn>
+__device__ __forceinline__ void theta_each(uint32_t tm, Fn&& f) {
+  if constexpr (C0 < TC) {
+    constexpr int N = (TC - C0) < 16 ? (TC - C0) : 16;
+    float v[N];
+    tmem_ld_cols<N>(tm + C0, v);
+    tmem_ld_wait();
+    if constexpr (CPLX) {
+#pragma unroll
+      for (int e = 0; e < N; e += 2) f((C0 + e) / 2, make_float2(v[e], v[e + 1]));
+    } else {
+#pragma unroll
+      for (int e = 0; e < N; ++e) f(C0 + e, v[e]);
+    }
+    theta_each<CPLX, TC, C0 + 16>(tm, f);
+  }
+}
+
 // NU hidden units per thread (even for complex RBMs), WPC warps per chain.
 template <bool CPLX, int NU, int WPC>
 __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
@@ -101,16 +153,15 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   constexpr int E = NU;
   constexpr int EP = (NU + 1) / 2;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int mp = A.mp, n = A.n, G = A.G;
+  const int mp = A.mp, n = A.n, G = A.G, R = A.ring;
   const size_t cd_row = CPLX ? cplx_row_bytes(NU, WPC) : (size_t)mp * sizeof(T2);
   const size_t slot_bytes = cd_row + (size_t)mp * sizeof(F);
   // ring slot k: the move's table row (cd_row bytes), then WD [mp] F
-  F* thall = reinterpret_cast<F*>(smem + kRing * slot_bytes);                       // [G][mp]
-  float* part = reinterpret_cast<float*>(reinterpret_cast<char*>(thall) +
-                                         (size_t)G * mp * sizeof(F));               // [2][G][WPC]
-  uint64_t* full = reinterpret_cast<uint64_t*>(part + round_up(2 * G * WPC, 2));    // [kRing]
-  uint64_t* empty = full + kRing;                                                    // [kRing]
-  int8_t* sgall = reinterpret_cast<int8_t*>(empty + kRing);                          // [G*WPC][n16]
+  float* part = reinterpret_cast<float*>(smem + (size_t)R * slot_bytes);            // [2][G][WPC]
+  uint64_t* full = reinterpret_cast<uint64_t*>(part + round_up(2 * G * WPC, 2));    // [kMaxRing]
+  uint64_t* empty = full + kMaxRing;                                                 // [kMaxRing]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + kMaxRing);                  // TMEM base
+  int8_t* sgall = reinterpret_cast<int8_t*>(tslot + 4);                              // [G*WPC][n16]
   const int n16 = (int)round_up(n, 16);
   const uint64_t ctr = A.counter_dev ? *A.counter_dev : A.counter;
 
@@ -120,7 +171,6 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   const int chains_here = min(G, A.nc - (int)blockIdx.x * G);
   const bool active = (cw < G) && (c < A.nc);
   const uint32_t g = (uint32_t)blockIdx.x;
-  F* th = thall + (size_t)(active ? cw : 0) * mp;
   int8_t* sg = sgall + (size_t)(active ? w : 0) * n16;  // one copy per warp
   const unsigned char* cdg = reinterpret_cast<const unsigned char*>(A.cd);
   const F* wdg = reinterpret_cast<const F*>(A.wd);
@@ -129,7 +179,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   auto jof = [&](int q) { return 32 * (h + WPC * q) + lane; };
 
   if (tid == 0) {
-    for (int k = 0; k < kRing; ++k) {
+    for (int k = 0; k < R; ++k) {
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], (uint32_t)(chains_here * WPC));
     }
@@ -137,7 +187,17 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   }
   if (active)
     for (int i = lane; i < n; i += 32) sg[i] = A.sigma[(int64_t)c * n + i];
+  // theta lives in tensor memory: thread (warp w, lane l) owns TMEM lane
+  // 32 (w % 4) + l, columns (w / 4) * TC .. + TC - 1 (its units' theta)
+  constexpr int TC = CPLX ? 2 * NU : NU;
+  const uint32_t tcols_total = (uint32_t)(((blockDim.x / 32 + 3) / 4) * TC);
+  const uint32_t tcols = tcols_total <= 32 ? 32 : tcols_total <= 64 ? 64 : tcols_total <= 128 ? 128
+                         : tcols_total <= 256 ? 256 : 512;
+  if (w == 0) tmem_alloc(tslot, tcols);
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_th = *tslot + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)((w >> 2) * TC);
 
   // theta = W sigma + b: rows of W^T staged through the (not yet used) ring
   float t[CPLX ? 1 : E];             // real: t of unit q
@@ -158,7 +218,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   };
   {
     F* stg = reinterpret_cast<F*>(smem);
-    const int KC = (int)((kRing * slot_bytes) / ((size_t)mp * sizeof(F)));
+    const int KC = (int)(((size_t)R * slot_bytes) / ((size_t)mp * sizeof(F)));
     F acc[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) {
@@ -189,19 +249,18 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
       __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const bool valid = jof(q) < mp;
-      if (valid && active) th[jof(q)] = acc[q];
-      set_t(q, acc[q], valid);
+    for (int q = 0; q < E; ++q) set_t(q, acc[q], jof(q) < mp);
+    if (active) {
+      tmem_st_cols<TC>(tmem_th, reinterpret_cast<const float*>(acc));
+      tmem_st_wait();
     }
   }
   __syncthreads();
-  if (!active) return;  // no CTA-wide barrier from here on
-
-  const int total = (A.n_discard + A.n_samples) * n;
+  // inactive warps skip the steps (no CTA-wide barrier until the end)
+  const int total = active ? (A.n_discard + A.n_samples) * n : 0;
   const uint32_t cd_bytes = (uint32_t)cd_row, wd_bytes = (uint32_t)(mp * sizeof(F));
   auto issue = [&](int step) {
-    const int k = step % kRing;
+    const int k = step % R;
     const int row = move_row(A, ctr, g, step);
     unsigned char* sl = smem + (size_t)k * slot_bytes;
     mbar_arrive_expect_tx(&full[k], cd_bytes + wd_bytes);
@@ -211,7 +270,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   const bool producer = (tid == 0);
   int issued = 0;  // steps whose columns have been requested (producer only)
   if (producer) {
-    for (; issued < kRing && issued < total; ++issued) issue(issued);
+    for (; issued < R && issued < total; ++issued) issue(issued);
   }
 
   uint64_t nacc = 0;
@@ -219,6 +278,8 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   int nn = 0;              // non-null steps so far (identical in the warps of a chain)
   // per lane: the draws of step (block start + lane): proposed sites, accept
   // uniform and a_i - a_k, fetched once per 32 steps and broadcast by shuffles
+  int kslot = 0;          // ring slot of the current step (step % R)
+  uint32_t kphase = 0u;   // phase of its full barrier ((step / R) & 1)
   int my_i = 0, my_k = -1;
   double my_u = 0.0;          // FP64 uniform (near-ties only)
   float my_u32 = 0.f, my_da = 0.f;
@@ -245,7 +306,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     const int kk2 = __shfl_sync(0xffffffffu, my_k, q32);
     const float u32 = __shfl_sync(0xffffffffu, my_u32, q32);
     const float da = __shfl_sync(0xffffffffu, my_da, q32);
-    const int k = step % kRing;
+    const int k = kslot;
     const T2* cd = reinterpret_cast<const T2*>(smem + (size_t)k * slot_bytes);
     const F* wdc = reinterpret_cast<const F*>(smem + (size_t)k * slot_bytes + cd_bytes);
     const float si = (float)sg[i];
@@ -253,7 +314,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     // every warp observes every phase of the slot's barrier, in order, so that
     // no barrier is ever more than one phase ahead of a waiting warp
     if (!timed_out) {
-      const bool ok = mbar_wait_bounded(&full[k], (uint32_t)((step / kRing) & 1));
+      const bool ok = mbar_wait_bounded(&full[k], kphase);
       timed_out = __any_sync(0xffffffffu, !ok);  // warp-uniform
     }
     if (!null_move) {
@@ -344,29 +405,20 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
             tx[qp] = f2mul(nx, inv);
             ty[qp] = f2mul(ny, inv);
           }
-#pragma unroll
-          for (int q = 0; q < E; ++q) {
-            const int j = jof(q);
-            if (j < mp) {
-              F x = th[j];
-              const F dw = wdc[j];
-              x.x = fmaf(-2.f * si, dw.x, x.x);
-              x.y = fmaf(-2.f * si, dw.y, x.y);
-              th[j] = x;
-            }
-          }
+          theta_add<true, WPC, TC, 0>(tmem_th, wdc, -2.f * si, h, lane, mp);
+          tmem_st_wait();
         } else {
 #pragma unroll
           for (int q = 0; q < E; ++q) {
             const int j = jof(q);
             if (j < mp) {
               const T2 v = cd[j];
-              const F dw = wdc[j];
               const float r = fmaf(-si * t[q], v.y, v.x);
               t[q] = __fdividef(fmaf(t[q], v.x, -si * v.y), r);
-              th[j] = fmaf(-2.f * si, dw, th[j]);
             }
           }
+          theta_add<false, WPC, TC, 0>(tmem_th, wdc, -2.f * si, h, lane, mp);
+          tmem_st_wait();
         }
         __syncwarp();
         if (lane == 0) {
@@ -380,12 +432,12 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     if (producer && !timed_out) {
       // refill slots whose previous step every warp has released; block only
       // when this warp's own next step would otherwise have no data
-      while (issued < total && issued <= step + kRing) {
-        const int prev = issued - kRing;  // last step that used the slot
-        const uint32_t par = (uint32_t)((prev / kRing) & 1);
-        if (!mbar_try_wait(&empty[prev % kRing], par)) {
+      while (issued < total && issued <= step + R) {
+        const int prev = issued - R;  // last step that used the slot
+        const uint32_t par = (uint32_t)((prev / R) & 1);
+        if (!mbar_try_wait(&empty[prev % R], par)) {
           if (issued > step + 1) break;
-          if (!mbar_wait_bounded(&empty[prev % kRing], par)) {
+          if (!mbar_wait_bounded(&empty[prev % R], par)) {
             timed_out = true;
             break;
           }
@@ -402,18 +454,28 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
         for (int ii = lane; ii < n; ii += 32) out[ii] = sg[ii];
       }
       // exact refresh of t from theta (this thread's own entries)
-#pragma unroll
-      for (int q = 0; q < E; ++q)
-        if (jof(q) < mp) set_t(q, th[jof(q)], true);
+      theta_each<CPLX, TC, 0>(tmem_th, [&](int q, F x) {
+        if (jof(q) < mp) set_t(q, x, true);
+      });
+    }
+    if (++kslot == R) {
+      kslot = 0;
+      kphase ^= 1u;
     }
   }
   if (timed_out && producer) {
     // let copies still in flight land before the CTA exits
-    for (int k = 0; k < kRing; ++k) mbar_wait_bounded(&full[k], 0, 1u << 20);
+    for (int k = 0; k < R; ++k) mbar_wait_bounded(&full[k], 0, 1u << 20);
   }
-  if (h == 0) {
+  if (active && h == 0) {
     for (int ii = lane; ii < n; ii += 32) A.sigma[(int64_t)c * n + ii] = sg[ii];
     if (A.n_acc && lane == 0) A.n_acc[c] = timed_out ? ~0ull : nacc;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (w == 0) {
+    tc_fence_after();
+    tmem_dealloc(*tslot, tcols);
   }
 }
 
@@ -652,14 +714,20 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
           (float4*)sc, (float2*)(sc + qbytes));
     if (nk_status e = check_launch("nk_metropolis_sweep(tables)")) return e;
   }
-  const size_t smem = (size_t)kRing * (cd_row + (size_t)L.mp * f) + (size_t)A.G * L.mp * f +
-                      (size_t)round_up(2 * A.G * wpc, 2) * 4 + 2 * kRing * 8 +
+  // ring depth: as many slots as fit next to the pair partials, barriers and
+  // the per-warp sigma copies (theta lives in tensor memory)
+  const size_t slot = cd_row + (size_t)L.mp * f;
+  const size_t rest = (size_t)round_up(2 * A.G * wpc, 2) * 4 + 2 * kMaxRing * 8 + 16 +
                       (size_t)A.G * wpc * round_up(r->n, 16);
-  if (smem > 227 * 1024)
+  const size_t cap = 227 * 1024;
+  const int ring = rest + 2 * slot > cap ? 0 : (int)std::min<size_t>(kMaxRing, (cap - rest) / slot);
+  if (ring < 2)
     return fail(NK_ERR_SHAPE,
-                "nk_metropolis_sweep: group_size %d with padded m %d needs %zu B of shared "
-                "memory (> 227 KB)",
-                A.G, L.mp, smem);
+                "nk_metropolis_sweep: group_size %d with padded m %d leaves room for fewer "
+                "than two table slots in 227 KB of shared memory",
+                A.G, L.mp);
+  A.ring = ring;
+  const size_t smem = (size_t)ring * slot + rest;
   if ((int64_t)(n_discard + n_samples) * r->n > 0x7fffffff)
     return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: too many proposals in one call");
   nk_status e = cplx ? launch_c<true>(A, nu, wpc, smem, st) : launch_c<false>(A, nu, wpc, smem, st);
