@@ -5,13 +5,13 @@
 // all propose the same site (bond) at a step.  Per proposal the ratio needs, for
 // every hidden unit j, the table column (cosh c_j, sinh c_j / s_i) of the move
 // and, on acceptance, its theta increment W_i (- W_k).  One thread streams each
-// step's columns into shared memory with 1-D TMA bulk copies through a
-// three-slot ring, so the warps read every table value from shared memory once
-// per chain.
+// step's columns into shared memory with 1-D TMA bulk copies through a ring
+// of slots, so the warps read every table value from shared memory once per
+// chain.
 //
-// Per chain: sigma and theta live in shared memory, t = tanh(theta) in
-// registers.  With C = cosh c, D = sinh c / s_i, the factor of hidden unit j is
-// r_j = C_j - s_i t_j D_j.  Real RBMs read (C, D) and multiply r_j.  Complex RBMs
+// Per chain: sigma lives in shared memory, theta in tensor memory (per-thread
+// TMEM columns), t = tanh(theta) in registers.  With C = cosh c and
+// D = sinh c / s_i, the factor of hidden unit j is r_j = C_j - s_i t_j D_j.  Real RBMs read (C, D) and multiply r_j.  Complex RBMs
 // need only |r_j|^2 for the accept test and read, per unit, the expanded form
 //   |r|^2 = |C|^2 + |t|^2 |D|^2 - 2 s_i Re(t conj(C) D),
 // from per-call tables (|C|^2, |D|^2, conj(C) D) laid out so that one 16-byte

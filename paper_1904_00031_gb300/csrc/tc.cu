@@ -261,13 +261,17 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = *slot;
-  const int total_it = A.mt * KC;
+  // hidden tiles of this CTA: all, or one half (blockIdx.y) when the launch is split
+  const int seg = blockIdx.y;
+  const int jt_begin = A.mt * seg / A.nseg, jt_end = A.mt * (seg + 1) / A.nseg;
+  const int total_it = (jt_end - jt_begin) * KC;
   bool bad = false;
 
   if (w == 0) {
     if (lane == 0) {
       for (int it = 0; it < total_it; ++it) {
-        const int st = it % kFwdStages, u = it / kFwdStages, jt = it / KC, kc = it % KC;
+        const int st = it % kFwdStages, u = it / kFwdStages, jt = jt_begin + it / KC,
+                  kc = it % KC;
         if (u > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((u - 1) & 1))) {
           bad = true;
           break;
@@ -282,8 +286,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(128, 128);
       int it = 0;
-      for (int jt = 0; jt < A.mt && !bad; ++jt) {
-        const int acc = jt & 1, ua = jt >> 1;
+      for (int jt = jt_begin; jt < jt_end && !bad; ++jt) {
+        const int acc = (jt - jt_begin) & 1, ua = (jt - jt_begin) >> 1;
         if (ua > 0 && !mbar_wait_bounded(&tempty[acc], (uint32_t)((ua - 1) & 1))) {
           bad = true;
           break;
@@ -361,11 +365,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         }
       }
     };
-    if (A.mode == 0 && A.mt > 0) load_t(0);
+    if (A.mode == 0 && jt_end > jt_begin) load_t(jt_begin);
     double sr = 0.0, si = 0.0;
-    for (int jt = 0; jt < A.mt; ++jt) {
-      const int acc = jt & 1;
-      if (!mbar_wait_bounded(&tfull[acc], (uint32_t)((jt >> 1) & 1))) {
+    for (int jt = jt_begin; jt < jt_end; ++jt) {
+      const int acc = (jt - jt_begin) & 1;
+      if (!mbar_wait_bounded(&tfull[acc], (uint32_t)(((jt - jt_begin) >> 1) & 1))) {
         bad = true;
         break;
       }
@@ -428,17 +432,26 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
-      if (A.mode == 0 && jt + 1 < A.mt) load_t(jt + 1);
+      if (A.mode == 0 && jt + 1 < jt_end) load_t(jt + 1);
     }
     if (live) {
       if (bad) sr = si = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a timeout
+      // split launches: two addends onto an exact zero (y, ln psi zeroed by the
+      // launcher), so the sum does not depend on which half lands first
+      double* yd = reinterpret_cast<double*>(A.mode == 0 ? A.y : (void*)A.logpsi);
+      const int cs = CPLX || A.mode == 1 ? 2 : 1;  // doubles per sample
       if (A.mode == 0) {
-        if (CPLX) reinterpret_cast<double2*>(A.y)[s] = make_double2(sr, si);
-        else reinterpret_cast<double*>(A.y)[s] = sr;
+        if (A.nseg == 1) {
+          yd[cs * s] = sr;
+          if (CPLX) yd[cs * s + 1] = si;
+        } else {
+          atomicAdd(&yd[cs * s], sr);
+          if (CPLX) atomicAdd(&yd[cs * s + 1], si);
+        }
       } else {
         double vr = 0.0, vi = 0.0;
         const int8_t* sg = A.sigma + s * A.n;
-        for (int i = 0; i < A.n; ++i) {
+        for (int i = 0; i < (seg == 0 ? A.n : 0); ++i) {
           const double sv = (double)sg[i];
           if (CPLX) {
             vr += A.a[2 * i] * sv;
@@ -447,8 +460,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             vr += A.a[i] * sv;
           }
         }
-        A.logpsi[2 * s] = sr + vr;
-        A.logpsi[2 * s + 1] = si + vi;
+        if (A.nseg == 1) {
+          yd[2 * s] = sr + vr;
+          yd[2 * s + 1] = si + vi;
+        } else {
+          atomicAdd(&yd[2 * s], sr + vr);
+          atomicAdd(&yd[2 * s + 1], si + vi);
+        }
       }
     }
   }
@@ -472,16 +490,32 @@ nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st)
   if (!tc_make_map(&map, planes, 2LL * A.mt * 128, A.na64, A.na64, 128)) return NK_ERR_CUDA;
   const size_t smem = fwd_smem_bytes(A.na64);
   const int64_t blocks = (A.ns + 127) / 128;
+  // one CTA per SM: for ln psi (mode 1), when the last wave would be far from
+  // full, split the hidden tiles into two halves (twice the CTAs) whose sums
+  // meet in the output.  (In the SR forward, mode 0, the extra sigma' tile
+  // builds and output atomics cost more than the evener waves save.)
+  auto wave_eff = [&](int64_t b) {
+    return (double)b / (double)(((b + 151) / 152) * 152);
+  };
+  FwdTcArgs B = A;
+  B.nseg = (A.mode == 1 && A.mt >= 2 && wave_eff(2 * blocks) > wave_eff(blocks)) ? 2 : 1;
+  if (B.nseg == 2) {
+    void* out = A.mode == 0 ? A.y : (void*)A.logpsi;
+    const size_t per = (A.mode == 1 || A.cplx) ? 16 : 8;
+    if (cudaMemsetAsync(out, 0, (size_t)A.ns * per, st) != cudaSuccess)
+      return fail(NK_ERR_CUDA, "fwd_tc: cudaMemsetAsync failed");
+  }
+  const dim3 grid((unsigned)blocks, (unsigned)B.nseg);
   if (A.cplx) {
     if (cudaFuncSetAttribute(fwd_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return fail(NK_ERR_CUDA, "fwd_tc: shared memory attribute");
-    fwd_tc_kernel<true><<<(unsigned)blocks, kFwdThreads, smem, st>>>(map, A);
+    fwd_tc_kernel<true><<<grid, kFwdThreads, smem, st>>>(map, B);
   } else {
     if (cudaFuncSetAttribute(fwd_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return fail(NK_ERR_CUDA, "fwd_tc: shared memory attribute");
-    fwd_tc_kernel<false><<<(unsigned)blocks, kFwdThreads, smem, st>>>(map, A);
+    fwd_tc_kernel<false><<<grid, kFwdThreads, smem, st>>>(map, B);
   }
   return check_launch("fwd_tc");
 }

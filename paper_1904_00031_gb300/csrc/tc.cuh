@@ -49,6 +49,7 @@ struct FwdTcArgs {
   void* theta_out;        // mode 1 (may be null)
   const double* skip;     // if non-null and *skip != 0, the kernel returns at once
   int* err;               // set on a timed-out wait (may be null)
+  int nseg = 1;           // set by launch_fwd_tc: 1, or 2 halves of the hidden tiles
 };
 nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st);
 

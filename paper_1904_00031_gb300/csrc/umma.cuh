@@ -205,31 +205,6 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float* v) {
 
 // ------------------------------------------------------------------ TMA tiles
 
-// ------------------------------------------------------------------ L2 policies
-
-// Cache policies for data read once (streamed: evict first) and for tiles every
-// CTA re-reads (keep: evict last), so that a streamed operand does not push the
-// shared tiles out of L2.
-__device__ __forceinline__ uint64_t l2_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t l2_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-
-// 16-byte global load that skips L1 and carries an L2 policy.
-__device__ __forceinline__ float4 ldg_hint(const void* ptr, uint64_t pol) {
-  float4 v;
-  asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(ptr), "l"(pol));
-  return v;
-}
-
 // 2-D tiled TMA load of box (c0 = inner element coordinate, c1 = row).
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int c0, int c1,
                                             uint64_t* bar) {
@@ -240,15 +215,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int c0,
       : "memory");
 }
 
-// The same with an L2 cache policy.
-__device__ __forceinline__ void tma_load_2d_hint(void* dst, const void* tmap, int c0, int c1,
-                                                 uint64_t* bar, uint64_t pol) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
-      "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(smem_addr(bar)), "l"(pol)
-      : "memory");
-}
 
 
 }  // namespace nk
