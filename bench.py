@@ -83,6 +83,13 @@ def run_oracle_subprocess(workload: str, n_chains: int, spc: int, n_cg: int) -> 
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+# DRAM bytes (read + write) per launch of a stage's dominant kernel, from one
+# single-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# workload at full size; a kernel that changed since its capture has no entry.
+NCU_TRAFFIC = {
+    ("j1j2_20x20_alpha4", "bf16x2", "local_energy_tiled"): 21.07e9 + 1.69e9,
+}
+
 ORACLE_SAMPLE = {"c5": (24, 2, 50), "c3": (64, 1, 50), "c2": (128, 4, 50), "c1": (16, 63, 120),
                  "c4": (64, 4, 50)}
 
@@ -334,7 +341,7 @@ def run_gpu(args):
             "sr": "SR step (fwd_tc + adj_tc + CG vector kernels)" if prec_name == "bf16x2"
                   else "SR step (forward/adjoint FP32 + CG vector kernels)"}[dom]
     roof = dict(rl[dom])
-    roof.update({"kernel": kern, "traffic": None,
+    roof.update({"kernel": kern, "traffic": NCU_TRAFFIC.get((w.name, prec_name, kern)),
                  "peak_source": (f"{pk_kind} bf16 dense TFLOP/s (sustained)" if roof["bound"] == "tensor"
                                  else f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz")})
     out = {
