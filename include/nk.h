@@ -272,6 +272,50 @@ nk_status nk_sr_step_noalloc(nk_rbm* rbm, const int8_t* sigma, const void* t, co
 nk_status nk_sr_tune(nk_rbm* rbm, const int8_t* sigma, const void* t, int64_t ns, int32_t prec,
                      void* scratch, size_t scratch_bytes, void* stream);
 
+/* ---------------------------------------------------------------- SR batches */
+
+/* One problem of an SR batch: the arguments nk_sr_step takes for one RBM.  The
+ * RBMs of a batch are independent and may differ in n, m, field and ns. */
+typedef struct nk_sr_batch_item {
+  nk_rbm* rbm;            /* sr_splits > 0 fixes the problem's split-K count;
+                             0 = a batch-wide default (about two waves of
+                             adjoint CTAs over the whole batch)                  */
+  const int8_t* sigma;    /* int8 [ns][n]                                      */
+  const void* t;          /* F32 [ns][m] tanh(theta)                           */
+  const double* eloc;     /* c128 [ns]                                         */
+  const double* weights;  /* F64 [ns] or NULL (1/ns)                           */
+  int64_t ns;
+  int32_t n_chains;
+  int32_t reserved;       /* 0                                                 */
+  void* scratch;          /* nk_sr_scratch_bytes(n, m, is_complex, ns) bytes,
+                             256-B aligned (device), one per problem           */
+  size_t scratch_bytes;
+  double* info_out;       /* double [NK_INFO_LEN] (device)                     */
+} nk_sr_batch_item;
+
+/* Bytes of the descriptor array of a batch of n_inst problems. */
+size_t nk_sr_batch_desc_bytes(int32_t n_inst);
+
+/* Fill desc_host (nk_sr_batch_desc_bytes(n_inst) bytes of host memory) with the
+ * device-side descriptors of the batch (every problem's sizes, device pointers
+ * and tensor maps).  No CUDA work is enqueued; the caller copies the bytes into
+ * device memory (256-B aligned) for nk_sr_step_batch, and describes the batch
+ * again whenever an item's pointers, sizes or rbm->sr_splits change. */
+nk_status nk_sr_batch_describe(const nk_sr_batch_item* items, int32_t n_inst, int32_t prec,
+                               void* desc_host, size_t desc_bytes);
+
+/* nk_sr_step (Sec. 2.2.5, Eq. 2) for every problem of a batch, with one launch
+ * of each kernel per group of up to 64 problems of one field (complex or real)
+ * instead of one launch per problem: many small RBMs fill the GPU together.
+ * Each problem's arithmetic and reduction order are those of nk_sr_step with
+ * the same split-K count, so the results are identical to n separate calls.
+ * Tensor-core precision only (prec = NK_PREC_BF16X2; NK_ERR_UNSUPPORTED else).
+ *   desc_dev  the bytes nk_sr_batch_describe wrote for these items, in device
+ *             memory, 256-B aligned */
+nk_status nk_sr_step_batch(const nk_sr_batch_item* items, int32_t n_inst,
+                           const void* desc_dev, double diag_shift, double lr, int32_t n_cg,
+                           double cg_rtol, int32_t prec, void* stream);
+
 /* Scratch bytes nk_rbm_logpsi_backward needs for ns samples. */
 size_t nk_backward_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns);
 

@@ -1,10 +1,12 @@
 """Many independent, unevenly sized VMC + SR problems advanced together.
 
-Every instance runs the ordinary iteration (``vmc.VmcSr``: sweep -> ln psi ->
-local energies -> SR step) on a stream of its own; the streams fork from and
-join the caller's stream, and the whole multi-instance iteration is captured
-once into a single CUDA graph, so each later iteration is one graph launch in
-which the instances' kernels run concurrently and fill the GPU.
+Every instance samples, evaluates ln psi and its local energies on a stream of
+its own (the streams fork from and join the caller's stream); the SR steps of
+all instances then run as one batch (nk_sr_step_batch: one launch of each
+kernel per group of up to 64 instances of one field, instead of one per
+instance), on the tensor-core path when every instance shares the SR settings.
+The whole multi-instance iteration is captured once into a single CUDA graph,
+so each later iteration is one graph launch.
 """
 from __future__ import annotations
 
@@ -17,14 +19,27 @@ from .vmc import VmcSr
 
 class BatchedVmc:
     def __init__(self, instances, prec: int = nk.NK_PREC_FP32, device="cuda",
-                 graph: bool = True, param_scale: float = 0.01):
+                 graph: bool = True, param_scale: float = 0.01, batch_sr: bool = True,
+                 sr_splits: int = 0):
         self.items = []
         for w in instances:
             p = W.init_params(w.n, w.m, w.is_complex, param_scale, w.seed)
-            self.items.append(VmcSr(w, p, prec=prec, device=device, graph=graph))
+            v = VmcSr(w, p, prec=prec, device=device, graph=graph)
+            v.rbm._s.sr_splits = int(sr_splits)  # 0: built-in (per call, or batch-wide) default
+            self.items.append(v)
         self.streams = [torch.cuda.Stream(device=device) for _ in instances]
         self.use_graph = graph
         self.graph = None
+        ws = list(instances)
+        same = all((w.diag_shift, w.lr, w.n_cg) == (ws[0].diag_shift, ws[0].lr, ws[0].n_cg)
+                   for w in ws)
+        self.srb = None
+        if batch_sr and same and prec == nk.NK_PREC_BF16X2:
+            self.sr_args = (ws[0].diag_shift, ws[0].lr, ws[0].n_cg)
+            self.srb = nk.SrBatch([
+                {"rbm": v.rbm, "sigma": v.samples, "t": v.t, "eloc": v.eloc,
+                 "scratch": v.scratch, "info": v.info_buf, "n_chains": v.w.n_chains}
+                for v in self.items], prec=prec, device=device)
 
     @property
     def n_samples(self) -> int:
@@ -35,9 +50,16 @@ class BatchedVmc:
         for v, st in zip(self.items, self.streams):
             st.wait_stream(cur)
             with torch.cuda.stream(st):
-                v._eager_step()
+                v.sample()
+                v.amplitudes()
+                v.energies()
+                if self.srb is None:
+                    v.sr()
         for st in self.streams:
             cur.wait_stream(st)
+        if self.srb is not None:
+            d, lr, n_cg = self.sr_args
+            self.srb.step(d, lr, n_cg)
 
     def capture(self):
         torch.cuda.synchronize()
@@ -61,4 +83,10 @@ class BatchedVmc:
         return [v.info() for v in self.items]
 
     def launches_per_step(self) -> int:
-        return sum(v.launches_per_step() for v in self.items)
+        if self.srb is None:
+            return sum(v.launches_per_step() for v in self.items)
+        n = sum(v.launches_per_step() - v.sr_launches() for v in self.items)
+        n_c = sum(1 for v in self.items if v.w.is_complex)
+        n_r = len(self.items) - n_c
+        groups = (n_c + 63) // 64 + (n_r + 63) // 64   # up to 64 instances of one field per launch
+        return n + groups * (10 + 8 * self.sr_args[2])

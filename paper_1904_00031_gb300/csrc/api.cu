@@ -369,6 +369,22 @@ nk_status nk_sr_tune(nk_rbm* rbm, const int8_t* sigma, const void* t, int64_t ns
   return run_sr_tune(rbm, sigma, t, ns, prec, scratch, scratch_bytes, (cudaStream_t)stream);
 }
 
+size_t nk_sr_batch_desc_bytes(int32_t n_inst) { return sr_batch_desc_bytes(n_inst); }
+
+nk_status nk_sr_batch_describe(const nk_sr_batch_item* items, int32_t n_inst, int32_t prec,
+                               void* desc_host, size_t desc_bytes) {
+  return sr_batch_describe(items, n_inst, prec, desc_host, desc_bytes);
+}
+
+nk_status nk_sr_step_batch(const nk_sr_batch_item* items, int32_t n_inst,
+                           const void* desc_dev, double diag_shift, double lr, int32_t n_cg,
+                           double cg_rtol, int32_t prec, void* stream) {
+  if (n_cg < 0 || !(diag_shift >= 0.0) || !(cg_rtol >= 0.0))
+    return fail(NK_ERR_INVALID_ARG, "nk_sr_step_batch: negative n_cg, diag_shift or cg_rtol");
+  return run_sr_step_batch(items, n_inst, desc_dev, diag_shift, lr, n_cg, cg_rtol, prec,
+                           (cudaStream_t)stream);
+}
+
 nk_status nk_rbm_logpsi_backward(const nk_rbm* rbm, const int8_t* sigma, int64_t ns,
                                  const double* g, double* grad_out, int32_t prec, void* scratch,
                                  size_t scratch_bytes, void* stream) {

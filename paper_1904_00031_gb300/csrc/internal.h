@@ -64,6 +64,14 @@ nk_status run_sr_step(nk_rbm* r, const int8_t* sigma, const void* t, const doubl
 int sr_choose_splits(const SrLayout& L, int prec, int requested);
 nk_status run_sr_tune(nk_rbm* r, const int8_t* sigma, const void* t, int64_t ns, int prec,
                       void* scratch, size_t scratch_bytes, cudaStream_t st);
+// SR batches (nk_sr_step_batch)
+nk_status sr_batch_check(const nk_sr_batch_item* items, int n_inst, int prec);
+size_t sr_batch_desc_bytes(int n_inst);
+nk_status sr_batch_describe(const nk_sr_batch_item* items, int n_inst, int prec, void* host,
+                            size_t bytes);
+nk_status run_sr_step_batch(const nk_sr_batch_item* items, int n_inst, const void* desc_dev,
+                            double eps, double lr, int n_cg, double rtol, int prec,
+                            cudaStream_t st);
 nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const double* g,
                        double* grad, int prec, void* scratch, size_t scratch_bytes,
                        cudaStream_t st);

@@ -13,12 +13,15 @@
 namespace nk {
 
 template <bool CPLX>
-__global__ void prepare_kernel(int n, int m, int mp, const double* __restrict__ a,
-                               const double* __restrict__ b, const double* __restrict__ w,
-                               char* __restrict__ ws, WsLayout L) {
+__device__ __forceinline__ void prepare_body(int bx, int gx, int n, int m, int mp,
+                                             const double* __restrict__ a,
+                                             const double* __restrict__ b,
+                                             const double* __restrict__ w, char* __restrict__ ws,
+                                             size_t o_a32, size_t o_b32, size_t o_wt,
+                                             size_t o_tab, size_t o_xw) {
   const int64_t total = (int64_t)n * mp;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gx * blockDim.x) {
     int i = (int)(e / mp), j = (int)(e % mp);
     double wr = 0.0, wi = 0.0;
     if (j < m) {
@@ -32,19 +35,19 @@ __global__ void prepare_kernel(int n, int m, int mp, const double* __restrict__ 
     double c2 = cosh(2.0 * wr), s2 = sinh(2.0 * wr);
     if (CPLX) {
       double cy = cos(2.0 * wi), sy = sin(2.0 * wi);
-      reinterpret_cast<float2*>(ws + L.wt)[e] = make_float2((float)wr, (float)wi);
+      reinterpret_cast<float2*>(ws + o_wt)[e] = make_float2((float)wr, (float)wi);
       // cosh(2w) = cosh 2x cos 2y + i sinh 2x sin 2y; sinh(2w) = sinh 2x cos 2y + i cosh 2x sin 2y
-      reinterpret_cast<float4*>(ws + L.tab)[e] =
+      reinterpret_cast<float4*>(ws + o_tab)[e] =
           make_float4((float)(c2 * cy), (float)(s2 * sy), (float)(s2 * cy), (float)(c2 * sy));
     } else {
-      reinterpret_cast<float*>(ws + L.wt)[e] = (float)wr;
-      reinterpret_cast<float2*>(ws + L.tab)[e] = make_float2((float)c2, (float)s2);
+      reinterpret_cast<float*>(ws + o_wt)[e] = (float)wr;
+      reinterpret_cast<float2*>(ws + o_tab)[e] = make_float2((float)c2, (float)s2);
     }
   }
   // augmented row-major W | b, rows j < mp, columns i <= n (column n = b)
   const int64_t total2 = (int64_t)mp * (n + 1);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total2;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < total2;
+       e += (int64_t)gx * blockDim.x) {
     int j = (int)(e / (n + 1)), i = (int)(e % (n + 1));
     double vr = 0.0, vi = 0.0;
     if (j < m) {
@@ -61,16 +64,16 @@ __global__ void prepare_kernel(int n, int m, int mp, const double* __restrict__ 
       }
     }
     if (CPLX)
-      reinterpret_cast<float2*>(ws + L.xw)[e] = make_float2((float)vr, (float)vi);
+      reinterpret_cast<float2*>(ws + o_xw)[e] = make_float2((float)vr, (float)vi);
     else
-      reinterpret_cast<float*>(ws + L.xw)[e] = (float)vr;
+      reinterpret_cast<float*>(ws + o_xw)[e] = (float)vr;
   }
-  const int64_t t3 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t t3 = bx * (int64_t)blockDim.x + threadIdx.x;
   if (t3 < n) {
     if (CPLX)
-      reinterpret_cast<float2*>(ws + L.a32)[t3] = make_float2((float)a[2 * t3], (float)a[2 * t3 + 1]);
+      reinterpret_cast<float2*>(ws + o_a32)[t3] = make_float2((float)a[2 * t3], (float)a[2 * t3 + 1]);
     else
-      reinterpret_cast<float*>(ws + L.a32)[t3] = (float)a[t3];
+      reinterpret_cast<float*>(ws + o_a32)[t3] = (float)a[t3];
   }
   if (t3 < mp) {
     double br = 0.0, bi = 0.0;
@@ -79,10 +82,36 @@ __global__ void prepare_kernel(int n, int m, int mp, const double* __restrict__ 
       bi = CPLX ? b[2 * t3 + 1] : 0.0;
     }
     if (CPLX)
-      reinterpret_cast<float2*>(ws + L.b32)[t3] = make_float2((float)br, (float)bi);
+      reinterpret_cast<float2*>(ws + o_b32)[t3] = make_float2((float)br, (float)bi);
     else
-      reinterpret_cast<float*>(ws + L.b32)[t3] = (float)br;
+      reinterpret_cast<float*>(ws + o_b32)[t3] = (float)br;
   }
+}
+
+template <bool CPLX>
+__global__ void prepare_kernel(int n, int m, int mp, const double* __restrict__ a,
+                               const double* __restrict__ b, const double* __restrict__ w,
+                               char* __restrict__ ws, WsLayout L) {
+  prepare_body<CPLX>(blockIdx.x, gridDim.x, n, m, mp, a, b, w, ws, L.a32, L.b32, L.wt, L.tab,
+                     L.xw);
+}
+
+// the same for every problem of an SR batch (blockIdx.y)
+template <bool CPLX>
+__global__ void prepare_batch(const SrDesc* __restrict__ D) {
+  const SrDesc& d = D[blockIdx.y];
+  prepare_body<CPLX>(blockIdx.x, gridDim.x, d.n, d.m, d.mp, d.a, d.b, d.w, d.ws, d.ws_a32,
+                     d.ws_b32, d.ws_wt, d.ws_tab, d.ws_xw);
+}
+
+nk_status launch_prepare_batch(const SrDesc* D, int G, int cplx, int64_t max_work,
+                               int64_t max_minb, cudaStream_t st) {
+  int64_t blocks = (max_work + 255) / 256;
+  blocks = std::max<int64_t>(std::min<int64_t>(blocks, 152 * 8), max_minb);
+  const dim3 grid((unsigned)blocks, (unsigned)G);
+  if (cplx) prepare_batch<true><<<grid, 256, 0, st>>>(D);
+  else prepare_batch<false><<<grid, 256, 0, st>>>(D);
+  return check_launch("prepare_batch");
 }
 
 nk_status launch_prepare(const nk_rbm* r, cudaStream_t st) {

@@ -13,6 +13,9 @@
 // inner products and every reduction are FP64, and every reduction has a fixed
 // order (no atomics), so a step is bitwise reproducible.
 #include <math.h>
+#include <string.h>
+
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -143,7 +146,7 @@ __device__ __forceinline__ double sum_partials(const double* red) {
 // One CTA.  E = sum w E_s, var = sum w |E_s - E|^2, error from chain means;
 // writes v_s = w_s (E_s - E) (the vector whose adjoint contraction is F).
 template <bool CPLX>
-__global__ void __launch_bounds__(1024) stats_kernel(const double* __restrict__ eloc,
+__device__ __forceinline__ void stats_body(int bx, int gx, const double* __restrict__ eloc,
                                                      const double* __restrict__ weights,
                                                      int64_t ns, int n_chains, double* info,
                                                      double* scal, void* vout) {
@@ -187,6 +190,14 @@ __global__ void __launch_bounds__(1024) stats_kernel(const double* __restrict__ 
     scal[SC_EBAR_IM] = ei;
     scal[SC_NONFINITE] = (isfinite(er) && isfinite(ei) && isfinite(var)) ? 0.0 : 1.0;
   }
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(1024) stats_kernel(const double* __restrict__ eloc,
+                                                     const double* __restrict__ weights,
+                                                     int64_t ns, int n_chains, double* info,
+                                                     double* scal, void* vout) {
+  stats_body<CPLX>(blockIdx.x, gridDim.x, eloc, weights, ns, n_chains, info, scal, vout);
 }
 
 // ------------------------------------------------------------------ adjoint contraction
@@ -367,14 +378,14 @@ __global__ void to_f32_kernel(const void* __restrict__ src, void* dst, int64_t p
 // pass 2 adds them in a fixed order (every block gets the same mean) and
 // writes y~.
 template <bool CPLX>
-__global__ void __launch_bounds__(kVecThreads) center_partial_kernel(
+__device__ __forceinline__ void center_partial_body(int bx, int gx, 
     const void* __restrict__ yv, const double* __restrict__ weights, int64_t ns, double* red,
     const double* scal) {
   if (scal[SC_DONE] != 0.0) return;
   const double invn = 1.0 / (double)ns;
   double sr = 0.0, si = 0.0;
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
-       s += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t s = bx * (int64_t)blockDim.x + threadIdx.x; s < ns;
+       s += (int64_t)gx * blockDim.x) {
     const double w = weights ? weights[s] : invn;
     if (CPLX) {
       const double2 y = reinterpret_cast<const double2*>(yv)[s];
@@ -387,21 +398,28 @@ __global__ void __launch_bounds__(kVecThreads) center_partial_kernel(
   const double br = block_sum(sr);
   const double bi = block_sum(si);
   if (threadIdx.x == 0) {
-    red[2 * kVecBlocks + blockIdx.x] = br;
-    red[3 * kVecBlocks + blockIdx.x] = bi;
+    red[2 * kVecBlocks + bx] = br;
+    red[3 * kVecBlocks + bx] = bi;
   }
 }
 
 template <bool CPLX>
-__global__ void __launch_bounds__(kVecThreads) center_apply_kernel(
+__global__ void __launch_bounds__(kVecThreads) center_partial_kernel(
+    const void* __restrict__ yv, const double* __restrict__ weights, int64_t ns, double* red,
+    const double* scal) {
+  center_partial_body<CPLX>(blockIdx.x, gridDim.x, yv, weights, ns, red, scal);
+}
+
+template <bool CPLX>
+__device__ __forceinline__ void center_apply_body(int bx, int gx, 
     const void* __restrict__ yv, void* vout, const double* __restrict__ weights, int64_t ns,
     const double* red, const double* scal) {
   if (scal[SC_DONE] != 0.0) return;
   const double mr = sum_partials(red + 2 * kVecBlocks);
   const double mi = sum_partials(red + 3 * kVecBlocks);
   const double invn = 1.0 / (double)ns;
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
-       s += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t s = bx * (int64_t)blockDim.x + threadIdx.x; s < ns;
+       s += (int64_t)gx * blockDim.x) {
     const double w = weights ? weights[s] : invn;
     if (CPLX) {
       const double2 y = reinterpret_cast<const double2*>(yv)[s];
@@ -412,10 +430,17 @@ __global__ void __launch_bounds__(kVecThreads) center_apply_kernel(
   }
 }
 
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) center_apply_kernel(
+    const void* __restrict__ yv, void* vout, const double* __restrict__ weights, int64_t ns,
+    const double* red, const double* scal) {
+  center_apply_body<CPLX>(blockIdx.x, gridDim.x, yv, vout, weights, ns, red, scal);
+}
+
 // out = sum_z part[z] (+ eps * p);  red[b] = sum conj(p) . out (if p given).
 // The element X'[m][n] (no parameter) is forced to 0.
 template <bool CPLX>
-__global__ void __launch_bounds__(kVecThreads) reduce_parts_kernel(
+__device__ __forceinline__ void reduce_parts_body(int bx, int gx, 
     const void* __restrict__ partv, int splits, int64_t pa, int64_t corner, void* outv,
     const void* __restrict__ pv, double eps, double* red, const double* scal) {
   if (scal && scal[SC_DONE] != 0.0) return;
@@ -423,8 +448,8 @@ __global__ void __launch_bounds__(kVecThreads) reduce_parts_kernel(
   DT* out = reinterpret_cast<DT*>(outv);
   const DT* p = reinterpret_cast<const DT*>(pv);
   double dot = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pa;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < pa;
+       e += (int64_t)gx * blockDim.x) {
     DT acc = D<CPLX>::zero();
     for (int z = 0; z < splits; ++z) {
       if constexpr (CPLX) {
@@ -442,30 +467,43 @@ __global__ void __launch_bounds__(kVecThreads) reduce_parts_kernel(
   }
   if (red) {
     double b = block_sum(dot);
-    if (threadIdx.x == 0) red[blockIdx.x] = b;
+    if (threadIdx.x == 0) red[bx] = b;
   }
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) reduce_parts_kernel(
+    const void* __restrict__ partv, int splits, int64_t pa, int64_t corner, void* outv,
+    const void* __restrict__ pv, double eps, double* red, const double* scal) {
+  reduce_parts_body<CPLX>(blockIdx.x, gridDim.x, partv, splits, pa, corner, outv, pv, eps, red, scal);
 }
 
 // x = 0, r = p = F, rs = ||F||^2 (run after F was reduced into r)
 template <bool CPLX>
-__global__ void __launch_bounds__(kVecThreads) cg_init_kernel(void* xv, void* rv, void* pv,
+__device__ __forceinline__ void cg_init_body(int bx, int gx, void* xv, void* rv, void* pv,
                                                               int64_t pa, double* red) {
   using DT = typename D<CPLX>::T;
   DT* x = reinterpret_cast<DT*>(xv);
   DT* r = reinterpret_cast<DT*>(rv);
   DT* p = reinterpret_cast<DT*>(pv);
   double nn = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pa;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < pa;
+       e += (int64_t)gx * blockDim.x) {
     x[e] = D<CPLX>::zero();
     p[e] = r[e];
     nn += norm2(r[e]);
   }
   double b = block_sum(nn);
-  if (threadIdx.x == 0) red[kVecBlocks + blockIdx.x] = b;
+  if (threadIdx.x == 0) red[kVecBlocks + bx] = b;
 }
 
-__global__ void cg_init_scalars_kernel(const double* red, double* scal, double rtol) {
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) cg_init_kernel(void* xv, void* rv, void* pv,
+                                                              int64_t pa, double* red) {
+  cg_init_body<CPLX>(blockIdx.x, gridDim.x, xv, rv, pv, pa, red);
+}
+
+__device__ __forceinline__ void cg_init_scalars_body(int bx, int gx, const double* red, double* scal, double rtol) {
   double rs = sum_partials(red + kVecBlocks);
   if (threadIdx.x == 0) {
     scal[SC_RS0] = rs;
@@ -480,9 +518,13 @@ __global__ void cg_init_scalars_kernel(const double* red, double* scal, double r
   }
 }
 
+__global__ void cg_init_scalars_kernel(const double* red, double* scal, double rtol) {
+  cg_init_scalars_body(blockIdx.x, gridDim.x, red, scal, rtol);
+}
+
 // alpha = rs / p^H A p; x += alpha p; r -= alpha A p; red2 = ||r||^2 partials
 template <bool CPLX>
-__global__ void __launch_bounds__(kVecThreads) cg_step_x_kernel(void* xv, void* rv,
+__device__ __forceinline__ void cg_step_x_body(int bx, int gx, void* xv, void* rv,
                                                                 const void* pv, const void* apv,
                                                                 int64_t pa, double* red,
                                                                 double* scal, int it) {
@@ -496,20 +538,28 @@ __global__ void __launch_bounds__(kVecThreads) cg_step_x_kernel(void* xv, void* 
   const double rs = scal[(it & 1) ? SC_RS1 : SC_RS0];
   const double alpha = rs / pap;
   double nn = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pa;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < pa;
+       e += (int64_t)gx * blockDim.x) {
     x[e] = axpy(alpha, p[e], x[e]);
     DT rr = axpy(-alpha, ap[e], r[e]);
     r[e] = rr;
     nn += norm2(rr);
   }
   double b = block_sum(nn);
-  if (threadIdx.x == 0) red[kVecBlocks + blockIdx.x] = b;
+  if (threadIdx.x == 0) red[kVecBlocks + bx] = b;
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) cg_step_x_kernel(void* xv, void* rv,
+                                                                const void* pv, const void* apv,
+                                                                int64_t pa, double* red,
+                                                                double* scal, int it) {
+  cg_step_x_body<CPLX>(blockIdx.x, gridDim.x, xv, rv, pv, apv, pa, red, scal, it);
 }
 
 // beta = rs_new / rs; p = r + beta p; convergence test on ||r|| <= rtol ||F||
 template <bool CPLX>
-__global__ void __launch_bounds__(kVecThreads) cg_step_p_kernel(const void* rv, void* pv,
+__device__ __forceinline__ void cg_step_p_body(int bx, int gx, const void* rv, void* pv,
                                                                 int64_t pa, const double* red,
                                                                 double* scal, int it,
                                                                 double rtol) {
@@ -524,11 +574,11 @@ __global__ void __launch_bounds__(kVecThreads) cg_step_p_kernel(const void* rv, 
   const bool bad = !isfinite(rs_new);
   if (!conv && !bad) {
     const double beta = rs_new / rs;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pa;
-         e += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < pa;
+         e += (int64_t)gx * blockDim.x)
       p[e] = axpy(beta, p[e], r[e]);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (bx == 0 && threadIdx.x == 0) {
     scal[(it & 1) ? SC_RS0 : SC_RS1] = rs_new;
     scal[SC_ITERS] = (double)(it + 1);
     if (conv || bad) scal[SC_DONE] = 1.0;
@@ -536,17 +586,25 @@ __global__ void __launch_bounds__(kVecThreads) cg_step_p_kernel(const void* rv, 
   }
 }
 
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) cg_step_p_kernel(const void* rv, void* pv,
+                                                                int64_t pa, const double* red,
+                                                                double* scal, int it,
+                                                                double rtol) {
+  cg_step_p_body<CPLX>(blockIdx.x, gridDim.x, rv, pv, pa, red, scal, it, rtol);
+}
+
 // alpha <- alpha - lr delta (FP64 master), delta in the augmented layout; info.
 template <bool CPLX>
-__global__ void sr_update_kernel(double* a, double* b, double* w, int n, int m,
+__device__ __forceinline__ void sr_update_body(int bx, int gx, double* a, double* b, double* w, int n, int m,
                                  const void* __restrict__ xv, double lr, const double* scal,
                                  double* info, int n_iter_final, double rtol) {
   using DT = typename D<CPLX>::T;
   const DT* x = reinterpret_cast<const DT*>(xv);
   const int na = n + 1;
   const int64_t tot = (int64_t)(m + 1) * na;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gx * blockDim.x) {
     int j = (int)(e / na), i = (int)(e % na);
     double* dst;
     if (j < m && i < n) dst = w + (CPLX ? 2 : 1) * ((int64_t)j * n + i);
@@ -560,7 +618,7 @@ __global__ void sr_update_kernel(double* a, double* b, double* w, int n, int m,
       dst[0] -= lr * x[e];
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (bx == 0 && threadIdx.x == 0) {
     const double iters = scal[SC_ITERS];
     const double fn = scal[SC_FNORM];
     const double rs = scal[((int)iters & 1) ? SC_RS1 : SC_RS0];
@@ -574,6 +632,13 @@ __global__ void sr_update_kernel(double* a, double* b, double* w, int n, int m,
     if (*reinterpret_cast<const int*>(scal + SC_ERR) != 0) flags |= 1 << NK_ERR_TIMEOUT;
     info[NK_INFO_FLAGS] = (double)flags;
   }
+}
+
+template <bool CPLX>
+__global__ void sr_update_kernel(double* a, double* b, double* w, int n, int m,
+                                 const void* __restrict__ xv, double lr, const double* scal,
+                                 double* info, int n_iter_final, double rtol) {
+  sr_update_body<CPLX>(blockIdx.x, gridDim.x, a, b, w, n, m, xv, lr, scal, info, n_iter_final, rtol);
 }
 
 // grad (a, b, W order) from the augmented adjoint result
@@ -598,6 +663,82 @@ __global__ void scatter_grad_kernel(const void* __restrict__ gv, int n, int m, d
       grad[k] = g[e];
     }
   }
+}
+
+// ------------------------------------------------------------------ batched kernels
+// The same kernels for every problem of an SR batch: blockIdx.y selects the
+// problem (its SrDesc), blockIdx.x runs over the same fixed grid as the
+// single-problem launch, so each problem's reductions keep their order and a
+// batched step computes exactly what nk_sr_step computes for each problem.
+
+template <bool CPLX>
+__global__ void __launch_bounds__(1024) stats_batch(const SrDesc* __restrict__ D) {
+  const SrDesc& d = D[blockIdx.y];
+  stats_body<CPLX>(0, 1, d.eloc, d.weights, d.ns, d.n_chains, d.info, d.scal, d.v);
+}
+
+__global__ void flags_reset_batch(const SrDesc* __restrict__ D) {
+  if (threadIdx.x == 0) {
+    D[blockIdx.y].scal[SC_DONE] = 0.0;
+    D[blockIdx.y].scal[SC_ERR] = 0.0;
+  }
+}
+
+// in_cg = 0: F into r (no shift, no inner product); 1: S p + eps p into ap
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) reduce_parts_batch(const SrDesc* __restrict__ D,
+                                                                  int in_cg, double eps) {
+  const SrDesc& d = D[blockIdx.y];
+  if (in_cg)
+    reduce_parts_body<CPLX>(blockIdx.x, gridDim.x, d.part, d.splits, d.pa, d.corner, d.ap, d.p,
+                            eps, d.red, d.scal);
+  else
+    reduce_parts_body<CPLX>(blockIdx.x, gridDim.x, d.part, d.splits, d.pa, d.corner, d.r,
+                            nullptr, 0.0, nullptr, nullptr);
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) cg_init_batch(const SrDesc* __restrict__ D) {
+  const SrDesc& d = D[blockIdx.y];
+  cg_init_body<CPLX>(blockIdx.x, gridDim.x, d.x, d.r, d.p, d.pa, d.red);
+}
+
+__global__ void cg_init_scalars_batch(const SrDesc* __restrict__ D, double rtol) {
+  const SrDesc& d = D[blockIdx.y];
+  cg_init_scalars_body(0, 1, d.red, d.scal, rtol);
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) center_partial_batch(const SrDesc* __restrict__ D) {
+  const SrDesc& d = D[blockIdx.y];
+  center_partial_body<CPLX>(blockIdx.x, gridDim.x, d.y, d.weights, d.ns, d.red, d.scal);
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) center_apply_batch(const SrDesc* __restrict__ D) {
+  const SrDesc& d = D[blockIdx.y];
+  center_apply_body<CPLX>(blockIdx.x, gridDim.x, d.y, d.v, d.weights, d.ns, d.red, d.scal);
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) cg_step_x_batch(const SrDesc* __restrict__ D,
+                                                               int it) {
+  const SrDesc& d = D[blockIdx.y];
+  cg_step_x_body<CPLX>(blockIdx.x, gridDim.x, d.x, d.r, d.p, d.ap, d.pa, d.red, d.scal, it);
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) cg_step_p_batch(const SrDesc* __restrict__ D,
+                                                               int it, double rtol) {
+  const SrDesc& d = D[blockIdx.y];
+  cg_step_p_body<CPLX>(blockIdx.x, gridDim.x, d.r, d.p, d.pa, d.red, d.scal, it, rtol);
+}
+
+template <bool CPLX>
+__global__ void sr_update_batch(const SrDesc* __restrict__ D, double lr, int n_cg, double rtol) {
+  const SrDesc& d = D[blockIdx.y];
+  sr_update_body<CPLX>(blockIdx.x, gridDim.x, d.a, d.b, d.w, d.n, d.m, d.x, lr, d.scal, d.info,
+                       n_cg, rtol);
 }
 
 // ------------------------------------------------------------------ drivers
@@ -710,6 +851,241 @@ nk_status run_sr_step(nk_rbm* r, const int8_t* sigma, const void* t, const doubl
                            prec, (char*)scratch, info, st);
   return sr_step_t<false>(r, sigma, t, eloc, weights, ns, n_chains, diag_shift, lr, n_cg, cg_rtol,
                           prec, (char*)scratch, info, st);
+}
+
+// ------------------------------------------------------------------ SR batches
+
+// Split count of item i of a batch: the RBM's own setting, else a batch-wide
+// default that spreads about two waves of adjoint CTAs over all problems.
+static int batch_item_splits(const nk_sr_batch_item* items, int n_inst, int i, int prec) {
+  const nk_rbm* r = items[i].rbm;
+  SrLayout L(r->n, r->m, r->is_complex, items[i].ns);
+  if (r->sr_splits > 0) return sr_choose_splits(L, prec, r->sr_splits);
+  int64_t tiles = 0;
+  for (int k = 0; k < n_inst; ++k) {
+    const int hj = items[k].rbm->is_complex ? 64 : 128;
+    tiles += (items[k].rbm->m + 1 + hj - 1) / hj;
+  }
+  const int s = (int)std::max<int64_t>(1, (2 * 152) / std::max<int64_t>(tiles, 1));
+  return sr_choose_splits(L, prec, s);
+}
+
+// Problems in descriptor order: complex ones first, then real ones (items order
+// within each field).
+static std::vector<int> batch_order(const nk_sr_batch_item* items, int n_inst) {
+  std::vector<int> order;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < n_inst; ++i)
+      if ((items[i].rbm->is_complex != 0) == (pass == 0)) order.push_back(i);
+  return order;
+}
+
+nk_status sr_batch_check(const nk_sr_batch_item* items, int n_inst, int prec) {
+  if (n_inst < 1 || !items) return fail(NK_ERR_INVALID_ARG, "SR batch: no items");
+  if (prec != NK_PREC_BF16X2)
+    return fail(NK_ERR_UNSUPPORTED, "SR batch: only the tensor-core precision NK_PREC_BF16X2");
+  for (int i = 0; i < n_inst; ++i) {
+    const nk_sr_batch_item& it = items[i];
+    const nk_rbm* r = it.rbm;
+    if (!r || !r->ws || !r->a || !r->b || !r->w)
+      return fail(NK_ERR_INVALID_ARG, "SR batch: item %d has no RBM or workspace", i);
+    if (it.ns < 1 || !it.sigma || !it.t || !it.eloc || !it.scratch || !it.info_out)
+      return fail(NK_ERR_INVALID_ARG, "SR batch: item %d: NULL pointer or ns < 1", i);
+    if (it.n_chains < 0 || (it.n_chains > 0 && it.ns % it.n_chains))
+      return fail(NK_ERR_SHAPE, "SR batch: item %d: ns not a multiple of n_chains", i);
+    if (((uintptr_t)it.scratch) & 255)
+      return fail(NK_ERR_INVALID_ARG, "SR batch: item %d: scratch not 256-byte aligned", i);
+    if (it.scratch_bytes < sr_scratch_bytes(r->n, r->m, r->is_complex, it.ns))
+      return fail(NK_ERR_SHAPE, "SR batch: item %d: scratch too small", i);
+    if (!tc_supported_shape(r->n, r->m))
+      return fail(NK_ERR_UNSUPPORTED, "SR batch: item %d: n + 1 > 448", i);
+  }
+  return NK_OK;
+}
+
+size_t sr_batch_desc_bytes(int n_inst) { return (size_t)std::max(n_inst, 0) * sizeof(SrDesc); }
+
+nk_status sr_batch_describe(const nk_sr_batch_item* items, int n_inst, int prec, void* host,
+                            size_t bytes) {
+  if (nk_status e = sr_batch_check(items, n_inst, prec)) return e;
+  if (!host || bytes < sr_batch_desc_bytes(n_inst))
+    return fail(NK_ERR_SHAPE, "SR batch: descriptor buffer of %zu B, need %zu B", bytes,
+                sr_batch_desc_bytes(n_inst));
+  const std::vector<int> order = batch_order(items, n_inst);
+  SrDesc* out = reinterpret_cast<SrDesc*>(host);
+  for (int z = 0; z < n_inst; ++z) {
+    const nk_sr_batch_item& it = items[order[z]];
+    nk_rbm* r = it.rbm;
+    const int cplx = r->is_complex ? 1 : 0;
+    SrLayout L(r->n, r->m, cplx, it.ns);
+    WsLayout W(r->n, r->m, cplx);
+    SrDesc d;
+    memset(&d, 0, sizeof(d));
+    char* sc = (char*)it.scratch;
+    if (!tc_make_map(&d.fwd_map, sc + L.xbf, 2LL * L.mt1 * 128, L.na64, L.na64, 128))
+      return NK_ERR_CUDA;
+    if (!tc_make_map(&d.adj_map, sc + L.sigt, L.na64, L.ns8, L.ns8, L.na64 / 2))
+      return NK_ERR_CUDA;
+    d.splits = batch_item_splits(items, n_inst, order[z], prec);
+    d.n = r->n;
+    d.m = r->m;
+    d.n_chains = it.n_chains;
+    d.na64 = L.na64;
+    d.mt1 = L.mt1;
+    d.mp = W.mp;
+    d.wmt = W.mt;
+    d.wna64 = W.na64;
+    d.ns = it.ns;
+    d.pa = L.pa;
+    d.corner = (int64_t)r->m * L.na + r->n;
+    d.ns8 = L.ns8;
+    d.sigma = it.sigma;
+    d.T = it.t;
+    d.eloc = it.eloc;
+    d.weights = it.weights;
+    d.a = r->a;
+    d.b = r->b;
+    d.w = r->w;
+    d.ws = (char*)r->ws;
+    d.ws_a32 = W.a32;
+    d.ws_b32 = W.b32;
+    d.ws_wt = W.wt;
+    d.ws_tab = W.tab;
+    d.ws_xw = W.xw;
+    d.ws_wbf = W.wbf;
+    d.x = sc + L.x;
+    d.r = sc + L.r;
+    d.p = sc + L.p;
+    d.ap = sc + L.ap;
+    d.part = sc + L.part;
+    d.y = sc + L.y;
+    d.v = sc + L.v;
+    d.sigt = sc + L.sigt;
+    d.xbf = sc + L.xbf;
+    d.red = (double*)(sc + L.red);
+    d.scal = (double*)(sc + L.scal);
+    d.done = d.scal + SC_DONE;
+    d.info = it.info_out;
+    memcpy(&out[z], &d, sizeof(d));
+  }
+  return NK_OK;
+}
+
+// one sub-batch: problems [z0, z0 + G) of the descriptor order, all of one field
+template <bool CPLX>
+static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
+                                const std::vector<int>& order, int z0, int G,
+                                const SrDesc* D, double eps, double lr, int n_cg, double rtol,
+                                int prec, cudaStream_t st) {
+  const SrDesc* Dg = D + z0;
+  FwdBatch fb;
+  AdjBatch ab;
+  memset(&fb, 0, sizeof(fb));
+  memset(&ab, 0, sizeof(ab));
+  int max_fwd = 1, max_adj = 1, max_sp = 1, max_na64 = 64;
+  int64_t max_ns8 = 8, max_xp = 1, max_wp = 1, max_work = 1, max_minb = 1;
+  const int HJ = CPLX ? 64 : 128;
+  for (int z = 0; z < G; ++z) {
+    const nk_sr_batch_item& it = items[order[z0 + z]];
+    const nk_rbm* r = it.rbm;
+    SrLayout L(r->n, r->m, CPLX, it.ns);
+    WsLayout W(r->n, r->m, CPLX);
+    char* sc = (char*)it.scratch;
+    double* scal = (double*)(sc + L.scal);
+    const int splits = batch_item_splits(items, n_inst, order[z0 + z], prec);
+    FwdTcArgs& fa = fb.a[z];
+    fa.sigma = it.sigma;
+    fa.ns = it.ns;
+    fa.n = r->n;
+    fa.m = r->m;
+    fa.cplx = CPLX;
+    fa.mode = 0;
+    fa.mt = L.mt1;
+    fa.na64 = L.na64;
+    fa.rows = r->m + 1;
+    fa.T = it.t;
+    fa.y = sc + L.y;
+    fa.skip = scal + SC_DONE;
+    fa.err = reinterpret_cast<int*>(scal + SC_ERR);
+    fa.nseg = 1;
+    fb.map[z] = &Dg[z].fwd_map;
+    fb.tiles[z] = (int)((it.ns + 127) / 128);
+    AdjTcArgs& aa = ab.a[z];
+    aa.T = it.t;
+    aa.v = sc + L.v;
+    aa.ns = it.ns;
+    aa.n = r->n;
+    aa.m = r->m;
+    aa.cplx = CPLX;
+    aa.na64 = L.na64;
+    aa.splits = splits;
+    aa.part = sc + L.part;
+    aa.skip = nullptr;
+    aa.err = reinterpret_cast<int*>(scal + SC_ERR);
+    ab.map[z] = &Dg[z].adj_map;
+    ab.chunk[z] = round_up(std::max<int64_t>((it.ns + splits - 1) / splits, 1), 64);
+    ab.tiles[z] = (r->m + 1 + HJ - 1) / HJ;
+    ab.splits[z] = splits;
+    max_fwd = std::max(max_fwd, fb.tiles[z]);
+    max_adj = std::max(max_adj, ab.tiles[z]);
+    max_sp = std::max(max_sp, splits);
+    max_na64 = std::max(max_na64, L.na64);
+    max_ns8 = std::max<int64_t>(max_ns8, L.ns8);
+    max_xp = std::max<int64_t>(max_xp, (int64_t)L.mt1 * 128 * L.na64);
+    max_wp = std::max<int64_t>(max_wp, (int64_t)W.mt * 128 * W.na64);
+    max_work = std::max<int64_t>(max_work, (int64_t)W.mp * (r->n + 1));
+    max_minb = std::max<int64_t>(max_minb, (std::max(W.mp, r->n) + 255) / 256);
+  }
+  const dim3 vg(kVecBlocks, G), one(1, G);
+  stats_batch<CPLX><<<one, 1024, 0, st>>>(Dg);
+  flags_reset_batch<<<one, 32, 0, st>>>(Dg);
+  if (nk_status e = check_launch("nk_sr_step_batch(stats)")) return e;
+  if (nk_status e = launch_sigma_t_batch(Dg, G, max_ns8, max_na64, st)) return e;
+  if (nk_status e = launch_adj_tc_batch(ab, G, CPLX, max_adj, max_sp, max_na64, st)) return e;
+  reduce_parts_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, 0, 0.0);
+  cg_init_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg);
+  cg_init_scalars_batch<<<one, 32, 0, st>>>(Dg, rtol);
+  if (nk_status e = check_launch("nk_sr_step_batch(force)")) return e;
+  for (int z = 0; z < G; ++z) ab.a[z].skip = fb.a[z].skip;
+  for (int it = 0; it < n_cg; ++it) {
+    if (nk_status e = launch_bplanes_p_batch(Dg, G, CPLX, max_xp, st)) return e;
+    if (nk_status e = launch_fwd_tc_batch(fb, G, CPLX, max_fwd, max_na64, st)) return e;
+    center_partial_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg);
+    center_apply_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg);
+    if (nk_status e = launch_adj_tc_batch(ab, G, CPLX, max_adj, max_sp, max_na64, st)) return e;
+    reduce_parts_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, 1, eps);
+    cg_step_x_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, it);
+    cg_step_p_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, it, rtol);
+    if (nk_status e = check_launch("nk_sr_step_batch(cg)")) return e;
+  }
+  sr_update_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, lr, n_cg, rtol);
+  if (nk_status e = check_launch("nk_sr_step_batch(update)")) return e;
+  if (nk_status e = launch_prepare_batch(Dg, G, CPLX, max_work, max_minb, st)) return e;
+  return launch_bplanes_rbm_batch(Dg, G, CPLX, max_wp, st);
+}
+
+nk_status run_sr_step_batch(const nk_sr_batch_item* items, int n_inst, const void* desc_dev,
+                            double eps, double lr, int n_cg, double rtol, int prec,
+                            cudaStream_t st) {
+  if (nk_status e = sr_batch_check(items, n_inst, prec)) return e;
+  if (!desc_dev || (((uintptr_t)desc_dev) & 255))
+    return fail(NK_ERR_INVALID_ARG, "nk_sr_step_batch: descriptors NULL or not 256-byte aligned");
+  const std::vector<int> order = batch_order(items, n_inst);
+  const SrDesc* D = reinterpret_cast<const SrDesc*>(desc_dev);
+  int z = 0;
+  while (z < n_inst) {
+    const bool cplx = items[order[z]].rbm->is_complex != 0;
+    int G = 0;
+    while (z + G < n_inst && G < kBatchMax && (items[order[z + G]].rbm->is_complex != 0) == cplx)
+      ++G;
+    nk_status e = cplx ? sr_batch_group<true>(items, n_inst, order, z, G, D, eps, lr, n_cg, rtol,
+                                              prec, st)
+                       : sr_batch_group<false>(items, n_inst, order, z, G, D, eps, lr, n_cg, rtol,
+                                               prec, st);
+    if (e) return e;
+    z += G;
+  }
+  return NK_OK;
 }
 
 // ------------------------------------------------------------------ autotuner

@@ -114,15 +114,17 @@ __device__ __forceinline__ void split_bf16(double x, uint32_t& hi, uint32_t& lo)
 // ------------------------------------------------------------------ B planes
 
 template <bool CPLX, bool FROM_RBM>
-__global__ void bplanes_kernel(const double* __restrict__ src, int src_rows, int ncols, int ld,
-                               const double* __restrict__ w, const double* __restrict__ b, int n,
-                               int mt, int na64, uint16_t* __restrict__ planes,
-                               const double* skip) {
+__device__ __forceinline__ void bplanes_body(int bx, int gx, const double* __restrict__ src,
+                                             int src_rows, int ncols, int ld,
+                                             const double* __restrict__ w,
+                                             const double* __restrict__ b, int n, int mt,
+                                             int na64, uint16_t* __restrict__ planes,
+                                             const double* skip) {
   if (skip && *skip != 0.0) return;
   const int HJ = CPLX ? 64 : 128;
   const int64_t plane = (int64_t)mt * 128 * na64;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < plane;
+       e += (int64_t)gx * blockDim.x) {
     const int row = (int)(e / na64), i = (int)(e % na64);
     const int jt = row >> 7, rr = row & 127;
     const int j = CPLX ? jt * HJ + (rr & 63) : jt * HJ + rr;
@@ -141,6 +143,15 @@ __global__ void bplanes_kernel(const double* __restrict__ src, int src_rows, int
     planes[e] = (uint16_t)hi;
     planes[plane + e] = (uint16_t)lo;
   }
+}
+
+template <bool CPLX, bool FROM_RBM>
+__global__ void bplanes_kernel(const double* __restrict__ src, int src_rows, int ncols, int ld,
+                               const double* __restrict__ w, const double* __restrict__ b, int n,
+                               int mt, int na64, uint16_t* __restrict__ planes,
+                               const double* skip) {
+  bplanes_body<CPLX, FROM_RBM>(blockIdx.x, gridDim.x, src, src_rows, ncols, ld, w, b, n, mt,
+                               na64, planes, skip);
 }
 
 nk_status launch_bplanes_from_f64(const void* src, int src_rows, int ncols, int ld, int cplx,
@@ -175,11 +186,11 @@ nk_status launch_bplanes_from_rbm(const nk_rbm* r, cudaStream_t st) {
 
 // ------------------------------------------------------------------ sigma'^T
 
-__global__ void sigma_t_kernel(const int8_t* __restrict__ sigma, int64_t ns, int n, int na64,
-                               int64_t ns8, uint16_t* __restrict__ out) {
-  const int i = blockIdx.y;
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns8;
-       s += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void sigma_t_body(int bx, int gx, int i,
+                                             const int8_t* __restrict__ sigma, int64_t ns, int n,
+                                             int64_t ns8, uint16_t* __restrict__ out) {
+  for (int64_t s = bx * (int64_t)blockDim.x + threadIdx.x; s < ns8;
+       s += (int64_t)gx * blockDim.x) {
     uint16_t v = 0;
     if (s < ns) {
       if (i < n) v = sigma[s * n + i] > 0 ? 0x3F80 : 0xBF80;
@@ -187,6 +198,12 @@ __global__ void sigma_t_kernel(const int8_t* __restrict__ sigma, int64_t ns, int
     }
     out[(int64_t)i * ns8 + s] = v;
   }
+}
+
+__global__ void sigma_t_kernel(const int8_t* __restrict__ sigma, int64_t ns, int n, int na64,
+                               int64_t ns8, uint16_t* __restrict__ out) {
+  (void)na64;
+  sigma_t_body(blockIdx.x, gridDim.x, blockIdx.y, sigma, ns, n, ns8, out);
 }
 
 nk_status launch_sigma_t(const int8_t* sigma, int64_t ns, int n, int na64, void* out,
@@ -215,8 +232,8 @@ __device__ __forceinline__ uint32_t sig_bits(const int8_t* sigma, int64_t s, int
 }
 
 template <bool CPLX>
-__global__ void __launch_bounds__(kFwdThreads, 1)
-    fwd_tc_kernel(const __grid_constant__ CUtensorMap tb, FwdTcArgs A) {
+__device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcArgs& A, int bx,
+                                            int seg) {
   if (A.skip && *A.skip != 0.0) return;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = align1024(smraw);
@@ -229,7 +246,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   uint64_t* tempty = tfull + 2;
   uint32_t* slot = reinterpret_cast<uint32_t*>(tempty + 2);
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int64_t s0 = (int64_t)blockIdx.x * 128;
+  const int64_t s0 = (int64_t)bx * 128;
 
   if (tid == 0) {
     for (int st = 0; st < kFwdStages; ++st) {
@@ -261,8 +278,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = *slot;
-  // hidden tiles of this CTA: all, or one half (blockIdx.y) when the launch is split
-  const int seg = blockIdx.y;
+  // hidden tiles of this CTA: all, or one half (seg) when the launch is split
   const int jt_begin = A.mt * seg / A.nseg, jt_end = A.mt * (seg + 1) / A.nseg;
   const int total_it = (jt_end - jt_begin) * KC;
   bool bad = false;
@@ -277,8 +293,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
           break;
         }
         mbar_arrive_expect_tx(&full[st], kStageB);
-        tma_load_2d(sB + (size_t)st * kStageB, &tb, kc * 64, jt * 128, &full[st]);
-        tma_load_2d(sB + (size_t)st * kStageB + 16384, &tb, kc * 64, (A.mt + jt) * 128,
+        tma_load_2d(sB + (size_t)st * kStageB, tbp, kc * 64, jt * 128, &full[st]);
+        tma_load_2d(sB + (size_t)st * kStageB + 16384, tbp, kc * 64, (A.mt + jt) * 128,
                     &full[st]);
       }
     }
@@ -479,6 +495,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   }
 }
 
+template <bool CPLX>
+__global__ void __launch_bounds__(kFwdThreads, 1)
+    fwd_tc_kernel(const __grid_constant__ CUtensorMap tb, FwdTcArgs A) {
+  fwd_tc_body<CPLX>(&tb, A, blockIdx.x, blockIdx.y);
+}
+
 static size_t fwd_smem_bytes(int na64) {
   return 1024 + (size_t)(na64 / 64) * 16384 + kFwdStages * kStageB + 128;
 }
@@ -526,8 +548,8 @@ constexpr int kAdjProducerWarps = 8;
 constexpr int kAdjThreads = 64 + 32 * kAdjProducerWarps;
 
 template <bool CPLX>
-__global__ void __launch_bounds__(kAdjThreads, 1)
-    adj_tc_kernel(const __grid_constant__ CUtensorMap ts_map, AdjTcArgs A, int64_t chunk) {
+__device__ __forceinline__ void adj_tc_body(const CUtensorMap* tsp, const AdjTcArgs& A,
+                                            int64_t chunk, int bx, int by) {
   if (A.skip && *A.skip != 0.0) return;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = align1024(smraw);
@@ -539,8 +561,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
   uint32_t* slot = reinterpret_cast<uint32_t*>(done + 1);
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int HJ = CPLX ? 64 : 128;
-  const int j0 = blockIdx.x * HJ;
-  const int z = blockIdx.y;
+  const int j0 = bx * HJ;
+  const int z = by;
   const int64_t sb = (int64_t)z * chunk;
   const int64_t se = std::min<int64_t>(A.ns, sb + chunk);
   const int nit = se > sb ? (int)((se - sb + 63) / 64) : 0;
@@ -571,8 +593,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
         }
         unsigned char* B = sm + (size_t)st * stage_bytes + 32768;
         mbar_arrive_expect_tx(&full[st], (uint32_t)NB * 128u);
-        tma_load_2d(B, &ts_map, (int)(sb + (int64_t)it * 64), 0, &full[st]);
-        tma_load_2d(B + (size_t)NH * 128, &ts_map, (int)(sb + (int64_t)it * 64), NH, &full[st]);
+        tma_load_2d(B, tsp, (int)(sb + (int64_t)it * 64), 0, &full[st]);
+        tma_load_2d(B + (size_t)NH * 128, tsp, (int)(sb + (int64_t)it * 64), NH, &full[st]);
       }
     }
   } else if (w == 1) {
@@ -758,6 +780,12 @@ __global__ void __launch_bounds__(kAdjThreads, 1)
   }
 }
 
+template <bool CPLX>
+__global__ void __launch_bounds__(kAdjThreads, 1)
+    adj_tc_kernel(const __grid_constant__ CUtensorMap ts_map, AdjTcArgs A, int64_t chunk) {
+  adj_tc_body<CPLX>(&ts_map, A, chunk, blockIdx.x, blockIdx.y);
+}
+
 int adj_tc_splits(int n, int m, int cplx, int64_t ns) {
   (void)n;
   const int HJ = cplx ? 64 : 128;
@@ -791,6 +819,119 @@ nk_status launch_adj_tc(const AdjTcArgs& A, const void* sigma_t, cudaStream_t st
     adj_tc_kernel<false><<<grid, kAdjThreads, smem, st>>>(map, A, chunk);
   }
   return check_launch("adj_tc");
+}
+
+// ------------------------------------------------------------------ batches
+
+// The tensor maps of a batch live in global memory (written before the launch);
+// make them visible to the TMA unit's tensor-map reads.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kFwdThreads, 1)
+    fwd_tc_batch(const __grid_constant__ FwdBatch P) {
+  const int z = blockIdx.z;
+  if ((int)blockIdx.x >= P.tiles[z]) return;
+  if (threadIdx.x == 0) tensormap_acquire(P.map[z]);
+  fwd_tc_body<CPLX>(P.map[z], P.a[z], blockIdx.x, 0);
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kAdjThreads, 1)
+    adj_tc_batch(const __grid_constant__ AdjBatch P) {
+  const int z = blockIdx.z;
+  if ((int)blockIdx.x >= P.tiles[z] || (int)blockIdx.y >= P.splits[z]) return;
+  if (threadIdx.x == 0) tensormap_acquire(P.map[z]);
+  adj_tc_body<CPLX>(P.map[z], P.a[z], P.chunk[z], blockIdx.x, blockIdx.y);
+}
+
+__global__ void sigma_t_batch(const SrDesc* __restrict__ D) {
+  const SrDesc& d = D[blockIdx.z];
+  if ((int)blockIdx.y >= d.na64) return;
+  sigma_t_body(blockIdx.x, gridDim.x, blockIdx.y, d.sigma, d.ns, d.n, d.ns8,
+               reinterpret_cast<uint16_t*>(d.sigt));
+}
+
+template <bool CPLX>
+__global__ void bplanes_p_batch(const SrDesc* __restrict__ D) {
+  const SrDesc& d = D[blockIdx.y];
+  bplanes_body<CPLX, false>(blockIdx.x, gridDim.x, reinterpret_cast<const double*>(d.p),
+                            d.m + 1, d.n + 1, d.n + 1, nullptr, nullptr, 0, d.mt1, d.na64,
+                            reinterpret_cast<uint16_t*>(d.xbf), d.done);
+}
+
+template <bool CPLX>
+__global__ void bplanes_rbm_batch(const SrDesc* __restrict__ D) {
+  const SrDesc& d = D[blockIdx.y];
+  bplanes_body<CPLX, true>(blockIdx.x, gridDim.x, nullptr, d.m, d.n + 1, 0, d.w, d.b, d.n,
+                           d.wmt, d.wna64, reinterpret_cast<uint16_t*>(d.ws + d.ws_wbf),
+                           nullptr);
+}
+
+static unsigned vec_blocks(int64_t elems) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((elems + 255) / 256, 152 * 8));
+}
+
+nk_status launch_fwd_tc_batch(const FwdBatch& P, int G, int cplx, int max_tiles, int max_na64,
+                              cudaStream_t st) {
+  const size_t smem = fwd_smem_bytes(max_na64);
+  const dim3 grid((unsigned)max_tiles, 1, (unsigned)G);
+  if (cplx) {
+    if (cudaFuncSetAttribute(fwd_tc_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return fail(NK_ERR_CUDA, "fwd_tc_batch: shared memory attribute");
+    fwd_tc_batch<true><<<grid, kFwdThreads, smem, st>>>(P);
+  } else {
+    if (cudaFuncSetAttribute(fwd_tc_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return fail(NK_ERR_CUDA, "fwd_tc_batch: shared memory attribute");
+    fwd_tc_batch<false><<<grid, kFwdThreads, smem, st>>>(P);
+  }
+  return check_launch("fwd_tc_batch");
+}
+
+nk_status launch_adj_tc_batch(const AdjBatch& P, int G, int cplx, int max_tiles, int max_splits,
+                              int max_na64, cudaStream_t st) {
+  const size_t smem = 1024 + 2 * (32768 + (size_t)max_na64 * 128) + 64;
+  const dim3 grid((unsigned)max_tiles, (unsigned)max_splits, (unsigned)G);
+  if (cplx) {
+    if (cudaFuncSetAttribute(adj_tc_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return fail(NK_ERR_CUDA, "adj_tc_batch: shared memory attribute");
+    adj_tc_batch<true><<<grid, kAdjThreads, smem, st>>>(P);
+  } else {
+    if (cudaFuncSetAttribute(adj_tc_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return fail(NK_ERR_CUDA, "adj_tc_batch: shared memory attribute");
+    adj_tc_batch<false><<<grid, kAdjThreads, smem, st>>>(P);
+  }
+  return check_launch("adj_tc_batch");
+}
+
+nk_status launch_sigma_t_batch(const SrDesc* D, int G, int64_t max_ns8, int max_na64,
+                               cudaStream_t st) {
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((max_ns8 + 255) / 256, 64)),
+                  (unsigned)max_na64, (unsigned)G);
+  sigma_t_batch<<<grid, 256, 0, st>>>(D);
+  return check_launch("sigma_t_batch");
+}
+
+nk_status launch_bplanes_p_batch(const SrDesc* D, int G, int cplx, int64_t max_elems,
+                                 cudaStream_t st) {
+  const dim3 grid(vec_blocks(max_elems), (unsigned)G);
+  if (cplx) bplanes_p_batch<true><<<grid, 256, 0, st>>>(D);
+  else bplanes_p_batch<false><<<grid, 256, 0, st>>>(D);
+  return check_launch("bplanes_p_batch");
+}
+
+nk_status launch_bplanes_rbm_batch(const SrDesc* D, int G, int cplx, int64_t max_elems,
+                                   cudaStream_t st) {
+  const dim3 grid(vec_blocks(max_elems), (unsigned)G);
+  if (cplx) bplanes_rbm_batch<true><<<grid, 256, 0, st>>>(D);
+  else bplanes_rbm_batch<false><<<grid, 256, 0, st>>>(D);
+  return check_launch("bplanes_rbm_batch");
 }
 
 }  // namespace nk

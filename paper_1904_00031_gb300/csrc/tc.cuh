@@ -69,4 +69,72 @@ nk_status launch_adj_tc(const AdjTcArgs& A, const void* sigma_t, cudaStream_t st
 int adj_tc_splits(int n, int m, int cplx, int64_t ns);
 bool tc_supported_shape(int n, int m);
 
+// ------------------------------------------------------------------ batches
+// One SR problem of a batch advanced by nk_sr_step_batch: everything the
+// batched kernels read, in device memory (blockIdx.z or blockIdx.y selects the
+// problem); TMA reads the two tensor maps from here.
+struct alignas(128) SrDesc {
+  CUtensorMap fwd_map;    // B planes of the CG direction (xbf)
+  CUtensorMap adj_map;    // sigma'^T (sigt)
+  const double* done;     // scal + SC_DONE: the CG has converged
+  int splits;
+  int n, m, n_chains, na64, mt1, mp, wmt, wna64;  // wmt, wna64: B planes of W | b
+  int64_t ns, pa, corner, ns8;
+  const int8_t* sigma;
+  const void* T;
+  const double* eloc;
+  const double* weights;
+  double* a;
+  double* b;
+  double* w;
+  char* ws;
+  size_t ws_a32, ws_b32, ws_wt, ws_tab, ws_xw, ws_wbf;
+  char* x;
+  char* r;
+  char* p;
+  char* ap;
+  char* part;
+  char* y;
+  char* v;
+  char* sigt;
+  char* xbf;
+  double* red;
+  double* scal;
+  double* info;
+};
+
+// Per-launch arguments of the batched tensor-core contractions, passed as
+// kernel parameters (the kernels read their problem's fields from the constant
+// bank, as the single-problem kernels do); up to kBatchMax problems per launch.
+constexpr int kBatchMax = 64;
+struct FwdBatch {
+  FwdTcArgs a[kBatchMax];
+  const CUtensorMap* map[kBatchMax];   // in the problem's SrDesc (global memory)
+  int tiles[kBatchMax];
+};
+struct AdjBatch {
+  AdjTcArgs a[kBatchMax];
+  const CUtensorMap* map[kBatchMax];
+  int64_t chunk[kBatchMax];
+  int tiles[kBatchMax], splits[kBatchMax];
+};
+
+// Batched launches over G problems of one field (all complex or all real); the
+// max_* arguments bound the grid, and every problem's CTAs beyond its own sizes
+// return at once.
+nk_status launch_fwd_tc_batch(const FwdBatch& P, int G, int cplx, int max_tiles, int max_na64,
+                              cudaStream_t st);
+nk_status launch_adj_tc_batch(const AdjBatch& P, int G, int cplx, int max_tiles, int max_splits,
+                              int max_na64, cudaStream_t st);
+nk_status launch_sigma_t_batch(const SrDesc* D, int G, int64_t max_ns8, int max_na64,
+                               cudaStream_t st);
+// B planes of the CG direction p (skipped once converged), or of W | b
+nk_status launch_bplanes_p_batch(const SrDesc* D, int G, int cplx, int64_t max_elems,
+                                 cudaStream_t st);
+nk_status launch_bplanes_rbm_batch(const SrDesc* D, int G, int cplx, int64_t max_elems,
+                                   cudaStream_t st);
+// the derived planes of every problem's RBM (prepare.cu)
+nk_status launch_prepare_batch(const SrDesc* D, int G, int cplx, int64_t max_work,
+                               int64_t max_minb, cudaStream_t st);
+
 }  // namespace nk

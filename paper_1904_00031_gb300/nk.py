@@ -34,7 +34,7 @@ EXPORTS = (
     "nk_operator_upload", "nk_local_energy", "nk_logderiv", "nk_sr_scratch_bytes", "nk_sr_step",
     "nk_backward_scratch_bytes", "nk_rbm_logpsi_backward", "nk_sr_step_noalloc",
     "nk_metropolis_scratch_bytes", "nk_operator_moves", "nk_local_energy_scratch_bytes",
-    "nk_sr_tune",
+    "nk_sr_tune", "nk_sr_batch_desc_bytes", "nk_sr_batch_describe", "nk_sr_step_batch",
 )
 NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
@@ -52,6 +52,13 @@ class _Rbm(C.Structure):
 class _Chains(C.Structure):
     _fields_ = [("nc", C.c_int32), ("group_size", C.c_int32), ("sigma", C.c_void_p),
                 ("seed", C.c_uint64), ("counter", C.c_uint64), ("counter_dev", C.c_void_p)]
+
+
+class _SrBatchItem(C.Structure):
+    _fields_ = [("rbm", C.c_void_p), ("sigma", C.c_void_p), ("t", C.c_void_p),
+                ("eloc", C.c_void_p), ("weights", C.c_void_p), ("ns", C.c_int64),
+                ("n_chains", C.c_int32), ("reserved", C.c_int32), ("scratch", C.c_void_p),
+                ("scratch_bytes", C.c_size_t), ("info_out", C.c_void_p)]
 
 
 class _Operator(C.Structure):
@@ -93,6 +100,9 @@ def load_library(path: str = LIB_PATH):
         "nk_rbm_logpsi_backward": (I32, [P, P, I64, P, P, I32, P, SZ, P]),
         "nk_sr_step_noalloc": (I32, [P, P, P, P, P, I64, I32, D, D, I32, D, I32, P, P]),
         "nk_sr_tune": (I32, [P, P, P, I64, I32, P, SZ, P]),
+        "nk_sr_batch_desc_bytes": (SZ, [I32]),
+        "nk_sr_batch_describe": (I32, [P, I32, I32, P, SZ]),
+        "nk_sr_step_batch": (I32, [P, I32, P, D, D, I32, D, I32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -387,3 +397,47 @@ def nk_sr_step_noalloc(rbm: Rbm, sigma, t, eloc, n_chains: int, diag_shift: floa
         float(diag_shift), float(lr), int(n_cg), float(cg_rtol), prec, _ptr(info_out),
         _stream(stream)), "nk_sr_step_noalloc")
     return info_out
+
+
+class SrBatch:
+    """Many independent SR problems advanced with one launch per kernel
+    (nk_sr_step_batch).  ``items`` is a list of dicts with keys rbm (Rbm), sigma,
+    t, eloc, scratch, info (device tensors), n_chains and optionally weights.
+    The descriptors are built once here; build a new SrBatch if a pointer or a
+    size changes."""
+
+    def __init__(self, items, prec=NK_PREC_BF16X2, device="cuda"):
+        lib = load_library()
+        self.prec = prec
+        self._keep = items
+        arr = (_SrBatchItem * len(items))()
+        for k, it in enumerate(items):
+            _require_gpu(it["sigma"], it["t"], it["eloc"], it["scratch"], it["info"],
+                         it.get("weights"))
+            r = it["rbm"]
+            arr[k].rbm = C.addressof(r._s)
+            arr[k].sigma = it["sigma"].data_ptr()
+            arr[k].t = it["t"].data_ptr()
+            arr[k].eloc = it["eloc"].data_ptr()
+            w = it.get("weights")
+            arr[k].weights = None if w is None else w.data_ptr()
+            arr[k].ns = int(it["sigma"].shape[0])
+            arr[k].n_chains = int(it["n_chains"])
+            arr[k].reserved = 0
+            arr[k].scratch = it["scratch"].data_ptr()
+            arr[k].scratch_bytes = it["scratch"].numel()
+            arr[k].info_out = it["info"].data_ptr()
+        self._items = arr
+        self.n = len(items)
+        nb = lib.nk_sr_batch_desc_bytes(self.n)
+        host = np.zeros(nb, dtype=np.uint8)
+        _check(lib.nk_sr_batch_describe(C.cast(arr, C.c_void_p), self.n, prec,
+                                        host.ctypes.data_as(C.c_void_p), nb),
+               "nk_sr_batch_describe")
+        self.desc = torch.from_numpy(host).to(device)
+
+    def step(self, diag_shift: float, lr: float, n_cg: int, cg_rtol: float = 1e-12, stream=None):
+        _check(load_library().nk_sr_step_batch(
+            C.cast(self._items, C.c_void_p), self.n, _ptr(self.desc), float(diag_shift),
+            float(lr), int(n_cg), float(cg_rtol), self.prec, _stream(stream)),
+            "nk_sr_step_batch")

@@ -105,6 +105,13 @@ class VmcSr:
         d["acceptance"] = float(self.n_acc.sum().item()) / (self.w.n_chains * sweeps * self.w.n)
         return d
 
+    def sr_launches(self) -> int:
+        """Kernel launches of one SR step (stats, force, CG, update, planes)."""
+        n = 5 + 8 * self.w.n_cg + 3
+        if self.prec == nk.NK_PREC_BF16X2:
+            n += 1
+        return n
+
     # kernel launches per step (for reporting)
     def launches_per_step(self) -> int:
         # move tables (exchanges; flips of complex RBMs), sweep

@@ -52,6 +52,26 @@ def test_status_strings_and_sizes(lib):
     assert lib.nk_backward_scratch_bytes(40, 80, 1, 16384) > 16384 * 80 * 8 * 2
 
 
+def test_sr_batch_host_checks(lib):
+    from paper_1904_00031_gb300 import nk
+    assert lib.nk_sr_batch_desc_bytes(0) == 0
+    one = lib.nk_sr_batch_desc_bytes(1)
+    assert one >= 2 * 128 and one % 128 == 0  # two tensor maps, 128-B aligned records
+    assert lib.nk_sr_batch_desc_bytes(5) == 5 * one
+    items = (nk._SrBatchItem * 1)()
+    buf = np.zeros(one, dtype=np.uint8)
+    assert lib.nk_sr_batch_describe(C.cast(items, C.c_void_p), 0, 1,
+                                    buf.ctypes.data_as(C.c_void_p), one) == 1
+    # the batch runs on the tensor-core path only
+    assert lib.nk_sr_batch_describe(C.cast(items, C.c_void_p), 1, 0,
+                                    buf.ctypes.data_as(C.c_void_p), one) == 7
+    # an item without an RBM is rejected before any device work
+    assert lib.nk_sr_step_batch(C.cast(items, C.c_void_p), 1, None, 0.01, 0.01, 5, 0.0, 1,
+                                None) == 1
+    assert lib.nk_sr_step_batch(C.cast(items, C.c_void_p), 1, None, 0.01, 0.01, -1, 0.0, 1,
+                                None) == 1
+
+
 def test_host_argument_validation(lib):
     from paper_1904_00031_gb300 import nk
     assert lib.nk_rbm_logpsi(None, None, 4, 0, None, None, None) == 1

@@ -54,3 +54,46 @@ def test_batched_first_iteration_per_instance(mods):
     torch.cuda.synchronize()
     for v in b.items:
         assert np.isfinite(v.info()["energy"])
+
+
+def test_batched_sr_step_equals_per_instance_steps(mods):
+    """nk_sr_step_batch (one launch per kernel for all instances of a field) runs
+    each instance's arithmetic in the order nk_sr_step does: with the same split
+    count, one iteration of the batch reproduces the per-instance SR steps bit
+    for bit (parameters and info vectors), for mixed real / complex, uneven
+    instances."""
+    nk, BatchedVmc = mods
+    insts = W.batched_instances(n_inst=7, seed=77, n_chains=96)
+    for w in insts:
+        w.n_cg = 12
+    a = BatchedVmc(insts, prec=nk.NK_PREC_BF16X2, graph=False, batch_sr=True, sr_splits=2)
+    b = BatchedVmc(insts, prec=nk.NK_PREC_BF16X2, graph=False, batch_sr=False, sr_splits=2)
+    assert a.srb is not None and b.srb is None
+    for _ in range(2):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    for va, vb in zip(a.items, b.items):
+        assert np.array_equal(va.samples.cpu().numpy(), vb.samples.cpu().numpy())
+        for xa, xb in zip(va.rbm.params_numpy(), vb.rbm.params_numpy()):
+            assert np.array_equal(xa, xb), va.w.name
+        assert np.array_equal(va.info_buf.cpu().numpy(), vb.info_buf.cpu().numpy()), va.w.name
+        assert va.info()["cg_iters"] == 12
+
+
+def test_batched_sr_graph_replays(mods):
+    """The batched SR step inside the captured multi-instance iteration: replays
+    keep every instance finite and the batch's energies decreasing on average."""
+    nk, BatchedVmc = mods
+    insts = W.batched_instances(n_inst=10, seed=5, n_chains=128)
+    b = BatchedVmc(insts, prec=nk.NK_PREC_BF16X2, graph=True)
+    assert b.srb is not None
+    b.step()
+    torch.cuda.synchronize()
+    e0 = np.array([v.info()["energy"] for v in b.items])
+    for _ in range(20):
+        b.step()
+    torch.cuda.synchronize()
+    e1 = np.array([v.info()["energy"] for v in b.items])
+    assert np.all(np.isfinite(e1))
+    assert np.mean(e1 / np.abs(e0)) < np.mean(e0 / np.abs(e0))
