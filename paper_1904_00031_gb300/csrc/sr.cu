@@ -24,7 +24,15 @@
 
 namespace nk {
 
-constexpr int kVecBlocks = 256;   // fixed grid of the CG vector kernels
+constexpr int kVecBlocks = 256;   // largest grid of the CG vector kernels
+
+// Blocks of a CG vector kernel over `elems` elements: about 2048 elements per
+// 256-thread block, at most kVecBlocks (the partial-sum slots of `red`).  The
+// single-problem and the batched launches use the same count per problem, so
+// their reductions run in the same order.
+static int sr_vec_blocks(int64_t elems) {
+  return (int)std::min<int64_t>(kVecBlocks, std::max<int64_t>(1, (elems + 2047) / 2048));
+}
 constexpr int kVecThreads = 256;
 constexpr int kAdjBK = 16;
 
@@ -129,11 +137,11 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // Sum of kVecBlocks partials in a fixed order (every block gets the same value).
-__device__ __forceinline__ double sum_partials(const double* red) {
+__device__ __forceinline__ double sum_partials(const double* red, int nb) {
   __shared__ double tot;
   if (threadIdx.x < 32) {
     double v = 0.0;
-    for (int u = threadIdx.x; u < kVecBlocks; u += 32) v += red[u];
+    for (int u = threadIdx.x; u < nb; u += 32) v += red[u];
     for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (threadIdx.x == 0) tot = v;
   }
@@ -413,10 +421,10 @@ __global__ void __launch_bounds__(kVecThreads) center_partial_kernel(
 template <bool CPLX>
 __device__ __forceinline__ void center_apply_body(int bx, int gx, 
     const void* __restrict__ yv, void* vout, const double* __restrict__ weights, int64_t ns,
-    const double* red, const double* scal) {
+    const double* red, const double* scal, int nb) {
   if (scal[SC_DONE] != 0.0) return;
-  const double mr = sum_partials(red + 2 * kVecBlocks);
-  const double mi = sum_partials(red + 3 * kVecBlocks);
+  const double mr = sum_partials(red + 2 * kVecBlocks, nb);
+  const double mi = sum_partials(red + 3 * kVecBlocks, nb);
   const double invn = 1.0 / (double)ns;
   for (int64_t s = bx * (int64_t)blockDim.x + threadIdx.x; s < ns;
        s += (int64_t)gx * blockDim.x) {
@@ -433,8 +441,8 @@ __device__ __forceinline__ void center_apply_body(int bx, int gx,
 template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) center_apply_kernel(
     const void* __restrict__ yv, void* vout, const double* __restrict__ weights, int64_t ns,
-    const double* red, const double* scal) {
-  center_apply_body<CPLX>(blockIdx.x, gridDim.x, yv, vout, weights, ns, red, scal);
+    const double* red, const double* scal, int nb) {
+  center_apply_body<CPLX>(blockIdx.x, gridDim.x, yv, vout, weights, ns, red, scal, nb);
 }
 
 // out = sum_z part[z] (+ eps * p);  red[b] = sum conj(p) . out (if p given).
@@ -503,8 +511,8 @@ __global__ void __launch_bounds__(kVecThreads) cg_init_kernel(void* xv, void* rv
   cg_init_body<CPLX>(blockIdx.x, gridDim.x, xv, rv, pv, pa, red);
 }
 
-__device__ __forceinline__ void cg_init_scalars_body(int bx, int gx, const double* red, double* scal, double rtol) {
-  double rs = sum_partials(red + kVecBlocks);
+__device__ __forceinline__ void cg_init_scalars_body(int bx, int gx, const double* red, double* scal, double rtol, int nb) {
+  double rs = sum_partials(red + kVecBlocks, nb);
   if (threadIdx.x == 0) {
     scal[SC_RS0] = rs;
     scal[SC_RS1] = rs;
@@ -518,8 +526,8 @@ __device__ __forceinline__ void cg_init_scalars_body(int bx, int gx, const doubl
   }
 }
 
-__global__ void cg_init_scalars_kernel(const double* red, double* scal, double rtol) {
-  cg_init_scalars_body(blockIdx.x, gridDim.x, red, scal, rtol);
+__global__ void cg_init_scalars_kernel(const double* red, double* scal, double rtol, int nb) {
+  cg_init_scalars_body(blockIdx.x, gridDim.x, red, scal, rtol, nb);
 }
 
 // alpha = rs / p^H A p; x += alpha p; r -= alpha A p; red2 = ||r||^2 partials
@@ -527,14 +535,14 @@ template <bool CPLX>
 __device__ __forceinline__ void cg_step_x_body(int bx, int gx, void* xv, void* rv,
                                                                 const void* pv, const void* apv,
                                                                 int64_t pa, double* red,
-                                                                double* scal, int it) {
+                                                                double* scal, int it, int nb) {
   if (scal[SC_DONE] != 0.0) return;
   using DT = typename D<CPLX>::T;
   DT* x = reinterpret_cast<DT*>(xv);
   DT* r = reinterpret_cast<DT*>(rv);
   const DT* p = reinterpret_cast<const DT*>(pv);
   const DT* ap = reinterpret_cast<const DT*>(apv);
-  const double pap = sum_partials(red);
+  const double pap = sum_partials(red, nb);
   const double rs = scal[(it & 1) ? SC_RS1 : SC_RS0];
   const double alpha = rs / pap;
   double nn = 0.0;
@@ -553,8 +561,8 @@ template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) cg_step_x_kernel(void* xv, void* rv,
                                                                 const void* pv, const void* apv,
                                                                 int64_t pa, double* red,
-                                                                double* scal, int it) {
-  cg_step_x_body<CPLX>(blockIdx.x, gridDim.x, xv, rv, pv, apv, pa, red, scal, it);
+                                                                double* scal, int it, int nb) {
+  cg_step_x_body<CPLX>(blockIdx.x, gridDim.x, xv, rv, pv, apv, pa, red, scal, it, nb);
 }
 
 // beta = rs_new / rs; p = r + beta p; convergence test on ||r|| <= rtol ||F||
@@ -562,12 +570,12 @@ template <bool CPLX>
 __device__ __forceinline__ void cg_step_p_body(int bx, int gx, const void* rv, void* pv,
                                                                 int64_t pa, const double* red,
                                                                 double* scal, int it,
-                                                                double rtol) {
+                                                                double rtol, int nb) {
   if (scal[SC_DONE] != 0.0) return;
   using DT = typename D<CPLX>::T;
   const DT* r = reinterpret_cast<const DT*>(rv);
   DT* p = reinterpret_cast<DT*>(pv);
-  const double rs_new = sum_partials(red + kVecBlocks);
+  const double rs_new = sum_partials(red + kVecBlocks, nb);
   const double rs = scal[(it & 1) ? SC_RS1 : SC_RS0];
   const double fn = scal[SC_FNORM];
   const bool conv = sqrt(rs_new) <= rtol * fn;
@@ -590,8 +598,8 @@ template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) cg_step_p_kernel(const void* rv, void* pv,
                                                                 int64_t pa, const double* red,
                                                                 double* scal, int it,
-                                                                double rtol) {
-  cg_step_p_body<CPLX>(blockIdx.x, gridDim.x, rv, pv, pa, red, scal, it, rtol);
+                                                                double rtol, int nb) {
+  cg_step_p_body<CPLX>(blockIdx.x, gridDim.x, rv, pv, pa, red, scal, it, rtol, nb);
 }
 
 // alpha <- alpha - lr delta (FP64 master), delta in the augmented layout; info.
@@ -689,55 +697,64 @@ template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) reduce_parts_batch(const SrDesc* __restrict__ D,
                                                                   int in_cg, double eps) {
   const SrDesc& d = D[blockIdx.y];
+  if ((int)blockIdx.x >= d.nb_pa) return;
   if (in_cg)
-    reduce_parts_body<CPLX>(blockIdx.x, gridDim.x, d.part, d.splits, d.pa, d.corner, d.ap, d.p,
+    reduce_parts_body<CPLX>(blockIdx.x, d.nb_pa, d.part, d.splits, d.pa, d.corner, d.ap, d.p,
                             eps, d.red, d.scal);
   else
-    reduce_parts_body<CPLX>(blockIdx.x, gridDim.x, d.part, d.splits, d.pa, d.corner, d.r,
-                            nullptr, 0.0, nullptr, nullptr);
+    reduce_parts_body<CPLX>(blockIdx.x, d.nb_pa, d.part, d.splits, d.pa, d.corner, d.r, nullptr,
+                            0.0, nullptr, nullptr);
 }
 
 template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) cg_init_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
-  cg_init_body<CPLX>(blockIdx.x, gridDim.x, d.x, d.r, d.p, d.pa, d.red);
+  if ((int)blockIdx.x >= d.nb_pa) return;
+  cg_init_body<CPLX>(blockIdx.x, d.nb_pa, d.x, d.r, d.p, d.pa, d.red);
 }
 
 __global__ void cg_init_scalars_batch(const SrDesc* __restrict__ D, double rtol) {
   const SrDesc& d = D[blockIdx.y];
-  cg_init_scalars_body(0, 1, d.red, d.scal, rtol);
+  cg_init_scalars_body(0, 1, d.red, d.scal, rtol, d.nb_pa);
 }
 
 template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) center_partial_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
-  center_partial_body<CPLX>(blockIdx.x, gridDim.x, d.y, d.weights, d.ns, d.red, d.scal);
+  if ((int)blockIdx.x >= d.nb_ns) return;
+  center_partial_body<CPLX>(blockIdx.x, d.nb_ns, d.y, d.weights, d.ns, d.red, d.scal);
 }
 
 template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) center_apply_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
-  center_apply_body<CPLX>(blockIdx.x, gridDim.x, d.y, d.v, d.weights, d.ns, d.red, d.scal);
+  if ((int)blockIdx.x >= d.nb_ns) return;
+  center_apply_body<CPLX>(blockIdx.x, d.nb_ns, d.y, d.v, d.weights, d.ns, d.red, d.scal,
+                          d.nb_ns);
 }
 
 template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) cg_step_x_batch(const SrDesc* __restrict__ D,
                                                                int it) {
   const SrDesc& d = D[blockIdx.y];
-  cg_step_x_body<CPLX>(blockIdx.x, gridDim.x, d.x, d.r, d.p, d.ap, d.pa, d.red, d.scal, it);
+  if ((int)blockIdx.x >= d.nb_pa) return;
+  cg_step_x_body<CPLX>(blockIdx.x, d.nb_pa, d.x, d.r, d.p, d.ap, d.pa, d.red, d.scal, it,
+                       d.nb_pa);
 }
 
 template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) cg_step_p_batch(const SrDesc* __restrict__ D,
                                                                int it, double rtol) {
   const SrDesc& d = D[blockIdx.y];
-  cg_step_p_body<CPLX>(blockIdx.x, gridDim.x, d.r, d.p, d.pa, d.red, d.scal, it, rtol);
+  if ((int)blockIdx.x >= d.nb_pa) return;
+  cg_step_p_body<CPLX>(blockIdx.x, d.nb_pa, d.r, d.p, d.pa, d.red, d.scal, it, rtol, d.nb_pa);
 }
 
 template <bool CPLX>
 __global__ void sr_update_batch(const SrDesc* __restrict__ D, double lr, int n_cg, double rtol) {
   const SrDesc& d = D[blockIdx.y];
-  sr_update_body<CPLX>(blockIdx.x, gridDim.x, d.a, d.b, d.w, d.n, d.m, d.x, lr, d.scal, d.info,
+  if ((int)blockIdx.x >= d.nb_pa) return;
+  sr_update_body<CPLX>(blockIdx.x, d.nb_pa, d.a, d.b, d.w, d.n, d.m, d.x, lr, d.scal, d.info,
                        n_cg, rtol);
 }
 
@@ -795,12 +812,12 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
   } else {
     launch_adjoint_fp32<CPLX>(sigma, T, sc + L.v, ns, n, m, splits, sc + L.part, nullptr, st);
   }
-  reduce_parts_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.part, splits, L.pa,
-                                                                corner, sc + L.r, nullptr, 0.0,
-                                                                nullptr, nullptr);
-  cg_init_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, sc + L.r, sc + L.p, L.pa,
-                                                           red);
-  cg_init_scalars_kernel<<<1, 32, 0, st>>>(red, scal, rtol);
+  const int nbp = sr_vec_blocks(L.pa), nbs = sr_vec_blocks(ns);
+  reduce_parts_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.part, splits, L.pa, corner,
+                                                         sc + L.r, nullptr, 0.0, nullptr,
+                                                         nullptr);
+  cg_init_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.x, sc + L.r, sc + L.p, L.pa, red);
+  cg_init_scalars_kernel<<<1, 32, 0, st>>>(red, scal, rtol, nbp);
   if (nk_status e = check_launch("nk_sr_step(force)")) return e;
   const int64_t sg_blocks = (ns + kSgBS - 1) / kSgBS;
   aa.v = sc + L.v;
@@ -816,25 +833,24 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
       forward_fp32_kernel<CPLX><<<(unsigned)sg_blocks, kSgThreads, 0, st>>>(
           sigma, ns, n, m, sc + L.xf, T, sc + L.y, scal);
     }
-    center_partial_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.y, weights, ns, red,
-                                                                    scal);
-    center_apply_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.y, sc + L.v, weights,
-                                                                  ns, red, scal);
+    center_partial_kernel<CPLX><<<nbs, kVecThreads, 0, st>>>(sc + L.y, weights, ns, red, scal);
+    center_apply_kernel<CPLX><<<nbs, kVecThreads, 0, st>>>(sc + L.y, sc + L.v, weights, ns, red,
+                                                           scal, nbs);
     if (tc) {
       if (nk_status e = launch_adj_tc(aa, sc + L.sigt, st)) return e;
     } else {
       launch_adjoint_fp32<CPLX>(sigma, T, sc + L.v, ns, n, m, splits, sc + L.part, scal, st);
     }
-    reduce_parts_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(
+    reduce_parts_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(
         sc + L.part, splits, L.pa, corner, sc + L.ap, sc + L.p, eps, red, scal);
-    cg_step_x_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, sc + L.r, sc + L.p,
-                                                               sc + L.ap, L.pa, red, scal, it);
-    cg_step_p_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.r, sc + L.p, L.pa, red,
-                                                               scal, it, rtol);
+    cg_step_x_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.x, sc + L.r, sc + L.p, sc + L.ap,
+                                                        L.pa, red, scal, it, nbp);
+    cg_step_p_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.r, sc + L.p, L.pa, red, scal, it,
+                                                        rtol, nbp);
     if (nk_status e = check_launch("nk_sr_step(cg)")) return e;
   }
-  sr_update_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(r->a, r->b, r->w, n, m, sc + L.x, lr,
-                                                             scal, info, n_cg, rtol);
+  sr_update_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(r->a, r->b, r->w, n, m, sc + L.x, lr,
+                                                      scal, info, n_cg, rtol);
   if (nk_status e = check_launch("nk_sr_step(update)")) return e;
   return launch_prepare(r, st);
 }
@@ -927,6 +943,8 @@ nk_status sr_batch_describe(const nk_sr_batch_item* items, int n_inst, int prec,
     if (!tc_make_map(&d.adj_map, sc + L.sigt, L.na64, L.ns8, L.ns8, L.na64 / 2))
       return NK_ERR_CUDA;
     d.splits = batch_item_splits(items, n_inst, order[z], prec);
+    d.nb_pa = sr_vec_blocks(L.pa);
+    d.nb_ns = sr_vec_blocks(it.ns);
     d.n = r->n;
     d.m = r->m;
     d.n_chains = it.n_chains;
@@ -1036,7 +1054,14 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
     max_work = std::max<int64_t>(max_work, (int64_t)W.mp * (r->n + 1));
     max_minb = std::max<int64_t>(max_minb, (std::max(W.mp, r->n) + 255) / 256);
   }
-  const dim3 vg(kVecBlocks, G), one(1, G);
+  int max_nbp = 1, max_nbs = 1;
+  for (int z = 0; z < G; ++z) {
+    const nk_sr_batch_item& it = items[order[z0 + z]];
+    SrLayout L(it.rbm->n, it.rbm->m, CPLX, it.ns);
+    max_nbp = std::max(max_nbp, sr_vec_blocks(L.pa));
+    max_nbs = std::max(max_nbs, sr_vec_blocks(it.ns));
+  }
+  const dim3 vg(max_nbp, G), vs(max_nbs, G), one(1, G);
   stats_batch<CPLX><<<one, 1024, 0, st>>>(Dg);
   flags_reset_batch<<<one, 32, 0, st>>>(Dg);
   if (nk_status e = check_launch("nk_sr_step_batch(stats)")) return e;
@@ -1050,8 +1075,8 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
   for (int it = 0; it < n_cg; ++it) {
     if (nk_status e = launch_bplanes_p_batch(Dg, G, CPLX, max_xp, st)) return e;
     if (nk_status e = launch_fwd_tc_batch(fb, G, CPLX, max_fwd, max_na64, st)) return e;
-    center_partial_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg);
-    center_apply_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg);
+    center_partial_batch<CPLX><<<vs, kVecThreads, 0, st>>>(Dg);
+    center_apply_batch<CPLX><<<vs, kVecThreads, 0, st>>>(Dg);
     if (nk_status e = launch_adj_tc_batch(ab, G, CPLX, max_adj, max_sp, max_na64, st)) return e;
     reduce_parts_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, 1, eps);
     cg_step_x_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, it);

@@ -78,6 +78,7 @@ struct alignas(128) SrDesc {
   CUtensorMap adj_map;    // sigma'^T (sigt)
   const double* done;     // scal + SC_DONE: the CG has converged
   int splits;
+  int nb_pa, nb_ns;       // blocks of the CG vector kernels over parameters / samples
   int n, m, n_chains, na64, mt1, mp, wmt, wna64;  // wmt, wna64: B planes of W | b
   int64_t ns, pa, corner, ns8;
   const int8_t* sigma;
