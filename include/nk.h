@@ -305,7 +305,7 @@ nk_status nk_sr_batch_describe(const nk_sr_batch_item* items, int32_t n_inst, in
                                void* desc_host, size_t desc_bytes);
 
 /* nk_sr_step (Sec. 2.2.5, Eq. 2) for every problem of a batch, with one launch
- * of each kernel per group of up to 64 problems of one field (complex or real)
+ * of each kernel per group of up to 64 problems (complex and real ones mixed)
  * instead of one launch per problem: many small RBMs fill the GPU together.
  * Each problem's arithmetic and reduction order are those of nk_sr_step with
  * the same split-K count, so the results are identical to n separate calls.

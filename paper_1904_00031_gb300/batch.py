@@ -3,8 +3,7 @@
 Every instance samples, evaluates ln psi and its local energies on a stream of
 its own (the streams fork from and join the caller's stream); the SR steps of
 all instances then run as one batch (nk_sr_step_batch: one launch of each
-kernel per group of up to 64 instances of one field, instead of one per
-instance), on the tensor-core path when every instance shares the SR settings.
+kernel per group of up to 64 instances, instead of one per instance), on the tensor-core path when every instance shares the SR settings.
 The whole multi-instance iteration is captured once into a single CUDA graph,
 so each later iteration is one graph launch.
 """
@@ -86,7 +85,5 @@ class BatchedVmc:
         if self.srb is None:
             return sum(v.launches_per_step() for v in self.items)
         n = sum(v.launches_per_step() - v.sr_launches() for v in self.items)
-        n_c = sum(1 for v in self.items if v.w.is_complex)
-        n_r = len(self.items) - n_c
-        groups = (n_c + 63) // 64 + (n_r + 63) // 64   # up to 64 instances of one field per launch
+        groups = (len(self.items) + 63) // 64   # up to 64 instances per launch
         return n + groups * (10 + 8 * self.sr_args[2])

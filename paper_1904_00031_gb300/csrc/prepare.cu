@@ -97,20 +97,21 @@ __global__ void prepare_kernel(int n, int m, int mp, const double* __restrict__ 
 }
 
 // the same for every problem of an SR batch (blockIdx.y)
-template <bool CPLX>
 __global__ void prepare_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
-  prepare_body<CPLX>(blockIdx.x, gridDim.x, d.n, d.m, d.mp, d.a, d.b, d.w, d.ws, d.ws_a32,
-                     d.ws_b32, d.ws_wt, d.ws_tab, d.ws_xw);
+  if (d.cplx)
+    prepare_body<true>(blockIdx.x, gridDim.x, d.n, d.m, d.mp, d.a, d.b, d.w, d.ws, d.ws_a32,
+                       d.ws_b32, d.ws_wt, d.ws_tab, d.ws_xw);
+  else
+    prepare_body<false>(blockIdx.x, gridDim.x, d.n, d.m, d.mp, d.a, d.b, d.w, d.ws, d.ws_a32,
+                        d.ws_b32, d.ws_wt, d.ws_tab, d.ws_xw);
 }
 
-nk_status launch_prepare_batch(const SrDesc* D, int G, int cplx, int64_t max_work,
-                               int64_t max_minb, cudaStream_t st) {
+nk_status launch_prepare_batch(const SrDesc* D, int G, int64_t max_work, int64_t max_minb,
+                               cudaStream_t st) {
   int64_t blocks = (max_work + 255) / 256;
   blocks = std::max<int64_t>(std::min<int64_t>(blocks, 152 * 8), max_minb);
-  const dim3 grid((unsigned)blocks, (unsigned)G);
-  if (cplx) prepare_batch<true><<<grid, 256, 0, st>>>(D);
-  else prepare_batch<false><<<grid, 256, 0, st>>>(D);
+  prepare_batch<<<dim3((unsigned)blocks, (unsigned)G), 256, 0, st>>>(D);
   return check_launch("prepare_batch");
 }
 

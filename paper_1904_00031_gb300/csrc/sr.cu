@@ -675,14 +675,17 @@ __global__ void scatter_grad_kernel(const void* __restrict__ gv, int n, int m, d
 
 // ------------------------------------------------------------------ batched kernels
 // The same kernels for every problem of an SR batch: blockIdx.y selects the
-// problem (its SrDesc), blockIdx.x runs over the same fixed grid as the
-// single-problem launch, so each problem's reductions keep their order and a
-// batched step computes exactly what nk_sr_step computes for each problem.
+// problem (its SrDesc; complex and real problems share a launch and branch on
+// its field), blockIdx.x runs over the problem's own grid (the one the
+// single-problem launch uses), so each problem's reductions keep their order
+// and a batched step computes exactly what nk_sr_step computes for it.
 
-template <bool CPLX>
 __global__ void __launch_bounds__(1024) stats_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
-  stats_body<CPLX>(0, 1, d.eloc, d.weights, d.ns, d.n_chains, d.info, d.scal, d.v);
+  if (d.cplx)
+    stats_body<true>(0, 1, d.eloc, d.weights, d.ns, d.n_chains, d.info, d.scal, d.v);
+  else
+    stats_body<false>(0, 1, d.eloc, d.weights, d.ns, d.n_chains, d.info, d.scal, d.v);
 }
 
 __global__ void flags_reset_batch(const SrDesc* __restrict__ D) {
@@ -693,24 +696,30 @@ __global__ void flags_reset_batch(const SrDesc* __restrict__ D) {
 }
 
 // in_cg = 0: F into r (no shift, no inner product); 1: S p + eps p into ap
-template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) reduce_parts_batch(const SrDesc* __restrict__ D,
                                                                   int in_cg, double eps) {
   const SrDesc& d = D[blockIdx.y];
   if ((int)blockIdx.x >= d.nb_pa) return;
-  if (in_cg)
-    reduce_parts_body<CPLX>(blockIdx.x, d.nb_pa, d.part, d.splits, d.pa, d.corner, d.ap, d.p,
-                            eps, d.red, d.scal);
+  char* out = in_cg ? d.ap : d.r;
+  const void* p = in_cg ? d.p : nullptr;
+  double* red = in_cg ? d.red : nullptr;
+  const double* scal = in_cg ? d.scal : nullptr;
+  const double e = in_cg ? eps : 0.0;
+  if (d.cplx)
+    reduce_parts_body<true>(blockIdx.x, d.nb_pa, d.part, d.splits, d.pa, d.corner, out, p, e,
+                            red, scal);
   else
-    reduce_parts_body<CPLX>(blockIdx.x, d.nb_pa, d.part, d.splits, d.pa, d.corner, d.r, nullptr,
-                            0.0, nullptr, nullptr);
+    reduce_parts_body<false>(blockIdx.x, d.nb_pa, d.part, d.splits, d.pa, d.corner, out, p, e,
+                             red, scal);
 }
 
-template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) cg_init_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
   if ((int)blockIdx.x >= d.nb_pa) return;
-  cg_init_body<CPLX>(blockIdx.x, d.nb_pa, d.x, d.r, d.p, d.pa, d.red);
+  if (d.cplx)
+    cg_init_body<true>(blockIdx.x, d.nb_pa, d.x, d.r, d.p, d.pa, d.red);
+  else
+    cg_init_body<false>(blockIdx.x, d.nb_pa, d.x, d.r, d.p, d.pa, d.red);
 }
 
 __global__ void cg_init_scalars_batch(const SrDesc* __restrict__ D, double rtol) {
@@ -718,43 +727,56 @@ __global__ void cg_init_scalars_batch(const SrDesc* __restrict__ D, double rtol)
   cg_init_scalars_body(0, 1, d.red, d.scal, rtol, d.nb_pa);
 }
 
-template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) center_partial_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
   if ((int)blockIdx.x >= d.nb_ns) return;
-  center_partial_body<CPLX>(blockIdx.x, d.nb_ns, d.y, d.weights, d.ns, d.red, d.scal);
+  if (d.cplx)
+    center_partial_body<true>(blockIdx.x, d.nb_ns, d.y, d.weights, d.ns, d.red, d.scal);
+  else
+    center_partial_body<false>(blockIdx.x, d.nb_ns, d.y, d.weights, d.ns, d.red, d.scal);
 }
 
-template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) center_apply_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
   if ((int)blockIdx.x >= d.nb_ns) return;
-  center_apply_body<CPLX>(blockIdx.x, d.nb_ns, d.y, d.v, d.weights, d.ns, d.red, d.scal,
+  if (d.cplx)
+    center_apply_body<true>(blockIdx.x, d.nb_ns, d.y, d.v, d.weights, d.ns, d.red, d.scal,
+                          d.nb_ns);
+  else
+    center_apply_body<false>(blockIdx.x, d.nb_ns, d.y, d.v, d.weights, d.ns, d.red, d.scal,
                           d.nb_ns);
 }
 
-template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) cg_step_x_batch(const SrDesc* __restrict__ D,
                                                                int it) {
   const SrDesc& d = D[blockIdx.y];
   if ((int)blockIdx.x >= d.nb_pa) return;
-  cg_step_x_body<CPLX>(blockIdx.x, d.nb_pa, d.x, d.r, d.p, d.ap, d.pa, d.red, d.scal, it,
+  if (d.cplx)
+    cg_step_x_body<true>(blockIdx.x, d.nb_pa, d.x, d.r, d.p, d.ap, d.pa, d.red, d.scal, it,
+                       d.nb_pa);
+  else
+    cg_step_x_body<false>(blockIdx.x, d.nb_pa, d.x, d.r, d.p, d.ap, d.pa, d.red, d.scal, it,
                        d.nb_pa);
 }
 
-template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) cg_step_p_batch(const SrDesc* __restrict__ D,
                                                                int it, double rtol) {
   const SrDesc& d = D[blockIdx.y];
   if ((int)blockIdx.x >= d.nb_pa) return;
-  cg_step_p_body<CPLX>(blockIdx.x, d.nb_pa, d.r, d.p, d.pa, d.red, d.scal, it, rtol, d.nb_pa);
+  if (d.cplx)
+    cg_step_p_body<true>(blockIdx.x, d.nb_pa, d.r, d.p, d.pa, d.red, d.scal, it, rtol, d.nb_pa);
+  else
+    cg_step_p_body<false>(blockIdx.x, d.nb_pa, d.r, d.p, d.pa, d.red, d.scal, it, rtol, d.nb_pa);
 }
 
-template <bool CPLX>
 __global__ void sr_update_batch(const SrDesc* __restrict__ D, double lr, int n_cg, double rtol) {
   const SrDesc& d = D[blockIdx.y];
   if ((int)blockIdx.x >= d.nb_pa) return;
-  sr_update_body<CPLX>(blockIdx.x, d.nb_pa, d.a, d.b, d.w, d.n, d.m, d.x, lr, d.scal, d.info,
+  if (d.cplx)
+    sr_update_body<true>(blockIdx.x, d.nb_pa, d.a, d.b, d.w, d.n, d.m, d.x, lr, d.scal, d.info,
+                       n_cg, rtol);
+  else
+    sr_update_body<false>(blockIdx.x, d.nb_pa, d.a, d.b, d.w, d.n, d.m, d.x, lr, d.scal, d.info,
                        n_cg, rtol);
 }
 
@@ -945,6 +967,7 @@ nk_status sr_batch_describe(const nk_sr_batch_item* items, int n_inst, int prec,
     d.splits = batch_item_splits(items, n_inst, order[z], prec);
     d.nb_pa = sr_vec_blocks(L.pa);
     d.nb_ns = sr_vec_blocks(it.ns);
+    d.cplx = cplx;
     d.n = r->n;
     d.m = r->m;
     d.n_chains = it.n_chains;
@@ -989,8 +1012,7 @@ nk_status sr_batch_describe(const nk_sr_batch_item* items, int n_inst, int prec,
   return NK_OK;
 }
 
-// one sub-batch: problems [z0, z0 + G) of the descriptor order, all of one field
-template <bool CPLX>
+// one sub-batch: problems [z0, z0 + G) of the descriptor order (up to kBatchMax)
 static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
                                 const std::vector<int>& order, int z0, int G,
                                 const SrDesc* D, double eps, double lr, int n_cg, double rtol,
@@ -1002,12 +1024,13 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
   memset(&ab, 0, sizeof(ab));
   int max_fwd = 1, max_adj = 1, max_sp = 1, max_na64 = 64;
   int64_t max_ns8 = 8, max_xp = 1, max_wp = 1, max_work = 1, max_minb = 1;
-  const int HJ = CPLX ? 64 : 128;
   for (int z = 0; z < G; ++z) {
     const nk_sr_batch_item& it = items[order[z0 + z]];
     const nk_rbm* r = it.rbm;
-    SrLayout L(r->n, r->m, CPLX, it.ns);
-    WsLayout W(r->n, r->m, CPLX);
+    const int cplx = r->is_complex ? 1 : 0;
+    const int HJ = cplx ? 64 : 128;
+    SrLayout L(r->n, r->m, cplx, it.ns);
+    WsLayout W(r->n, r->m, cplx);
     char* sc = (char*)it.scratch;
     double* scal = (double*)(sc + L.scal);
     const int splits = batch_item_splits(items, n_inst, order[z0 + z], prec);
@@ -1016,7 +1039,7 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
     fa.ns = it.ns;
     fa.n = r->n;
     fa.m = r->m;
-    fa.cplx = CPLX;
+    fa.cplx = cplx;
     fa.mode = 0;
     fa.mt = L.mt1;
     fa.na64 = L.na64;
@@ -1034,7 +1057,7 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
     aa.ns = it.ns;
     aa.n = r->n;
     aa.m = r->m;
-    aa.cplx = CPLX;
+    aa.cplx = cplx;
     aa.na64 = L.na64;
     aa.splits = splits;
     aa.part = sc + L.part;
@@ -1057,36 +1080,36 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
   int max_nbp = 1, max_nbs = 1;
   for (int z = 0; z < G; ++z) {
     const nk_sr_batch_item& it = items[order[z0 + z]];
-    SrLayout L(it.rbm->n, it.rbm->m, CPLX, it.ns);
+    SrLayout L(it.rbm->n, it.rbm->m, it.rbm->is_complex ? 1 : 0, it.ns);
     max_nbp = std::max(max_nbp, sr_vec_blocks(L.pa));
     max_nbs = std::max(max_nbs, sr_vec_blocks(it.ns));
   }
   const dim3 vg(max_nbp, G), vs(max_nbs, G), one(1, G);
-  stats_batch<CPLX><<<one, 1024, 0, st>>>(Dg);
+  stats_batch<<<one, 1024, 0, st>>>(Dg);
   flags_reset_batch<<<one, 32, 0, st>>>(Dg);
   if (nk_status e = check_launch("nk_sr_step_batch(stats)")) return e;
   if (nk_status e = launch_sigma_t_batch(Dg, G, max_ns8, max_na64, st)) return e;
-  if (nk_status e = launch_adj_tc_batch(ab, G, CPLX, max_adj, max_sp, max_na64, st)) return e;
-  reduce_parts_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, 0, 0.0);
-  cg_init_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg);
+  if (nk_status e = launch_adj_tc_batch(ab, G, max_adj, max_sp, max_na64, st)) return e;
+  reduce_parts_batch<<<vg, kVecThreads, 0, st>>>(Dg, 0, 0.0);
+  cg_init_batch<<<vg, kVecThreads, 0, st>>>(Dg);
   cg_init_scalars_batch<<<one, 32, 0, st>>>(Dg, rtol);
   if (nk_status e = check_launch("nk_sr_step_batch(force)")) return e;
   for (int z = 0; z < G; ++z) ab.a[z].skip = fb.a[z].skip;
   for (int it = 0; it < n_cg; ++it) {
-    if (nk_status e = launch_bplanes_p_batch(Dg, G, CPLX, max_xp, st)) return e;
-    if (nk_status e = launch_fwd_tc_batch(fb, G, CPLX, max_fwd, max_na64, st)) return e;
-    center_partial_batch<CPLX><<<vs, kVecThreads, 0, st>>>(Dg);
-    center_apply_batch<CPLX><<<vs, kVecThreads, 0, st>>>(Dg);
-    if (nk_status e = launch_adj_tc_batch(ab, G, CPLX, max_adj, max_sp, max_na64, st)) return e;
-    reduce_parts_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, 1, eps);
-    cg_step_x_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, it);
-    cg_step_p_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, it, rtol);
+    if (nk_status e = launch_bplanes_p_batch(Dg, G, max_xp, st)) return e;
+    if (nk_status e = launch_fwd_tc_batch(fb, G, max_fwd, max_na64, st)) return e;
+    center_partial_batch<<<vs, kVecThreads, 0, st>>>(Dg);
+    center_apply_batch<<<vs, kVecThreads, 0, st>>>(Dg);
+    if (nk_status e = launch_adj_tc_batch(ab, G, max_adj, max_sp, max_na64, st)) return e;
+    reduce_parts_batch<<<vg, kVecThreads, 0, st>>>(Dg, 1, eps);
+    cg_step_x_batch<<<vg, kVecThreads, 0, st>>>(Dg, it);
+    cg_step_p_batch<<<vg, kVecThreads, 0, st>>>(Dg, it, rtol);
     if (nk_status e = check_launch("nk_sr_step_batch(cg)")) return e;
   }
-  sr_update_batch<CPLX><<<vg, kVecThreads, 0, st>>>(Dg, lr, n_cg, rtol);
+  sr_update_batch<<<vg, kVecThreads, 0, st>>>(Dg, lr, n_cg, rtol);
   if (nk_status e = check_launch("nk_sr_step_batch(update)")) return e;
-  if (nk_status e = launch_prepare_batch(Dg, G, CPLX, max_work, max_minb, st)) return e;
-  return launch_bplanes_rbm_batch(Dg, G, CPLX, max_wp, st);
+  if (nk_status e = launch_prepare_batch(Dg, G, max_work, max_minb, st)) return e;
+  return launch_bplanes_rbm_batch(Dg, G, max_wp, st);
 }
 
 nk_status run_sr_step_batch(const nk_sr_batch_item* items, int n_inst, const void* desc_dev,
@@ -1097,18 +1120,10 @@ nk_status run_sr_step_batch(const nk_sr_batch_item* items, int n_inst, const voi
     return fail(NK_ERR_INVALID_ARG, "nk_sr_step_batch: descriptors NULL or not 256-byte aligned");
   const std::vector<int> order = batch_order(items, n_inst);
   const SrDesc* D = reinterpret_cast<const SrDesc*>(desc_dev);
-  int z = 0;
-  while (z < n_inst) {
-    const bool cplx = items[order[z]].rbm->is_complex != 0;
-    int G = 0;
-    while (z + G < n_inst && G < kBatchMax && (items[order[z + G]].rbm->is_complex != 0) == cplx)
-      ++G;
-    nk_status e = cplx ? sr_batch_group<true>(items, n_inst, order, z, G, D, eps, lr, n_cg, rtol,
-                                              prec, st)
-                       : sr_batch_group<false>(items, n_inst, order, z, G, D, eps, lr, n_cg, rtol,
-                                               prec, st);
-    if (e) return e;
-    z += G;
+  for (int z = 0; z < n_inst; z += kBatchMax) {
+    const int G = std::min(kBatchMax, n_inst - z);
+    if (nk_status e = sr_batch_group(items, n_inst, order, z, G, D, eps, lr, n_cg, rtol, prec, st))
+      return e;
   }
   return NK_OK;
 }

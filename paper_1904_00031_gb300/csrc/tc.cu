@@ -829,22 +829,24 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
 }
 
-template <bool CPLX>
-__global__ void __launch_bounds__(kFwdThreads, 1)
-    fwd_tc_batch(const __grid_constant__ FwdBatch P) {
+__global__ void __launch_bounds__(kFwdThreads, 1) fwd_tc_batch(const __grid_constant__ FwdBatch P) {
   const int z = blockIdx.z;
   if ((int)blockIdx.x >= P.tiles[z]) return;
   if (threadIdx.x == 0) tensormap_acquire(P.map[z]);
-  fwd_tc_body<CPLX>(P.map[z], P.a[z], blockIdx.x, 0);
+  if (P.a[z].cplx)
+    fwd_tc_body<true>(P.map[z], P.a[z], blockIdx.x, 0);
+  else
+    fwd_tc_body<false>(P.map[z], P.a[z], blockIdx.x, 0);
 }
 
-template <bool CPLX>
-__global__ void __launch_bounds__(kAdjThreads, 1)
-    adj_tc_batch(const __grid_constant__ AdjBatch P) {
+__global__ void __launch_bounds__(kAdjThreads, 1) adj_tc_batch(const __grid_constant__ AdjBatch P) {
   const int z = blockIdx.z;
   if ((int)blockIdx.x >= P.tiles[z] || (int)blockIdx.y >= P.splits[z]) return;
   if (threadIdx.x == 0) tensormap_acquire(P.map[z]);
-  adj_tc_body<CPLX>(P.map[z], P.a[z], P.chunk[z], blockIdx.x, blockIdx.y);
+  if (P.a[z].cplx)
+    adj_tc_body<true>(P.map[z], P.a[z], P.chunk[z], blockIdx.x, blockIdx.y);
+  else
+    adj_tc_body<false>(P.map[z], P.a[z], P.chunk[z], blockIdx.x, blockIdx.y);
 }
 
 __global__ void sigma_t_batch(const SrDesc* __restrict__ D) {
@@ -854,59 +856,52 @@ __global__ void sigma_t_batch(const SrDesc* __restrict__ D) {
                reinterpret_cast<uint16_t*>(d.sigt));
 }
 
-template <bool CPLX>
 __global__ void bplanes_p_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
-  bplanes_body<CPLX, false>(blockIdx.x, gridDim.x, reinterpret_cast<const double*>(d.p),
-                            d.m + 1, d.n + 1, d.n + 1, nullptr, nullptr, 0, d.mt1, d.na64,
-                            reinterpret_cast<uint16_t*>(d.xbf), d.done);
+  if (d.cplx)
+    bplanes_body<true, false>(blockIdx.x, gridDim.x, reinterpret_cast<const double*>(d.p),
+                              d.m + 1, d.n + 1, d.n + 1, nullptr, nullptr, 0, d.mt1, d.na64,
+                              reinterpret_cast<uint16_t*>(d.xbf), d.done);
+  else
+    bplanes_body<false, false>(blockIdx.x, gridDim.x, reinterpret_cast<const double*>(d.p),
+                               d.m + 1, d.n + 1, d.n + 1, nullptr, nullptr, 0, d.mt1, d.na64,
+                               reinterpret_cast<uint16_t*>(d.xbf), d.done);
 }
 
-template <bool CPLX>
 __global__ void bplanes_rbm_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
-  bplanes_body<CPLX, true>(blockIdx.x, gridDim.x, nullptr, d.m, d.n + 1, 0, d.w, d.b, d.n,
-                           d.wmt, d.wna64, reinterpret_cast<uint16_t*>(d.ws + d.ws_wbf),
-                           nullptr);
+  if (d.cplx)
+    bplanes_body<true, true>(blockIdx.x, gridDim.x, nullptr, d.m, d.n + 1, 0, d.w, d.b, d.n,
+                             d.wmt, d.wna64, reinterpret_cast<uint16_t*>(d.ws + d.ws_wbf),
+                             nullptr);
+  else
+    bplanes_body<false, true>(blockIdx.x, gridDim.x, nullptr, d.m, d.n + 1, 0, d.w, d.b, d.n,
+                              d.wmt, d.wna64, reinterpret_cast<uint16_t*>(d.ws + d.ws_wbf),
+                              nullptr);
 }
 
 static unsigned vec_blocks(int64_t elems) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((elems + 255) / 256, 152 * 8));
 }
 
-nk_status launch_fwd_tc_batch(const FwdBatch& P, int G, int cplx, int max_tiles, int max_na64,
+nk_status launch_fwd_tc_batch(const FwdBatch& P, int G, int max_tiles, int max_na64,
                               cudaStream_t st) {
   const size_t smem = fwd_smem_bytes(max_na64);
-  const dim3 grid((unsigned)max_tiles, 1, (unsigned)G);
-  if (cplx) {
-    if (cudaFuncSetAttribute(fwd_tc_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return fail(NK_ERR_CUDA, "fwd_tc_batch: shared memory attribute");
-    fwd_tc_batch<true><<<grid, kFwdThreads, smem, st>>>(P);
-  } else {
-    if (cudaFuncSetAttribute(fwd_tc_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return fail(NK_ERR_CUDA, "fwd_tc_batch: shared memory attribute");
-    fwd_tc_batch<false><<<grid, kFwdThreads, smem, st>>>(P);
-  }
+  if (cudaFuncSetAttribute(fwd_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return fail(NK_ERR_CUDA, "fwd_tc_batch: shared memory attribute");
+  fwd_tc_batch<<<dim3((unsigned)max_tiles, 1, (unsigned)G), kFwdThreads, smem, st>>>(P);
   return check_launch("fwd_tc_batch");
 }
 
-nk_status launch_adj_tc_batch(const AdjBatch& P, int G, int cplx, int max_tiles, int max_splits,
+nk_status launch_adj_tc_batch(const AdjBatch& P, int G, int max_tiles, int max_splits,
                               int max_na64, cudaStream_t st) {
   const size_t smem = 1024 + 2 * (32768 + (size_t)max_na64 * 128) + 64;
-  const dim3 grid((unsigned)max_tiles, (unsigned)max_splits, (unsigned)G);
-  if (cplx) {
-    if (cudaFuncSetAttribute(adj_tc_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return fail(NK_ERR_CUDA, "adj_tc_batch: shared memory attribute");
-    adj_tc_batch<true><<<grid, kAdjThreads, smem, st>>>(P);
-  } else {
-    if (cudaFuncSetAttribute(adj_tc_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return fail(NK_ERR_CUDA, "adj_tc_batch: shared memory attribute");
-    adj_tc_batch<false><<<grid, kAdjThreads, smem, st>>>(P);
-  }
+  if (cudaFuncSetAttribute(adj_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return fail(NK_ERR_CUDA, "adj_tc_batch: shared memory attribute");
+  adj_tc_batch<<<dim3((unsigned)max_tiles, (unsigned)max_splits, (unsigned)G), kAdjThreads, smem,
+                 st>>>(P);
   return check_launch("adj_tc_batch");
 }
 
@@ -918,19 +913,13 @@ nk_status launch_sigma_t_batch(const SrDesc* D, int G, int64_t max_ns8, int max_
   return check_launch("sigma_t_batch");
 }
 
-nk_status launch_bplanes_p_batch(const SrDesc* D, int G, int cplx, int64_t max_elems,
-                                 cudaStream_t st) {
-  const dim3 grid(vec_blocks(max_elems), (unsigned)G);
-  if (cplx) bplanes_p_batch<true><<<grid, 256, 0, st>>>(D);
-  else bplanes_p_batch<false><<<grid, 256, 0, st>>>(D);
+nk_status launch_bplanes_p_batch(const SrDesc* D, int G, int64_t max_elems, cudaStream_t st) {
+  bplanes_p_batch<<<dim3(vec_blocks(max_elems), (unsigned)G), 256, 0, st>>>(D);
   return check_launch("bplanes_p_batch");
 }
 
-nk_status launch_bplanes_rbm_batch(const SrDesc* D, int G, int cplx, int64_t max_elems,
-                                   cudaStream_t st) {
-  const dim3 grid(vec_blocks(max_elems), (unsigned)G);
-  if (cplx) bplanes_rbm_batch<true><<<grid, 256, 0, st>>>(D);
-  else bplanes_rbm_batch<false><<<grid, 256, 0, st>>>(D);
+nk_status launch_bplanes_rbm_batch(const SrDesc* D, int G, int64_t max_elems, cudaStream_t st) {
+  bplanes_rbm_batch<<<dim3(vec_blocks(max_elems), (unsigned)G), 256, 0, st>>>(D);
   return check_launch("bplanes_rbm_batch");
 }
 

@@ -79,6 +79,7 @@ struct alignas(128) SrDesc {
   const double* done;     // scal + SC_DONE: the CG has converged
   int splits;
   int nb_pa, nb_ns;       // blocks of the CG vector kernels over parameters / samples
+  int cplx;               // 1: complex RBM
   int n, m, n_chains, na64, mt1, mp, wmt, wna64;  // wmt, wna64: B planes of W | b
   int64_t ns, pa, corner, ns8;
   const int8_t* sigma;
@@ -120,22 +121,20 @@ struct AdjBatch {
   int tiles[kBatchMax], splits[kBatchMax];
 };
 
-// Batched launches over G problems of one field (all complex or all real); the
-// max_* arguments bound the grid, and every problem's CTAs beyond its own sizes
-// return at once.
-nk_status launch_fwd_tc_batch(const FwdBatch& P, int G, int cplx, int max_tiles, int max_na64,
+// Batched launches over G problems (complex and real ones branch on their
+// field); the max_* arguments bound the grid, and every problem's CTAs beyond
+// its own sizes return at once.
+nk_status launch_fwd_tc_batch(const FwdBatch& P, int G, int max_tiles, int max_na64,
                               cudaStream_t st);
-nk_status launch_adj_tc_batch(const AdjBatch& P, int G, int cplx, int max_tiles, int max_splits,
+nk_status launch_adj_tc_batch(const AdjBatch& P, int G, int max_tiles, int max_splits,
                               int max_na64, cudaStream_t st);
 nk_status launch_sigma_t_batch(const SrDesc* D, int G, int64_t max_ns8, int max_na64,
                                cudaStream_t st);
 // B planes of the CG direction p (skipped once converged), or of W | b
-nk_status launch_bplanes_p_batch(const SrDesc* D, int G, int cplx, int64_t max_elems,
-                                 cudaStream_t st);
-nk_status launch_bplanes_rbm_batch(const SrDesc* D, int G, int cplx, int64_t max_elems,
-                                   cudaStream_t st);
+nk_status launch_bplanes_p_batch(const SrDesc* D, int G, int64_t max_elems, cudaStream_t st);
+nk_status launch_bplanes_rbm_batch(const SrDesc* D, int G, int64_t max_elems, cudaStream_t st);
 // the derived planes of every problem's RBM (prepare.cu)
-nk_status launch_prepare_batch(const SrDesc* D, int G, int cplx, int64_t max_work,
-                               int64_t max_minb, cudaStream_t st);
+nk_status launch_prepare_batch(const SrDesc* D, int G, int64_t max_work, int64_t max_minb,
+                               cudaStream_t st);
 
 }  // namespace nk
