@@ -231,7 +231,10 @@ __device__ __forceinline__ uint32_t sig_bits(const int8_t* sigma, int64_t s, int
   return i == n ? 0x3F80u : 0u;
 }
 
-template <bool CPLX>
+// STAGES: B-operand stages; PREFETCH: the next tile's T values are loaded into
+// registers while its MMAs run (else each 16-unit chunk is loaded just before
+// use, which needs far fewer registers).
+template <bool CPLX, int STAGES, bool PREFETCH>
 __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcArgs& A, int bx,
                                             int seg) {
   if (A.skip && *A.skip != 0.0) return;
@@ -240,16 +243,16 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
   const int KC = A.na64 / 64;
   unsigned char* sA = sm;
   unsigned char* sB = sm + (size_t)KC * 16384;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kFwdStages * kStageB);
-  uint64_t* empty = full + kFwdStages;
-  uint64_t* tfull = empty + kFwdStages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * kStageB);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
   uint32_t* slot = reinterpret_cast<uint32_t*>(tempty + 2);
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int64_t s0 = (int64_t)bx * 128;
 
   if (tid == 0) {
-    for (int st = 0; st < kFwdStages; ++st) {
+    for (int st = 0; st < STAGES; ++st) {
       mbar_init(&full[st], 1);
       mbar_init(&empty[st], 1);
     }
@@ -286,7 +289,7 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
   if (w == 0) {
     if (lane == 0) {
       for (int it = 0; it < total_it; ++it) {
-        const int st = it % kFwdStages, u = it / kFwdStages, jt = jt_begin + it / KC,
+        const int st = it % STAGES, u = it / STAGES, jt = jt_begin + it / KC,
                   kc = it % KC;
         if (u > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((u - 1) & 1))) {
           bad = true;
@@ -311,7 +314,7 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
         tc_fence_after();
         const uint32_t d = taddr + (uint32_t)(acc * 128);
         for (int kc = 0; kc < KC; ++kc, ++it) {
-          const int st = it % kFwdStages, u = it / kFwdStages;
+          const int st = it % STAGES, u = it / STAGES;
           if (!mbar_wait_bounded(&full[st], (uint32_t)(u & 1))) {
             bad = true;
             break;
@@ -343,7 +346,7 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
     constexpr int HJ = CPLX ? 64 : 128;
     using F = typename std::conditional<CPLX, float2, float>::type;
     const F* T = reinterpret_cast<const F*>(A.T);
-    F tp[HJ];
+    F tp[PREFETCH ? HJ : 1];
     // 16-byte loads when every row of T starts 16-B aligned (m even for complex,
     // m a multiple of 4 for real); the tile's tail and j = m are handled per element
     const bool vec = CPLX ? (A.m % 2 == 0) : (A.m % 4 == 0);
@@ -381,7 +384,42 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
         }
       }
     };
-    if (A.mode == 0 && jt_end > jt_begin) load_t(jt_begin);
+    // one 16-unit chunk c of tile jt (the loads of the no-prefetch variant)
+    auto load_chunk = [&](int jt, int c, F (&tc)[16]) {
+      const int j0 = jt * HJ + c * 16;
+      if (vec && live && j0 + 16 <= A.m) {
+        const float4* src = reinterpret_cast<const float4*>(T + s * A.m + j0);
+        constexpr int NV = CPLX ? 8 : 4;
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+          const float4 x = src[e];
+          if constexpr (CPLX) {
+            tc[2 * e] = make_float2(x.x, x.y);
+            tc[2 * e + 1] = make_float2(x.z, x.w);
+          } else {
+            tc[4 * e] = x.x;
+            tc[4 * e + 1] = x.y;
+            tc[4 * e + 2] = x.z;
+            tc[4 * e + 3] = x.w;
+          }
+        }
+        return;
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int j = j0 + e;
+        if constexpr (CPLX) {
+          tc[e] = make_float2(0.f, 0.f);
+          if (live && j < A.m) tc[e] = T[s * A.m + j];
+          else if (j == A.m) tc[e] = make_float2(1.f, 0.f);
+        } else {
+          tc[e] = 0.f;
+          if (live && j < A.m) tc[e] = T[s * A.m + j];
+          else if (j == A.m) tc[e] = 1.f;
+        }
+      }
+    };
+    if (PREFETCH && A.mode == 0 && jt_end > jt_begin) load_t(jt_begin);
     double sr = 0.0, si = 0.0;
     for (int jt = jt_begin; jt < jt_end; ++jt) {
       const int acc = (jt - jt_begin) & 1;
@@ -397,6 +435,8 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
         float2* th = reinterpret_cast<float2*>(A.theta_out);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
+          float2 tc[16];
+          if (!PREFETCH && A.mode == 0) load_chunk(jt, c, tc);
           float ur[16], ui[16];
           tmem_ld16(tb0 + c * 16, ur);
           tmem_ld16(tb0 + 64 + c * 16, ui);
@@ -404,7 +444,7 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
           if (A.mode == 0) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-              const float2 t = tp[c * 16 + e];
+              const float2 t = PREFETCH ? tp[c * 16 + e] : tc[e];
               pr += t.x * ur[e] - t.y * ui[e];
               pi += t.x * ui[e] + t.y * ur[e];
             }
@@ -425,12 +465,14 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
         float* th = reinterpret_cast<float*>(A.theta_out);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
+          float tc[16];
+          if (!PREFETCH && A.mode == 0) load_chunk(jt, c, tc);
           float u[16];
           tmem_ld16(tb0 + c * 16, u);
           tmem_ld_wait();
           if (A.mode == 0) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) pr += tp[c * 16 + e] * u[e];
+            for (int e = 0; e < 16; ++e) pr += (PREFETCH ? tp[c * 16 + e] : tc[e]) * u[e];
           } else if (live) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
@@ -448,7 +490,7 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
-      if (A.mode == 0 && jt + 1 < jt_end) load_t(jt + 1);
+      if (PREFETCH && A.mode == 0 && jt + 1 < jt_end) load_t(jt + 1);
     }
     if (live) {
       if (bad) sr = si = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a timeout
@@ -498,11 +540,11 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
 template <bool CPLX>
 __global__ void __launch_bounds__(kFwdThreads, 1)
     fwd_tc_kernel(const __grid_constant__ CUtensorMap tb, FwdTcArgs A) {
-  fwd_tc_body<CPLX>(&tb, A, blockIdx.x, blockIdx.y);
+  fwd_tc_body<CPLX, kFwdStages, true>(&tb, A, blockIdx.x, blockIdx.y);
 }
 
-static size_t fwd_smem_bytes(int na64) {
-  return 1024 + (size_t)(na64 / 64) * 16384 + kFwdStages * kStageB + 128;
+static size_t fwd_smem_bytes(int na64, int stages = kFwdStages) {
+  return 1024 + (size_t)(na64 / 64) * 16384 + (size_t)stages * kStageB + 128;
 }
 
 nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st) {
@@ -829,17 +871,21 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
 }
 
-__global__ void __launch_bounds__(kFwdThreads, 1) fwd_tc_batch(const __grid_constant__ FwdBatch P) {
+// Batched forward: two B stages and no T prefetch, so that two CTAs fit on an
+// SM (the problems of a batch are small: many short CTAs).
+constexpr int kFwdBatchStages = 2;
+__global__ void __launch_bounds__(kFwdThreads, 2) fwd_tc_batch(const __grid_constant__ FwdBatch P) {
   const int z = blockIdx.z;
   if ((int)blockIdx.x >= P.tiles[z]) return;
   if (threadIdx.x == 0) tensormap_acquire(P.map[z]);
   if (P.a[z].cplx)
-    fwd_tc_body<true>(P.map[z], P.a[z], blockIdx.x, 0);
+    fwd_tc_body<true, kFwdBatchStages, false>(P.map[z], P.a[z], blockIdx.x, 0);
   else
-    fwd_tc_body<false>(P.map[z], P.a[z], blockIdx.x, 0);
+    fwd_tc_body<false, kFwdBatchStages, false>(P.map[z], P.a[z], blockIdx.x, 0);
 }
 
-__global__ void __launch_bounds__(kAdjThreads, 1) adj_tc_batch(const __grid_constant__ AdjBatch P) {
+// Batched adjoint: two CTAs per SM (96 registers per thread).
+__global__ void __launch_bounds__(kAdjThreads, 2) adj_tc_batch(const __grid_constant__ AdjBatch P) {
   const int z = blockIdx.z;
   if ((int)blockIdx.x >= P.tiles[z] || (int)blockIdx.y >= P.splits[z]) return;
   if (threadIdx.x == 0) tensormap_acquire(P.map[z]);
@@ -851,31 +897,43 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adj_tc_batch(const __grid_cons
 
 __global__ void sigma_t_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.z];
-  if ((int)blockIdx.y >= d.na64) return;
-  sigma_t_body(blockIdx.x, gridDim.x, blockIdx.y, d.sigma, d.ns, d.n, d.ns8,
+  const int64_t nbx = (d.ns8 + 255) / 256;
+  const int nb = (int)(nbx < 1 ? 1 : (nbx > 64 ? 64 : nbx));
+  if ((int)blockIdx.y >= d.na64 || (int)blockIdx.x >= nb) return;
+  sigma_t_body(blockIdx.x, nb, blockIdx.y, d.sigma, d.ns, d.n, d.ns8,
                reinterpret_cast<uint16_t*>(d.sigt));
+}
+
+// blocks of an elementwise kernel over `elems` (the single-problem launches' count)
+__device__ __host__ __forceinline__ int elem_blocks(int64_t elems) {
+  const int64_t b = (elems + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b));
 }
 
 __global__ void bplanes_p_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
+  const int nb = elem_blocks((int64_t)d.mt1 * 128 * d.na64);
+  if ((int)blockIdx.x >= nb) return;
   if (d.cplx)
-    bplanes_body<true, false>(blockIdx.x, gridDim.x, reinterpret_cast<const double*>(d.p),
+    bplanes_body<true, false>(blockIdx.x, nb, reinterpret_cast<const double*>(d.p),
                               d.m + 1, d.n + 1, d.n + 1, nullptr, nullptr, 0, d.mt1, d.na64,
                               reinterpret_cast<uint16_t*>(d.xbf), d.done);
   else
-    bplanes_body<false, false>(blockIdx.x, gridDim.x, reinterpret_cast<const double*>(d.p),
+    bplanes_body<false, false>(blockIdx.x, nb, reinterpret_cast<const double*>(d.p),
                                d.m + 1, d.n + 1, d.n + 1, nullptr, nullptr, 0, d.mt1, d.na64,
                                reinterpret_cast<uint16_t*>(d.xbf), d.done);
 }
 
 __global__ void bplanes_rbm_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
+  const int nb = elem_blocks((int64_t)d.wmt * 128 * d.wna64);
+  if ((int)blockIdx.x >= nb) return;
   if (d.cplx)
-    bplanes_body<true, true>(blockIdx.x, gridDim.x, nullptr, d.m, d.n + 1, 0, d.w, d.b, d.n,
+    bplanes_body<true, true>(blockIdx.x, nb, nullptr, d.m, d.n + 1, 0, d.w, d.b, d.n,
                              d.wmt, d.wna64, reinterpret_cast<uint16_t*>(d.ws + d.ws_wbf),
                              nullptr);
   else
-    bplanes_body<false, true>(blockIdx.x, gridDim.x, nullptr, d.m, d.n + 1, 0, d.w, d.b, d.n,
+    bplanes_body<false, true>(blockIdx.x, nb, nullptr, d.m, d.n + 1, 0, d.w, d.b, d.n,
                               d.wmt, d.wna64, reinterpret_cast<uint16_t*>(d.ws + d.ws_wbf),
                               nullptr);
 }
@@ -886,7 +944,7 @@ static unsigned vec_blocks(int64_t elems) {
 
 nk_status launch_fwd_tc_batch(const FwdBatch& P, int G, int max_tiles, int max_na64,
                               cudaStream_t st) {
-  const size_t smem = fwd_smem_bytes(max_na64);
+  const size_t smem = fwd_smem_bytes(max_na64, kFwdBatchStages);
   if (cudaFuncSetAttribute(fwd_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return fail(NK_ERR_CUDA, "fwd_tc_batch: shared memory attribute");
