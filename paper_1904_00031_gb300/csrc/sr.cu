@@ -24,14 +24,15 @@
 
 namespace nk {
 
-constexpr int kVecBlocks = 256;   // largest grid of the CG vector kernels
+constexpr int kVecBlocks = 1024;  // largest grid of the CG vector kernels
 
-// Blocks of a CG vector kernel over `elems` elements: about 2048 elements per
-// 256-thread block, at most kVecBlocks (the partial-sum slots of `red`).  The
-// single-problem and the batched launches use the same count per problem, so
-// their reductions run in the same order.
+// Blocks of a CG vector kernel over `elems` elements: about 1024 elements per
+// 256-thread block, at most kVecBlocks (the partial-sum slots of `red`), so that
+// large problems keep enough loads in flight and small ones do not pay for idle
+// blocks.  The single-problem and the batched launches use the same count per
+// problem, so their reductions run in the same order.
 static int sr_vec_blocks(int64_t elems) {
-  return (int)std::min<int64_t>(kVecBlocks, std::max<int64_t>(1, (elems + 2047) / 2048));
+  return (int)std::min<int64_t>(kVecBlocks, std::max<int64_t>(1, (elems + 1023) / 1024));
 }
 constexpr int kVecThreads = 256;
 constexpr int kAdjBK = 16;
@@ -136,7 +137,7 @@ __device__ __forceinline__ double block_sum(double v) {
   return t;
 }
 
-// Sum of kVecBlocks partials in a fixed order (every block gets the same value).
+// Sum of nb block partials in a fixed order (every block gets the same value).
 __device__ __forceinline__ double sum_partials(const double* red, int nb) {
   __shared__ double tot;
   if (threadIdx.x < 32) {
@@ -851,7 +852,7 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
         return e;
       if (nk_status e = launch_fwd_tc(fa, sc + L.xbf, st)) return e;
     } else {
-      to_f32_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.p, sc + L.xf, L.pa, scal);
+      to_f32_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.p, sc + L.xf, L.pa, scal);
       forward_fp32_kernel<CPLX><<<(unsigned)sg_blocks, kSgThreads, 0, st>>>(
           sigma, ns, n, m, sc + L.xf, T, sc + L.y, scal);
     }
@@ -1157,7 +1158,7 @@ static nk_status time_adjoint(const nk_rbm* r, const int8_t* sigma, const void* 
     else
       launch_adjoint_fp32<CPLX>(sigma, T, sc + L.v, ns, r->n, r->m, splits, sc + L.part, nullptr,
                                 st);
-    reduce_parts_kernel<CPLX><<<kVecBlocks, kVecThreads, 0, st>>>(
+    reduce_parts_kernel<CPLX><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(
         sc + L.part, splits, L.pa, corner, sc + L.ap, nullptr, 0.0, nullptr, nullptr);
     cudaEventRecord(e1, st);
     if (e == NK_OK) e = check_launch("nk_sr_tune");
@@ -1269,9 +1270,9 @@ nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const d
       launch_adjoint_fp32<true>(sigma, T, sc + L.v, ns, r->n, r->m, splits, sc + L.part, nullptr,
                                 st);
     }
-    reduce_parts_kernel<true><<<kVecBlocks, kVecThreads, 0, st>>>(
+    reduce_parts_kernel<true><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(
         sc + L.part, splits, L.pa, corner, sc + L.x, nullptr, 0.0, nullptr, nullptr);
-    scatter_grad_kernel<true><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, r->n, r->m, grad);
+    scatter_grad_kernel<true><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(sc + L.x, r->n, r->m, grad);
   } else {
     copy_g_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(g, sc + L.v, ns);
     if (tc) {
@@ -1280,9 +1281,9 @@ nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const d
       launch_adjoint_fp32<false>(sigma, T, sc + L.v, ns, r->n, r->m, splits, sc + L.part, nullptr,
                                  st);
     }
-    reduce_parts_kernel<false><<<kVecBlocks, kVecThreads, 0, st>>>(
+    reduce_parts_kernel<false><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(
         sc + L.part, splits, L.pa, corner, sc + L.x, nullptr, 0.0, nullptr, nullptr);
-    scatter_grad_kernel<false><<<kVecBlocks, kVecThreads, 0, st>>>(sc + L.x, r->n, r->m, grad);
+    scatter_grad_kernel<false><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(sc + L.x, r->n, r->m, grad);
   }
   return check_launch("nk_rbm_logpsi_backward");
 }
