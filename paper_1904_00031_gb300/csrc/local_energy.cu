@@ -344,9 +344,8 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
             const float2 tdy = f2fma(tx, dy, f2mul(ty, dx));
             const float2 rx = f2fma(ns2[p][qp], tdx, cx);
             const float2 ry = f2fma(ns2[p][qp], tdy, cy);
-            const float2 nry = f2mul(ry, make_float2(-1.f, -1.f));
             const float2 px = Px[p][qp], py = Py[p][qp];
-            Px[p][qp] = f2fma(py, nry, f2mul(px, rx));
+            Px[p][qp] = f2fma(make_float2(-py.x, -py.y), ry, f2mul(px, rx));
             Py[p][qp] = f2fma(py, rx, f2mul(px, ry));
           }
         }
