@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   int nn = 0;              // non-null steps so far (identical in the warps of a chain)
   // per lane: the draws of step (block start + lane): proposed sites, accept
   // uniform and a_i - a_k, fetched once per 32 steps and broadcast by shuffles
+  int sweep_pos = 0, sweep_no = 0;  // step within the sweep, sweeps completed
   int kslot = 0;          // ring slot of the current step (step % R)
   uint32_t kphase = 0u;   // phase of its full barrier ((step / R) & 1)
   int my_i = 0, my_k = -1;
@@ -447,8 +448,9 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
       }
     }
     if (w == 0) timed_out = __shfl_sync(0xffffffffu, (int)timed_out, 0) != 0;
-    if ((step + 1) % n == 0) {
-      const int sweep = (step + 1) / n - 1;
+    if (++sweep_pos == n) {  // the last step of a sweep
+      sweep_pos = 0;
+      const int sweep = sweep_no++;
       if (sweep >= A.n_discard && h == 0) {
         int8_t* out = A.samples + ((int64_t)c * A.n_samples + (sweep - A.n_discard)) * n;
         for (int ii = lane; ii < n; ii += 32) out[ii] = sg[ii];
