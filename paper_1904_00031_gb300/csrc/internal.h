@@ -51,7 +51,7 @@ struct SrLayout {
   int splits_fp32, splits_tc;  // heuristic split-K counts
   int na64, mt1;      // tensor-core path: n + 1 padded to 64; tiles of the m + 1 rows
   int64_t ns8;        // ns rounded up to 8
-  size_t x, r, p, ap, xf, part, y, v, red, scal, sigt, xbf, total;
+  size_t x, r, p, ap, xf, part, y, v, red, scal, sigt, sigr, xbf, total;
   SrLayout(int n_, int m_, int cplx_, int64_t ns_);
 };
 

@@ -35,6 +35,9 @@ static int sr_vec_blocks(int64_t elems) {
   return (int)std::min<int64_t>(kVecBlocks, std::max<int64_t>(1, (elems + 1023) / 1024));
 }
 constexpr int kVecThreads = 256;
+// Elements per thread whose loads are issued together in the vector kernels
+// (a thread's elements are still visited, and summed, in grid-stride order).
+constexpr int kVecUnroll = 4;
 constexpr int kAdjBK = 16;
 
 // scalars in the scratch `scal` block
@@ -58,7 +61,8 @@ SrLayout::SrLayout(int n_, int m_, int cplx_, int64_t ns_) : n(n_), m(m_), cplx(
   sp = std::min<int64_t>(sp, std::max<int64_t>(1, ns / 256));
   splits_fp32 = (int)std::max<int64_t>(1, std::min<int64_t>(sp, 64));
   splits_tc = adj_tc_splits(n, m, cplx, ns);
-  splits = std::min(64, 2 * std::max(splits_fp32, splits_tc));
+  const int tiles_tc = (m + 1 + tc_hidden_per_tile(cplx) - 1) / tc_hidden_per_tile(cplx);
+  splits = std::min(64, std::max(2 * std::max(splits_fp32, splits_tc), (4 * 152) / tiles_tc));
   na64 = (int)round_up(n + 1, 64);
   mt1 = (m + 1 + tc_hidden_per_tile(cplx) - 1) / tc_hidden_per_tile(cplx);
   ns8 = round_up(std::max<int64_t>(ns, 1), 8);
@@ -81,6 +85,7 @@ SrLayout::SrLayout(int n_, int m_, int cplx_, int64_t ns_) : n(n_), m(m_), cplx(
   red = take(4 * kVecBlocks * sizeof(double));
   scal = take(SC_LEN * sizeof(double));
   sigt = take((size_t)na64 * ns8 * 2);
+  sigr = take((size_t)std::max<int64_t>(ns, 1) * na64 * 2);
   xbf = take((size_t)2 * mt1 * 128 * na64 * 2);
   total = off;
 }
@@ -393,15 +398,26 @@ __device__ __forceinline__ void center_partial_body(int bx, int gx,
   if (scal[SC_DONE] != 0.0) return;
   const double invn = 1.0 / (double)ns;
   double sr = 0.0, si = 0.0;
-  for (int64_t s = bx * (int64_t)blockDim.x + threadIdx.x; s < ns;
-       s += (int64_t)gx * blockDim.x) {
-    const double w = weights ? weights[s] : invn;
-    if (CPLX) {
-      const double2 y = reinterpret_cast<const double2*>(yv)[s];
-      sr += w * y.x;
-      si += w * y.y;
-    } else {
-      sr += w * reinterpret_cast<const double*>(yv)[s];
+  const int64_t stride = (int64_t)gx * blockDim.x;
+  for (int64_t s0 = bx * (int64_t)blockDim.x + threadIdx.x; s0 < ns;
+       s0 += kVecUnroll * stride) {
+    double w[kVecUnroll];
+    double2 y[kVecUnroll];
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      const int64_t s = s0 + u * stride;
+      if (s < ns) {
+        w[u] = weights ? weights[s] : invn;
+        y[u] = CPLX ? reinterpret_cast<const double2*>(yv)[s]
+                    : make_double2(reinterpret_cast<const double*>(yv)[s], 0.0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      if (s0 + u * stride < ns) {
+        sr += w[u] * y[u].x;
+        if (CPLX) si += w[u] * y[u].y;
+      }
     }
   }
   const double br = block_sum(sr);
@@ -427,14 +443,30 @@ __device__ __forceinline__ void center_apply_body(int bx, int gx,
   const double mr = sum_partials(red + 2 * kVecBlocks, nb);
   const double mi = sum_partials(red + 3 * kVecBlocks, nb);
   const double invn = 1.0 / (double)ns;
-  for (int64_t s = bx * (int64_t)blockDim.x + threadIdx.x; s < ns;
-       s += (int64_t)gx * blockDim.x) {
-    const double w = weights ? weights[s] : invn;
-    if (CPLX) {
-      const double2 y = reinterpret_cast<const double2*>(yv)[s];
-      reinterpret_cast<double2*>(vout)[s] = make_double2(w * (y.x - mr), w * (y.y - mi));
-    } else {
-      reinterpret_cast<double*>(vout)[s] = w * (reinterpret_cast<const double*>(yv)[s] - mr);
+  const int64_t stride = (int64_t)gx * blockDim.x;
+  for (int64_t s0 = bx * (int64_t)blockDim.x + threadIdx.x; s0 < ns;
+       s0 += kVecUnroll * stride) {
+    double w[kVecUnroll];
+    double2 y[kVecUnroll];
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      const int64_t s = s0 + u * stride;
+      if (s < ns) {
+        w[u] = weights ? weights[s] : invn;
+        y[u] = CPLX ? reinterpret_cast<const double2*>(yv)[s]
+                    : make_double2(reinterpret_cast<const double*>(yv)[s], 0.0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      const int64_t s = s0 + u * stride;
+      if (s < ns) {
+        if (CPLX)
+          reinterpret_cast<double2*>(vout)[s] =
+              make_double2(w[u] * (y[u].x - mr), w[u] * (y[u].y - mi));
+        else
+          reinterpret_cast<double*>(vout)[s] = w[u] * (y[u].x - mr);
+      }
     }
   }
 }
@@ -457,22 +489,42 @@ __device__ __forceinline__ void reduce_parts_body(int bx, int gx,
   DT* out = reinterpret_cast<DT*>(outv);
   const DT* p = reinterpret_cast<const DT*>(pv);
   double dot = 0.0;
-  for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < pa;
-       e += (int64_t)gx * blockDim.x) {
-    DT acc = D<CPLX>::zero();
+  const int64_t stride = (int64_t)gx * blockDim.x;
+  for (int64_t e0 = bx * (int64_t)blockDim.x + threadIdx.x; e0 < pa;
+       e0 += kVecUnroll * stride) {
+    DT acc[kVecUnroll], pp[kVecUnroll];
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      acc[u] = D<CPLX>::zero();
+      pp[u] = D<CPLX>::zero();
+      if (p && e0 + u * stride < pa) pp[u] = p[e0 + u * stride];
+    }
     for (int z = 0; z < splits; ++z) {
-      if constexpr (CPLX) {
-        float2 v = reinterpret_cast<const float2*>(partv)[(int64_t)z * pa + e];
-        acc.x += (double)v.x;
-        acc.y += (double)v.y;
-      } else {
-        acc += (double)reinterpret_cast<const float*>(partv)[(int64_t)z * pa + e];
+#pragma unroll
+      for (int u = 0; u < kVecUnroll; ++u) {
+        const int64_t e = e0 + u * stride;
+        if (e < pa) {
+          if constexpr (CPLX) {
+            const float2 v = reinterpret_cast<const float2*>(partv)[(int64_t)z * pa + e];
+            acc[u].x += (double)v.x;
+            acc[u].y += (double)v.y;
+          } else {
+            acc[u] += (double)reinterpret_cast<const float*>(partv)[(int64_t)z * pa + e];
+          }
+        }
       }
     }
-    if (p) acc = axpy(eps, p[e], acc);
-    if (e == corner) acc = D<CPLX>::zero();
-    out[e] = acc;
-    if (p) dot += cdot_re(p[e], acc);
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      const int64_t e = e0 + u * stride;
+      if (e < pa) {
+        DT a = acc[u];
+        if (p) a = axpy(eps, pp[u], a);
+        if (e == corner) a = D<CPLX>::zero();
+        out[e] = a;
+        if (p) dot += cdot_re(pp[u], a);
+      }
+    }
   }
   if (red) {
     double b = block_sum(dot);
@@ -496,11 +548,22 @@ __device__ __forceinline__ void cg_init_body(int bx, int gx, void* xv, void* rv,
   DT* r = reinterpret_cast<DT*>(rv);
   DT* p = reinterpret_cast<DT*>(pv);
   double nn = 0.0;
-  for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < pa;
-       e += (int64_t)gx * blockDim.x) {
-    x[e] = D<CPLX>::zero();
-    p[e] = r[e];
-    nn += norm2(r[e]);
+  const int64_t stride = (int64_t)gx * blockDim.x;
+  for (int64_t e0 = bx * (int64_t)blockDim.x + threadIdx.x; e0 < pa;
+       e0 += kVecUnroll * stride) {
+    DT rr[kVecUnroll];
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u)
+      if (e0 + u * stride < pa) rr[u] = r[e0 + u * stride];
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      const int64_t e = e0 + u * stride;
+      if (e < pa) {
+        x[e] = D<CPLX>::zero();
+        p[e] = rr[u];
+        nn += norm2(rr[u]);
+      }
+    }
   }
   double b = block_sum(nn);
   if (threadIdx.x == 0) red[kVecBlocks + bx] = b;
@@ -547,12 +610,30 @@ __device__ __forceinline__ void cg_step_x_body(int bx, int gx, void* xv, void* r
   const double rs = scal[(it & 1) ? SC_RS1 : SC_RS0];
   const double alpha = rs / pap;
   double nn = 0.0;
-  for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < pa;
-       e += (int64_t)gx * blockDim.x) {
-    x[e] = axpy(alpha, p[e], x[e]);
-    DT rr = axpy(-alpha, ap[e], r[e]);
-    r[e] = rr;
-    nn += norm2(rr);
+  const int64_t stride = (int64_t)gx * blockDim.x;
+  for (int64_t e0 = bx * (int64_t)blockDim.x + threadIdx.x; e0 < pa;
+       e0 += kVecUnroll * stride) {
+    DT pp[kVecUnroll], xx[kVecUnroll], aa[kVecUnroll], rr[kVecUnroll];
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      const int64_t e = e0 + u * stride;
+      if (e < pa) {
+        pp[u] = p[e];
+        xx[u] = x[e];
+        aa[u] = ap[e];
+        rr[u] = r[e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      const int64_t e = e0 + u * stride;
+      if (e < pa) {
+        x[e] = axpy(alpha, pp[u], xx[u]);
+        const DT q = axpy(-alpha, aa[u], rr[u]);
+        r[e] = q;
+        nn += norm2(q);
+      }
+    }
   }
   double b = block_sum(nn);
   if (threadIdx.x == 0) red[kVecBlocks + bx] = b;
@@ -583,9 +664,24 @@ __device__ __forceinline__ void cg_step_p_body(int bx, int gx, const void* rv, v
   const bool bad = !isfinite(rs_new);
   if (!conv && !bad) {
     const double beta = rs_new / rs;
-    for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < pa;
-         e += (int64_t)gx * blockDim.x)
-      p[e] = axpy(beta, p[e], r[e]);
+    const int64_t stride = (int64_t)gx * blockDim.x;
+    for (int64_t e0 = bx * (int64_t)blockDim.x + threadIdx.x; e0 < pa;
+         e0 += kVecUnroll * stride) {
+      DT pp[kVecUnroll], rr[kVecUnroll];
+#pragma unroll
+      for (int u = 0; u < kVecUnroll; ++u) {
+        const int64_t e = e0 + u * stride;
+        if (e < pa) {
+          pp[u] = p[e];
+          rr[u] = r[e];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kVecUnroll; ++u) {
+        const int64_t e = e0 + u * stride;
+        if (e < pa) p[e] = axpy(beta, pp[u], rr[u]);
+      }
+    }
   }
   if (bx == 0 && threadIdx.x == 0) {
     scal[(it & 1) ? SC_RS0 : SC_RS1] = rs_new;
@@ -821,6 +917,7 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
     fa.y = sc + L.y;
     fa.skip = scal + SC_DONE;
     fa.err = err;
+    fa.sig_rows = sc + L.sigr;
   }
   stats_kernel<CPLX><<<1, 1024, 0, st>>>(eloc, weights, ns, n_chains, info, scal, sc + L.v);
   if (nk_status e = check_launch("nk_sr_step(stats)")) return e;
@@ -829,6 +926,7 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
   // F = adjoint(w o (E - <E>)) -> r
   if (tc) {
     if (nk_status e = launch_sigma_t(sigma, ns, n, L.na64, sc + L.sigt, st)) return e;
+    if (nk_status e = launch_sigma_rows(sigma, ns, n, L.na64, sc + L.sigr, st)) return e;
     aa.v = sc + L.v;
     aa.skip = nullptr;
     if (nk_status e = launch_adj_tc(aa, sc + L.sigt, st)) return e;
@@ -1186,14 +1284,23 @@ nk_status run_sr_tune(nk_rbm* r, const int8_t* sigma, const void* t, int64_t ns,
     if (nk_status e = launch_sigma_t(sigma, ns, r->n, L.na64, sc + L.sigt, st)) return e;
   }
   const int h = prec == NK_PREC_BF16X2 ? L.splits_tc : L.splits_fp32;
-  int cand[6] = {h / 4, h / 2, h, (3 * h) / 2, 2 * h, 0};
+  // candidates: the heuristic, half of it, and the split counts that fill
+  // one to four whole waves of adjoint CTAs (one per SM)
+  const int hj = tc_hidden_per_tile(r->is_complex);
+  const int tiles = prec == NK_PREC_BF16X2 ? (r->m + 1 + hj - 1) / hj
+                                           : ceil_div(L.na, 64) * ceil_div(L.ma, 64);
+  int cand[6] = {h, h / 2};
+  for (int k = 1; k <= 4; ++k) cand[1 + k] = (k * 152) / tiles;
   int best_s = sr_choose_splits(L, prec, h);
   float best_t = 1e30f;
-  int last = -1;
-  for (int k = 0; k < 5; ++k) {
+  int tried[6];
+  int n_tried = 0;
+  for (int k = 0; k < 6; ++k) {
     const int sp = sr_choose_splits(L, prec, std::max(1, cand[k]));
-    if (sp == last) continue;
-    last = sp;
+    bool seen = false;
+    for (int u = 0; u < n_tried; ++u) seen = seen || tried[u] == sp;
+    if (seen) continue;
+    tried[n_tried++] = sp;
     float ms = 0.f;
     nk_status e = r->is_complex
                       ? time_adjoint<true>(r, sigma, t, ns, prec, sc, L, sp, st, &ms)

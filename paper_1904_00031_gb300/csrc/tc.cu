@@ -214,6 +214,38 @@ nk_status launch_sigma_t(const int8_t* sigma, int64_t ns, int n, int na64, void*
   return check_launch("sigma_t");
 }
 
+// sigma' rows: thread per 16-B chunk of 8 BF16 values (coalesced stores)
+__global__ void sigma_rows_kernel(const int8_t* __restrict__ sigma, int64_t ns, int n, int na64,
+                                  uint16_t* __restrict__ out) {
+  const int cpr = na64 / 8;  // chunks per row
+  const int64_t tot = ns * cpr;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < tot;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = x / cpr;
+    const int i0 = (int)(x % cpr) * 8;
+    uint32_t pk[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t v[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + 2 * q + h;
+        v[h] = i < n ? (sigma[s * n + i] > 0 ? 0x3F80u : 0xBF80u) : (i == n ? 0x3F80u : 0u);
+      }
+      pk[q] = v[0] | (v[1] << 16);
+    }
+    *reinterpret_cast<uint4*>(out + s * na64 + i0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+}
+
+nk_status launch_sigma_rows(const int8_t* sigma, int64_t ns, int n, int na64, void* out,
+                            cudaStream_t st) {
+  const int64_t tot = ns * (na64 / 8);
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 8));
+  sigma_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(sigma, ns, n, na64, (uint16_t*)out);
+  return check_launch("sigma_rows");
+}
+
 // ------------------------------------------------------------------ forward
 
 constexpr int kFwdStages = 3;
@@ -233,10 +265,12 @@ __device__ __forceinline__ uint32_t sig_bits(const int8_t* sigma, int64_t s, int
 
 // STAGES: B-operand stages; PREFETCH: the next tile's T values are loaded into
 // registers while its MMAs run (else each 16-unit chunk is loaded just before
-// use, which needs far fewer registers).
-template <bool CPLX, int STAGES, bool PREFETCH>
+// use, which needs far fewer registers); SIG_TMA: the sigma' sample tile is
+// TMA-loaded from the BF16 rows of launch_sigma_rows (map `sgp`), else built
+// from the int8 samples by the CTA.
+template <bool CPLX, int STAGES, bool PREFETCH, bool SIG_TMA = false>
 __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcArgs& A, int bx,
-                                            int seg) {
+                                            int seg, const CUtensorMap* sgp = nullptr) {
   if (A.skip && *A.skip != 0.0) return;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = align1024(smraw);
@@ -247,7 +281,8 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
-  uint32_t* slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* afull = tempty + 2;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(afull + 1);
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int64_t s0 = (int64_t)bx * 128;
 
@@ -260,11 +295,12 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
       mbar_init(&tfull[k], 1);
       mbar_init(&tempty[k], 4);
     }
+    mbar_init(afull, 1);
     mbar_fence_init();
   }
   if (w == 1) tmem_alloc(slot, 256);
   // resident sigma' tile: 128 rows x KC * 64 columns, 16-B chunks of 8 BF16
-  for (int x = tid; x < 128 * KC * 8; x += blockDim.x) {
+  for (int x = tid; x < (SIG_TMA ? 0 : 128 * KC * 8); x += blockDim.x) {
     const int r = x / (KC * 8), rem = x % (KC * 8), kc = rem >> 3, c = rem & 7;
     const int64_t s = s0 + r;
     const int i0 = kc * 64 + c * 8;
@@ -288,6 +324,11 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
 
   if (w == 0) {
     if (lane == 0) {
+      if (SIG_TMA && total_it > 0) {
+        mbar_arrive_expect_tx(afull, (uint32_t)KC * 16384u);
+        for (int kc = 0; kc < KC; ++kc)
+          tma_load_2d(sA + (size_t)kc * 16384, sgp, kc * 64, (int)s0, afull);
+      }
       for (int it = 0; it < total_it; ++it) {
         const int st = it % STAGES, u = it / STAGES, jt = jt_begin + it / KC,
                   kc = it % KC;
@@ -305,6 +346,7 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(128, 128);
       int it = 0;
+      if (SIG_TMA && total_it > 0 && !mbar_wait_bounded(afull, 0u)) bad = true;
       for (int jt = jt_begin; jt < jt_end && !bad; ++jt) {
         const int acc = (jt - jt_begin) & 1, ua = (jt - jt_begin) >> 1;
         if (ua > 0 && !mbar_wait_bounded(&tempty[acc], (uint32_t)((ua - 1) & 1))) {
@@ -537,10 +579,11 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
   }
 }
 
-template <bool CPLX>
+template <bool CPLX, bool SIG_TMA>
 __global__ void __launch_bounds__(kFwdThreads, 1)
-    fwd_tc_kernel(const __grid_constant__ CUtensorMap tb, FwdTcArgs A) {
-  fwd_tc_body<CPLX, kFwdStages, true>(&tb, A, blockIdx.x, blockIdx.y);
+    fwd_tc_kernel(const __grid_constant__ CUtensorMap tb, const __grid_constant__ CUtensorMap sg,
+                  FwdTcArgs A) {
+  fwd_tc_body<CPLX, kFwdStages, true, SIG_TMA>(&tb, A, blockIdx.x, blockIdx.y, &sg);
 }
 
 static size_t fwd_smem_bytes(int na64, int stages = kFwdStages) {
@@ -550,19 +593,27 @@ static size_t fwd_smem_bytes(int na64, int stages = kFwdStages) {
 nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st) {
   if (!tc_supported_shape(A.n, A.m))
     return fail(NK_ERR_UNSUPPORTED, "tensor-core path supports n + 1 <= 448 (n = %d)", A.n);
-  CUtensorMap map;
+  CUtensorMap map, smap;
   if (!tc_make_map(&map, planes, 2LL * A.mt * 128, A.na64, A.na64, 128)) return NK_ERR_CUDA;
+  const bool sig_tma = A.mode == 0 && A.sig_rows != nullptr;
+  if (sig_tma) {
+    if (!tc_make_map(&smap, A.sig_rows, A.ns, A.na64, A.na64, 128)) return NK_ERR_CUDA;
+  } else {
+    smap = map;  // unused
+  }
   const size_t smem = fwd_smem_bytes(A.na64);
   const int64_t blocks = (A.ns + 127) / 128;
-  // one CTA per SM: for ln psi (mode 1), when the last wave would be far from
-  // full, split the hidden tiles into two halves (twice the CTAs) whose sums
-  // meet in the output.  (In the SR forward, mode 0, the extra sigma' tile
-  // builds and output atomics cost more than the evener waves save.)
+  // one CTA per SM: when the last wave would be far from full, split the hidden
+  // tiles into two halves (twice the CTAs) whose sums meet in the output.  (An
+  // SR forward that builds its sigma' tiles itself does not split: the extra
+  // builds cost more than the evener waves save.)
   auto wave_eff = [&](int64_t b) {
     return (double)b / (double)(((b + 151) / 152) * 152);
   };
   FwdTcArgs B = A;
-  B.nseg = (A.mode == 1 && A.mt >= 2 && wave_eff(2 * blocks) > wave_eff(blocks)) ? 2 : 1;
+  B.nseg = ((A.mode == 1 || sig_tma) && A.mt >= 2 && wave_eff(2 * blocks) > wave_eff(blocks))
+               ? 2
+               : 1;
   if (B.nseg == 2) {
     void* out = A.mode == 0 ? A.y : (void*)A.logpsi;
     const size_t per = (A.mode == 1 || A.cplx) ? 16 : 8;
@@ -570,18 +621,15 @@ nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st)
       return fail(NK_ERR_CUDA, "fwd_tc: cudaMemsetAsync failed");
   }
   const dim3 grid((unsigned)blocks, (unsigned)B.nseg);
-  if (A.cplx) {
-    if (cudaFuncSetAttribute(fwd_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+  auto go = [&](auto kern) -> nk_status {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
       return fail(NK_ERR_CUDA, "fwd_tc: shared memory attribute");
-    fwd_tc_kernel<true><<<grid, kFwdThreads, smem, st>>>(map, B);
-  } else {
-    if (cudaFuncSetAttribute(fwd_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return fail(NK_ERR_CUDA, "fwd_tc: shared memory attribute");
-    fwd_tc_kernel<false><<<grid, kFwdThreads, smem, st>>>(map, B);
-  }
-  return check_launch("fwd_tc");
+    kern<<<grid, kFwdThreads, smem, st>>>(map, smap, B);
+    return check_launch("fwd_tc");
+  };
+  if (A.cplx) return sig_tma ? go(fwd_tc_kernel<true, true>) : go(fwd_tc_kernel<true, false>);
+  return sig_tma ? go(fwd_tc_kernel<false, true>) : go(fwd_tc_kernel<false, false>);
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -832,7 +880,9 @@ int adj_tc_splits(int n, int m, int cplx, int64_t ns) {
   (void)n;
   const int HJ = cplx ? 64 : 128;
   const int tiles = (m + 1 + HJ - 1) / HJ;
-  int64_t sp = (2 * 152 + tiles - 1) / tiles;
+  // at most two full waves of one CTA per SM (a third, nearly empty wave
+  // would cost as much as a full one)
+  int64_t sp = std::max(1, (2 * 152) / tiles);
   sp = std::min<int64_t>(sp, std::max<int64_t>(1, (ns + 63) / 64));
   return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 64));
 }

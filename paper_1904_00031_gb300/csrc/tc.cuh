@@ -30,6 +30,10 @@ nk_status launch_bplanes_from_rbm(const nk_rbm* r, cudaStream_t st);
 
 // sigma' transposed, BF16 [na64][ns8]: sigma'[s][i] = sigma (i < n), 1 (i = n),
 // 0 beyond; ns8 = ns rounded up to 8.
+// sigma' rows as BF16 [ns][na64]: sigma_i (i < n), 1 (i = n), 0 beyond; the A
+// operand of the SR forward, TMA-loaded per 128-sample tile.
+nk_status launch_sigma_rows(const int8_t* sigma, int64_t ns, int n, int na64, void* out,
+                            cudaStream_t st);
 nk_status launch_sigma_t(const int8_t* sigma, int64_t ns, int n, int na64, void* out,
                          cudaStream_t st);
 
@@ -50,6 +54,8 @@ struct FwdTcArgs {
   const double* skip;     // if non-null and *skip != 0, the kernel returns at once
   int* err;               // set on a timed-out wait (may be null)
   int nseg = 1;           // set by launch_fwd_tc: 1, or 2 halves of the hidden tiles
+  const void* sig_rows = nullptr;  // mode 0: sigma' as BF16 [ns][na64] (launch_sigma_rows);
+                                   // the sample tiles are then TMA-loaded, else built
 };
 nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st);
 
