@@ -478,7 +478,17 @@ __global__ void __launch_bounds__(kVecThreads) center_apply_kernel(
   center_apply_body<CPLX>(blockIdx.x, gridDim.x, yv, vout, weights, ns, red, scal, nb);
 }
 
+// s + e = a + b exactly (Knuth's TwoSum in FP32)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 // out = sum_z part[z] (+ eps * p);  red[b] = sum conj(p) . out (if p given).
+// The FP32 partials of the splits are added in split order as an unevaluated
+// FP32 pair (running sum and running error of TwoSum), converted to FP64 once:
+// FP64 arithmetic is a small fraction of the FP32 rate on this GPU.
 // The element X'[m][n] (no parameter) is forced to 0.
 template <bool CPLX>
 __device__ __forceinline__ void reduce_parts_body(int bx, int gx, 
@@ -492,33 +502,55 @@ __device__ __forceinline__ void reduce_parts_body(int bx, int gx,
   const int64_t stride = (int64_t)gx * blockDim.x;
   for (int64_t e0 = bx * (int64_t)blockDim.x + threadIdx.x; e0 < pa;
        e0 += kVecUnroll * stride) {
-    DT acc[kVecUnroll], pp[kVecUnroll];
+    float2 hi[kVecUnroll], lo[kVecUnroll];
+    DT pp[kVecUnroll];
 #pragma unroll
     for (int u = 0; u < kVecUnroll; ++u) {
-      acc[u] = D<CPLX>::zero();
+      hi[u] = make_float2(0.f, 0.f);
+      lo[u] = make_float2(0.f, 0.f);
       pp[u] = D<CPLX>::zero();
       if (p && e0 + u * stride < pa) pp[u] = p[e0 + u * stride];
     }
-    for (int z = 0; z < splits; ++z) {
+    // the partials of up to kZ splits are loaded together, then added in split order
+    constexpr int kZ = 4;
+    for (int z0 = 0; z0 < splits; z0 += kZ) {
+      float2 v[kZ][kVecUnroll];
 #pragma unroll
-      for (int u = 0; u < kVecUnroll; ++u) {
-        const int64_t e = e0 + u * stride;
-        if (e < pa) {
-          if constexpr (CPLX) {
-            const float2 v = reinterpret_cast<const float2*>(partv)[(int64_t)z * pa + e];
-            acc[u].x += (double)v.x;
-            acc[u].y += (double)v.y;
-          } else {
-            acc[u] += (double)reinterpret_cast<const float*>(partv)[(int64_t)z * pa + e];
+      for (int zz = 0; zz < kZ; ++zz)
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+          const int64_t e = e0 + u * stride;
+          v[zz][u] = make_float2(0.f, 0.f);
+          if (z0 + zz < splits && e < pa) {
+            const int64_t o = (int64_t)(z0 + zz) * pa + e;
+            if constexpr (CPLX) v[zz][u] = reinterpret_cast<const float2*>(partv)[o];
+            else v[zz][u].x = reinterpret_cast<const float*>(partv)[o];
           }
         }
-      }
+#pragma unroll
+      for (int zz = 0; zz < kZ; ++zz)
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+          if (z0 + zz < splits) {
+            float er;
+            two_sum(hi[u].x, v[zz][u].x, hi[u].x, er);
+            lo[u].x += er;
+            if constexpr (CPLX) {
+              two_sum(hi[u].y, v[zz][u].y, hi[u].y, er);
+              lo[u].y += er;
+            }
+          }
+        }
     }
 #pragma unroll
     for (int u = 0; u < kVecUnroll; ++u) {
       const int64_t e = e0 + u * stride;
       if (e < pa) {
-        DT a = acc[u];
+        DT a;
+        if constexpr (CPLX)
+          a = make_double2((double)hi[u].x + (double)lo[u].x, (double)hi[u].y + (double)lo[u].y);
+        else
+          a = (double)hi[u].x + (double)lo[u].x;
         if (p) a = axpy(eps, pp[u], a);
         if (e == corner) a = D<CPLX>::zero();
         out[e] = a;
@@ -1063,6 +1095,8 @@ nk_status sr_batch_describe(const nk_sr_batch_item* items, int n_inst, int prec,
       return NK_ERR_CUDA;
     if (!tc_make_map(&d.adj_map, sc + L.sigt, L.na64, L.ns8, L.ns8, L.na64 / 2))
       return NK_ERR_CUDA;
+    if (!tc_make_map(&d.sig_map, sc + L.sigr, it.ns, L.na64, L.na64, 128)) return NK_ERR_CUDA;
+    d.fwd_nseg = fwd_tc_nseg(it.ns, L.mt1, 0, true);
     d.splits = batch_item_splits(items, n_inst, order[z], prec);
     d.nb_pa = sr_vec_blocks(L.pa);
     d.nb_ns = sr_vec_blocks(it.ns);
@@ -1101,6 +1135,7 @@ nk_status sr_batch_describe(const nk_sr_batch_item* items, int n_inst, int prec,
     d.y = sc + L.y;
     d.v = sc + L.v;
     d.sigt = sc + L.sigt;
+    d.sigr = sc + L.sigr;
     d.xbf = sc + L.xbf;
     d.red = (double*)(sc + L.red);
     d.scal = (double*)(sc + L.scal);
@@ -1122,7 +1157,7 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
   memset(&fb, 0, sizeof(fb));
   memset(&ab, 0, sizeof(ab));
   int max_fwd = 1, max_adj = 1, max_sp = 1, max_na64 = 64;
-  int64_t max_ns8 = 8, max_xp = 1, max_wp = 1, max_work = 1, max_minb = 1;
+  int64_t max_ns8 = 8, max_xp = 1, max_wp = 1, max_work = 1, max_minb = 1, max_rows = 1;
   for (int z = 0; z < G; ++z) {
     const nk_sr_batch_item& it = items[order[z0 + z]];
     const nk_rbm* r = it.rbm;
@@ -1147,8 +1182,9 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
     fa.y = sc + L.y;
     fa.skip = scal + SC_DONE;
     fa.err = reinterpret_cast<int*>(scal + SC_ERR);
-    fa.nseg = 1;
+    fa.nseg = fwd_tc_nseg(it.ns, L.mt1, 0, true);
     fb.map[z] = &Dg[z].fwd_map;
+    fb.smap[z] = &Dg[z].sig_map;
     fb.tiles[z] = (int)((it.ns + 127) / 128);
     AdjTcArgs& aa = ab.a[z];
     aa.T = it.t;
@@ -1166,7 +1202,8 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
     ab.chunk[z] = round_up(std::max<int64_t>((it.ns + splits - 1) / splits, 1), 64);
     ab.tiles[z] = (r->m + 1 + HJ - 1) / HJ;
     ab.splits[z] = splits;
-    max_fwd = std::max(max_fwd, fb.tiles[z]);
+    max_fwd = std::max(max_fwd, fb.tiles[z] * fa.nseg);
+    max_rows = std::max<int64_t>(max_rows, it.ns * (L.na64 / 8));
     max_adj = std::max(max_adj, ab.tiles[z]);
     max_sp = std::max(max_sp, splits);
     max_na64 = std::max(max_na64, L.na64);
@@ -1188,6 +1225,7 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
   flags_reset_batch<<<one, 32, 0, st>>>(Dg);
   if (nk_status e = check_launch("nk_sr_step_batch(stats)")) return e;
   if (nk_status e = launch_sigma_t_batch(Dg, G, max_ns8, max_na64, st)) return e;
+  if (nk_status e = launch_sigma_rows_batch(Dg, G, max_rows, st)) return e;
   if (nk_status e = launch_adj_tc_batch(ab, G, max_adj, max_sp, max_na64, st)) return e;
   reduce_parts_batch<<<vg, kVecThreads, 0, st>>>(Dg, 0, 0.0);
   cg_init_batch<<<vg, kVecThreads, 0, st>>>(Dg);

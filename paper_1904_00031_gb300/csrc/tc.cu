@@ -215,12 +215,13 @@ nk_status launch_sigma_t(const int8_t* sigma, int64_t ns, int n, int na64, void*
 }
 
 // sigma' rows: thread per 16-B chunk of 8 BF16 values (coalesced stores)
-__global__ void sigma_rows_kernel(const int8_t* __restrict__ sigma, int64_t ns, int n, int na64,
-                                  uint16_t* __restrict__ out) {
+__device__ __forceinline__ void sigma_rows_body(int bx, int gx, const int8_t* __restrict__ sigma,
+                                                int64_t ns, int n, int na64,
+                                                uint16_t* __restrict__ out) {
   const int cpr = na64 / 8;  // chunks per row
   const int64_t tot = ns * cpr;
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < tot;
-       x += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t x = bx * (int64_t)blockDim.x + threadIdx.x; x < tot;
+       x += (int64_t)gx * blockDim.x) {
     const int64_t s = x / cpr;
     const int i0 = (int)(x % cpr) * 8;
     uint32_t pk[4];
@@ -236,6 +237,11 @@ __global__ void sigma_rows_kernel(const int8_t* __restrict__ sigma, int64_t ns, 
     }
     *reinterpret_cast<uint4*>(out + s * na64 + i0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
+}
+
+__global__ void sigma_rows_kernel(const int8_t* __restrict__ sigma, int64_t ns, int n, int na64,
+                                  uint16_t* __restrict__ out) {
+  sigma_rows_body(blockIdx.x, gridDim.x, sigma, ns, n, na64, out);
 }
 
 nk_status launch_sigma_rows(const int8_t* sigma, int64_t ns, int n, int na64, void* out,
@@ -590,6 +596,16 @@ static size_t fwd_smem_bytes(int na64, int stages = kFwdStages) {
   return 1024 + (size_t)(na64 / 64) * 16384 + (size_t)stages * kStageB + 128;
 }
 
+// One CTA per SM: when the last wave would be far from full, split the hidden
+// tiles into two halves (twice the CTAs) whose sums meet in the output.  (An
+// SR forward that builds its sigma' tiles itself does not split: the extra
+// builds cost more than the evener waves save.)
+int fwd_tc_nseg(int64_t ns, int mt, int mode, bool sig_tma) {
+  const int64_t blocks = (ns + 127) / 128;
+  auto wave_eff = [](int64_t b) { return (double)b / (double)(((b + 151) / 152) * 152); };
+  return ((mode == 1 || sig_tma) && mt >= 2 && wave_eff(2 * blocks) > wave_eff(blocks)) ? 2 : 1;
+}
+
 nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st) {
   if (!tc_supported_shape(A.n, A.m))
     return fail(NK_ERR_UNSUPPORTED, "tensor-core path supports n + 1 <= 448 (n = %d)", A.n);
@@ -603,17 +619,8 @@ nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st)
   }
   const size_t smem = fwd_smem_bytes(A.na64);
   const int64_t blocks = (A.ns + 127) / 128;
-  // one CTA per SM: when the last wave would be far from full, split the hidden
-  // tiles into two halves (twice the CTAs) whose sums meet in the output.  (An
-  // SR forward that builds its sigma' tiles itself does not split: the extra
-  // builds cost more than the evener waves save.)
-  auto wave_eff = [&](int64_t b) {
-    return (double)b / (double)(((b + 151) / 152) * 152);
-  };
   FwdTcArgs B = A;
-  B.nseg = ((A.mode == 1 || sig_tma) && A.mt >= 2 && wave_eff(2 * blocks) > wave_eff(blocks))
-               ? 2
-               : 1;
+  B.nseg = fwd_tc_nseg(A.ns, A.mt, A.mode, sig_tma);
   if (B.nseg == 2) {
     void* out = A.mode == 0 ? A.y : (void*)A.logpsi;
     const size_t per = (A.mode == 1 || A.cplx) ? 16 : 8;
@@ -926,12 +933,17 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
 constexpr int kFwdBatchStages = 2;
 __global__ void __launch_bounds__(kFwdThreads, 2) fwd_tc_batch(const __grid_constant__ FwdBatch P) {
   const int z = blockIdx.z;
-  if ((int)blockIdx.x >= P.tiles[z]) return;
-  if (threadIdx.x == 0) tensormap_acquire(P.map[z]);
+  const int t = P.tiles[z];
+  if ((int)blockIdx.x >= t * P.a[z].nseg) return;
+  if (threadIdx.x == 0) {
+    tensormap_acquire(P.map[z]);
+    tensormap_acquire(P.smap[z]);
+  }
+  const int bx = (int)blockIdx.x % t, seg = (int)blockIdx.x / t;
   if (P.a[z].cplx)
-    fwd_tc_body<true, kFwdBatchStages, false>(P.map[z], P.a[z], blockIdx.x, 0);
+    fwd_tc_body<true, kFwdBatchStages, false, true>(P.map[z], P.a[z], bx, seg, P.smap[z]);
   else
-    fwd_tc_body<false, kFwdBatchStages, false>(P.map[z], P.a[z], blockIdx.x, 0);
+    fwd_tc_body<false, kFwdBatchStages, false, true>(P.map[z], P.a[z], bx, seg, P.smap[z]);
 }
 
 // Batched adjoint: two CTAs per SM (96 registers per thread).
@@ -964,6 +976,14 @@ __global__ void bplanes_p_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
   const int nb = elem_blocks((int64_t)d.mt1 * 128 * d.na64);
   if ((int)blockIdx.x >= nb) return;
+  if (d.fwd_nseg == 2 && *d.done == 0.0) {
+    // the two halves of the forward add their sums onto zero
+    double* y = reinterpret_cast<double*>(d.y);
+    const int64_t len = d.ns * (d.cplx ? 2 : 1);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)nb * blockDim.x)
+      y[e] = 0.0;
+  }
   if (d.cplx)
     bplanes_body<true, false>(blockIdx.x, nb, reinterpret_cast<const double*>(d.p),
                               d.m + 1, d.n + 1, d.n + 1, nullptr, nullptr, 0, d.mt1, d.na64,
@@ -1019,6 +1039,18 @@ nk_status launch_sigma_t_batch(const SrDesc* D, int G, int64_t max_ns8, int max_
                   (unsigned)max_na64, (unsigned)G);
   sigma_t_batch<<<grid, 256, 0, st>>>(D);
   return check_launch("sigma_t_batch");
+}
+
+__global__ void sigma_rows_batch(const SrDesc* __restrict__ D) {
+  const SrDesc& d = D[blockIdx.y];
+  const int nb = elem_blocks(d.ns * (d.na64 / 8));
+  if ((int)blockIdx.x >= nb) return;
+  sigma_rows_body(blockIdx.x, nb, d.sigma, d.ns, d.n, d.na64, reinterpret_cast<uint16_t*>(d.sigr));
+}
+
+nk_status launch_sigma_rows_batch(const SrDesc* D, int G, int64_t max_elems, cudaStream_t st) {
+  sigma_rows_batch<<<dim3(vec_blocks(max_elems), (unsigned)G), 256, 0, st>>>(D);
+  return check_launch("sigma_rows_batch");
 }
 
 nk_status launch_bplanes_p_batch(const SrDesc* D, int G, int64_t max_elems, cudaStream_t st) {

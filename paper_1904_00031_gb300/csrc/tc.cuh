@@ -58,6 +58,10 @@ struct FwdTcArgs {
                                    // the sample tiles are then TMA-loaded, else built
 };
 nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st);
+// Hidden-tile halves (1 or 2) launch_fwd_tc uses for ns samples and mt hidden
+// tiles: 2 when twice the CTAs fill their last wave better (ln psi, and the SR
+// forward with TMA-loaded sigma' tiles).
+int fwd_tc_nseg(int64_t ns, int mt, int mode, bool sig_tma);
 
 // Adjoint contraction: part[z][j][i] = sum_{s in split z} conj(T'_sj) v_s sigma'_si
 // (FP32 partials, complex interleaved for a complex RBM), j < m + 1, i < n + 1.
@@ -82,10 +86,12 @@ bool tc_supported_shape(int n, int m);
 struct alignas(128) SrDesc {
   CUtensorMap fwd_map;    // B planes of the CG direction (xbf)
   CUtensorMap adj_map;    // sigma'^T (sigt)
+  CUtensorMap sig_map;    // sigma' rows (sigr), the forward's A operand
   const double* done;     // scal + SC_DONE: the CG has converged
   int splits;
   int nb_pa, nb_ns;       // blocks of the CG vector kernels over parameters / samples
   int cplx;               // 1: complex RBM
+  int fwd_nseg;           // hidden-tile halves of the forward (fwd_tc_nseg); 2: y zeroed first
   int n, m, n_chains, na64, mt1, mp, wmt, wna64;  // wmt, wna64: B planes of W | b
   int64_t ns, pa, corner, ns8;
   const int8_t* sigma;
@@ -105,6 +111,7 @@ struct alignas(128) SrDesc {
   char* y;
   char* v;
   char* sigt;
+  char* sigr;
   char* xbf;
   double* red;
   double* scal;
@@ -118,7 +125,8 @@ constexpr int kBatchMax = 64;
 struct FwdBatch {
   FwdTcArgs a[kBatchMax];
   const CUtensorMap* map[kBatchMax];   // in the problem's SrDesc (global memory)
-  int tiles[kBatchMax];
+  const CUtensorMap* smap[kBatchMax];  // sigma' rows map, also in the SrDesc
+  int tiles[kBatchMax];                // sample tiles (CTAs per hidden-tile half)
 };
 struct AdjBatch {
   AdjTcArgs a[kBatchMax];
@@ -138,6 +146,7 @@ nk_status launch_sigma_t_batch(const SrDesc* D, int G, int64_t max_ns8, int max_
                                cudaStream_t st);
 // B planes of the CG direction p (skipped once converged), or of W | b
 nk_status launch_bplanes_p_batch(const SrDesc* D, int G, int64_t max_elems, cudaStream_t st);
+nk_status launch_sigma_rows_batch(const SrDesc* D, int G, int64_t max_elems, cudaStream_t st);
 nk_status launch_bplanes_rbm_batch(const SrDesc* D, int G, int64_t max_elems, cudaStream_t st);
 // the derived planes of every problem's RBM (prepare.cu)
 nk_status launch_prepare_batch(const SrDesc* D, int G, int64_t max_work, int64_t max_minb,
