@@ -157,43 +157,79 @@ __device__ __forceinline__ double sum_partials(const double* red, int nb) {
 
 // ------------------------------------------------------------------ K7 statistics
 
-// One CTA.  E = sum w E_s, var = sum w |E_s - E|^2, error from chain means;
-// writes v_s = w_s (E_s - E) (the vector whose adjoint contraction is F).
+// Three passes over the samples in nb blocks (sums of per-block partials in a
+// fixed order, so the result does not depend on scheduling):
+//   mean:   per-block partials of sum w E_s                 -> red[2K + b], red[3K + b]
+//   dev:    E = sum of those; v_s = w_s (E_s - E); per-block partials of
+//           sum w |E_s - E|^2 -> red[b] and, over whole chains, of
+//           sum_c (mean_c Re E - Re E)^2 -> red[K + b]      (K = kVecBlocks)
+//   finish: info {E, var, error from chain means} and the scalars the CG reads.
+// v_s is the vector whose adjoint contraction is F.
 template <bool CPLX>
-__device__ __forceinline__ void stats_body(int bx, int gx, const double* __restrict__ eloc,
-                                                     const double* __restrict__ weights,
-                                                     int64_t ns, int n_chains, double* info,
-                                                     double* scal, void* vout) {
+__device__ __forceinline__ void stats_mean_body(int bx, int gx, const double* __restrict__ eloc,
+                                                const double* __restrict__ weights, int64_t ns,
+                                                double* red) {
   const double invn = 1.0 / (double)ns;
   double sr = 0.0, si = 0.0;
-  for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) {
-    double w = weights ? weights[s] : invn;
+  for (int64_t s = bx * (int64_t)blockDim.x + threadIdx.x; s < ns;
+       s += (int64_t)gx * blockDim.x) {
+    const double w = weights ? weights[s] : invn;
     sr += w * eloc[2 * s];
     si += w * eloc[2 * s + 1];
   }
-  const double er = block_sum(sr), ei = block_sum(si);
+  const double br = block_sum(sr);
+  const double bi = block_sum(si);
+  if (threadIdx.x == 0) {
+    red[2 * kVecBlocks + bx] = br;
+    red[3 * kVecBlocks + bx] = bi;
+  }
+}
+
+template <bool CPLX>
+__device__ __forceinline__ void stats_dev_body(int bx, int gx, const double* __restrict__ eloc,
+                                               const double* __restrict__ weights, int64_t ns,
+                                               int n_chains, double* red, void* vout, int nb) {
+  const double er = sum_partials(red + 2 * kVecBlocks, nb);
+  const double ei = sum_partials(red + 3 * kVecBlocks, nb);
+  const double invn = 1.0 / (double)ns;
   double vv = 0.0;
-  for (int64_t s = threadIdx.x; s < ns; s += blockDim.x) {
-    double w = weights ? weights[s] : invn;
-    double dr = eloc[2 * s] - er, di = eloc[2 * s + 1] - ei;
+  for (int64_t s = bx * (int64_t)blockDim.x + threadIdx.x; s < ns;
+       s += (int64_t)gx * blockDim.x) {
+    const double w = weights ? weights[s] : invn;
+    const double dr = eloc[2 * s] - er, di = eloc[2 * s + 1] - ei;
     vv += w * (dr * dr + di * di);
     if (CPLX)
       reinterpret_cast<double2*>(vout)[s] = make_double2(w * dr, w * di);
     else
       reinterpret_cast<double*>(vout)[s] = w * dr;
   }
-  const double var = block_sum(vv);
   double ce = 0.0;
   const int64_t spc = n_chains > 0 ? ns / n_chains : 0;
   if (!weights && n_chains > 1 && spc > 0) {
-    for (int c = threadIdx.x; c < n_chains; c += blockDim.x) {
+    for (int64_t c = bx * (int64_t)blockDim.x + threadIdx.x; c < n_chains;
+         c += (int64_t)gx * blockDim.x) {
       double mc = 0.0;
       for (int64_t u = 0; u < spc; ++u) mc += eloc[2 * (c * spc + u)];
       mc /= (double)spc;
       ce += (mc - er) * (mc - er);
     }
   }
-  ce = block_sum(ce);
+  const double bv = block_sum(vv);
+  const double bc = block_sum(ce);
+  if (threadIdx.x == 0) {
+    red[bx] = bv;
+    red[kVecBlocks + bx] = bc;
+  }
+}
+
+__device__ __forceinline__ void stats_finish_body(const double* __restrict__ weights, int64_t ns,
+                                                  int n_chains, const double* red, int nb,
+                                                  double* info, double* scal) {
+  const double er = sum_partials(red + 2 * kVecBlocks, nb);
+  const double ei = sum_partials(red + 3 * kVecBlocks, nb);
+  const double var = sum_partials(red, nb);
+  const double ce = sum_partials(red + kVecBlocks, nb);
+  const int64_t spc = n_chains > 0 ? ns / n_chains : 0;
   if (threadIdx.x == 0) {
     info[NK_INFO_E_RE] = er;
     info[NK_INFO_E_IM] = ei;
@@ -207,11 +243,23 @@ __device__ __forceinline__ void stats_body(int bx, int gx, const double* __restr
 }
 
 template <bool CPLX>
-__global__ void __launch_bounds__(1024) stats_kernel(const double* __restrict__ eloc,
-                                                     const double* __restrict__ weights,
-                                                     int64_t ns, int n_chains, double* info,
-                                                     double* scal, void* vout) {
-  stats_body<CPLX>(blockIdx.x, gridDim.x, eloc, weights, ns, n_chains, info, scal, vout);
+__global__ void __launch_bounds__(kVecThreads) stats_mean_kernel(const double* __restrict__ eloc,
+                                                                 const double* __restrict__ weights,
+                                                                 int64_t ns, double* red) {
+  stats_mean_body<CPLX>(blockIdx.x, gridDim.x, eloc, weights, ns, red);
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) stats_dev_kernel(const double* __restrict__ eloc,
+                                                                const double* __restrict__ weights,
+                                                                int64_t ns, int n_chains,
+                                                                double* red, void* vout, int nb) {
+  stats_dev_body<CPLX>(blockIdx.x, gridDim.x, eloc, weights, ns, n_chains, red, vout, nb);
+}
+
+__global__ void stats_finish_kernel(const double* __restrict__ weights, int64_t ns, int n_chains,
+                                    const double* red, int nb, double* info, double* scal) {
+  stats_finish_body(weights, ns, n_chains, red, nb, info, scal);
 }
 
 // ------------------------------------------------------------------ adjoint contraction
@@ -809,12 +857,27 @@ __global__ void scatter_grad_kernel(const void* __restrict__ gv, int n, int m, d
 // single-problem launch uses), so each problem's reductions keep their order
 // and a batched step computes exactly what nk_sr_step computes for it.
 
-__global__ void __launch_bounds__(1024) stats_batch(const SrDesc* __restrict__ D) {
+__global__ void __launch_bounds__(kVecThreads) stats_mean_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
+  if ((int)blockIdx.x >= d.nb_ns) return;
+  if (d.cplx) stats_mean_body<true>(blockIdx.x, d.nb_ns, d.eloc, d.weights, d.ns, d.red);
+  else stats_mean_body<false>(blockIdx.x, d.nb_ns, d.eloc, d.weights, d.ns, d.red);
+}
+
+__global__ void __launch_bounds__(kVecThreads) stats_dev_batch(const SrDesc* __restrict__ D) {
+  const SrDesc& d = D[blockIdx.y];
+  if ((int)blockIdx.x >= d.nb_ns) return;
   if (d.cplx)
-    stats_body<true>(0, 1, d.eloc, d.weights, d.ns, d.n_chains, d.info, d.scal, d.v);
+    stats_dev_body<true>(blockIdx.x, d.nb_ns, d.eloc, d.weights, d.ns, d.n_chains, d.red, d.v,
+                         d.nb_ns);
   else
-    stats_body<false>(0, 1, d.eloc, d.weights, d.ns, d.n_chains, d.info, d.scal, d.v);
+    stats_dev_body<false>(blockIdx.x, d.nb_ns, d.eloc, d.weights, d.ns, d.n_chains, d.red, d.v,
+                          d.nb_ns);
+}
+
+__global__ void stats_finish_batch(const SrDesc* __restrict__ D) {
+  const SrDesc& d = D[blockIdx.y];
+  stats_finish_body(d.weights, d.ns, d.n_chains, d.red, d.nb_ns, d.info, d.scal);
 }
 
 __global__ void flags_reset_batch(const SrDesc* __restrict__ D) {
@@ -951,7 +1014,13 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
     fa.err = err;
     fa.sig_rows = sc + L.sigr;
   }
-  stats_kernel<CPLX><<<1, 1024, 0, st>>>(eloc, weights, ns, n_chains, info, scal, sc + L.v);
+  {
+    const int nbs0 = sr_vec_blocks(ns);
+    stats_mean_kernel<CPLX><<<nbs0, kVecThreads, 0, st>>>(eloc, weights, ns, red);
+    stats_dev_kernel<CPLX><<<nbs0, kVecThreads, 0, st>>>(eloc, weights, ns, n_chains, red,
+                                                        sc + L.v, nbs0);
+    stats_finish_kernel<<<1, 32, 0, st>>>(weights, ns, n_chains, red, nbs0, info, scal);
+  }
   if (nk_status e = check_launch("nk_sr_step(stats)")) return e;
   cudaMemsetAsync(scal + SC_DONE, 0, sizeof(double), st);
   cudaMemsetAsync(scal + SC_ERR, 0, sizeof(double), st);
@@ -1221,7 +1290,9 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
     max_nbs = std::max(max_nbs, sr_vec_blocks(it.ns));
   }
   const dim3 vg(max_nbp, G), vs(max_nbs, G), one(1, G);
-  stats_batch<<<one, 1024, 0, st>>>(Dg);
+  stats_mean_batch<<<vs, kVecThreads, 0, st>>>(Dg);
+  stats_dev_batch<<<vs, kVecThreads, 0, st>>>(Dg);
+  stats_finish_batch<<<one, 32, 0, st>>>(Dg);
   flags_reset_batch<<<one, 32, 0, st>>>(Dg);
   if (nk_status e = check_launch("nk_sr_step_batch(stats)")) return e;
   if (nk_status e = launch_sigma_t_batch(Dg, G, max_ns8, max_na64, st)) return e;
