@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp32-arm", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--checkpoint-iters", type=int, default=50,
+                    help="also time the iteration after this many more SR iterations "
+                         "(structured psi, realistic acceptance); 0 skips it")
     return ap.parse_args()
 
 
@@ -87,7 +90,7 @@ def run_oracle_subprocess(workload: str, n_chains: int, spc: int, n_cg: int) -> 
 # single-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # workload at full size; a kernel that changed since its capture has no entry.
 NCU_TRAFFIC = {
-    ("j1j2_20x20_alpha4", "bf16x2", "local_energy_tiled"): 21.08e9 + 1.69e9,
+    ("j1j2_20x20_alpha4", "bf16x2", "local_energy_tiled"): 21.09e9 + 1.69e9,
 }
 
 ORACLE_SAMPLE = {"c5": (24, 2, 50), "c3": (64, 1, 50), "c2": (128, 4, 50), "c1": (16, 63, 120),
@@ -326,7 +329,14 @@ def run_gpu(args):
     n_accept = float(v.n_acc.sum().item())
     n_conn = connected_per_config(w.op, v.samples[:4096].cpu().numpy())
     fl = stage_flops(w, n_prop * nonnull_frac, n_accept, n_conn)
-    alu_peak = fp32_peak_tflops(sm_max)
+    try:
+        alu_meas = nk.nk_measure_alu_peaks()
+        alu_peak = alu_meas["fp32_fma_flops"] / 1e12
+        alu_src = "measured packed FP32 FMA rate (nk_measure_alu_peaks)"
+    except Exception as e:  # noqa: BLE001 - report the derived figure instead
+        alu_meas = {"error": str(e)[:200]}
+        alu_peak = fp32_peak_tflops(sm_max)
+        alu_src = f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived)"
     tc_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0))
     rl = {}
     for st_name, ms in stage_ms.items():
@@ -343,7 +353,32 @@ def run_gpu(args):
     roof = dict(rl[dom])
     roof.update({"kernel": kern, "traffic": NCU_TRAFFIC.get((w.name, prec_name, kern)),
                  "peak_source": (f"{pk_kind} bf16 dense TFLOP/s (sustained)" if roof["bound"] == "tensor"
-                                 else f"152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz")})
+                                 else alu_src)})
+    # the same measurement after more SR iterations: psi has structure and the
+    # acceptance is the optimisation's, not the near-uniform initial one
+    ckpt = None
+    if args.checkpoint_iters > 0:
+        for _ in range(args.checkpoint_iters):
+            v.step()
+        barrier()
+        ev_ck = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+        for k in range(args.steps):
+            if flush is not None:
+                flush.zero_()
+            ev_ck[k][0].record(stream)
+            v.step()
+            ev_ck[k][1].record(stream)
+        barrier()
+        tck = torch.tensor([sum(a.elapsed_time(b) for a, b in ev_ck)], device="cuda")
+        if world > 1:
+            dist.all_reduce(tck, op=dist.ReduceOp.MAX)
+        ck_ms = float(tck.item()) / args.steps
+        info_ck = v.info()
+        ckpt = {"sr_iterations_before": args.checkpoint_iters + 3 * args.steps + args.warmup,
+                "value": round(world * w.n_samples / (ck_ms / 1e3), 2), "unit": "samples/s",
+                "ms_per_step": round(ck_ms, 3), "acceptance": round(info_ck["acceptance"], 4),
+                "energy": info_ck["energy"]}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
@@ -362,6 +397,12 @@ def run_gpu(args):
         "nonnull_proposal_fraction": round(nonnull_frac, 4),
         "connected_per_sample": round(n_conn, 2), "moves": v.op.n_moves,
         "roofline": roof, "stage_roofline": rl,
+        "alu_peaks_measured": ({"fp32_fma_tflops": round(alu_meas["fp32_fma_flops"] / 1e12, 2),
+                                "mufu_ex2_tops": round(alu_meas["mufu_ex2_ops"] / 1e12, 3),
+                                "mufu_lg2_tops": round(alu_meas["mufu_lg2_ops"] / 1e12, 3),
+                                "mufu_sin_tops": round(alu_meas["mufu_sin_ops"] / 1e12, 3)}
+                               if "fp32_fma_flops" in alu_meas else alu_meas),
+        "after_sr_iterations": ckpt,
         "e2e": {"value": round(world * w.n_samples / (e2e_ms / 1e3), 2), "unit": "samples/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nk.NK_INFO_LEN * 8},
         "gpu_launches": v.launches_per_step() * args.steps,

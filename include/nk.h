@@ -127,6 +127,31 @@ const char* nk_last_error(void);
  * current; 0 otherwise (no error is raised). */
 int32_t nk_device_supported(void);
 
+/* Device-side status (the paper has no counterpart: failure reporting of this
+ * library).  Every wait of a kernel on an mbarrier (a bulk copy or a producer /
+ * consumer hand-off) gives up after a bounded number of polls; the kernel then
+ * finishes without hanging, marks its own outputs (NaN ln psi / E_loc / SR info,
+ * UINT64_MAX accept counts) and sets bit (1 << NK_ERR_TIMEOUT) in a device
+ * status word.  nk_query_status enqueues on `stream`: *flags (device int32,
+ * caller-owned) = OR of the status bits set since the previous query, and
+ * clears them.  Read *flags after the stream has passed the call.  Returns
+ * NK_ERR_INVALID_ARG for a NULL flags pointer, NK_ERR_CUDA on a launch failure. */
+nk_status nk_query_status(int32_t* flags, void* stream);
+
+/* Measured ALU peaks of the current GPU (the paper has no counterpart: the
+ * roofline denominators of the kernels bound by plain arithmetic).  HOST
+ * out[4] = { packed FP32 FMA FLOP/s, MUFU ex2 op/s, MUFU lg2 op/s, MUFU sin
+ * op/s }, each the best of 3 timed launches (8 CTAs of 256 threads per SM, 8
+ * independent chains per thread).  Runs on its own stream and SYNCHRONISES it
+ * (about 0.1 s).  NK_ERR_INVALID_ARG for NULL out, NK_ERR_CUDA on failure. */
+nk_status nk_measure_alu_peaks(double* out);
+
+/* Exercise the timeout path: one thread waits for an mbarrier phase that
+ * nothing completes and gives up after `polls` polls (1 .. 2^20), setting
+ * (1 << NK_ERR_TIMEOUT) in the status word read by nk_query_status.  For tests
+ * of the failure reporting; it touches no caller memory. */
+nk_status nk_debug_bounded_wait(uint32_t polls, void* stream);
+
 /* ---------------------------------------------------------------- RBM */
 
 /* Bytes of the derived-plane workspace of an (n, m, is_complex) RBM. */
@@ -271,6 +296,62 @@ nk_status nk_sr_step_noalloc(nk_rbm* rbm, const int8_t* sigma, const void* t, co
  * CUDA events) and must not be called while a stream is being captured. */
 nk_status nk_sr_tune(nk_rbm* rbm, const int8_t* sigma, const void* t, int64_t ns, int32_t prec,
                      void* scratch, size_t scratch_bytes, void* stream);
+
+/* ------------------------------------------- batches of independent instances */
+
+/* Many independent RBMs (uneven n, m, field, sample counts) in one call each
+ * for ln psi, sampling and local energies -- the multi-instance workload
+ * (independent problems advanced together; the paper runs one problem per
+ * process).  Each item holds the arguments of the single call; `stream` of an
+ * item, if not NULL, overrides the call's stream (items on different streams
+ * run concurrently, e.g. as parallel branches of a captured CUDA graph).
+ * Every item passes all argument and shape checks of the single call before
+ * anything is enqueued; on a failure the status names the first bad item (via
+ * nk_last_error) and nothing is enqueued.  Results are identical to the single
+ * calls.  Kernels are launched per item, in item order. */
+typedef struct nk_logpsi_item {
+  const nk_rbm* rbm;
+  const int8_t* sigma;  /* int8 [ns][n] */
+  int64_t ns;
+  double* logpsi_out;   /* c128 [ns] */
+  void* theta_out;      /* F32 [ns][m] or NULL */
+  void* stream;
+} nk_logpsi_item;
+nk_status nk_batch_logpsi(const nk_logpsi_item* items, int32_t n_inst, int32_t prec,
+                          void* stream);
+
+typedef struct nk_sweep_item {
+  const nk_rbm* rbm;
+  nk_chains* chains;    /* counter advanced as by nk_metropolis_sweep */
+  int32_t move;
+  int32_t n_bonds;
+  const int32_t* bond_i;
+  const int32_t* bond_k;
+  int32_t n_discard;
+  int32_t n_samples_per_chain;
+  int8_t* samples_out;
+  uint64_t* n_accept_out;
+  void* scratch;
+  size_t scratch_bytes;
+  void* stream;
+} nk_sweep_item;
+nk_status nk_batch_sweep(const nk_sweep_item* items, int32_t n_inst, void* stream);
+
+typedef struct nk_eloc_item {
+  const nk_rbm* rbm;
+  const void* op_dev;   /* nk_operator_upload output */
+  int32_t n_moves;
+  int32_t reserved;
+  const int8_t* sigma;
+  const void* theta;
+  int64_t ns;
+  double* eloc_out;
+  void* t_out;
+  void* scratch;
+  size_t scratch_bytes;
+  void* stream;
+} nk_eloc_item;
+nk_status nk_batch_local_energy(const nk_eloc_item* items, int32_t n_inst, void* stream);
 
 /* ---------------------------------------------------------------- SR batches */
 

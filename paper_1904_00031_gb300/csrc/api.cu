@@ -11,7 +11,9 @@
 #include "common.cuh"
 #include "internal.h"
 #include "opdev.h"
+#include "status.cuh"
 #include "tc.cuh"
+#include "tma.cuh"
 
 namespace nk {
 
@@ -159,9 +161,47 @@ static size_t layout_sizes(const Compiled& c, int32_t* off_ds, int32_t* off_db, 
   return off;
 }
 
+// One thread waits for a phase of a fresh mbarrier that nothing completes,
+// giving up after `polls` polls: exercises the timeout path of the bounded
+// waits (the status bit and a context that stays usable) without a hang.
+__global__ void bounded_wait_probe_kernel(uint32_t polls) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    if (!mbar_wait_bounded(&bar, 0u, polls)) dev_status_set(1u << NK_ERR_TIMEOUT);
+  }
+}
+
+NK_STATUS_COLLECTOR(collect_status_api)
+
 }  // namespace nk
 
 using namespace nk;
+
+// Every item is checked (all argument and shape checks of the single call)
+// before any is enqueued; then the items are launched in order, each on its own
+// stream if it names one.
+template <typename Item, typename Call>
+static nk_status run_batch(const char* what, const Item* items, int32_t n_inst, void* stream,
+                           Call call) {
+  if (n_inst < 0 || (n_inst > 0 && !items))
+    return fail(NK_ERR_INVALID_ARG, "%s: bad item array", what);
+  char msg[512];
+  for (int32_t k = 0; k < n_inst; ++k) {
+    if (nk_status e = call(items[k], items[k].stream ? items[k].stream : stream, true)) {
+      snprintf(msg, sizeof(msg), "%s", g_err);
+      return fail(e, "%s item %d: %s", what, k, msg);
+    }
+  }
+  for (int32_t k = 0; k < n_inst; ++k) {
+    if (nk_status e = call(items[k], items[k].stream ? items[k].stream : stream, false)) {
+      snprintf(msg, sizeof(msg), "%s", g_err);
+      return fail(e, "%s item %d: %s", what, k, msg);
+    }
+  }
+  return NK_OK;
+}
 
 extern "C" {
 
@@ -205,17 +245,25 @@ nk_status nk_rbm_prepare(const nk_rbm* rbm, void* stream) {
   return launch_prepare(rbm, (cudaStream_t)stream);
 }
 
-nk_status nk_rbm_logpsi(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int32_t prec,
-                        double* logpsi_out, void* theta_out, void* stream) {
+static nk_status logpsi_call(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int32_t prec,
+                             double* logpsi_out, void* theta_out, void* stream, bool dry) {
   if (nk_status e = check_rbm(rbm, "nk_rbm_logpsi")) return e;
   if (ns < 0) return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi: ns < 0");
+  if (prec != NK_PREC_FP32 && prec != NK_PREC_BF16X2)
+    return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi: unknown precision %d", prec);
   if (ns == 0) return NK_OK;
   if (!sigma || !logpsi_out) return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi: NULL pointer");
+  if (prec == NK_PREC_BF16X2 && !tc_supported_shape(rbm->n, rbm->m))
+    return fail(NK_ERR_UNSUPPORTED, "nk_rbm_logpsi: the tensor-core path supports n + 1 <= 448");
+  if (dry) return NK_OK;
   if (prec == NK_PREC_FP32)
     return launch_logpsi_fp32(rbm, sigma, ns, logpsi_out, theta_out, (cudaStream_t)stream);
-  if (prec == NK_PREC_BF16X2)
-    return launch_logpsi_bf16(rbm, sigma, ns, logpsi_out, theta_out, (cudaStream_t)stream);
-  return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi: unknown precision %d", prec);
+  return launch_logpsi_bf16(rbm, sigma, ns, logpsi_out, theta_out, (cudaStream_t)stream);
+}
+
+nk_status nk_rbm_logpsi(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int32_t prec,
+                        double* logpsi_out, void* theta_out, void* stream) {
+  return logpsi_call(rbm, sigma, ns, prec, logpsi_out, theta_out, stream, false);
 }
 
 size_t nk_metropolis_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int32_t move,
@@ -225,11 +273,11 @@ size_t nk_metropolis_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int
   return metropolis_scratch_bytes(n, m, is_complex ? 1 : 0, move, n_bonds);
 }
 
-nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move,
+static nk_status sweep_call(const nk_rbm* rbm, nk_chains* chains, int32_t move,
                               const int32_t* bond_i, const int32_t* bond_k, int32_t n_bonds,
                               int32_t n_discard, int32_t n_samples_per_chain,
                               int8_t* samples_out, uint64_t* n_accept_out, void* scratch,
-                              size_t scratch_bytes, void* stream) {
+                              size_t scratch_bytes, void* stream, bool dry) {
   if (nk_status e = check_rbm(rbm, "nk_metropolis_sweep")) return e;
   if (!chains || !chains->sigma)
     return fail(NK_ERR_INVALID_ARG, "nk_metropolis_sweep: NULL chains");
@@ -249,9 +297,18 @@ nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move
   if (chains->nc == 0 || n_discard + n_samples_per_chain == 0) return NK_OK;
   nk_status e = launch_metropolis(rbm, chains, move, bond_i, bond_k, n_bonds, n_discard,
                                   n_samples_per_chain, samples_out, n_accept_out, scratch,
-                                  scratch_bytes, (cudaStream_t)stream);
-  if (e == NK_OK) chains->counter += (uint64_t)(n_discard + n_samples_per_chain) * rbm->n;
+                                  scratch_bytes, (cudaStream_t)stream, dry);
+  if (e == NK_OK && !dry) chains->counter += (uint64_t)(n_discard + n_samples_per_chain) * rbm->n;
   return e;
+}
+
+nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move,
+                              const int32_t* bond_i, const int32_t* bond_k, int32_t n_bonds,
+                              int32_t n_discard, int32_t n_samples_per_chain,
+                              int8_t* samples_out, uint64_t* n_accept_out, void* scratch,
+                              size_t scratch_bytes, void* stream) {
+  return sweep_call(rbm, chains, move, bond_i, bond_k, n_bonds, n_discard, n_samples_per_chain,
+                    samples_out, n_accept_out, scratch, scratch_bytes, stream, false);
 }
 
 size_t nk_operator_bytes(const nk_operator* op) {
@@ -297,9 +354,10 @@ size_t nk_local_energy_scratch_bytes(int32_t m, int32_t is_complex, int32_t n_mo
   return local_energy_scratch_bytes(m, is_complex ? 1 : 0, n_moves);
 }
 
-nk_status nk_local_energy(const nk_rbm* rbm, const void* op_dev, int32_t n_moves,
+static nk_status eloc_call(const nk_rbm* rbm, const void* op_dev, int32_t n_moves,
                           const int8_t* sigma, const void* theta, int64_t ns, double* eloc_out,
-                          void* t_out, void* scratch, size_t scratch_bytes, void* stream) {
+                          void* t_out, void* scratch, size_t scratch_bytes, void* stream,
+                          bool dry) {
   if (nk_status e = check_rbm(rbm, "nk_local_energy")) return e;
   if (ns < 0 || n_moves < 0) return fail(NK_ERR_INVALID_ARG, "nk_local_energy: negative size");
   if (ns == 0) return NK_OK;
@@ -307,8 +365,52 @@ nk_status nk_local_energy(const nk_rbm* rbm, const void* op_dev, int32_t n_moves
     return fail(NK_ERR_INVALID_ARG, "nk_local_energy: NULL pointer");
   if (scratch && (((uintptr_t)scratch) & 255))
     return fail(NK_ERR_INVALID_ARG, "nk_local_energy: scratch not 256-byte aligned");
+  if (n_moves > 0) {
+    const size_t need = local_energy_scratch_bytes(rbm->m, rbm->is_complex ? 1 : 0, n_moves);
+    if (!scratch || scratch_bytes < need)
+      return fail(NK_ERR_SHAPE, "nk_local_energy: scratch of %zu B, need %zu B", scratch_bytes,
+                  need);
+  }
+  if (dry) return NK_OK;
   return launch_local_energy(rbm, op_dev, n_moves, sigma, theta, ns, eloc_out, t_out, scratch,
                              scratch_bytes, (cudaStream_t)stream);
+}
+
+nk_status nk_local_energy(const nk_rbm* rbm, const void* op_dev, int32_t n_moves,
+                          const int8_t* sigma, const void* theta, int64_t ns, double* eloc_out,
+                          void* t_out, void* scratch, size_t scratch_bytes, void* stream) {
+  return eloc_call(rbm, op_dev, n_moves, sigma, theta, ns, eloc_out, t_out, scratch,
+                   scratch_bytes, stream, false);
+}
+
+// ---------------------------------------------------------------- batches of instances
+
+nk_status nk_batch_logpsi(const nk_logpsi_item* items, int32_t n_inst, int32_t prec,
+                          void* stream) {
+  return run_batch("nk_batch_logpsi", items, n_inst, stream,
+                   [prec](const nk_logpsi_item& it, void* st, bool dry) {
+                     return logpsi_call(it.rbm, it.sigma, it.ns, prec, it.logpsi_out,
+                                        it.theta_out, st, dry);
+                   });
+}
+
+nk_status nk_batch_sweep(const nk_sweep_item* items, int32_t n_inst, void* stream) {
+  return run_batch("nk_batch_sweep", items, n_inst, stream,
+                   [](const nk_sweep_item& it, void* st, bool dry) {
+                     return sweep_call(it.rbm, it.chains, it.move, it.bond_i, it.bond_k,
+                                       it.n_bonds, it.n_discard, it.n_samples_per_chain,
+                                       it.samples_out, it.n_accept_out, it.scratch,
+                                       it.scratch_bytes, st, dry);
+                   });
+}
+
+nk_status nk_batch_local_energy(const nk_eloc_item* items, int32_t n_inst, void* stream) {
+  return run_batch("nk_batch_local_energy", items, n_inst, stream,
+                   [](const nk_eloc_item& it, void* st, bool dry) {
+                     return eloc_call(it.rbm, it.op_dev, it.n_moves, it.sigma, it.theta, it.ns,
+                                      it.eloc_out, it.t_out, it.scratch, it.scratch_bytes, st,
+                                      dry);
+                   });
 }
 
 nk_status nk_logderiv(const nk_rbm* rbm, const int8_t* sigma, const void* theta, int64_t ns,
@@ -398,6 +500,34 @@ nk_status nk_rbm_logpsi_backward(const nk_rbm* rbm, const int8_t* sigma, int64_t
     return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi_backward: unknown precision %d", prec);
   return run_backward(rbm, sigma, ns, g, grad_out, prec, scratch, scratch_bytes,
                       (cudaStream_t)stream);
+}
+
+nk_status nk_query_status(int32_t* flags, void* stream) {
+  if (!flags) return fail(NK_ERR_INVALID_ARG, "nk_query_status: flags is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(flags, 0, sizeof(int32_t), st) != cudaSuccess)
+    return fail(NK_ERR_CUDA, "nk_query_status: cudaMemsetAsync failed");
+  if (nk_status e = collect_status_tc(flags, st)) return e;
+  if (nk_status e = collect_status_metropolis(flags, st)) return e;
+  if (nk_status e = collect_status_local_energy(flags, st)) return e;
+  return collect_status_api(flags, st);
+}
+
+nk_status nk_measure_alu_peaks(double* out) {
+  if (!out) return fail(NK_ERR_INVALID_ARG, "nk_measure_alu_peaks: out is NULL");
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(NK_ERR_CUDA, "nk_measure_alu_peaks: cannot create a stream");
+  const nk_status e = measure_alu_peaks(out, st);
+  cudaStreamDestroy(st);
+  return e;
+}
+
+nk_status nk_debug_bounded_wait(uint32_t polls, void* stream) {
+  if (polls < 1 || polls > (1u << 20))
+    return fail(NK_ERR_INVALID_ARG, "nk_debug_bounded_wait: polls must be in [1, 2^20]");
+  bounded_wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(polls);
+  return check_launch("nk_debug_bounded_wait");
 }
 
 }  // extern "C"

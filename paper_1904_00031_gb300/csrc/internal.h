@@ -17,6 +17,16 @@ nk_status check_launch(const char* where);
 
 nk_status launch_prepare(const nk_rbm* r, cudaStream_t st);
 
+// Device status words (status.cuh): OR each translation unit's word into *out
+// (device int32) and clear it.
+nk_status collect_status_tc(int32_t* out, cudaStream_t st);
+nk_status collect_status_metropolis(int32_t* out, cudaStream_t st);
+nk_status collect_status_local_energy(int32_t* out, cudaStream_t st);
+nk_status collect_status_api(int32_t* out, cudaStream_t st);
+
+// FP32 FMA FLOP/s and MUFU ex2 / lg2 / sin op/s of the current GPU (host out[4]).
+nk_status measure_alu_peaks(double* out, cudaStream_t st);
+
 // theta = W sigma + b and ln psi; theta_out may be null.
 nk_status launch_logpsi_fp32(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,
                              void* theta_out, cudaStream_t st);
@@ -26,7 +36,7 @@ nk_status launch_logpsi_bf16(const nk_rbm* r, const int8_t* sigma, int64_t ns, d
 nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int32_t* bi,
                             const int32_t* bk, int nb, int n_discard, int n_samples,
                             int8_t* samples, uint64_t* n_acc, void* scratch, size_t scratch_bytes,
-                            cudaStream_t st);
+                            cudaStream_t st, bool dry = false);
 size_t metropolis_scratch_bytes(int n, int m, int cplx, int move, int nb);
 
 nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,

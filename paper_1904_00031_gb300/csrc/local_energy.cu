@@ -12,6 +12,7 @@
 #include "opdev.h"
 #include "ratio.cuh"
 #include "tc.cuh"
+#include "status.cuh"
 #include "umma.cuh"
 
 #include <string.h>
@@ -244,9 +245,18 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   int Pe[4][4];
   float sgn[4][4];      // real: sigma_i of the configuration for each move
   float2 ns2[4][2];     // complex: -sigma_i packed over the move pairs
+  bool bad = false;     // a bounded wait for a move-table chunk gave up
+  __shared__ volatile int s_bad;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  int it_stop = it_end; // first chunk not processed
   for (int it = it_begin; it < it_end; ++it) {
     const int b = (it - it_begin) & 1, kc = it % nchunk, mt = it / nchunk, mt0 = mt * kEBM;
     __syncthreads();  // chunk it-1 fully consumed; t tile of chunk it stored
+    if (s_bad) {      // a wait timed out: all threads stop together
+      it_stop = it;
+      break;
+    }
     if (kc == 0) {
       // new tile of moves: metadata and mel * exp(visible) per sign pattern
       if (tid < kEBM) {
@@ -314,7 +324,10 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
                       (it1 / nchunk) * kEBM * (CPLX ? 4 : 2), (it1 % nchunk) * kEBK, &mbar[b ^ 1]);
     }
     if (it + 1 < it_end) load_t(it + 1);
-    mbar_wait_bounded(&mbar[b], (uint32_t)(((it - it_begin) >> 1) & 1));
+    if (!mbar_wait_bounded(&mbar[b], (uint32_t)(((it - it_begin) >> 1) & 1))) {
+      bad = true;
+      s_bad = 1;
+    }
     const T2* mv_b = mvt + (size_t)b * kEBK * kEBM;
     const TS* t_b = tS + (size_t)b * kEBK * kETS;
     if constexpr (CPLX) {
@@ -411,11 +424,24 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
       }
     }
   }
+  __syncthreads();
+  bad = s_bad != 0;
+  if (bad) {
+    if (tid == 0) {
+      // let the chunk copies still in flight (the one waited for and the next)
+      // land before the CTA exits
+      for (int c = it_stop - 1; c <= it_stop && c < it_end; ++c)
+        if (c >= it_begin)
+          mbar_wait_bounded(&mbar[(c - it_begin) & 1], (uint32_t)(((c - it_begin) >> 1) & 1),
+                            1u << 20);
+      dev_status_set(1u << NK_ERR_TIMEOUT);
+    }
+  }
   // the 16 threads of a configuration are lanes tid ^ 1, 2, 4, 8 of one warp
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
-    er[p] = eacc[p * 256 + tid].x;
-    ei[p] = eacc[p * 256 + tid].y;
+    er[p] = bad ? __longlong_as_double(0x7ff8000000000000ll) : eacc[p * 256 + tid].x;
+    ei[p] = bad ? __longlong_as_double(0x7ff8000000000000ll) : eacc[p * 256 + tid].y;
 #pragma unroll
     for (int off = 8; off >= 1; off >>= 1) {
       er[p] += __shfl_xor_sync(0xffffffffu, er[p], off);
@@ -582,5 +608,7 @@ nk_status launch_logderiv(const nk_rbm* r, const int8_t* sigma, const void* thet
                                                             o_out);
   return check_launch("nk_logderiv");
 }
+
+NK_STATUS_COLLECTOR(collect_status_local_energy)
 
 }  // namespace nk

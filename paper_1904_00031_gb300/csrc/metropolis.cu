@@ -26,6 +26,7 @@
 #include "internal.h"
 #include "ratio.cuh"
 #include "tma.cuh"
+#include "status.cuh"
 #include "umma.cuh"
 
 namespace nk {
@@ -465,6 +466,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
       kphase ^= 1u;
     }
   }
+  if (timed_out && lane == 0) dev_status_set(1u << NK_ERR_TIMEOUT);
   if (timed_out && producer) {
     // let copies still in flight land before the CTA exits
     for (int k = 0; k < R; ++k) mbar_wait_bounded(&full[k], 0, 1u << 20);
@@ -648,7 +650,7 @@ static nk_status launch_c(const MetroArgs& A, int nu, int wpc, size_t smem, cuda
 nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int32_t* bi,
                             const int32_t* bk, int nb, int n_discard, int n_samples,
                             int8_t* samples, uint64_t* n_acc, void* scratch, size_t scratch_bytes,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool dry) {
   WsLayout L(r->n, r->m, r->is_complex);
   MetroArgs A;
   A.n = r->n;
@@ -684,6 +686,23 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
   if (need && (!scratch || scratch_bytes < need))
     return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: scratch of %zu B, need %zu B", scratch_bytes,
                 need);
+  // ring depth: as many slots as fit next to the pair partials, barriers and
+  // the per-warp sigma copies (theta lives in tensor memory)
+  const size_t slot = cd_row + (size_t)L.mp * f;
+  const size_t rest = (size_t)round_up(2 * A.G * wpc, 2) * 4 + 2 * kMaxRing * 8 + 16 +
+                      (size_t)A.G * wpc * round_up(r->n, 16);
+  const size_t cap = 227 * 1024;
+  const int ring = rest + 2 * slot > cap ? 0 : (int)std::min<size_t>(kMaxRing, (cap - rest) / slot);
+  if (ring < 2)
+    return fail(NK_ERR_SHAPE,
+                "nk_metropolis_sweep: group_size %d with padded m %d leaves room for fewer "
+                "than two table slots in 227 KB of shared memory",
+                A.G, L.mp);
+  A.ring = ring;
+  const size_t smem = (size_t)ring * slot + rest;
+  if ((int64_t)(n_discard + n_samples) * r->n > 0x7fffffff)
+    return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: too many proposals in one call");
+  if (dry) return NK_OK;  // every check passed; nothing is enqueued
   char* sc = (char*)scratch;
   const int rows = move == NK_MOVE_FLIP ? r->n : nb;
   const int64_t qbytes = round_up((int64_t)rows * (int64_t)cd_row, 256);
@@ -716,22 +735,6 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
           (float4*)sc, (float2*)(sc + qbytes));
     if (nk_status e = check_launch("nk_metropolis_sweep(tables)")) return e;
   }
-  // ring depth: as many slots as fit next to the pair partials, barriers and
-  // the per-warp sigma copies (theta lives in tensor memory)
-  const size_t slot = cd_row + (size_t)L.mp * f;
-  const size_t rest = (size_t)round_up(2 * A.G * wpc, 2) * 4 + 2 * kMaxRing * 8 + 16 +
-                      (size_t)A.G * wpc * round_up(r->n, 16);
-  const size_t cap = 227 * 1024;
-  const int ring = rest + 2 * slot > cap ? 0 : (int)std::min<size_t>(kMaxRing, (cap - rest) / slot);
-  if (ring < 2)
-    return fail(NK_ERR_SHAPE,
-                "nk_metropolis_sweep: group_size %d with padded m %d leaves room for fewer "
-                "than two table slots in 227 KB of shared memory",
-                A.G, L.mp);
-  A.ring = ring;
-  const size_t smem = (size_t)ring * slot + rest;
-  if ((int64_t)(n_discard + n_samples) * r->n > 0x7fffffff)
-    return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: too many proposals in one call");
   nk_status e = cplx ? launch_c<true>(A, nu, wpc, smem, st) : launch_c<false>(A, nu, wpc, smem, st);
   if (e == NK_OK && ch->counter_dev) {
     advance_counter_kernel<<<1, 1, 0, st>>>(ch->counter_dev,
@@ -740,5 +743,7 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
   }
   return e;
 }
+
+NK_STATUS_COLLECTOR(collect_status_metropolis)
 
 }  // namespace nk

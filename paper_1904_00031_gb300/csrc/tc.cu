@@ -27,6 +27,7 @@
 #include <type_traits>
 
 #include "tc.cuh"
+#include "status.cuh"
 #include "umma.cuh"
 
 namespace nk {
@@ -275,12 +276,8 @@ __device__ __forceinline__ uint32_t sig_bits(const int8_t* sigma, int64_t s, int
 // registers while its MMAs run (else each 16-unit chunk is loaded just before
 // use, which needs far fewer registers); SIG_TMA: the sigma' sample tile is
 // TMA-loaded from the BF16 rows of launch_sigma_rows (map `sgp`), else built
-// from the int8 samples by the CTA; ATM: the sigma' tile is held in tensor
-// memory instead (the epilogue warps copy their rows of launch_sigma_rows' BF16
-// buffer there; the MMAs read A from TMEM), which leaves shared memory to the
-// B stages.
-template <bool CPLX, int STAGES, bool PREFETCH, bool SIG_TMA = false, bool ATM = false,
-          int CPS = 1>
+// from the int8 samples by the CTA.
+template <bool CPLX, int STAGES, bool PREFETCH, bool SIG_TMA = false>
 __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcArgs& A, int bx,
                                             int seg, const CUtensorMap* sgp = nullptr) {
   if (A.skip && *A.skip != 0.0) return;
@@ -288,10 +285,8 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
   unsigned char* sm = align1024(smraw);
   const int KC = A.na64 / 64;
   unsigned char* sA = sm;
-  unsigned char* sB = ATM ? sm : sm + (size_t)KC * 16384;
-  constexpr uint32_t kTmemCols = ATM ? 512 : 256;
-  constexpr uint32_t kSigCol = 256;  // ATM: first TMEM column of the sigma' tile
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * CPS * kStageB);
+  unsigned char* sB = sm + (size_t)KC * 16384;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * kStageB);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
@@ -309,12 +304,12 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
       mbar_init(&tfull[k], 1);
       mbar_init(&tempty[k], 4);
     }
-    mbar_init(afull, ATM ? 4 : 1);
+    mbar_init(afull, 1);
     mbar_fence_init();
   }
-  if (w == 1) tmem_alloc(slot, kTmemCols);
+  if (w == 1) tmem_alloc(slot, 256);
   // resident sigma' tile: 128 rows x KC * 64 columns, 16-B chunks of 8 BF16
-  for (int x = tid; x < (SIG_TMA || ATM ? 0 : 128 * KC * 8); x += blockDim.x) {
+  for (int x = tid; x < (SIG_TMA ? 0 : 128 * KC * 8); x += blockDim.x) {
     const int r = x / (KC * 8), rem = x % (KC * 8), kc = rem >> 3, c = rem & 7;
     const int64_t s = s0 + r;
     const int i0 = kc * 64 + c * 8;
@@ -338,71 +333,56 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
 
   if (w == 0) {
     if (lane == 0) {
-      if (SIG_TMA && !ATM && total_it > 0) {
+      if (SIG_TMA && total_it > 0) {
         mbar_arrive_expect_tx(afull, (uint32_t)KC * 16384u);
         for (int kc = 0; kc < KC; ++kc)
           tma_load_2d(sA + (size_t)kc * 16384, sgp, kc * 64, (int)s0, afull);
       }
-      // stage g holds chunks g * CPS .. + CPS - 1 of the flat (tile, K chunk) sequence
       for (int it = 0; it < total_it; ++it) {
-        const int g = it / CPS, st = g % STAGES, u = g / STAGES, c = it % CPS;
-        const int jt = jt_begin + it / KC, kc = it % KC;
-        if (c == 0) {
-          if (u > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((u - 1) & 1))) {
-            bad = true;
-            break;
-          }
-          const int nck = min(CPS, total_it - it);
-          mbar_arrive_expect_tx(&full[st], (uint32_t)nck * kStageB);
+        const int st = it % STAGES, u = it / STAGES, jt = jt_begin + it / KC,
+                  kc = it % KC;
+        if (u > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((u - 1) & 1))) {
+          bad = true;
+          break;
         }
-        unsigned char* dst = sB + ((size_t)st * CPS + c) * kStageB;
-        tma_load_2d(dst, tbp, kc * 64, jt * 128, &full[st]);
-        tma_load_2d(dst + 16384, tbp, kc * 64, (A.mt + jt) * 128, &full[st]);
+        mbar_arrive_expect_tx(&full[st], kStageB);
+        tma_load_2d(sB + (size_t)st * kStageB, tbp, kc * 64, jt * 128, &full[st]);
+        tma_load_2d(sB + (size_t)st * kStageB + 16384, tbp, kc * 64, (A.mt + jt) * 128,
+                    &full[st]);
       }
     }
   } else if (w == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(128, 128);
-      // (each wait on the issuing thread idles the tensor pipe for about 170
-      // cycles; waiting for the next stage before this one is fully queued and
-      // committed measured slower, as the ring then refills later)
-      if ((SIG_TMA || ATM) && total_it > 0 && !mbar_wait_bounded(afull, 0u)) bad = true;
-      tc_fence_after();
-      for (int it = 0; it < total_it && !bad; ++it) {
-        const int g = it / CPS, st = g % STAGES, u = g / STAGES, c = it % CPS;
-        const int t = it / KC, kc = it % KC, acc = t & 1;
-        if (kc == 0 && t >= 2) {
-          if (!mbar_wait_bounded(&tempty[acc], (uint32_t)(((t >> 1) - 1) & 1))) {
-            bad = true;
-            break;
-          }
-          tc_fence_after();
+      int it = 0;
+      if (SIG_TMA && total_it > 0 && !mbar_wait_bounded(afull, 0u)) bad = true;
+      for (int jt = jt_begin; jt < jt_end && !bad; ++jt) {
+        const int acc = (jt - jt_begin) & 1, ua = (jt - jt_begin) >> 1;
+        if (ua > 0 && !mbar_wait_bounded(&tempty[acc], (uint32_t)((ua - 1) & 1))) {
+          bad = true;
+          break;
         }
-        if (c == 0) {
+        tc_fence_after();
+        const uint32_t d = taddr + (uint32_t)(acc * 128);
+        for (int kc = 0; kc < KC; ++kc, ++it) {
+          const int st = it % STAGES, u = it / STAGES;
           if (!mbar_wait_bounded(&full[st], (uint32_t)(u & 1))) {
             bad = true;
             break;
           }
           tc_fence_after();
-        }
-        const uint32_t d = taddr + (uint32_t)(acc * 128);
-        unsigned char* sb = sB + ((size_t)st * CPS + c) * kStageB;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t bh = sdesc_sw128(smem_addr(sb + kk * 32));
-          const uint64_t bl = sdesc_sw128(smem_addr(sb + 16384 + kk * 32));
-          if constexpr (ATM) {
-            const uint32_t at = taddr + kSigCol + (uint32_t)(kc * 32 + kk * 8);
-            umma_bf16_ts(d, at, bh, idesc, (kc | kk) != 0);
-            umma_bf16_ts(d, at, bl, idesc, 1u);
-          } else {
+          for (int kk = 0; kk < 4; ++kk) {
             const uint64_t ad = sdesc_sw128(smem_addr(sA + (size_t)kc * 16384 + kk * 32));
+            const uint64_t bh = sdesc_sw128(smem_addr(sB + (size_t)st * kStageB + kk * 32));
+            const uint64_t bl =
+                sdesc_sw128(smem_addr(sB + (size_t)st * kStageB + 16384 + kk * 32));
             umma_bf16(d, ad, bh, idesc, (kc | kk) != 0);
             umma_bf16(d, ad, bl, idesc, 1u);
           }
+          umma_commit(&empty[st]);
         }
-        if (kc == KC - 1) umma_commit(&tfull[acc]);
-        if (c == CPS - 1 || it == total_it - 1) umma_commit(&empty[st]);
+        if (!bad) umma_commit(&tfull[acc]);
       }
     }
   } else {
@@ -490,27 +470,6 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
         }
       }
     };
-    if constexpr (ATM) {
-      // this thread's sigma' row into its TMEM lane, 16 columns (32 BF16) at a time
-      const uint16_t* srow = reinterpret_cast<const uint16_t*>(A.sig_rows) + s * A.na64;
-      for (int g = 0; g < KC * 2; ++g) {
-        float x[16];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const uint4 u =
-              live ? reinterpret_cast<const uint4*>(srow + g * 32)[e] : make_uint4(0, 0, 0, 0);
-          x[4 * e] = __uint_as_float(u.x);
-          x[4 * e + 1] = __uint_as_float(u.y);
-          x[4 * e + 2] = __uint_as_float(u.z);
-          x[4 * e + 3] = __uint_as_float(u.w);
-        }
-        tmem_st_cols<16>(taddr + lane_base + kSigCol + (uint32_t)(g * 16), x);
-      }
-      tmem_st_wait();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(afull);
-    }
     if (PREFETCH && A.mode == 0 && jt_end > jt_begin) load_t(jt_begin);
     double sr = 0.0, si = 0.0;
     for (int jt = jt_begin; jt < jt_end; ++jt) {
@@ -620,35 +579,27 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
       }
     }
   }
-  if (bad && A.err) atomicOr(A.err, 1);
+  if (bad) {
+    if (A.err) atomicOr(A.err, 1);
+    dev_status_set(1u << NK_ERR_TIMEOUT);
+  }
   tc_fence_before();
   __syncthreads();
   if (w == 1) {
     tc_fence_after();
-    tmem_dealloc(taddr, kTmemCols);
+    tmem_dealloc(taddr, 256);
   }
 }
 
-// B ring of the forward with sigma' in tensor memory (shared memory holds only
-// the B ring).  Six one-chunk stages measured faster than three two-chunk ones
-// (98 against 116 us on the profiling case).
-constexpr int kFwdStagesAtm = 6;
-constexpr int kFwdCpsAtm = 1;
-
-// SIG: the SR forward (sigma' rows in global memory, tile held in TMEM);
-// else ln psi (tile built in shared memory by the CTA)
-template <bool CPLX, bool SIG>
+template <bool CPLX, bool SIG_TMA>
 __global__ void __launch_bounds__(kFwdThreads, 1)
-    fwd_tc_kernel(const __grid_constant__ CUtensorMap tb, FwdTcArgs A) {
-  if constexpr (SIG)
-    fwd_tc_body<CPLX, kFwdStagesAtm, true, false, true, kFwdCpsAtm>(&tb, A, blockIdx.x,
-                                                                     blockIdx.y);
-  else
-    fwd_tc_body<CPLX, kFwdStages, true>(&tb, A, blockIdx.x, blockIdx.y);
+    fwd_tc_kernel(const __grid_constant__ CUtensorMap tb, const __grid_constant__ CUtensorMap sg,
+                  FwdTcArgs A) {
+  fwd_tc_body<CPLX, kFwdStages, true, SIG_TMA>(&tb, A, blockIdx.x, blockIdx.y, &sg);
 }
 
-static size_t fwd_smem_bytes(int na64, int stages = kFwdStages, bool atm = false) {
-  return 1024 + (atm ? 0 : (size_t)(na64 / 64) * 16384) + (size_t)stages * kStageB + 128;
+static size_t fwd_smem_bytes(int na64, int stages = kFwdStages) {
+  return 1024 + (size_t)(na64 / 64) * 16384 + (size_t)stages * kStageB + 128;
 }
 
 // One CTA per SM: when the last wave would be far from full, split the hidden
@@ -664,11 +615,15 @@ int fwd_tc_nseg(int64_t ns, int mt, int mode, bool sig_tma) {
 nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st) {
   if (!tc_supported_shape(A.n, A.m))
     return fail(NK_ERR_UNSUPPORTED, "tensor-core path supports n + 1 <= 448 (n = %d)", A.n);
-  CUtensorMap map;
+  CUtensorMap map, smap;
   if (!tc_make_map(&map, planes, 2LL * A.mt * 128, A.na64, A.na64, 128)) return NK_ERR_CUDA;
   const bool sig_tma = A.mode == 0 && A.sig_rows != nullptr;
-  const size_t smem = sig_tma ? fwd_smem_bytes(A.na64, kFwdStagesAtm * kFwdCpsAtm, true)
-                              : fwd_smem_bytes(A.na64);
+  if (sig_tma) {
+    if (!tc_make_map(&smap, A.sig_rows, A.ns, A.na64, A.na64, 128)) return NK_ERR_CUDA;
+  } else {
+    smap = map;  // unused
+  }
+  const size_t smem = fwd_smem_bytes(A.na64);
   const int64_t blocks = (A.ns + 127) / 128;
   FwdTcArgs B = A;
   B.nseg = fwd_tc_nseg(A.ns, A.mt, A.mode, sig_tma);
@@ -683,7 +638,7 @@ nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st)
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return fail(NK_ERR_CUDA, "fwd_tc: shared memory attribute");
-    kern<<<grid, kFwdThreads, smem, st>>>(map, B);
+    kern<<<grid, kFwdThreads, smem, st>>>(map, smap, B);
     return check_launch("fwd_tc");
   };
   if (A.cplx) return sig_tma ? go(fwd_tc_kernel<true, true>) : go(fwd_tc_kernel<true, false>);
@@ -748,21 +703,16 @@ __device__ __forceinline__ void adj_tc_body(const CUtensorMap* tsp, const AdjTcA
   } else if (w == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(128, NH);
-      // the next stage's wait is made after three quarters of this stage's MMAs
-      // are queued (a wait on the issuing thread would otherwise idle the pipe)
-      if (nit > 0) {
-        if (!mbar_wait_bounded(&full[0], 0u)) bad = true;
-        tc_fence_after();
-      }
-      for (int it = 0; it < nit && !bad; ++it) {
+      for (int it = 0; it < nit; ++it) {
         const int st = it & 1;
+        if (!mbar_wait_bounded(&full[st], (uint32_t)((it >> 1) & 1))) {
+          bad = true;
+          break;
+        }
+        tc_fence_after();
         unsigned char* S = sm + (size_t)st * stage_bytes;
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          if (kk == 3 && it + 1 < nit) {
-            if (!mbar_wait_bounded(&full[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1))) bad = true;
-            tc_fence_after();
-          }
           const uint64_t ah = sdesc_sw128(smem_addr(S + kk * 32));
           const uint64_t al = sdesc_sw128(smem_addr(S + 16384 + kk * 32));
           const uint64_t b0 = sdesc_sw128(smem_addr(S + 32768 + kk * 32));
@@ -838,45 +788,6 @@ __device__ __forceinline__ void adj_tc_body(const CUtensorMap* tsp, const AdjTcA
         vq0 = smp < se ? (float)reinterpret_cast<const double*>(A.v)[smp] : 0.f;
       }
     };
-    // Z of a stage as packed BF16 pairs: rows jb + u2 (and 64 + row for Im), the
-    // thread's 8 samples.  (Building it before the wait for the buffer, with the
-    // next stage's T loads issued earlier, measured slower: 179 against 172 us.)
-    uint32_t zh[JPT][4], zl[JPT][4], zhi[CPLX ? JPT : 1][4], zli[CPLX ? JPT : 1][4];
-    auto build_z = [&]() {
-#pragma unroll
-      for (int u2 = 0; u2 < JPT; ++u2) {
-#pragma unroll
-        for (int e2 = 0; e2 < 4; ++e2) {
-          float zr[2], zi[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int e = 2 * e2 + h;
-            if constexpr (CPLX) {
-              const float vr = __shfl_sync(0xffffffffu, vq0, e);
-              const float vi = __shfl_sync(0xffffffffu, vq1, e);
-              const float2 t = tq[e][u2];
-              zr[h] = t.x * vr + t.y * vi;  // conj(t) v
-              zi[h] = t.x * vi - t.y * vr;
-            } else {
-              zr[h] = tq[e][u2] * __shfl_sync(0xffffffffu, vq0, e);
-              zi[h] = 0.f;
-            }
-          }
-          uint32_t a0, b0, a1, b1;
-          split_bf16(zr[0], a0, b0);
-          split_bf16(zr[1], a1, b1);
-          zh[u2][e2] = a0 | (a1 << 16);
-          zl[u2][e2] = b0 | (b1 << 16);
-          if constexpr (CPLX) {
-            split_bf16(zi[0], a0, b0);
-            split_bf16(zi[1], a1, b1);
-            zhi[u2][e2] = a0 | (a1 << 16);
-            zli[u2][e2] = b0 | (b1 << 16);
-          }
-        }
-      }
-    };
-    static_assert(SPT == 8, "one 16-byte chunk of 8 samples per thread and stage");
     if (nit > 0) load_stage(0);
     for (int it = 0; it < nit && !bad; ++it) {
       const int st = it & 1, u = it >> 1;
@@ -884,22 +795,52 @@ __device__ __forceinline__ void adj_tc_body(const CUtensorMap* tsp, const AdjTcA
         bad = true;
         break;
       }
-      build_z();
       unsigned char* Ahi = sm + (size_t)st * stage_bytes;
       unsigned char* Alo = Ahi + 16384;
-      const int kl = qs * SPT;
 #pragma unroll
-      for (int u2 = 0; u2 < JPT; ++u2) {
-        const int row = jb + u2;
-        *reinterpret_cast<uint4*>(Ahi + sw128_offset(row, kl)) =
-            make_uint4(zh[u2][0], zh[u2][1], zh[u2][2], zh[u2][3]);
-        *reinterpret_cast<uint4*>(Alo + sw128_offset(row, kl)) =
-            make_uint4(zl[u2][0], zl[u2][1], zl[u2][2], zl[u2][3]);
-        if constexpr (CPLX) {
-          *reinterpret_cast<uint4*>(Ahi + sw128_offset(64 + row, kl)) =
-              make_uint4(zhi[u2][0], zhi[u2][1], zhi[u2][2], zhi[u2][3]);
-          *reinterpret_cast<uint4*>(Alo + sw128_offset(64 + row, kl)) =
-              make_uint4(zli[u2][0], zli[u2][1], zli[u2][2], zli[u2][3]);
+      for (int cc = 0; cc < SPT / 8; ++cc) {
+        const int kl = qs * SPT + cc * 8;
+#pragma unroll
+        for (int u2 = 0; u2 < JPT; ++u2) {
+          uint32_t hr[4], lr[4], hi_[4], li[4];
+#pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) {
+            float zr[2], zi[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int e = cc * 8 + 2 * e2 + h;
+              if constexpr (CPLX) {
+                const float vr = __shfl_sync(0xffffffffu, vq0, e);
+                const float vi = __shfl_sync(0xffffffffu, vq1, e);
+                const float2 t = tq[e][u2];
+                zr[h] = t.x * vr + t.y * vi;  // conj(t) v
+                zi[h] = t.x * vi - t.y * vr;
+              } else {
+                zr[h] = tq[e][u2] * __shfl_sync(0xffffffffu, vq0, e);
+                zi[h] = 0.f;
+              }
+            }
+            uint32_t a0, b0, a1, b1;
+            split_bf16(zr[0], a0, b0);
+            split_bf16(zr[1], a1, b1);
+            hr[e2] = a0 | (a1 << 16);
+            lr[e2] = b0 | (b1 << 16);
+            if constexpr (CPLX) {
+              split_bf16(zi[0], a0, b0);
+              split_bf16(zi[1], a1, b1);
+              hi_[e2] = a0 | (a1 << 16);
+              li[e2] = b0 | (b1 << 16);
+            }
+          }
+          const int row = jb + u2;
+          *reinterpret_cast<uint4*>(Ahi + sw128_offset(row, kl)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+          *reinterpret_cast<uint4*>(Alo + sw128_offset(row, kl)) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+          if constexpr (CPLX) {
+            *reinterpret_cast<uint4*>(Ahi + sw128_offset(64 + row, kl)) =
+                make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
+            *reinterpret_cast<uint4*>(Alo + sw128_offset(64 + row, kl)) =
+                make_uint4(li[0], li[1], li[2], li[3]);
+          }
         }
       }
       fence_async_smem();
@@ -933,7 +874,10 @@ __device__ __forceinline__ void adj_tc_body(const CUtensorMap* tsp, const AdjTcA
       }
     }
   }
-  if (bad && A.err) atomicOr(A.err, 1);
+  if (bad) {
+    if (A.err) atomicOr(A.err, 1);
+    dev_status_set(1u << NK_ERR_TIMEOUT);
+  }
   tc_fence_before();
   __syncthreads();
   if (w == 1) {
@@ -1127,5 +1071,7 @@ nk_status launch_bplanes_rbm_batch(const SrDesc* D, int G, int64_t max_elems, cu
   bplanes_rbm_batch<<<dim3(vec_blocks(max_elems), (unsigned)G), 256, 0, st>>>(D);
   return check_launch("bplanes_rbm_batch");
 }
+
+NK_STATUS_COLLECTOR(collect_status_tc)
 
 }  // namespace nk

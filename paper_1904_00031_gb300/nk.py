@@ -18,6 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnk.so")
 
 NK_OK = 0
+NK_ERR_INVALID_ARG = 1
+NK_ERR_TIMEOUT = 6
 NK_PREC_FP32 = 0
 NK_PREC_BF16X2 = 1
 NK_MOVE_FLIP = 0
@@ -35,6 +37,8 @@ EXPORTS = (
     "nk_backward_scratch_bytes", "nk_rbm_logpsi_backward", "nk_sr_step_noalloc",
     "nk_metropolis_scratch_bytes", "nk_operator_moves", "nk_local_energy_scratch_bytes",
     "nk_sr_tune", "nk_sr_batch_desc_bytes", "nk_sr_batch_describe", "nk_sr_step_batch",
+    "nk_query_status", "nk_debug_bounded_wait", "nk_measure_alu_peaks",
+    "nk_batch_logpsi", "nk_batch_sweep", "nk_batch_local_energy",
 )
 NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
@@ -59,6 +63,26 @@ class _SrBatchItem(C.Structure):
                 ("eloc", C.c_void_p), ("weights", C.c_void_p), ("ns", C.c_int64),
                 ("n_chains", C.c_int32), ("reserved", C.c_int32), ("scratch", C.c_void_p),
                 ("scratch_bytes", C.c_size_t), ("info_out", C.c_void_p)]
+
+
+class _LogpsiItem(C.Structure):
+    _fields_ = [("rbm", C.c_void_p), ("sigma", C.c_void_p), ("ns", C.c_int64),
+                ("logpsi_out", C.c_void_p), ("theta_out", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class _SweepItem(C.Structure):
+    _fields_ = [("rbm", C.c_void_p), ("chains", C.c_void_p), ("move", C.c_int32),
+                ("n_bonds", C.c_int32), ("bond_i", C.c_void_p), ("bond_k", C.c_void_p),
+                ("n_discard", C.c_int32), ("n_samples_per_chain", C.c_int32),
+                ("samples_out", C.c_void_p), ("n_accept_out", C.c_void_p),
+                ("scratch", C.c_void_p), ("scratch_bytes", C.c_size_t), ("stream", C.c_void_p)]
+
+
+class _ElocItem(C.Structure):
+    _fields_ = [("rbm", C.c_void_p), ("op_dev", C.c_void_p), ("n_moves", C.c_int32),
+                ("reserved", C.c_int32), ("sigma", C.c_void_p), ("theta", C.c_void_p),
+                ("ns", C.c_int64), ("eloc_out", C.c_void_p), ("t_out", C.c_void_p),
+                ("scratch", C.c_void_p), ("scratch_bytes", C.c_size_t), ("stream", C.c_void_p)]
 
 
 class _Operator(C.Structure):
@@ -103,6 +127,12 @@ def load_library(path: str = LIB_PATH):
         "nk_sr_batch_desc_bytes": (SZ, [I32]),
         "nk_sr_batch_describe": (I32, [P, I32, I32, P, SZ]),
         "nk_sr_step_batch": (I32, [P, I32, P, D, D, I32, D, I32, P]),
+        "nk_query_status": (I32, [P, P]),
+        "nk_debug_bounded_wait": (I32, [C.c_uint32, P]),
+        "nk_measure_alu_peaks": (I32, [P]),
+        "nk_batch_logpsi": (I32, [P, I32, I32, P]),
+        "nk_batch_sweep": (I32, [P, I32, P]),
+        "nk_batch_local_energy": (I32, [P, I32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -185,6 +215,28 @@ class Rbm:
 
     def f32_dtype(self):
         return torch.complex64 if self.is_complex else torch.float32
+
+
+def nk_query_status(flags=None, stream=None):
+    """Enqueue the device status query; returns the int32 device tensor that
+    receives the OR of the status bits (read it after the stream passes)."""
+    if flags is None:
+        flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(load_library().nk_query_status(_ptr(flags), _stream(stream)), "nk_query_status")
+    return flags
+
+
+def nk_measure_alu_peaks() -> dict:
+    """FP32 FMA FLOP/s and MUFU ex2 / lg2 / sin op/s measured on the current GPU."""
+    out = (C.c_double * 4)()
+    _check(load_library().nk_measure_alu_peaks(C.cast(out, C.c_void_p)), "nk_measure_alu_peaks")
+    return {"fp32_fma_flops": out[0], "mufu_ex2_ops": out[1], "mufu_lg2_ops": out[2],
+            "mufu_sin_ops": out[3]}
+
+
+def nk_debug_bounded_wait(polls: int, stream=None):
+    _check(load_library().nk_debug_bounded_wait(int(polls), _stream(stream)),
+           "nk_debug_bounded_wait")
 
 
 def nk_rbm_prepare(rbm: Rbm, stream=None):
@@ -441,3 +493,52 @@ class SrBatch:
             C.cast(self._items, C.c_void_p), self.n, _ptr(self.desc), float(diag_shift),
             float(lr), int(n_cg), float(cg_rtol), self.prec, _stream(stream)),
             "nk_sr_step_batch")
+
+
+# ---------------------------------------------------------------------- batches
+
+def _item_stream(st):
+    return None if st is None else C.c_void_p(st.cuda_stream).value
+
+
+def nk_batch_logpsi(jobs, prec=NK_PREC_FP32, stream=None):
+    """jobs: list of dicts {rbm, sigma, logpsi_out, theta_out?, stream?}; one call."""
+    items = (_LogpsiItem * max(1, len(jobs)))()
+    for k, j in enumerate(jobs):
+        _require_gpu(j["sigma"], j["logpsi_out"], j.get("theta_out"))
+        items[k] = _LogpsiItem(C.addressof(j["rbm"]._s), _ptr(j["sigma"]), int(j["sigma"].shape[0]),
+                               _ptr(j["logpsi_out"]), _ptr(j.get("theta_out")),
+                               _item_stream(j.get("stream")))
+    _check(load_library().nk_batch_logpsi(C.cast(items, C.c_void_p), len(jobs), prec,
+                                          _stream(stream)), "nk_batch_logpsi")
+
+
+def nk_batch_sweep(jobs, stream=None):
+    """jobs: list of dicts {rbm, chains, move, bond_i?, bond_k?, n_discard,
+    n_samples_per_chain, samples_out, n_accept_out?, scratch?, stream?}."""
+    items = (_SweepItem * max(1, len(jobs)))()
+    for k, j in enumerate(jobs):
+        rbm, ch = j["rbm"], j["chains"]
+        bi, bk = j.get("bond_i"), j.get("bond_k")
+        _require_gpu(bi, bk, j["samples_out"], j.get("n_accept_out"), j.get("scratch"))
+        sc = j.get("scratch")
+        items[k] = _SweepItem(C.addressof(rbm._s), C.addressof(ch._s),
+                              j["move"], 0 if bi is None else int(bi.shape[0]), _ptr(bi),
+                              _ptr(bk), j["n_discard"], j["n_samples_per_chain"],
+                              _ptr(j["samples_out"]), _ptr(j.get("n_accept_out")), _ptr(sc),
+                              0 if sc is None else sc.numel(), _item_stream(j.get("stream")))
+    _check(load_library().nk_batch_sweep(C.cast(items, C.c_void_p), len(jobs), _stream(stream)),
+           "nk_batch_sweep")
+
+
+def nk_batch_local_energy(jobs, stream=None):
+    """jobs: list of dicts {rbm, op, sigma, theta, eloc_out, t_out?, scratch, stream?}."""
+    items = (_ElocItem * max(1, len(jobs)))()
+    for k, j in enumerate(jobs):
+        _require_gpu(j["sigma"], j["theta"], j["eloc_out"], j.get("t_out"), j["scratch"])
+        items[k] = _ElocItem(C.addressof(j["rbm"]._s), _ptr(j["op"].dev), j["op"].n_moves, 0,
+                             _ptr(j["sigma"]), _ptr(j["theta"]), int(j["sigma"].shape[0]),
+                             _ptr(j["eloc_out"]), _ptr(j.get("t_out")), _ptr(j["scratch"]),
+                             j["scratch"].numel(), _item_stream(j.get("stream")))
+    _check(load_library().nk_batch_local_energy(C.cast(items, C.c_void_p), len(jobs),
+                                                _stream(stream)), "nk_batch_local_energy")

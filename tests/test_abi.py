@@ -72,6 +72,13 @@ def test_sr_batch_host_checks(lib):
                                 None) == 1
 
 
+def test_status_query_host_checks(lib):
+    # rejected on the host, before any device work
+    assert lib.nk_query_status(None, None) == 1
+    assert lib.nk_debug_bounded_wait(0, None) == 1
+    assert lib.nk_debug_bounded_wait((1 << 20) + 1, None) == 1
+
+
 def test_host_argument_validation(lib):
     from paper_1904_00031_gb300 import nk
     assert lib.nk_rbm_logpsi(None, None, 4, 0, None, None, None) == 1

@@ -97,3 +97,71 @@ def test_batched_sr_graph_replays(mods):
     e1 = np.array([v.info()["energy"] for v in b.items])
     assert np.all(np.isfinite(e1))
     assert np.mean(e1 / np.abs(e0)) < np.mean(e0 / np.abs(e0))
+
+
+def _batch_jobs(nk, vs, streams=None):
+    sweep, amp, eloc = [], [], []
+    for k, v in enumerate(vs):
+        st = None if streams is None else streams[k]
+        sweep.append(dict(rbm=v.rbm, chains=v.chains, move=v.move, bond_i=v.bond_i,
+                          bond_k=v.bond_k, n_discard=v.w.n_discard,
+                          n_samples_per_chain=v.w.samples_per_chain, samples_out=v.samples,
+                          n_accept_out=v.n_acc, scratch=v.metro_scratch, stream=st))
+        amp.append(dict(rbm=v.rbm, sigma=v.samples, logpsi_out=v.logpsi, theta_out=v.theta,
+                        stream=st))
+        eloc.append(dict(rbm=v.rbm, op=v.op, sigma=v.samples, theta=v.theta, eloc_out=v.eloc,
+                         t_out=v.t, scratch=v.eloc_scratch, stream=st))
+    return sweep, amp, eloc
+
+
+@pytest.mark.parametrize("prec_name", ["fp32", "bf16x2"])
+@pytest.mark.parametrize("own_streams", [False, True])
+def test_batch_entry_points_equal_single_calls(mods, prec_name, own_streams):
+    """nk_batch_sweep / nk_batch_logpsi / nk_batch_local_energy over uneven
+    instances give bit for bit the results of the single calls (chains,
+    accept counts, ln psi, theta, E_loc, tanh theta), also with one stream per
+    item."""
+    nk, _ = mods
+    from paper_1904_00031_gb300.vmc import VmcSr
+    prec = nk.NK_PREC_FP32 if prec_name == "fp32" else nk.NK_PREC_BF16X2
+    insts = W.batched_instances(n_inst=5, seed=321, n_chains=64)
+    mk = lambda w: VmcSr(w, W.init_params(w.n, w.m, w.is_complex, 0.05, w.seed), prec=prec)
+    single = [mk(w) for w in insts]
+    batch = [mk(w) for w in insts]
+    for v in single:
+        v.sample()
+        v.amplitudes()
+        v.energies()
+    streams = [torch.cuda.Stream() for _ in insts] if own_streams else None
+    sweep, amp, eloc = _batch_jobs(nk, batch, streams)
+    cur = torch.cuda.current_stream()
+    if streams:
+        for s in streams:
+            s.wait_stream(cur)
+    nk.nk_batch_sweep(sweep)
+    nk.nk_batch_logpsi(amp, prec=prec)
+    nk.nk_batch_local_energy(eloc)
+    torch.cuda.synchronize()
+    for a, b in zip(single, batch):
+        for x, y in ((a.samples, b.samples), (a.n_acc, b.n_acc), (a.chains.sigma, b.chains.sigma),
+                     (a.logpsi, b.logpsi), (a.theta, b.theta), (a.eloc, b.eloc), (a.t, b.t)):
+            assert torch.equal(x, y), a.w.name
+        assert a.chains.counter == b.chains.counter
+
+
+def test_batch_entry_point_rejects_bad_item_before_enqueueing(mods):
+    nk, _ = mods
+    from paper_1904_00031_gb300.vmc import VmcSr
+    insts = W.batched_instances(n_inst=3, seed=5, n_chains=32)
+    vs = [VmcSr(w, W.init_params(w.n, w.m, w.is_complex, 0.05, w.seed)) for w in insts]
+    sweep, amp, eloc = _batch_jobs(nk, vs)
+    before = [v.samples.clone() for v in vs]
+    counters = [v.chains.counter for v in vs]
+    sweep[2]["scratch"] = None if sweep[2]["scratch"] is None else sweep[2]["scratch"][:256]
+    sweep[2]["n_samples_per_chain"] = -1
+    with pytest.raises(nk.NkError, match="item 2"):
+        nk.nk_batch_sweep(sweep)
+    torch.cuda.synchronize()
+    for v, s0, c0 in zip(vs, before, counters):
+        assert torch.equal(v.samples, s0)      # nothing ran, item 0 included
+        assert v.chains.counter == c0
