@@ -99,13 +99,19 @@ __device__ __forceinline__ void pair_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// theta += m2s * increment for this thread's units, in chunks of 8 TMEM
+constexpr int kThetaChunk = 13;  // TMEM columns per load / wait / store round trip
+
+// theta += m2s * increment for this thread's units, in chunks of kThetaChunk TMEM
 // columns (complex: column 2 q + 0/1 = Re/Im theta of unit q; real: column q).
+// The stores are not waited for here: the wait comes before the next read of
+// theta (the next accepted move, the end-of-sweep refresh, the kernel's end),
+// so that their latency overlaps the steps in between.
 template <bool CPLX, int WPC, int TC, int C0>
 __device__ __forceinline__ void theta_add(uint32_t tm, const typename RatioTypes<CPLX>::F* wdc,
                                           float m2s, int h, int lane, int mp) {
+  if constexpr (C0 == 0) tmem_st_wait();  // the previous update's stores
   if constexpr (C0 < TC) {
-    constexpr int N = (TC - C0) < 8 ? (TC - C0) : 8;
+    constexpr int N = (TC - C0) < kThetaChunk ? (TC - C0) : kThetaChunk;
     float v[N];
     tmem_ld_cols<N>(tm + C0, v);
     tmem_ld_wait();
@@ -122,7 +128,7 @@ __device__ __forceinline__ void theta_add(uint32_t tm, const typename RatioTypes
       }
     }
     tmem_st_cols<N>(tm + C0, v);
-    theta_add<CPLX, WPC, TC, C0 + 8>(tm, wdc, m2s, h, lane, mp);
+    theta_add<CPLX, WPC, TC, C0 + kThetaChunk>(tm, wdc, m2s, h, lane, mp);
   }
 }
 
@@ -408,7 +414,6 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
             ty[qp] = f2mul(ny, inv);
           }
           theta_add<true, WPC, TC, 0>(tmem_th, wdc, -2.f * si, h, lane, mp);
-          tmem_st_wait();
         } else {
 #pragma unroll
           for (int q = 0; q < E; ++q) {
@@ -420,7 +425,6 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
             }
           }
           theta_add<false, WPC, TC, 0>(tmem_th, wdc, -2.f * si, h, lane, mp);
-          tmem_st_wait();
         }
         __syncwarp();
         if (lane == 0) {
@@ -457,6 +461,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
         for (int ii = lane; ii < n; ii += 32) out[ii] = sg[ii];
       }
       // exact refresh of t from theta (this thread's own entries)
+      tmem_st_wait();
       theta_each<CPLX, TC, 0>(tmem_th, [&](int q, F x) {
         if (jof(q) < mp) set_t(q, x, true);
       });
@@ -466,6 +471,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
       kphase ^= 1u;
     }
   }
+  tmem_st_wait();  // the last update's stores, before the columns are freed
   if (timed_out && lane == 0) dev_status_set(1u << NK_ERR_TIMEOUT);
   if (timed_out && producer) {
     // let copies still in flight land before the CTA exits
