@@ -201,17 +201,14 @@ def stage_flops(w, n_nonnull: float, n_accept: float, n_connected: float) -> dic
 def run_gpu(args):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     from paper_1904_00031_gb300 import nk
     from paper_1904_00031_gb300 import workloads as W
+    from paper_1904_00031_gb300 import replicas as R
     from paper_1904_00031_gb300.vmc import VmcSr
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
+    world, rank, local = R.env_world()
+    R.init(world, "nccl")
     torch.cuda.set_device(local)
     nk.load_library()
     w = W.workload(args.workload)
@@ -219,13 +216,12 @@ def run_gpu(args):
     prec_name = args.prec if args.prec != "auto" else "bf16x2"
     prec = nk.NK_PREC_FP32 if prec_name == "fp32" else nk.NK_PREC_BF16X2
     # each rank samples its own chains (independent replicas)
-    sigma0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed + 7919 * rank)
+    sigma0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, R.replica_seed(w.seed, rank))
     v = VmcSr(w, params, sigma0, prec, graph=bool(args.graph), autotune=True)
     stream = torch.cuda.current_stream()
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        R.barrier(world)
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
@@ -260,12 +256,9 @@ def run_gpu(args):
                                      for k in range(args.steps)]))
                 for si, name in enumerate(stages)}
     info = v.info()
-    t = torch.tensor([total_ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = R.max_over_ranks(total_ms, world, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * w.n_samples / (ms_per_step / 1e3)
+    value = R.aggregate_rate(w.n_samples, world, ms_per_step / 1e3)
 
     # end to end through the public API: parameters H2D from pinned memory,
     # one iteration, the FP64 status block D2H, every step
@@ -286,11 +279,7 @@ def run_gpu(args):
         host_info.copy_(v.info_buf, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([e2e_ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t.item())
+    e2e_ms = R.max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
     h2d = (pa.numel() + pb.numel() + pw.numel()) * 8
 
     # the plain FP32 path on the same workload (for the mixed-precision ratio)
@@ -370,13 +359,12 @@ def run_gpu(args):
             v.step()
             ev_ck[k][1].record(stream)
         barrier()
-        tck = torch.tensor([sum(a.elapsed_time(b) for a, b in ev_ck)], device="cuda")
-        if world > 1:
-            dist.all_reduce(tck, op=dist.ReduceOp.MAX)
-        ck_ms = float(tck.item()) / args.steps
+        ck_ms = R.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev_ck), world,
+                                 "cuda") / args.steps
         info_ck = v.info()
         ckpt = {"sr_iterations_before": args.checkpoint_iters + 3 * args.steps + args.warmup,
-                "value": round(world * w.n_samples / (ck_ms / 1e3), 2), "unit": "samples/s",
+                "value": round(R.aggregate_rate(w.n_samples, world, ck_ms / 1e3), 2),
+                "unit": "samples/s",
                 "ms_per_step": round(ck_ms, 3), "acceptance": round(info_ck["acceptance"], 4),
                 "energy": info_ck["energy"]}
     out = {
@@ -403,7 +391,8 @@ def run_gpu(args):
                                 "mufu_sin_tops": round(alu_meas["mufu_sin_ops"] / 1e12, 3)}
                                if "fp32_fma_flops" in alu_meas else alu_meas),
         "after_sr_iterations": ckpt,
-        "e2e": {"value": round(world * w.n_samples / (e2e_ms / 1e3), 2), "unit": "samples/s",
+        "e2e": {"value": round(R.aggregate_rate(w.n_samples, world, e2e_ms / 1e3), 2),
+                "unit": "samples/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nk.NK_INFO_LEN * 8},
         "gpu_launches": v.launches_per_step() * args.steps,
         "graph": bool(args.graph), "sr_split_k": getattr(v, "split_k", None),
@@ -440,28 +429,24 @@ def profile_kernels():
 def run_gpu_batched(args):
     """64 uneven independent instances, one CUDA graph launch per iteration."""
     import torch
-    import torch.distributed as dist
 
     from paper_1904_00031_gb300 import nk
     from paper_1904_00031_gb300 import workloads as W
+    from paper_1904_00031_gb300 import replicas as R
     from paper_1904_00031_gb300.batch import BatchedVmc
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
+    world, rank, local = R.env_world()
+    R.init(world, "nccl")
     torch.cuda.set_device(local)
     nk.load_library()
     prec_name = args.prec if args.prec != "auto" else "bf16x2"
     prec = nk.NK_PREC_FP32 if prec_name == "fp32" else nk.NK_PREC_BF16X2
-    insts = W.batched_instances(64, 4242 + 1000 * rank, 1024)
+    insts = W.batched_instances(64, R.replica_seed(4242, rank), 1024)
     b = BatchedVmc(insts, prec=prec, graph=bool(args.graph))
     stream = torch.cuda.current_stream()
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        R.barrier(world)
         torch.cuda.synchronize()
 
     for _ in range(max(args.warmup, 2)):
@@ -481,13 +466,11 @@ def run_gpu_batched(args):
         ev_it[k][1].record(stream)
     barrier()
     clk = clocks.stop()
-    t = torch.tensor([sum(a.elapsed_time(e) for a, e in ev_it)], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item()) / args.steps
+    ms = R.max_over_ranks(sum(a.elapsed_time(e) for a, e in ev_it), world, "cuda") / args.steps
     ns = b.n_samples
     return rank, {
-        "metric": METRIC, "value": round(world * ns / (ms / 1e3), 2), "unit": "samples/s",
+        "metric": METRIC, "value": round(R.aggregate_rate(ns, world, ms / 1e3), 2),
+        "unit": "samples/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (64 seeded uneven 1D TFIM / Heisenberg instances)",
