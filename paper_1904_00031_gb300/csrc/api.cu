@@ -56,7 +56,45 @@ struct Compiled {
   std::vector<OpDSite> ds;
   std::vector<OpDBond> db;
   std::vector<OpMove> mv;
+  int32_t flags = 0;  // OpDevHeader::flags
 };
+
+// Site-quad layout of the move list (kOpQuadMoves): the moves whose first spin
+// is the same site are taken four at a time (a short last quad is completed by
+// null moves of that site: all matrix elements zero), and within every tile of
+// 64 moves, quad g of the tile occupies positions g, g + 16, g + 32, g + 48 --
+// the four moves one thread of the local-energy tile evaluates, which then share
+// the sign s_i of every configuration.  Used when it adds at most 1/16 null
+// moves (e.g. a square lattice with nearest and next-nearest bonds: four moves
+// per site); the move set and so the local energies are unchanged.
+static bool quad_layout(std::vector<OpMove>& mv) {
+  auto null_move = [](int site) {
+    OpMove z;
+    memset(&z, 0, sizeof(z));
+    z.i = z.k = site;
+    return z;
+  };
+  std::vector<OpMove> quads;  // 4 consecutive entries per quad
+  size_t a = 0;
+  while (a < mv.size()) {  // mv is ordered by first site
+    size_t b = a;
+    while (b < mv.size() && mv[b].i == mv[a].i) ++b;
+    for (size_t c = a; c < b; c += 4)
+      for (size_t u = 0; u < 4; ++u) quads.push_back(c + u < b ? mv[c + u] : null_move(mv[a].i));
+    a = b;
+  }
+  const size_t nq = quads.size() / 4, nq16 = (nq + 15) / 16 * 16;
+  if (mv.empty() || nq16 * 4 * 16 > mv.size() * 17) return false;
+  for (size_t q = nq; q < nq16; ++q)
+    for (int u = 0; u < 4; ++u) quads.push_back(null_move(0));
+  std::vector<OpMove> out(nq16 * 4);
+  for (size_t q = 0; q < nq16; ++q) {
+    const size_t t = q / 16, g = q % 16;
+    for (int u = 0; u < 4; ++u) out[64 * t + 16 * u + g] = quads[4 * q + u];
+  }
+  mv.swap(out);
+  return true;
+}
 
 static bool nz(const double* c) { return c[0] != 0.0 || c[1] != 0.0; }
 
@@ -147,6 +185,7 @@ static nk_status compile_op(const nk_operator* op, Compiled& out) {
       if (any) out.mv.push_back(v);
     }
   }
+  if (quad_layout(out.mv)) out.flags |= kOpQuadMoves;
   return NK_OK;
 }
 
@@ -328,6 +367,7 @@ nk_status nk_operator_upload(const nk_operator* op, void* dev, size_t bytes, voi
   h.n_dsite = (int32_t)c.ds.size();
   h.n_dbond = (int32_t)c.db.size();
   h.n_moves = (int32_t)c.mv.size();
+  h.flags = c.flags;
   size_t total = layout_sizes(c, &h.off_dsite, &h.off_dbond, &h.off_moves);
   if (bytes < total)
     return fail(NK_ERR_SHAPE, "nk_operator_upload: %zu B given, %zu B needed", bytes, total);

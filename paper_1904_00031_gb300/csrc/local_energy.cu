@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   const F* th = reinterpret_cast<const F*>(A.theta);
   F* tout = reinterpret_cast<F*>(A.t_out);
   const int nm = A.n_moves;
+  const bool quad = (H->flags & kOpQuadMoves) != 0;  // site-quad move layout
   const int ntile = (nm + kEBM - 1) / kEBM, nchunk = mp / kEBK;
   const int seg = blockIdx.y;
   const int tile_begin = ntile * seg / A.nseg, tile_end = ntile * (seg + 1) / A.nseg;
@@ -330,69 +331,88 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
     }
     const T2* mv_b = mvt + (size_t)b * kEBK * kEBM;
     const TS* t_b = tS + (size_t)b * kEBK * kETS;
-    if constexpr (CPLX) {
-      // r = C - s t D for two moves at once: with ns = -s,
-      // Re r = Re C + ns (Re t Re D - Im t Im D), Im r = Im C + ns (Re t Im D + Im t Re D),
-      // then P *= r.
-      const float4* mvc = reinterpret_cast<const float4*>(mv_b);
+    // QUAD (site-quad move layout): the thread's four moves share s_i, so -s t
+    // is formed once per configuration and hidden unit instead of per move
+    auto chunk = [&](auto quad_tag) {
+      constexpr bool QUAD = decltype(quad_tag)::value;
+      if constexpr (CPLX) {
+        // r = C - s t D for two moves at once: with ns = -s,
+        // Re r = Re C + ns (Re t Re D - Im t Im D), Im r = Im C + ns (Re t Im D + Im t Re D),
+        // then P *= r.
+        const float4* mvc = reinterpret_cast<const float4*>(mv_b);
 #pragma unroll
-      for (int kk = 0; kk < kEBK; ++kk) {
-        float4 t4[4], c4[2], d4[2];
+        for (int kk = 0; kk < kEBK; ++kk) {
+          float4 t4[4], c4[2], d4[2];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) t4[p] = t_b[kk * kETS + ts * 4 + p];
-#pragma unroll
-        for (int qp = 0; qp < 2; ++qp) {
-          c4[qp] = mvc[kk * kEBM + tm + 16 * qp];
-          d4[qp] = mvc[kk * kEBM + 32 + tm + 16 * qp];
-        }
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const float2 tx = make_float2(t4[p].x, t4[p].y), ty = make_float2(t4[p].z, t4[p].w);
-          const float2 nty = make_float2(-t4[p].z, -t4[p].w);
+          for (int p = 0; p < 4; ++p) t4[p] = t_b[kk * kETS + ts * 4 + p];
 #pragma unroll
           for (int qp = 0; qp < 2; ++qp) {
-            const float2 cx = make_float2(c4[qp].x, c4[qp].y), cy = make_float2(c4[qp].z, c4[qp].w);
-            const float2 dx = make_float2(d4[qp].x, d4[qp].y), dy = make_float2(d4[qp].z, d4[qp].w);
-            const float2 tdx = f2fma(tx, dx, f2mul(nty, dy));
-            const float2 tdy = f2fma(tx, dy, f2mul(ty, dx));
-            const float2 rx = f2fma(ns2[p][qp], tdx, cx);
-            const float2 ry = f2fma(ns2[p][qp], tdy, cy);
-            const float2 px = Px[p][qp], py = Py[p][qp];
-            Px[p][qp] = f2fma(make_float2(-py.x, -py.y), ry, f2mul(px, rx));
-            Py[p][qp] = f2fma(py, rx, f2mul(px, ry));
+            c4[qp] = mvc[kk * kEBM + tm + 16 * qp];
+            d4[qp] = mvc[kk * kEBM + 32 + tm + 16 * qp];
           }
-        }
-        if ((kk & 7) == 7) {
 #pragma unroll
-          for (int p = 0; p < 4; ++p)
+          for (int p = 0; p < 4; ++p) {
+            const float2 tx = make_float2(t4[p].x, t4[p].y), ty = make_float2(t4[p].z, t4[p].w);
+            const float2 nty = make_float2(-t4[p].z, -t4[p].w);
+            // QUAD: (nux, nuy) = -s t, shared by both move pairs
+            const float2 nux = QUAD ? f2mul(ns2[p][0], tx) : tx;
+            const float2 nuy = QUAD ? f2mul(ns2[p][0], ty) : ty;
 #pragma unroll
             for (int qp = 0; qp < 2; ++qp) {
-              renorm_lane(Px[p][qp].x, Py[p][qp].x, Pe[p][2 * qp]);
-              renorm_lane(Px[p][qp].y, Py[p][qp].y, Pe[p][2 * qp + 1]);
+              const float2 cx = make_float2(c4[qp].x, c4[qp].y), cy = make_float2(c4[qp].z, c4[qp].w);
+              const float2 dx = make_float2(d4[qp].x, d4[qp].y), dy = make_float2(d4[qp].z, d4[qp].w);
+              float2 rx, ry;
+              if constexpr (QUAD) {
+                rx = f2fma(nux, dx, f2fma(make_float2(-nuy.x, -nuy.y), dy, cx));
+                ry = f2fma(nux, dy, f2fma(nuy, dx, cy));
+              } else {
+                const float2 tdx = f2fma(tx, dx, f2mul(nty, dy));
+                const float2 tdy = f2fma(tx, dy, f2mul(ty, dx));
+                rx = f2fma(ns2[p][qp], tdx, cx);
+                ry = f2fma(ns2[p][qp], tdy, cy);
+              }
+              const float2 px = Px[p][qp], py = Py[p][qp];
+              Px[p][qp] = f2fma(make_float2(-py.x, -py.y), ry, f2mul(px, rx));
+              Py[p][qp] = f2fma(py, rx, f2mul(px, ry));
             }
+          }
+          if ((kk & 7) == 7) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+              for (int qp = 0; qp < 2; ++qp) {
+                renorm_lane(Px[p][qp].x, Py[p][qp].x, Pe[p][2 * qp]);
+                renorm_lane(Px[p][qp].y, Py[p][qp].y, Pe[p][2 * qp + 1]);
+              }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < kEBK; ++kk) {
+          F t[4];
+          T2 v[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) t[p] = t_b[kk * kETS + ts * 4 + p];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[q] = mv_b[kk * kEBM + tm + 16 * q];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const float nst = -sgn[p][0] * t[p];  // QUAD: -s t of all four moves
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              P[p][q].v *= fmaf(QUAD ? nst : -sgn[p][q] * t[p], v[q].y, v[q].x);
+          }
+          if ((kk & 7) == 7) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) P[p][q].renorm();
+          }
         }
       }
-    } else {
-#pragma unroll
-      for (int kk = 0; kk < kEBK; ++kk) {
-        F t[4];
-        T2 v[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) t[p] = t_b[kk * kETS + ts * 4 + p];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = mv_b[kk * kEBM + tm + 16 * q];
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) P[p][q].v *= fmaf(-sgn[p][q] * t[p], v[q].y, v[q].x);
-        if ((kk & 7) == 7) {
-#pragma unroll
-          for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) P[p][q].renorm();
-        }
-      }
-    }
+    };
+    if (quad) chunk(std::true_type{});
+    else chunk(std::false_type{});
     if (it + 1 < it_end) store_t(it + 1, b ^ 1);
     if (kc == nchunk - 1) {
       // fold the tile's ratios into the local energies (FP64)

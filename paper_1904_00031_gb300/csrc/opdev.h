@@ -17,8 +17,12 @@ struct OpDevHeader {
   int32_t n;
   int32_t n_dsite, n_dbond, n_moves;
   int32_t off_dsite, off_dbond, off_moves;  // byte offsets from the header
-  int32_t reserved;
+  int32_t flags;                            // kOpQuadMoves
 };
+
+// The moves are laid out in site quads: in every tile of 64, positions g,
+// g + 16, g + 32, g + 48 (g < 16) are moves with the same first spin i.
+constexpr int32_t kOpQuadMoves = 1;
 
 struct OpDSite {  // diagonal of a site term: d[idx(s_i)]
   int32_t i, reserved;

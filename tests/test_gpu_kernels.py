@@ -98,6 +98,8 @@ OPS = {
     "tfim2d": (lambda: W.ising(36, W.square_bonds(6), h=3.04), 36, False),
     # 72 exchange moves: two move tiles, the second ragged
     "j1j2_6x6": (lambda: W.j1j2(6, 1.0, 0.5, True), 36, True),
+    # four moves per site and 64 sites: the site-quad move layout, four move tiles
+    "j1j2_8x8": (lambda: W.j1j2(8, 1.0, 0.5, True), 64, True),
 }
 
 
