@@ -107,6 +107,15 @@ __device__ __forceinline__ void split_bf16(float x, uint32_t& hi, uint32_t& lo) 
   hi = bf16_bits(x);
   lo = bf16_bits(x - bf16_val(hi));
 }
+// The same split of two values at once, packed (a in the low half): the paired
+// conversions give bit for bit the results of two split_bf16 calls.
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
 // FP64 input: rounded to FP32 first (one conversion; the FP64 pipe is slow on
 // this GPU), which perturbs hi + lo by at most 2^-24 relative, far below the
 // 2^-17 of the two-term split itself
@@ -800,6 +809,13 @@ __device__ __forceinline__ void adj_tc_body(const CUtensorMap* tsp, const AdjTcA
 #pragma unroll
       for (int cc = 0; cc < SPT / 8; ++cc) {
         const int kl = qs * SPT + cc * 8;
+        // v of the chunk's 8 samples, fetched once for all of the thread's rows
+        float vr8[8], vi8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          vr8[e] = __shfl_sync(0xffffffffu, vq0, cc * 8 + e);
+          vi8[e] = CPLX ? __shfl_sync(0xffffffffu, vq1, cc * 8 + e) : 0.f;
+        }
 #pragma unroll
         for (int u2 = 0; u2 < JPT; ++u2) {
           uint32_t hr[4], lr[4], hi_[4], li[4];
@@ -809,28 +825,20 @@ __device__ __forceinline__ void adj_tc_body(const CUtensorMap* tsp, const AdjTcA
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const int e = cc * 8 + 2 * e2 + h;
+              const float vr = vr8[2 * e2 + h], vi = vi8[2 * e2 + h];
               if constexpr (CPLX) {
-                const float vr = __shfl_sync(0xffffffffu, vq0, e);
-                const float vi = __shfl_sync(0xffffffffu, vq1, e);
                 const float2 t = tq[e][u2];
                 zr[h] = t.x * vr + t.y * vi;  // conj(t) v
                 zi[h] = t.x * vi - t.y * vr;
               } else {
-                zr[h] = tq[e][u2] * __shfl_sync(0xffffffffu, vq0, e);
+                zr[h] = tq[e][u2] * vr;
                 zi[h] = 0.f;
+                (void)vi;
               }
             }
             uint32_t a0, b0, a1, b1;
-            split_bf16(zr[0], a0, b0);
-            split_bf16(zr[1], a1, b1);
-            hr[e2] = a0 | (a1 << 16);
-            lr[e2] = b0 | (b1 << 16);
-            if constexpr (CPLX) {
-              split_bf16(zi[0], a0, b0);
-              split_bf16(zi[1], a1, b1);
-              hi_[e2] = a0 | (a1 << 16);
-              li[e2] = b0 | (b1 << 16);
-            }
+            split_bf16x2(zr[0], zr[1], hr[e2], lr[e2]);
+            if constexpr (CPLX) split_bf16x2(zi[0], zi[1], hi_[e2], li[e2]);
           }
           const int row = jb + u2;
           *reinterpret_cast<uint4*>(Ahi + sw128_offset(row, kl)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
