@@ -190,10 +190,17 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
     eacc[p * 256 + tid] = make_double2(er[p], ei[p]);
   }
 
+  // Hidden-unit chunk of iteration it: each move tile walks the chunks in the
+  // direction opposite to the previous one, so its first chunks are the ones the
+  // CTA read last (still in L2) -- fewer DRAM re-reads of the t rows.
+  auto chunk_of = [&](int it) {
+    const int r = it % nchunk;
+    return ((it / nchunk - tile_begin) & 1) ? nchunk - 1 - r : r;
+  };
   // t tile of a chunk: thread covers (ss, kk) = (e >> 4, e & 15), e = tid + 256 u
   F tv[4];
   auto load_t = [&](int it) {
-    const int kc = it % nchunk, mt = it / nchunk;
+    const int kc = chunk_of(it), mt = it / nchunk;
     const bool reuse = tout && mt > tile_begin;  // t was written by this CTA at its first tile
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
     }
   };
   auto store_t = [&](int it, int buf) {
-    const int kc = it % nchunk, mt = it / nchunk;
+    const int kc = chunk_of(it), mt = it / nchunk;
     const bool reuse = tout && mt > tile_begin;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -322,7 +329,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
       const int it1 = it + 1;
       mbar_arrive_expect_tx(&mbar[b ^ 1], tile_bytes);
       tma_load_2d(mvt + (size_t)(b ^ 1) * kEBK * kEBM, &mtab,
-                      (it1 / nchunk) * kEBM * (CPLX ? 4 : 2), (it1 % nchunk) * kEBK, &mbar[b ^ 1]);
+                      (it1 / nchunk) * kEBM * (CPLX ? 4 : 2), chunk_of(it1) * kEBK, &mbar[b ^ 1]);
     }
     if (it + 1 < it_end) load_t(it + 1);
     if (!mbar_wait_bounded(&mbar[b], (uint32_t)(((it - it_begin) >> 1) & 1))) {
