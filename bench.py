@@ -503,7 +503,9 @@ def main():
         if rank != 0:
             return
         from paper_1904_00031_gb300 import workloads as W
-        w = W.workload(args.workload)
+        # the 64-instance batch: its first instance stands for the workload
+        w = (W.workload(args.workload) if args.workload != "c4"
+             else W.batched_instances(64, 4242, 1024)[0])
         tot_s, tot_n = 0.0, 0
         for k in range(args.warmup + args.steps):
             r = run_oracle_subprocess(args.workload, nc, spc, ncg)
@@ -518,7 +520,10 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * tot_s / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "oracle_sample": sample},
+            "config": {"workload": w.name, "n": w.n, "m": w.m, "complex": w.is_complex,
+                       "chains": w.n_chains, "samples_per_chain": w.samples_per_chain,
+                       "burn_in_sweeps": w.n_discard, "samples_per_iter": w.n_samples,
+                       "moves": w.move, "n_cg": w.n_cg, "oracle_sample": sample},
             "cpu_baseline": {"value": round(val, 4), "unit": "samples/s", "cores": 1,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(val, 4), "unit": "samples/s", "h2d_bytes_per_step": 0,

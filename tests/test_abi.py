@@ -133,3 +133,32 @@ def test_operator_compilation_sizes(lib):
     bad = nk._Operator(3, 0, None, None, 1, 0, np.array([0], np.int32).ctypes.data,
                        np.array([7], np.int32).ctypes.data, np.zeros(32).ctypes.data)
     assert lib.nk_operator_bytes(C.byref(bad)) == 0
+
+
+def test_batch_calls_check_every_item_first(lib):
+    """Items are checked on the host, all before any launch: a bad item is named,
+    and the shape limits of the single calls apply (no device is touched here:
+    every call below has a failing item)."""
+    from paper_1904_00031_gb300 import nk
+
+    def sweep_items(m, bad_second):
+        n, cplx = 8, 1
+        r = nk._Rbm(n, m, cplx, 0, 256, 256, 256, 4096, lib.nk_rbm_workspace_bytes(n, m, cplx))
+        ch = nk._Chains(16, 4, 4096, 1, 0, None)
+        need = lib.nk_metropolis_scratch_bytes(n, m, cplx, 0, 0)
+        good = nk._SweepItem(C.addressof(r), C.addressof(ch), 0, 0, None, None, 1, 2, 4096, None,
+                             4096, need, None)
+        bad = nk._SweepItem(C.addressof(r), C.addressof(ch), 0, 0, None, None, -1, 2, 4096, None,
+                            4096, need, None)
+        items = (nk._SweepItem * 2)(good, bad if bad_second else good)
+        return items, (r, ch)
+
+    items, keep = sweep_items(2048, True)     # the widest sampler layer passes its checks
+    assert lib.nk_batch_sweep(C.cast(items, C.c_void_p), 2, None) == 1
+    assert b"item 1" in lib.nk_last_error()
+    items, keep = sweep_items(2049, True)     # one unit too many: item 0 is rejected
+    assert lib.nk_batch_sweep(C.cast(items, C.c_void_p), 2, None) == 2
+    assert b"item 0" in lib.nk_last_error()
+    assert lib.nk_batch_sweep(None, 3, None) == 1
+    assert lib.nk_batch_logpsi(None, -1, 0, None) == 1
+    assert lib.nk_batch_local_energy(None, 2, None) == 1
