@@ -86,4 +86,6 @@ class BatchedVmc:
             return sum(v.launches_per_step() for v in self.items)
         n = sum(v.launches_per_step() - v.sr_launches() for v in self.items)
         groups = (len(self.items) + 63) // 64   # up to 64 instances per launch
-        return n + groups * (10 + 8 * self.sr_args[2])
+        # per group: statistics (3), flags, sigma' planes (2), force, CG start (2),
+        # 7 per CG iteration plus the first iteration's planes, update, prepare (2)
+        return n + groups * (3 + 1 + 2 + 2 + 2 + 7 * self.sr_args[2] + 1 + 3)

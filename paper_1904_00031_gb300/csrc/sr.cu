@@ -20,6 +20,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "sgemm.cuh"
+#include "bf16split.cuh"
 #include "tc.cuh"
 
 namespace nk {
@@ -119,6 +120,16 @@ struct D<false> {
 
 __device__ __forceinline__ double re(double x) { return x; }
 __device__ __forceinline__ double re(double2 x) { return x.x; }
+__device__ __forceinline__ double im(double) { return 0.0; }
+__device__ __forceinline__ double im(double2 x) { return x.y; }
+
+// Where cg_step_p also writes the BF16 hi/lo planes of p (tensor-core path):
+// planes [2][mt*128][na64], p in the augmented [m+1][na] layout.  planes = NULL:
+// not written (the FP32 path, or the first iteration's planes come from bplanes).
+struct PlaneOut {
+  uint16_t* planes = nullptr;
+  int na = 1, mt = 0, na64 = 64;
+};
 __device__ __forceinline__ double norm2(double x) { return x * x; }
 __device__ __forceinline__ double norm2(double2 x) { return x.x * x.x + x.y * x.y; }
 __device__ __forceinline__ double cdot_re(double a, double b) { return a * b; }
@@ -732,7 +743,8 @@ template <bool CPLX>
 __device__ __forceinline__ void cg_step_p_body(int bx, int gx, const void* rv, void* pv,
                                                                 int64_t pa, const double* red,
                                                                 double* scal, int it,
-                                                                double rtol, int nb) {
+                                                                double rtol, int nb,
+                                                                const PlaneOut& po = PlaneOut{}) {
   if (scal[SC_DONE] != 0.0) return;
   using DT = typename D<CPLX>::T;
   const DT* r = reinterpret_cast<const DT*>(rv);
@@ -759,7 +771,26 @@ __device__ __forceinline__ void cg_step_p_body(int bx, int gx, const void* rv, v
 #pragma unroll
       for (int u = 0; u < kVecUnroll; ++u) {
         const int64_t e = e0 + u * stride;
-        if (e < pa) p[e] = axpy(beta, pp[u], rr[u]);
+        if (e < pa) {
+          const DT q = axpy(beta, pp[u], rr[u]);
+          p[e] = q;
+          if (po.planes) {
+            // the BF16 hi/lo planes of the new p for the next forward contraction
+            const int j = (int)(e / po.na), i = (int)(e % po.na);
+            const int64_t pl = (int64_t)po.mt * 128 * po.na64;
+            uint32_t hi, lo;
+            split_bf16(re(q), hi, lo);
+            const int64_t k0 = bplane_index(j, i, 0, CPLX, po.na64);
+            po.planes[k0] = (uint16_t)hi;
+            po.planes[pl + k0] = (uint16_t)lo;
+            if constexpr (CPLX) {
+              split_bf16(im(q), hi, lo);
+              const int64_t k1 = bplane_index(j, i, 1, CPLX, po.na64);
+              po.planes[k1] = (uint16_t)hi;
+              po.planes[pl + k1] = (uint16_t)lo;
+            }
+          }
+        }
       }
     }
   }
@@ -775,8 +806,9 @@ template <bool CPLX>
 __global__ void __launch_bounds__(kVecThreads) cg_step_p_kernel(const void* rv, void* pv,
                                                                 int64_t pa, const double* red,
                                                                 double* scal, int it,
-                                                                double rtol, int nb) {
-  cg_step_p_body<CPLX>(blockIdx.x, gridDim.x, rv, pv, pa, red, scal, it, rtol, nb);
+                                                                double rtol, int nb,
+                                                                PlaneOut po) {
+  cg_step_p_body<CPLX>(blockIdx.x, gridDim.x, rv, pv, pa, red, scal, it, rtol, nb, po);
 }
 
 // alpha <- alpha - lr delta (FP64 master), delta in the augmented layout; info.
@@ -955,10 +987,25 @@ __global__ void __launch_bounds__(kVecThreads) cg_step_p_batch(const SrDesc* __r
                                                                int it, double rtol) {
   const SrDesc& d = D[blockIdx.y];
   if ((int)blockIdx.x >= d.nb_pa) return;
+  PlaneOut po;
+  po.planes = reinterpret_cast<uint16_t*>(d.xbf);
+  po.na = d.n + 1;
+  po.mt = d.mt1;
+  po.na64 = d.na64;
   if (d.cplx)
-    cg_step_p_body<true>(blockIdx.x, d.nb_pa, d.r, d.p, d.pa, d.red, d.scal, it, rtol, d.nb_pa);
+    cg_step_p_body<true>(blockIdx.x, d.nb_pa, d.r, d.p, d.pa, d.red, d.scal, it, rtol, d.nb_pa,
+                         po);
   else
-    cg_step_p_body<false>(blockIdx.x, d.nb_pa, d.r, d.p, d.pa, d.red, d.scal, it, rtol, d.nb_pa);
+    cg_step_p_body<false>(blockIdx.x, d.nb_pa, d.r, d.p, d.pa, d.red, d.scal, it, rtol, d.nb_pa,
+                          po);
+  if (d.fwd_nseg == 2) {
+    // the next forward's two halves add onto zero (y of this iteration is consumed)
+    double* y = reinterpret_cast<double*>(d.y);
+    const int64_t len = d.ns * (d.cplx ? 2 : 1);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)d.nb_pa * blockDim.x)
+      y[e] = 0.0;
+  }
 }
 
 __global__ void sr_update_batch(const SrDesc* __restrict__ D, double lr, int n_cg, double rtol) {
@@ -1044,11 +1091,21 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
   const int64_t sg_blocks = (ns + kSgBS - 1) / kSgBS;
   aa.v = sc + L.v;
   aa.skip = scal + SC_DONE;
+  // from the second CG iteration on, cg_step_p writes the planes of p itself
+  PlaneOut po;
+  if (tc) {
+    po.planes = (uint16_t*)(sc + L.xbf);
+    po.na = L.na;
+    po.mt = L.mt1;
+    po.na64 = L.na64;
+  }
   for (int it = 0; it < n_cg; ++it) {
     if (tc) {
-      if (nk_status e = launch_bplanes_from_f64(sc + L.p, m + 1, n + 1, L.na, CPLX, L.mt1, L.na64,
-                                                sc + L.xbf, scal + SC_DONE, st))
-        return e;
+      if (it == 0) {
+        if (nk_status e = launch_bplanes_from_f64(sc + L.p, m + 1, n + 1, L.na, CPLX, L.mt1,
+                                                  L.na64, sc + L.xbf, scal + SC_DONE, st))
+          return e;
+      }
       if (nk_status e = launch_fwd_tc(fa, sc + L.xbf, st)) return e;
     } else {
       to_f32_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.p, sc + L.xf, L.pa, scal);
@@ -1068,7 +1125,7 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
     cg_step_x_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.x, sc + L.r, sc + L.p, sc + L.ap,
                                                         L.pa, red, scal, it, nbp);
     cg_step_p_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.r, sc + L.p, L.pa, red, scal, it,
-                                                        rtol, nbp);
+                                                        rtol, nbp, po);
     if (nk_status e = check_launch("nk_sr_step(cg)")) return e;
   }
   sr_update_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(r->a, r->b, r->w, n, m, sc + L.x, lr,
@@ -1304,7 +1361,10 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
   if (nk_status e = check_launch("nk_sr_step_batch(force)")) return e;
   for (int z = 0; z < G; ++z) ab.a[z].skip = fb.a[z].skip;
   for (int it = 0; it < n_cg; ++it) {
-    if (nk_status e = launch_bplanes_p_batch(Dg, G, max_xp, st)) return e;
+    // from the second CG iteration on, cg_step_p_batch writes the planes of p itself
+    if (it == 0) {
+      if (nk_status e = launch_bplanes_p_batch(Dg, G, max_xp, st)) return e;
+    }
     if (nk_status e = launch_fwd_tc_batch(fb, G, max_fwd, max_na64, st)) return e;
     center_partial_batch<<<vs, kVecThreads, 0, st>>>(Dg);
     center_apply_batch<<<vs, kVecThreads, 0, st>>>(Dg);

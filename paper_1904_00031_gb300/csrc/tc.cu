@@ -26,6 +26,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "bf16split.cuh"
 #include "tc.cuh"
 #include "status.cuh"
 #include "umma.cuh"
@@ -94,34 +95,8 @@ bool make_map_f32(CUtensorMap* map, const void* base, int64_t rows, int64_t cols
 
 bool tc_supported_shape(int n, int m) { return n + 1 <= 448 && m >= 1; }
 
-// ------------------------------------------------------------------ BF16 helpers
+// BF16 hi/lo splits: bf16split.cuh
 
-__device__ __forceinline__ uint32_t bf16_bits(float x) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
-}
-__device__ __forceinline__ float bf16_val(uint32_t b) {
-  return __bfloat162float(__ushort_as_bfloat16((unsigned short)b));
-}
-// hi = bf16(x), lo = bf16(x - hi)
-__device__ __forceinline__ void split_bf16(float x, uint32_t& hi, uint32_t& lo) {
-  hi = bf16_bits(x);
-  lo = bf16_bits(x - bf16_val(hi));
-}
-// The same split of two values at once, packed (a in the low half): the paired
-// conversions give bit for bit the results of two split_bf16 calls.
-__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  const float2 hf = __bfloat1622float2(h);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
-}
-// FP64 input: rounded to FP32 first (one conversion; the FP64 pipe is slow on
-// this GPU), which perturbs hi + lo by at most 2^-24 relative, far below the
-// 2^-17 of the two-term split itself
-__device__ __forceinline__ void split_bf16(double x, uint32_t& hi, uint32_t& lo) {
-  split_bf16((float)x, hi, lo);
-}
 
 // ------------------------------------------------------------------ B planes
 

@@ -106,11 +106,14 @@ class VmcSr:
         return d
 
     def sr_launches(self) -> int:
-        """Kernel launches of one SR step (stats, force, CG, update, planes)."""
-        n = 5 + 8 * self.w.n_cg + 3
+        """Kernel launches of one SR step: statistics (3), force and CG start, the
+        CG iterations, the update and the refreshed planes (2)."""
         if self.prec == nk.NK_PREC_BF16X2:
-            n += 1
-        return n
+            # sigma'^T, sigma' rows, adjoint, reduction, CG start (2); per CG
+            # iteration 7 (the first also builds the planes of p)
+            return 3 + 6 + 7 * self.w.n_cg + 1 + 3
+        # adjoint, reduction, CG start (2); 8 per CG iteration
+        return 3 + 4 + 8 * self.w.n_cg + 3
 
     # kernel launches per step (for reporting)
     def launches_per_step(self) -> int:
@@ -118,7 +121,5 @@ class VmcSr:
         n = 1 + (1 if self.move == nk.NK_MOVE_EXCHANGE or self.w.is_complex else 0)
         n += 1                                                  # ln psi / theta
         n += 2                                                  # move tables, local energy
-        n += 5 + 8 * self.w.n_cg + 3                            # SR: stats, force, CG, update
-        if self.prec == nk.NK_PREC_BF16X2:
-            n += 1                                              # sigma^T plane
+        n += self.sr_launches()                                 # SR step
         return n
