@@ -13,7 +13,7 @@ import torch
 
 from . import nk
 from . import workloads as W
-from .vmc import VmcSr
+from .vmc import VmcSr, centring_fused
 
 
 class BatchedVmc:
@@ -87,5 +87,8 @@ class BatchedVmc:
         n = sum(v.launches_per_step() - v.sr_launches() for v in self.items)
         groups = (len(self.items) + 63) // 64   # up to 64 instances per launch
         # per group: statistics (3), flags, sigma' planes (2), force, CG start (2),
-        # 7 per CG iteration plus the first iteration's planes, update, prepare (2)
-        return n + groups * (3 + 1 + 2 + 2 + 2 + 7 * self.sr_args[2] + 1 + 3)
+        # 7 per CG iteration (6 when every forward writes its centring partials)
+        # plus the first iteration's planes, update, prepare (2)
+        fused = all(centring_fused(v.ns, v.w.m, v.w.is_complex) for v in self.items)
+        per = 6 if fused else 7
+        return n + groups * (3 + 1 + 2 + 2 + 2 + per * self.sr_args[2] + 1 + 3)

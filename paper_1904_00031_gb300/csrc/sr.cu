@@ -36,6 +36,13 @@ static int sr_vec_blocks(int64_t elems) {
   return (int)std::min<int64_t>(kVecBlocks, std::max<int64_t>(1, (elems + 1023) / 1024));
 }
 constexpr int kVecThreads = 256;
+
+// Centring partials written by the SR forward (one per CTA: sample tiles x
+// hidden-tile halves), or 0 when they would not fit the partials buffer.
+static int fwd_centring_parts(int64_t ns, int mt) {
+  const int64_t parts = ((ns + 127) / 128) * fwd_tc_nseg(ns, mt, 0, true);
+  return parts <= kVecBlocks ? (int)parts : 0;
+}
 // Elements per thread whose loads are issued together in the vector kernels
 // (a thread's elements are still visited, and summed, in grid-stride order).
 constexpr int kVecUnroll = 4;
@@ -953,7 +960,7 @@ __global__ void cg_init_scalars_batch(const SrDesc* __restrict__ D, double rtol)
 
 __global__ void __launch_bounds__(kVecThreads) center_partial_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
-  if ((int)blockIdx.x >= d.nb_ns) return;
+  if ((int)blockIdx.x >= d.nb_ns || d.ctr_parts > 0) return;  // else the forward wrote them
   if (d.cplx)
     center_partial_body<true>(blockIdx.x, d.nb_ns, d.y, d.weights, d.ns, d.red, d.scal);
   else
@@ -963,12 +970,13 @@ __global__ void __launch_bounds__(kVecThreads) center_partial_batch(const SrDesc
 __global__ void __launch_bounds__(kVecThreads) center_apply_batch(const SrDesc* __restrict__ D) {
   const SrDesc& d = D[blockIdx.y];
   if ((int)blockIdx.x >= d.nb_ns) return;
+  const int parts = d.ctr_parts > 0 ? d.ctr_parts : d.nb_ns;
   if (d.cplx)
     center_apply_body<true>(blockIdx.x, d.nb_ns, d.y, d.v, d.weights, d.ns, d.red, d.scal,
-                          d.nb_ns);
+                            parts);
   else
     center_apply_body<false>(blockIdx.x, d.nb_ns, d.y, d.v, d.weights, d.ns, d.red, d.scal,
-                          d.nb_ns);
+                             parts);
 }
 
 __global__ void __launch_bounds__(kVecThreads) cg_step_x_batch(const SrDesc* __restrict__ D,
@@ -1091,6 +1099,14 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
   const int64_t sg_blocks = (ns + kSgBS - 1) / kSgBS;
   aa.v = sc + L.v;
   aa.skip = scal + SC_DONE;
+  // The tensor-core forward also writes the partial sums of the centring mean
+  // (one per CTA), when they fit the partials buffer: no separate partial pass.
+  const int ctr_parts = tc ? fwd_centring_parts(ns, L.mt1) : 0;
+  if (ctr_parts) {
+    fa.mean_part = red + 2 * kVecBlocks;
+    fa.mean_stride = kVecBlocks;
+    fa.weights = weights;
+  }
   // from the second CG iteration on, cg_step_p writes the planes of p itself
   PlaneOut po;
   if (tc) {
@@ -1112,9 +1128,10 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
       forward_fp32_kernel<CPLX><<<(unsigned)sg_blocks, kSgThreads, 0, st>>>(
           sigma, ns, n, m, sc + L.xf, T, sc + L.y, scal);
     }
-    center_partial_kernel<CPLX><<<nbs, kVecThreads, 0, st>>>(sc + L.y, weights, ns, red, scal);
+    if (ctr_parts == 0)
+      center_partial_kernel<CPLX><<<nbs, kVecThreads, 0, st>>>(sc + L.y, weights, ns, red, scal);
     center_apply_kernel<CPLX><<<nbs, kVecThreads, 0, st>>>(sc + L.y, sc + L.v, weights, ns, red,
-                                                           scal, nbs);
+                                                           scal, ctr_parts ? ctr_parts : nbs);
     if (tc) {
       if (nk_status e = launch_adj_tc(aa, sc + L.sigt, st)) return e;
     } else {
@@ -1223,6 +1240,7 @@ nk_status sr_batch_describe(const nk_sr_batch_item* items, int n_inst, int prec,
       return NK_ERR_CUDA;
     if (!tc_make_map(&d.sig_map, sc + L.sigr, it.ns, L.na64, L.na64, 128)) return NK_ERR_CUDA;
     d.fwd_nseg = fwd_tc_nseg(it.ns, L.mt1, 0, true);
+    d.ctr_parts = fwd_centring_parts(it.ns, L.mt1);
     d.splits = batch_item_splits(items, n_inst, order[z], prec);
     d.nb_pa = sr_vec_blocks(L.pa);
     d.nb_ns = sr_vec_blocks(it.ns);
@@ -1278,10 +1296,8 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
                                 const SrDesc* D, double eps, double lr, int n_cg, double rtol,
                                 int prec, cudaStream_t st) {
   const SrDesc* Dg = D + z0;
-  FwdBatch fb;
-  AdjBatch ab;
-  memset(&fb, 0, sizeof(fb));
-  memset(&ab, 0, sizeof(ab));
+  FwdBatch fb{};
+  AdjBatch ab{};
   int max_fwd = 1, max_adj = 1, max_sp = 1, max_na64 = 64;
   int64_t max_ns8 = 8, max_xp = 1, max_wp = 1, max_work = 1, max_minb = 1, max_rows = 1;
   for (int z = 0; z < G; ++z) {
@@ -1309,6 +1325,11 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
     fa.skip = scal + SC_DONE;
     fa.err = reinterpret_cast<int*>(scal + SC_ERR);
     fa.nseg = fwd_tc_nseg(it.ns, L.mt1, 0, true);
+    if (fwd_centring_parts(it.ns, L.mt1)) {
+      fa.mean_part = (double*)(sc + L.red) + 2 * kVecBlocks;
+      fa.mean_stride = kVecBlocks;
+      fa.weights = it.weights;
+    }
     fb.map[z] = &Dg[z].fwd_map;
     fb.smap[z] = &Dg[z].sig_map;
     fb.tiles[z] = (int)((it.ns + 127) / 128);
@@ -1347,6 +1368,8 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
     max_nbs = std::max(max_nbs, sr_vec_blocks(it.ns));
   }
   const dim3 vg(max_nbp, G), vs(max_nbs, G), one(1, G);
+  bool all_fused = true;  // every forward of the group writes its centring partials
+  for (int z = 0; z < G; ++z) all_fused = all_fused && fb.a[z].mean_part != nullptr;
   stats_mean_batch<<<vs, kVecThreads, 0, st>>>(Dg);
   stats_dev_batch<<<vs, kVecThreads, 0, st>>>(Dg);
   stats_finish_batch<<<one, 32, 0, st>>>(Dg);
@@ -1366,7 +1389,7 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
       if (nk_status e = launch_bplanes_p_batch(Dg, G, max_xp, st)) return e;
     }
     if (nk_status e = launch_fwd_tc_batch(fb, G, max_fwd, max_na64, st)) return e;
-    center_partial_batch<<<vs, kVecThreads, 0, st>>>(Dg);
+    if (!all_fused) center_partial_batch<<<vs, kVecThreads, 0, st>>>(Dg);
     center_apply_batch<<<vs, kVecThreads, 0, st>>>(Dg);
     if (nk_status e = launch_adj_tc_batch(ab, G, max_adj, max_sp, max_na64, st)) return e;
     reduce_parts_batch<<<vg, kVecThreads, 0, st>>>(Dg, 1, eps);

@@ -562,6 +562,32 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
         }
       }
     }
+    if (A.mode == 0 && A.mean_part) {
+      // this CTA's partial of the centring mean sum_s w_s y_s, in a fixed order:
+      // within each warp, then the four warps in lane-quarter order
+      __shared__ double mp[4][2];
+      double wr = 0.0, wi = 0.0;
+      if (live) {
+        const double wgt = A.weights ? A.weights[s] : 1.0 / (double)A.ns;
+        wr = wgt * sr;
+        wi = wgt * si;
+      }
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        wr += __shfl_xor_sync(0xffffffffu, wr, off);
+        wi += __shfl_xor_sync(0xffffffffu, wi, off);
+      }
+      if (lane == 0) {
+        mp[q][0] = wr;
+        mp[q][1] = wi;
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
+      if (q == 0 && lane == 0) {
+        const int64_t pidx = (int64_t)seg * ((A.ns + 127) / 128) + bx;
+        A.mean_part[pidx] = ((mp[0][0] + mp[1][0]) + mp[2][0]) + mp[3][0];
+        A.mean_part[A.mean_stride + pidx] = ((mp[0][1] + mp[1][1]) + mp[2][1]) + mp[3][1];
+      }
+    }
   }
   if (bad) {
     if (A.err) atomicOr(A.err, 1);
@@ -811,7 +837,6 @@ __device__ __forceinline__ void adj_tc_body(const CUtensorMap* tsp, const AdjTcA
                 (void)vi;
               }
             }
-            uint32_t a0, b0, a1, b1;
             split_bf16x2(zr[0], zr[1], hr[e2], lr[e2]);
             if constexpr (CPLX) split_bf16x2(zi[0], zi[1], hi_[e2], li[e2]);
           }

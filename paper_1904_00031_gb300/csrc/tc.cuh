@@ -56,6 +56,12 @@ struct FwdTcArgs {
   int nseg = 1;           // set by launch_fwd_tc: 1, or 2 halves of the hidden tiles
   const void* sig_rows = nullptr;  // mode 0: sigma' as BF16 [ns][na64] (launch_sigma_rows);
                                    // the sample tiles are then TMA-loaded, else built
+  // mode 0, optional: per-CTA partial sums of w_s y_s (the centring mean of the
+  // SR forward) at mean_part[seg * tiles + tile] (Re) and mean_part[mean_stride +
+  // same] (Im); w_s = weights[s], or 1 / ns when weights is NULL
+  double* mean_part = nullptr;
+  int64_t mean_stride = 0;
+  const double* weights = nullptr;
 };
 nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st);
 // Hidden-tile halves (1 or 2) launch_fwd_tc uses for ns samples and mt hidden
@@ -92,6 +98,8 @@ struct alignas(128) SrDesc {
   int nb_pa, nb_ns;       // blocks of the CG vector kernels over parameters / samples
   int cplx;               // 1: complex RBM
   int fwd_nseg;           // hidden-tile halves of the forward (fwd_tc_nseg); 2: y zeroed first
+  int ctr_parts;          // > 0: the forward writes that many centring partials (no
+                          // separate partial pass); 0: center_partial computes them
   int n, m, n_chains, na64, mt1, mp, wmt, wna64;  // wmt, wna64: B planes of W | b
   int64_t ns, pa, corner, ns8;
   const int8_t* sigma;

@@ -15,6 +15,21 @@ from . import nk
 from . import workloads as W
 
 
+def centring_fused(ns: int, m: int, is_complex: bool) -> bool:
+    """Whether the tensor-core SR forward writes the centring partials itself:
+    one per CTA (sample tiles x hidden-tile halves) must fit 1024 slots.  The
+    halves rule is the library's: two when the hidden tiles are at least two
+    and twice the CTAs fill their last wave of 152 better."""
+    tiles = (ns + 127) // 128
+    mt = (m + 1 + (63 if is_complex else 127)) // (64 if is_complex else 128)
+
+    def eff(b):
+        return b / (((b + 151) // 152) * 152)
+
+    nseg = 2 if mt >= 2 and eff(2 * tiles) > eff(tiles) else 1
+    return tiles * nseg <= 1024
+
+
 class VmcSr:
     def __init__(self, w: W.Workload, params: W.RbmParams, sigma0=None,
                  prec: int = nk.NK_PREC_FP32, device="cuda", graph: bool = False,
@@ -110,8 +125,10 @@ class VmcSr:
         CG iterations, the update and the refreshed planes (2)."""
         if self.prec == nk.NK_PREC_BF16X2:
             # sigma'^T, sigma' rows, adjoint, reduction, CG start (2); per CG
-            # iteration 7 (the first also builds the planes of p)
-            return 3 + 6 + 7 * self.w.n_cg + 1 + 3
+            # iteration 7, or 6 when the forward writes the centring partials
+            # (the first iteration also builds the planes of p)
+            per = 6 if centring_fused(self.ns, self.w.m, self.w.is_complex) else 7
+            return 3 + 6 + per * self.w.n_cg + 1 + 3
         # adjoint, reduction, CG start (2); 8 per CG iteration
         return 3 + 4 + 8 * self.w.n_cg + 3
 
