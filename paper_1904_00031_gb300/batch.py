@@ -13,7 +13,7 @@ import torch
 
 from . import nk
 from . import workloads as W
-from .vmc import VmcSr, centring_fused
+from .vmc import VmcSr, adj_centres, centring_fused
 
 
 class BatchedVmc:
@@ -87,8 +87,10 @@ class BatchedVmc:
         n = sum(v.launches_per_step() - v.sr_launches() for v in self.items)
         groups = (len(self.items) + 63) // 64   # up to 64 instances per launch
         # per group: statistics (3), flags, sigma' planes (2), force, CG start (2),
-        # 7 per CG iteration (6 when every forward writes its centring partials)
+        # 7 per CG iteration (6 when every forward writes its centring partials, 5
+        # when every adjoint also centres its input)
         # plus the first iteration's planes, update, prepare (2)
         fused = all(centring_fused(v.ns, v.w.m, v.w.is_complex) for v in self.items)
-        per = 6 if fused else 7
+        adj = fused and all(adj_centres(v.w.m, v.w.is_complex) for v in self.items)
+        per = 5 if adj else (6 if fused else 7)
         return n + groups * (3 + 1 + 2 + 2 + 2 + per * self.sr_args[2] + 1 + 3)

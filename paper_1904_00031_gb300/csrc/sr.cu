@@ -43,6 +43,13 @@ static int fwd_centring_parts(int64_t ns, int mt) {
   const int64_t parts = ((ns + 127) / 128) * fwd_tc_nseg(ns, mt, 0, true);
   return parts <= kVecBlocks ? (int)parts : 0;
 }
+
+// Whether the SR adjoint centres the forward's output itself (v = w (y - mean)
+// formed while loading): every parameter tile's CTAs repeat that FP64 work, so
+// only for at most four tiles, where the launch it saves costs more.
+static bool adj_centres(int m, int cplx) {
+  return (m + 1 + tc_hidden_per_tile(cplx) - 1) / tc_hidden_per_tile(cplx) <= 4;
+}
 // Elements per thread whose loads are issued together in the vector kernels
 // (a thread's elements are still visited, and summed, in grid-stride order).
 constexpr int kVecUnroll = 4;
@@ -1107,6 +1114,15 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
     fa.mean_stride = kVecBlocks;
     fa.weights = weights;
   }
+  // and for small hidden layers the adjoint centres y itself while loading it
+  const bool adj_ctr = ctr_parts && adj_centres(m, CPLX);
+  if (adj_ctr) {
+    aa.y = sc + L.y;
+    aa.mean_part = red + 2 * kVecBlocks;
+    aa.mean_stride = kVecBlocks;
+    aa.mean_parts = ctr_parts;
+    aa.weights = weights;
+  }
   // from the second CG iteration on, cg_step_p writes the planes of p itself
   PlaneOut po;
   if (tc) {
@@ -1130,8 +1146,9 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
     }
     if (ctr_parts == 0)
       center_partial_kernel<CPLX><<<nbs, kVecThreads, 0, st>>>(sc + L.y, weights, ns, red, scal);
-    center_apply_kernel<CPLX><<<nbs, kVecThreads, 0, st>>>(sc + L.y, sc + L.v, weights, ns, red,
-                                                           scal, ctr_parts ? ctr_parts : nbs);
+    if (!adj_ctr)
+      center_apply_kernel<CPLX><<<nbs, kVecThreads, 0, st>>>(sc + L.y, sc + L.v, weights, ns,
+                                                             red, scal, ctr_parts ? ctr_parts : nbs);
     if (tc) {
       if (nk_status e = launch_adj_tc(aa, sc + L.sigt, st)) return e;
     } else {
@@ -1382,7 +1399,25 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
   cg_init_batch<<<vg, kVecThreads, 0, st>>>(Dg);
   cg_init_scalars_batch<<<one, 32, 0, st>>>(Dg, rtol);
   if (nk_status e = check_launch("nk_sr_step_batch(force)")) return e;
-  for (int z = 0; z < G; ++z) ab.a[z].skip = fb.a[z].skip;
+  // the adjoints centre the forwards' outputs themselves when every problem of
+  // the group qualifies (otherwise the centring launch runs for all of them)
+  bool all_adj_ctr = all_fused;
+  for (int z = 0; z < G; ++z) {
+    const nk_rbm* r = items[order[z0 + z]].rbm;
+    all_adj_ctr = all_adj_ctr && adj_centres(r->m, r->is_complex ? 1 : 0);
+  }
+  for (int z = 0; z < G; ++z) {
+    ab.a[z].skip = fb.a[z].skip;
+    if (all_adj_ctr) {
+      const nk_sr_batch_item& it = items[order[z0 + z]];
+      SrLayout L(it.rbm->n, it.rbm->m, it.rbm->is_complex ? 1 : 0, it.ns);
+      ab.a[z].y = (char*)it.scratch + L.y;
+      ab.a[z].mean_part = fb.a[z].mean_part;
+      ab.a[z].mean_stride = kVecBlocks;
+      ab.a[z].mean_parts = fwd_centring_parts(it.ns, L.mt1);
+      ab.a[z].weights = it.weights;
+    }
+  }
   for (int it = 0; it < n_cg; ++it) {
     // from the second CG iteration on, cg_step_p_batch writes the planes of p itself
     if (it == 0) {
@@ -1390,7 +1425,7 @@ static nk_status sr_batch_group(const nk_sr_batch_item* items, int n_inst,
     }
     if (nk_status e = launch_fwd_tc_batch(fb, G, max_fwd, max_na64, st)) return e;
     if (!all_fused) center_partial_batch<<<vs, kVecThreads, 0, st>>>(Dg);
-    center_apply_batch<<<vs, kVecThreads, 0, st>>>(Dg);
+    if (!all_adj_ctr) center_apply_batch<<<vs, kVecThreads, 0, st>>>(Dg);
     if (nk_status e = launch_adj_tc_batch(ab, G, max_adj, max_sp, max_na64, st)) return e;
     reduce_parts_batch<<<vg, kVecThreads, 0, st>>>(Dg, 1, eps);
     cg_step_x_batch<<<vg, kVecThreads, 0, st>>>(Dg, it);

@@ -746,6 +746,8 @@ __device__ __forceinline__ void adj_tc_body(const CUtensorMap* tsp, const AdjTcA
     // j0 + 4 jq .. + 3.  The next stage's T values are loaded into registers
     // before the thread waits for its buffer; v_s reaches the warp by shuffles.
     const int pt = tid - 64;
+    __shared__ double cmean[2];              // the centring mean (A.y mode)
+    const double invn = 1.0 / (double)A.ns;
     constexpr int JPT = CPLX ? 2 : 4;        // parameter rows per thread
     const int jb = (pt & 31) * JPT;          // first local row
     const int qs = pt >> 5;                  // sample quarter of the stage
@@ -789,7 +791,22 @@ __device__ __forceinline__ void adj_tc_body(const CUtensorMap* tsp, const AdjTcA
         }
       }
       const int64_t smp = kb + (lane % SPT);
-      if constexpr (CPLX) {
+      if (A.y) {
+        // centred on the fly: v = w (y - mean)
+        double vr = 0.0, vi = 0.0;
+        if (smp < se) {
+          const double wgt = A.weights ? A.weights[smp] : invn;
+          if constexpr (CPLX) {
+            const double2 yv = reinterpret_cast<const double2*>(A.y)[smp];
+            vr = wgt * (yv.x - cmean[0]);
+            vi = wgt * (yv.y - cmean[1]);
+          } else {
+            vr = wgt * (reinterpret_cast<const double*>(A.y)[smp] - cmean[0]);
+          }
+        }
+        vq0 = (float)vr;
+        vq1 = (float)vi;
+      } else if constexpr (CPLX) {
         const double2 vd = smp < se ? reinterpret_cast<const double2*>(A.v)[smp]
                                     : make_double2(0.0, 0.0);
         vq0 = (float)vd.x;
@@ -798,6 +815,27 @@ __device__ __forceinline__ void adj_tc_body(const CUtensorMap* tsp, const AdjTcA
         vq0 = smp < se ? (float)reinterpret_cast<const double*>(A.v)[smp] : 0.f;
       }
     };
+    if (A.y) {
+      // the centring mean, summed by the first producer warp in the centring
+      // kernel's order (lane-strided partial sums, then a butterfly)
+      if (pt < 32) {
+        double r = 0.0, i = 0.0;
+        for (int u = pt; u < A.mean_parts; u += 32) {
+          r += A.mean_part[u];
+          i += A.mean_part[A.mean_stride + u];
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+          r += __shfl_xor_sync(0xffffffffu, r, off);
+          i += __shfl_xor_sync(0xffffffffu, i, off);
+        }
+        if (pt == 0) {
+          cmean[0] = r;
+          cmean[1] = i;
+        }
+      }
+      asm volatile("bar.sync 2, %0;" ::"r"(32 * kAdjProducerWarps) : "memory");  // producers
+    }
     if (nit > 0) load_stage(0);
     for (int it = 0; it < nit && !bad; ++it) {
       const int st = it & 1, u = it >> 1;

@@ -79,6 +79,15 @@ struct AdjTcArgs {
   void* part;
   const double* skip;
   int* err;
+  // optional, instead of v: v_s = w_s (y_s - mean) formed while loading, with
+  // mean = the fixed-order sum of mean_parts partials at mean_part (Re) and
+  // mean_part + mean_stride (Im), w_s = weights[s] or 1 / ns (the centring of
+  // the SR forward's output, same formula and order as the centring kernel)
+  const void* y = nullptr;
+  const double* mean_part = nullptr;
+  int64_t mean_stride = 0;
+  int mean_parts = 0;
+  const double* weights = nullptr;
 };
 nk_status launch_adj_tc(const AdjTcArgs& A, const void* sigma_t, cudaStream_t st);
 

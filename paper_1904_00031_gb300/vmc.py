@@ -30,6 +30,13 @@ def centring_fused(ns: int, m: int, is_complex: bool) -> bool:
     return tiles * nseg <= 1024
 
 
+def adj_centres(m: int, is_complex: bool) -> bool:
+    """Whether the SR adjoint centres the forward's output itself (at most four
+    parameter tiles of 64 complex or 128 real hidden units)."""
+    per = 64 if is_complex else 128
+    return (m + 1 + per - 1) // per <= 4
+
+
 class VmcSr:
     def __init__(self, w: W.Workload, params: W.RbmParams, sigma0=None,
                  prec: int = nk.NK_PREC_FP32, device="cuda", graph: bool = False,
@@ -125,9 +132,11 @@ class VmcSr:
         CG iterations, the update and the refreshed planes (2)."""
         if self.prec == nk.NK_PREC_BF16X2:
             # sigma'^T, sigma' rows, adjoint, reduction, CG start (2); per CG
-            # iteration 7, or 6 when the forward writes the centring partials
-            # (the first iteration also builds the planes of p)
-            per = 6 if centring_fused(self.ns, self.w.m, self.w.is_complex) else 7
+            # iteration 7, or 5 when the forward writes the centring partials and
+            # the adjoint centres its input itself (the first iteration also
+            # builds the planes of p)
+            fused = centring_fused(self.ns, self.w.m, self.w.is_complex)
+            per = (5 if adj_centres(self.w.m, self.w.is_complex) else 6) if fused else 7
             return 3 + 6 + per * self.w.n_cg + 1 + 3
         # adjoint, reduction, CG start (2); 8 per CG iteration
         return 3 + 4 + 8 * self.w.n_cg + 3
