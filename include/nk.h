@@ -40,7 +40,7 @@ typedef int32_t nk_status;
 #define NK_ERR_NOT_CONVERGED 4 /* (info flag) CG stopped at n_cg above cg_rtol */
 #define NK_ERR_NONFINITE 5     /* (info flag) NaN/Inf met in E_loc or CG       */
 #define NK_ERR_TIMEOUT 6       /* a bounded device-side wait gave up           */
-#define NK_ERR_UNSUPPORTED 7   /* valid request this build does not implement  */
+#define NK_ERR_UNSUPPORTED 7   /* valid request this library does not implement */
 
 /* Arithmetic of the dense contractions (theta GEMM, SR matvec, backward). */
 #define NK_PREC_FP32 0   /* FP32 FMA on the CUDA cores ("plain FP32 path")          */
@@ -54,7 +54,7 @@ typedef int32_t nk_status;
                                 O_W = T (x) sigma are implied                       */
 #define NK_LAYOUT_DENSE 1    /* O as F32 [ns][P]                                    */
 
-/* Size limits of this build. */
+/* Size limits of this library. */
 #define NK_MAX_N 4096      /* sites                                               */
 #define NK_MAX_M 8192      /* hidden units (kernels hold tanh(theta) in registers) */
 #define NK_MAX_GROUP 32    /* chains sharing one proposal stream (one CTA)         */
