@@ -31,8 +31,12 @@ struct ElocArgs {
   const void* tab;     // [n][mp] T2
   double* eloc;        // c128 [ns]
   void* t_out;         // [ns][m] F or null
-  int nseg;            // 1, or 2: blockIdx.y takes half of the move tiles and the
-                       // two halves are added into eloc (zeroed first) atomically
+  int nseg;            // 1, or 2: each configuration tile is split over two CTAs
+                       // taking half of the move tiles each, whose sums are added
+                       // into eloc (zeroed first) atomically
+  int seg_fast;        // 1: the grid is (nseg, tiles), so the two halves of a
+                       // configuration tile run back to back and share its theta /
+                       // T rows in L2; 0: (tiles, nseg)
 };
 
 __device__ __forceinline__ int idx_of(int8_t s) { return s > 0 ? 0 : 1; }
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   uint64_t* mbar = reinterpret_cast<uint64_t*>(eacc + 4 * 256);              // [2]
 
   const int tid = threadIdx.x, ts = tid >> 4, tm = tid & 15;
-  const int64_t s0 = (int64_t)blockIdx.x * kEBS;
+  const int64_t s0 = (int64_t)(A.seg_fast ? blockIdx.y : blockIdx.x) * kEBS;
   const int n = A.n, m = A.m, mp = A.mp;
   const OpDevHeader* H = reinterpret_cast<const OpDevHeader*>(A.op);
   const OpDSite* ds = reinterpret_cast<const OpDSite*>(A.op + H->off_dsite);
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   const int nm = A.n_moves;
   const bool quad = (H->flags & kOpQuadMoves) != 0;  // site-quad move layout
   const int ntile = (nm + kEBM - 1) / kEBM, nchunk = mp / kEBK;
-  const int seg = blockIdx.y;
+  const int seg = A.seg_fast ? blockIdx.x : blockIdx.y;
   const int tile_begin = ntile * seg / A.nseg, tile_end = ntile * (seg + 1) / A.nseg;
   const int it_begin = tile_begin * nchunk, it_end = tile_end * nchunk;
   const uint32_t tile_bytes = kEBK * kEBM * sizeof(T2);
@@ -563,7 +567,9 @@ nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
   if (A.nseg == 2 &&
       cudaMemsetAsync(eloc, 0, (size_t)ns * 2 * sizeof(double), st) != cudaSuccess)
     return fail(NK_ERR_CUDA, "nk_local_energy: cudaMemsetAsync failed");
-  const dim3 grid((unsigned)blocks, (unsigned)A.nseg);
+  A.seg_fast = A.nseg == 2 && blocks <= 65535 ? 1 : 0;
+  const dim3 grid = A.seg_fast ? dim3((unsigned)A.nseg, (unsigned)blocks)
+                               : dim3((unsigned)blocks, (unsigned)A.nseg);
   if (cplx) {
     if (cudaFuncSetAttribute(local_energy_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
