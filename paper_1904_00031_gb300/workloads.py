@@ -53,6 +53,76 @@ def square_bonds(L: int) -> np.ndarray:
     return np.asarray(out, dtype=np.int32)
 
 
+def chain_translations(n: int) -> np.ndarray:
+    """Translation group of a periodic chain as a permutation table [n][n]:
+    row g maps site i to (i + g) mod n (the lattice symmetries an
+    ``RbmSpinSymm`` is built on, Sec. 2.2.2)."""
+    i = np.arange(n, dtype=np.int64)
+    return np.stack([(i + g) % n for g in range(n)]).astype(np.int32)
+
+
+def square_translations(L: int) -> np.ndarray:
+    """Translation group of an L x L periodic square lattice, [L*L][L*L]: row
+    g = dx + L*dy maps site x + L*y to (x+dx mod L) + L*((y+dy) mod L)."""
+    x = np.arange(L * L) % L
+    y = np.arange(L * L) // L
+    rows = [((x + dx) % L) + L * ((y + dy) % L) for dy in range(L) for dx in range(L)]
+    return np.stack(rows).astype(np.int32)
+
+
+@dataclass
+class RbmSymmParams:
+    """FP64 parameters of a symmetric RBM with ``alpha`` feature families:
+    ``a`` [1] (one visible bias), ``b`` [alpha], ``w`` [alpha, N]."""
+
+    a: np.ndarray
+    b: np.ndarray
+    w: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.w.shape[1])
+
+    @property
+    def alpha(self) -> int:
+        return int(self.b.shape[0])
+
+    @property
+    def is_complex(self) -> bool:
+        return np.iscomplexobj(self.w)
+
+    @property
+    def n_params(self) -> int:
+        return 1 + self.alpha + self.alpha * self.n
+
+    def flat(self) -> np.ndarray:
+        """Parameter vector in the order (a, b, W row-major)."""
+        return np.concatenate([self.a, self.b, self.w.reshape(-1)])
+
+    @staticmethod
+    def from_flat(x: np.ndarray, n: int, alpha: int) -> "RbmSymmParams":
+        return RbmSymmParams(a=x[:1].copy(), b=x[1:1 + alpha].copy(),
+                             w=x[1 + alpha:].reshape(alpha, n).copy())
+
+    def copy(self) -> "RbmSymmParams":
+        return RbmSymmParams(self.a.copy(), self.b.copy(), self.w.copy())
+
+
+def init_symm_params(n: int, alpha: int, is_complex: bool, sigma: float = 0.01,
+                     seed: int = 1234) -> RbmSymmParams:
+    """Gaussian initialisation N(0, sigma^2) of every real component, as
+    ``init_params``."""
+    rng = np.random.default_rng(seed)
+
+    def draw(shape):
+        re = rng.normal(0.0, sigma, size=shape)
+        if not is_complex:
+            return re
+        return re + 1j * rng.normal(0.0, sigma, size=shape)
+
+    return RbmSymmParams(a=draw(1), b=draw(alpha), w=draw((alpha, n)))
+
+
 def square_diag_bonds(L: int) -> np.ndarray:
     """Next-nearest-neighbour (J2, colour 1) bonds of an L x L periodic lattice.
 
