@@ -411,6 +411,63 @@ nk_status nk_rbm_logpsi_backward(const nk_rbm* rbm, const int8_t* sigma, int64_t
                                  const double* g, double* grad_out, int32_t prec, void* scratch,
                                  size_t scratch_bytes, void* stream);
 
+/* --------------------------------------------------- symmetric RBM (RbmSpinSymm) */
+/* The RBM variant of Sec. 2.2.2 that carries lattice symmetries.  A group of
+ * n_perm site permutations perm[g][i] (the image of site i under g) ties the
+ * parameters: alpha feature families, one hidden unit (f, g) = f n_perm + g
+ * per family and group element, with
+ *   W[(f, g)][i] = Wt[f][perm[g][i]],  b[(f, g)] = bt[f],  a_i = at,
+ * so psi(sigma o h) = psi(sigma) for every h of a group.  Amplitudes, sampling
+ * and local energies run on the untied RBM this stands for (m = alpha n_perm,
+ * written by nk_symm_expand); SR runs in the tied space (S_t = P^T S P,
+ * F_t = P^T F, P the copy of a tied parameter into the untied ones it stands
+ * for), with the untied contractions of nk_sr_step.  Tied parameter vectors
+ * are ordered (at, bt, Wt row-major), length 1 + alpha + alpha n. */
+typedef struct nk_rbm_symm {
+  int32_t n;          /* sites                                                     */
+  int32_t alpha;      /* feature families, >= 1                                    */
+  int32_t n_perm;     /* permutations in the table, >= 1; alpha n_perm <= NK_MAX_M */
+  int32_t is_complex;
+  double* a;          /* F64 [1]          (device)                                 */
+  double* b;          /* F64 [alpha]      (device)                                 */
+  double* w;          /* F64 [alpha][n]   (device, row-major)                      */
+  const void* tables; /* nk_symm_tables_bytes() bytes filled by nk_symm_upload     */
+  size_t tables_bytes;
+} nk_rbm_symm;
+
+/* Bytes of the tie tables of a symmetric RBM (0 for sizes out of range). */
+size_t nk_symm_tables_bytes(int32_t n, int32_t alpha, int32_t n_perm);
+
+/* Builds the tie tables from the HOST permutation table perm [n_perm][n]
+ * (each row a permutation of 0..n-1, else NK_ERR_INVALID_ARG) and copies them
+ * into `dev` (device, 256-B aligned, nk_symm_tables_bytes() bytes).  Like
+ * nk_operator_upload it synchronises `stream` before returning, so the host
+ * table may be freed afterwards. */
+nk_status nk_symm_upload(const int32_t* perm, int32_t n, int32_t alpha, int32_t n_perm,
+                         void* dev, size_t bytes, void* stream);
+
+/* Writes the untied parameters (a, b, W) of rbm from the tied ones and
+ * prepares rbm's planes (nk_rbm_prepare).  rbm->n == s->n,
+ * rbm->m == s->alpha * s->n_perm and the same is_complex, else NK_ERR_SHAPE. */
+nk_status nk_symm_expand(const nk_rbm_symm* s, nk_rbm* rbm, void* stream);
+
+/* Scratch bytes of nk_sr_step_symm. */
+size_t nk_sr_symm_scratch_bytes(int32_t n, int32_t alpha, int32_t n_perm,
+                                int32_t is_complex, int64_t ns);
+
+/* One SR step of a symmetric RBM: the system (S_t + diag_shift I) delta = F_t
+ * in the tied space by CG (every product S_t x expands x into the untied
+ * layout, runs the untied O and O^H contractions of nk_sr_step at `prec`, and
+ * folds the result back with fixed-order sums), then
+ * theta_t <- theta_t - lr delta and nk_symm_expand into rbm.  sigma, t, eloc,
+ * weights, info_out as for nk_sr_step, with t = tanh(theta) of the expanded
+ * RBM; rbm must be s's expansion (nk_symm_expand).  Not available in batches. */
+nk_status nk_sr_step_symm(nk_rbm_symm* s, nk_rbm* rbm, const int8_t* sigma, const void* t,
+                          const double* eloc, const double* weights, int64_t ns,
+                          int32_t n_chains, double diag_shift, double lr, int32_t n_cg,
+                          double cg_rtol, int32_t prec, void* scratch, size_t scratch_bytes,
+                          double* info_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

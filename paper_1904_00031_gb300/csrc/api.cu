@@ -511,6 +511,94 @@ nk_status nk_sr_tune(nk_rbm* rbm, const int8_t* sigma, const void* t, int64_t ns
   return run_sr_tune(rbm, sigma, t, ns, prec, scratch, scratch_bytes, (cudaStream_t)stream);
 }
 
+static bool symm_sizes_ok(int32_t n, int32_t alpha, int32_t n_perm) {
+  return n >= 1 && n <= NK_MAX_N && alpha >= 1 && n_perm >= 1 &&
+         (int64_t)alpha * n_perm <= NK_MAX_M;
+}
+
+static nk_status check_symm(const nk_rbm_symm* s, const nk_rbm* r, const char* who) {
+  if (!s) return fail(NK_ERR_INVALID_ARG, "%s: symmetric RBM is NULL", who);
+  if (!symm_sizes_ok(s->n, s->alpha, s->n_perm))
+    return fail(NK_ERR_SHAPE, "%s: n = %d, alpha = %d, n_perm = %d out of range", who, s->n,
+                s->alpha, s->n_perm);
+  if (s->is_complex != 0 && s->is_complex != 1)
+    return fail(NK_ERR_INVALID_ARG, "%s: is_complex must be 0 or 1", who);
+  if (!s->a || !s->b || !s->w || !s->tables)
+    return fail(NK_ERR_INVALID_ARG, "%s: NULL tied parameter or table pointer", who);
+  if (((uintptr_t)s->tables) & 255)
+    return fail(NK_ERR_INVALID_ARG, "%s: tables not 256-byte aligned", who);
+  const size_t need = SymmTables(s->n, s->alpha, s->n_perm).total;
+  if (s->tables_bytes < need)
+    return fail(NK_ERR_SHAPE, "%s: tables of %zu B, need %zu B", who, s->tables_bytes, need);
+  if (nk_status e = check_rbm(r, who)) return e;
+  if (r->n != s->n || (int64_t)r->m != (int64_t)s->alpha * s->n_perm ||
+      r->is_complex != s->is_complex)
+    return fail(NK_ERR_SHAPE, "%s: rbm (n = %d, m = %d) is not the expansion of the symmetric "
+                "RBM (n = %d, alpha n_perm = %d)", who, r->n, r->m, s->n, s->alpha * s->n_perm);
+  return NK_OK;
+}
+
+size_t nk_symm_tables_bytes(int32_t n, int32_t alpha, int32_t n_perm) {
+  if (!symm_sizes_ok(n, alpha, n_perm)) return 0;
+  return SymmTables(n, alpha, n_perm).total;
+}
+
+nk_status nk_symm_upload(const int32_t* perm, int32_t n, int32_t alpha, int32_t n_perm,
+                         void* dev, size_t bytes, void* stream) {
+  if (!perm || !dev) return fail(NK_ERR_INVALID_ARG, "nk_symm_upload: NULL pointer");
+  if (!symm_sizes_ok(n, alpha, n_perm))
+    return fail(NK_ERR_SHAPE, "nk_symm_upload: n = %d, alpha = %d, n_perm = %d out of range", n,
+                alpha, n_perm);
+  if (((uintptr_t)dev) & 255)
+    return fail(NK_ERR_INVALID_ARG, "nk_symm_upload: dev not 256-byte aligned");
+  const size_t need = SymmTables(n, alpha, n_perm).total;
+  if (bytes < need)
+    return fail(NK_ERR_SHAPE, "nk_symm_upload: %zu B given, %zu B needed", bytes, need);
+  std::vector<int32_t> buf;
+  if (nk_status e = symm_build_tables(perm, n, alpha, n_perm, &buf)) return e;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(dev, buf.data(), need, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(NK_ERR_CUDA, "nk_symm_upload: %s", cudaGetErrorString(cudaGetLastError()));
+  return NK_OK;
+}
+
+nk_status nk_symm_expand(const nk_rbm_symm* s, nk_rbm* rbm, void* stream) {
+  if (nk_status e = check_symm(s, rbm, "nk_symm_expand")) return e;
+  return run_symm_expand(s, rbm, (cudaStream_t)stream);
+}
+
+size_t nk_sr_symm_scratch_bytes(int32_t n, int32_t alpha, int32_t n_perm, int32_t is_complex,
+                                int64_t ns) {
+  if (!symm_sizes_ok(n, alpha, n_perm) || ns < 0) return 0;
+  return sr_symm_scratch_bytes(n, alpha, n_perm, is_complex ? 1 : 0, ns);
+}
+
+nk_status nk_sr_step_symm(nk_rbm_symm* s, nk_rbm* rbm, const int8_t* sigma, const void* t,
+                          const double* eloc, const double* weights, int64_t ns,
+                          int32_t n_chains, double diag_shift, double lr, int32_t n_cg,
+                          double cg_rtol, int32_t prec, void* scratch, size_t scratch_bytes,
+                          double* info_out, void* stream) {
+  const char* who = "nk_sr_step_symm";
+  if (nk_status e = check_symm(s, rbm, who)) return e;
+  if (ns < 1) return fail(NK_ERR_INVALID_ARG, "%s: ns < 1", who);
+  if (!sigma || !t || !eloc || !scratch || !info_out)
+    return fail(NK_ERR_INVALID_ARG, "%s: NULL pointer", who);
+  if (n_cg < 0 || !(diag_shift >= 0.0) || !(cg_rtol >= 0.0))
+    return fail(NK_ERR_INVALID_ARG, "%s: negative n_cg, diag_shift or cg_rtol", who);
+  if (n_chains < 0 || (n_chains > 0 && ns % n_chains))
+    return fail(NK_ERR_SHAPE, "%s: ns = %lld not a multiple of n_chains = %d", who,
+                (long long)ns, n_chains);
+  if (((uintptr_t)scratch) & 255)
+    return fail(NK_ERR_INVALID_ARG, "%s: scratch not 256-byte aligned", who);
+  if (prec != NK_PREC_FP32 && prec != NK_PREC_BF16X2)
+    return fail(NK_ERR_INVALID_ARG, "%s: unknown precision %d", who, prec);
+  if (prec == NK_PREC_BF16X2 && !tc_supported_shape(rbm->n, rbm->m))
+    return fail(NK_ERR_UNSUPPORTED, "%s: the tensor-core path supports n + 1 <= 448", who);
+  return run_sr_step_symm(s, rbm, sigma, t, eloc, weights, ns, n_chains, diag_shift, lr, n_cg,
+                          cg_rtol, prec, scratch, scratch_bytes, info_out, (cudaStream_t)stream);
+}
+
 size_t nk_sr_batch_desc_bytes(int32_t n_inst) { return sr_batch_desc_bytes(n_inst); }
 
 nk_status nk_sr_batch_describe(const nk_sr_batch_item* items, int32_t n_inst, int32_t prec,

@@ -1,6 +1,8 @@
 // Internal declarations shared by the nk library's translation units.
 #pragma once
 
+#include <vector>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -72,6 +74,24 @@ nk_status run_sr_step(nk_rbm* r, const int8_t* sigma, const void* t, const doubl
                       double lr, int n_cg, double cg_rtol, int prec, void* scratch,
                       size_t scratch_bytes, double* info, cudaStream_t st);
 int sr_choose_splits(const SrLayout& L, int prec, int requested);
+// Symmetric RBM (tied parameters over a permutation group, nk_sr_step_symm).
+// Tables in one device buffer: perm [n_perm][n], tie [pa] (untied augmented
+// element -> tied element or -1), fold CSR off [pa_t + 1] / idx [pa - 1].
+struct SymmTables {
+  int n, alpha, n_perm;
+  int64_t pa, pa_t;  // (m + 1)(n + 1) with m = alpha n_perm; (alpha + 1)(n + 1)
+  size_t perm, tie, off, idx, total;
+  SymmTables(int n_, int alpha_, int n_perm_);
+};
+nk_status symm_build_tables(const int32_t* perm, int n, int alpha, int n_perm,
+                            std::vector<int32_t>* out);
+size_t sr_symm_scratch_bytes(int n, int alpha, int n_perm, int cplx, int64_t ns);
+nk_status run_symm_expand(const nk_rbm_symm* s, nk_rbm* r, cudaStream_t st);
+nk_status run_sr_step_symm(nk_rbm_symm* s, nk_rbm* r, const int8_t* sigma, const void* t,
+                           const double* eloc, const double* weights, int64_t ns,
+                           int n_chains, double diag_shift, double lr, int n_cg,
+                           double cg_rtol, int prec, void* scratch, size_t scratch_bytes,
+                           double* info, cudaStream_t st);
 nk_status run_sr_tune(nk_rbm* r, const int8_t* sigma, const void* t, int64_t ns, int prec,
                       void* scratch, size_t scratch_bytes, cudaStream_t st);
 // SR batches (nk_sr_step_batch)

@@ -825,6 +825,8 @@ __global__ void __launch_bounds__(kVecThreads) cg_step_p_kernel(const void* rv, 
   cg_step_p_body<CPLX>(blockIdx.x, gridDim.x, rv, pv, pa, red, scal, it, rtol, nb, po);
 }
 
+__device__ __forceinline__ void sr_write_info(const double* scal, double* info, double rtol);
+
 // alpha <- alpha - lr delta (FP64 master), delta in the augmented layout; info.
 template <bool CPLX>
 __device__ __forceinline__ void sr_update_body(int bx, int gx, double* a, double* b, double* w, int n, int m,
@@ -849,7 +851,12 @@ __device__ __forceinline__ void sr_update_body(int bx, int gx, double* a, double
       dst[0] -= lr * x[e];
     }
   }
-  if (bx == 0 && threadIdx.x == 0) {
+  if (bx == 0 && threadIdx.x == 0) sr_write_info(scal, info, rtol);
+}
+
+// info {CG iterations, residual, ||F||, flags} from the CG scalars (one thread)
+__device__ __forceinline__ void sr_write_info(const double* scal, double* info, double rtol) {
+  {
     const double iters = scal[SC_ITERS];
     const double fn = scal[SC_FNORM];
     const double rs = scal[((int)iters & 1) ? SC_RS1 : SC_RS0];
@@ -870,6 +877,130 @@ __global__ void sr_update_kernel(double* a, double* b, double* w, int n, int m,
                                  const void* __restrict__ xv, double lr, const double* scal,
                                  double* info, int n_iter_final, double rtol) {
   sr_update_body<CPLX>(blockIdx.x, gridDim.x, a, b, w, n, m, xv, lr, scal, info, n_iter_final, rtol);
+}
+
+// ------------------------------------------------------------------ symmetric RBM
+// Tied parameters in the augmented layout [alpha + 1][n + 1]: (f, i < n) = Wt[f][i],
+// (f, n) = bt[f], (alpha, 0) = at; the other entries of the last row stand for
+// nothing and stay 0 in every CG vector (their fold lists are empty).
+
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double shfl_xor(double v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
+__device__ __forceinline__ double2 shfl_xor(double2 v, int o) {
+  return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+// P x: out[e] = x[tie[e]] over the untied augmented layout (0 where tie < 0)
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) symm_expand_vec_kernel(
+    const void* __restrict__ xv, const int* __restrict__ tie, int64_t pa, void* outv,
+    const double* scal) {
+  if (scal && scal[SC_DONE] != 0.0) return;
+  using DT = typename D<CPLX>::T;
+  const DT* x = reinterpret_cast<const DT*>(xv);
+  DT* out = reinterpret_cast<DT*>(outv);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pa;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = tie[e];
+    out[e] = k >= 0 ? x[k] : D<CPLX>::zero();
+  }
+}
+
+// P^T u (+ eps p): one warp per tied element sums its untied elements (lane l
+// takes list entries l, l + 32, ..., then a fixed xor tree), so the result does
+// not depend on scheduling; with p, per-block partials of Re p^H out -> red[bx].
+template <bool CPLX>
+__global__ void __launch_bounds__(kVecThreads) symm_fold_kernel(
+    const void* __restrict__ uv, const int* __restrict__ off, const int* __restrict__ idx,
+    int64_t pa_t, void* outv, const void* __restrict__ pv, double eps, double* red,
+    const double* scal) {
+  if (scal && scal[SC_DONE] != 0.0) return;
+  using DT = typename D<CPLX>::T;
+  const DT* u = reinterpret_cast<const DT*>(uv);
+  const DT* p = reinterpret_cast<const DT*>(pv);
+  DT* out = reinterpret_cast<DT*>(outv);
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double dot = 0.0;
+  for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < pa_t; q += nw) {
+    DT acc = D<CPLX>::zero();
+    const int k1 = off[q + 1];
+    for (int k = off[q] + lane; k < k1; k += 32) acc = vadd(acc, u[idx[k]]);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc = vadd(acc, shfl_xor(acc, o));
+    if (lane == 0) {
+      if (p) {
+        acc = axpy(eps, p[q], acc);
+        dot += cdot_re(p[q], acc);
+      }
+      out[q] = acc;
+    }
+  }
+  if (red) {
+    const double b = block_sum(dot);
+    if (threadIdx.x == 0) red[blockIdx.x] = b;
+  }
+}
+
+// theta_t <- theta_t - lr delta (tied layout); info
+template <bool CPLX>
+__global__ void symm_update_kernel(double* a, double* b, double* w, int n, int alpha,
+                                   const void* __restrict__ xv, double lr,
+                                   const double* scal, double* info, double rtol) {
+  using DT = typename D<CPLX>::T;
+  const DT* x = reinterpret_cast<const DT*>(xv);
+  const int na = n + 1, c = CPLX ? 2 : 1;
+  const int64_t tot = (int64_t)(alpha + 1) * na;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(e / na), i = (int)(e % na);
+    double* dst;
+    if (f < alpha && i < n) dst = w + c * ((int64_t)f * n + i);
+    else if (f < alpha) dst = b + c * f;
+    else if (i == 0) dst = a;
+    else continue;
+    if constexpr (CPLX) {
+      dst[0] -= lr * x[e].x;
+      dst[1] -= lr * x[e].y;
+    } else {
+      dst[0] -= lr * x[e];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) sr_write_info(scal, info, rtol);
+}
+
+// untied (a, b, W) from the tied parameters: a_i = at, b_(f,g) = bt_f,
+// W[(f,g)][i] = Wt[f][perm[g][i]]
+__global__ void symm_params_kernel(const double* __restrict__ ta, const double* __restrict__ tb,
+                                   const double* __restrict__ tw, int n, int alpha, int ng,
+                                   const int* __restrict__ perm, int cplx, double* a, double* b,
+                                   double* w) {
+  const int m = alpha * ng, c = cplx ? 2 : 1;
+  const int64_t nw = (int64_t)m * n, tot = nw + m + n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double* src;
+    double* dst;
+    if (e < nw) {
+      const int j = (int)(e / n), i = (int)(e % n);
+      src = tw + c * ((int64_t)(j / ng) * n + perm[(int64_t)(j % ng) * n + i]);
+      dst = w + c * e;
+    } else if (e < nw + m) {
+      const int j = (int)(e - nw);
+      src = tb + c * (j / ng);
+      dst = b + c * j;
+    } else {
+      src = ta;
+      dst = a + c * (e - nw - m);
+    }
+    dst[0] = src[0];
+    if (c == 2) dst[1] = src[1];
+  }
 }
 
 // grad (a, b, W order) from the augmented adjoint result
@@ -1036,17 +1167,37 @@ __global__ void sr_update_batch(const SrDesc* __restrict__ D, double lr, int n_c
 
 // ------------------------------------------------------------------ drivers
 
+// A symmetric RBM's tables, tied parameters and tied CG vectors (nk_sr_step_symm).
+struct SymmRun {
+  const int *tie, *off, *idx, *perm;
+  int64_t pa_t;
+  int alpha, n_perm;
+  double *a, *b, *w;
+  char *x, *r, *p, *ap;
+};
+
+// sy = NULL: SR in the RBM's own parameters.  sy: SR in the tied parameters;
+// the untied vectors x, r, p, ap of the scratch then hold expanded and
+// not-yet-folded products only.
 template <bool CPLX>
 static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const double* eloc,
                            const double* weights, int64_t ns, int n_chains, double eps,
                            double lr, int n_cg, double rtol, int prec, char* sc,
-                           double* info, cudaStream_t st) {
+                           double* info, cudaStream_t st, const SymmRun* sy = nullptr) {
   SrLayout L(r->n, r->m, CPLX, ns);
   double* scal = (double*)(sc + L.scal);
   double* red = (double*)(sc + L.red);
   const int n = r->n, m = r->m;
   const int64_t corner = (int64_t)m * L.na + n;
   const bool tc = prec == NK_PREC_BF16X2;
+  // the CG runs on these vectors (the tied ones for a symmetric RBM)
+  const int64_t pa_cg = sy ? sy->pa_t : L.pa;
+  char* cx = sy ? sy->x : sc + L.x;
+  char* cr = sy ? sy->r : sc + L.r;
+  char* cp = sy ? sy->p : sc + L.p;
+  char* cap = sy ? sy->ap : sc + L.ap;
+  const int nbc = sr_vec_blocks(pa_cg);
+  const int nbf = sy ? (int)std::min<int64_t>(kVecBlocks, (pa_cg + 7) / 8) : 0;
   int* err = reinterpret_cast<int*>(scal + SC_ERR);
   const int splits = sr_choose_splits(L, prec, r->sr_splits);
   AdjTcArgs aa{};
@@ -1100,8 +1251,11 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
   reduce_parts_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.part, splits, L.pa, corner,
                                                          sc + L.r, nullptr, 0.0, nullptr,
                                                          nullptr);
-  cg_init_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.x, sc + L.r, sc + L.p, L.pa, red);
-  cg_init_scalars_kernel<<<1, 32, 0, st>>>(red, scal, rtol, nbp);
+  if (sy)
+    symm_fold_kernel<CPLX><<<nbf, kVecThreads, 0, st>>>(sc + L.r, sy->off, sy->idx, pa_cg, cr,
+                                                        nullptr, 0.0, nullptr, nullptr);
+  cg_init_kernel<CPLX><<<nbc, kVecThreads, 0, st>>>(cx, cr, cp, pa_cg, red);
+  cg_init_scalars_kernel<<<1, 32, 0, st>>>(red, scal, rtol, nbc);
   if (nk_status e = check_launch("nk_sr_step(force)")) return e;
   const int64_t sg_blocks = (ns + kSgBS - 1) / kSgBS;
   aa.v = sc + L.v;
@@ -1132,8 +1286,11 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
     po.na64 = L.na64;
   }
   for (int it = 0; it < n_cg; ++it) {
+    if (sy)  // the untied p = P p_t for the contractions
+      symm_expand_vec_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(cp, sy->tie, L.pa, sc + L.p,
+                                                                scal);
     if (tc) {
-      if (it == 0) {
+      if (it == 0 || sy) {
         if (nk_status e = launch_bplanes_from_f64(sc + L.p, m + 1, n + 1, L.na, CPLX, L.mt1,
                                                   L.na64, sc + L.xbf, scal + SC_DONE, st))
           return e;
@@ -1154,16 +1311,30 @@ static nk_status sr_step_t(nk_rbm* r, const int8_t* sigma, const void* T, const 
     } else {
       launch_adjoint_fp32<CPLX>(sigma, T, sc + L.v, ns, n, m, splits, sc + L.part, scal, st);
     }
-    reduce_parts_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(
-        sc + L.part, splits, L.pa, corner, sc + L.ap, sc + L.p, eps, red, scal);
-    cg_step_x_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.x, sc + L.r, sc + L.p, sc + L.ap,
-                                                        L.pa, red, scal, it, nbp);
-    cg_step_p_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(sc + L.r, sc + L.p, L.pa, red, scal, it,
-                                                        rtol, nbp, po);
+    if (sy) {  // S_t p_t + eps p_t = P^T (S P p_t) + eps p_t
+      reduce_parts_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(
+          sc + L.part, splits, L.pa, corner, sc + L.ap, nullptr, 0.0, nullptr, scal);
+      symm_fold_kernel<CPLX><<<nbf, kVecThreads, 0, st>>>(sc + L.ap, sy->off, sy->idx, pa_cg,
+                                                          cap, cp, eps, red, scal);
+    } else {
+      reduce_parts_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(
+          sc + L.part, splits, L.pa, corner, sc + L.ap, sc + L.p, eps, red, scal);
+    }
+    cg_step_x_kernel<CPLX><<<nbc, kVecThreads, 0, st>>>(cx, cr, cp, cap, pa_cg, red, scal, it,
+                                                        sy ? nbf : nbc);
+    cg_step_p_kernel<CPLX><<<nbc, kVecThreads, 0, st>>>(cr, cp, pa_cg, red, scal, it, rtol, nbc,
+                                                        sy ? PlaneOut{} : po);
     if (nk_status e = check_launch("nk_sr_step(cg)")) return e;
   }
-  sr_update_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(r->a, r->b, r->w, n, m, sc + L.x, lr,
-                                                      scal, info, n_cg, rtol);
+  if (sy) {
+    symm_update_kernel<CPLX><<<nbc, kVecThreads, 0, st>>>(sy->a, sy->b, sy->w, n, sy->alpha, cx,
+                                                          lr, scal, info, rtol);
+    symm_params_kernel<<<nbp, kVecThreads, 0, st>>>(sy->a, sy->b, sy->w, n, sy->alpha,
+                                                    sy->n_perm, sy->perm, CPLX, r->a, r->b, r->w);
+  } else {
+    sr_update_kernel<CPLX><<<nbp, kVecThreads, 0, st>>>(r->a, r->b, r->w, n, m, sc + L.x, lr,
+                                                        scal, info, n_cg, rtol);
+  }
   if (nk_status e = check_launch("nk_sr_step(update)")) return e;
   return launch_prepare(r, st);
 }
@@ -1180,6 +1351,128 @@ nk_status run_sr_step(nk_rbm* r, const int8_t* sigma, const void* t, const doubl
                            prec, (char*)scratch, info, st);
   return sr_step_t<false>(r, sigma, t, eloc, weights, ns, n_chains, diag_shift, lr, n_cg, cg_rtol,
                           prec, (char*)scratch, info, st);
+}
+
+// ------------------------------------------------------------------ symmetric RBM (host)
+
+SymmTables::SymmTables(int n_, int alpha_, int n_perm_) : n(n_), alpha(alpha_), n_perm(n_perm_) {
+  const int64_t m = (int64_t)alpha * n_perm;
+  pa = (m + 1) * (n + 1);
+  pa_t = (int64_t)(alpha + 1) * (n + 1);
+  size_t o = 0;
+  auto take = [&](int64_t count) {
+    size_t at = o;
+    o += (size_t)round_up(count * (int64_t)sizeof(int32_t), 256);
+    return at;
+  };
+  perm = take((int64_t)n_perm * n);
+  tie = take(pa);
+  off = take(pa_t + 1);
+  idx = take(std::max<int64_t>(pa - 1, 1));
+  total = o;
+}
+
+// tie: untied augmented element (j, i) -> tied element; the fold lists are the
+// untied elements of each tied one in ascending order (a counting sort).
+nk_status symm_build_tables(const int32_t* perm, int n, int alpha, int n_perm,
+                            std::vector<int32_t>* out) {
+  const SymmTables T(n, alpha, n_perm);
+  std::vector<char> seen((size_t)n);
+  for (int g = 0; g < n_perm; ++g) {
+    std::fill(seen.begin(), seen.end(), 0);
+    for (int i = 0; i < n; ++i) {
+      const int32_t k = perm[(int64_t)g * n + i];
+      if (k < 0 || k >= n || seen[k])
+        return fail(NK_ERR_INVALID_ARG, "nk_symm_upload: row %d of perm is not a permutation", g);
+      seen[k] = 1;
+    }
+  }
+  out->assign(T.total / sizeof(int32_t), 0);
+  int32_t* base = out->data();
+  int32_t* P = base + T.perm / 4;
+  int32_t* tie = base + T.tie / 4;
+  int32_t* off = base + T.off / 4;
+  int32_t* idx = base + T.idx / 4;
+  std::copy(perm, perm + (int64_t)n_perm * n, P);
+  const int na = n + 1, m = alpha * n_perm;
+  for (int j = 0; j <= m; ++j)
+    for (int i = 0; i <= n; ++i) {
+      int64_t t;
+      if (j < m && i < n) t = (int64_t)(j / n_perm) * na + perm[(int64_t)(j % n_perm) * n + i];
+      else if (j < m) t = (int64_t)(j / n_perm) * na + n;
+      else if (i < n) t = (int64_t)alpha * na;
+      else t = -1;
+      tie[(int64_t)j * na + i] = (int32_t)t;
+    }
+  std::vector<int64_t> cnt((size_t)T.pa_t + 1, 0);
+  for (int64_t e = 0; e < T.pa; ++e)
+    if (tie[e] >= 0) ++cnt[(size_t)tie[e] + 1];
+  for (int64_t q = 0; q < T.pa_t; ++q) cnt[(size_t)q + 1] += cnt[(size_t)q];
+  for (int64_t q = 0; q <= T.pa_t; ++q) off[q] = (int32_t)cnt[(size_t)q];
+  for (int64_t e = 0; e < T.pa; ++e)
+    if (tie[e] >= 0) idx[cnt[(size_t)tie[e]]++] = (int32_t)e;
+  return NK_OK;
+}
+
+static size_t symm_vec_bytes(int n, int alpha, int cplx) {
+  return (size_t)round_up((int64_t)(alpha + 1) * (n + 1) * (cplx ? 16 : 8), 256);
+}
+
+size_t sr_symm_scratch_bytes(int n, int alpha, int n_perm, int cplx, int64_t ns) {
+  return sr_scratch_bytes(n, alpha * n_perm, cplx, ns) + 4 * symm_vec_bytes(n, alpha, cplx);
+}
+
+static SymmRun symm_run(const nk_rbm_symm* s, char* vec) {
+  const SymmTables T(s->n, s->alpha, s->n_perm);
+  const char* tb = (const char*)s->tables;
+  SymmRun y;
+  y.perm = (const int*)(tb + T.perm);
+  y.tie = (const int*)(tb + T.tie);
+  y.off = (const int*)(tb + T.off);
+  y.idx = (const int*)(tb + T.idx);
+  y.pa_t = T.pa_t;
+  y.alpha = s->alpha;
+  y.n_perm = s->n_perm;
+  y.a = s->a;
+  y.b = s->b;
+  y.w = s->w;
+  y.x = y.r = y.p = y.ap = nullptr;
+  if (vec) {
+    const size_t vb = symm_vec_bytes(s->n, s->alpha, s->is_complex);
+    y.x = vec;
+    y.r = vec + vb;
+    y.p = vec + 2 * vb;
+    y.ap = vec + 3 * vb;
+  }
+  return y;
+}
+
+nk_status run_symm_expand(const nk_rbm_symm* s, nk_rbm* r, cudaStream_t st) {
+  const SymmRun y = symm_run(s, nullptr);
+  const int64_t tot = (int64_t)r->m * r->n + r->m + r->n;
+  const int blocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (tot + 1023) / 1024));
+  symm_params_kernel<<<blocks, kVecThreads, 0, st>>>(s->a, s->b, s->w, s->n, s->alpha, s->n_perm,
+                                                     y.perm, s->is_complex, r->a, r->b, r->w);
+  if (nk_status e = check_launch("nk_symm_expand")) return e;
+  return launch_prepare(r, st);
+}
+
+nk_status run_sr_step_symm(nk_rbm_symm* s, nk_rbm* r, const int8_t* sigma, const void* t,
+                           const double* eloc, const double* weights, int64_t ns,
+                           int n_chains, double diag_shift, double lr, int n_cg,
+                           double cg_rtol, int prec, void* scratch, size_t scratch_bytes,
+                           double* info, cudaStream_t st) {
+  const size_t base = sr_scratch_bytes(r->n, r->m, r->is_complex, ns);
+  const size_t need = sr_symm_scratch_bytes(s->n, s->alpha, s->n_perm, s->is_complex, ns);
+  if (scratch_bytes < need)
+    return fail(NK_ERR_SHAPE, "nk_sr_step_symm: scratch of %zu B, need %zu B", scratch_bytes,
+                need);
+  const SymmRun y = symm_run(s, (char*)scratch + base);
+  if (r->is_complex)
+    return sr_step_t<true>(r, sigma, t, eloc, weights, ns, n_chains, diag_shift, lr, n_cg,
+                           cg_rtol, prec, (char*)scratch, info, st, &y);
+  return sr_step_t<false>(r, sigma, t, eloc, weights, ns, n_chains, diag_shift, lr, n_cg,
+                          cg_rtol, prec, (char*)scratch, info, st, &y);
 }
 
 // ------------------------------------------------------------------ SR batches

@@ -39,6 +39,8 @@ EXPORTS = (
     "nk_sr_tune", "nk_sr_batch_desc_bytes", "nk_sr_batch_describe", "nk_sr_step_batch",
     "nk_query_status", "nk_debug_bounded_wait", "nk_measure_alu_peaks",
     "nk_batch_logpsi", "nk_batch_sweep", "nk_batch_local_energy",
+    "nk_symm_tables_bytes", "nk_symm_upload", "nk_symm_expand", "nk_sr_symm_scratch_bytes",
+    "nk_sr_step_symm",
 )
 NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
@@ -51,6 +53,12 @@ class _Rbm(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("is_complex", C.c_int32),
                 ("sr_splits", C.c_int32), ("a", C.c_void_p), ("b", C.c_void_p), ("w", C.c_void_p),
                 ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
+
+
+class _RbmSymm(C.Structure):
+    _fields_ = [("n", C.c_int32), ("alpha", C.c_int32), ("n_perm", C.c_int32),
+                ("is_complex", C.c_int32), ("a", C.c_void_p), ("b", C.c_void_p),
+                ("w", C.c_void_p), ("tables", C.c_void_p), ("tables_bytes", C.c_size_t)]
 
 
 class _Chains(C.Structure):
@@ -133,6 +141,11 @@ def load_library(path: str = LIB_PATH):
         "nk_batch_logpsi": (I32, [P, I32, I32, P]),
         "nk_batch_sweep": (I32, [P, I32, P]),
         "nk_batch_local_energy": (I32, [P, I32, P]),
+        "nk_symm_tables_bytes": (SZ, [I32, I32, I32]),
+        "nk_symm_upload": (I32, [P, I32, I32, I32, P, SZ, P]),
+        "nk_symm_expand": (I32, [P, P, P]),
+        "nk_sr_symm_scratch_bytes": (SZ, [I32, I32, I32, I32, I64]),
+        "nk_sr_step_symm": (I32, [P, P, P, P, P, P, I64, I32, D, D, I32, D, I32, P, SZ, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -542,3 +555,88 @@ def nk_batch_local_energy(jobs, stream=None):
                              j["scratch"].numel(), _item_stream(j.get("stream")))
     _check(load_library().nk_batch_local_energy(C.cast(items, C.c_void_p), len(jobs),
                                                 _stream(stream)), "nk_batch_local_energy")
+
+
+# ---------------------------------------------------------------------- symmetric RBM
+
+class RbmSymm:
+    """Tied FP64 parameters (at [1], bt [alpha], Wt [alpha, n]) of a symmetric RBM
+    over the permutation table ``perm`` [n_perm, n], its tie tables on the device,
+    and ``rbm``, the untied RBM (m = alpha n_perm) it stands for."""
+
+    def __init__(self, perm, alpha: int, is_complex: bool, device="cuda", stream=None):
+        lib = load_library()
+        perm = np.ascontiguousarray(np.asarray(perm, dtype=np.int32))
+        self.n_perm, self.n = (int(v) for v in perm.shape)
+        self.alpha, self.is_complex = int(alpha), bool(is_complex)
+        k = 2 if is_complex else 1
+        dt = torch.float64
+        self.a = torch.zeros(k, dtype=dt, device=device)
+        self.b = torch.zeros(self.alpha * k, dtype=dt, device=device)
+        self.w = torch.zeros(self.alpha * self.n * k, dtype=dt, device=device)
+        nb = lib.nk_symm_tables_bytes(self.n, self.alpha, self.n_perm)
+        if nb == 0:
+            raise NkError("nk_symm_tables_bytes: sizes out of range")
+        self.tables = torch.empty(nb + 256, dtype=torch.uint8, device=device)
+        off = (-self.tables.data_ptr()) % 256
+        tp = self.tables.data_ptr() + off
+        _check(lib.nk_symm_upload(perm.ctypes.data_as(C.c_void_p), self.n, self.alpha,
+                                  self.n_perm, C.c_void_p(tp), nb, _stream(stream)),
+               "nk_symm_upload")
+        self._s = _RbmSymm(self.n, self.alpha, self.n_perm, int(is_complex), self.a.data_ptr(),
+                           self.b.data_ptr(), self.w.data_ptr(), tp, nb)
+        self.rbm = Rbm(self.n, self.alpha * self.n_perm, is_complex, device)
+
+    @property
+    def n_params(self) -> int:
+        return 1 + self.alpha + self.alpha * self.n
+
+    def struct(self):
+        return C.byref(self._s)
+
+    def load(self, a, b, w, stream=None):
+        """Copy tied FP64 parameters (numpy) in and expand them into ``rbm``."""
+        def flat(x):
+            x = np.asarray(x)
+            if self.is_complex:
+                x = x.astype(np.complex128).reshape(-1)
+                return torch.from_numpy(np.stack([x.real, x.imag], axis=1).reshape(-1).copy())
+            return torch.from_numpy(np.asarray(x, dtype=np.float64).reshape(-1).copy())
+        self.a.copy_(flat(a))
+        self.b.copy_(flat(b))
+        self.w.copy_(flat(w))
+        nk_symm_expand(self, stream)
+
+    def params_numpy(self):
+        def un(t, shape):
+            x = t.detach().cpu().numpy()
+            if self.is_complex:
+                x = x[0::2] + 1j * x[1::2]
+            return x.reshape(shape)
+        return un(self.a, (1,)), un(self.b, (self.alpha,)), un(self.w, (self.alpha, self.n))
+
+
+def nk_symm_expand(s: RbmSymm, stream=None):
+    _check(load_library().nk_symm_expand(s.struct(), s.rbm.struct(), _stream(stream)),
+           "nk_symm_expand")
+
+
+def sr_symm_scratch(s: RbmSymm, ns: int, device="cuda"):
+    nb = load_library().nk_sr_symm_scratch_bytes(s.n, s.alpha, s.n_perm, int(s.is_complex), ns)
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def nk_sr_step_symm(s: RbmSymm, sigma, t, eloc, n_chains: int, diag_shift: float, lr: float,
+                    n_cg: int, cg_rtol: float = 1e-12, prec=NK_PREC_FP32, weights=None,
+                    scratch=None, info_out=None, stream=None):
+    _require_gpu(sigma, t, eloc, weights, scratch, info_out)
+    ns = sigma.shape[0]
+    if scratch is None:
+        scratch = sr_symm_scratch(s, ns, sigma.device)
+    if info_out is None:
+        info_out = torch.zeros(NK_INFO_LEN, dtype=torch.float64, device=sigma.device)
+    _check(load_library().nk_sr_step_symm(
+        s.struct(), s.rbm.struct(), _ptr(sigma), _ptr(t), _ptr(eloc), _ptr(weights), ns,
+        n_chains, float(diag_shift), float(lr), int(n_cg), float(cg_rtol), prec, _ptr(scratch),
+        scratch.numel(), _ptr(info_out), _stream(stream)), "nk_sr_step_symm")
+    return info_out

@@ -162,3 +162,31 @@ def test_batch_calls_check_every_item_first(lib):
     assert lib.nk_batch_sweep(None, 3, None) == 1
     assert lib.nk_batch_logpsi(None, -1, 0, None) == 1
     assert lib.nk_batch_local_energy(None, 2, None) == 1
+
+
+def test_symm_host_checks(lib):
+    from paper_1904_00031_gb300 import nk
+    n, alpha, g = 9, 2, 9
+    pa, pa_t = (alpha * g + 1) * (n + 1), (alpha + 1) * (n + 1)
+    nb = lib.nk_symm_tables_bytes(n, alpha, g)
+    assert nb >= 4 * (g * n + pa + pa_t + 1 + pa - 1) and nb % 256 == 0
+    assert lib.nk_symm_tables_bytes(0, alpha, g) == 0
+    assert lib.nk_symm_tables_bytes(400, 21, 400) == 0  # alpha n_perm above NK_MAX_M
+    assert lib.nk_sr_symm_scratch_bytes(n, alpha, g, 1, 64) > lib.nk_sr_scratch_bytes(
+        n, alpha * g, 1, 64)
+    # a row that is not a permutation is rejected on the host, nothing copied
+    perm = W.square_translations(3).copy()
+    perm[4, 0] = perm[4, 1]
+    assert lib.nk_symm_upload(perm.ctypes.data_as(C.c_void_p), n, alpha, g, C.c_void_p(256),
+                              nb, None) == 1
+    assert b"not a permutation" in lib.nk_last_error()
+    # the untied RBM must be the expansion (m = alpha n_perm)
+    s = nk._RbmSymm(n, alpha, g, 0, 8, 8, 8, 256, nb)
+    r = nk._Rbm(n, alpha * g + 1, 0, 0, 8, 8, 8, 256, 1 << 24)
+    assert lib.nk_symm_expand(C.byref(s), C.byref(r), None) == 2
+    r = nk._Rbm(n, alpha * g, 0, 0, 8, 8, 8, 256, 1 << 24)
+    s_small = nk._RbmSymm(n, alpha, g, 0, 8, 8, 8, 256, nb - 256)
+    assert lib.nk_symm_expand(C.byref(s_small), C.byref(r), None) == 2
+    assert b"tables" in lib.nk_last_error()
+    assert lib.nk_sr_step_symm(C.byref(s), C.byref(r), 8, 8, 8, None, 10, 3, 0.01, 0.01, 5, 0.0,
+                               0, 256, 1 << 24, 8, None) == 2  # 10 samples, 3 chains
