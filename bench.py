@@ -36,6 +36,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x2"])
     ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--model", default="rbm", choices=["rbm", "symm"],
+                    help="symm: the translation-symmetric RBM (alpha = m / n families) on the "
+                         "workload's lattice, SR in its tied parameters")
     ap.add_argument("--graph", type=int, default=1, help="replay iterations as CUDA graphs")
     ap.add_argument("--profile-kernels", action="store_true",
                     help="small 20x20 J1-J2 case for ncu captures: one CTA per SM per kernel")
@@ -205,7 +208,7 @@ def run_gpu(args):
     from paper_1904_00031_gb300 import nk
     from paper_1904_00031_gb300 import workloads as W
     from paper_1904_00031_gb300 import replicas as R
-    from paper_1904_00031_gb300.vmc import VmcSr
+    from paper_1904_00031_gb300.vmc import VmcSr, VmcSrSymm
 
     world, rank, local = R.env_world()
     R.init(world, "nccl")
@@ -217,7 +220,18 @@ def run_gpu(args):
     prec = nk.NK_PREC_FP32 if prec_name == "fp32" else nk.NK_PREC_BF16X2
     # each rank samples its own chains (independent replicas)
     sigma0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, R.replica_seed(w.seed, rank))
-    v = VmcSr(w, params, sigma0, prec, graph=bool(args.graph), autotune=True)
+    symm = args.model == "symm"
+    if symm:
+        perm = W.translations(w)
+        sparams = W.init_symm_params(w.n, w.m // w.n, w.is_complex, 0.01, w.seed)
+
+        def make(pr, **kw):
+            return VmcSrSymm(w, sparams, perm, sigma0, pr, **kw)
+    else:
+        def make(pr, **kw):
+            return VmcSr(w, params, sigma0, pr, **kw)
+    v = make(prec, graph=bool(args.graph), autotune=True)
+    wname = w.name + ("_symm" if symm else "")
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -262,30 +276,28 @@ def run_gpu(args):
 
     # end to end through the public API: parameters H2D from pinned memory,
     # one iteration, the FP64 status block D2H, every step
-    pa = v.rbm.a.cpu().pin_memory()
-    pb = v.rbm.b.cpu().pin_memory()
-    pw = v.rbm.w.cpu().pin_memory()
+    dev_params = v.param_tensors()
+    host_params = [x.cpu().pin_memory() for x in dev_params]
     host_info = torch.empty(nk.NK_INFO_LEN, dtype=torch.float64).pin_memory()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        v.rbm.a.copy_(pa, non_blocking=True)
-        v.rbm.b.copy_(pb, non_blocking=True)
-        v.rbm.w.copy_(pw, non_blocking=True)
-        nk.nk_rbm_prepare(v.rbm)
+        for d, h in zip(dev_params, host_params):
+            d.copy_(h, non_blocking=True)
+        v.refresh()
         v.step()
         host_info.copy_(v.info_buf, non_blocking=True)
     e1.record(stream)
     barrier()
     e2e_ms = R.max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
-    h2d = (pa.numel() + pb.numel() + pw.numel()) * 8
+    h2d = sum(h.numel() for h in host_params) * 8
 
     # the plain FP32 path on the same workload (for the mixed-precision ratio)
     fp32_arm = None
     if prec != nk.NK_PREC_FP32 and not args.no_fp32_arm:
-        v32 = VmcSr(w, params, sigma0, nk.NK_PREC_FP32)
+        v32 = make(nk.NK_PREC_FP32)
         for _ in range(max(1, args.warmup)):
             v32.step()
         barrier()
@@ -340,7 +352,7 @@ def run_gpu(args):
             "sr": "SR step (fwd_tc + adj_tc + CG vector kernels)" if prec_name == "bf16x2"
                   else "SR step (forward/adjoint FP32 + CG vector kernels)"}[dom]
     roof = dict(rl[dom])
-    roof.update({"kernel": kern, "traffic": NCU_TRAFFIC.get((w.name, prec_name, kern)),
+    roof.update({"kernel": kern, "traffic": NCU_TRAFFIC.get((wname, prec_name, kern)),
                  "peak_source": (f"{pk_kind} bf16 dense TFLOP/s (sustained)" if roof["bound"] == "tensor"
                                  else alu_src)})
     # the same measurement after more SR iterations: psi has structure and the
@@ -372,7 +384,7 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded RBM parameters N(0,0.01^2), random S^z=0 chain starts)",
-        "config": {"workload": w.name, "n": w.n, "m": w.m, "complex": w.is_complex,
+        "config": {"workload": wname, "n": w.n, "m": w.m, "complex": w.is_complex,
                    "chains": w.n_chains, "samples_per_chain": w.samples_per_chain,
                    "burn_in_sweeps": w.n_discard, "samples_per_iter": w.n_samples,
                    "moves": w.move, "n_cg": w.n_cg, "diag_shift": w.diag_shift, "lr": w.lr,
@@ -502,6 +514,10 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
+        if args.model != "rbm":
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle arm times the "
+                              "untied RBM only; run it without --model"}))
+            return
         from paper_1904_00031_gb300 import workloads as W
         # the 64-instance batch: its first instance stands for the workload
         w = (W.workload(args.workload) if args.workload != "c4"
@@ -531,13 +547,15 @@ def main():
         }))
         return
     base = None
-    if rank == 0 and world == 1 and not args.no_baseline:
+    if rank == 0 and world == 1 and not args.no_baseline and args.model == "rbm":
         # before any CUDA call: the oracle runs in a fresh single-threaded process
         r = run_oracle_subprocess(args.workload, nc, spc, ncg)
         base = {"value": round(r["samples"] / r["seconds"], 4), "unit": "samples/s", "cores": 1,
                 "kind": "oracle",
                 "sample": f"{nc} chains x ({spc} samples + 1 burn-in sweep), one full oracle "
                           f"VMC+SR iteration ({ncg} CG iterations), {r['seconds']:.1f} s"}
+    if args.workload == "c4" and args.model != "rbm":
+        raise SystemExit("--model symm runs the single-instance workloads (c1, c2, c3, c5)")
     rank, out = run_gpu_batched(args) if args.workload == "c4" else run_gpu(args)
     out["cpu_baseline"] = base
     if rank == 0:

@@ -141,6 +141,14 @@ class VmcSr:
         # adjoint, reduction, CG start (2); 8 per CG iteration
         return 3 + 4 + 8 * self.w.n_cg + 3
 
+    def param_tensors(self):
+        """The FP64 master parameters a caller uploads (device tensors)."""
+        return [self.rbm.a, self.rbm.b, self.rbm.w]
+
+    def refresh(self):
+        """Derive the kernels' planes after new master parameters were uploaded."""
+        nk.nk_rbm_prepare(self.rbm)
+
     # kernel launches per step (for reporting)
     def launches_per_step(self) -> int:
         # move tables (exchanges; flips of complex RBMs), sweep
@@ -149,3 +157,42 @@ class VmcSr:
         n += 2                                                  # move tables, local energy
         n += self.sr_launches()                                 # SR step
         return n
+
+
+class VmcSrSymm(VmcSr):
+    """The same iteration for a symmetric RBM (RbmSpinSymm, Sec. 2.2.2): sampling,
+    amplitudes and local energies run on the untied RBM it stands for; SR runs in
+    the tied parameters (nk_sr_step_symm), which also rewrites the untied RBM."""
+
+    def __init__(self, w: W.Workload, params: W.RbmSymmParams, perm, sigma0=None,
+                 prec: int = nk.NK_PREC_FP32, device="cuda", graph: bool = False,
+                 autotune: bool = False):
+        self.sy = nk.RbmSymm(perm, params.alpha, params.is_complex, device)
+        self.sy.load(params.a, params.b, params.w)
+        full = W.RbmParams(*(x.copy() for x in self._untied(self.sy)))
+        super().__init__(w, full, sigma0, prec, device, graph, autotune)
+        self.rbm = self.sy.rbm
+        self.scratch = nk.sr_symm_scratch(self.sy, self.ns, device)
+
+    @staticmethod
+    def _untied(sy):
+        return sy.rbm.params_numpy()
+
+    def sr(self):
+        nk.nk_sr_step_symm(self.sy, self.samples, self.t, self.eloc, self.w.n_chains,
+                           self.w.diag_shift, self.w.lr, self.w.n_cg, 1e-12, self.prec,
+                           scratch=self.scratch, info_out=self.info_buf)
+
+    def param_tensors(self):
+        return [self.sy.a, self.sy.b, self.sy.w]
+
+    def refresh(self):
+        nk.nk_symm_expand(self.sy)
+
+    def sr_launches(self) -> int:
+        """As the untied step, plus per CG iteration the expansion of p, its planes
+        and the fold of S p (tensor cores; expansion and fold on the FP32 path),
+        the fold of F, and the expansion of the updated parameters."""
+        if self.prec == nk.NK_PREC_BF16X2:
+            return super().sr_launches() + 3 * self.w.n_cg + 1
+        return super().sr_launches() + 2 * self.w.n_cg + 2

@@ -348,6 +348,7 @@ class Workload:
     n_cg: int
     seed: int
     group_size: int = 8
+    lattice: str = "chain"    # "chain" or "square" (periodic), for its translation group
 
     @property
     def n_samples(self) -> int:
@@ -382,11 +383,21 @@ def workload(name: str, n_chains: int | None = None, samples_per_chain: int | No
                      square_bonds(L), True, 16384, 4, 1, 0.01, 0.01, 50, 1237)
     else:
         raise KeyError(name)
+    if name in ("c3", "c5"):
+        w.lattice = "square"
     if n_chains is not None:
         w.n_chains = n_chains
     if samples_per_chain is not None:
         w.samples_per_chain = samples_per_chain
     return w
+
+
+def translations(w: Workload) -> np.ndarray:
+    """Translation group of a workload's periodic lattice (permutation table)."""
+    if w.lattice == "square":
+        L = int(round(math.sqrt(w.n)))
+        return square_translations(L)
+    return chain_translations(w.n)
 
 
 def batched_instances(n_inst: int = 64, seed: int = 4242, n_chains: int = 1024):
