@@ -28,6 +28,7 @@ MASK32 = np.uint64(0xFFFFFFFF)
 
 TAG_SITE = 0x53495445    # proposal (site or bond) draw, one per chain group and step
 TAG_ACCEPT = 0x41434350  # accept/reject uniform, one per chain and step
+TAG_SWAP = 0x53574150    # replica-exchange uniform, one per replica and sweep
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):

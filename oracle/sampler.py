@@ -32,13 +32,16 @@ from . import philox, rbm
 
 
 def metropolis(p, sigma0, move: str, bonds, group_size: int, seed: int, counter: int,
-               n_discard: int, n_samples: int, return_margin: bool = False):
+               n_discard: int, n_samples: int, return_margin: bool = False, betas=None):
     """Run every chain (rows of ``sigma0``) for n_discard + n_samples sweeps.
 
     Returns (samples [nc * n_samples, N] int8, final states [nc, N] int8,
     new counter, accepted count per chain [nc]) and, if ``return_margin``, the
     smallest |ln U - 2 Re Delta| over the chain's non-null proposals (how close
-    an accept decision came to a tie), for trajectory comparisons."""
+    an accept decision came to a tie), for trajectory comparisons.
+
+    ``betas`` [nc] (parallel tempering): chain c samples |psi|^(2 beta_c) and
+    accepts iff U < exp(2 beta_c Re Delta); None is beta = 1 for every chain."""
     sigma = np.array(sigma0, dtype=np.int8, copy=True)
     nc, n = sigma.shape
     sig = sigma.astype(np.float64)
@@ -72,6 +75,8 @@ def metropolis(p, sigma0, move: str, bonds, group_size: int, seed: int, counter:
             lcp = rbm.lncosh(thp)
             dlog = dlog + (lcp - lc).sum(axis=1)
             two_re = 2.0 * np.real(dlog)
+            if betas is not None:
+                two_re = np.asarray(betas, dtype=np.float64) * two_re
             with np.errstate(over="ignore"):
                 acc = valid & (U < np.exp(two_re))
             if return_margin:
