@@ -438,6 +438,21 @@ typedef struct nk_rbm_symm {
 /* Bytes of the tie tables of a symmetric RBM (0 for sizes out of range). */
 size_t nk_symm_tables_bytes(int32_t n, int32_t alpha, int32_t n_perm);
 
+/* Builds the tie tables from the HOST permutation table perm [n_perm][n] into
+ * HOST memory `host` (nk_symm_tables_bytes() bytes), for callers that stage the
+ * copy themselves; no CUDA call.  Layout (int32, each section starting on a
+ * 256-byte boundary, in this order), with m = alpha n_perm and the augmented
+ * layouts of the SR vectors -- untied (m + 1) x (n + 1): W[j][i] at (j, i),
+ * b_j at (j, n), a_i at (m, i); tied (alpha + 1) x (n + 1): Wt[f][i] at (f, i),
+ * bt_f at (f, n), at at (alpha, 0):
+ *   perm [n_perm][n]            the table as given
+ *   tie  [(m + 1)(n + 1)]       untied element -> the tied element it copies, -1 for (m, n)
+ *   off  [(alpha + 1)(n + 1) + 1], idx [(m + 1)(n + 1) - 1]
+ *                               the untied elements of each tied one, ascending (CSR)
+ * Errors as nk_symm_upload. */
+nk_status nk_symm_build(const int32_t* perm, int32_t n, int32_t alpha, int32_t n_perm, void* host,
+                        size_t bytes);
+
 /* Builds the tie tables from the HOST permutation table perm [n_perm][n]
  * (each row a permutation of 0..n-1, else NK_ERR_INVALID_ARG) and copies them
  * into `dev` (device, 256-B aligned, nk_symm_tables_bytes() bytes).  Like

@@ -543,6 +543,21 @@ size_t nk_symm_tables_bytes(int32_t n, int32_t alpha, int32_t n_perm) {
   return SymmTables(n, alpha, n_perm).total;
 }
 
+nk_status nk_symm_build(const int32_t* perm, int32_t n, int32_t alpha, int32_t n_perm, void* host,
+                        size_t bytes) {
+  if (!perm || !host) return fail(NK_ERR_INVALID_ARG, "nk_symm_build: NULL pointer");
+  if (!symm_sizes_ok(n, alpha, n_perm))
+    return fail(NK_ERR_SHAPE, "nk_symm_build: n = %d, alpha = %d, n_perm = %d out of range", n,
+                alpha, n_perm);
+  const size_t need = SymmTables(n, alpha, n_perm).total;
+  if (bytes < need)
+    return fail(NK_ERR_SHAPE, "nk_symm_build: %zu B given, %zu B needed", bytes, need);
+  std::vector<int32_t> buf;
+  if (nk_status e = symm_build_tables(perm, n, alpha, n_perm, &buf)) return e;
+  memcpy(host, buf.data(), need);
+  return NK_OK;
+}
+
 nk_status nk_symm_upload(const int32_t* perm, int32_t n, int32_t alpha, int32_t n_perm,
                          void* dev, size_t bytes, void* stream) {
   if (!perm || !dev) return fail(NK_ERR_INVALID_ARG, "nk_symm_upload: NULL pointer");

@@ -40,7 +40,7 @@ EXPORTS = (
     "nk_query_status", "nk_debug_bounded_wait", "nk_measure_alu_peaks",
     "nk_batch_logpsi", "nk_batch_sweep", "nk_batch_local_energy",
     "nk_symm_tables_bytes", "nk_symm_upload", "nk_symm_expand", "nk_sr_symm_scratch_bytes",
-    "nk_sr_step_symm",
+    "nk_sr_step_symm", "nk_symm_build",
 )
 NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
@@ -143,6 +143,7 @@ def load_library(path: str = LIB_PATH):
         "nk_batch_local_energy": (I32, [P, I32, P]),
         "nk_symm_tables_bytes": (SZ, [I32, I32, I32]),
         "nk_symm_upload": (I32, [P, I32, I32, I32, P, SZ, P]),
+        "nk_symm_build": (I32, [P, I32, I32, I32, P, SZ]),
         "nk_symm_expand": (I32, [P, P, P]),
         "nk_sr_symm_scratch_bytes": (SZ, [I32, I32, I32, I32, I64]),
         "nk_sr_step_symm": (I32, [P, P, P, P, P, P, I64, I32, D, D, I32, D, I32, P, SZ, P, P]),

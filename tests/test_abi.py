@@ -190,3 +190,64 @@ def test_symm_host_checks(lib):
     assert b"tables" in lib.nk_last_error()
     assert lib.nk_sr_step_symm(C.byref(s), C.byref(r), 8, 8, 8, None, 10, 3, 0.01, 0.01, 5, 0.0,
                                0, 256, 1 << 24, 8, None) == 2  # 10 samples, 3 chains
+
+
+def _sections(n, alpha, g):
+    m = alpha * g
+    pa, pa_t = (m + 1) * (n + 1), (alpha + 1) * (n + 1)
+    sizes = [g * n, pa, pa_t + 1, max(pa - 1, 1)]
+    offs, o = [], 0
+    for k in sizes:
+        offs.append(o // 4)
+        o += -(-4 * k // 256) * 256
+    return offs, sizes, o
+
+
+def _aug_full(v, n, m):
+    """(a, b, W) flat -> untied augmented [(m + 1)(n + 1)]."""
+    out = np.zeros((m + 1, n + 1), dtype=v.dtype)
+    out[:m, :n] = v[n + m:].reshape(m, n)
+    out[:m, n] = v[n:n + m]
+    out[m, :n] = v[:n]
+    return out.reshape(-1)
+
+
+def _aug_tied(x, n, alpha):
+    """(at, bt, Wt) flat -> tied augmented [(alpha + 1)(n + 1)]."""
+    out = np.zeros((alpha + 1, n + 1), dtype=x.dtype)
+    out[:alpha, :n] = x[1 + alpha:].reshape(alpha, n)
+    out[:alpha, n] = x[1:1 + alpha]
+    out[alpha, 0] = x[0]
+    return out.reshape(-1)
+
+
+@pytest.mark.parametrize("lattice,alpha", [("square3", 2), ("chain7", 3), ("identity5", 2)])
+def test_symm_tables_match_the_oracle_ties(lib, lattice, alpha):
+    """The C++ tie and fold tables realise the oracle's expand (P x) and fold
+    (P^T u) exactly, in the augmented layouts the SR kernels use."""
+    from oracle import rbm_symm
+    perm = {"square3": W.square_translations(3), "chain7": W.chain_translations(7),
+            "identity5": np.arange(5, dtype=np.int32)[None, :]}[lattice]
+    g, n = perm.shape
+    m = alpha * g
+    nb = lib.nk_symm_tables_bytes(n, alpha, g)
+    offs, sizes, total = _sections(n, alpha, g)
+    assert nb == total
+    buf = np.zeros(nb // 4, dtype=np.int32)
+    pc = np.ascontiguousarray(perm, dtype=np.int32)
+    assert lib.nk_symm_build(pc.ctypes.data_as(C.c_void_p), n, alpha, g,
+                             buf.ctypes.data_as(C.c_void_p), nb) == 0
+    P, tie, off, idx = (buf[o:o + k] for o, k in zip(offs, sizes))
+    assert np.array_equal(P.reshape(g, n), perm)
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=1 + alpha + alpha * n) + 1j * rng.normal(size=1 + alpha + alpha * n)
+    xt = _aug_tied(x, n, alpha)
+    got = np.where(tie >= 0, xt[np.maximum(tie, 0)], 0)
+    assert np.array_equal(got, _aug_full(rbm_symm.expand_vector(x, n, alpha, perm), n, m))
+    u = rng.normal(size=n + m + n * m) + 1j * rng.normal(size=n + m + n * m)
+    ua = _aug_full(u, n, m)
+    assert np.all(np.diff(off) >= 0) and off[-1] == len(ua) - 1
+    fold = np.array([ua[idx[off[q]:off[q + 1]]].sum() for q in range(len(off) - 1)])
+    assert np.allclose(fold, _aug_tied(rbm_symm.fold(u, n, alpha, perm), n, alpha), atol=1e-12)
+    for q in range(len(off) - 1):  # ascending lists: the fold's fixed summation order
+        assert np.all(np.diff(idx[off[q]:off[q + 1]]) > 0)
