@@ -38,13 +38,17 @@ def adj_centres(m: int, is_complex: bool) -> bool:
 
 
 class VmcSr:
-    def __init__(self, w: W.Workload, params: W.RbmParams, sigma0=None,
+    def __init__(self, w: W.Workload, params: W.RbmParams | None, sigma0=None,
                  prec: int = nk.NK_PREC_FP32, device="cuda", graph: bool = False,
-                 autotune: bool = False):
+                 autotune: bool = False, rbm: nk.Rbm | None = None):
+        """``params`` are loaded into a new RBM, or ``rbm`` (already loaded and
+        prepared, params None) is used as it is."""
         self.w = w
         self.prec = prec
-        self.rbm = nk.Rbm(w.n, w.m, w.is_complex, device)
-        self.rbm.load(params.a, params.b, params.w)
+        if rbm is None:
+            rbm = nk.Rbm(w.n, w.m, w.is_complex, device)
+            rbm.load(params.a, params.b, params.w)
+        self.rbm = rbm
         if sigma0 is None:
             sigma0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed)
         self.chains = nk.Chains(sigma0, w.group_size, w.seed, device, device_counter=graph)
@@ -65,11 +69,14 @@ class VmcSr:
         self.logpsi = torch.empty(ns, dtype=torch.complex128, device=device)
         self.eloc = torch.empty(ns, dtype=torch.complex128, device=device)
         self.n_acc = torch.zeros(w.n_chains, dtype=torch.int64, device=device)
-        self.scratch = nk.sr_scratch(self.rbm, ns, device)
+        self.scratch = self._sr_scratch(device)
         self.info_buf = torch.zeros(nk.NK_INFO_LEN, dtype=torch.float64, device=device)
         self.move = nk.NK_MOVE_FLIP if w.move == "flip" else nk.NK_MOVE_EXCHANGE
         self.metro_scratch = nk.metropolis_scratch(self.rbm, self.move, len(b), device)
         self.eloc_scratch = nk.local_energy_scratch(self.rbm, self.op, device)
+
+    def _sr_scratch(self, device):
+        return nk.sr_scratch(self.rbm, self.ns, device)
 
     # stages ---------------------------------------------------------------
     def sample(self):
@@ -169,14 +176,10 @@ class VmcSrSymm(VmcSr):
                  autotune: bool = False):
         self.sy = nk.RbmSymm(perm, params.alpha, params.is_complex, device)
         self.sy.load(params.a, params.b, params.w)
-        full = W.RbmParams(*(x.copy() for x in self._untied(self.sy)))
-        super().__init__(w, full, sigma0, prec, device, graph, autotune)
-        self.rbm = self.sy.rbm
-        self.scratch = nk.sr_symm_scratch(self.sy, self.ns, device)
+        super().__init__(w, None, sigma0, prec, device, graph, autotune, rbm=self.sy.rbm)
 
-    @staticmethod
-    def _untied(sy):
-        return sy.rbm.params_numpy()
+    def _sr_scratch(self, device):
+        return nk.sr_symm_scratch(self.sy, self.ns, device)
 
     def sr(self):
         nk.nk_sr_step_symm(self.sy, self.samples, self.t, self.eloc, self.w.n_chains,
