@@ -128,3 +128,33 @@ def test_full_sum_tied_sr_converges_to_the_tfim_ground_state():
         ps = W.RbmSymmParams.from_flat(sr.sgd_update(ps.flat(), d, 0.05), n, 2)
     assert energies[-1] < energies[0]
     assert abs((energies[-1] - e0) / e0) < 2e-3
+
+
+@pytest.mark.parametrize("case", ["heis_chain12", "j1j2_4x4"])
+def test_marshall_rotated_hamiltonians_commute_with_translations(case):
+    """The symmetric ansatz suits the bench workloads: the Marshall-rotated
+    Heisenberg chain and J1-J2 square lattice commute with every lattice
+    translation in the S^z = 0 sector (N/2 even), so the ground state is
+    translation invariant."""
+    if case == "heis_chain12":
+        n = 12
+        op = W.heisenberg(n, W.chain_bonds(n), 1.0, True, W.sublattice(n))
+        perm = W.chain_translations(n)
+    else:
+        n = 16
+        op = W.j1j2(4, 1.0, 0.5, True)
+        perm = W.square_translations(4)
+    xs = hamiltonian.basis(n, True)
+    cf = hamiltonian.configs(xs, n)
+    h = hamiltonian.sparse_h(op, xs)
+    rng = np.random.default_rng(0)
+    v = rng.normal(size=len(xs)) + 1j * rng.normal(size=len(xs))
+    for g in perm[1:3]:
+        # (T v)(sigma) = v(sigma o g): configurations permuted by the translation
+        moved = cf[:, g]
+        ints = ((1 - moved.astype(np.int64)) // 2) @ (1 << np.arange(n))
+        at = np.searchsorted(xs, ints)
+        tv = v[at]
+        htv = h @ tv
+        th_v = (h @ v)[at]
+        assert np.allclose(htv, th_v, atol=1e-10)
