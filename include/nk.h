@@ -6,7 +6,8 @@
  * ---------------------------------------------------------------
  * - Pointers are DEVICE pointers, allocated and owned by the caller.  The
  *   library never allocates or frees device memory and never synchronises the
- *   stream inside a call (nk_operator_upload is the one exception and says so).
+ *   stream inside a call (nk_operator_upload and nk_symm_upload are the
+ *   exceptions and say so).
  * - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
  *   stream).  Argument errors are detected on the host and returned
  *   synchronously, with nothing enqueued.  A kernel launch failure returns
