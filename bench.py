@@ -28,6 +28,9 @@ sys.path.insert(0, ROOT)
 METRIC = "RBM-VMC samples/s and SR steps/s at N=400 vs plain FP32 GPU path; % roofline"
 
 
+T_START = time.perf_counter()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -45,6 +48,8 @@ def parse():
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp32-arm", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--phase-times", action="store_true",
+                    help="print the wall time of each bench phase to stderr")
     ap.add_argument("--checkpoint-iters", type=int, default=50,
                     help="also time the iteration after this many more SR iterations "
                          "(structured psi, realistic acceptance); 0 skips it")
@@ -230,7 +235,18 @@ def run_gpu(args):
     else:
         def make(pr, **kw):
             return VmcSr(w, params, sigma0, pr, **kw)
+    t_phase = [T_START]
+
+    def phase(name):
+        if args.phase_times:
+            torch.cuda.synchronize()
+            now = time.perf_counter()
+            print(f"[bench] {name}: {now - t_phase[0]:.2f} s", file=sys.stderr, flush=True)
+            t_phase[0] = now
+
+    phase("setup (imports, CUDA context, workload)")
     v = make(prec, graph=bool(args.graph), autotune=True)
+    phase("driver construction")
     wname = w.name + ("_symm" if symm else "")
     stream = torch.cuda.current_stream()
 
@@ -241,6 +257,7 @@ def run_gpu(args):
     for _ in range(args.warmup):
         v.step()
     barrier()
+    phase("warm-up (first step autotunes and captures)")
     # timed region: K whole iterations (CUDA-graph replays unless --graph 0)
     clocks = ClockSampler(local)
     barrier()
@@ -257,6 +274,7 @@ def run_gpu(args):
     barrier()
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in ev_it)
+    phase("timed steps and clock sampling")
     # per-stage breakdown (eager launches, CUDA events between the stages)
     stages = ["sample", "amplitudes", "energies", "sr"]
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
@@ -274,6 +292,7 @@ def run_gpu(args):
     ms_per_step = total_ms / args.steps
     value = R.aggregate_rate(w.n_samples, world, ms_per_step / 1e3)
 
+    phase("stage breakdown")
     # end to end through the public API: parameters H2D from pinned memory,
     # one iteration, the FP64 status block D2H, every step
     dev_params = v.param_tensors()
@@ -294,6 +313,7 @@ def run_gpu(args):
     e2e_ms = R.max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
     h2d = sum(h.numel() for h in host_params) * 8
 
+    phase("end to end")
     # the plain FP32 path on the same workload (for the mixed-precision ratio)
     fp32_arm = None
     if prec != nk.NK_PREC_FP32 and not args.no_fp32_arm:
@@ -314,6 +334,7 @@ def run_gpu(args):
     l2_note = (f"inputs larger than L2 (T = tanh theta is {t_bytes / 1e6:.0f} MB)" if t_bytes > 129e6
                else f"inputs smaller than L2 (T is {t_bytes / 1e6:.1f} MB); L2 flushed before each "
                     "timed iteration")
+    phase("FP32 arm")
     pk, pk_kind = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
     # proposals that needed a ratio: every flip; exchanges of two unequal spins
@@ -357,6 +378,7 @@ def run_gpu(args):
                                  else alu_src)})
     # the same measurement after more SR iterations: psi has structure and the
     # acceptance is the optimisation's, not the near-uniform initial one
+    phase("rooflines and ALU peaks")
     ckpt = None
     if args.checkpoint_iters > 0:
         for _ in range(args.checkpoint_iters):
@@ -379,6 +401,7 @@ def run_gpu(args):
                 "unit": "samples/s",
                 "ms_per_step": round(ck_ms, 3), "acceptance": round(info_ck["acceptance"], 4),
                 "energy": info_ck["energy"]}
+    phase("checkpoint iterations")
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
