@@ -24,6 +24,8 @@ Modules and the passages of the NetKet paper (arXiv:1904.00031) they follow:
                 nearest-neighbour exchange moves (Sec. 2.2.5; listing of Sec. 3.1).
 * ``tempering`` parallel tempering (replica exchange) of Metropolis chains over
                 |psi|^(2 beta) ladders (the sampler option named in Sec. 2.2.5).
+* ``supervised`` the negative log overlap loss of Eq. 1 (Sec. 2.2.3), its gradient
+                from samples of the target, and AdaMax (Kingma and Ba, Algorithm 2).
 * ``sr``        energy statistics, the SR system S delta = F solved exactly or by
                 conjugate gradient, and the SGD step alpha <- alpha - lambda delta
                 (Sec. 2.2.5; Eq. (2) of Sec. 2.2.3).
