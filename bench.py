@@ -235,6 +235,7 @@ def run_gpu(args):
     else:
         def make(pr, **kw):
             return VmcSr(w, params, sigma0, pr, **kw)
+
     t_phase = [T_START]
 
     def phase(name):
