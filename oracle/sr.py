@@ -15,22 +15,28 @@ The paper prints no SR formulas; this follows Sorella's SR, which it cites
   alpha <- alpha - lr * delta.
 For real parameters S and F are replaced by their real parts [r].
 Statistics [r]: E = <E_loc> (complex mean; Re E is the energy estimate),
-variance = <|E_loc - E|^2>, error bar from chain means m_c:
-sigma_E = sqrt(sum_c (Re m_c - Re E)^2 / (Nc (Nc - 1))).
+variance = <|E_loc - E|^2>, error bar from the means m_g of n_blocks equal blocks
+of consecutive samples that are independent of one another:
+sigma_E = sqrt(sum_g (Re m_g - Re E)^2 / (n_blocks (n_blocks - 1))).
+The chains of one proposal group share their proposal sequence (``sampler``),
+so they are not independent of one another; the independent units are whole
+groups, and the VMC iteration passes n_blocks = number of groups.
 """
 from __future__ import annotations
 
 import numpy as np
 
 
-def stats(eloc, n_chains: int):
-    """(mean, variance, error bar) of E_loc; samples are chain-major."""
+def stats(eloc, n_blocks: int):
+    """(mean, variance, error bar) of E_loc; samples are chain-major and the
+    error bar comes from the means of ``n_blocks`` equal blocks of consecutive
+    samples (independent units: chains, or proposal groups of chains)."""
     e = np.asarray(eloc, dtype=np.complex128)
     mean = e.mean()
     var = float(np.mean(np.abs(e - mean) ** 2))
-    m = e.reshape(n_chains, -1).mean(axis=1).real
-    if n_chains > 1:
-        err = float(np.sqrt(np.sum((m - mean.real) ** 2) / (n_chains * (n_chains - 1))))
+    m = e.reshape(n_blocks, -1).mean(axis=1).real
+    if n_blocks > 1:
+        err = float(np.sqrt(np.sum((m - mean.real) ** 2) / (n_blocks * (n_blocks - 1))))
     else:
         err = float("nan")
     return complex(mean), var, err

@@ -46,7 +46,9 @@ def vmc_sr_iteration(p: RbmParams, op, chains: ChainState, *, move: str, bonds, 
         nc = None
     eloc = local_energy.local_energy_rbm(p, op, samples)
     if weights is None:
-        mean, var, err = sr.stats(eloc, nc)
+        # independent units of the error bar: whole proposal groups
+        blocks = nc // group_size if nc % group_size == 0 else 1
+        mean, var, err = sr.stats(eloc, blocks)
     else:
         mean = complex(weights @ eloc)
         var = float(weights @ np.abs(eloc - mean) ** 2)

@@ -291,6 +291,36 @@ def test_stats_hand_example():
     assert abs(err - np.sqrt(((2 - 3) ** 2 + (4 - 3) ** 2) / 2)) < 1e-15
 
 
+@pytest.mark.parametrize("move", ["flip", "exchange"])
+def test_error_bar_matches_spread_over_independent_runs(move):
+    """The error bar of one iteration's mean energy, computed from the means of
+    whole proposal groups (the independent units of the sampler), must match the
+    standard deviation of that mean over independent runs (different seeds and
+    chain starts).  160 runs of 64 chains in 8 groups: the ratio of the two is
+    known to about 6 %; a wrong normalisation (e.g. n_blocks^2 for
+    n_blocks (n_blocks - 1)), a missing square root or per-sample errors that
+    ignore autocorrelation miss the band."""
+    n, nc, group, nd, spc = 8, 64, 8, 10, 8
+    sz = move == "exchange"
+    if sz:
+        op = W.heisenberg(n, W.chain_bonds(n), 1.0, True, W.sublattice(n))
+        p = W.perturb_params(W.init_params(n, 2 * n, True, 0.01, 5), 0.6 / np.sqrt(n), 6)
+    else:
+        op = W.ising(n, W.chain_bonds(n), h=1.0)
+        p = W.perturb_params(W.init_params(n, n, False, 0.01, 5), 0.6 / np.sqrt(n), 6)
+    means, errs = [], []
+    for run in range(160):
+        s0 = W.init_chains(nc, n, sz, 1000 + run)
+        samp, _, _, _ = sampler.metropolis(p, s0, move, W.chain_bonds(n), group, 7000 + run, 0, nd,
+                                           spc)
+        e = local_energy.local_energy_rbm(p, op, samp)
+        mean, _, err = sr.stats(e, nc // group)
+        means.append(mean.real)
+        errs.append(err)
+    ratio = np.std(means, ddof=1) / np.sqrt(np.mean(np.square(errs)))
+    assert 0.75 < ratio < 1.33, ratio
+
+
 # ---------------------------------------------------------------- sampler
 
 def test_zero_parameters_accept_every_flip():
