@@ -71,7 +71,8 @@ def oracle_sample(workload: str, n_chains: int, spc: int, n_cg: int) -> dict:
     samples, fin, cnt, nacc = sampler.metropolis(p, s0, w.move, w.sampler_bonds, w.group_size,
                                                  w.seed, 0, 1, spc)
     e = local_energy.local_energy_rbm(p, w.op, samples)
-    mean, var, err = sr.stats(e, n_chains)
+    blocks = n_chains // w.group_size if n_chains % w.group_size == 0 else 1
+    mean, var, err = sr.stats(e, blocks)
     sig, t = rbm.logderiv_factored(p, samples)
     real = not p.is_complex
     f = sr.force_lazy(sig, t, e, p.n, p.m, None, real)

@@ -111,7 +111,7 @@ typedef struct nk_operator {
 #define NK_INFO_E_RE 0     /* Re <E_loc>                                     */
 #define NK_INFO_E_IM 1     /* Im <E_loc>                                     */
 #define NK_INFO_VAR 2      /* <|E_loc - <E_loc>|^2>                          */
-#define NK_INFO_ERR 3      /* error bar from chain means (0 with weights)    */
+#define NK_INFO_ERR 3      /* error bar from block means (0 with weights)    */
 #define NK_INFO_CG_ITERS 4 /* CG iterations run                              */
 #define NK_INFO_CG_RESID 5 /* final ||r|| / ||F||                            */
 #define NK_INFO_F_NORM 6   /* ||F||                                          */
@@ -256,9 +256,12 @@ size_t nk_sr_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns)
  *   formed: conjugate gradient from x0 = 0, n_cg iterations unless
  *   ||r|| <= cg_rtol ||F|| first (decided on the device, no host sync),
  *   then alpha <- alpha - lr delta in the FP64 master and nk_rbm_prepare.
- * Real RBMs use Re S and Re F.  Samples are chain-major over n_chains chains
- * (for the error bar).  CG vectors and all reductions are FP64; the O and O^H
- * contractions run at `prec`.
+ * Real RBMs use Re S and Re F.  n_chains (>= 0, dividing ns) is the number of
+ * equal blocks of consecutive samples that are independent of one another, for
+ * the error bar NK_INFO_ERR (from the block means): with chain-major samples,
+ * the number of proposal groups (nk_chains.nc / nk_chains.group_size), since the
+ * chains of one group share their proposals; 0 or 1 gives no error bar.  CG
+ * vectors and all reductions are FP64; the O and O^H contractions run at `prec`.
  *   t        F32 [ns][m] tanh(theta) (nk_local_energy t_out or nk_logderiv)
  *   eloc     c128 [ns]
  *   info_out double [NK_INFO_LEN] (device)
@@ -282,7 +285,10 @@ nk_status nk_sr_step(nk_rbm* rbm, const int8_t* sigma, const void* t, const doub
  *   limit) return NK_ERR_SHAPE with nothing enqueued.
  *   The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make it before any
- *   stream capture.  All calls share the array: calls that overlap on the GPU
+ *   stream capture.  The address is cached per device ordinal for the primary
+ *   context (the runtime's): after cudaDeviceReset, or from another context
+ *   made current by the driver API, the cached address is stale; do not call
+ *   this entry point there.  All calls share the array: calls that overlap on the GPU
  *   race and must be serialised by the caller.  No memory is allocated or
  *   freed. */
 nk_status nk_sr_step_noalloc(nk_rbm* rbm, const int8_t* sigma, const void* t, const double* eloc,
@@ -367,7 +373,7 @@ typedef struct nk_sr_batch_item {
   const double* eloc;     /* c128 [ns]                                         */
   const double* weights;  /* F64 [ns] or NULL (1/ns)                           */
   int64_t ns;
-  int32_t n_chains;
+  int32_t n_chains;       /* blocks of the error bar, as for nk_sr_step        */
   int32_t reserved;       /* 0                                                 */
   void* scratch;          /* nk_sr_scratch_bytes(n, m, is_complex, ns) bytes,
                              256-B aligned (device), one per problem           */

@@ -37,7 +37,7 @@ class BatchedVmc:
             self.sr_args = (ws[0].diag_shift, ws[0].lr, ws[0].n_cg)
             self.srb = nk.SrBatch([
                 {"rbm": v.rbm, "sigma": v.samples, "t": v.t, "eloc": v.eloc,
-                 "scratch": v.scratch, "info": v.info_buf, "n_chains": v.w.n_chains}
+                 "scratch": v.scratch, "info": v.info_buf, "n_chains": v.blocks}
                 for v in self.items], prec=prec, device=device)
 
     @property

@@ -30,6 +30,13 @@ def centring_fused(ns: int, m: int, is_complex: bool) -> bool:
     return tiles * nseg <= 1024
 
 
+def error_blocks(n_chains: int, group_size: int) -> int:
+    """Independent units of the energy error bar: the chains of one proposal
+    group share their proposal sequence, so whole groups are the blocks (one
+    block, i.e. no error bar, when the chains do not split into whole groups)."""
+    return n_chains // group_size if n_chains % group_size == 0 else 1
+
+
 def adj_centres(m: int, is_complex: bool) -> bool:
     """Whether the SR adjoint centres the forward's output itself (at most four
     parameter tiles of 64 complex or 128 real hidden units)."""
@@ -52,6 +59,7 @@ class VmcSr:
         if sigma0 is None:
             sigma0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed)
         self.chains = nk.Chains(sigma0, w.group_size, w.seed, device, device_counter=graph)
+        self.blocks = error_blocks(w.n_chains, w.group_size)
         self.use_graph = graph
         self.graph = None
         self.autotune = autotune
@@ -92,7 +100,7 @@ class VmcSr:
                            self.eloc_scratch)
 
     def sr(self):
-        nk.nk_sr_step(self.rbm, self.samples, self.t, self.eloc, self.w.n_chains,
+        nk.nk_sr_step(self.rbm, self.samples, self.t, self.eloc, self.blocks,
                       self.w.diag_shift, self.w.lr, self.w.n_cg, 1e-12, self.prec,
                       scratch=self.scratch, info_out=self.info_buf)
 
@@ -182,7 +190,7 @@ class VmcSrSymm(VmcSr):
         return nk.sr_symm_scratch(self.sy, self.ns, device)
 
     def sr(self):
-        nk.nk_sr_step_symm(self.sy, self.samples, self.t, self.eloc, self.w.n_chains,
+        nk.nk_sr_step_symm(self.sy, self.samples, self.t, self.eloc, self.blocks,
                            self.w.diag_shift, self.w.lr, self.w.n_cg, 1e-12, self.prec,
                            scratch=self.scratch, info_out=self.info_buf)
 

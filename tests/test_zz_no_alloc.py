@@ -42,13 +42,17 @@ def _setup(nk, n, m, cplx, ns, seed):
 
 
 @pytest.mark.parametrize("cplx", [False, True])
-def test_noalloc_matches_caller_scratch_twice(nk, cplx):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_matches_caller_scratch_twice(nk, cplx, prec):
+    """Both precisions: the BF16 hi + lo path also places its sigma' planes, the
+    split direction and its tensor maps inside the built-in array."""
     n, m, ns, nc = 16, 32, 2048, 64
     (ra, rb), s, t, e = _setup(nk, n, m, cplx, ns, 5)
     scratch = nk.sr_scratch(ra, ns)
     for call in range(2):
-        ia = nk.info_dict(nk.nk_sr_step(ra, s, t, e, nc, 0.01, 0.05, 30, scratch=scratch))
-        ib = nk.info_dict(nk.nk_sr_step_noalloc(rb, s, t, e, nc, 0.01, 0.05, 30))
+        ia = nk.info_dict(nk.nk_sr_step(ra, s, t, e, nc, 0.01, 0.05, 30, prec=prec,
+                                        scratch=scratch))
+        ib = nk.info_dict(nk.nk_sr_step_noalloc(rb, s, t, e, nc, 0.01, 0.05, 30, prec=prec))
         torch.cuda.synchronize()
         for k in ("energy", "variance", "error", "cg_iters", "f_norm", "cg_resid"):
             assert ia[k] == pytest.approx(ib[k], rel=1e-12, abs=1e-300), (call, k)
