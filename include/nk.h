@@ -167,9 +167,10 @@ nk_status nk_rbm_prepare(const nk_rbm* rbm, void* stream);
 /* ln psi(sigma) for ns configurations (Sec. 2.2.2).
  *   sigma      int8 [ns][n]
  *   prec       NK_PREC_FP32 or NK_PREC_BF16X2 (theta = W sigma + b contraction)
- *   logpsi_out c128 [ns]
+ *   logpsi_out c128 [ns], or NULL to compute theta only (no ln cosh; the local
+ *              energies of a VMC iteration need theta, not ln psi)
  *   theta_out  F32 [ns][m] theta of every configuration, or NULL
- * ns = 0 is a no-op. */
+ * At least one of logpsi_out and theta_out must be given.  ns = 0 is a no-op. */
 nk_status nk_rbm_logpsi(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int32_t prec,
                         double* logpsi_out, void* theta_out, void* stream);
 
@@ -304,6 +305,45 @@ nk_status nk_sr_step_noalloc(nk_rbm* rbm, const int8_t* sigma, const void* t, co
 nk_status nk_sr_tune(nk_rbm* rbm, const int8_t* sigma, const void* t, int64_t ns, int32_t prec,
                      void* scratch, size_t scratch_bytes, void* stream);
 
+/* ------------------------------------------------------ supervised learning */
+
+/* Scratch bytes nk_supervised_step needs for ns samples. */
+size_t nk_supervised_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns);
+
+/* One step of supervised learning of a target wavefunction (Sec. 2.2.3): the
+ * negative log overlap of Eq. 1, L = -log(|<tar|psi>|^2 / (<tar|tar><psi|psi>)),
+ * estimated from samples sigma_s of |tar|^2 as L = -log(|<R>|^2 / <|R|^2>) with
+ * R_s = psi(sigma_s) / tar(sigma_s) and <X> = sum_s w_s X_s / sum_s w_s; its
+ * gradient 2 dL/d conj(alpha) = sum_s conj(O_sk) g_s with
+ * g_s = 2 w_s (|R_s|^2 / <|R|^2> - conj(R_s) / conj(<R>)) / sum w (the analytic
+ * log-derivatives O of Sec. 2.2.5; for real parameters its real part, which is
+ * dL/dalpha); then, if `moments` is given, one AdaMax update (the optimiser
+ * list of Sec. 2.2.3; Kingma and Ba, Algorithm 2) of the FP64 master and
+ * nk_rbm_prepare.  AdaMax treats the real and imaginary parts of a complex
+ * parameter as two real parameters, in the master layout a | b | W:
+ *   m <- beta1 m + (1 - beta1) g, u <- max(beta2 u, |g|),
+ *   x <- x - lr / (1 - beta1^step) m / u   (a component with u = 0 does not move).
+ *   sigma       int8 [ns][n] samples of |tar|^2
+ *   log_target  c128 [ns] ln tar(sigma_s) (any branch of the complex log)
+ *   weights     F64 [ns] sample weights, or NULL (equal weights)
+ *   prec        contraction precision of ln psi and of the gradient
+ *   lr, beta1, beta2, step  AdaMax step size, moment decays, 1-based step count
+ *   moments     F64 [2][Pr] (m then u), Pr = P (real) or 2 P (complex), zeroed
+ *               by the caller before step 1; NULL: loss and gradient only
+ *   grad_out    F64 [P] or c128 [P] gradient (a | b | W order), or NULL
+ *   scratch     nk_supervised_scratch_bytes(n, m, is_complex, ns) bytes, 256-B
+ *               aligned
+ *   info_out    double [4] (device) or NULL: L, the overlap |<R>|^2 / <|R|^2>
+ *               (= exp(-L)), the shift c of the ratios R = exp(ln psi - ln tar - c)
+ *               (c = max Re, which keeps them finite; L and g do not depend on it),
+ *               flags (bit 1 << NK_ERR_NONFINITE).
+ * Reductions run in a fixed order: a step is bitwise reproducible. */
+nk_status nk_supervised_step(nk_rbm* rbm, const int8_t* sigma, const double* log_target,
+                             const double* weights, int64_t ns, int32_t prec, double lr,
+                             double beta1, double beta2, int32_t step, double* moments,
+                             double* grad_out, void* scratch, size_t scratch_bytes,
+                             double* info_out, void* stream);
+
 /* ------------------------------------------- batches of independent instances */
 
 /* Many independent RBMs (uneven n, m, field, sample counts) in one call each
@@ -404,16 +444,21 @@ nk_status nk_sr_step_batch(const nk_sr_batch_item* items, int32_t n_inst,
                            const void* desc_dev, double diag_shift, double lr, int32_t n_cg,
                            double cg_rtol, int32_t prec, void* stream);
 
-/* Scratch bytes nk_rbm_logpsi_backward needs for ns samples. */
+/* Scratch bytes nk_rbm_logpsi_backward needs for ns samples: one chunk of at
+ * most 16384 samples (tanh(theta) of the chunk and the adjoint's buffers), so it
+ * stops growing with ns beyond that. */
 size_t nk_backward_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns);
 
 /* Backward of ln psi (the analytic derivatives of Sec. 2.2.5 contracted with
  * an upstream gradient): grad_k = sum_s conj(O_sk) g_s (PyTorch's convention
- * for a holomorphic function), theta recomputed from sigma.
+ * for a holomorphic function).  theta is recomputed from sigma chunk by chunk
+ * (16384 samples at most), never stored for all ns: per chunk the theta
+ * contraction writes tanh(theta) at `prec`, the adjoint contraction sums over
+ * the chunk, and the chunk sums are added in FP64 in chunk order.
  *   g           c128 [ns]
  *   grad_out    F64 [P]
  *   scratch     nk_backward_scratch_bytes(n, m, is_complex, ns) bytes, 256-B
- *               aligned (holds theta and tanh(theta) of the ns configurations) */
+ *               aligned */
 nk_status nk_rbm_logpsi_backward(const nk_rbm* rbm, const int8_t* sigma, int64_t ns,
                                  const double* g, double* grad_out, int32_t prec, void* scratch,
                                  size_t scratch_bytes, void* stream);

@@ -291,7 +291,8 @@ static nk_status logpsi_call(const nk_rbm* rbm, const int8_t* sigma, int64_t ns,
   if (prec != NK_PREC_FP32 && prec != NK_PREC_BF16X2)
     return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi: unknown precision %d", prec);
   if (ns == 0) return NK_OK;
-  if (!sigma || !logpsi_out) return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi: NULL pointer");
+  if (!sigma || (!logpsi_out && !theta_out))
+    return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi: NULL pointer");
   if (prec == NK_PREC_BF16X2 && !tc_supported_shape(rbm->n, rbm->m))
     return fail(NK_ERR_UNSUPPORTED, "nk_rbm_logpsi: the tensor-core path supports n + 1 <= 448");
   if (dry) return NK_OK;
@@ -643,6 +644,36 @@ nk_status nk_rbm_logpsi_backward(const nk_rbm* rbm, const int8_t* sigma, int64_t
     return fail(NK_ERR_INVALID_ARG, "nk_rbm_logpsi_backward: unknown precision %d", prec);
   return run_backward(rbm, sigma, ns, g, grad_out, prec, scratch, scratch_bytes,
                       (cudaStream_t)stream);
+}
+
+size_t nk_supervised_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns) {
+  if (n < 1 || m < 1 || ns < 1) return 0;
+  return supervised_scratch_bytes(n, m, is_complex ? 1 : 0, ns);
+}
+
+nk_status nk_supervised_step(nk_rbm* rbm, const int8_t* sigma, const double* log_target,
+                             const double* weights, int64_t ns, int32_t prec, double lr,
+                             double beta1, double beta2, int32_t step, double* moments,
+                             double* grad_out, void* scratch, size_t scratch_bytes,
+                             double* info_out, void* stream) {
+  if (nk_status e = check_rbm(rbm, "nk_supervised_step")) return e;
+  if (ns < 1) return fail(NK_ERR_INVALID_ARG, "nk_supervised_step: ns < 1");
+  if (!sigma || !log_target || !scratch)
+    return fail(NK_ERR_INVALID_ARG, "nk_supervised_step: NULL pointer");
+  if (((uintptr_t)scratch) & 255)
+    return fail(NK_ERR_INVALID_ARG, "nk_supervised_step: scratch not 256-byte aligned");
+  if (prec != NK_PREC_FP32 && prec != NK_PREC_BF16X2)
+    return fail(NK_ERR_INVALID_ARG, "nk_supervised_step: unknown precision %d", prec);
+  if (prec == NK_PREC_BF16X2 && !tc_supported_shape(rbm->n, rbm->m))
+    return fail(NK_ERR_UNSUPPORTED, "nk_supervised_step: the tensor-core path supports n + 1 <= 448");
+  if (moments && (step < 1 || !(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) ||
+                  !(beta2 >= 0.0 && beta2 <= 1.0)))
+    return fail(NK_ERR_INVALID_ARG,
+                "nk_supervised_step: AdaMax needs step >= 1, lr >= 0, 0 <= beta1 < 1, "
+                "0 <= beta2 <= 1");
+  return run_supervised_step(rbm, sigma, log_target, weights, ns, prec, lr, beta1, beta2, step,
+                             moments, grad_out, scratch, scratch_bytes, info_out,
+                             (cudaStream_t)stream);
 }
 
 nk_status nk_query_status(int32_t* flags, void* stream) {

@@ -30,10 +30,11 @@ nk_status collect_status_api(int32_t* out, cudaStream_t st);
 nk_status measure_alu_peaks(double* out, cudaStream_t st);
 
 // theta = W sigma + b and ln psi; theta_out may be null.
+// logpsi may be null (then only theta_out and / or t_out = tanh(theta) are written).
 nk_status launch_logpsi_fp32(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,
-                             void* theta_out, cudaStream_t st);
+                             void* theta_out, cudaStream_t st, void* t_out = nullptr);
 nk_status launch_logpsi_bf16(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,
-                             void* theta_out, cudaStream_t st);
+                             void* theta_out, cudaStream_t st, void* t_out = nullptr);
 
 nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int32_t* bi,
                             const int32_t* bk, int nb, int n_discard, int n_samples,
@@ -105,5 +106,12 @@ nk_status run_sr_step_batch(const nk_sr_batch_item* items, int n_inst, const voi
 nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const double* g,
                        double* grad, int prec, void* scratch, size_t scratch_bytes,
                        cudaStream_t st);
+// Supervised learning (Eq. 1 loss, its gradient, AdaMax): supervised.cu
+size_t supervised_scratch_bytes(int n, int m, int cplx, int64_t ns);
+nk_status run_supervised_step(nk_rbm* r, const int8_t* sigma, const double* log_target,
+                              const double* weights, int64_t ns, int prec, double lr,
+                              double beta1, double beta2, int step, double* moments,
+                              double* grad_out, void* scratch, size_t scratch_bytes,
+                              double* info, cudaStream_t st);
 
 }  // namespace nk

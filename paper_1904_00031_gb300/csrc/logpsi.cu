@@ -3,6 +3,9 @@
 // ln cosh activation).  theta is computed as the augmented contraction
 // [W | b] [sigma; 1] on the CUDA cores, ln cosh is fused into the epilogue and
 // summed per sample in FP64; a . sigma is added in FP64 from the master a.
+// Without a ln psi output the epilogue only stores theta and / or tanh(theta)
+// (the local energies need theta; the backward recomputes tanh(theta) per
+// chunk of samples).
 #include "common.cuh"
 #include "internal.h"
 #include "sgemm.cuh"
@@ -15,9 +18,10 @@ struct LogpsiEpi {
   int m, n;
   int64_t ns;
   F* theta_out;            // [ns][m] or null
+  F* t_out;                // [ns][m] tanh(theta) or null
   const double* a;         // master a (F64)
   const int8_t* sigma;
-  double* logpsi;          // c128 [ns]
+  double* logpsi;          // c128 [ns], or null: theta / tanh(theta) only, no ln cosh
 
   __device__ __forceinline__ void tile(float (&ar)[4][4], float (&ai)[4][4], int64_t sb, int jb,
                                        double2 (&part)[4]) {
@@ -31,13 +35,20 @@ struct LogpsiEpi {
         int j = jb + 16 * q;
         if (j >= m) continue;
         if constexpr (CPLX) {
-          cf l = lncosh_c(cf{ar[p][q], ai[p][q]});
-          lr += l.x;
-          li += l.y;
+          if (logpsi) {
+            cf l = lncosh_c(cf{ar[p][q], ai[p][q]});
+            lr += l.x;
+            li += l.y;
+          }
           if (theta_out) theta_out[s * m + j] = make_float2(ar[p][q], ai[p][q]);
+          if (t_out) {
+            cf t = tanh_c(cf{ar[p][q], ai[p][q]});
+            t_out[s * m + j] = make_float2(t.x, t.y);
+          }
         } else {
-          lr += lncosh_f(ar[p][q]);
+          if (logpsi) lr += lncosh_f(ar[p][q]);
           if (theta_out) theta_out[s * m + j] = ar[p][q];
+          if (t_out) t_out[s * m + j] = tanh_f(ar[p][q]);
         }
       }
       part[p].x += (double)lr;
@@ -46,6 +57,7 @@ struct LogpsiEpi {
   }
 
   __device__ __forceinline__ void finish(int64_t s, double2 v) {
+    if (!logpsi) return;
     double vr = 0.0, vi = 0.0;
     const int8_t* sg = sigma + s * n;
     for (int i = 0; i < n; ++i) {
@@ -67,12 +79,14 @@ __global__ void __launch_bounds__(kSgThreads) logpsi_fp32_kernel(const int8_t* _
                                                                  int64_t ns, int n, int m,
                                                                  const void* __restrict__ xw,
                                                                  int rows, const double* a,
-                                                                 double* logpsi, void* theta_out) {
+                                                                 double* logpsi, void* theta_out,
+                                                                 void* t_out) {
   LogpsiEpi<CPLX> epi;
   epi.m = m;
   epi.n = n;
   epi.ns = ns;
   epi.theta_out = reinterpret_cast<typename SgTypes<CPLX>::F*>(theta_out);
+  epi.t_out = reinterpret_cast<typename SgTypes<CPLX>::F*>(t_out);
   epi.a = a;
   epi.sigma = sigma;
   epi.logpsi = logpsi;
@@ -80,16 +94,16 @@ __global__ void __launch_bounds__(kSgThreads) logpsi_fp32_kernel(const int8_t* _
 }
 
 nk_status launch_logpsi_fp32(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,
-                             void* theta_out, cudaStream_t st) {
+                             void* theta_out, cudaStream_t st, void* t_out) {
   WsLayout L(r->n, r->m, r->is_complex);
   const char* ws = (const char*)r->ws;
   int64_t blocks = (ns + kSgBS - 1) / kSgBS;
   if (r->is_complex)
     logpsi_fp32_kernel<true><<<(unsigned)blocks, kSgThreads, 0, st>>>(
-        sigma, ns, r->n, r->m, ws + L.xw, r->m, r->a, logpsi, theta_out);
+        sigma, ns, r->n, r->m, ws + L.xw, r->m, r->a, logpsi, theta_out, t_out);
   else
     logpsi_fp32_kernel<false><<<(unsigned)blocks, kSgThreads, 0, st>>>(
-        sigma, ns, r->n, r->m, ws + L.xw, r->m, r->a, logpsi, theta_out);
+        sigma, ns, r->n, r->m, ws + L.xw, r->m, r->a, logpsi, theta_out, t_out);
   return check_launch("nk_rbm_logpsi");
 }
 

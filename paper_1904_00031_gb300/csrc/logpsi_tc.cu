@@ -1,13 +1,14 @@
 // K1 (tensor-core path): theta = [W | b] [sigma; 1] on the tensor cores (W | b
 // split into BF16 hi + lo planes by nk_rbm_prepare, sigma exact in BF16, FP32
 // accumulation in TMEM), ln cosh fused into the epilogue and summed per
-// configuration in FP64, a . sigma added in FP64 (Sec. 2.2.2, RbmSpin).
+// configuration in FP64, a . sigma added in FP64 (Sec. 2.2.2, RbmSpin).  With
+// logpsi NULL the epilogue only stores theta and / or tanh(theta).
 #include "tc.cuh"
 
 namespace nk {
 
 nk_status launch_logpsi_bf16(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,
-                             void* theta_out, cudaStream_t st) {
+                             void* theta_out, cudaStream_t st, void* t_out) {
   WsLayout L(r->n, r->m, r->is_complex);
   FwdTcArgs A{};
   A.sigma = sigma;
@@ -22,6 +23,7 @@ nk_status launch_logpsi_bf16(const nk_rbm* r, const int8_t* sigma, int64_t ns, d
   A.a = r->a;
   A.logpsi = logpsi;
   A.theta_out = theta_out;
+  A.t_out = t_out;
   return launch_fwd_tc(A, (const char*)r->ws + L.wbf, st);
 }
 

@@ -1836,12 +1836,26 @@ nk_status run_sr_tune(nk_rbm* r, const int8_t* sigma, const void* t, int64_t ns,
 }
 
 // ------------------------------------------------------------------ K8 backward
+// grad_k = sum_s conj(O_sk) g_s (analytic RBM log-derivatives, Sec. 2.2.5) over
+// chunks of at most kBackChunk samples: per chunk, T = tanh(theta) is
+// recomputed from sigma (the theta contraction of ln psi with a tanh epilogue
+// and no ln cosh), the adjoint contraction writes its split-K partials, the
+// partials are reduced over splits (fixed order) and the chunk's sum is added
+// to an FP64 accumulator in chunk order.  Scratch holds one chunk's T and the
+// adjoint's buffers for one chunk: it does not grow with ns beyond kBackChunk.
+
+constexpr int64_t kBackChunk = 16384;
+
+static int64_t backward_chunk(int64_t ns) {
+  return std::min<int64_t>(std::max<int64_t>(ns, 1), kBackChunk);
+}
 
 size_t backward_scratch_bytes(int n, int m, int cplx, int64_t ns) {
-  SrLayout L(n, m, cplx, ns);
-  size_t f = cplx ? 8 : 4;
-  return L.total + 2 * (size_t)round_up(std::max<int64_t>(ns, 1) * m * f, 256) +
-         (size_t)round_up(std::max<int64_t>(ns, 1) * 16, 256);
+  const int64_t c = backward_chunk(ns);
+  SrLayout L(n, m, cplx, c);
+  const size_t f = cplx ? 8 : 4;
+  return L.total + (size_t)round_up(c * m * f, 256) +
+         (size_t)round_up(L.pa * (cplx ? 16 : 8), 256);
 }
 
 template <bool CPLX>
@@ -1853,6 +1867,72 @@ __global__ void copy_g_kernel(const double* g, void* v, int64_t ns) {
   }
 }
 
+// acc = x (first chunk) or acc + x
+template <bool CPLX>
+__global__ void accumulate_kernel(void* accv, const void* xv, int64_t pa, int first) {
+  using DT = typename D<CPLX>::T;
+  DT* acc = reinterpret_cast<DT*>(accv);
+  const DT* x = reinterpret_cast<const DT*>(xv);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < pa;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (first) {
+      acc[e] = x[e];
+    } else if constexpr (CPLX) {
+      acc[e] = make_double2(acc[e].x + x[e].x, acc[e].y + x[e].y);
+    } else {
+      acc[e] += x[e];
+    }
+  }
+}
+
+template <bool CPLX>
+static nk_status backward_t(const nk_rbm* r, const int8_t* sigma, int64_t ns, const double* g,
+                            double* grad, int prec, char* sc, cudaStream_t st) {
+  const int64_t chunk = backward_chunk(ns);
+  SrLayout L(r->n, r->m, CPLX, chunk);
+  const size_t f = CPLX ? 8 : 4;
+  char* T = sc + L.total;
+  char* acc = T + round_up(chunk * r->m * f, 256);
+  const bool tc = prec == NK_PREC_BF16X2;
+  const int splits = sr_choose_splits(L, prec, r->sr_splits);
+  const int64_t corner = (int64_t)r->m * L.na + r->n;
+  const int64_t nchunks = (ns + chunk - 1) / chunk;
+  for (int64_t k = 0; k < nchunks; ++k) {
+    const int64_t c0 = k * chunk, cn = std::min<int64_t>(chunk, ns - c0);
+    const int8_t* sg = sigma + c0 * r->n;
+    const int sp = (int)std::max<int64_t>(1, std::min<int64_t>(splits, (cn + 63) / 64));
+    nk_status e = tc ? launch_logpsi_bf16(r, sg, cn, nullptr, nullptr, st, T)
+                     : launch_logpsi_fp32(r, sg, cn, nullptr, nullptr, st, T);
+    if (e) return e;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((cn + 255) / 256, 1024));
+    copy_g_kernel<CPLX><<<(unsigned)blocks, 256, 0, st>>>(g + 2 * c0, sc + L.v, cn);
+    if (tc) {
+      if ((e = launch_sigma_t(sg, cn, r->n, L.na64, sc + L.sigt, st))) return e;
+      AdjTcArgs aa{};
+      aa.T = T;
+      aa.v = sc + L.v;
+      aa.ns = cn;
+      aa.n = r->n;
+      aa.m = r->m;
+      aa.cplx = CPLX;
+      aa.na64 = L.na64;
+      aa.splits = sp;
+      aa.part = sc + L.part;
+      if ((e = launch_adj_tc(aa, sc + L.sigt, st))) return e;
+    } else {
+      launch_adjoint_fp32<CPLX>(sg, T, sc + L.v, cn, r->n, r->m, sp, sc + L.part, nullptr, st);
+    }
+    reduce_parts_kernel<CPLX><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(
+        sc + L.part, sp, L.pa, corner, sc + L.x, nullptr, 0.0, nullptr, nullptr);
+    if (nchunks > 1)
+      accumulate_kernel<CPLX><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(acc, sc + L.x, L.pa,
+                                                                           k == 0 ? 1 : 0);
+  }
+  scatter_grad_kernel<CPLX><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(
+      nchunks > 1 ? acc : sc + L.x, r->n, r->m, grad);
+  return check_launch("nk_rbm_logpsi_backward");
+}
+
 nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const double* g,
                        double* grad, int prec, void* scratch, size_t scratch_bytes,
                        cudaStream_t st) {
@@ -1860,59 +1940,8 @@ nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const d
   if (scratch_bytes < need)
     return fail(NK_ERR_SHAPE, "nk_rbm_logpsi_backward: scratch of %zu B, need %zu B",
                 scratch_bytes, need);
-  SrLayout L(r->n, r->m, r->is_complex, ns);
-  char* sc = (char*)scratch;
-  size_t f = r->is_complex ? 8 : 4;
-  char* theta = sc + L.total;
-  char* T = theta + round_up(std::max<int64_t>(ns, 1) * r->m * f, 256);
-  char* lp = T + round_up(std::max<int64_t>(ns, 1) * r->m * f, 256);
-  nk_status e = prec == NK_PREC_BF16X2
-                    ? launch_logpsi_bf16(r, sigma, ns, (double*)lp, theta, st)
-                    : launch_logpsi_fp32(r, sigma, ns, (double*)lp, theta, st);
-  if (e) return e;
-  if ((e = launch_logderiv(r, sigma, theta, ns, NK_LAYOUT_FACTORED, T, st))) return e;
-  int64_t blocks = std::min<int64_t>((ns + 255) / 256, 1024);
-  if (blocks < 1) blocks = 1;
-  const bool tc = prec == NK_PREC_BF16X2;
-  const int splits = sr_choose_splits(L, prec, r->sr_splits);
-  if (tc) {
-    if ((e = launch_sigma_t(sigma, ns, r->n, L.na64, sc + L.sigt, st))) return e;
-  }
-  AdjTcArgs aa{};
-  aa.T = T;
-  aa.v = sc + L.v;
-  aa.ns = ns;
-  aa.n = r->n;
-  aa.m = r->m;
-  aa.cplx = r->is_complex;
-  aa.na64 = L.na64;
-  aa.splits = splits;
-  aa.part = sc + L.part;
-  const int64_t corner = (int64_t)r->m * L.na + r->n;
-  if (r->is_complex) {
-    copy_g_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(g, sc + L.v, ns);
-    if (tc) {
-      if ((e = launch_adj_tc(aa, sc + L.sigt, st))) return e;
-    } else {
-      launch_adjoint_fp32<true>(sigma, T, sc + L.v, ns, r->n, r->m, splits, sc + L.part, nullptr,
-                                st);
-    }
-    reduce_parts_kernel<true><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(
-        sc + L.part, splits, L.pa, corner, sc + L.x, nullptr, 0.0, nullptr, nullptr);
-    scatter_grad_kernel<true><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(sc + L.x, r->n, r->m, grad);
-  } else {
-    copy_g_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(g, sc + L.v, ns);
-    if (tc) {
-      if ((e = launch_adj_tc(aa, sc + L.sigt, st))) return e;
-    } else {
-      launch_adjoint_fp32<false>(sigma, T, sc + L.v, ns, r->n, r->m, splits, sc + L.part, nullptr,
-                                 st);
-    }
-    reduce_parts_kernel<false><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(
-        sc + L.part, splits, L.pa, corner, sc + L.x, nullptr, 0.0, nullptr, nullptr);
-    scatter_grad_kernel<false><<<sr_vec_blocks(L.pa), kVecThreads, 0, st>>>(sc + L.x, r->n, r->m, grad);
-  }
-  return check_launch("nk_rbm_logpsi_backward");
+  return r->is_complex ? backward_t<true>(r, sigma, ns, g, grad, prec, (char*)scratch, st)
+                       : backward_t<false>(r, sigma, ns, g, grad, prec, (char*)scratch, st);
 }
 
 }  // namespace nk

@@ -468,6 +468,7 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
       float pr = 0.f, pi = 0.f;
       if constexpr (CPLX) {
         float2* th = reinterpret_cast<float2*>(A.theta_out);
+        float2* tt = reinterpret_cast<float2*>(A.t_out);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           float2 tc[16];
@@ -488,16 +489,23 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
             for (int e = 0; e < 16; ++e) {
               const int j = j0 + c * 16 + e;
               if (j < A.m) {
-                cf l = lncosh_c(cf{ur[e], ui[e]});
-                pr += l.x;
-                pi += l.y;
+                if (A.logpsi) {
+                  cf l = lncosh_c(cf{ur[e], ui[e]});
+                  pr += l.x;
+                  pi += l.y;
+                }
                 if (th) th[s * A.m + j] = make_float2(ur[e], ui[e]);
+                if (tt) {
+                  cf t = tanh_c(cf{ur[e], ui[e]});
+                  tt[s * A.m + j] = make_float2(t.x, t.y);
+                }
               }
             }
           }
         }
       } else {
         float* th = reinterpret_cast<float*>(A.theta_out);
+        float* tt = reinterpret_cast<float*>(A.t_out);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           float tc[16];
@@ -513,8 +521,9 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
             for (int e = 0; e < 16; ++e) {
               const int j = j0 + c * 16 + e;
               if (j < A.m) {
-                pr += lncosh_f(u[e]);
+                if (A.logpsi) pr += lncosh_f(u[e]);
                 if (th) th[s * A.m + j] = u[e];
+                if (tt) tt[s * A.m + j] = tanh_f(u[e]);
               }
             }
           }
@@ -527,7 +536,7 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
       if (lane == 0) mbar_arrive(&tempty[acc]);
       if (PREFETCH && A.mode == 0 && jt + 1 < jt_end) load_t(jt + 1);
     }
-    if (live) {
+    if (live && (A.mode == 0 || A.logpsi)) {
       if (bad) sr = si = __longlong_as_double(0x7ff8000000000000ll);  // NaN marks a timeout
       // split launches: two addends onto an exact zero (y, ln psi zeroed by the
       // launcher), so the sum does not depend on which half lands first
@@ -637,7 +646,7 @@ nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st)
   const int64_t blocks = (A.ns + 127) / 128;
   FwdTcArgs B = A;
   B.nseg = fwd_tc_nseg(A.ns, A.mt, A.mode, sig_tma);
-  if (B.nseg == 2) {
+  if (B.nseg == 2 && (A.mode == 0 || A.logpsi)) {
     void* out = A.mode == 0 ? A.y : (void*)A.logpsi;
     const size_t per = (A.mode == 1 || A.cplx) ? 16 : 8;
     if (cudaMemsetAsync(out, 0, (size_t)A.ns * per, st) != cudaSuccess)

@@ -49,8 +49,9 @@ struct FwdTcArgs {
   const void* T;          // mode 0
   void* y;                // mode 0: F64 [ns]
   const double* a;        // mode 1: master a
-  double* logpsi;         // mode 1
+  double* logpsi;         // mode 1 (may be null: no ln cosh, theta / tanh theta only)
   void* theta_out;        // mode 1 (may be null)
+  void* t_out = nullptr;  // mode 1: tanh(theta) [ns][m] (may be null)
   const double* skip;     // if non-null and *skip != 0, the kernel returns at once
   int* err;               // set on a timed-out wait (may be null)
   int nseg = 1;           // set by launch_fwd_tc: 1, or 2 halves of the hidden tiles

@@ -40,7 +40,7 @@ EXPORTS = (
     "nk_query_status", "nk_debug_bounded_wait", "nk_measure_alu_peaks",
     "nk_batch_logpsi", "nk_batch_sweep", "nk_batch_local_energy",
     "nk_symm_tables_bytes", "nk_symm_upload", "nk_symm_expand", "nk_sr_symm_scratch_bytes",
-    "nk_sr_step_symm", "nk_symm_build",
+    "nk_sr_step_symm", "nk_symm_build", "nk_supervised_scratch_bytes", "nk_supervised_step",
 )
 NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
@@ -147,6 +147,8 @@ def load_library(path: str = LIB_PATH):
         "nk_symm_expand": (I32, [P, P, P]),
         "nk_sr_symm_scratch_bytes": (SZ, [I32, I32, I32, I32, I64]),
         "nk_sr_step_symm": (I32, [P, P, P, P, P, P, I64, I32, D, D, I32, D, I32, P, SZ, P, P]),
+        "nk_supervised_scratch_bytes": (SZ, [I32, I32, I32, I64]),
+        "nk_supervised_step": (I32, [P, P, P, P, I64, I32, D, D, D, I32, P, P, P, SZ, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -267,6 +269,15 @@ def nk_rbm_logpsi(rbm: Rbm, sigma, prec=NK_PREC_FP32, logpsi_out=None, theta_out
     _check(load_library().nk_rbm_logpsi(rbm.struct(), _ptr(sigma), ns, prec, _ptr(logpsi_out),
                                         _ptr(theta_out), _stream(stream)), "nk_rbm_logpsi")
     return logpsi_out
+
+
+def nk_rbm_theta(rbm: Rbm, sigma, theta_out, prec=NK_PREC_FP32, stream=None):
+    """theta = W sigma + b only ([ns, m] F32 into ``theta_out``): nk_rbm_logpsi
+    with a NULL ln psi output, which skips the ln cosh epilogue."""
+    _require_gpu(sigma, theta_out)
+    _check(load_library().nk_rbm_logpsi(rbm.struct(), _ptr(sigma), sigma.shape[0], prec, None,
+                                        _ptr(theta_out), _stream(stream)), "nk_rbm_logpsi")
+    return theta_out
 
 
 class Chains:
@@ -462,6 +473,30 @@ def nk_sr_step_noalloc(rbm: Rbm, sigma, t, eloc, n_chains: int, diag_shift: floa
         rbm.struct(), _ptr(sigma), _ptr(t), _ptr(eloc), _ptr(weights), ns, n_chains,
         float(diag_shift), float(lr), int(n_cg), float(cg_rtol), prec, _ptr(info_out),
         _stream(stream)), "nk_sr_step_noalloc")
+    return info_out
+
+
+def supervised_scratch(rbm: Rbm, ns: int, device="cuda"):
+    nb = load_library().nk_supervised_scratch_bytes(rbm.n, rbm.m, int(rbm.is_complex), ns)
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def nk_supervised_step(rbm: Rbm, sigma, log_target, prec=NK_PREC_FP32, lr: float = 1e-3,
+                       beta1: float = 0.9, beta2: float = 0.999, step: int = 1, moments=None,
+                       grad_out=None, weights=None, scratch=None, info_out=None, stream=None):
+    """One supervised step (loss of Eq. 1, its gradient, AdaMax if ``moments``);
+    returns the info tensor [loss, overlap, shift, flags]."""
+    _require_gpu(sigma, log_target, weights, moments, grad_out, scratch, info_out)
+    ns = sigma.shape[0]
+    if scratch is None:
+        scratch = supervised_scratch(rbm, ns, sigma.device)
+    if info_out is None:
+        info_out = torch.zeros(4, dtype=torch.float64, device=sigma.device)
+    lt = log_target.to(torch.complex128).contiguous()
+    _check(load_library().nk_supervised_step(
+        rbm.struct(), _ptr(sigma), _ptr(lt), _ptr(weights), ns, prec, float(lr), float(beta1),
+        float(beta2), int(step), _ptr(moments), _ptr(grad_out), _ptr(scratch), scratch.numel(),
+        _ptr(info_out), _stream(stream)), "nk_supervised_step")
     return info_out
 
 

@@ -1,6 +1,6 @@
 """One VMC + SR iteration (Sec. 2.2.5) driven through the C ABI:
 
-    nk_metropolis_sweep -> nk_rbm_logpsi (theta, ln psi) -> nk_local_energy
+    nk_metropolis_sweep -> nk_rbm_logpsi (theta only) -> nk_local_energy
     (E_loc and T = tanh theta) -> nk_sr_step (statistics, force, lazy CG, update)
 
 All buffers are allocated once; a step launches only library kernels and does
@@ -93,7 +93,9 @@ class VmcSr:
                                self.n_acc, self.metro_scratch)
 
     def amplitudes(self):
-        nk.nk_rbm_logpsi(self.rbm, self.samples, self.prec, self.logpsi, self.theta)
+        """theta = W sigma + b of the samples (the local energies and T need theta;
+        the iteration consumes no ln psi, so the ln cosh epilogue is skipped)."""
+        nk.nk_rbm_theta(self.rbm, self.samples, self.theta, self.prec)
 
     def energies(self):
         nk.nk_local_energy(self.rbm, self.op, self.samples, self.theta, self.eloc, self.t,

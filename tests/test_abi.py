@@ -49,7 +49,12 @@ def test_status_strings_and_sizes(lib):
     b = lib.nk_rbm_workspace_bytes(400, 1600, 0)
     assert a > b > 400 * 1600 * 4
     assert lib.nk_sr_scratch_bytes(40, 80, 1, 16384) > 41 * 81 * 16 * 4
-    assert lib.nk_backward_scratch_bytes(40, 80, 1, 16384) > 16384 * 80 * 8 * 2
+    # backward: one chunk of at most 16384 samples (tanh theta and the adjoint's
+    # buffers), not all ns
+    assert lib.nk_backward_scratch_bytes(40, 80, 1, 16384) > 16384 * 80 * 8
+    assert lib.nk_backward_scratch_bytes(400, 1600, 1, 65536) == \
+        lib.nk_backward_scratch_bytes(400, 1600, 1, 16384)
+    assert lib.nk_backward_scratch_bytes(400, 1600, 1, 65536) < 65536 * 1600 * 8
 
 
 def test_sr_batch_host_checks(lib):

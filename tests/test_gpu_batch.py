@@ -130,7 +130,7 @@ def test_batch_entry_points_equal_single_calls(mods, prec_name, own_streams):
     batch = [mk(w) for w in insts]
     for v in single:
         v.sample()
-        v.amplitudes()
+        nk.nk_rbm_logpsi(v.rbm, v.samples, prec, v.logpsi, v.theta)
         v.energies()
     streams = [torch.cuda.Stream() for _ in insts] if own_streams else None
     sweep, amp, eloc = _batch_jobs(nk, batch, streams)
