@@ -189,7 +189,13 @@ size_t nk_metropolis_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int
  * sweeps.  The proposal of step t for the chains of group g = c / group_size is
  * drawn from Philox4x32-10 stream (g, t, "SITE"); the accept uniform of chain c
  * from (c, t, "ACCP") (key = seed).  An exchange of two equal spins is a null
- * move and is rejected.  Accept iff U < exp(2 Re(ln psi' - ln psi)) (FP64 test).
+ * move and is rejected.  Accept iff U < exp(2 Re(ln psi' - ln psi)): the
+ * log-ratio is formed in FP32 (per-unit factors, their running products and
+ * logs) and compared with U in FP32, or in FP64 when the two are within 1e-5
+ * (relative) of a tie; decisions agree with an FP64 evaluation except where
+ * |ln U - 2 Re(ln psi' - ln psi)| is below the FP32 error of the log-ratio (none
+ * of the decisions with a margin of 1e-4 or more differed in the parity tests,
+ * up to m = 1600).
  *   bond_i, bond_k  int32 [n_bonds] exchange bonds (ignored for FLIP; may be NULL)
  *   samples_out     int8 [nc * n_samples_per_chain][n], chain-major
  *                   (row c * n_samples_per_chain + s)
@@ -206,6 +212,40 @@ nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move
                               int32_t n_discard, int32_t n_samples_per_chain,
                               int8_t* samples_out, uint64_t* n_accept_out, void* scratch,
                               size_t scratch_bytes, void* stream);
+
+/* Scratch bytes nk_pt_sweep needs: the move tables of nk_metropolis_sweep and
+ * one double per replica (nc = chains->nc counts replicas). */
+size_t nk_pt_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int32_t move,
+                           int32_t n_bonds, int32_t nc);
+
+/* Parallel tempering (replica exchange; the sampler option of Sec. 2.2.5).
+ * chains holds nc = n_ladders * n_replicas replicas, chain-major: replica
+ * c * R + r (R = n_replicas) of ladder c samples |psi|^(2 beta_r) with
+ * beta_r = 1 - r / R, by the Metropolis sweep of nk_metropolis_sweep (its
+ * proposal group and Philox streams indexed by replica number) with the accept
+ * test U < exp(beta_r 2 Re(ln psi' - ln psi)).  After every sweep, neighbouring
+ * replicas (r, r + 1), over the pairs starting at r = 0 when the sweep number
+ * is even and at r = 1 when it is odd, exchange states iff
+ * U < exp((beta_r - beta_(r+1)) (L_(r+1) - L_r)), L = 2 Re ln psi (decided in
+ * FP64 from L formed at the end of the sweep: FP32 ln cosh per unit, summed in
+ * FP64), U from Philox stream (c * R + r, sweep, "SWAP").  The sweep number is
+ * floor(counter / n) with counter the chains' proposal counter before that
+ * sweep.  After each of the last n_samples_per_chain sweeps the beta = 1
+ * replica of every ladder is recorded.  R = 1 is nk_metropolis_sweep.
+ *   samples_out   int8 [n_ladders * n_samples_per_chain][n], ladder-major
+ *   n_accept_out  uint64 [nc] accepted proposals per replica in this call, or NULL
+ *   n_swap_out    uint64 [n_ladders][R - 1] accepted exchanges per pair in this
+ *                 call, or NULL
+ *   scratch       nk_pt_scratch_bytes(n, m, is_complex, move, n_bonds, nc) bytes,
+ *                 256-B aligned
+ * Two launches per sweep (the sweep, the exchanges).  chains->sigma holds the
+ * replicas' states after the call; chains->counter advances by
+ * (n_discard + n_samples_per_chain) * n. */
+nk_status nk_pt_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t n_replicas, int32_t move,
+                      const int32_t* bond_i, const int32_t* bond_k, int32_t n_bonds,
+                      int32_t n_discard, int32_t n_samples_per_chain, int8_t* samples_out,
+                      uint64_t* n_accept_out, uint64_t* n_swap_out, void* scratch,
+                      size_t scratch_bytes, void* stream);
 
 /* ---------------------------------------------------------------- operators */
 

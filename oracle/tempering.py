@@ -37,12 +37,16 @@ def swap_log_ratio(beta_r, beta_s, l_r, l_s):
 
 
 def parallel_tempering(p, sigma0, n_replicas: int, move: str, bonds, group_size: int,
-                       seed: int, counter: int, sweep0: int, n_discard: int, n_samples: int):
+                       seed: int, counter: int, sweep0: int, n_discard: int, n_samples: int,
+                       return_margin: bool = False):
     """Run every ladder (rows c R .. c R + R - 1 of ``sigma0``) for n_discard +
     n_samples sweeps.  ``sweep0`` numbers the first sweep (exchange parity and
     SWAP streams).  Returns (samples [nc * n_samples, N] of the beta = 1
     replicas, final replica states [nc R, N], new counter, accepted moves per
-    replica [nc R], accepted exchanges per pair [nc, R - 1])."""
+    replica [nc R], accepted exchanges per pair [nc, R - 1]) and, if
+    ``return_margin``, per ladder the smallest distance to a tie of any of its
+    decisions (|ln U - beta 2 Re Delta| of its replicas' moves, |ln U - ln ratio|
+    of its exchanges), for trajectory comparisons."""
     sig = np.array(sigma0, dtype=np.int8, copy=True)
     nrep, n = sig.shape
     R = n_replicas
@@ -51,9 +55,13 @@ def parallel_tempering(p, sigma0, n_replicas: int, move: str, bonds, group_size:
     samples = np.zeros((nc, n_samples, n), dtype=np.int8)
     n_acc = np.zeros(nrep, dtype=np.int64)
     n_swap = np.zeros((nc, max(R - 1, 0)), dtype=np.int64)
+    margin = np.full(nc, np.inf)
     for k in range(n_discard + n_samples):
-        _, sig, counter, acc = sampler.metropolis(p, sig, move, bonds, group_size, seed, counter,
-                                                  1, 0, betas=betas)
+        out = sampler.metropolis(p, sig, move, bonds, group_size, seed, counter, 1, 0,
+                                 betas=betas, return_margin=return_margin)
+        _, sig, counter, acc = out[:4]
+        if return_margin:
+            margin = np.minimum(margin, out[4].reshape(nc, R).min(axis=1))
         n_acc += acc
         sweep = sweep0 + k
         lval = 2.0 * np.real(rbm.logpsi(p, sig))
@@ -62,8 +70,11 @@ def parallel_tempering(p, sigma0, n_replicas: int, move: str, bonds, group_size:
             hi = lo + 1
             u = philox.draw(lo, sweep, philox.TAG_SWAP, seed)
             U = philox.uniform53(u[0], u[1])
+            lr = swap_log_ratio(betas[lo], betas[hi], lval[lo], lval[hi])
             with np.errstate(over="ignore"):
-                ok = U < np.exp(swap_log_ratio(betas[lo], betas[hi], lval[lo], lval[hi]))
+                ok = U < np.exp(lr)
+            if return_margin:
+                margin = np.minimum(margin, np.abs(np.log(U) - lr))
             a, b = sig[lo[ok]].copy(), sig[hi[ok]].copy()
             sig[lo[ok]], sig[hi[ok]] = b, a
             la, lb = lval[lo[ok]].copy(), lval[hi[ok]].copy()
@@ -71,4 +82,5 @@ def parallel_tempering(p, sigma0, n_replicas: int, move: str, bonds, group_size:
             n_swap[:, r] += ok
         if k >= n_discard:
             samples[:, k - n_discard] = sig[np.arange(nc) * R]
-    return (samples.reshape(nc * n_samples, n), sig, counter, n_acc, n_swap)
+    out = (samples.reshape(nc * n_samples, n), sig, counter, n_acc, n_swap)
+    return out + (margin,) if return_margin else out

@@ -342,6 +342,44 @@ static nk_status sweep_call(const nk_rbm* rbm, nk_chains* chains, int32_t move,
   return e;
 }
 
+size_t nk_pt_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int32_t move,
+                           int32_t n_bonds, int32_t nc) {
+  if (n < 1 || m < 1 || nc < 0) return 0;
+  return pt_scratch_bytes(n, m, is_complex ? 1 : 0, move, n_bonds, nc);
+}
+
+nk_status nk_pt_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t n_replicas, int32_t move,
+                      const int32_t* bond_i, const int32_t* bond_k, int32_t n_bonds,
+                      int32_t n_discard, int32_t n_samples_per_chain, int8_t* samples_out,
+                      uint64_t* n_accept_out, uint64_t* n_swap_out, void* scratch,
+                      size_t scratch_bytes, void* stream) {
+  if (nk_status e = check_rbm(rbm, "nk_pt_sweep")) return e;
+  if (!chains || !chains->sigma) return fail(NK_ERR_INVALID_ARG, "nk_pt_sweep: NULL chains");
+  if (n_replicas < 1) return fail(NK_ERR_INVALID_ARG, "nk_pt_sweep: n_replicas < 1");
+  if (chains->nc < 0 || n_discard < 0 || n_samples_per_chain < 0)
+    return fail(NK_ERR_INVALID_ARG, "nk_pt_sweep: negative size");
+  if (chains->nc % n_replicas)
+    return fail(NK_ERR_SHAPE, "nk_pt_sweep: nc = %d is not a multiple of n_replicas = %d",
+                chains->nc, n_replicas);
+  if (chains->group_size < 1 || chains->group_size > NK_MAX_GROUP)
+    return fail(NK_ERR_SHAPE, "nk_pt_sweep: group_size %d outside [1, %d]", chains->group_size,
+                NK_MAX_GROUP);
+  if (move != NK_MOVE_FLIP && move != NK_MOVE_EXCHANGE)
+    return fail(NK_ERR_INVALID_ARG, "nk_pt_sweep: unknown move %d", move);
+  if (move == NK_MOVE_EXCHANGE && (n_bonds < 1 || !bond_i || !bond_k))
+    return fail(NK_ERR_INVALID_ARG, "nk_pt_sweep: exchange moves need a bond list");
+  if (n_samples_per_chain > 0 && !samples_out)
+    return fail(NK_ERR_INVALID_ARG, "nk_pt_sweep: NULL samples_out");
+  if (!scratch || (((uintptr_t)scratch) & 255))
+    return fail(NK_ERR_INVALID_ARG, "nk_pt_sweep: scratch NULL or not 256-byte aligned");
+  if (chains->nc == 0 || n_discard + n_samples_per_chain == 0) return NK_OK;
+  if ((int64_t)(n_discard + n_samples_per_chain) * rbm->n > 0x7fffffff)
+    return fail(NK_ERR_SHAPE, "nk_pt_sweep: too many proposals in one call");
+  return run_pt_sweep(rbm, chains, n_replicas, move, bond_i, bond_k, n_bonds, n_discard,
+                      n_samples_per_chain, samples_out, n_accept_out, n_swap_out, scratch,
+                      scratch_bytes, (cudaStream_t)stream, false);
+}
+
 nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move,
                               const int32_t* bond_i, const int32_t* bond_k, int32_t n_bonds,
                               int32_t n_discard, int32_t n_samples_per_chain,

@@ -36,10 +36,20 @@ nk_status launch_logpsi_fp32(const nk_rbm* r, const int8_t* sigma, int64_t ns, d
 nk_status launch_logpsi_bf16(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,
                              void* theta_out, cudaStream_t st, void* t_out = nullptr);
 
+// Parallel-tempering options of a Metropolis launch: chain c is replica c % R of
+// its ladder (beta = 1 - (c % R) / R); lval (if set) receives 2 Re ln psi of every
+// chain's final state; acc_add adds to n_acc instead of overwriting it;
+// skip_tables reuses the move tables an earlier launch of the same call built.
+struct MetroPt {
+  int R = 0;
+  double* lval = nullptr;
+  int acc_add = 0;
+  int skip_tables = 0;
+};
 nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int32_t* bi,
                             const int32_t* bk, int nb, int n_discard, int n_samples,
                             int8_t* samples, uint64_t* n_acc, void* scratch, size_t scratch_bytes,
-                            cudaStream_t st, bool dry = false);
+                            cudaStream_t st, bool dry = false, const MetroPt* pt = nullptr);
 size_t metropolis_scratch_bytes(int n, int m, int cplx, int move, int nb);
 
 nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
@@ -106,6 +116,12 @@ nk_status run_sr_step_batch(const nk_sr_batch_item* items, int n_inst, const voi
 nk_status run_backward(const nk_rbm* r, const int8_t* sigma, int64_t ns, const double* g,
                        double* grad, int prec, void* scratch, size_t scratch_bytes,
                        cudaStream_t st);
+// Parallel tempering (tempering.cu)
+size_t pt_scratch_bytes(int n, int m, int cplx, int move, int nb, int nc);
+nk_status run_pt_sweep(const nk_rbm* r, nk_chains* ch, int R, int move, const int32_t* bi,
+                       const int32_t* bk, int nb, int n_discard, int n_samples, int8_t* samples,
+                       uint64_t* n_acc, uint64_t* n_swap, void* scratch, size_t scratch_bytes,
+                       cudaStream_t st, bool dry);
 // Supervised learning (Eq. 1 loss, its gradient, AdaMax): supervised.cu
 size_t supervised_scratch_bytes(int n, int m, int cplx, int64_t ns);
 nk_status run_supervised_step(nk_rbm* r, const int8_t* sigma, const double* log_target,

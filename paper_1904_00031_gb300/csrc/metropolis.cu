@@ -47,6 +47,11 @@ struct MetroArgs {
   const void* wd;       // [rows][mp] F : W_i (flip) or W_i - W_k (bond)
   const void* wt;       // [n][mp] F    : W transposed (initial theta)
   const void* b32;      // [mp] F
+  // parallel tempering (0 / null: plain sampling): chain c is replica c % pt_R
+  // of its ladder, sampling |psi|^(2 beta) with beta = 1 - (c % pt_R) / pt_R
+  int pt_R = 0;
+  double* lval = nullptr;  // [nc] 2 Re ln psi of each chain's final state, or null
+  int acc_add = 0;         // n_acc[c] += accepted (else =)
 };
 
 // Accept test U < exp(two_re), decided in FP64.  A float pre-test on
@@ -274,6 +279,9 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     bulk_g2s(sl, cdg + (int64_t)row * cd_row, cd_bytes, &full[k]);
     bulk_g2s(sl + cd_bytes, wdg + (int64_t)row * mp, wd_bytes, &full[k]);
   };
+  // inverse temperature of this chain (exactly 1 without tempering, so that the
+  // accept test below is unchanged bit for bit)
+  const float beta = A.pt_R > 0 ? 1.f - (float)(c % A.pt_R) / (float)A.pt_R : 1.f;
   const bool producer = (tid == 0);
   int issued = 0;  // steps whose columns have been requested (producer only)
   if (producer) {
@@ -388,7 +396,7 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
       // visible term -2 s_i a_i (- 2 s_k a_k) = -2 s_i (a_i - a_k) (s_k = -s_i),
       // in FP32 like the hidden-unit product
       const float two_re = (CPLX ? 1.f : 2.f) * 0.69314718055994531f * l2 - 4.f * si * da;
-      if (!timed_out && accept_test(u32, two_re, my_u, q32)) {
+      if (!timed_out && accept_test(u32, beta * two_re, my_u, q32)) {
         ++nacc;
         if constexpr (CPLX) {
           const float4* row4 = reinterpret_cast<const float4*>(smem + (size_t)k * slot_bytes);
@@ -472,6 +480,40 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
     }
   }
   tmem_st_wait();  // the last update's stores, before the columns are freed
+  if (A.lval && active) {
+    // 2 Re ln psi of the final state: Re ln cosh of this thread's units from
+    // theta in tensor memory (FP32 each, summed in FP64), reduced over the
+    // chain's lanes and warps; the visible term in FP64 from the master a
+    double lr = 0.0;
+    theta_each<CPLX, TC, 0>(tmem_th, [&](int q, F x) {
+      if (jof(q) < A.m) {
+        if constexpr (CPLX) lr += (double)lncosh_c(cf{x.x, x.y}).x;
+        else lr += (double)lncosh_f(x);
+      }
+    });
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) lr += __shfl_xor_sync(0xffffffffu, lr, off);
+    if (WPC > 1) {
+      // the chain's own slots of the pair partials (both parity halves) carry
+      // each warp's sum as hi + lo floats; the first barrier makes sure that
+      // both warps have left the step loop, whose last reads used those slots
+      pair_sync(1 + cw, 32 * WPC);
+      if (lane == 0) {
+        const float hi = (float)lr;
+        part[cw * WPC + h] = hi;
+        part[G * WPC + cw * WPC + h] = (float)(lr - (double)hi);
+      }
+      pair_sync(1 + cw, 32 * WPC);
+      lr = 0.0;
+      for (int hh = 0; hh < WPC; ++hh)
+        lr += (double)part[cw * WPC + hh] + (double)part[G * WPC + cw * WPC + hh];
+    }
+    if (h == 0 && lane == 0) {
+      double va = 0.0;
+      for (int ii = 0; ii < n; ++ii) va += (CPLX ? A.a[2 * ii] : A.a[ii]) * (double)sg[ii];
+      A.lval[c] = timed_out ? __longlong_as_double(0x7ff8000000000000ll) : 2.0 * (lr + va);
+    }
+  }
   if (timed_out && lane == 0) dev_status_set(1u << NK_ERR_TIMEOUT);
   if (timed_out && producer) {
     // let copies still in flight land before the CTA exits
@@ -479,7 +521,13 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   }
   if (active && h == 0) {
     for (int ii = lane; ii < n; ii += 32) A.sigma[(int64_t)c * n + ii] = sg[ii];
-    if (A.n_acc && lane == 0) A.n_acc[c] = timed_out ? ~0ull : nacc;
+    if (A.n_acc && lane == 0) {
+      if (timed_out) A.n_acc[c] = ~0ull;
+      else if (A.acc_add) {
+        if (A.n_acc[c] != ~0ull) A.n_acc[c] += nacc;  // a timeout marked earlier stays
+      }
+      else A.n_acc[c] = nacc;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -656,9 +704,15 @@ static nk_status launch_c(const MetroArgs& A, int nu, int wpc, size_t smem, cuda
 nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int32_t* bi,
                             const int32_t* bk, int nb, int n_discard, int n_samples,
                             int8_t* samples, uint64_t* n_acc, void* scratch, size_t scratch_bytes,
-                            cudaStream_t st, bool dry) {
+                            cudaStream_t st, bool dry, const MetroPt* pt) {
   WsLayout L(r->n, r->m, r->is_complex);
   MetroArgs A;
+  if (pt) {
+    A.pt_R = pt->R;
+    A.lval = pt->lval;
+    A.acc_add = pt->acc_add;
+  }
+  const bool skip_tables = pt && pt->skip_tables;
   A.n = r->n;
   A.m = r->m;
   A.mp = L.mp;
@@ -719,19 +773,23 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
     } else {
       A.cd = sc;
       A.wd = sc + round_up((int64_t)nb * L.mp * 2 * f, 256);
-      const int64_t tot = (int64_t)nb * L.mp;
+      const int64_t tot = skip_tables ? 0 : (int64_t)nb * L.mp;
       const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
-      pair_tables_real_kernel<<<(unsigned)blocks, 256, 0, st>>>(
-          (const float2*)(ws + L.tab), (const float*)(ws + L.wt), bi, bk, nb, L.mp, (float2*)A.cd,
-          (float*)A.wd);
-      if (nk_status e = check_launch("nk_metropolis_sweep(pair tables)")) return e;
+      if (tot > 0) {
+        pair_tables_real_kernel<<<(unsigned)blocks, 256, 0, st>>>(
+            (const float2*)(ws + L.tab), (const float*)(ws + L.wt), bi, bk, nb, L.mp,
+            (float2*)A.cd, (float*)A.wd);
+        if (nk_status e = check_launch("nk_metropolis_sweep(pair tables)")) return e;
+      }
     }
   } else {
     A.cd = sc;
     A.wd = move == NK_MOVE_FLIP ? (const void*)(ws + L.wt) : (const void*)(sc + qbytes);
     const int64_t tot = (int64_t)rows * (nu / 2) * wpc * 32;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
-    if (move == NK_MOVE_FLIP)
+    if (skip_tables) {
+      // tables of an earlier launch of the same call
+    } else if (move == NK_MOVE_FLIP)
       cplx_rows_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(
           (const float4*)(ws + L.tab), (const float2*)(ws + L.wt), bi, bk, rows, L.mp, nu, wpc,
           (float4*)sc, nullptr);
@@ -739,7 +797,8 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
       cplx_rows_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(
           (const float4*)(ws + L.tab), (const float2*)(ws + L.wt), bi, bk, rows, L.mp, nu, wpc,
           (float4*)sc, (float2*)(sc + qbytes));
-    if (nk_status e = check_launch("nk_metropolis_sweep(tables)")) return e;
+    if (!skip_tables)
+      if (nk_status e = check_launch("nk_metropolis_sweep(tables)")) return e;
   }
   nk_status e = cplx ? launch_c<true>(A, nu, wpc, smem, st) : launch_c<false>(A, nu, wpc, smem, st);
   if (e == NK_OK && ch->counter_dev) {

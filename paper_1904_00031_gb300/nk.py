@@ -41,6 +41,7 @@ EXPORTS = (
     "nk_batch_logpsi", "nk_batch_sweep", "nk_batch_local_energy",
     "nk_symm_tables_bytes", "nk_symm_upload", "nk_symm_expand", "nk_sr_symm_scratch_bytes",
     "nk_sr_step_symm", "nk_symm_build", "nk_supervised_scratch_bytes", "nk_supervised_step",
+    "nk_pt_scratch_bytes", "nk_pt_sweep",
 )
 NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
@@ -148,6 +149,8 @@ def load_library(path: str = LIB_PATH):
         "nk_sr_symm_scratch_bytes": (SZ, [I32, I32, I32, I32, I64]),
         "nk_sr_step_symm": (I32, [P, P, P, P, P, P, I64, I32, D, D, I32, D, I32, P, SZ, P, P]),
         "nk_supervised_scratch_bytes": (SZ, [I32, I32, I32, I64]),
+        "nk_pt_scratch_bytes": (SZ, [I32, I32, I32, I32, I32, I32]),
+        "nk_pt_sweep": (I32, [P, P, I32, I32, P, P, I32, I32, I32, P, P, P, P, SZ, P]),
         "nk_supervised_step": (I32, [P, P, P, P, I64, I32, D, D, D, I32, P, P, P, SZ, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -338,6 +341,31 @@ def nk_metropolis_sweep(rbm: Rbm, chains: Chains, move: int, bond_i=None, bond_k
         rbm.struct(), C.byref(chains._s), move, _ptr(bond_i), _ptr(bond_k), nb, n_discard,
         n_samples_per_chain, _ptr(samples_out), _ptr(n_accept_out), _ptr(scratch),
         0 if scratch is None else scratch.numel(), _stream(stream)), "nk_metropolis_sweep")
+    return samples_out
+
+
+def pt_scratch(rbm: Rbm, move: int, n_bonds: int, nc: int, device="cuda"):
+    nb = load_library().nk_pt_scratch_bytes(rbm.n, rbm.m, int(rbm.is_complex), move, n_bonds, nc)
+    return torch.empty(max(nb, 1), dtype=torch.uint8, device=device)
+
+
+def nk_pt_sweep(rbm: Rbm, chains: Chains, n_replicas: int, move: int, bond_i=None, bond_k=None,
+                n_discard: int = 1, n_samples_per_chain: int = 1, samples_out=None,
+                n_accept_out=None, n_swap_out=None, scratch=None, stream=None):
+    """Parallel tempering over ladders of ``n_replicas`` replicas (chain-major in
+    ``chains``); returns the samples of the beta = 1 replicas."""
+    _require_gpu(bond_i, bond_k, samples_out, n_accept_out, n_swap_out, scratch)
+    nb = 0 if bond_i is None else int(bond_i.shape[0])
+    n_lad = chains.nc // n_replicas
+    if samples_out is None:
+        samples_out = torch.empty(n_lad * n_samples_per_chain, rbm.n, dtype=torch.int8,
+                                  device=chains.sigma.device)
+    if scratch is None:
+        scratch = pt_scratch(rbm, move, nb, chains.nc, chains.sigma.device)
+    _check(load_library().nk_pt_sweep(
+        rbm.struct(), C.byref(chains._s), n_replicas, move, _ptr(bond_i), _ptr(bond_k), nb,
+        n_discard, n_samples_per_chain, _ptr(samples_out), _ptr(n_accept_out), _ptr(n_swap_out),
+        _ptr(scratch), scratch.numel(), _stream(stream)), "nk_pt_sweep")
     return samples_out
 
 
