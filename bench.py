@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-fp32-arm", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--phase-times", action="store_true",
                     help="print the wall time of each bench phase to stderr")
+    ap.add_argument("--replicas", type=int, default=1,
+                    help="sample by parallel tempering with this many replicas per chain")
     ap.add_argument("--checkpoint-iters", type=int, default=50,
                     help="also time the iteration after this many more SR iterations "
                          "(structured psi, realistic acceptance); 0 skips it")
@@ -58,15 +60,22 @@ def parse():
 
 # ---------------------------------------------------------------------- CPU oracle sample
 
-def oracle_sample(workload: str, n_chains: int, spc: int, n_cg: int) -> dict:
-    """One oracle VMC + SR iteration on a bounded sample (n_chains chains, spc
-    samples per chain, 1 burn-in sweep); returns seconds and samples."""
-    import numpy as np
-    from oracle import local_energy, rbm, sampler, sr
+def oracle_setup(workload: str, n_chains: int, offset: int = 0):
+    """Inputs of a bounded oracle sample: the workload, its initial parameters
+    and n_chains chain states from chain ``offset`` on."""
     from paper_1904_00031_gb300 import workloads as W
     w = W.workload(workload) if workload != "c4" else W.batched_instances(64, 4242, 1024)[0]
     p = W.init_params(w.n, w.m, w.is_complex, 0.01, w.seed)
-    s0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed)[:n_chains]
+    s0 = W.init_chains(max(w.n_chains, offset + n_chains), w.n, w.zero_magnetisation,
+                       w.seed)[offset:offset + n_chains]
+    return w, p, s0
+
+
+def oracle_iteration(w, p, s0, spc: int, n_cg: int) -> dict:
+    """One oracle VMC + SR iteration on the given chains (spc samples per chain,
+    1 burn-in sweep); returns seconds and samples."""
+    from oracle import local_energy, rbm, sampler, sr
+    n_chains = len(s0)
     t0 = time.perf_counter()
     samples, fin, cnt, nacc = sampler.metropolis(p, s0, w.move, w.sampler_bonds, w.group_size,
                                                  w.seed, 0, 1, spc)
@@ -83,16 +92,67 @@ def oracle_sample(workload: str, n_chains: int, spc: int, n_cg: int) -> dict:
     return {"seconds": dt, "samples": int(len(samples)), "energy": float(mean.real)}
 
 
-def run_oracle_subprocess(workload: str, n_chains: int, spc: int, n_cg: int) -> dict:
+def oracle_sample(workload: str, n_chains: int, spc: int, n_cg: int, offset: int = 0) -> dict:
+    """One oracle VMC + SR iteration on a bounded sample (n_chains chains from
+    chain ``offset`` on, spc samples per chain, 1 burn-in sweep)."""
+    w, p, s0 = oracle_setup(workload, n_chains, offset)
+    return oracle_iteration(w, p, s0, spc, n_cg)
+
+
+def _oracle_env():
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
+    return env
+
+
+def run_oracle_subprocess(workload: str, n_chains: int, spc: int, n_cg: int) -> dict:
     spec = json.dumps({"workload": workload, "n_chains": n_chains, "spc": spc, "n_cg": n_cg})
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", spec],
-                       capture_output=True, text=True, env=env, cwd=ROOT)
+                       capture_output=True, text=True, env=_oracle_env(), cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _oracle_worker(workload, n_chains, spc, n_cg, offset, n_iter, barrier, out):
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    sys.path.insert(0, ROOT)
+    w, p, s0 = oracle_setup(workload, n_chains, offset)
+    for _ in range(n_iter):
+        barrier.wait()
+        r = oracle_iteration(w, p, s0, spc, n_cg)
+        barrier.wait()
+    out.put(r["samples"])
+
+
+def run_oracle_all_cores(workload: str, n_chains: int, spc: int, n_cg: int,
+                         n_iter: int = 1) -> dict:
+    """The oracle on every host core at once: one single-threaded worker process
+    per core (started with spawn, before any CUDA call), each on its own
+    n_chains chains; every iteration starts and ends on a barrier of all
+    workers, and its rate is all samples / the wall time between the two."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores + 1)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(workload, n_chains, spc, n_cg,
+                                                      k * n_chains, n_iter, barrier, out))
+             for k in range(cores)]
+    for pr in procs:
+        pr.start()
+    secs = []
+    for _ in range(n_iter):
+        barrier.wait()
+        t0 = time.perf_counter()
+        barrier.wait()
+        secs.append(time.perf_counter() - t0)
+    per = sum(out.get() for _ in procs)
+    for pr in procs:
+        pr.join()
+    return {"seconds": secs, "samples": per, "cores": cores}
 
 
 # DRAM bytes (read + write) per launch of a stage's dominant kernel, from one
@@ -104,6 +164,9 @@ NCU_TRAFFIC = {
 
 ORACLE_SAMPLE = {"c5": (24, 2, 50), "c3": (64, 1, 50), "c2": (128, 4, 50), "c1": (16, 63, 120),
                  "c4": (64, 4, 50)}
+# per process of the all-core oracle runs (one single-threaded process per core)
+ORACLE_SAMPLE_CORE = {"c5": (8, 2, 50), "c3": (24, 1, 50), "c2": (48, 4, 50), "c1": (16, 63, 120),
+                      "c4": (24, 4, 50)}
 
 
 # ---------------------------------------------------------------------- clocks
@@ -234,8 +297,12 @@ def run_gpu(args):
         def make(pr, **kw):
             return VmcSrSymm(w, sparams, perm, sigma0, pr, **kw)
     else:
+        if args.replicas > 1:
+            sigma0 = W.init_chains(w.n_chains * args.replicas, w.n, w.zero_magnetisation,
+                                   R.replica_seed(w.seed, rank))
+
         def make(pr, **kw):
-            return VmcSr(w, params, sigma0, pr, **kw)
+            return VmcSr(w, params, sigma0, pr, replicas=args.replicas, **kw)
 
     t_phase = [T_START]
 
@@ -316,21 +383,56 @@ def run_gpu(args):
     h2d = sum(h.numel() for h in host_params) * 8
 
     phase("end to end")
-    # the plain FP32 path on the same workload (for the mixed-precision ratio)
-    fp32_arm = None
+    # the plain FP32 path on the same workload (the mixed-precision ratio) and the
+    # same-accuracy evidence: both paths from the same parameters, chains and
+    # random streams for warm-up + timed iterations (eager, the energy read after
+    # every iteration outside the CUDA-event bracket), energy by energy
+    fp32_arm, same_acc, v32 = None, None, None
     if prec != nk.NK_PREC_FP32 and not args.no_fp32_arm:
-        v32 = make(nk.NK_PREC_FP32)
-        for _ in range(max(1, args.warmup)):
-            v32.step()
+        n_it = args.warmup + args.steps
+
+        def trace(pr):
+            vv = make(pr)
+            es, errs, ms = [], [], []
+            for _ in range(n_it):
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                vv.step()
+                a1.record(stream)
+                inf = vv.info()  # synchronises
+                es.append(inf["energy"])
+                errs.append(inf["error"])
+                ms.append(a0.elapsed_time(a1))
+            return vv, np.array(es), np.array(errs), np.array(ms)
+
+        v32, e32, s32, ms32 = trace(nk.NK_PREC_FP32)
+        _, ebf, sbf, _ = trace(prec)
         barrier()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(args.steps):
-            v32.step()
-        a1.record(stream)
+        fp32_ms = R.max_over_ranks(float(np.mean(ms32[args.warmup:])), world, "cuda")
+        fp32_arm = R.aggregate_rate(w.n_samples, world, fp32_ms / 1e3)
+        d = np.abs(ebf - e32) / np.sqrt(sbf ** 2 + s32 ** 2)
+        half = n_it // 2
+        same_acc = {
+            "iterations": n_it,
+            "energy_bf16x2": [round(float(x), 6) for x in ebf],
+            "energy_fp32": [round(float(x), 6) for x in e32],
+            "error_bar_bf16x2_last": round(float(sbf[-1]), 6),
+            "error_bar_fp32_last": round(float(s32[-1]), 6),
+            "mean_last_half_bf16x2": round(float(ebf[half:].mean()), 6),
+            "mean_last_half_fp32": round(float(e32[half:].mean()), 6),
+            "max_abs_diff_over_error_bar": round(float(d.max()), 4),
+            "note": "same seeds, parameters and chains; error bars from proposal-group means "
+                    "of each iteration",
+        }
+        # the FP32 arm's own stage breakdown and SR roofline (one eager iteration)
+        e32v = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        e32v[0].record(stream)
+        for si, name in enumerate(stages):
+            getattr(v32, name)()
+            e32v[si + 1].record(stream)
         barrier()
-        fp32_arm = w.n_samples / (a0.elapsed_time(a1) / args.steps / 1e3)
+        stage_ms_fp32 = {name: e32v[si].elapsed_time(e32v[si + 1]) for si, name in enumerate(stages)}
 
     t_bytes = w.n_samples * w.m * (8 if w.is_complex else 4)
     l2_note = (f"inputs larger than L2 (T = tanh theta is {t_bytes / 1e6:.0f} MB)" if t_bytes > 129e6
@@ -371,9 +473,22 @@ def run_gpu(args):
                        "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 4)}
     dom = max(stage_ms, key=stage_ms.get)
     kern = {"sample": "metropolis_kernel", "energies": "local_energy_tiled",
-            "amplitudes": "fwd_tc_kernel (ln psi)" if prec_name == "bf16x2" else "logpsi_fp32_kernel",
+            "amplitudes": ("fwd_tc_kernel (theta only)" if prec_name == "bf16x2"
+                           else "logpsi_fp32_kernel (theta only)"),
             "sr": "SR step (fwd_tc + adj_tc + CG vector kernels)" if prec_name == "bf16x2"
                   else "SR step (forward/adjoint FP32 + CG vector kernels)"}[dom]
+    fp32_info = None
+    if fp32_arm is not None:
+        fl32 = {k: fl[k] for k in stage_ms_fp32}
+        fp32_info = {"samples_per_s": round(fp32_arm, 2),
+                     "stage_ms": {k: round(x, 3) for k, x in stage_ms_fp32.items()},
+                     "stage_roofline": {k: {"bound": "alu", "achieved":
+                                            round(fl32[k] / (x / 1e3) / 1e12, 3),
+                                            "peak": round(alu_peak, 1), "unit": "TFLOP/s",
+                                            "frac": round(fl32[k] / (x / 1e3) / 1e12 / alu_peak, 4)}
+                                        for k, x in stage_ms_fp32.items()},
+                     "note": "plain FP32 CUDA-core contractions, same algorithm; peak = the "
+                             "measured FP32 FMA rate"}
     roof = dict(rl[dom])
     roof.update({"kernel": kern, "traffic": NCU_TRAFFIC.get((wname, prec_name, kern)),
                  "peak_source": (f"{pk_kind} bf16 dense TFLOP/s (sustained)" if roof["bound"] == "tensor"
@@ -413,12 +528,15 @@ def run_gpu(args):
                    "chains": w.n_chains, "samples_per_chain": w.samples_per_chain,
                    "burn_in_sweeps": w.n_discard, "samples_per_iter": w.n_samples,
                    "moves": w.move, "n_cg": w.n_cg, "diag_shift": w.diag_shift, "lr": w.lr,
-                   "prec": prec_name, "l2": l2_note,
+                   "prec": prec_name, "l2": l2_note, "replicas": args.replicas,
                    "parallelism": f"replicas x{world}"},
         "sr_steps_per_s": round(1e3 / ms_per_step, 4),
         "stage_ms": {k: round(x, 3) for k, x in stage_ms.items()},
         "fp32_path_samples_per_s": None if fp32_arm is None else round(fp32_arm, 2),
+        "fp32_arm": fp32_info, "same_accuracy": same_acc,
+        "cg_iters": int(info["cg_iters"]), "cg_resid": info["cg_resid"],
         "acceptance": round(info["acceptance"], 4), "energy": info["energy"],
+        "energy_error_bar": info["error"],
         "nonnull_proposal_fraction": round(nonnull_frac, 4),
         "connected_per_sample": round(n_conn, 2), "moves": v.op.n_moves,
         "roofline": roof, "stage_roofline": rl,
@@ -528,7 +646,7 @@ def main():
     if args.oracle_sample:
         spec = json.loads(args.oracle_sample)
         print(json.dumps(oracle_sample(spec["workload"], spec["n_chains"], spec["spc"],
-                                       spec["n_cg"])))
+                                       spec["n_cg"], spec.get("offset", 0))))
         return
     if args.profile_kernels:
         profile_kernels()
@@ -548,14 +666,16 @@ def main():
         w = (W.workload(args.workload) if args.workload != "c4"
              else W.batched_instances(64, 4242, 1024)[0])
         tot_s, tot_n = 0.0, 0
-        for k in range(args.warmup + args.steps):
-            r = run_oracle_subprocess(args.workload, nc, spc, ncg)
-            if k >= args.warmup:
-                tot_s += r["seconds"]
-                tot_n += r["samples"]
+        ncc, spcc, ncgc = ORACLE_SAMPLE_CORE[args.workload]
+        cores = 1
+        r = run_oracle_all_cores(args.workload, ncc, spcc, ncgc, args.warmup + args.steps)
+        cores = r["cores"]
+        tot_s = sum(r["seconds"][args.warmup:])
+        tot_n = r["samples"] * args.steps
         val = tot_n / tot_s
-        sample = (f"{nc} chains x ({spc} samples + 1 burn-in sweep) of the {w.name} workload, "
-                  f"full oracle iteration incl. {ncg} CG iterations, per step")
+        sample = (f"{cores} single-threaded oracle processes at once (one per host core), each "
+                  f"{ncc} chains x ({spcc} samples + 1 burn-in sweep) of the {w.name} workload "
+                  f"and a full oracle iteration incl. {ncgc} CG iterations, per step")
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "samples/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -565,7 +685,7 @@ def main():
                        "chains": w.n_chains, "samples_per_chain": w.samples_per_chain,
                        "burn_in_sweeps": w.n_discard, "samples_per_iter": w.n_samples,
                        "moves": w.move, "n_cg": w.n_cg, "oracle_sample": sample},
-            "cpu_baseline": {"value": round(val, 4), "unit": "samples/s", "cores": 1,
+            "cpu_baseline": {"value": round(val, 4), "unit": "samples/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(val, 4), "unit": "samples/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
@@ -575,10 +695,19 @@ def main():
     if rank == 0 and world == 1 and not args.no_baseline and args.model == "rbm":
         # before any CUDA call: the oracle runs in a fresh single-threaded process
         r = run_oracle_subprocess(args.workload, nc, spc, ncg)
-        base = {"value": round(r["samples"] / r["seconds"], 4), "unit": "samples/s", "cores": 1,
-                "kind": "oracle",
-                "sample": f"{nc} chains x ({spc} samples + 1 burn-in sweep), one full oracle "
-                          f"VMC+SR iteration ({ncg} CG iterations), {r['seconds']:.1f} s"}
+        ncc, spcc, ncgc = ORACLE_SAMPLE_CORE[args.workload]
+        ra = run_oracle_all_cores(args.workload, ncc, spcc, ncgc)
+        ra["seconds"] = ra["seconds"][0]
+        base = {"value": round(ra["samples"] / ra["seconds"], 4), "unit": "samples/s",
+                "cores": ra["cores"], "kind": "oracle",
+                "sample": f"{ra['cores']} single-threaded oracle processes at once, each "
+                          f"{ncc} chains x ({spcc} samples + 1 burn-in sweep) and one full "
+                          f"oracle VMC+SR iteration ({ncgc} CG iterations), "
+                          f"{ra['seconds']:.1f} s wall",
+                "one_core": {"value": round(r["samples"] / r["seconds"], 4), "cores": 1,
+                             "sample": f"{nc} chains x ({spc} samples + 1 burn-in sweep), one "
+                                       f"full oracle VMC+SR iteration ({ncg} CG iterations), "
+                                       f"{r['seconds']:.1f} s"}}
     if args.workload == "c4" and args.model != "rbm":
         raise SystemExit("--model symm runs the single-instance workloads (c1, c2, c3, c5)")
     rank, out = run_gpu_batched(args) if args.workload == "c4" else run_gpu(args)

@@ -47,17 +47,22 @@ def adj_centres(m: int, is_complex: bool) -> bool:
 class VmcSr:
     def __init__(self, w: W.Workload, params: W.RbmParams | None, sigma0=None,
                  prec: int = nk.NK_PREC_FP32, device="cuda", graph: bool = False,
-                 autotune: bool = False, rbm: nk.Rbm | None = None):
+                 autotune: bool = False, rbm: nk.Rbm | None = None, replicas: int = 1):
         """``params`` are loaded into a new RBM, or ``rbm`` (already loaded and
-        prepared, params None) is used as it is."""
+        prepared, params None) is used as it is.  ``replicas`` > 1 samples by
+        parallel tempering: every chain becomes a ladder of that many replicas
+        (``sigma0``, if given, holds all n_chains * replicas states, ladder-major)
+        and only the beta = 1 replicas are recorded."""
         self.w = w
         self.prec = prec
+        self.replicas = int(replicas)
         if rbm is None:
             rbm = nk.Rbm(w.n, w.m, w.is_complex, device)
             rbm.load(params.a, params.b, params.w)
         self.rbm = rbm
+        n_rep = w.n_chains * self.replicas
         if sigma0 is None:
-            sigma0 = W.init_chains(w.n_chains, w.n, w.zero_magnetisation, w.seed)
+            sigma0 = W.init_chains(n_rep, w.n, w.zero_magnetisation, w.seed)
         self.chains = nk.Chains(sigma0, w.group_size, w.seed, device, device_counter=graph)
         self.blocks = error_blocks(w.n_chains, w.group_size)
         self.use_graph = graph
@@ -76,11 +81,15 @@ class VmcSr:
         self.t = torch.empty(ns, w.m, dtype=f32, device=device)
         self.logpsi = torch.empty(ns, dtype=torch.complex128, device=device)
         self.eloc = torch.empty(ns, dtype=torch.complex128, device=device)
-        self.n_acc = torch.zeros(w.n_chains, dtype=torch.int64, device=device)
+        self.n_acc = torch.zeros(n_rep, dtype=torch.int64, device=device)
+        self.n_swap = (torch.zeros(w.n_chains * (self.replicas - 1), dtype=torch.int64,
+                                   device=device) if self.replicas > 1 else None)
         self.scratch = self._sr_scratch(device)
         self.info_buf = torch.zeros(nk.NK_INFO_LEN, dtype=torch.float64, device=device)
         self.move = nk.NK_MOVE_FLIP if w.move == "flip" else nk.NK_MOVE_EXCHANGE
-        self.metro_scratch = nk.metropolis_scratch(self.rbm, self.move, len(b), device)
+        self.metro_scratch = (nk.metropolis_scratch(self.rbm, self.move, len(b), device)
+                              if self.replicas == 1 else
+                              nk.pt_scratch(self.rbm, self.move, len(b), n_rep, device))
         self.eloc_scratch = nk.local_energy_scratch(self.rbm, self.op, device)
 
     def _sr_scratch(self, device):
@@ -88,6 +97,11 @@ class VmcSr:
 
     # stages ---------------------------------------------------------------
     def sample(self):
+        if self.replicas > 1:
+            nk.nk_pt_sweep(self.rbm, self.chains, self.replicas, self.move, self.bond_i,
+                           self.bond_k, self.w.n_discard, self.w.samples_per_chain, self.samples,
+                           self.n_acc, self.n_swap, self.metro_scratch)
+            return
         nk.nk_metropolis_sweep(self.rbm, self.chains, self.move, self.bond_i, self.bond_k,
                                self.w.n_discard, self.w.samples_per_chain, self.samples,
                                self.n_acc, self.metro_scratch)
@@ -141,7 +155,11 @@ class VmcSr:
     def info(self) -> dict:
         d = nk.info_dict(self.info_buf)
         sweeps = self.w.n_discard + self.w.samples_per_chain
-        d["acceptance"] = float(self.n_acc.sum().item()) / (self.w.n_chains * sweeps * self.w.n)
+        d["acceptance"] = float(self.n_acc.sum().item()) / (self.w.n_chains * self.replicas *
+                                                           sweeps * self.w.n)
+        if self.n_swap is not None:
+            d["exchange_rate"] = float(self.n_swap.sum().item()) / (
+                self.w.n_chains * sweeps * (self.replicas - 1) / 2)
         return d
 
     def sr_launches(self) -> int:
@@ -168,8 +186,14 @@ class VmcSr:
 
     # kernel launches per step (for reporting)
     def launches_per_step(self) -> int:
-        # move tables (exchanges; flips of complex RBMs), sweep
+        # move tables (exchanges; flips of complex RBMs), sweep; with tempering
+        # a sweep launch and an exchange launch per sweep (the tables once)
         n = 1 + (1 if self.move == nk.NK_MOVE_EXCHANGE or self.w.is_complex else 0)
+        sweeps = self.w.n_discard + self.w.samples_per_chain
+        if self.replicas > 1:
+            n += 2 * sweeps - 1
+        if self.use_graph:  # the device counter is advanced by a kernel after each sweep launch
+            n += sweeps if self.replicas > 1 else 1
         n += 1                                                  # ln psi / theta
         n += 2                                                  # move tables, local energy
         n += self.sr_launches()                                 # SR step
