@@ -18,6 +18,9 @@ Modules and the passages of the NetKet paper (arXiv:1904.00031) they follow:
                 Lanczos (Sec. 2.1, ``exact`` module), the TFIM free-fermion closed form.
 * ``rbm_symm``  symmetric RBM (RbmSpinSymm, Sec. 2.2.2): tied weights over a lattice
                 symmetry group, its tied log-derivatives, and SR in the tied space.
+* ``ffnn``      multi-layer feed-forward network of dense layers and ln cosh
+                activations with a sum output (Sec. 2.2.2, FFNN), its holomorphic
+                log-derivatives and backward.
 * ``local_energy`` E_loc(sigma) = sum_sigma' H_{sigma sigma'} psi(sigma')/psi(sigma)
                 (the energy estimator equation of Sec. 2.2.5).
 * ``sampler``   Metropolis Markov chains over |psi|^2 with single-spin-flip and

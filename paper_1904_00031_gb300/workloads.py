@@ -291,6 +291,23 @@ def init_params(n: int, m: int, is_complex: bool, sigma: float = 0.01, seed: int
     return RbmParams(a=draw(n), b=draw(m), w=draw((m, n)))
 
 
+def ffnn_n_params(widths) -> int:
+    """Parameters of a dense ln cosh network with layer widths [n, w_1, .., w_L]:
+    W_l [w_l][w_(l-1)] and b_l [w_l] per layer."""
+    return int(sum(widths[l] * (widths[l - 1] + 1) for l in range(1, len(widths))))
+
+
+def init_ffnn_params(widths, is_complex: bool, sigma: float = 0.01, seed: int = 1234):
+    """Flat FFNN parameters (layer by layer: W_l row-major, then b_l), every real
+    component N(0, sigma^2) from a seeded generator."""
+    rng = np.random.default_rng(seed)
+    p = ffnn_n_params(widths)
+    x = sigma * rng.normal(size=p)
+    if is_complex:
+        x = x + 1j * sigma * rng.normal(size=p)
+    return x
+
+
 def init_chains(nc: int, n: int, zero_magnetisation: bool, seed: int) -> np.ndarray:
     """Initial chain states, int8 [nc, n]: uniform +-1 spins, or a uniformly
     random arrangement of n/2 up and n/2 down spins (total S^z = 0 sector)."""
