@@ -384,6 +384,46 @@ nk_status nk_supervised_step(nk_rbm* rbm, const int8_t* sigma, const double* log
                              double* grad_out, void* scratch, size_t scratch_bytes,
                              double* info_out, void* stream);
 
+/* ----------------------------------------------- feed-forward ln cosh networks */
+
+/* A multi-layer feed-forward network (Sec. 2.2.2, FFNN machines): dense layers
+ * h_l = W_l x_(l-1) + b_l, each followed by the ln cosh activation
+ * x_l = ln cosh(h_l), x_0 = sigma, and a sum output ln psi = sum_j x_(L, j).  The
+ * one-layer network is the RBM without visible bias; deeper ones generalise
+ * it.  Real or complex (holomorphic) parameters. */
+typedef struct nk_ffnn {
+  int32_t n_layers;       /* L, 1..8                                               */
+  int32_t is_complex;
+  const int32_t* widths;  /* HOST int32 [L + 1]: widths[0] = n (sites), widths[l] =
+                             outputs of layer l (1..2^20)                          */
+  double* params;         /* F64 (device) master parameters, layer by layer: W_l
+                             row-major [w_l][w_(l-1)] then b_l [w_l]; complex
+                             interleaved (re, im)                                  */
+} nk_ffnn;
+
+/* Scratch bytes nk_ffnn_logpsi / nk_ffnn_backward need for ns samples (the
+ * pre-activations and activations of every layer, two backpropagation buffers
+ * and the weight-gradient split partials); 0 for an invalid network. */
+size_t nk_ffnn_scratch_bytes(const nk_ffnn* f, int64_t ns);
+
+/* ln psi(sigma) of ns configurations: every dense layer a 64 x 64-tiled FP32
+ * CUDA-core contraction reading the FP64 master parameters, ln cosh fused into
+ * its epilogue, the output sum in FP64.
+ *   sigma       int8 [ns][n];  logpsi_out  c128 [ns]
+ *   scratch     nk_ffnn_scratch_bytes(f, ns) bytes, 256-B aligned */
+nk_status nk_ffnn_logpsi(const nk_ffnn* f, const int8_t* sigma, int64_t ns, double* logpsi_out,
+                         void* scratch, size_t scratch_bytes, void* stream);
+
+/* Backward of ln psi: grad_k = sum_s conj(O_sk) g_s with O the holomorphic
+ * log-derivatives (for real parameters sum_s O_sk Re g_s), by the chain rule
+ * through the layers: e_L = conj(tanh h_L) g, e_(l-1) = conj(tanh h_(l-1))
+ * (e_l conj(W_l)), grad W_l = e_l^T conj(x_(l-1)), grad b_l = sum_s e_l.  The
+ * forward is recomputed into the scratch first; weight gradients are FP32
+ * split partials summed in FP64 in a fixed order.
+ *   g         c128 [ns];  grad_out  F64 [P] or c128 [P] in the parameter order */
+nk_status nk_ffnn_backward(const nk_ffnn* f, const int8_t* sigma, int64_t ns, const double* g,
+                           double* grad_out, void* scratch, size_t scratch_bytes, void* stream);
+
 /* ------------------------------------------- batches of independent instances */
 
 /* Many independent RBMs (uneven n, m, field, sample counts) in one call each

@@ -46,3 +46,33 @@ class RbmLogPsi(torch.autograd.Function):
 def logpsi(params, rbm: nk.Rbm, sigma, prec: int = nk.NK_PREC_FP32):
     """ln psi(sigma) as a differentiable function of the flat parameter tensor."""
     return RbmLogPsi.apply(params, rbm, sigma, prec)
+
+
+class FfnnLogPsi(torch.autograd.Function):
+    """ln psi of a dense ln cosh network (Sec. 2.2.2, FFNN): forward
+    nk_ffnn_logpsi, backward nk_ffnn_backward (the chain rule through the
+    layers in hand-written kernels).  Parameters: one flat tensor in the
+    network's order, complex128 (holomorphic) or float64."""
+
+    @staticmethod
+    def forward(ctx, params, net: nk.Ffnn, sigma):
+        with torch.no_grad():
+            p = params.detach()
+            if net.is_complex:
+                p = torch.view_as_real(p.to(torch.complex128)).reshape(-1)
+            net.params.copy_(p.to(torch.float64))
+            lp = nk.nk_ffnn_logpsi(net, sigma)
+        ctx.net = net
+        ctx.save_for_backward(sigma)
+        return lp if net.is_complex else lp.real.contiguous()
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (sigma,) = ctx.saved_tensors
+        grad = nk.nk_ffnn_backward(ctx.net, sigma, grad_out.to(torch.complex128).contiguous())
+        return grad, None, None
+
+
+def ffnn_logpsi(params, net: nk.Ffnn, sigma):
+    """ln psi(sigma) of the network as a differentiable function of its flat parameters."""
+    return FfnnLogPsi.apply(params, net, sigma)

@@ -684,6 +684,35 @@ nk_status nk_rbm_logpsi_backward(const nk_rbm* rbm, const int8_t* sigma, int64_t
                       (cudaStream_t)stream);
 }
 
+size_t nk_ffnn_scratch_bytes(const nk_ffnn* f, int64_t ns) {
+  if (check_ffnn(f, "nk_ffnn_scratch_bytes") || ns < 0) return 0;
+  return ffnn_scratch_bytes(f, ns);
+}
+
+nk_status nk_ffnn_logpsi(const nk_ffnn* f, const int8_t* sigma, int64_t ns, double* logpsi_out,
+                         void* scratch, size_t scratch_bytes, void* stream) {
+  if (nk_status e = check_ffnn(f, "nk_ffnn_logpsi")) return e;
+  if (ns < 0) return fail(NK_ERR_INVALID_ARG, "nk_ffnn_logpsi: ns < 0");
+  if (ns == 0) return NK_OK;
+  if (!sigma || !logpsi_out || !scratch)
+    return fail(NK_ERR_INVALID_ARG, "nk_ffnn_logpsi: NULL pointer");
+  if (((uintptr_t)scratch) & 255)
+    return fail(NK_ERR_INVALID_ARG, "nk_ffnn_logpsi: scratch not 256-byte aligned");
+  return run_ffnn_logpsi(f, sigma, ns, logpsi_out, scratch, scratch_bytes, (cudaStream_t)stream);
+}
+
+nk_status nk_ffnn_backward(const nk_ffnn* f, const int8_t* sigma, int64_t ns, const double* g,
+                           double* grad_out, void* scratch, size_t scratch_bytes, void* stream) {
+  if (nk_status e = check_ffnn(f, "nk_ffnn_backward")) return e;
+  if (ns < 1) return fail(NK_ERR_INVALID_ARG, "nk_ffnn_backward: ns < 1");
+  if (!sigma || !g || !grad_out || !scratch)
+    return fail(NK_ERR_INVALID_ARG, "nk_ffnn_backward: NULL pointer");
+  if (((uintptr_t)scratch) & 255)
+    return fail(NK_ERR_INVALID_ARG, "nk_ffnn_backward: scratch not 256-byte aligned");
+  return run_ffnn_backward(f, sigma, ns, g, grad_out, scratch, scratch_bytes,
+                           (cudaStream_t)stream);
+}
+
 size_t nk_supervised_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int64_t ns) {
   if (n < 1 || m < 1 || ns < 1) return 0;
   return supervised_scratch_bytes(n, m, is_complex ? 1 : 0, ns);

@@ -122,6 +122,13 @@ nk_status run_pt_sweep(const nk_rbm* r, nk_chains* ch, int R, int move, const in
                        const int32_t* bk, int nb, int n_discard, int n_samples, int8_t* samples,
                        uint64_t* n_acc, uint64_t* n_swap, void* scratch, size_t scratch_bytes,
                        cudaStream_t st, bool dry);
+// Feed-forward ln cosh networks (ffnn.cu)
+nk_status check_ffnn(const nk_ffnn* f, const char* who);
+size_t ffnn_scratch_bytes(const nk_ffnn* f, int64_t ns);
+nk_status run_ffnn_logpsi(const nk_ffnn* f, const int8_t* sigma, int64_t ns, double* logpsi,
+                          void* scratch, size_t bytes, cudaStream_t st);
+nk_status run_ffnn_backward(const nk_ffnn* f, const int8_t* sigma, int64_t ns, const double* g,
+                            double* grad, void* scratch, size_t bytes, cudaStream_t st);
 // Supervised learning (Eq. 1 loss, its gradient, AdaMax): supervised.cu
 size_t supervised_scratch_bytes(int n, int m, int cplx, int64_t ns);
 nk_status run_supervised_step(nk_rbm* r, const int8_t* sigma, const double* log_target,

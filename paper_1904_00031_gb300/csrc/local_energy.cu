@@ -120,14 +120,18 @@ __global__ void move_tables_kernel(const char* __restrict__ op, const void* __re
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-// One running product kept as mantissa * 2^e, renormalised from a packed lane.
-__device__ __forceinline__ void renorm_lane(float& x, float& y, int& e) {
-  const float mx = fmaxf(fabsf(x), fabsf(y));
+// Two running products (the lanes of a packed pair, complex: Re in x, Im in y)
+// renormalised with one shared power of two, the exponent of the largest of
+// their four parts: each is kept as mantissa * 2^e with the pair's e.  The
+// smaller product keeps its full FP32 precision unless it is below 2^-126 of
+// the larger, where its local-energy term is negligible against the larger one.
+__device__ __forceinline__ void renorm_pair(float2& x, float2& y, int& e) {
+  const float mx = fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(y.x), fabsf(y.y)));
   int ex = ((__float_as_int(mx) >> 23) & 0xff) - 127;
   if (mx == 0.f) ex = 0;
   const float sc = __int_as_float((127 - ex) << 23);
-  x *= sc;
-  y *= sc;
+  x = f2mul(x, make_float2(sc, sc));
+  y = f2mul(y, make_float2(sc, sc));
   e += ex;
 }
 
@@ -251,10 +255,10 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   }
 
   // running products: real, P[p][q]; complex, packed over the move pairs
-  // (q = 2 qp, 2 qp + 1): Px/Py[p][qp] = (Re, Im) parts, exponents Pe[p][q]
+  // (q = 2 qp, 2 qp + 1): Px/Py[p][qp] = (Re, Im) parts, shared exponent Pe[p][qp]
   ScaledReal P[4][4];
   float2 Px[4][2], Py[4][2];
-  int Pe[4][4];
+  int Pe[4][4];         // real: unused; complex: Pe[p][qp] is the exponent of move pair qp
   float sgn[4][4];      // real: sigma_i of the configuration for each move
   float2 ns2[4][2];     // complex: -sigma_i packed over the move pairs
   bool bad = false;     // a bounded wait for a move-table chunk gave up
@@ -387,14 +391,11 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
               Py[p][qp] = f2fma(py, rx, f2mul(px, ry));
             }
           }
-          if ((kk & 7) == 7) {
+          if (kk == kEBK - 1) {  // once per chunk of 16 hidden units
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
-              for (int qp = 0; qp < 2; ++qp) {
-                renorm_lane(Px[p][qp].x, Py[p][qp].x, Pe[p][2 * qp]);
-                renorm_lane(Px[p][qp].y, Py[p][qp].y, Pe[p][2 * qp + 1]);
-              }
+              for (int qp = 0; qp < 2; ++qp) renorm_pair(Px[p][qp], Py[p][qp], Pe[p][qp]);
           }
         }
       } else {
@@ -442,8 +443,8 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
           double pr, pi;
           if constexpr (CPLX) {
             const float2 px = Px[p][q >> 1], py = Py[p][q >> 1];
-            pr = ldexp((double)((q & 1) ? px.y : px.x), Pe[p][q]);
-            pi = ldexp((double)((q & 1) ? py.y : py.x), Pe[p][q]);
+            pr = ldexp((double)((q & 1) ? px.y : px.x), Pe[p][q >> 1]);
+            pi = ldexp((double)((q & 1) ? py.y : py.x), Pe[p][q >> 1]);
           } else {
             pr = ldexp((double)P[p][q].v, P[p][q].e);
             pi = 0.0;

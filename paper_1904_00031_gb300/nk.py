@@ -41,7 +41,8 @@ EXPORTS = (
     "nk_batch_logpsi", "nk_batch_sweep", "nk_batch_local_energy",
     "nk_symm_tables_bytes", "nk_symm_upload", "nk_symm_expand", "nk_sr_symm_scratch_bytes",
     "nk_sr_step_symm", "nk_symm_build", "nk_supervised_scratch_bytes", "nk_supervised_step",
-    "nk_pt_scratch_bytes", "nk_pt_sweep",
+    "nk_pt_scratch_bytes", "nk_pt_sweep", "nk_ffnn_scratch_bytes", "nk_ffnn_logpsi",
+    "nk_ffnn_backward",
 )
 NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
@@ -65,6 +66,11 @@ class _RbmSymm(C.Structure):
 class _Chains(C.Structure):
     _fields_ = [("nc", C.c_int32), ("group_size", C.c_int32), ("sigma", C.c_void_p),
                 ("seed", C.c_uint64), ("counter", C.c_uint64), ("counter_dev", C.c_void_p)]
+
+
+class _Ffnn(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("is_complex", C.c_int32), ("widths", C.c_void_p),
+                ("params", C.c_void_p)]
 
 
 class _SrBatchItem(C.Structure):
@@ -150,6 +156,9 @@ def load_library(path: str = LIB_PATH):
         "nk_sr_step_symm": (I32, [P, P, P, P, P, P, I64, I32, D, D, I32, D, I32, P, SZ, P, P]),
         "nk_supervised_scratch_bytes": (SZ, [I32, I32, I32, I64]),
         "nk_pt_scratch_bytes": (SZ, [I32, I32, I32, I32, I32, I32]),
+        "nk_ffnn_scratch_bytes": (SZ, [P, I64]),
+        "nk_ffnn_logpsi": (I32, [P, P, I64, P, P, SZ, P]),
+        "nk_ffnn_backward": (I32, [P, P, I64, P, P, P, SZ, P]),
         "nk_pt_sweep": (I32, [P, P, I32, I32, P, P, I32, I32, I32, P, P, P, P, SZ, P]),
         "nk_supervised_step": (I32, [P, P, P, P, I64, I32, D, D, D, I32, P, P, P, SZ, P, P]),
     }
@@ -526,6 +535,66 @@ def nk_supervised_step(rbm: Rbm, sigma, log_target, prec=NK_PREC_FP32, lr: float
         float(beta2), int(step), _ptr(moments), _ptr(grad_out), _ptr(scratch), scratch.numel(),
         _ptr(info_out), _stream(stream)), "nk_supervised_step")
     return info_out
+
+
+class Ffnn:
+    """A dense ln cosh network (widths [n, w_1, .., w_L]) with FP64 master
+    parameters on the device (flat, layer by layer: W_l row-major, then b_l)."""
+
+    def __init__(self, widths, is_complex: bool, device="cuda"):
+        load_library()
+        self.widths = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+        self.is_complex = bool(is_complex)
+        self.n_params = int(sum(int(self.widths[l]) * (int(self.widths[l - 1]) + 1)
+                                for l in range(1, len(self.widths))))
+        self.params = torch.zeros(self.n_params * (2 if is_complex else 1), dtype=torch.float64,
+                                  device=device)
+        self._s = _Ffnn(len(self.widths) - 1, int(is_complex), self.widths.ctypes.data,
+                        self.params.data_ptr())
+
+    def struct(self):
+        return C.byref(self._s)
+
+    def load(self, flat):
+        x = np.asarray(flat)
+        if self.is_complex:
+            x = x.astype(np.complex128)
+            x = np.stack([x.real, x.imag], axis=1).reshape(-1)
+        self.params.copy_(torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)))
+
+    def scratch(self, ns: int, device="cuda"):
+        nb = load_library().nk_ffnn_scratch_bytes(self.struct(), ns)
+        return torch.empty(max(nb, 1), dtype=torch.uint8, device=device)
+
+
+def nk_ffnn_logpsi(f: Ffnn, sigma, logpsi_out=None, scratch=None, stream=None):
+    _require_gpu(sigma, logpsi_out, scratch)
+    ns = sigma.shape[0]
+    if logpsi_out is None:
+        logpsi_out = torch.empty(ns, dtype=torch.complex128, device=sigma.device)
+    if scratch is None:
+        scratch = f.scratch(ns, sigma.device)
+    _check(load_library().nk_ffnn_logpsi(f.struct(), _ptr(sigma), ns, _ptr(logpsi_out),
+                                         _ptr(scratch), scratch.numel(), _stream(stream)),
+           "nk_ffnn_logpsi")
+    return logpsi_out
+
+
+def nk_ffnn_backward(f: Ffnn, sigma, g, grad_out=None, scratch=None, stream=None):
+    """grad_k = sum_s conj(O_sk) g_s (complex128 [P], or float64 [P] if real)."""
+    _require_gpu(sigma, g, grad_out, scratch)
+    ns = sigma.shape[0]
+    if scratch is None:
+        scratch = f.scratch(ns, sigma.device)
+    if grad_out is None:
+        grad_out = torch.empty(f.n_params,
+                               dtype=torch.complex128 if f.is_complex else torch.float64,
+                               device=sigma.device)
+    g = g.to(torch.complex128).contiguous()
+    _check(load_library().nk_ffnn_backward(f.struct(), _ptr(sigma), ns, _ptr(g), _ptr(grad_out),
+                                           _ptr(scratch), scratch.numel(), _stream(stream)),
+           "nk_ffnn_backward")
+    return grad_out
 
 
 class SrBatch:

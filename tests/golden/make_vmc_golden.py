@@ -4,7 +4,12 @@ Calls only the FP64 oracle (oracle/) and the seeded input generators.  Output:
 tests/golden/vmc_<name>.json with the per-iteration energies and the mean and
 blocked error bar (blocks of 10) of the last 50 iterations.
 
-    python tests/golden/make_vmc_golden.py [tfim10|heis12] ...
+    python tests/golden/make_vmc_golden.py [tfim10|heis12|c2|c4_0|c4_2|c4_3|c4_8] ...
+
+Runs: tfim10 (the 10-site TFIM workload), heis12 (a 12-site Heisenberg ring),
+c2 (the 40-site Heisenberg workload: complex RBM alpha = 2, 4096 chains x 4
+samples, 50 CG iterations), c4_<k> (instance k of the 64 uneven 1D instances,
+1024 chains x 4 samples, 50 CG iterations).
 """
 import json
 import os
@@ -25,6 +30,15 @@ RUNS = {
     # 1D Heisenberg N=12 (Marshall-rotated), complex RBM alpha=2, exchange moves,
     # 256 chains x 4 samples, CG 50 iterations; 150 iterations
     "heis12": dict(workload=None, n_iter=150, lr=0.02),
+    # 1D Heisenberg N=40 (Marshall-rotated, S^z = 0), complex RBM alpha=2 (M=80),
+    # exchange moves, 4096 chains x 4 samples, CG 50 iterations; 150 iterations
+    "c2": dict(workload="c2", n_iter=150, lr=0.01),
+    # instances of the 64 uneven 1D problems (seed 4242): TFIM n=82 alpha=4,
+    # Heisenberg n=32 alpha=4, TFIM n=18 alpha=1, Heisenberg n=64 alpha=2; 100 iterations
+    "c4_0": dict(workload="c4", instance=0, n_iter=100, lr=0.01),
+    "c4_2": dict(workload="c4", instance=2, n_iter=100, lr=0.01),
+    "c4_3": dict(workload="c4", instance=3, n_iter=100, lr=0.01),
+    "c4_8": dict(workload="c4", instance=8, n_iter=100, lr=0.01),
 }
 
 
@@ -40,6 +54,13 @@ def run(name):
         w = W.workload("c1")
         e_exact = hamiltonian.tfim_chain_ground(w.n, 1.0, 1.0)
         n_cg = None
+    elif spec["workload"] in ("c2", "c4"):
+        w = (W.workload("c2") if spec["workload"] == "c2"
+             else W.batched_instances(64, 4242, 1024)[spec["instance"]])
+        # exact ground energy where a closed form exists (TFIM chains of even length)
+        e_exact = (hamiltonian.tfim_chain_ground(w.n, 1.0, 1.0)
+                   if w.move == "flip" and w.n % 2 == 0 else None)
+        n_cg = w.n_cg
     else:
         n = 12
         w = W.Workload("heisenberg1d_n12_alpha2", n, 2 * n, True,

@@ -65,6 +65,60 @@ def test_vmc_energy_matches_oracle(mods, name, prec):
     assert e_or >= g["e_exact"] - 3 * s_or
 
 
+def _criterion(g, energies):
+    e_gpu, s_gpu = blocked(energies)
+    e_or, s_or = g["last50_mean"], g["last50_err"]
+    comb = np.sqrt(s_gpu ** 2 + s_or ** 2)
+    assert abs(e_gpu - e_or) <= 3 * comb, (g["name"], e_gpu, s_gpu, e_or, s_or)
+    if g["e_exact"] is not None:
+        assert e_gpu >= g["e_exact"] - 3 * s_gpu
+        assert e_or >= g["e_exact"] - 3 * s_or
+    return e_gpu, s_gpu, e_or, s_or
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_vmc_energy_matches_oracle_heisenberg40(mods, prec):
+    """The 40-site Heisenberg workload (complex RBM alpha = 2, 4096 chains x 4
+    samples, exchange moves, SR with 50 CG iterations), 150 iterations from the
+    same seeds as the oracle's run (tests/golden/vmc_c2.json)."""
+    nk, VmcSr = mods
+    g = json.load(open(os.path.join(GOLDEN, "vmc_c2.json")))
+    w = W.workload("c2")
+    p = W.init_params(w.n, w.m, w.is_complex, 0.01, w.seed)
+    v = VmcSr(w, p, prec=prec, graph=True)
+    energies = []
+    for _ in range(len(g["energies"])):
+        v.step()
+        energies.append(v.info()["energy"])
+    e_gpu, s_gpu, e_or, s_or = _criterion(g, energies)
+    print(f"\nHeisenberg N=40 prec={prec}: GPU {e_gpu:.4f} +- {s_gpu:.4f}, "
+          f"oracle {e_or:.4f} +- {s_or:.4f}")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_instances_match_oracle_runs(mods, prec):
+    """All 64 uneven 1D instances advanced together (one graph per iteration,
+    batched SR at BF16 hi + lo) for 100 iterations; the energy traces of
+    instances 0, 2, 3 and 8 (TFIM n = 82 alpha 4, Heisenberg n = 32 alpha 4,
+    TFIM n = 18 alpha 1, Heisenberg n = 64 alpha 2) against the oracle's runs of
+    those instances alone (tests/golden/vmc_c4_*.json)."""
+    nk, _ = mods
+    from paper_1904_00031_gb300.batch import BatchedVmc
+    insts = W.batched_instances(64, 4242, 1024)
+    b = BatchedVmc(insts, prec=prec, graph=True)
+    keys = [0, 2, 3, 8]
+    goldens = {k: json.load(open(os.path.join(GOLDEN, f"vmc_c4_{k}.json"))) for k in keys}
+    traces = {k: [] for k in keys}
+    for _ in range(len(goldens[0]["energies"])):
+        b.step()
+        for k in keys:
+            traces[k].append(b.items[k].info()["energy"])
+    for k in keys:
+        e_gpu, s_gpu, e_or, s_or = _criterion(goldens[k], traces[k])
+        print(f"\ninstance {k} prec={prec}: GPU {e_gpu:.4f} +- {s_gpu:.4f}, "
+              f"oracle {e_or:.4f} +- {s_or:.4f}")
+
+
 def test_heisenberg20_listing_run(mods):
     """The VMC listing of Sec. 3.1 (1D Heisenberg N=20, S^z=0, RBM alpha=1, init
     sigma 0.01 seed 1234, exchange moves, 1000 samples per iteration, SR with an
