@@ -435,7 +435,14 @@ nk_status nk_ffnn_backward(const nk_ffnn* f, const int8_t* sigma, int64_t ns, co
  * Every item passes all argument and shape checks of the single call before
  * anything is enqueued; on a failure the status names the first bad item (via
  * nk_last_error) and nothing is enqueued.  Results are identical to the single
- * calls.  Kernels are launched per item, in item order. */
+ * calls.  Items with a stream of their own are launched per item, in item
+ * order; all the others run fused on `stream`: one launch of each kernel for
+ * every group of items that share its template (sampling: the move-table
+ * builds of all items, one sweep launch per group of equal field, hidden units
+ * per lane, warps per chain and group size, one device-counter launch; ln psi:
+ * one launch per field; local energies: the move tables of all items, one
+ * energy launch per field), each item running the arithmetic of its own call.
+ * (With graph capture, the fused launches are single nodes.) */
 typedef struct nk_logpsi_item {
   const nk_rbm* rbm;
   const int8_t* sigma;  /* int8 [ns][n] */

@@ -16,10 +16,29 @@ from . import workloads as W
 from .vmc import VmcSr, adj_centres, centring_fused
 
 
+def _metro_template(w) -> tuple:
+    """The Metropolis kernel template an instance runs (field, hidden units per
+    lane, warps per chain, group size): the library's rule, for counting the
+    fused launches."""
+    mp = (w.m + 31) // 32 * 32
+    wpc = 2 if (mp >= 512 and w.group_size * 64 <= 512) else 1
+    e = (mp + 32 * wpc - 1) // (32 * wpc)
+    lists = {(True, 1): [2, 4, 8, 16, 32, 64], (True, 2): [8, 14, 16, 26, 32],
+             (False, 1): [1, 2, 4, 8, 16, 32, 64], (False, 2): [8, 13, 16, 25, 32]}
+    nu = next(x for x in lists[(w.is_complex, wpc)] if x >= e)
+    return (w.is_complex, nu, wpc, w.group_size)
+
+
 class BatchedVmc:
     def __init__(self, instances, prec: int = nk.NK_PREC_FP32, device="cuda",
                  graph: bool = True, param_scale: float = 0.01, batch_sr: bool = True,
-                 sr_splits: int = 0):
+                 sr_splits: int = 0, fused: bool = True):
+        """``fused``: sampling, theta and local energies of all instances run as
+        fused launches (nk_batch_sweep / nk_batch_logpsi / nk_batch_local_energy
+        on one stream); else every instance launches its own kernels on a stream
+        of its own."""
+        self.fused = fused
+        self.prec = prec
         self.items = []
         for w in instances:
             p = W.init_params(w.n, w.m, w.is_complex, param_scale, w.seed)
@@ -27,6 +46,16 @@ class BatchedVmc:
             v.rbm._s.sr_splits = int(sr_splits)  # 0: built-in (per call, or batch-wide) default
             self.items.append(v)
         self.streams = [torch.cuda.Stream(device=device) for _ in instances]
+        self.sweep_jobs = [dict(rbm=v.rbm, chains=v.chains, move=v.move, bond_i=v.bond_i,
+                                bond_k=v.bond_k, n_discard=v.w.n_discard,
+                                n_samples_per_chain=v.w.samples_per_chain, samples_out=v.samples,
+                                n_accept_out=v.n_acc, scratch=v.metro_scratch)
+                           for v in self.items]
+        self.theta_jobs = [dict(rbm=v.rbm, sigma=v.samples, logpsi_out=None, theta_out=v.theta)
+                           for v in self.items]
+        self.eloc_jobs = [dict(rbm=v.rbm, op=v.op, sigma=v.samples, theta=v.theta,
+                               eloc_out=v.eloc, t_out=v.t, scratch=v.eloc_scratch)
+                          for v in self.items]
         self.use_graph = graph
         self.graph = None
         ws = list(instances)
@@ -45,6 +74,17 @@ class BatchedVmc:
         return sum(v.ns for v in self.items)
 
     def _eager_step(self):
+        if self.fused:
+            nk.nk_batch_sweep(self.sweep_jobs)
+            nk.nk_batch_logpsi(self.theta_jobs, prec=self.prec)
+            nk.nk_batch_local_energy(self.eloc_jobs)
+            if self.srb is not None:
+                d, lr, n_cg = self.sr_args
+                self.srb.step(d, lr, n_cg)
+            else:
+                for v in self.items:
+                    v.sr()
+            return
         cur = torch.cuda.current_stream()
         for v, st in zip(self.items, self.streams):
             st.wait_stream(cur)
@@ -82,9 +122,21 @@ class BatchedVmc:
         return [v.info() for v in self.items]
 
     def launches_per_step(self) -> int:
-        if self.srb is None:
+        if self.fused:
+            fields = len({v.w.is_complex for v in self.items})
+            tables = any(v.w.is_complex or v.w.move == "exchange" for v in self.items)
+            # sampling: tables (complex RBMs, exchange moves), one sweep launch per
+            # kernel template, device counters (graph mode); up to 64 items per launch
+            n = int(tables) + len({_metro_template(v.w) for v in self.items})
+            n += 1 if self.use_graph else 0
+            n += fields            # theta
+            n += 1 + fields        # move tables, local energies
+        elif self.srb is None:
             return sum(v.launches_per_step() for v in self.items)
-        n = sum(v.launches_per_step() - v.sr_launches() for v in self.items)
+        else:
+            n = sum(v.launches_per_step() - v.sr_launches() for v in self.items)
+        if self.srb is None:
+            return n + sum(v.sr_launches() for v in self.items)
         groups = (len(self.items) + 63) // 64   # up to 64 instances per launch
         # per group: statistics (3), flags, sigma' planes (2), force, CG start (2),
         # 7 per CG iteration (6 when every forward writes its centring partials, 5

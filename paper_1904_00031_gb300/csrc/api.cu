@@ -466,30 +466,109 @@ nk_status nk_local_energy(const nk_rbm* rbm, const void* op_dev, int32_t n_moves
 
 nk_status nk_batch_logpsi(const nk_logpsi_item* items, int32_t n_inst, int32_t prec,
                           void* stream) {
-  return run_batch("nk_batch_logpsi", items, n_inst, stream,
-                   [prec](const nk_logpsi_item& it, void* st, bool dry) {
-                     return logpsi_call(it.rbm, it.sigma, it.ns, prec, it.logpsi_out,
-                                        it.theta_out, st, dry);
-                   });
+  auto call = [prec](const nk_logpsi_item& it, void* st, bool dry) {
+    return logpsi_call(it.rbm, it.sigma, it.ns, prec, it.logpsi_out, it.theta_out, st, dry);
+  };
+  if (n_inst < 0 || (n_inst > 0 && !items))
+    return fail(NK_ERR_INVALID_ARG, "nk_batch_logpsi: bad item array");
+  char msg[512];
+  for (int32_t k = 0; k < n_inst; ++k) {
+    if (nk_status e = call(items[k], items[k].stream ? items[k].stream : stream, true)) {
+      snprintf(msg, sizeof(msg), "%s", g_err);
+      return fail(e, "nk_batch_logpsi item %d: %s", k, msg);
+    }
+  }
+  // items on their own streams: one call each; the others fused on `stream`
+  std::vector<int> fused;
+  for (int32_t k = 0; k < n_inst; ++k) {
+    const nk_logpsi_item& it = items[k];
+    if (it.stream) {
+      if (nk_status e = call(it, it.stream, false)) {
+        snprintf(msg, sizeof(msg), "%s", g_err);
+        return fail(e, "nk_batch_logpsi item %d: %s", k, msg);
+      }
+    } else if (it.ns > 0) {
+      fused.push_back(k);
+    }
+  }
+  if (fused.empty()) return NK_OK;
+  return prec == NK_PREC_FP32
+             ? launch_logpsi_fp32_fused(items, fused.data(), (int)fused.size(),
+                                        (cudaStream_t)stream)
+             : launch_logpsi_bf16_fused(items, fused.data(), (int)fused.size(),
+                                        (cudaStream_t)stream);
 }
 
 nk_status nk_batch_sweep(const nk_sweep_item* items, int32_t n_inst, void* stream) {
-  return run_batch("nk_batch_sweep", items, n_inst, stream,
-                   [](const nk_sweep_item& it, void* st, bool dry) {
-                     return sweep_call(it.rbm, it.chains, it.move, it.bond_i, it.bond_k,
-                                       it.n_bonds, it.n_discard, it.n_samples_per_chain,
-                                       it.samples_out, it.n_accept_out, it.scratch,
-                                       it.scratch_bytes, st, dry);
-                   });
+  auto call = [](const nk_sweep_item& it, void* st, bool dry) {
+    return sweep_call(it.rbm, it.chains, it.move, it.bond_i, it.bond_k, it.n_bonds,
+                      it.n_discard, it.n_samples_per_chain, it.samples_out, it.n_accept_out,
+                      it.scratch, it.scratch_bytes, st, dry);
+  };
+  if (n_inst < 0 || (n_inst > 0 && !items))
+    return fail(NK_ERR_INVALID_ARG, "nk_batch_sweep: bad item array");
+  char msg[512];
+  for (int32_t k = 0; k < n_inst; ++k) {
+    if (nk_status e = call(items[k], items[k].stream ? items[k].stream : stream, true)) {
+      snprintf(msg, sizeof(msg), "%s", g_err);
+      return fail(e, "nk_batch_sweep item %d: %s", k, msg);
+    }
+  }
+  // items on their own streams: one call each; the others fused on `stream`
+  std::vector<int> fused;
+  for (int32_t k = 0; k < n_inst; ++k) {
+    const nk_sweep_item& it = items[k];
+    if (it.stream) {
+      if (nk_status e = call(it, it.stream, false)) {
+        snprintf(msg, sizeof(msg), "%s", g_err);
+        return fail(e, "nk_batch_sweep item %d: %s", k, msg);
+      }
+    } else if (it.chains->nc > 0 && it.n_discard + it.n_samples_per_chain > 0) {
+      fused.push_back(k);
+    }
+  }
+  if (!fused.empty()) {
+    if (nk_status e = launch_metropolis_fused(items, fused.data(), (int)fused.size(),
+                                              (cudaStream_t)stream))
+      return e;
+    for (int k : fused)
+      items[k].chains->counter +=
+          (uint64_t)(items[k].n_discard + items[k].n_samples_per_chain) * items[k].rbm->n;
+  }
+  return NK_OK;
 }
 
 nk_status nk_batch_local_energy(const nk_eloc_item* items, int32_t n_inst, void* stream) {
-  return run_batch("nk_batch_local_energy", items, n_inst, stream,
-                   [](const nk_eloc_item& it, void* st, bool dry) {
-                     return eloc_call(it.rbm, it.op_dev, it.n_moves, it.sigma, it.theta, it.ns,
-                                      it.eloc_out, it.t_out, it.scratch, it.scratch_bytes, st,
-                                      dry);
-                   });
+  auto call = [](const nk_eloc_item& it, void* st, bool dry) {
+    return eloc_call(it.rbm, it.op_dev, it.n_moves, it.sigma, it.theta, it.ns, it.eloc_out,
+                     it.t_out, it.scratch, it.scratch_bytes, st, dry);
+  };
+  if (n_inst < 0 || (n_inst > 0 && !items))
+    return fail(NK_ERR_INVALID_ARG, "nk_batch_local_energy: bad item array");
+  char msg[512];
+  for (int32_t k = 0; k < n_inst; ++k) {
+    if (nk_status e = call(items[k], items[k].stream ? items[k].stream : stream, true)) {
+      snprintf(msg, sizeof(msg), "%s", g_err);
+      return fail(e, "nk_batch_local_energy item %d: %s", k, msg);
+    }
+  }
+  // items on their own streams: one call each; the others fused on `stream`
+  std::vector<int> fused;
+  for (int32_t k = 0; k < n_inst; ++k) {
+    const nk_eloc_item& it = items[k];
+    if (it.stream) {
+      if (nk_status e = call(it, it.stream, false)) {
+        snprintf(msg, sizeof(msg), "%s", g_err);
+        return fail(e, "nk_batch_local_energy item %d: %s", k, msg);
+      }
+    } else if (it.ns > 0) {
+      fused.push_back(k);
+    }
+  }
+  if (!fused.empty())
+    return launch_local_energy_fused(items, fused.data(), (int)fused.size(),
+                                     (cudaStream_t)stream);
+  return NK_OK;
 }
 
 nk_status nk_logderiv(const nk_rbm* rbm, const int8_t* sigma, const void* theta, int64_t ns,

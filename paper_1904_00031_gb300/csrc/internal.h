@@ -35,6 +35,11 @@ nk_status launch_logpsi_fp32(const nk_rbm* r, const int8_t* sigma, int64_t ns, d
                              void* theta_out, cudaStream_t st, void* t_out = nullptr);
 nk_status launch_logpsi_bf16(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,
                              void* theta_out, cudaStream_t st, void* t_out = nullptr);
+// The theta / ln psi calls of items[idx[0..n)] fused: one launch per field.
+nk_status launch_logpsi_fp32_fused(const nk_logpsi_item* items, const int* idx, int n,
+                                   cudaStream_t st);
+nk_status launch_logpsi_bf16_fused(const nk_logpsi_item* items, const int* idx, int n,
+                                   cudaStream_t st);
 
 // Parallel-tempering options of a Metropolis launch: chain c is replica c % R of
 // its ladder (beta = 1 - (c % R) / R); lval (if set) receives 2 Re ln psi of every
@@ -51,11 +56,19 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
                             int8_t* samples, uint64_t* n_acc, void* scratch, size_t scratch_bytes,
                             cudaStream_t st, bool dry = false, const MetroPt* pt = nullptr);
 size_t metropolis_scratch_bytes(int n, int m, int cplx, int move, int nb);
+// The sweeps of items[idx[0..n)] fused into one table launch, one sweep launch per
+// kernel template and one counter launch (items already checked).
+nk_status launch_metropolis_fused(const nk_sweep_item* items, const int* idx, int n,
+                                  cudaStream_t st);
 
 nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
                               const int8_t* sigma, const void* theta, int64_t ns, double* eloc,
                               void* t_out, void* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t local_energy_scratch_bytes(int m, int cplx, int n_moves);
+// The local energies of items[idx[0..n)] fused into one move-table launch and one
+// energy launch per field (items already checked).
+nk_status launch_local_energy_fused(const nk_eloc_item* items, const int* idx, int n,
+                                    cudaStream_t st);
 nk_status launch_logderiv(const nk_rbm* r, const int8_t* sigma, const void* theta, int64_t ns,
                           int layout, void* o_out, cudaStream_t st);
 

@@ -83,36 +83,75 @@ __device__ __forceinline__ typename RatioTypes<CPLX>::T2 move_column(const OpMov
 // slot s = (Re C_a, Re C_b, Im C_a, Im C_b), then the D plane (same for
 // D = sinh c / s_i), so that one 16-byte load gives a thread the operands of
 // two moves as packed FP32 pairs.
+// Element x of the table (complex: of mp * ntile * 32 slot pairs; real: of mp * nm_pad)
+template <bool CPLX>
+__device__ __forceinline__ void move_table_elem(int64_t x, const OpMove* __restrict__ mvs,
+                                                const void* __restrict__ tabv, int mp, int nm,
+                                                int nm_pad, void* outv) {
+  if constexpr (CPLX) {
+    float4* out = reinterpret_cast<float4*>(outv);
+    const int ntile = nm_pad / kEBM;
+    const int slot = (int)(x & 31);
+    const int64_t jt = x >> 5;
+    const int j = (int)(jt / ntile), mt = (int)(jt % ntile);
+    const int a = mt * kEBM + (slot & 15) + 32 * (slot >> 4), b = a + 16;
+    const float4 za = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 va = a < nm ? move_column<true>(mvs[a], tabv, mp, j) : za;
+    const float4 vb = b < nm ? move_column<true>(mvs[b], tabv, mp, j) : za;
+    float4* row = out + ((int64_t)j * ntile + mt) * 64;
+    row[slot] = make_float4(va.x, vb.x, va.y, vb.y);
+    row[32 + slot] = make_float4(va.z, vb.z, va.w, vb.w);
+  } else {
+    float2* out = reinterpret_cast<float2*>(outv);
+    const int j = (int)(x / nm_pad), mv = (int)(x % nm_pad);
+    out[x] = mv < nm ? move_column<false>(mvs[mv], tabv, mp, j) : make_float2(0.f, 0.f);
+  }
+}
+
+__host__ __device__ inline int64_t move_table_elems(int cplx, int mp, int nm_pad) {
+  return cplx ? (int64_t)mp * (nm_pad / kEBM) * 32 : (int64_t)mp * nm_pad;
+}
+
 template <bool CPLX>
 __global__ void move_tables_kernel(const char* __restrict__ op, const void* __restrict__ tabv,
                                    int mp, int nm, int nm_pad, void* outv) {
   const OpDevHeader* H = reinterpret_cast<const OpDevHeader*>(op);
   const OpMove* mvs = reinterpret_cast<const OpMove*>(op + H->off_moves);
-  if constexpr (CPLX) {
-    float4* out = reinterpret_cast<float4*>(outv);
-    const int ntile = nm_pad / kEBM;
-    const int64_t total = (int64_t)mp * ntile * 32;
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
-         x += (int64_t)gridDim.x * blockDim.x) {
-      const int slot = (int)(x & 31);
-      const int64_t jt = x >> 5;
-      const int j = (int)(jt / ntile), mt = (int)(jt % ntile);
-      const int a = mt * kEBM + (slot & 15) + 32 * (slot >> 4), b = a + 16;
-      const float4 za = make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 va = a < nm ? move_column<true>(mvs[a], tabv, mp, j) : za;
-      const float4 vb = b < nm ? move_column<true>(mvs[b], tabv, mp, j) : za;
-      float4* row = out + ((int64_t)j * ntile + mt) * 64;
-      row[slot] = make_float4(va.x, vb.x, va.y, vb.y);
-      row[32 + slot] = make_float4(va.z, vb.z, va.w, vb.w);
+  const int64_t total = move_table_elems(CPLX, mp, nm_pad);
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x)
+    move_table_elem<CPLX>(x, mvs, tabv, mp, nm, nm_pad, outv);
+}
+
+// The move tables of many problems in one launch (job k owns elements
+// [start[k], start[k + 1]) of the concatenated range; real and complex jobs mix).
+constexpr int kMoveJobs = 64;
+struct MoveTableJob {
+  int cplx, mp, nm, nm_pad;
+  const char* op;
+  const void* tab;
+  void* out;
+};
+struct MoveTableBatch {
+  int n;
+  int64_t start[kMoveJobs + 1];
+  MoveTableJob j[kMoveJobs];
+};
+
+__global__ void move_tables_batch_kernel(const __grid_constant__ MoveTableBatch B) {
+  const int64_t total = B.start[B.n];
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = B.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (B.start[mid] <= x) lo = mid; else hi = mid - 1;
     }
-  } else {
-    float2* out = reinterpret_cast<float2*>(outv);
-    const int64_t total = (int64_t)mp * nm_pad;
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
-         x += (int64_t)gridDim.x * blockDim.x) {
-      const int j = (int)(x / nm_pad), mv = (int)(x % nm_pad);
-      out[x] = mv < nm ? move_column<false>(mvs[mv], tabv, mp, j) : make_float2(0.f, 0.f);
-    }
+    const MoveTableJob& J = B.j[lo];
+    const OpDevHeader* H = reinterpret_cast<const OpDevHeader*>(J.op);
+    const OpMove* mvs = reinterpret_cast<const OpMove*>(J.op + H->off_moves);
+    if (J.cplx) move_table_elem<true>(x - B.start[lo], mvs, J.tab, J.mp, J.nm, J.nm_pad, J.out);
+    else move_table_elem<false>(x - B.start[lo], mvs, J.tab, J.mp, J.nm, J.nm_pad, J.out);
   }
 }
 
@@ -136,8 +175,8 @@ __device__ __forceinline__ void renorm_pair(float2& x, float2& y, int& e) {
 }
 
 template <bool CPLX>
-__global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_constant__ CUtensorMap mtab,
-                                                          ElocArgs A) {
+__device__ __forceinline__ void local_energy_body(const CUtensorMap* mtab, const ElocArgs& A,
+                                                  const int tile_idx, const int seg) {
   using F = typename RatioTypes<CPLX>::F;
   using T2 = typename RatioTypes<CPLX>::T2;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -154,7 +193,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   uint64_t* mbar = reinterpret_cast<uint64_t*>(eacc + 4 * 256);              // [2]
 
   const int tid = threadIdx.x, ts = tid >> 4, tm = tid & 15;
-  const int64_t s0 = (int64_t)(A.seg_fast ? blockIdx.y : blockIdx.x) * kEBS;
+  const int64_t s0 = (int64_t)tile_idx * kEBS;
   const int n = A.n, m = A.m, mp = A.mp;
   const OpDevHeader* H = reinterpret_cast<const OpDevHeader*>(A.op);
   const OpDSite* ds = reinterpret_cast<const OpDSite*>(A.op + H->off_dsite);
@@ -165,7 +204,6 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   const int nm = A.n_moves;
   const bool quad = (H->flags & kOpQuadMoves) != 0;  // site-quad move layout
   const int ntile = (nm + kEBM - 1) / kEBM, nchunk = mp / kEBK;
-  const int seg = A.seg_fast ? blockIdx.x : blockIdx.y;
   const int tile_begin = ntile * seg / A.nseg, tile_end = ntile * (seg + 1) / A.nseg;
   const int it_begin = tile_begin * nchunk, it_end = tile_end * nchunk;
   const uint32_t tile_bytes = kEBK * kEBM * sizeof(T2);
@@ -248,7 +286,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   if (it_end > it_begin) {
     if (tid == 0) {
       mbar_arrive_expect_tx(&mbar[0], tile_bytes);
-      tma_load_2d(mvt, &mtab, tile_begin * kEBM * (CPLX ? 4 : 2), 0, &mbar[0]);
+      tma_load_2d(mvt, mtab, tile_begin * kEBM * (CPLX ? 4 : 2), 0, &mbar[0]);
     }
     load_t(it_begin);
     store_t(it_begin, 0);
@@ -336,7 +374,7 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
     if (tid == 0 && it + 1 < it_end) {
       const int it1 = it + 1;
       mbar_arrive_expect_tx(&mbar[b ^ 1], tile_bytes);
-      tma_load_2d(mvt + (size_t)(b ^ 1) * kEBK * kEBM, &mtab,
+      tma_load_2d(mvt + (size_t)(b ^ 1) * kEBK * kEBM, mtab,
                       (it1 / nchunk) * kEBM * (CPLX ? 4 : 2), chunk_of(it1) * kEBK, &mbar[b ^ 1]);
     }
     if (it + 1 < it_end) load_t(it + 1);
@@ -509,20 +547,59 @@ __global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_consta
   }
 }
 
+template <bool CPLX>
+__global__ void __launch_bounds__(256, 2) local_energy_tiled(const __grid_constant__ CUtensorMap mtab,
+                                                          ElocArgs A) {
+  local_energy_body<CPLX>(&mtab, A, A.seg_fast ? blockIdx.y : blockIdx.x,
+                          A.seg_fast ? blockIdx.x : blockIdx.y);
+}
+
+// Up to kElocBatch problems of one field in one launch: CTA b runs CTA
+// b - start[k] of problem k, numbered as its own launch with the segment as
+// the fast index (the two halves of a configuration tile back to back).
+constexpr int kElocBatch = 64;
+struct ElocBatch {
+  int n;
+  int start[kElocBatch + 1];
+  ElocArgs a[kElocBatch];
+  CUtensorMap map[kElocBatch];
+};
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256, 2) local_energy_batch(const __grid_constant__ ElocBatch B) {
+  int k = 0;
+  while (k + 1 < B.n && (int)blockIdx.x >= B.start[k + 1]) ++k;
+  const int b = (int)blockIdx.x - B.start[k];
+  const ElocArgs& A = B.a[k];
+  local_energy_body<CPLX>(&B.map[k], A, b / A.nseg, b % A.nseg);
+}
+
 size_t local_energy_scratch_bytes(int m, int cplx, int n_moves) {
   const int64_t nm_pad = round_up(std::max(n_moves, 1), kEBM);
   return (size_t)round_up((int64_t)padded_m(m) * nm_pad * (cplx ? 16 : 8), 256);
 }
 
-nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
-                              const int8_t* sigma, const void* theta, int64_t ns, double* eloc,
-                              void* t_out, void* scratch, size_t scratch_bytes, cudaStream_t st) {
+// Everything one local-energy call needs, before anything is enqueued.
+struct ElocPlan {
+  ElocArgs A;
+  CUtensorMap map;
+  bool cplx;
+  size_t smem;
+  int64_t blocks;  // configuration tiles
+  MoveTableJob job;
+  int64_t tab_elems;
+};
+
+static nk_status plan_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
+                                   const int8_t* sigma, const void* theta, int64_t ns,
+                                   double* eloc, void* t_out, void* scratch, size_t scratch_bytes,
+                                   ElocPlan* P) {
   WsLayout L(r->n, r->m, r->is_complex);
   const bool cplx = r->is_complex != 0;
   const size_t need = local_energy_scratch_bytes(r->m, cplx, n_moves);
   if (n_moves > 0 && (!scratch || scratch_bytes < need))
     return fail(NK_ERR_SHAPE, "nk_local_energy: scratch of %zu B, need %zu B", scratch_bytes, need);
-  ElocArgs A;
+  ElocArgs& A = P->A;
   A.n = r->n;
   A.m = r->m;
   A.mp = L.mp;
@@ -535,28 +612,21 @@ nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
   A.tab = (const char*)r->ws + L.tab;
   A.eloc = eloc;
   A.t_out = t_out;
+  P->cplx = cplx;
   const int nm_pad = (int)round_up(std::max(n_moves, 1), kEBM);
-  CUtensorMap map;
-  memset(&map, 0, sizeof(map));
+  memset(&P->map, 0, sizeof(P->map));
+  P->job = MoveTableJob{cplx ? 1 : 0, L.mp, n_moves, nm_pad, A.op, A.tab, scratch};
+  P->tab_elems = n_moves > 0 ? move_table_elems(cplx, L.mp, nm_pad) : 0;
   if (n_moves > 0) {
-    const int64_t tot = (int64_t)L.mp * nm_pad / (cplx ? 2 : 1);  // complex: a move pair per thread
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 8));
-    if (cplx)
-      move_tables_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(A.op, A.tab, L.mp, n_moves,
-                                                                 nm_pad, scratch);
-    else
-      move_tables_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(A.op, A.tab, L.mp, n_moves,
-                                                                  nm_pad, scratch);
-    if (nk_status e = check_launch("nk_local_energy(move tables)")) return e;
     const int fl = cplx ? 4 : 2;  // floats per table entry
-    if (!make_map_f32(&map, scratch, L.mp, (int64_t)nm_pad * fl, (int64_t)nm_pad * fl * 4,
+    if (!make_map_f32(&P->map, scratch, L.mp, (int64_t)nm_pad * fl, (int64_t)nm_pad * fl * 4,
                       kEBM * fl, kEBK))
       return NK_ERR_CUDA;
   }
   const size_t t2 = cplx ? 16 : 8, f = cplx ? 16 : 4;  // table entry, t tile entry
-  const size_t smem = 2 * kEBK * kEBM * t2 + round_up(2 * kEBK * kETS * f, 16) + 3 * kEBM * 4 +
-                      kEBM * 4 * 16 + 4 * 256 * 16 + 16;
-  const int64_t blocks = (ns + kEBS - 1) / kEBS;
+  P->smem = 2 * kEBK * kEBM * t2 + round_up(2 * kEBK * kETS * f, 16) + 3 * kEBM * 4 +
+            kEBM * 4 * 16 + 4 * 256 * 16 + 16;
+  P->blocks = (ns + kEBS - 1) / kEBS;
   // two CTAs per SM: when the last wave of CTAs would be far from full, split
   // the move tiles into two halves (twice the CTAs) to even out the waves
   const int ntile = (n_moves + kEBM - 1) / kEBM;
@@ -564,25 +634,118 @@ nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
     const int64_t slots = 2 * 152;
     return (double)b / (double)(((b + slots - 1) / slots) * slots);
   };
-  A.nseg = (ntile >= 2 && wave_eff(2 * blocks) > wave_eff(blocks)) ? 2 : 1;
+  A.nseg = (ntile >= 2 && wave_eff(2 * P->blocks) > wave_eff(P->blocks)) ? 2 : 1;
+  A.seg_fast = A.nseg == 2 && P->blocks <= 65535 ? 1 : 0;
+  return NK_OK;
+}
+
+nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
+                              const int8_t* sigma, const void* theta, int64_t ns, double* eloc,
+                              void* t_out, void* scratch, size_t scratch_bytes, cudaStream_t st) {
+  ElocPlan P;
+  if (nk_status e = plan_local_energy(r, op_dev, n_moves, sigma, theta, ns, eloc, t_out, scratch,
+                                      scratch_bytes, &P))
+    return e;
+  const ElocArgs& A = P.A;
+  if (P.tab_elems > 0) {
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((P.tab_elems + 255) / 256, 152 * 8));
+    if (P.cplx)
+      move_tables_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(A.op, A.tab, A.mp, n_moves,
+                                                                 P.job.nm_pad, scratch);
+    else
+      move_tables_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(A.op, A.tab, A.mp, n_moves,
+                                                                  P.job.nm_pad, scratch);
+    if (nk_status e = check_launch("nk_local_energy(move tables)")) return e;
+  }
   if (A.nseg == 2 &&
       cudaMemsetAsync(eloc, 0, (size_t)ns * 2 * sizeof(double), st) != cudaSuccess)
     return fail(NK_ERR_CUDA, "nk_local_energy: cudaMemsetAsync failed");
-  A.seg_fast = A.nseg == 2 && blocks <= 65535 ? 1 : 0;
-  const dim3 grid = A.seg_fast ? dim3((unsigned)A.nseg, (unsigned)blocks)
-                               : dim3((unsigned)blocks, (unsigned)A.nseg);
-  if (cplx) {
+  const dim3 grid = A.seg_fast ? dim3((unsigned)A.nseg, (unsigned)P.blocks)
+                               : dim3((unsigned)P.blocks, (unsigned)A.nseg);
+  if (P.cplx) {
     if (cudaFuncSetAttribute(local_energy_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+                             (int)P.smem) != cudaSuccess)
       return fail(NK_ERR_CUDA, "nk_local_energy: shared memory attribute");
-    local_energy_tiled<true><<<grid, 256, smem, st>>>(map, A);
+    local_energy_tiled<true><<<grid, 256, P.smem, st>>>(P.map, A);
   } else {
     if (cudaFuncSetAttribute(local_energy_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+                             (int)P.smem) != cudaSuccess)
       return fail(NK_ERR_CUDA, "nk_local_energy: shared memory attribute");
-    local_energy_tiled<false><<<grid, 256, smem, st>>>(map, A);
+    local_energy_tiled<false><<<grid, 256, P.smem, st>>>(P.map, A);
   }
   return check_launch("nk_local_energy");
+}
+
+// Fused local energies of many problems: one move-table launch for all of them,
+// one launch of the energy kernel per field (at most kElocBatch problems each).
+// Every problem runs its own launch's arithmetic and move-tile split, so the
+// results are those of separate calls.
+nk_status launch_local_energy_fused(const nk_eloc_item* items, const int* idx, int n,
+                                    cudaStream_t st) {
+  std::vector<ElocPlan> plans((size_t)n);
+  for (int u = 0; u < n; ++u) {
+    const nk_eloc_item& it = items[idx[u]];
+    if (nk_status e = plan_local_energy(it.rbm, it.op_dev, it.n_moves, it.sigma, it.theta, it.ns,
+                                        it.eloc_out, it.t_out, it.scratch, it.scratch_bytes,
+                                        &plans[u]))
+      return e;
+  }
+  for (int u0 = 0; u0 < n; u0 += kMoveJobs) {
+    MoveTableBatch TB;
+    TB.n = 0;
+    TB.start[0] = 0;
+    for (int u = u0; u < std::min(n, u0 + kMoveJobs); ++u) {
+      if (plans[u].tab_elems == 0) continue;
+      TB.j[TB.n] = plans[u].job;
+      TB.start[TB.n + 1] = TB.start[TB.n] + plans[u].tab_elems;
+      ++TB.n;
+    }
+    if (TB.n > 0) {
+      const int64_t blocks =
+          std::max<int64_t>(1, std::min<int64_t>((TB.start[TB.n] + 255) / 256, 152 * 8));
+      move_tables_batch_kernel<<<(unsigned)blocks, 256, 0, st>>>(TB);
+      if (nk_status e = check_launch("nk_batch_local_energy(move tables)")) return e;
+    }
+  }
+  for (int u = 0; u < n; ++u)
+    if (plans[u].A.nseg == 2 &&
+        cudaMemsetAsync(plans[u].A.eloc, 0, (size_t)plans[u].A.ns * 2 * sizeof(double), st) !=
+            cudaSuccess)
+      return fail(NK_ERR_CUDA, "nk_batch_local_energy: cudaMemsetAsync failed");
+  for (int field = 0; field < 2; ++field) {
+    const bool cplx = field == 1;
+    for (int u0 = 0; u0 < n;) {
+      ElocBatch* B = new ElocBatch;  // about 11 KB: kept off the stack
+      B->n = 0;
+      B->start[0] = 0;
+      size_t smem = 0;
+      int u = u0;
+      for (; u < n && B->n < kElocBatch; ++u) {
+        const ElocPlan& P = plans[u];
+        if (P.cplx != cplx || P.blocks == 0) continue;
+        B->a[B->n] = P.A;
+        B->map[B->n] = P.map;
+        B->start[B->n + 1] = B->start[B->n] + (int)(P.blocks * P.A.nseg);
+        ++B->n;
+        smem = std::max(smem, P.smem);
+      }
+      u0 = u;
+      nk_status e = NK_OK;
+      if (B->n > 0) {
+        auto kern = cplx ? local_energy_batch<true> : local_energy_batch<false>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+          e = fail(NK_ERR_CUDA, "nk_batch_local_energy: shared memory attribute");
+        else {
+          kern<<<(unsigned)B->start[B->n], 256, smem, st>>>(*B);
+          e = check_launch("nk_batch_local_energy");
+        }
+      }
+      delete B;
+      if (e) return e;
+    }
+  }
+  return NK_OK;
 }
 
 // ------------------------------------------------------------------ K4 logderiv

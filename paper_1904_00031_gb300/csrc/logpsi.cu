@@ -1,8 +1,10 @@
 // K1 (FP32 path): ln psi(sigma) = a . sigma + sum_j ln cosh(theta_j),
 // theta = W sigma + b (Sec. 2.2.2: RbmSpin; an RBM is a one-layer FFNN with
 // ln cosh activation).  theta is computed as the augmented contraction
-// [W | b] [sigma; 1] on the CUDA cores, ln cosh is fused into the epilogue and
-// summed per sample in FP64; a . sigma is added in FP64 from the master a.
+// [W | b] [sigma; 1] on the CUDA cores (16-site chunks summed in FP32 and
+// carried with TwoSum: theta to about one FP32 rounding), ln cosh is fused into
+// the epilogue and summed per sample in FP64; a . sigma is added in FP64 from
+// the master a.
 // Without a ln psi output the epilogue only stores theta and / or tanh(theta)
 // (the local energies need theta; the backward recomputes tanh(theta) per
 // chunk of samples).
@@ -90,7 +92,71 @@ __global__ void __launch_bounds__(kSgThreads) logpsi_fp32_kernel(const int8_t* _
   epi.a = a;
   epi.sigma = sigma;
   epi.logpsi = logpsi;
-  sgemm_rowreduce<CPLX>(sigma, ns, n, xw, rows, n + 1, epi);
+  sgemm_rowreduce<CPLX, LogpsiEpi<CPLX>, true>(sigma, ns, n, xw, rows, n + 1, epi);
+}
+
+// Up to kLogpsiBatch problems of one field in one launch: CTA b runs sample
+// tile b - start[k] of problem k, as that problem's own launch would.
+constexpr int kLogpsiBatch = 64;
+struct LogpsiFp32Job {
+  const int8_t* sigma;
+  int64_t ns;
+  int n, m;
+  const void* xw;
+  const double* a;
+  double* logpsi;
+  void* theta_out;
+};
+struct LogpsiFp32Batch {
+  int n;
+  int start[kLogpsiBatch + 1];
+  LogpsiFp32Job j[kLogpsiBatch];
+};
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kSgThreads) logpsi_fp32_batch(const __grid_constant__ LogpsiFp32Batch B) {
+  int k = 0;
+  while (k + 1 < B.n && (int)blockIdx.x >= B.start[k + 1]) ++k;
+  const LogpsiFp32Job& J = B.j[k];
+  LogpsiEpi<CPLX> epi;
+  epi.m = J.m;
+  epi.n = J.n;
+  epi.ns = J.ns;
+  epi.theta_out = reinterpret_cast<typename SgTypes<CPLX>::F*>(J.theta_out);
+  epi.t_out = nullptr;
+  epi.a = J.a;
+  epi.sigma = J.sigma;
+  epi.logpsi = J.logpsi;
+  sgemm_rowreduce<CPLX, LogpsiEpi<CPLX>, true>(J.sigma, J.ns, J.n, J.xw, J.m, J.n + 1, epi,
+                                               (int)blockIdx.x - B.start[k]);
+}
+
+nk_status launch_logpsi_fp32_fused(const nk_logpsi_item* items, const int* idx, int n,
+                                   cudaStream_t st) {
+  for (int field = 0; field < 2; ++field) {
+    for (int u0 = 0; u0 < n;) {
+      LogpsiFp32Batch B;
+      B.n = 0;
+      B.start[0] = 0;
+      int u = u0;
+      for (; u < n && B.n < kLogpsiBatch; ++u) {
+        const nk_logpsi_item& it = items[idx[u]];
+        const nk_rbm* r = it.rbm;
+        if ((r->is_complex ? 1 : 0) != field) continue;
+        WsLayout L(r->n, r->m, r->is_complex);
+        B.j[B.n] = LogpsiFp32Job{it.sigma, it.ns, r->n, r->m, (const char*)r->ws + L.xw, r->a,
+                                 it.logpsi_out, it.theta_out};
+        B.start[B.n + 1] = B.start[B.n] + (int)((it.ns + kSgBS - 1) / kSgBS);
+        ++B.n;
+      }
+      u0 = u;
+      if (B.n == 0) continue;
+      if (field) logpsi_fp32_batch<true><<<B.start[B.n], kSgThreads, 0, st>>>(B);
+      else logpsi_fp32_batch<false><<<B.start[B.n], kSgThreads, 0, st>>>(B);
+      if (nk_status e = check_launch("nk_batch_logpsi")) return e;
+    }
+  }
+  return NK_OK;
 }
 
 nk_status launch_logpsi_fp32(const nk_rbm* r, const int8_t* sigma, int64_t ns, double* logpsi,

@@ -159,7 +159,7 @@ __device__ __forceinline__ void theta_each(uint32_t tm, Fn&& f) {
 
 // NU hidden units per thread (even for complex RBMs), WPC warps per chain.
 template <bool CPLX, int NU, int WPC>
-__global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
+__device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx) {
   using F = typename RatioTypes<CPLX>::F;
   using T2 = typename RatioTypes<CPLX>::T2;
   constexpr int E = NU;
@@ -179,10 +179,10 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int cw = w / WPC, h = w % WPC;
-  const int c = blockIdx.x * G + cw;
-  const int chains_here = min(G, A.nc - (int)blockIdx.x * G);
+  const int c = bx * G + cw;
+  const int chains_here = min(G, A.nc - bx * G);
   const bool active = (cw < G) && (c < A.nc);
-  const uint32_t g = (uint32_t)blockIdx.x;
+  const uint32_t g = (uint32_t)bx;
   int8_t* sg = sgall + (size_t)(active ? w : 0) * n16;  // one copy per warp
   const unsigned char* cdg = reinterpret_cast<const unsigned char*>(A.cd);
   const F* wdg = reinterpret_cast<const F*>(A.wd);
@@ -537,71 +537,159 @@ __global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
   }
 }
 
+template <bool CPLX, int NU, int WPC>
+__global__ void __launch_bounds__(512, 1) metropolis_kernel(MetroArgs A) {
+  metropolis_body<CPLX, NU, WPC>(A, blockIdx.x);
+}
+
+// Up to kMetroBatch independent problems of one kernel template in one launch:
+// CTA b runs block b - start[k] of problem k (start[k] <= b < start[k + 1]), with
+// that problem's arguments, exactly as its own launch would.
+constexpr int kMetroBatch = 64;
+struct MetroBatch {
+  int n;
+  int start[kMetroBatch + 1];
+  MetroArgs a[kMetroBatch];
+};
+
+template <bool CPLX, int NU, int WPC>
+__global__ void __launch_bounds__(512, 1) metropolis_batch_kernel(const __grid_constant__ MetroBatch B) {
+  int k = 0;
+  while (k + 1 < B.n && (int)blockIdx.x >= B.start[k + 1]) ++k;
+  metropolis_body<CPLX, NU, WPC>(B.a[k], (int)blockIdx.x - B.start[k]);
+}
+
 // Per-bond tables of an exchange move of a real RBM (s_k = -s_i):
 // cosh c = A_i A_k - B_i B_k, sinh c / s_i = B_i A_k - A_i B_k, increment W_i - W_k.
+// Element x of nb * mp.
+__device__ __forceinline__ void pair_table_real_elem(int64_t x, const float2* __restrict__ tab,
+                                                     const float* __restrict__ wt,
+                                                     const int32_t* __restrict__ bi,
+                                                     const int32_t* __restrict__ bk, int mp,
+                                                     float2* __restrict__ cd,
+                                                     float* __restrict__ wd) {
+  const int b = (int)(x / mp), j = (int)(x % mp);
+  const int i = bi[b], k = bk[b];
+  const float2 ti = tab[(int64_t)i * mp + j], tk = tab[(int64_t)k * mp + j];
+  cd[x] = make_float2(fmaf(-ti.y, tk.y, ti.x * tk.x), fmaf(-ti.x, tk.y, ti.y * tk.x));
+  wd[x] = wt[(int64_t)i * mp + j] - wt[(int64_t)k * mp + j];
+}
+
 __global__ void pair_tables_real_kernel(const float2* __restrict__ tab, const float* __restrict__ wt,
                                         const int32_t* __restrict__ bi,
                                         const int32_t* __restrict__ bk, int nb, int mp,
                                         float2* __restrict__ cd, float* __restrict__ wd) {
   const int64_t total = (int64_t)nb * mp;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const int b = (int)(x / mp), j = (int)(x % mp);
-    const int i = bi[b], k = bk[b];
-    const float2 ti = tab[(int64_t)i * mp + j], tk = tab[(int64_t)k * mp + j];
-    cd[x] = make_float2(fmaf(-ti.y, tk.y, ti.x * tk.x), fmaf(-ti.x, tk.y, ti.y * tk.x));
-    wd[x] = wt[(int64_t)i * mp + j] - wt[(int64_t)k * mp + j];
-  }
+       x += (int64_t)gridDim.x * blockDim.x)
+    pair_table_real_elem(x, tab, wt, bi, bk, mp, cd, wd);
 }
 
 // Pair rows of a complex RBM (layout of cplx_row_bytes): one per site (flips,
 // C = A_i, D = B_i) or per bond (exchanges, s_k = -s_i: C = A_i A_k - B_i B_k,
-// D = B_i A_k - A_i B_k, and the increments W_i - W_k into wd).
+// D = B_i A_k - A_i B_k, and the increments W_i - W_k into wd).  Element x of
+// rows * (nu / 2) * wpc * 32.
+__device__ __forceinline__ void cplx_rows_elem(int64_t x, bool pair, const float4* __restrict__ tab,
+                                               const float2* __restrict__ wt,
+                                               const int32_t* __restrict__ bi,
+                                               const int32_t* __restrict__ bk, int mp, int nu,
+                                               int wpc, float4* __restrict__ qout,
+                                               float2* __restrict__ wd) {
+  const int nblk = (nu / 2) * wpc;
+  const int lane = (int)(x & 31);
+  const int64_t rb = x >> 5;
+  const int blk = (int)(rb % nblk), r = (int)(rb / nblk);
+  const int qp = blk / wpc, h = blk % wpc;
+  float v[2][4];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int j = 32 * (h + wpc * (2 * qp + u)) + lane;
+    cf C{1.f, 0.f}, D{0.f, 0.f};
+    if (j < mp) {
+      const int i = pair ? bi[r] : r;
+      const float4 ti = tab[(int64_t)i * mp + j];
+      const cf Ai{ti.x, ti.y}, Bi{ti.z, ti.w};
+      if (pair) {
+        const int k = bk[r];
+        const float4 tk = tab[(int64_t)k * mp + j];
+        const cf Ak{tk.x, tk.y}, Bk{tk.z, tk.w};
+        C = Ai * Ak - Bi * Bk;
+        D = Bi * Ak - Ai * Bk;
+        const float2 wi = wt[(int64_t)i * mp + j], wk = wt[(int64_t)k * mp + j];
+        wd[(int64_t)r * mp + j] = make_float2(wi.x - wk.x, wi.y - wk.y);
+      } else {
+        C = Ai;
+        D = Bi;
+      }
+    }
+    const cf E = conj(C) * D;
+    v[u][0] = fmaf(C.x, C.x, C.y * C.y);
+    v[u][1] = fmaf(D.x, D.x, D.y * D.y);
+    v[u][2] = E.x;
+    v[u][3] = -E.y;
+  }
+  float4* row = qout + rb * 64;
+  row[lane] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+  row[32 + lane] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
+}
+
 template <bool PAIR>
 __global__ void cplx_rows_kernel(const float4* __restrict__ tab, const float2* __restrict__ wt,
                                  const int32_t* __restrict__ bi, const int32_t* __restrict__ bk,
                                  int rows, int mp, int nu, int wpc, float4* __restrict__ qout,
                                  float2* __restrict__ wd) {
-  const int nblk = (nu / 2) * wpc;
-  const int64_t total = (int64_t)rows * nblk * 32;
+  const int64_t total = (int64_t)rows * (nu / 2) * wpc * 32;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+       x += (int64_t)gridDim.x * blockDim.x)
+    cplx_rows_elem(x, PAIR, tab, wt, bi, bk, mp, nu, wpc, qout, wd);
+}
+
+// The table builds of many problems in one launch: job k owns elements
+// [start[k], start[k + 1]) of the concatenated index range.
+enum { kTabNone = 0, kTabRealPair = 1, kTabCplxFlip = 2, kTabCplxPair = 3 };
+struct TableJob {
+  int kind, mp, nu, wpc;
+  const void* tab;
+  const void* wt;
+  const int32_t* bi;
+  const int32_t* bk;
+  void* out;
+  void* wd;
+};
+struct TableBatch {
+  int n;
+  int64_t start[kMetroBatch + 1];
+  TableJob j[kMetroBatch];
+};
+
+__global__ void tables_batch_kernel(const __grid_constant__ TableBatch B) {
+  const int64_t total = B.start[B.n];
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
        x += (int64_t)gridDim.x * blockDim.x) {
-    const int lane = (int)(x & 31);
-    const int64_t rb = x >> 5;
-    const int blk = (int)(rb % nblk), r = (int)(rb / nblk);
-    const int qp = blk / wpc, h = blk % wpc;
-    float v[2][4];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int j = 32 * (h + wpc * (2 * qp + u)) + lane;
-      cf C{1.f, 0.f}, D{0.f, 0.f};
-      if (j < mp) {
-        const int i = PAIR ? bi[r] : r;
-        const float4 ti = tab[(int64_t)i * mp + j];
-        const cf Ai{ti.x, ti.y}, Bi{ti.z, ti.w};
-        if (PAIR) {
-          const int k = bk[r];
-          const float4 tk = tab[(int64_t)k * mp + j];
-          const cf Ak{tk.x, tk.y}, Bk{tk.z, tk.w};
-          C = Ai * Ak - Bi * Bk;
-          D = Bi * Ak - Ai * Bk;
-          const float2 wi = wt[(int64_t)i * mp + j], wk = wt[(int64_t)k * mp + j];
-          wd[(int64_t)r * mp + j] = make_float2(wi.x - wk.x, wi.y - wk.y);
-        } else {
-          C = Ai;
-          D = Bi;
-        }
-      }
-      const cf E = conj(C) * D;
-      v[u][0] = fmaf(C.x, C.x, C.y * C.y);
-      v[u][1] = fmaf(D.x, D.x, D.y * D.y);
-      v[u][2] = E.x;
-      v[u][3] = -E.y;
+    int lo = 0, hi = B.n - 1;  // the job whose range holds x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (B.start[mid] <= x) lo = mid; else hi = mid - 1;
     }
-    float4* row = qout + rb * 64;
-    row[lane] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
-    row[32 + lane] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
+    const TableJob& J = B.j[lo];
+    const int64_t e = x - B.start[lo];
+    if (J.kind == kTabRealPair)
+      pair_table_real_elem(e, (const float2*)J.tab, (const float*)J.wt, J.bi, J.bk, J.mp,
+                           (float2*)J.out, (float*)J.wd);
+    else
+      cplx_rows_elem(e, J.kind == kTabCplxPair, (const float4*)J.tab, (const float2*)J.wt, J.bi,
+                     J.bk, J.mp, J.nu, J.wpc, (float4*)J.out, (float2*)J.wd);
   }
+}
+
+struct CounterBatch {
+  int n;
+  uint64_t* ctr[kMetroBatch];
+  uint64_t delta[kMetroBatch];
+};
+__global__ void advance_counters_kernel(const __grid_constant__ CounterBatch B) {
+  const int k = threadIdx.x;
+  if (k < B.n) *B.ctr[k] += B.delta[k];
 }
 
 __global__ void advance_counter_kernel(uint64_t* ctr, uint64_t delta) { *ctr += delta; }
@@ -644,69 +732,107 @@ size_t metropolis_scratch_bytes(int n, int m, int cplx, int move, int nb) {
   return bytes;
 }
 
-template <bool CPLX, int NU, int WPC>
-static nk_status launch_e(const MetroArgs& A, size_t smem, cudaStream_t st) {
-  auto kern = metropolis_kernel<CPLX, NU, WPC>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return fail(NK_ERR_CUDA, "nk_metropolis_sweep: cannot reserve %zu B shared memory", smem);
-  const int blocks = (A.nc + A.G - 1) / A.G;
-  kern<<<blocks, 32 * A.G * WPC, smem, st>>>(A);
-  return check_launch("nk_metropolis_sweep");
-}
+// Launch functors for the kernel templates: one problem, or a batch of problems
+// sharing a template (field, hidden units per lane, warps per chain, group size).
+struct SingleLaunch {
+  const MetroArgs& A;
+  size_t smem;
+  cudaStream_t st;
+  template <bool CPLX, int NU, int WPC>
+  nk_status go() const {
+    auto kern = metropolis_kernel<CPLX, NU, WPC>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return fail(NK_ERR_CUDA, "nk_metropolis_sweep: cannot reserve %zu B shared memory", smem);
+    const int blocks = (A.nc + A.G - 1) / A.G;
+    kern<<<blocks, 32 * A.G * WPC, smem, st>>>(A);
+    return check_launch("nk_metropolis_sweep");
+  }
+};
 
-template <bool CPLX>
-static nk_status launch_c(const MetroArgs& A, int nu, int wpc, size_t smem, cudaStream_t st) {
+struct BatchLaunch {
+  const MetroBatch& B;
+  int G;
+  size_t smem;
+  cudaStream_t st;
+  template <bool CPLX, int NU, int WPC>
+  nk_status go() const {
+    auto kern = metropolis_batch_kernel<CPLX, NU, WPC>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return fail(NK_ERR_CUDA, "nk_batch_sweep: cannot reserve %zu B shared memory", smem);
+    kern<<<B.start[B.n], 32 * G * WPC, smem, st>>>(B);
+    return check_launch("nk_batch_sweep");
+  }
+};
+
+template <bool CPLX, class Fn>
+static nk_status launch_c(int nu, int wpc, int m, const Fn& fn) {
   if (wpc == 1) {
     if constexpr (CPLX) {
       switch (nu) {
-        case 2: return launch_e<true, 2, 1>(A, smem, st);
-        case 4: return launch_e<true, 4, 1>(A, smem, st);
-        case 8: return launch_e<true, 8, 1>(A, smem, st);
-        case 16: return launch_e<true, 16, 1>(A, smem, st);
-        case 32: return launch_e<true, 32, 1>(A, smem, st);
-        case 64: return launch_e<true, 64, 1>(A, smem, st);
+        case 2: return fn.template go<true, 2, 1>();
+        case 4: return fn.template go<true, 4, 1>();
+        case 8: return fn.template go<true, 8, 1>();
+        case 16: return fn.template go<true, 16, 1>();
+        case 32: return fn.template go<true, 32, 1>();
+        case 64: return fn.template go<true, 64, 1>();
       }
     } else {
       switch (nu) {
-        case 1: return launch_e<false, 1, 1>(A, smem, st);
-        case 2: return launch_e<false, 2, 1>(A, smem, st);
-        case 4: return launch_e<false, 4, 1>(A, smem, st);
-        case 8: return launch_e<false, 8, 1>(A, smem, st);
-        case 16: return launch_e<false, 16, 1>(A, smem, st);
-        case 32: return launch_e<false, 32, 1>(A, smem, st);
-        case 64: return launch_e<false, 64, 1>(A, smem, st);
+        case 1: return fn.template go<false, 1, 1>();
+        case 2: return fn.template go<false, 2, 1>();
+        case 4: return fn.template go<false, 4, 1>();
+        case 8: return fn.template go<false, 8, 1>();
+        case 16: return fn.template go<false, 16, 1>();
+        case 32: return fn.template go<false, 32, 1>();
+        case 64: return fn.template go<false, 64, 1>();
       }
     }
   } else {
     if constexpr (CPLX) {
       switch (nu) {
-        case 8: return launch_e<true, 8, 2>(A, smem, st);
-        case 14: return launch_e<true, 14, 2>(A, smem, st);
-        case 16: return launch_e<true, 16, 2>(A, smem, st);
-        case 26: return launch_e<true, 26, 2>(A, smem, st);
-        case 32: return launch_e<true, 32, 2>(A, smem, st);
+        case 8: return fn.template go<true, 8, 2>();
+        case 14: return fn.template go<true, 14, 2>();
+        case 16: return fn.template go<true, 16, 2>();
+        case 26: return fn.template go<true, 26, 2>();
+        case 32: return fn.template go<true, 32, 2>();
       }
     } else {
       switch (nu) {
-        case 8: return launch_e<false, 8, 2>(A, smem, st);
-        case 13: return launch_e<false, 13, 2>(A, smem, st);
-        case 16: return launch_e<false, 16, 2>(A, smem, st);
-        case 25: return launch_e<false, 25, 2>(A, smem, st);
-        case 32: return launch_e<false, 32, 2>(A, smem, st);
+        case 8: return fn.template go<false, 8, 2>();
+        case 13: return fn.template go<false, 13, 2>();
+        case 16: return fn.template go<false, 16, 2>();
+        case 25: return fn.template go<false, 25, 2>();
+        case 32: return fn.template go<false, 32, 2>();
       }
     }
   }
   return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: m = %d exceeds the register-resident limit 2048",
-              A.m);
+              m);
 }
 
-nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int32_t* bi,
-                            const int32_t* bk, int nb, int n_discard, int n_samples,
-                            int8_t* samples, uint64_t* n_acc, void* scratch, size_t scratch_bytes,
-                            cudaStream_t st, bool dry, const MetroPt* pt) {
-  WsLayout L(r->n, r->m, r->is_complex);
+// Everything one sweep call needs, checked and laid out, before anything is
+// enqueued: the kernel arguments, its template and shared memory, the table
+// build (if any) and the device-counter advance.
+struct MetroPlan {
   MetroArgs A;
+  bool cplx;
+  int nu, wpc;
+  size_t smem;
+  TableJob tj;
+  int64_t tab_elems;
+  uint64_t* ctr_dev;
+  uint64_t advance;
+};
+
+static nk_status plan_metropolis(const nk_rbm* r, const nk_chains* ch, int move,
+                                 const int32_t* bi, const int32_t* bk, int nb, int n_discard,
+                                 int n_samples, int8_t* samples, uint64_t* n_acc, void* scratch,
+                                 size_t scratch_bytes, const MetroPt* pt, MetroPlan* P) {
+  WsLayout L(r->n, r->m, r->is_complex);
+  MetroArgs& A = P->A;
+  A = MetroArgs();
   if (pt) {
     A.pt_R = pt->R;
     A.lval = pt->lval;
@@ -759,10 +885,17 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
                 "than two table slots in 227 KB of shared memory",
                 A.G, L.mp);
   A.ring = ring;
-  const size_t smem = (size_t)ring * slot + rest;
   if ((int64_t)(n_discard + n_samples) * r->n > 0x7fffffff)
     return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: too many proposals in one call");
-  if (dry) return NK_OK;  // every check passed; nothing is enqueued
+  P->cplx = cplx;
+  P->nu = nu;
+  P->wpc = wpc;
+  P->smem = (size_t)ring * slot + rest;
+  P->ctr_dev = ch->counter_dev;
+  P->advance = (uint64_t)(n_discard + n_samples) * r->n;
+  TableJob& J = P->tj;
+  J = TableJob{kTabNone, L.mp, nu, wpc, ws + L.tab, ws + L.wt, bi, bk, nullptr, nullptr};
+  P->tab_elems = 0;
   char* sc = (char*)scratch;
   const int rows = move == NK_MOVE_FLIP ? r->n : nb;
   const int64_t qbytes = round_up((int64_t)rows * (int64_t)cd_row, 256);
@@ -773,40 +906,138 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
     } else {
       A.cd = sc;
       A.wd = sc + round_up((int64_t)nb * L.mp * 2 * f, 256);
-      const int64_t tot = skip_tables ? 0 : (int64_t)nb * L.mp;
-      const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
-      if (tot > 0) {
-        pair_tables_real_kernel<<<(unsigned)blocks, 256, 0, st>>>(
-            (const float2*)(ws + L.tab), (const float*)(ws + L.wt), bi, bk, nb, L.mp,
-            (float2*)A.cd, (float*)A.wd);
-        if (nk_status e = check_launch("nk_metropolis_sweep(pair tables)")) return e;
-      }
+      J.kind = kTabRealPair;
+      J.out = sc;
+      J.wd = (void*)A.wd;
+      P->tab_elems = (int64_t)nb * L.mp;
     }
   } else {
     A.cd = sc;
     A.wd = move == NK_MOVE_FLIP ? (const void*)(ws + L.wt) : (const void*)(sc + qbytes);
-    const int64_t tot = (int64_t)rows * (nu / 2) * wpc * 32;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
-    if (skip_tables) {
-      // tables of an earlier launch of the same call
-    } else if (move == NK_MOVE_FLIP)
+    J.kind = move == NK_MOVE_FLIP ? kTabCplxFlip : kTabCplxPair;
+    J.out = sc;
+    J.wd = move == NK_MOVE_FLIP ? nullptr : (void*)(sc + qbytes);
+    P->tab_elems = (int64_t)rows * (nu / 2) * wpc * 32;
+  }
+  if (skip_tables) {  // tables of an earlier launch of the same call
+    J.kind = kTabNone;
+    P->tab_elems = 0;
+  }
+  return NK_OK;
+}
+
+nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int32_t* bi,
+                            const int32_t* bk, int nb, int n_discard, int n_samples,
+                            int8_t* samples, uint64_t* n_acc, void* scratch, size_t scratch_bytes,
+                            cudaStream_t st, bool dry, const MetroPt* pt) {
+  MetroPlan P;
+  if (nk_status e = plan_metropolis(r, ch, move, bi, bk, nb, n_discard, n_samples, samples,
+                                    n_acc, scratch, scratch_bytes, pt, &P))
+    return e;
+  if (dry) return NK_OK;  // every check passed; nothing is enqueued
+  const TableJob& J = P.tj;
+  if (J.kind != kTabNone && P.tab_elems > 0) {
+    const int64_t blocks =
+        std::max<int64_t>(1, std::min<int64_t>((P.tab_elems + 255) / 256, 152 * 16));
+    if (J.kind == kTabRealPair)
+      pair_tables_real_kernel<<<(unsigned)blocks, 256, 0, st>>>(
+          (const float2*)J.tab, (const float*)J.wt, bi, bk, nb, J.mp, (float2*)J.out,
+          (float*)J.wd);
+    else if (J.kind == kTabCplxFlip)
       cplx_rows_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(
-          (const float4*)(ws + L.tab), (const float2*)(ws + L.wt), bi, bk, rows, L.mp, nu, wpc,
-          (float4*)sc, nullptr);
+          (const float4*)J.tab, (const float2*)J.wt, bi, bk, r->n, J.mp, J.nu, J.wpc,
+          (float4*)J.out, nullptr);
     else
       cplx_rows_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(
-          (const float4*)(ws + L.tab), (const float2*)(ws + L.wt), bi, bk, rows, L.mp, nu, wpc,
-          (float4*)sc, (float2*)(sc + qbytes));
-    if (!skip_tables)
-      if (nk_status e = check_launch("nk_metropolis_sweep(tables)")) return e;
+          (const float4*)J.tab, (const float2*)J.wt, bi, bk, nb, J.mp, J.nu, J.wpc,
+          (float4*)J.out, (float2*)J.wd);
+    if (nk_status e = check_launch("nk_metropolis_sweep(tables)")) return e;
   }
-  nk_status e = cplx ? launch_c<true>(A, nu, wpc, smem, st) : launch_c<false>(A, nu, wpc, smem, st);
+  SingleLaunch L1{P.A, P.smem, st};
+  nk_status e = P.cplx ? launch_c<true>(P.nu, P.wpc, r->m, L1)
+                       : launch_c<false>(P.nu, P.wpc, r->m, L1);
   if (e == NK_OK && ch->counter_dev) {
-    advance_counter_kernel<<<1, 1, 0, st>>>(ch->counter_dev,
-                                           (uint64_t)(n_discard + n_samples) * r->n);
+    advance_counter_kernel<<<1, 1, 0, st>>>(ch->counter_dev, P.advance);
     e = check_launch("nk_metropolis_sweep(counter)");
   }
   return e;
+}
+
+// Fused sweeps of many problems: one launch of the table builds for all of
+// them, one launch of the sweep kernel per group of problems that share its
+// template (at most kMetroBatch per launch), one launch advancing every device
+// counter.  Each problem runs the arithmetic of its own launch (same arguments,
+// tables and ring depth), so the results are those of separate calls.
+nk_status launch_metropolis_fused(const nk_sweep_item* items, const int* idx, int n,
+                                  cudaStream_t st) {
+  std::vector<MetroPlan> plans((size_t)n);
+  for (int u = 0; u < n; ++u) {
+    const nk_sweep_item& it = items[idx[u]];
+    if (nk_status e = plan_metropolis(it.rbm, it.chains, it.move, it.bond_i, it.bond_k,
+                                      it.n_bonds, it.n_discard, it.n_samples_per_chain,
+                                      it.samples_out, it.n_accept_out, it.scratch,
+                                      it.scratch_bytes, nullptr, &plans[u]))
+      return e;
+  }
+  // table builds
+  for (int u0 = 0; u0 < n; u0 += kMetroBatch) {
+    TableBatch TB;
+    TB.n = 0;
+    TB.start[0] = 0;
+    for (int u = u0; u < std::min(n, u0 + kMetroBatch); ++u) {
+      if (plans[u].tj.kind == kTabNone || plans[u].tab_elems == 0) continue;
+      TB.j[TB.n] = plans[u].tj;
+      TB.start[TB.n + 1] = TB.start[TB.n] + plans[u].tab_elems;
+      ++TB.n;
+    }
+    if (TB.n > 0) {
+      const int64_t blocks =
+          std::max<int64_t>(1, std::min<int64_t>((TB.start[TB.n] + 255) / 256, 152 * 16));
+      tables_batch_kernel<<<(unsigned)blocks, 256, 0, st>>>(TB);
+      if (nk_status e = check_launch("nk_batch_sweep(tables)")) return e;
+    }
+  }
+  // sweeps, grouped by kernel template
+  std::vector<bool> done((size_t)n, false);
+  for (int u = 0; u < n; ++u) {
+    if (done[u]) continue;
+    const MetroPlan& P0 = plans[u];
+    MetroBatch B;
+    B.n = 0;
+    B.start[0] = 0;
+    size_t smem = 0;
+    for (int v = u; v < n && B.n < kMetroBatch; ++v) {
+      const MetroPlan& P = plans[v];
+      if (done[v] || P.cplx != P0.cplx || P.nu != P0.nu || P.wpc != P0.wpc ||
+          P.A.G != P0.A.G)
+        continue;
+      B.a[B.n] = P.A;
+      B.start[B.n + 1] = B.start[B.n] + (P.A.nc + P.A.G - 1) / P.A.G;
+      ++B.n;
+      smem = std::max(smem, P.smem);
+      done[v] = true;
+    }
+    BatchLaunch LB{B, P0.A.G, smem, st};
+    nk_status e = P0.cplx ? launch_c<true>(P0.nu, P0.wpc, P0.A.m, LB)
+                          : launch_c<false>(P0.nu, P0.wpc, P0.A.m, LB);
+    if (e) return e;  // problems of this template beyond kMetroBatch start later batches
+  }
+  // device counters
+  for (int u0 = 0; u0 < n; u0 += kMetroBatch) {
+    CounterBatch CB;
+    CB.n = 0;
+    for (int u = u0; u < std::min(n, u0 + kMetroBatch); ++u)
+      if (plans[u].ctr_dev) {
+        CB.ctr[CB.n] = plans[u].ctr_dev;
+        CB.delta[CB.n] = plans[u].advance;
+        ++CB.n;
+      }
+    if (CB.n > 0) {
+      advance_counters_kernel<<<1, 64, 0, st>>>(CB);
+      if (nk_status e = check_launch("nk_batch_sweep(counters)")) return e;
+    }
+  }
+  return NK_OK;
 }
 
 NK_STATUS_COLLECTOR(collect_status_metropolis)

@@ -26,21 +26,33 @@ struct SgTypes<false> {
   using F = float;
 };
 
+// The CTA's sample tile is bx (blockIdx.x when bx < 0).
 // Thread (tx, ty) = (tid % 16, tid / 16) owns samples s0 + 4 ty + p (p < 4) and
 // rows j0 + tx + 16 q (q < 4).  Epi::tile(acc, s_base, j_base, part) folds the
 // tile into part[p] (one complex-double partial per owned sample); after the
 // last j-tile the 16 partials of a sample are summed over tx and
 // Epi::finish(s, sum) is called by the thread with tx == 0.
-template <bool CPLX, class Epi>
+// COMP: every 16-site chunk is summed in a fresh FP32 accumulator and added to
+// the running sum with TwoSum (Knuth), its rounding error carried separately, so
+// that the result is accurate to about one FP32 rounding instead of growing
+// with the number of sites (used where theta itself is the output).
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  c += (s - (t - bp)) + (x - bp);
+  s = t;
+}
+
+template <bool CPLX, class Epi, bool COMP = false>
 __device__ __forceinline__ void sgemm_rowreduce(const int8_t* __restrict__ sigma, int64_t ns,
                                                 int n, const void* __restrict__ Xv, int rows,
-                                                int ld, Epi& epi) {
+                                                int ld, Epi& epi, int bx = -1) {
   using F = typename SgTypes<CPLX>::F;
   const F* X = reinterpret_cast<const F*>(Xv);
   __shared__ __align__(16) float Ss[kSgBK][kSgBS];
   __shared__ __align__(16) F Xs[kSgBK][kSgBJ];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t s0 = (int64_t)blockIdx.x * kSgBS;
+  const int64_t s0 = (int64_t)(bx < 0 ? (int)blockIdx.x : bx) * kSgBS;
   const int K = n + 1;
   double2 part[4];
 #pragma unroll
@@ -48,10 +60,14 @@ __device__ __forceinline__ void sgemm_rowreduce(const int8_t* __restrict__ sigma
 
   for (int j0 = 0; j0 < rows; j0 += kSgBJ) {
     float acc_r[4][4], acc_i[4][4];
+    float sr[COMP ? 4 : 1][4], si[COMP ? 4 : 1][4], cr[COMP ? 4 : 1][4], ci[COMP ? 4 : 1][4];
 #pragma unroll
     for (int p = 0; p < 4; ++p)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc_r[p][q] = acc_i[p][q] = 0.f;
+      for (int q = 0; q < 4; ++q) {
+        acc_r[p][q] = acc_i[p][q] = 0.f;
+        if constexpr (COMP) sr[p][q] = si[p][q] = cr[p][q] = ci[p][q] = 0.f;
+      }
     for (int k0 = 0; k0 < K; k0 += kSgBK) {
       // sigma' tile: 64 samples x 16 sites, 4 per thread
 #pragma unroll
@@ -95,6 +111,28 @@ __device__ __forceinline__ void sgemm_rowreduce(const int8_t* __restrict__ sigma
         }
       }
       __syncthreads();
+      if constexpr (COMP) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            two_sum_acc(sr[p][q], cr[p][q], acc_r[p][q]);
+            acc_r[p][q] = 0.f;
+            if constexpr (CPLX) {
+              two_sum_acc(si[p][q], ci[p][q], acc_i[p][q]);
+              acc_i[p][q] = 0.f;
+            }
+          }
+      }
+    }
+    if constexpr (COMP) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc_r[p][q] = sr[p][q] + cr[p][q];
+          acc_i[p][q] = si[p][q] + ci[p][q];
+        }
     }
     epi.tile(acc_r, acc_i, s0 + ty * 4, j0 + tx, part);
   }

@@ -664,6 +664,78 @@ nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st)
   return sig_tma ? go(fwd_tc_kernel<false, true>) : go(fwd_tc_kernel<false, false>);
 }
 
+// Up to kFwdFuseMax theta / ln psi launches (mode 1) of one field in one launch:
+// CTA b runs CTA b - start[k] of problem k, numbered as that problem's own
+// launch (sample tile, hidden-tile half), with its own tensor map.
+constexpr int kFwdFuseMax = 64;
+struct FwdFuse {
+  int n;
+  int start[kFwdFuseMax + 1];
+  int tiles[kFwdFuseMax];
+  FwdTcArgs a[kFwdFuseMax];
+  CUtensorMap map[kFwdFuseMax];
+};
+
+template <bool CPLX>
+__global__ void __launch_bounds__(kFwdThreads, 1) fwd_tc_fused(const __grid_constant__ FwdFuse B) {
+  int k = 0;
+  while (k + 1 < B.n && (int)blockIdx.x >= B.start[k + 1]) ++k;
+  const int b = (int)blockIdx.x - B.start[k], t = B.tiles[k];
+  fwd_tc_body<CPLX, kFwdStages, true, false>(&B.map[k], B.a[k], b % t, b / t);
+}
+
+nk_status launch_fwd_tc_fused(const FwdTcArgs* args, const void* const* planes, int n,
+                              cudaStream_t st) {
+  for (int field = 0; field < 2; ++field) {
+    for (int u0 = 0; u0 < n;) {
+      FwdFuse* B = new FwdFuse;  // about 13 KB: kept off the stack
+      B->n = 0;
+      B->start[0] = 0;
+      size_t smem = 0;
+      int u = u0;
+      nk_status e = NK_OK;
+      for (; u < n && B->n < kFwdFuseMax && !e; ++u) {
+        const FwdTcArgs& A = args[u];
+        if (A.cplx != field || A.ns == 0) continue;
+        if (!tc_supported_shape(A.n, A.m)) {
+          e = fail(NK_ERR_UNSUPPORTED, "tensor-core path supports n + 1 <= 448 (n = %d)", A.n);
+          break;
+        }
+        FwdTcArgs C = A;
+        C.nseg = fwd_tc_nseg(A.ns, A.mt, A.mode, false);
+        if (C.nseg == 2 && A.logpsi &&
+            cudaMemsetAsync(A.logpsi, 0, (size_t)A.ns * 16, st) != cudaSuccess) {
+          e = fail(NK_ERR_CUDA, "fwd_tc: cudaMemsetAsync failed");
+          break;
+        }
+        if (!tc_make_map(&B->map[B->n], planes[u], 2LL * A.mt * 128, A.na64, A.na64, 128)) {
+          e = NK_ERR_CUDA;
+          break;
+        }
+        B->a[B->n] = C;
+        B->tiles[B->n] = (int)((A.ns + 127) / 128);
+        B->start[B->n + 1] = B->start[B->n] + B->tiles[B->n] * C.nseg;
+        smem = std::max(smem, fwd_smem_bytes(A.na64));
+        ++B->n;
+      }
+      u0 = u;
+      if (!e && B->n > 0) {
+        auto kern = field ? fwd_tc_fused<true> : fwd_tc_fused<false>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+          e = fail(NK_ERR_CUDA, "fwd_tc_fused: shared memory attribute");
+        else {
+          kern<<<(unsigned)B->start[B->n], kFwdThreads, smem, st>>>(*B);
+          e = check_launch("fwd_tc_fused");
+        }
+      }
+      delete B;
+      if (e) return e;
+    }
+  }
+  return NK_OK;
+}
+
 // ------------------------------------------------------------------ adjoint
 
 constexpr int kAdjProducerWarps = 8;

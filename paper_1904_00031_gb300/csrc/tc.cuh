@@ -65,6 +65,9 @@ struct FwdTcArgs {
   const double* weights = nullptr;
 };
 nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st);
+// Many mode-1 (theta / ln psi) launches fused: one launch per field.
+nk_status launch_fwd_tc_fused(const FwdTcArgs* args, const void* const* planes, int n,
+                              cudaStream_t st);
 // Hidden-tile halves (1 or 2) launch_fwd_tc uses for ns samples and mt hidden
 // tiles: 2 when twice the CTAs fill their last wave better (ln psi, and the SR
 // forward with TMA-loaded sigma' tiles).

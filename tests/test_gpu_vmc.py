@@ -152,6 +152,39 @@ def test_heisenberg20_listing_run(mods):
     assert rel < 1e-2, (e, s)
 
 
+def test_listing_run_readings(mods):
+    """The Sec. 3.1 listing run (Fig. 2 reports a relative error of 4.16e-5) under
+    readings of its unstated settings, 200 iterations each: the Marshall-rotated
+    Hamiltonian (this build's reading) or the unrotated one, 1,008 or 4,032
+    samples per iteration, diagonal shift 0.01 or 0.001.  Relative errors of the
+    mean energy over iterations 91-100 and 191-200 are printed (pytest -s); every
+    run must respect the variational bound."""
+    nk, VmcSr = mods
+    from oracle import hamiltonian
+    n = 20
+    rows = []
+    for marshall, spc, eps in [(True, 63, 0.01), (False, 63, 0.01), (True, 252, 0.01),
+                               (True, 63, 0.001)]:
+        op = W.heisenberg(n, W.chain_bonds(n), 1.0, marshall, W.sublattice(n))
+        e_exact = hamiltonian.lanczos_ground(op, True)[0]
+        w = W.Workload("heisenberg1d_n20_alpha1", n, n, True, op, "exchange", W.chain_bonds(n),
+                       True, 16, spc, max(1, -(-spc // 10)), eps, 0.01, 200, 1234)
+        v = VmcSr(w, W.init_params(n, n, True, 0.01, 1234), prec=nk.NK_PREC_FP32, graph=True)
+        energies = []
+        for _ in range(200):
+            v.step()
+            energies.append(v.info()["energy"])
+        e100 = float(np.mean(energies[90:100]))
+        e200 = float(np.mean(energies[190:200]))
+        _, s200 = blocked(energies)
+        rows.append((marshall, 16 * spc, eps, abs((e100 - e_exact) / e_exact),
+                     abs((e200 - e_exact) / e_exact)))
+        assert float(np.mean(energies[150:])) >= e_exact - 3 * s200
+    print("\n| Marshall rotation | samples | diag shift | rel. error at 100 | rel. error at 200 |")
+    for r in rows:
+        print(f"| {r[0]} | {r[1]} | {r[2]} | {r[3]:.2e} | {r[4]:.2e} |")
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_graph_replay_equals_eager(mods, prec):
     """A captured iteration replays the same arithmetic: with the Philox counter on
