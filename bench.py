@@ -597,7 +597,7 @@ def run_gpu_batched(args):
     prec_name = args.prec if args.prec != "auto" else "bf16x2"
     prec = nk.NK_PREC_FP32 if prec_name == "fp32" else nk.NK_PREC_BF16X2
     insts = W.batched_instances(64, R.replica_seed(4242, rank), 1024)
-    b = BatchedVmc(insts, prec=prec, graph=bool(args.graph))
+    b = BatchedVmc(insts, prec=prec, graph=bool(args.graph), autotune=True)
     stream = torch.cuda.current_stream()
 
     def barrier():

@@ -68,6 +68,12 @@ typedef struct nk_rbm {
   int32_t sr_splits;  /* split-K count of the adjoint contraction of nk_sr_step and
                          nk_rbm_logpsi_backward; 0 = built-in heuristic.  Set by
                          nk_sr_tune (or by hand); clamped to the scratch capacity */
+  int32_t eloc_segs;  /* nk_local_energy: CTAs per configuration tile, each taking a
+                         share of the move tiles (1 or 2); 0 = built-in heuristic.
+                         Set by nk_tune_shapes (or by hand)                       */
+  int32_t theta_segs; /* tensor-core ln psi / theta: CTAs per sample tile, each
+                         taking a share of the hidden tiles (1 or 2); 0 = built-in
+                         heuristic.  Set by nk_tune_shapes (or by hand)           */
   double* a;          /* F64 [n]    (device)                                        */
   double* b;          /* F64 [m]    (device)                                        */
   double* w;          /* F64 [m][n] (device, row-major)                             */
@@ -423,6 +429,20 @@ nk_status nk_ffnn_logpsi(const nk_ffnn* f, const int8_t* sigma, int64_t ns, doub
  *   g         c128 [ns];  grad_out  F64 [P] or c128 [P] in the parameter order */
 nk_status nk_ffnn_backward(const nk_ffnn* f, const int8_t* sigma, int64_t ns, const double* g,
                            double* grad_out, void* scratch, size_t scratch_bytes, void* stream);
+
+/* Autotuner of the tile shapes of the ln psi / theta contraction (tensor-core
+ * path) and of the local energies: times each kernel with one and with two
+ * CTAs per tile (the second CTA taking half of the hidden or move tiles; the
+ * results agree to FP64 rounding of the two partial sums) on the given
+ * samples and stores the faster counts in rbm->theta_segs and rbm->eloc_segs.
+ * theta_tmp (F32 [ns][m]) and eloc_tmp (c128 [ns]) are overwritten; scratch as
+ * for nk_local_energy.  Unlike the other calls this one SYNCHRONISES `stream`
+ * (it measures with CUDA events) and must not be called while a stream is
+ * being captured.  (The paper has no counterpart: a tuning aid of this
+ * library.) */
+nk_status nk_tune_shapes(nk_rbm* rbm, const void* op_dev, int32_t n_moves, const int8_t* sigma,
+                         int64_t ns, void* theta_tmp, double* eloc_tmp, void* scratch,
+                         size_t scratch_bytes, void* stream);
 
 /* ------------------------------------------- batches of independent instances */
 

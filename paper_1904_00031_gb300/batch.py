@@ -32,13 +32,14 @@ def _metro_template(w) -> tuple:
 class BatchedVmc:
     def __init__(self, instances, prec: int = nk.NK_PREC_FP32, device="cuda",
                  graph: bool = True, param_scale: float = 0.01, batch_sr: bool = True,
-                 sr_splits: int = 0, fused: bool = True):
+                 sr_splits: int = 0, fused: bool = True, autotune: bool = False):
         """``fused``: sampling, theta and local energies of all instances run as
         fused launches (nk_batch_sweep / nk_batch_logpsi / nk_batch_local_energy
         on one stream); else every instance launches its own kernels on a stream
         of its own."""
         self.fused = fused
         self.prec = prec
+        self.autotune = autotune
         self.items = []
         for w in instances:
             p = W.init_params(w.n, w.m, w.is_complex, param_scale, w.seed)
@@ -106,12 +107,26 @@ class BatchedVmc:
         with torch.cuda.graph(self.graph):
             self._eager_step()
 
+    def tune_shapes(self):
+        """Autotune every instance's theta and local-energy tile shapes on its
+        current samples (tensor-core path; synchronises), then recompute theta and
+        the local energies the tuner overwrote."""
+        if self.prec != nk.NK_PREC_BF16X2:
+            return
+        for v in self.items:
+            nk.nk_tune_shapes(v.rbm, v.op, v.samples, v.theta, v.eloc, v.eloc_scratch)
+            v.amplitudes()
+            v.energies()
+
     def step(self):
         """One iteration of every instance.  In graph mode the first call runs
-        eagerly and captures the graph; later calls replay it."""
+        eagerly (and autotunes, if asked) and captures the graph; later calls
+        replay it."""
         if self.use_graph:
             if self.graph is None:
                 self._eager_step()
+                if self.autotune:
+                    self.tune_shapes()
                 self.capture()
             else:
                 self.graph.replay()

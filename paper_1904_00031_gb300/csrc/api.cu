@@ -242,6 +242,25 @@ static nk_status run_batch(const char* what, const Item* items, int32_t n_inst, 
   return NK_OK;
 }
 
+// Mean time of `reps` launches of `fn` on `st` (CUDA events), after one warm-up launch.
+template <typename Fn>
+static nk_status time_launches(cudaStream_t st, int reps, Fn fn, float* ms) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(NK_ERR_CUDA, "nk_tune_shapes: cudaEventCreate failed");
+  nk_status e = fn();
+  if (!e && cudaEventRecord(e0, st) != cudaSuccess) e = fail(NK_ERR_CUDA, "event record failed");
+  for (int k = 0; k < reps && !e; ++k) e = fn();
+  if (!e && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+    e = fail(NK_ERR_CUDA, "nk_tune_shapes: event synchronisation failed");
+  float t = 0.f;
+  if (!e) cudaEventElapsedTime(&t, e0, e1);
+  *ms = t / (float)reps;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return e;
+}
+
 extern "C" {
 
 const char* nk_status_string(nk_status s) {
@@ -820,6 +839,61 @@ nk_status nk_supervised_step(nk_rbm* rbm, const int8_t* sigma, const double* log
   return run_supervised_step(rbm, sigma, log_target, weights, ns, prec, lr, beta1, beta2, step,
                              moments, grad_out, scratch, scratch_bytes, info_out,
                              (cudaStream_t)stream);
+}
+
+nk_status nk_tune_shapes(nk_rbm* rbm, const void* op_dev, int32_t n_moves, const int8_t* sigma,
+                         int64_t ns, void* theta_tmp, double* eloc_tmp, void* scratch,
+                         size_t scratch_bytes, void* stream) {
+  if (nk_status e = check_rbm(rbm, "nk_tune_shapes")) return e;
+  if (ns < 1 || n_moves < 0) return fail(NK_ERR_INVALID_ARG, "nk_tune_shapes: ns < 1");
+  if (!op_dev || !sigma || !theta_tmp || !eloc_tmp)
+    return fail(NK_ERR_INVALID_ARG, "nk_tune_shapes: NULL pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int reps = 3;
+  nk_rbm r = *rbm;
+  // theta (tensor-core path), one and two CTAs per sample tile
+  if (tc_supported_shape(r.n, r.m)) {
+    float best = 1e30f;
+    int best_s = 0;
+    for (int segs = 1; segs <= 2; ++segs) {
+      r.theta_segs = segs;
+      float ms = 0.f;
+      if (nk_status e = time_launches(st, reps, [&] {
+            return launch_logpsi_bf16(&r, sigma, ns, nullptr, theta_tmp, st);
+          }, &ms))
+        return e;
+      if (ms < best) {
+        best = ms;
+        best_s = segs;
+      }
+    }
+    rbm->theta_segs = best_s;
+  }
+  // local energies, one and two CTAs per configuration tile (theta from above)
+  if (n_moves > 0) {
+    const size_t need = local_energy_scratch_bytes(r.m, r.is_complex ? 1 : 0, n_moves);
+    if (!scratch || scratch_bytes < need || (((uintptr_t)scratch) & 255))
+      return fail(NK_ERR_SHAPE, "nk_tune_shapes: scratch of %zu B, need %zu B (256-B aligned)",
+                  scratch_bytes, need);
+    r.theta_segs = rbm->theta_segs;
+    float best = 1e30f;
+    int best_s = 0;
+    for (int segs = 1; segs <= 2; ++segs) {
+      r.eloc_segs = segs;
+      float ms = 0.f;
+      if (nk_status e = time_launches(st, reps, [&] {
+            return launch_local_energy(&r, op_dev, n_moves, sigma, theta_tmp, ns, eloc_tmp,
+                                       nullptr, scratch, scratch_bytes, st);
+          }, &ms))
+        return e;
+      if (ms < best) {
+        best = ms;
+        best_s = segs;
+      }
+    }
+    rbm->eloc_segs = best_s;
+  }
+  return NK_OK;
 }
 
 nk_status nk_query_status(int32_t* flags, void* stream) {

@@ -635,6 +635,7 @@ static nk_status plan_local_energy(const nk_rbm* r, const void* op_dev, int n_mo
     return (double)b / (double)(((b + slots - 1) / slots) * slots);
   };
   A.nseg = (ntile >= 2 && wave_eff(2 * P->blocks) > wave_eff(P->blocks)) ? 2 : 1;
+  if (r->eloc_segs > 0) A.nseg = (r->eloc_segs >= 2 && ntile >= 2) ? 2 : 1;  // tuned or set
   A.seg_fast = A.nseg == 2 && P->blocks <= 65535 ? 1 : 0;
   return NK_OK;
 }

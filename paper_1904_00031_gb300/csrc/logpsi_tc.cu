@@ -26,6 +26,7 @@ nk_status launch_logpsi_bf16(const nk_rbm* r, const int8_t* sigma, int64_t ns, d
   A.logpsi = logpsi;
   A.theta_out = theta_out;
   A.t_out = t_out;
+  A.nseg_req = r->theta_segs;
   return launch_fwd_tc(A, (const char*)r->ws + L.wbf, st);
 }
 
@@ -51,6 +52,7 @@ nk_status launch_logpsi_bf16_fused(const nk_logpsi_item* items, const int* idx, 
     A.a = r->a;
     A.logpsi = it.logpsi_out;
     A.theta_out = it.theta_out;
+    A.nseg_req = r->theta_segs;
     planes[u] = (const char*)r->ws + L.wbf;
   }
   return launch_fwd_tc_fused(args.data(), planes.data(), n, st);

@@ -646,6 +646,7 @@ nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st)
   const int64_t blocks = (A.ns + 127) / 128;
   FwdTcArgs B = A;
   B.nseg = fwd_tc_nseg(A.ns, A.mt, A.mode, sig_tma);
+  if (A.mode == 1 && A.nseg_req > 0) B.nseg = (A.nseg_req >= 2 && A.mt >= 2) ? 2 : 1;
   if (B.nseg == 2 && (A.mode == 0 || A.logpsi)) {
     void* out = A.mode == 0 ? A.y : (void*)A.logpsi;
     const size_t per = (A.mode == 1 || A.cplx) ? 16 : 8;
@@ -703,6 +704,7 @@ nk_status launch_fwd_tc_fused(const FwdTcArgs* args, const void* const* planes, 
         }
         FwdTcArgs C = A;
         C.nseg = fwd_tc_nseg(A.ns, A.mt, A.mode, false);
+        if (A.mode == 1 && A.nseg_req > 0) C.nseg = (A.nseg_req >= 2 && A.mt >= 2) ? 2 : 1;
         if (C.nseg == 2 && A.logpsi &&
             cudaMemsetAsync(A.logpsi, 0, (size_t)A.ns * 16, st) != cudaSuccess) {
           e = fail(NK_ERR_CUDA, "fwd_tc: cudaMemsetAsync failed");

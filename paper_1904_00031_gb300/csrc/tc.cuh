@@ -55,6 +55,7 @@ struct FwdTcArgs {
   const double* skip;     // if non-null and *skip != 0, the kernel returns at once
   int* err;               // set on a timed-out wait (may be null)
   int nseg = 1;           // set by launch_fwd_tc: 1, or 2 halves of the hidden tiles
+  int nseg_req = 0;       // 1 or 2 to override the heuristic (mode 1), 0 = heuristic
   const void* sig_rows = nullptr;  // mode 0: sigma' as BF16 [ns][na64] (launch_sigma_rows);
                                    // the sample tiles are then TMA-loaded, else built
   // mode 0, optional: per-CTA partial sums of w_s y_s (the centring mean of the

@@ -42,7 +42,7 @@ EXPORTS = (
     "nk_symm_tables_bytes", "nk_symm_upload", "nk_symm_expand", "nk_sr_symm_scratch_bytes",
     "nk_sr_step_symm", "nk_symm_build", "nk_supervised_scratch_bytes", "nk_supervised_step",
     "nk_pt_scratch_bytes", "nk_pt_sweep", "nk_ffnn_scratch_bytes", "nk_ffnn_logpsi",
-    "nk_ffnn_backward",
+    "nk_ffnn_backward", "nk_tune_shapes",
 )
 NK_SR_NOALLOC_MAX_BYTES = 16 << 20
 
@@ -53,7 +53,8 @@ class NkError(RuntimeError):
 
 class _Rbm(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("is_complex", C.c_int32),
-                ("sr_splits", C.c_int32), ("a", C.c_void_p), ("b", C.c_void_p), ("w", C.c_void_p),
+                ("sr_splits", C.c_int32), ("eloc_segs", C.c_int32), ("theta_segs", C.c_int32),
+                ("a", C.c_void_p), ("b", C.c_void_p), ("w", C.c_void_p),
                 ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
 
 
@@ -157,6 +158,7 @@ def load_library(path: str = LIB_PATH):
         "nk_supervised_scratch_bytes": (SZ, [I32, I32, I32, I64]),
         "nk_pt_scratch_bytes": (SZ, [I32, I32, I32, I32, I32, I32]),
         "nk_ffnn_scratch_bytes": (SZ, [P, I64]),
+        "nk_tune_shapes": (I32, [P, P, I32, P, I64, P, P, P, SZ, P]),
         "nk_ffnn_logpsi": (I32, [P, P, I64, P, P, SZ, P]),
         "nk_ffnn_backward": (I32, [P, P, I64, P, P, P, SZ, P]),
         "nk_pt_sweep": (I32, [P, P, I32, I32, P, P, I32, I32, I32, P, P, P, P, SZ, P]),
@@ -210,8 +212,8 @@ class Rbm:
         off = (-self.ws.data_ptr()) % 256
         self._ws_ptr = self.ws.data_ptr() + off
         self._ws_bytes = nb
-        self._s = _Rbm(self.n, self.m, int(is_complex), 0, self.a.data_ptr(), self.b.data_ptr(),
-                       self.w.data_ptr(), self._ws_ptr, nb)
+        self._s = _Rbm(self.n, self.m, int(is_complex), 0, 0, 0, self.a.data_ptr(),
+                       self.b.data_ptr(), self.w.data_ptr(), self._ws_ptr, nb)
 
     @property
     def n_params(self) -> int:
@@ -466,6 +468,17 @@ def nk_sr_tune(rbm: Rbm, sigma, t, prec=NK_PREC_FP32, scratch=None, stream=None)
     _check(load_library().nk_sr_tune(rbm.struct(), _ptr(sigma), _ptr(t), ns, prec, _ptr(scratch),
                                      scratch.numel(), _stream(stream)), "nk_sr_tune")
     return int(rbm._s.sr_splits)
+
+
+def nk_tune_shapes(rbm: Rbm, op: Operator, sigma, theta_tmp, eloc_tmp, scratch, stream=None):
+    """Autotune the theta / local-energy tile shapes on these samples
+    (synchronises); returns (theta_segs, eloc_segs), also stored in the RBM."""
+    _require_gpu(sigma, theta_tmp, eloc_tmp, scratch)
+    _check(load_library().nk_tune_shapes(rbm.struct(), _ptr(op.dev), op.n_moves, _ptr(sigma),
+                                         sigma.shape[0], _ptr(theta_tmp), _ptr(eloc_tmp),
+                                         _ptr(scratch), scratch.numel(), _stream(stream)),
+           "nk_tune_shapes")
+    return int(rbm._s.theta_segs), int(rbm._s.eloc_segs)
 
 
 def info_dict(info) -> dict:

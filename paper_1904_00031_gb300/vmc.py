@@ -136,8 +136,16 @@ class VmcSr:
             self._eager_step()
 
     def tune(self):
-        """Autotune the SR contractions on the current samples (synchronises)."""
+        """Autotune the tile shapes on the current samples (synchronises): the SR
+        adjoint's split-K count, and the CTAs per tile of the theta contraction
+        (tensor-core path) and of the local energies."""
         self.split_k = nk.nk_sr_tune(self.rbm, self.samples, self.t, self.prec, self.scratch)
+        if self.prec == nk.NK_PREC_BF16X2:
+            self.shapes = nk.nk_tune_shapes(self.rbm, self.op, self.samples, self.theta,
+                                            self.eloc, self.eloc_scratch)
+            # the tuner overwrote theta and E_loc: recompute them for the SR inputs
+            self.amplitudes()
+            self.energies()
         self.tuned = True
 
     def step(self):

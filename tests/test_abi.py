@@ -88,12 +88,12 @@ def test_host_argument_validation(lib):
     from paper_1904_00031_gb300 import nk
     assert lib.nk_rbm_logpsi(None, None, 4, 0, None, None, None) == 1
     assert b"rbm is NULL" in lib.nk_last_error()
-    r = nk._Rbm(0, 10, 0, 0, 8, 8, 8, 256, 1 << 20)
+    r = nk._Rbm(0, 10, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 20)
     assert lib.nk_rbm_logpsi(C.byref(r), None, 4, 0, None, None, None) == 2
-    r = nk._Rbm(10, 10, 0, 0, 8, 8, 8, 256, 16)
+    r = nk._Rbm(10, 10, 0, 0, 0, 0, 8, 8, 8, 256, 16)
     assert lib.nk_rbm_prepare(C.byref(r), None) == 2
     assert b"workspace" in lib.nk_last_error()
-    r = nk._Rbm(10, 10, 0, 0, 8, 8, 8, 256, 1 << 20)
+    r = nk._Rbm(10, 10, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 20)
     ch = nk._Chains(4, 64, 8, 1, 0)
     assert lib.nk_metropolis_sweep(C.byref(r), C.byref(ch), 0, None, None, 0, 1, 1, 8, None,
                                    None, 0, None) == 2
@@ -148,7 +148,7 @@ def test_batch_calls_check_every_item_first(lib):
 
     def sweep_items(m, bad_second):
         n, cplx = 8, 1
-        r = nk._Rbm(n, m, cplx, 0, 256, 256, 256, 4096, lib.nk_rbm_workspace_bytes(n, m, cplx))
+        r = nk._Rbm(n, m, cplx, 0, 0, 0, 256, 256, 256, 4096, lib.nk_rbm_workspace_bytes(n, m, cplx))
         ch = nk._Chains(16, 4, 4096, 1, 0, None)
         need = lib.nk_metropolis_scratch_bytes(n, m, cplx, 0, 0)
         good = nk._SweepItem(C.addressof(r), C.addressof(ch), 0, 0, None, None, 1, 2, 4096, None,
@@ -187,9 +187,9 @@ def test_symm_host_checks(lib):
     assert b"not a permutation" in lib.nk_last_error()
     # the untied RBM must be the expansion (m = alpha n_perm)
     s = nk._RbmSymm(n, alpha, g, 0, 8, 8, 8, 256, nb)
-    r = nk._Rbm(n, alpha * g + 1, 0, 0, 8, 8, 8, 256, 1 << 24)
+    r = nk._Rbm(n, alpha * g + 1, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 24)
     assert lib.nk_symm_expand(C.byref(s), C.byref(r), None) == 2
-    r = nk._Rbm(n, alpha * g, 0, 0, 8, 8, 8, 256, 1 << 24)
+    r = nk._Rbm(n, alpha * g, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 24)
     s_small = nk._RbmSymm(n, alpha, g, 0, 8, 8, 8, 256, nb - 256)
     assert lib.nk_symm_expand(C.byref(s_small), C.byref(r), None) == 2
     assert b"tables" in lib.nk_last_error()

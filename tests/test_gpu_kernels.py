@@ -386,3 +386,30 @@ def test_sr_autotune_keeps_results(nk, prec):
     d = (p.flat() - a) / 0.05
     d2 = (p.flat() - b) / 0.05
     assert np.linalg.norm(d - d2) <= 1e-4 * np.linalg.norm(d)
+
+
+def test_tune_shapes_keeps_results(nk):
+    """The tile-shape tuner picks one or two CTAs per tile for the theta
+    contraction and the local energies; theta is the same bits either way and
+    E_loc agrees to FP64 rounding of the two partial sums."""
+    w = W.workload("c5")
+    p = W.perturb_params(W.init_params(w.n, w.m, True, 0.01, w.seed), 0.02, 5)
+    ns = 1000
+    s = dev(W.random_configs(ns, w.n, 13, True))
+    r = make_rbm(nk, p)
+    gop = nk.Operator(w.op)
+    th = torch.empty(ns, w.m, dtype=torch.complex64, device="cuda")
+    el = torch.empty(ns, dtype=torch.complex128, device="cuda")
+    sc = nk.local_energy_scratch(r, gop)
+    ts, es = nk.nk_tune_shapes(r, gop, s, th, el, sc)
+    assert ts in (1, 2) and es in (1, 2)
+    out = {}
+    for segs in (1, 2):
+        r._s.theta_segs = segs
+        r._s.eloc_segs = segs
+        t = torch.empty_like(th)
+        nk.nk_rbm_theta(r, s, t, nk.NK_PREC_BF16X2)
+        e = nk.nk_local_energy(r, gop, s, t, scratch=sc)
+        out[segs] = (t.cpu().numpy(), e.cpu().numpy())
+    assert np.array_equal(out[1][0], out[2][0])
+    assert np.abs(out[1][1] - out[2][1]).max() <= 1e-12 * np.abs(out[1][1]).max()
