@@ -159,7 +159,7 @@ def run_oracle_all_cores(workload: str, n_chains: int, spc: int, n_cg: int,
 # single-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # workload at full size; a kernel that changed since its capture has no entry.
 NCU_TRAFFIC = {
-    ("j1j2_20x20_alpha4", "bf16x2", "local_energy_tiled"): 9.40e9 + 0.859e9,
+    ("j1j2_20x20_alpha4", "bf16x2", "local_energy_tiled"): 9.44e9 + 0.868e9,
 }
 
 ORACLE_SAMPLE = {"c5": (24, 2, 50), "c3": (64, 1, 50), "c2": (128, 4, 50), "c1": (16, 63, 120),
@@ -551,6 +551,8 @@ def run_gpu(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": nk.NK_INFO_LEN * 8},
         "gpu_launches": v.launches_per_step() * args.steps,
         "graph": bool(args.graph), "sr_split_k": getattr(v, "split_k", None),
+        "tile_shapes": (None if not hasattr(v, "shapes") else
+                        {"theta_ctas_per_tile": v.shapes[0], "eloc_ctas_per_tile": v.shapes[1]}),
         "clocks": clk,
     }
     return rank, out

@@ -435,14 +435,15 @@ nk_status nk_ffnn_backward(const nk_ffnn* f, const int8_t* sigma, int64_t ns, co
  * CTAs per tile (the second CTA taking half of the hidden or move tiles; the
  * results agree to FP64 rounding of the two partial sums) on the given
  * samples and stores the faster counts in rbm->theta_segs and rbm->eloc_segs.
- * theta_tmp (F32 [ns][m]) and eloc_tmp (c128 [ns]) are overwritten; scratch as
- * for nk_local_energy.  Unlike the other calls this one SYNCHRONISES `stream`
+ * theta_tmp (F32 [ns][m]), eloc_tmp (c128 [ns]) and t_tmp (F32 [ns][m], or NULL;
+ * given, the local energies are timed with their tanh(theta) output, as a VMC
+ * iteration runs them) are overwritten; scratch as for nk_local_energy.  Unlike the other calls this one SYNCHRONISES `stream`
  * (it measures with CUDA events) and must not be called while a stream is
  * being captured.  (The paper has no counterpart: a tuning aid of this
  * library.) */
 nk_status nk_tune_shapes(nk_rbm* rbm, const void* op_dev, int32_t n_moves, const int8_t* sigma,
-                         int64_t ns, void* theta_tmp, double* eloc_tmp, void* scratch,
-                         size_t scratch_bytes, void* stream);
+                         int64_t ns, void* theta_tmp, double* eloc_tmp, void* t_tmp,
+                         void* scratch, size_t scratch_bytes, void* stream);
 
 /* ------------------------------------------- batches of independent instances */
 

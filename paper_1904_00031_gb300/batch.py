@@ -114,7 +114,7 @@ class BatchedVmc:
         if self.prec != nk.NK_PREC_BF16X2:
             return
         for v in self.items:
-            nk.nk_tune_shapes(v.rbm, v.op, v.samples, v.theta, v.eloc, v.eloc_scratch)
+            nk.nk_tune_shapes(v.rbm, v.op, v.samples, v.theta, v.eloc, v.eloc_scratch, v.t)
             v.amplitudes()
             v.energies()
 

@@ -842,8 +842,8 @@ nk_status nk_supervised_step(nk_rbm* rbm, const int8_t* sigma, const double* log
 }
 
 nk_status nk_tune_shapes(nk_rbm* rbm, const void* op_dev, int32_t n_moves, const int8_t* sigma,
-                         int64_t ns, void* theta_tmp, double* eloc_tmp, void* scratch,
-                         size_t scratch_bytes, void* stream) {
+                         int64_t ns, void* theta_tmp, double* eloc_tmp, void* t_tmp,
+                         void* scratch, size_t scratch_bytes, void* stream) {
   if (nk_status e = check_rbm(rbm, "nk_tune_shapes")) return e;
   if (ns < 1 || n_moves < 0) return fail(NK_ERR_INVALID_ARG, "nk_tune_shapes: ns < 1");
   if (!op_dev || !sigma || !theta_tmp || !eloc_tmp)
@@ -883,7 +883,7 @@ nk_status nk_tune_shapes(nk_rbm* rbm, const void* op_dev, int32_t n_moves, const
       float ms = 0.f;
       if (nk_status e = time_launches(st, reps, [&] {
             return launch_local_energy(&r, op_dev, n_moves, sigma, theta_tmp, ns, eloc_tmp,
-                                       nullptr, scratch, scratch_bytes, st);
+                                       t_tmp, scratch, scratch_bytes, st);
           }, &ms))
         return e;
       if (ms < best) {

@@ -158,7 +158,7 @@ def load_library(path: str = LIB_PATH):
         "nk_supervised_scratch_bytes": (SZ, [I32, I32, I32, I64]),
         "nk_pt_scratch_bytes": (SZ, [I32, I32, I32, I32, I32, I32]),
         "nk_ffnn_scratch_bytes": (SZ, [P, I64]),
-        "nk_tune_shapes": (I32, [P, P, I32, P, I64, P, P, P, SZ, P]),
+        "nk_tune_shapes": (I32, [P, P, I32, P, I64, P, P, P, P, SZ, P]),
         "nk_ffnn_logpsi": (I32, [P, P, I64, P, P, SZ, P]),
         "nk_ffnn_backward": (I32, [P, P, I64, P, P, P, SZ, P]),
         "nk_pt_sweep": (I32, [P, P, I32, I32, P, P, I32, I32, I32, P, P, P, P, SZ, P]),
@@ -470,14 +470,15 @@ def nk_sr_tune(rbm: Rbm, sigma, t, prec=NK_PREC_FP32, scratch=None, stream=None)
     return int(rbm._s.sr_splits)
 
 
-def nk_tune_shapes(rbm: Rbm, op: Operator, sigma, theta_tmp, eloc_tmp, scratch, stream=None):
+def nk_tune_shapes(rbm: Rbm, op: Operator, sigma, theta_tmp, eloc_tmp, scratch, t_tmp=None,
+                   stream=None):
     """Autotune the theta / local-energy tile shapes on these samples
     (synchronises); returns (theta_segs, eloc_segs), also stored in the RBM."""
-    _require_gpu(sigma, theta_tmp, eloc_tmp, scratch)
+    _require_gpu(sigma, theta_tmp, eloc_tmp, scratch, t_tmp)
     _check(load_library().nk_tune_shapes(rbm.struct(), _ptr(op.dev), op.n_moves, _ptr(sigma),
                                          sigma.shape[0], _ptr(theta_tmp), _ptr(eloc_tmp),
-                                         _ptr(scratch), scratch.numel(), _stream(stream)),
-           "nk_tune_shapes")
+                                         _ptr(t_tmp), _ptr(scratch), scratch.numel(),
+                                         _stream(stream)), "nk_tune_shapes")
     return int(rbm._s.theta_segs), int(rbm._s.eloc_segs)
 
 

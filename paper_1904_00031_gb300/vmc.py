@@ -142,7 +142,7 @@ class VmcSr:
         self.split_k = nk.nk_sr_tune(self.rbm, self.samples, self.t, self.prec, self.scratch)
         if self.prec == nk.NK_PREC_BF16X2:
             self.shapes = nk.nk_tune_shapes(self.rbm, self.op, self.samples, self.theta,
-                                            self.eloc, self.eloc_scratch)
+                                            self.eloc, self.eloc_scratch, self.t)
             # the tuner overwrote theta and E_loc: recompute them for the SR inputs
             self.amplitudes()
             self.energies()
