@@ -7,19 +7,23 @@
 //
 // Forward (theta and the O x half of the SR matvec): one CTA owns 128
 // configurations; their sigma' rows stay resident in shared memory as K-major
-// 128-byte-swizzled tiles written by the CTA itself, the B planes of X stream
-// in by TMA through a 3-stage ring, one thread issues the MMAs (M = 128
-// configurations, N = 128 plane rows, K = n + 1 padded to 64) into one of two
-// TMEM accumulators, and four epilogue warps fold each finished 128 x 128 tile
-// (tcgen05.ld) into per-configuration FP64 sums while the next tile is built.
+// 128-byte-swizzled tiles (TMA-loaded from a BF16 copy of sigma' in the SR
+// forward; built by the CTA from the int8 samples for theta / ln psi), the B
+// planes of X stream in by TMA through a 3-stage ring, one thread issues the
+// MMAs (M = 128 configurations, N = 128 plane rows, K = n + 1 padded to 64)
+// into one of two TMEM accumulators, and four epilogue warps fold each
+// finished 128 x 128 tile (tcgen05.ld): ln cosh sums, theta / tanh(theta)
+// stores, or the T'.U dot products of the SR forward, while the next tile's
+// MMAs run.  The hidden tiles may be split over two CTAs.
 //
 // Adjoint (the O^H v half): one CTA owns 64 complex (128 real) parameter rows
-// j and a range of samples (split-K).  Four producer warps compute
+// j and a range of samples (split-K).  Eight producer warps compute
 // Z = conj(T'_sj) v_s for 64 samples at a time, split it into BF16 hi/lo and
 // write it, swizzled, as the A operand; sigma'^T tiles (a BF16 plane built once
 // per SR step) arrive by TMA; MMAs accumulate G[j][0..n] in TMEM (two halves of
-// N <= 224); the epilogue writes FP32 partials that a fixed-order FP64
-// reduction sums over the splits.
+// N <= 224); the epilogue writes FP32 partials that a fixed-order reduction
+// (FP32 sum plus its TwoSum error term, one FP64 conversion) sums over the
+// splits.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
