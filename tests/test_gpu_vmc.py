@@ -82,10 +82,7 @@ def test_vmc_energy_matches_oracle_heisenberg40(mods, prec):
     samples, exchange moves, SR with 50 CG iterations), 150 iterations from the
     same seeds as the oracle's run (tests/golden/vmc_c2.json)."""
     nk, VmcSr = mods
-    path = os.path.join(GOLDEN, "vmc_c2.json")
-    if not os.path.exists(path):
-        pytest.skip("oracle trace not written yet (tests/golden/make_vmc_golden.py c2)")
-    g = json.load(open(path))
+    g = json.load(open(os.path.join(GOLDEN, "vmc_c2.json")))
     w = W.workload("c2")
     p = W.init_params(w.n, w.m, w.is_complex, 0.01, w.seed)
     v = VmcSr(w, p, prec=prec, graph=True)
@@ -110,8 +107,6 @@ def test_batched_instances_match_oracle_runs(mods, prec):
     insts = W.batched_instances(64, 4242, 1024)
     b = BatchedVmc(insts, prec=prec, graph=True)
     keys = [0, 2, 3, 8]
-    if not all(os.path.exists(os.path.join(GOLDEN, f"vmc_c4_{k}.json")) for k in keys):
-        pytest.skip("oracle traces not written yet (tests/golden/make_vmc_golden.py c4_<k>)")
     goldens = {k: json.load(open(os.path.join(GOLDEN, f"vmc_c4_{k}.json"))) for k in keys}
     traces = {k: [] for k in keys}
     for _ in range(len(goldens[0]["energies"])):
