@@ -74,6 +74,12 @@ typedef struct nk_rbm {
   int32_t theta_segs; /* tensor-core ln psi / theta: CTAs per sample tile, each
                          taking a share of the hidden tiles (1 or 2); 0 = built-in
                          heuristic.  Set by nk_tune_shapes (or by hand)           */
+  int32_t sampler;    /* nk_metropolis_sweep kernel: 0 = built-in choice; 1 = one
+                         or two warps per chain; 2, 3, 4 = one CTA per proposal
+                         group (complex RBMs, group_size <= 8, m <= 1024, 2048,
+                         2304) with k - 1 hidden-unit pairs per thread, k this
+                         value.  Built-in: 2 for complex RBMs with m <= 256 and
+                         group_size <= 8, 4 for m > 2048, else 1             */
   double* a;          /* F64 [n]    (device)                                        */
   double* b;          /* F64 [m]    (device)                                        */
   double* w;          /* F64 [m][n] (device, row-major)                             */

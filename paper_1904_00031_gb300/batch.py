@@ -17,9 +17,15 @@ from .vmc import VmcSr, adj_centres, centring_fused
 
 
 def _metro_template(w) -> tuple:
-    """The Metropolis kernel template an instance runs (field, hidden units per
-    lane, warps per chain, group size): the library's rule, for counting the
-    fused launches."""
+    """The Metropolis kernel template an instance runs: the library's built-in
+    rule, for counting the fused launches.  One CTA per proposal group (complex
+    RBMs, group size <= 8, m <= 256 or > 2048): (unit pairs per thread, block
+    size); else warps per chain: (field, hidden units per lane, warps per chain,
+    group size)."""
+    if w.is_complex and w.group_size <= 8 and (w.m <= 256 or w.m > 2048):
+        pp = 1 if w.m <= 256 else 3
+        pairs = (w.m + 1) // 2
+        return ("group", pp, (pairs + pp - 1) // pp + (-((pairs + pp - 1) // pp)) % 32)
     mp = (w.m + 31) // 32 * 32
     wpc = 2 if (mp >= 512 and w.group_size * 64 <= 512) else 1
     e = (mp + 32 * wpc - 1) // (32 * wpc)

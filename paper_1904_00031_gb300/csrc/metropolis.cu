@@ -52,6 +52,7 @@ struct MetroArgs {
   int pt_R = 0;
   double* lval = nullptr;  // [nc] 2 Re ln psi of each chain's final state, or null
   int acc_add = 0;         // n_acc[c] += accepted (else =)
+  int m2p = 0;             // group kernel: unit pairs per table row (threads x pairs)
 };
 
 // Accept test U < exp(two_re), decided in FP64.  A float pre-test on
@@ -67,6 +68,16 @@ __device__ __forceinline__ bool accept_test(float u32, float two_re, double my_u
   const double U = __shfl_sync(0xffffffffu, my_u, src_lane);
   return U < exp((double)two_re);
 }
+
+// A lane's share of log2 prod_j |r_j|^2, made finite before it is summed with
+// the other lanes'.  The expanded |r|^2 = |C|^2 + |t|^2 |D|^2 - 2 s Re(t E)
+// loses its relative accuracy when |t| is large (theta near a zero of cosh) and
+// can round to zero or below for a move whose true |r|^2 is tiny: log2 is then
+// -inf or NaN.  Both become -1e30 (the move's ratio underflows to zero and it is
+// rejected, as it is in exact arithmetic up to a U below ~1e-30), +inf becomes
+// +1e30 (accepted), so that the sums stay finite and a NaN partial can only mean
+// a wait that gave up.
+__device__ __forceinline__ float clamp_log2(float x) { return fminf(fmaxf(x, -1e30f), 1e30f); }
 
 __device__ __forceinline__ int move_row(const MetroArgs& A, uint64_t ctr, uint32_t g, int step) {
   u4 us = philox_stream(g, ctr + (uint64_t)step, kTagSite, A.seed);
@@ -99,6 +110,25 @@ __host__ __device__ constexpr size_t cplx_row_bytes(int nu, int wpc) {
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// tanh addition update of two units' t after an accepted move with s_i = si,
+// from the unit pair's table values (|C|^2, |D|^2 as c2, d2; Re E, -Im E as
+// ex, ney):  Re t' = (t_x (|C|^2 + |D|^2) - s Re E (|t|^2 + 1)) / |r|^2,
+//            Im t' = (t_y (|C|^2 - |D|^2) - s Im E (1 - |t|^2)) / |r|^2.
+__device__ __forceinline__ void t_add_pair(float2& tx, float2& ty, float2 c2, float2 d2, float2 ex,
+                                           float2 ney, float si) {
+  const float2 m2s = make_float2(-2.f * si, -2.f * si);
+  const float2 ns2 = make_float2(-si, -si), s2 = make_float2(si, si);
+  const float2 one = make_float2(1.f, 1.f), mone = make_float2(-1.f, -1.f);
+  const float2 tt = f2fma(tx, tx, f2mul(ty, ty));
+  const float2 e = f2fma(tx, ex, f2mul(ty, ney));
+  const float2 r2 = f2fma(m2s, e, f2fma(tt, d2, c2));
+  const float2 inv = make_float2(__fdividef(1.f, r2.x), __fdividef(1.f, r2.y));
+  const float2 nx = f2fma(ns2, f2mul(ex, f2add(tt, one)), f2mul(tx, f2add(c2, d2)));
+  const float2 ny = f2fma(s2, f2mul(ney, f2fma(tt, mone, one)), f2mul(ty, f2fma(d2, mone, c2)));
+  tx = f2mul(nx, inv);
+  ty = f2mul(ny, inv);
+}
 
 __device__ __forceinline__ void pair_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -376,6 +406,7 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
         }
         l2 = P[0].log2v() + P[1].log2v() + P[2].log2v() + P[3].log2v();
         }
+        l2 = clamp_log2(l2);
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, off);
       }
@@ -400,26 +431,12 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
         ++nacc;
         if constexpr (CPLX) {
           const float4* row4 = reinterpret_cast<const float4*>(smem + (size_t)k * slot_bytes);
-          const float2 m2s = make_float2(-2.f * si, -2.f * si);
-          const float2 ns2 = make_float2(-si, -si), s2 = make_float2(si, si);
-          const float2 one = make_float2(1.f, 1.f), mone = make_float2(-1.f, -1.f);
 #pragma unroll
           for (int qp = 0; qp < EP; ++qp) {
             const float4 q0 = row4[(qp * WPC + h) * 64 + lane];
             const float4 q1 = row4[(qp * WPC + h) * 64 + 32 + lane];
-            const float2 c2 = make_float2(q0.x, q0.y), d2 = make_float2(q0.z, q0.w);
-            const float2 ex = make_float2(q1.x, q1.y), ney = make_float2(q1.z, q1.w);
-            const float2 tt = f2fma(tx[qp], tx[qp], f2mul(ty[qp], ty[qp]));
-            const float2 e = f2fma(tx[qp], ex, f2mul(ty[qp], ney));
-            const float2 r2 = f2fma(m2s, e, f2fma(tt, d2, c2));
-            const float2 inv = make_float2(__fdividef(1.f, r2.x), __fdividef(1.f, r2.y));
-            // Re: t_x (|C|^2 + |D|^2) - s Re E (|t|^2 + 1)
-            // Im: t_y (|C|^2 - |D|^2) - s Im E (1 - |t|^2)
-            const float2 nx = f2fma(ns2, f2mul(ex, f2add(tt, one)), f2mul(tx[qp], f2add(c2, d2)));
-            const float2 ny = f2fma(s2, f2mul(ney, f2fma(tt, mone, one)),
-                                    f2mul(ty[qp], f2fma(d2, mone, c2)));
-            tx[qp] = f2mul(nx, inv);
-            ty[qp] = f2mul(ny, inv);
+            t_add_pair(tx[qp], ty[qp], make_float2(q0.x, q0.y), make_float2(q0.z, q0.w),
+                       make_float2(q1.x, q1.y), make_float2(q1.z, q1.w), si);
           }
           theta_add<true, WPC, TC, 0>(tmem_th, wdc, -2.f * si, h, lane, mp);
         } else {
@@ -559,6 +576,12 @@ __global__ void __launch_bounds__(512, 1) metropolis_batch_kernel(const __grid_c
   metropolis_body<CPLX, NU, WPC>(B.a[k], (int)blockIdx.x - B.start[k]);
 }
 
+}  // namespace nk
+
+#include "metro_group.cuh"
+
+namespace nk {
+
 // Per-bond tables of an exchange move of a real RBM (s_k = -s_i):
 // cosh c = A_i A_k - B_i B_k, sinh c / s_i = B_i A_k - A_i B_k, increment W_i - W_k.
 // Element x of nb * mp.
@@ -646,7 +669,8 @@ __global__ void cplx_rows_kernel(const float4* __restrict__ tab, const float2* _
 
 // The table builds of many problems in one launch: job k owns elements
 // [start[k], start[k + 1]) of the concatenated index range.
-enum { kTabNone = 0, kTabRealPair = 1, kTabCplxFlip = 2, kTabCplxPair = 3 };
+enum { kTabNone = 0, kTabRealPair = 1, kTabCplxFlip = 2, kTabCplxPair = 3, kTabGroupFlip = 4,
+       kTabGroupPair = 5 };
 struct TableJob {
   int kind, mp, nu, wpc;
   const void* tab;
@@ -655,6 +679,7 @@ struct TableJob {
   const int32_t* bk;
   void* out;
   void* wd;
+  int m = 0, m2p = 0;  // group rows
 };
 struct TableBatch {
   int n;
@@ -676,6 +701,9 @@ __global__ void tables_batch_kernel(const __grid_constant__ TableBatch B) {
     if (J.kind == kTabRealPair)
       pair_table_real_elem(e, (const float2*)J.tab, (const float*)J.wt, J.bi, J.bk, J.mp,
                            (float2*)J.out, (float*)J.wd);
+    else if (J.kind == kTabGroupFlip || J.kind == kTabGroupPair)
+      group_rows_elem(e, J.kind == kTabGroupPair, (const float4*)J.tab, (const float2*)J.wt, J.bi,
+                      J.bk, J.m, J.mp, J.m2p, (float4*)J.out);
     else
       cplx_rows_elem(e, J.kind == kTabCplxPair, (const float4*)J.tab, (const float2*)J.wt, J.bi,
                      J.bk, J.mp, J.nu, J.wpc, (float4*)J.out, (float2*)J.wd);
@@ -729,7 +757,12 @@ size_t metropolis_scratch_bytes(int n, int m, int cplx, int move, int nb) {
   const int64_t rows = move == NK_MOVE_FLIP ? n : nb;
   size_t bytes = (size_t)round_up((int64_t)(rows * row), 256);
   if (move != NK_MOVE_FLIP) bytes += (size_t)round_up((int64_t)nb * mp * f, 256);
-  return bytes;
+  // or the group kernel's rows (any of its unit-pair choices)
+  size_t grow = 0;
+  for (int pp = 1; pp <= 3; ++pp)
+    if (group_threads(m, pp) <= group_max_threads(pp))
+      grow = std::max(grow, group_row_bytes(group_threads(m, pp) * pp));
+  return std::max(bytes, (size_t)round_up((int64_t)rows * (int64_t)grow, 256));
 }
 
 // Launch functors for the kernel templates: one problem, or a batch of problems
@@ -765,6 +798,49 @@ struct BatchLaunch {
     return check_launch("nk_batch_sweep");
   }
 };
+
+struct GroupSingleLaunch {
+  const MetroArgs& A;
+  int threads;
+  size_t smem;
+  cudaStream_t st;
+  template <int PP>
+  nk_status go() const {
+    auto kern = metropolis_group_kernel<PP>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return fail(NK_ERR_CUDA, "nk_metropolis_sweep: cannot reserve %zu B shared memory", smem);
+    const int blocks = (A.nc + A.G - 1) / A.G;
+    kern<<<blocks, threads, smem, st>>>(A);
+    return check_launch("nk_metropolis_sweep");
+  }
+};
+
+struct GroupBatchLaunch {
+  const MetroBatch& B;
+  int threads;
+  size_t smem;
+  cudaStream_t st;
+  template <int PP>
+  nk_status go() const {
+    auto kern = metropolis_group_batch_kernel<PP>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return fail(NK_ERR_CUDA, "nk_batch_sweep: cannot reserve %zu B shared memory", smem);
+    kern<<<B.start[B.n], threads, smem, st>>>(B);
+    return check_launch("nk_batch_sweep");
+  }
+};
+
+template <class Fn>
+static nk_status launch_group(int pp, const Fn& fn) {
+  switch (pp) {
+    case 1: return fn.template go<1>();
+    case 2: return fn.template go<2>();
+    case 3: return fn.template go<3>();
+  }
+  return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: %d unit pairs per thread", pp);
+}
 
 template <bool CPLX, class Fn>
 static nk_status launch_c(int nu, int wpc, int m, const Fn& fn) {
@@ -819,6 +895,8 @@ struct MetroPlan {
   MetroArgs A;
   bool cplx;
   int nu, wpc;
+  int group_pp = 0;   // > 0: the group kernel with this many unit pairs per thread
+  int threads = 0;    // its block size
   size_t smem;
   TableJob tj;
   int64_t tab_elems;
@@ -861,6 +939,78 @@ static nk_status plan_metropolis(const nk_rbm* r, const nk_chains* ch, int move,
   A.wt = ws + L.wt;
   A.b32 = ws + L.b32;
   const bool cplx = r->is_complex != 0;
+  // kernel: one CTA per proposal group (complex RBMs, group_size <= 8) or one
+  // or two warps per chain
+  const int choice = r->sampler;
+  if (choice < 0 || choice > 4)
+    return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: sampler %d is not 0..4", choice);
+  // built-in choice (measured on the 1D Heisenberg shapes, 16384 chains): the
+  // group kernel with one unit pair per thread up to m = 256 (1.3 - 1.7x faster
+  // at m = 80 - 160), warps per chain from m = 400 to 2048 (1.2 - 1.35x faster
+  // there), the group kernel with three pairs per thread above 2048 (the only
+  // one that holds t on chip there)
+  int gpp = 0;
+  if (cplx && A.G <= kGroupChains) {
+    if (choice == 0)
+      gpp = r->m <= 256 ? 1 : (r->m > 2048 ? 3 : 0);
+    else if (choice >= 2)
+      gpp = choice - 1;
+  }
+  if (gpp && group_threads(r->m, gpp) > group_max_threads(gpp)) gpp = 0;
+  if (choice >= 2 && !gpp)
+    return fail(NK_ERR_SHAPE,
+                "nk_metropolis_sweep: sampler %d needs a complex RBM, group_size <= 8 and "
+                "m <= %d",
+                choice, 2 * (choice - 1) * group_max_threads(choice - 1));
+  if (gpp) {
+    const int T = group_threads(r->m, gpp), NW = T / 32;
+    const int m2p = T * gpp;
+    const size_t row = group_row_bytes(m2p);
+    const size_t need = metropolis_scratch_bytes(r->n, r->m, 1, move, nb);
+    if (!scratch || scratch_bytes < need)
+      return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: scratch of %zu B, need %zu B",
+                  scratch_bytes, need);
+    // ring depth: as many row slots as fit next to the partials, barriers and
+    // the per-warp spin bytes (theta lives in tensor memory)
+    const size_t rest = (size_t)64 * NW + 8 * kMaxRing + 16 + (size_t)NW * round_up(r->n, 16);
+    const size_t cap = 227 * 1024;
+    const int ring =
+        rest + 2 * row > cap ? 0 : (int)std::min<size_t>(kMaxRing, (cap - rest) / row);
+    if (ring < 2)
+      return fail(NK_ERR_SHAPE,
+                  "nk_metropolis_sweep: m = %d leaves room for fewer than two row slots in "
+                  "227 KB of shared memory",
+                  r->m);
+    if ((int64_t)(n_discard + n_samples) * r->n > 0x7fffffff)
+      return fail(NK_ERR_SHAPE, "nk_metropolis_sweep: too many proposals in one call");
+    A.ring = ring;
+    A.m2p = m2p;
+    A.cd = scratch;
+    A.wd = nullptr;
+    P->cplx = true;
+    P->nu = 0;
+    P->wpc = 0;
+    P->group_pp = gpp;
+    P->threads = T;
+    // tensor memory admits 512 / tcols CTAs per SM: ask for enough shared
+    // memory that no more are resident (228 KB per SM, 1 KB reserved per CTA)
+    const int tcw = 32 * gpp * ((NW + 3) / 4);
+    const int tcols = tcw <= 32 ? 32 : tcw <= 64 ? 64 : tcw <= 128 ? 128 : tcw <= 256 ? 256 : 512;
+    const size_t floor_smem = (size_t)233472 / (size_t)(512 / tcols + 1) + 1 - 1024;
+    P->smem = std::max((size_t)ring * row + rest, floor_smem);
+    P->ctr_dev = ch->counter_dev;
+    P->advance = (uint64_t)(n_discard + n_samples) * r->n;
+    const int rows = move == NK_MOVE_FLIP ? r->n : nb;
+    TableJob& J = P->tj;
+    J = TableJob{move == NK_MOVE_FLIP ? kTabGroupFlip : kTabGroupPair,
+                 L.mp, 0, 0, ws + L.tab, ws + L.wt, bi, bk, scratch, nullptr, r->m, m2p};
+    P->tab_elems = (int64_t)rows * m2p;
+    if (skip_tables) {  // rows of an earlier launch of the same call
+      J.kind = kTabNone;
+      P->tab_elems = 0;
+    }
+    return NK_OK;
+  }
   const size_t f = cplx ? 8 : 4;
   const int wpc = metro_wpc(L.mp, A.G);
   const int nu = metro_nu(L.mp, cplx, wpc);
@@ -943,6 +1093,14 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
       pair_tables_real_kernel<<<(unsigned)blocks, 256, 0, st>>>(
           (const float2*)J.tab, (const float*)J.wt, bi, bk, nb, J.mp, (float2*)J.out,
           (float*)J.wd);
+    else if (J.kind == kTabGroupFlip)
+      group_rows_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(
+          (const float4*)J.tab, (const float2*)J.wt, bi, bk, r->n, J.m, J.mp, J.m2p,
+          (float4*)J.out);
+    else if (J.kind == kTabGroupPair)
+      group_rows_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(
+          (const float4*)J.tab, (const float2*)J.wt, bi, bk, nb, J.m, J.mp, J.m2p,
+          (float4*)J.out);
     else if (J.kind == kTabCplxFlip)
       cplx_rows_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(
           (const float4*)J.tab, (const float2*)J.wt, bi, bk, r->n, J.mp, J.nu, J.wpc,
@@ -953,9 +1111,14 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
           (float4*)J.out, (float2*)J.wd);
     if (nk_status e = check_launch("nk_metropolis_sweep(tables)")) return e;
   }
-  SingleLaunch L1{P.A, P.smem, st};
-  nk_status e = P.cplx ? launch_c<true>(P.nu, P.wpc, r->m, L1)
-                       : launch_c<false>(P.nu, P.wpc, r->m, L1);
+  nk_status e;
+  if (P.group_pp) {
+    GroupSingleLaunch LG{P.A, P.threads, P.smem, st};
+    e = launch_group(P.group_pp, LG);
+  } else {
+    SingleLaunch L1{P.A, P.smem, st};
+    e = P.cplx ? launch_c<true>(P.nu, P.wpc, r->m, L1) : launch_c<false>(P.nu, P.wpc, r->m, L1);
+  }
   if (e == NK_OK && ch->counter_dev) {
     advance_counter_kernel<<<1, 1, 0, st>>>(ch->counter_dev, P.advance);
     e = check_launch("nk_metropolis_sweep(counter)");
@@ -1009,7 +1172,7 @@ nk_status launch_metropolis_fused(const nk_sweep_item* items, const int* idx, in
     for (int v = u; v < n && B.n < kMetroBatch; ++v) {
       const MetroPlan& P = plans[v];
       if (done[v] || P.cplx != P0.cplx || P.nu != P0.nu || P.wpc != P0.wpc ||
-          P.A.G != P0.A.G)
+          P.A.G != P0.A.G || P.group_pp != P0.group_pp || P.threads != P0.threads)
         continue;
       B.a[B.n] = P.A;
       B.start[B.n + 1] = B.start[B.n] + (P.A.nc + P.A.G - 1) / P.A.G;
@@ -1017,9 +1180,15 @@ nk_status launch_metropolis_fused(const nk_sweep_item* items, const int* idx, in
       smem = std::max(smem, P.smem);
       done[v] = true;
     }
-    BatchLaunch LB{B, P0.A.G, smem, st};
-    nk_status e = P0.cplx ? launch_c<true>(P0.nu, P0.wpc, P0.A.m, LB)
-                          : launch_c<false>(P0.nu, P0.wpc, P0.A.m, LB);
+    nk_status e;
+    if (P0.group_pp) {
+      GroupBatchLaunch LB{B, P0.threads, smem, st};
+      e = launch_group(P0.group_pp, LB);
+    } else {
+      BatchLaunch LB{B, P0.A.G, smem, st};
+      e = P0.cplx ? launch_c<true>(P0.nu, P0.wpc, P0.A.m, LB)
+                  : launch_c<false>(P0.nu, P0.wpc, P0.A.m, LB);
+    }
     if (e) return e;  // problems of this template beyond kMetroBatch start later batches
   }
   // device counters

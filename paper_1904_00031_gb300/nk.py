@@ -54,7 +54,7 @@ class NkError(RuntimeError):
 class _Rbm(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("is_complex", C.c_int32),
                 ("sr_splits", C.c_int32), ("eloc_segs", C.c_int32), ("theta_segs", C.c_int32),
-                ("a", C.c_void_p), ("b", C.c_void_p), ("w", C.c_void_p),
+                ("sampler", C.c_int32), ("a", C.c_void_p), ("b", C.c_void_p), ("w", C.c_void_p),
                 ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
 
 
@@ -212,7 +212,7 @@ class Rbm:
         off = (-self.ws.data_ptr()) % 256
         self._ws_ptr = self.ws.data_ptr() + off
         self._ws_bytes = nb
-        self._s = _Rbm(self.n, self.m, int(is_complex), 0, 0, 0, self.a.data_ptr(),
+        self._s = _Rbm(self.n, self.m, int(is_complex), 0, 0, 0, 0, self.a.data_ptr(),
                        self.b.data_ptr(), self.w.data_ptr(), self._ws_ptr, nb)
 
     @property

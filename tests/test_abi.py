@@ -88,12 +88,12 @@ def test_host_argument_validation(lib):
     from paper_1904_00031_gb300 import nk
     assert lib.nk_rbm_logpsi(None, None, 4, 0, None, None, None) == 1
     assert b"rbm is NULL" in lib.nk_last_error()
-    r = nk._Rbm(0, 10, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 20)
+    r = nk._Rbm(0, 10, 0, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 20)
     assert lib.nk_rbm_logpsi(C.byref(r), None, 4, 0, None, None, None) == 2
-    r = nk._Rbm(10, 10, 0, 0, 0, 0, 8, 8, 8, 256, 16)
+    r = nk._Rbm(10, 10, 0, 0, 0, 0, 0, 8, 8, 8, 256, 16)
     assert lib.nk_rbm_prepare(C.byref(r), None) == 2
     assert b"workspace" in lib.nk_last_error()
-    r = nk._Rbm(10, 10, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 20)
+    r = nk._Rbm(10, 10, 0, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 20)
     ch = nk._Chains(4, 64, 8, 1, 0)
     assert lib.nk_metropolis_sweep(C.byref(r), C.byref(ch), 0, None, None, 0, 1, 1, 8, None,
                                    None, 0, None) == 2
@@ -106,9 +106,13 @@ def test_host_argument_validation(lib):
     assert lib.nk_metropolis_scratch_bytes(400, 1600, 0, 1, 800) == 800 * 1600 * 12
     # complex RBM: pair rows of 512 * NU * WPC bytes, sized for the larger of one
     # warp per chain (NU = 64) and two (NU = 26), per site (flips) or bond
-    # (exchanges, plus complex increments)
-    assert lib.nk_metropolis_scratch_bytes(400, 1600, 1, 0, 800) == 400 * 512 * 64
-    assert lib.nk_metropolis_scratch_bytes(400, 1600, 1, 1, 800) == 800 * 512 * 64 + 800 * 1600 * 8
+    # (exchanges, plus complex increments), or the group kernel's rows of 48 bytes
+    # per unit pair, sized for its widest padding (3 pairs per thread: 288 threads,
+    # 864 pairs), whichever is larger
+    assert lib.nk_metropolis_scratch_bytes(400, 1600, 1, 0, 800) == max(400 * 512 * 64,
+                                                                        400 * 48 * 864)
+    assert lib.nk_metropolis_scratch_bytes(400, 1600, 1, 1, 800) == max(
+        800 * 512 * 64 + 800 * 1600 * 8, 800 * 48 * 864)
     assert lib.nk_sr_step(C.byref(r), 8, 8, 8, None, 10, 3, 0.01, 0.01, 5, 0.0, 0, 256, 1 << 20,
                           8, None) == 2  # 10 samples do not split into 3 chains
     assert ch.counter == 0
@@ -148,7 +152,7 @@ def test_batch_calls_check_every_item_first(lib):
 
     def sweep_items(m, bad_second):
         n, cplx = 8, 1
-        r = nk._Rbm(n, m, cplx, 0, 0, 0, 256, 256, 256, 4096, lib.nk_rbm_workspace_bytes(n, m, cplx))
+        r = nk._Rbm(n, m, cplx, 0, 0, 0, 0, 256, 256, 256, 4096, lib.nk_rbm_workspace_bytes(n, m, cplx))
         ch = nk._Chains(16, 4, 4096, 1, 0, None)
         need = lib.nk_metropolis_scratch_bytes(n, m, cplx, 0, 0)
         good = nk._SweepItem(C.addressof(r), C.addressof(ch), 0, 0, None, None, 1, 2, 4096, None,
@@ -158,10 +162,11 @@ def test_batch_calls_check_every_item_first(lib):
         items = (nk._SweepItem * 2)(good, bad if bad_second else good)
         return items, (r, ch)
 
-    items, keep = sweep_items(2048, True)     # the widest sampler layer passes its checks
+    # complex RBM, 4 chains per group: the group kernel holds up to 2304 hidden units
+    items, keep = sweep_items(2304, True)     # the widest sampler layer passes its checks
     assert lib.nk_batch_sweep(C.cast(items, C.c_void_p), 2, None) == 1
     assert b"item 1" in lib.nk_last_error()
-    items, keep = sweep_items(2049, True)     # one unit too many: item 0 is rejected
+    items, keep = sweep_items(2305, True)     # one unit too many: item 0 is rejected
     assert lib.nk_batch_sweep(C.cast(items, C.c_void_p), 2, None) == 2
     assert b"item 0" in lib.nk_last_error()
     assert lib.nk_batch_sweep(None, 3, None) == 1
@@ -187,9 +192,9 @@ def test_symm_host_checks(lib):
     assert b"not a permutation" in lib.nk_last_error()
     # the untied RBM must be the expansion (m = alpha n_perm)
     s = nk._RbmSymm(n, alpha, g, 0, 8, 8, 8, 256, nb)
-    r = nk._Rbm(n, alpha * g + 1, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 24)
+    r = nk._Rbm(n, alpha * g + 1, 0, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 24)
     assert lib.nk_symm_expand(C.byref(s), C.byref(r), None) == 2
-    r = nk._Rbm(n, alpha * g, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 24)
+    r = nk._Rbm(n, alpha * g, 0, 0, 0, 0, 0, 8, 8, 8, 256, 1 << 24)
     s_small = nk._RbmSymm(n, alpha, g, 0, 8, 8, 8, 256, nb - 256)
     assert lib.nk_symm_expand(C.byref(s_small), C.byref(r), None) == 2
     assert b"tables" in lib.nk_last_error()

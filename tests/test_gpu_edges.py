@@ -54,10 +54,12 @@ def test_logpsi_bf16x2_rejects_too_wide(nk):
         nk.nk_rbm_logpsi(r, dev(W.random_configs(4, 448, 1)), prec=nk.NK_PREC_BF16X2)
 
 
-@pytest.mark.parametrize("cplx", [False, True])
-def test_metropolis_widest_hidden_layer(nk, cplx):
-    """m = 2048, the largest hidden layer the sampler holds on chip."""
-    n, m, nc, G = 8, 2048, 16, 4
+@pytest.mark.parametrize("cplx,sampler,m", [(False, 0, 2048), (True, 1, 2048), (True, 0, 2048),
+                                             (True, 4, 2304)])
+def test_metropolis_widest_hidden_layer(nk, cplx, sampler, m):
+    """The largest hidden layers the samplers hold on chip: m = 2048 with warps
+    per chain, 2048 and 2304 with one CTA per proposal group."""
+    n, nc, G = 8, 16, 4
     p = W.perturb_params(W.init_params(n, m, cplx, 0.01, 21), 0.05, 22)
     s0 = W.init_chains(nc, n, False, 23)
     bonds = W.chain_bonds(n)
@@ -65,6 +67,7 @@ def test_metropolis_widest_hidden_layer(nk, cplx):
     samp, fin, cnt, nacc, marg = osam.metropolis(p, s0, "flip", bonds, G, seed, counter, nd, nsamp,
                                                  return_margin=True)
     r = make_rbm(nk, p)
+    r._s.sampler = sampler
     ch = nk.Chains(s0, G, seed)
     acc = torch.zeros(nc, dtype=torch.int64, device="cuda")
     out = nk.nk_metropolis_sweep(r, ch, nk.NK_MOVE_FLIP, None, None, nd, nsamp, n_accept_out=acc)
@@ -76,10 +79,18 @@ def test_metropolis_widest_hidden_layer(nk, cplx):
     assert np.array_equal(acc.cpu().numpy()[ok], nacc[ok])
 
 
-def test_metropolis_rejects_too_many_hidden_units(nk):
-    p = W.init_params(8, 2049, True, 0.01, 2)
+@pytest.mark.parametrize("cplx,m,G,sampler", [(True, 2049, 4, 1), (False, 2049, 4, 0),
+                                              (True, 2049, 16, 0), (True, 2305, 4, 0),
+                                              (True, 1025, 4, 2), (True, 2049, 4, 3),
+                                              (True, 40, 16, 3), (False, 40, 4, 3),
+                                              (True, 40, 4, 5)])
+def test_metropolis_rejects_shapes_out_of_range(nk, cplx, m, G, sampler):
+    """Hidden layers beyond what a sampler holds on chip, the group kernel on a
+    real RBM or with more than 8 chains per group, an unknown sampler."""
+    p = W.init_params(8, m, cplx, 0.01, 2)
     r = make_rbm(nk, p)
-    ch = nk.Chains(W.init_chains(4, 8, False, 3), 4, 5)
+    r._s.sampler = sampler
+    ch = nk.Chains(W.init_chains(G, 8, False, 3), G, 5)
     with pytest.raises(nk.NkError):
         nk.nk_metropolis_sweep(r, ch, nk.NK_MOVE_FLIP, None, None, 1, 1)
     assert ch.counter == 0

@@ -161,12 +161,17 @@ def test_logderiv_dense(nk, cplx):
 
 # ---------------------------------------------------------------- sampling
 
-@pytest.mark.parametrize("move,n,m,cplx,G", [("flip", 10, 10, False, 8), ("flip", 24, 40, True, 4),
-                                             ("exchange", 12, 24, True, 8),
-                                             ("exchange", 20, 20, False, 1)])
-def test_metropolis_trajectories(nk, move, n, m, cplx, G):
+# sampler: 1 = warps per chain; 2, 3, 4 = one CTA per proposal group with 1, 2, 3
+# hidden-unit pairs per thread (complex RBMs, group_size <= 8); 0 = built-in choice
+@pytest.mark.parametrize("move,n,m,cplx,G,nc,sampler", [
+    ("flip", 10, 10, False, 8, 40, 0), ("flip", 24, 40, True, 4, 40, 1),
+    ("flip", 24, 40, True, 4, 40, 2), ("flip", 24, 40, True, 4, 40, 3),
+    ("flip", 24, 40, True, 4, 40, 4), ("exchange", 12, 24, True, 8, 40, 1),
+    ("exchange", 12, 24, True, 8, 43, 3), ("exchange", 12, 24, True, 8, 43, 4),
+    ("exchange", 16, 300, True, 8, 43, 2), ("exchange", 16, 300, True, 5, 43, 3),
+    ("exchange", 20, 20, False, 1, 40, 0)])
+def test_metropolis_trajectories(nk, move, n, m, cplx, G, nc, sampler):
     p = W.perturb_params(W.init_params(n, m, cplx, 0.01, 77), 0.5 / np.sqrt(n), 3)
-    nc = 40
     sz = move == "exchange"
     s0 = W.init_chains(nc, n, sz, 8)
     bonds = W.chain_bonds(n)
@@ -174,6 +179,7 @@ def test_metropolis_trajectories(nk, move, n, m, cplx, G):
     samp, fin, cnt, nacc, marg = osam.metropolis(p, s0, move, bonds, G, seed, counter, nd, nsamp,
                                                  return_margin=True)
     r = make_rbm(nk, p)
+    r._s.sampler = sampler
     ch = nk.Chains(s0, G, seed)
     ch.counter = counter
     acc = torch.zeros(nc, dtype=torch.int64, device="cuda")
@@ -185,6 +191,7 @@ def test_metropolis_trajectories(nk, move, n, m, cplx, G):
     ref = samp.reshape(nc, nsamp, n)
     ok = marg > 1e-3
     assert ok.sum() >= nc // 2
+    assert 0 < nacc.sum() < nc * (nd + nsamp) * n
     assert np.array_equal(got[ok], ref[ok])
     assert np.array_equal(ch.sigma.cpu().numpy()[ok], fin[ok])
     assert np.array_equal(acc.cpu().numpy()[ok], nacc[ok])

@@ -73,8 +73,11 @@ def make_rbm(nk, p):
 
 # ---------------------------------------------------------------- Metropolis, bench template
 
+# sampler 1: two warps per chain; 3 (the built-in choice here) and 4: one CTA per
+# proposal group with 2 and 3 hidden-unit pairs per thread
+@pytest.mark.parametrize("sampler", [1, 3, 4])
 @pytest.mark.parametrize("move", ["exchange", "flip"])
-def test_metropolis_trajectories_m1600_two_warps(nk, move):
+def test_metropolis_trajectories_m1600(nk, move, sampler):
     L, m = 8, 1600
     n = L * L
     p = W.perturb_params(W.init_params(n, m, True, 0.01, 1237), 0.03, 5)
@@ -86,6 +89,7 @@ def test_metropolis_trajectories_m1600_two_warps(nk, move):
     samp, fin, cnt, nacc, marg = osam.metropolis(p, s0, move, bonds, group, seed, counter, nd,
                                                  nsamp, return_margin=True)
     r = make_rbm(nk, p)
+    r._s.sampler = sampler
     ch = nk.Chains(s0, group, seed)
     ch.counter = counter
     acc = torch.zeros(nc, dtype=torch.int64, device="cuda")
@@ -96,7 +100,8 @@ def test_metropolis_trajectories_m1600_two_warps(nk, move):
     got = out.cpu().numpy().reshape(nc, nsamp, n)
     ref = samp.reshape(nc, nsamp, n)
     ok = marg > EPS_TIE
-    print(f"\nMetropolis m=1600 {move}: {ok.sum()} of {nc} chains away from ties, acceptance "
+    print(f"\nMetropolis m=1600 {move} sampler {sampler}: {ok.sum()} of {nc} chains away from "
+          f"ties, acceptance "
           f"{nacc.sum() / (nc * (nd + nsamp) * n):.3f}")
     assert ok.sum() >= (3 * nc) // 4, ok.sum()
     assert 0 < nacc.sum() < nc * (nd + nsamp) * n  # neither frozen nor trivially accepting
@@ -104,6 +109,38 @@ def test_metropolis_trajectories_m1600_two_warps(nk, move):
     assert not bad, (bad, marg[bad])
     assert np.array_equal(ch.sigma.cpu().numpy()[ok], fin[ok])
     assert np.array_equal(acc.cpu().numpy()[ok], nacc[ok])
+
+
+@pytest.mark.parametrize("sampler", [1, 3])
+def test_metropolis_low_acceptance_reports_no_timeout(nk, sampler):
+    """Chains of a 400-site, 1600-unit complex RBM (parameters perturbed by 0.05)
+    that have settled where almost every exchange is rejected: some proposals
+    then have |r_j|^2 that rounds to zero or below in the expanded FP32 form
+    (theta near a zero of cosh).  Such a move is rejected; it must not read as a
+    timed-out warp (which once stopped a CTA's copies until its bounded waits ran
+    out, and marked its chains).  Two calls of 1 + 4 sweeps of 16384 chains."""
+    n, m, nc, group = 400, 1600, 16384, 8
+    p = W.perturb_params(W.init_params(n, m, True, 0.01, 7), 0.05, 5)
+    r = make_rbm(nk, p)
+    r._s.sampler = sampler
+    bonds = W.chain_bonds(n)
+    bi, bk = dev(bonds[:, 0].copy()), dev(bonds[:, 1].copy())
+    ch = nk.Chains(W.init_chains(nc, n, True, 3), group, 11)
+    acc = torch.zeros(nc, dtype=torch.int64, device="cuda")
+    flags = nk.nk_query_status()  # clears earlier bits
+    out = None
+    for _ in range(2):
+        out = nk.nk_metropolis_sweep(r, ch, nk.NK_MOVE_EXCHANGE, bi, bk, 1, 4, samples_out=out,
+                                     n_accept_out=acc)
+    nk.nk_query_status(flags)
+    torch.cuda.synchronize()
+    a = acc.cpu().numpy()
+    assert int(flags.item()) == 0
+    assert np.all(a >= 0)  # no chain marked (UINT64_MAX reads as -1)
+    rate = a.sum() / (nc * 5 * n)
+    print(f"\nlow-acceptance sampling, sampler {sampler}: acceptance {rate:.4f}")
+    assert 0 < rate < 0.05
+    assert np.all(out.cpu().numpy().astype(int).sum(axis=1) == 0)  # S^z = 0 kept
 
 
 # ---------------------------------------------------------------- SR force entry by entry
