@@ -43,8 +43,9 @@ struct MetroArgs {
   uint64_t* n_acc;      // [nc] or null
   const double* a;      // master a (F64)
   const void* cd;       // real: [rows][mp] T2 (cosh c, sinh c / s_i) per site (flip) or bond;
-                        // complex: [rows] pair rows of cplx_row_bytes(NU, WPC)
-  const void* wd;       // [rows][mp] F : W_i (flip) or W_i - W_k (bond)
+                        // complex: [rows] pair rows of cplx_row_stride(NU, WPC, mp) bytes,
+                        // the theta increments included
+  const void* wd;       // real: [rows][mp] F : W_i (flip) or W_i - W_k (bond); complex: unused
   const void* wt;       // [n][mp] F    : W transposed (initial theta)
   const void* b32;      // [mp] F
   // parallel tempering (0 / null: plain sampling): chain c is replica c % pt_R
@@ -101,10 +102,16 @@ constexpr int kMaxRing = 8;
 // Complex tables: a thread (half h, lane l) owns units j = 32 (h + WPC q) + l,
 // q < NU, taken in pairs (2 qp, 2 qp + 1).  A row holds one 1024-byte block per
 // (qp, h), in the order qp * WPC + h: 32 float4 (|C|^2 of the pair, |D|^2 of
-// the pair), then 32 float4 (Re E of the pair, -Im E of the pair), E = conj(C) D.
+// the pair), then 32 float4 (Re E of the pair, -Im E of the pair), E = conj(C) D,
+// followed by the row's theta increments [mp] float2 (W_i for a flip, W_i - W_k
+// for an exchange), so that one bulk copy brings a step's whole slot (a CTA's
+// bulk copies complete one after another, a few hundred cycles each).
 // Units beyond m hold C = 1, D = 0 (a factor of exactly 1).
 __host__ __device__ constexpr size_t cplx_row_bytes(int nu, int wpc) {
   return (size_t)512 * nu * wpc;
+}
+__host__ __device__ constexpr size_t cplx_row_stride(int nu, int wpc, int mp) {
+  return cplx_row_bytes(nu, wpc) + (size_t)mp * 8;
 }
 
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -306,8 +313,12 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
     const int row = move_row(A, ctr, g, step);
     unsigned char* sl = smem + (size_t)k * slot_bytes;
     mbar_arrive_expect_tx(&full[k], cd_bytes + wd_bytes);
-    bulk_g2s(sl, cdg + (int64_t)row * cd_row, cd_bytes, &full[k]);
-    bulk_g2s(sl + cd_bytes, wdg + (int64_t)row * mp, wd_bytes, &full[k]);
+    if constexpr (CPLX) {  // table block and increments of a row are contiguous
+      bulk_g2s(sl, cdg + (int64_t)row * slot_bytes, cd_bytes + wd_bytes, &full[k]);
+    } else {
+      bulk_g2s(sl, cdg + (int64_t)row * cd_row, cd_bytes, &full[k]);
+      bulk_g2s(sl + cd_bytes, wdg + (int64_t)row * mp, wd_bytes, &full[k]);
+    }
   };
   // inverse temperature of this chain (exactly 1 without tempering, so that the
   // accept test below is unchanged bit for bit)
@@ -616,13 +627,14 @@ __device__ __forceinline__ void cplx_rows_elem(int64_t x, bool pair, const float
                                                const float2* __restrict__ wt,
                                                const int32_t* __restrict__ bi,
                                                const int32_t* __restrict__ bk, int mp, int nu,
-                                               int wpc, float4* __restrict__ qout,
-                                               float2* __restrict__ wd) {
+                                               int wpc, unsigned char* __restrict__ qout) {
   const int nblk = (nu / 2) * wpc;
   const int lane = (int)(x & 31);
   const int64_t rb = x >> 5;
   const int blk = (int)(rb % nblk), r = (int)(rb / nblk);
   const int qp = blk / wpc, h = blk % wpc;
+  unsigned char* base = qout + (int64_t)r * cplx_row_stride(nu, wpc, mp);
+  float2* wd = reinterpret_cast<float2*>(base + cplx_row_bytes(nu, wpc));
   float v[2][4];
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
@@ -639,10 +651,11 @@ __device__ __forceinline__ void cplx_rows_elem(int64_t x, bool pair, const float
         C = Ai * Ak - Bi * Bk;
         D = Bi * Ak - Ai * Bk;
         const float2 wi = wt[(int64_t)i * mp + j], wk = wt[(int64_t)k * mp + j];
-        wd[(int64_t)r * mp + j] = make_float2(wi.x - wk.x, wi.y - wk.y);
+        wd[j] = make_float2(wi.x - wk.x, wi.y - wk.y);
       } else {
         C = Ai;
         D = Bi;
+        wd[j] = wt[(int64_t)i * mp + j];
       }
     }
     const cf E = conj(C) * D;
@@ -651,7 +664,7 @@ __device__ __forceinline__ void cplx_rows_elem(int64_t x, bool pair, const float
     v[u][2] = E.x;
     v[u][3] = -E.y;
   }
-  float4* row = qout + rb * 64;
+  float4* row = reinterpret_cast<float4*>(base) + (int64_t)blk * 64;
   row[lane] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
   row[32 + lane] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
 }
@@ -659,12 +672,11 @@ __device__ __forceinline__ void cplx_rows_elem(int64_t x, bool pair, const float
 template <bool PAIR>
 __global__ void cplx_rows_kernel(const float4* __restrict__ tab, const float2* __restrict__ wt,
                                  const int32_t* __restrict__ bi, const int32_t* __restrict__ bk,
-                                 int rows, int mp, int nu, int wpc, float4* __restrict__ qout,
-                                 float2* __restrict__ wd) {
+                                 int rows, int mp, int nu, int wpc, unsigned char* __restrict__ qout) {
   const int64_t total = (int64_t)rows * (nu / 2) * wpc * 32;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
        x += (int64_t)gridDim.x * blockDim.x)
-    cplx_rows_elem(x, PAIR, tab, wt, bi, bk, mp, nu, wpc, qout, wd);
+    cplx_rows_elem(x, PAIR, tab, wt, bi, bk, mp, nu, wpc, qout);
 }
 
 // The table builds of many problems in one launch: job k owns elements
@@ -706,7 +718,7 @@ __global__ void tables_batch_kernel(const __grid_constant__ TableBatch B) {
                       J.bk, J.m, J.mp, J.m2p, (float4*)J.out);
     else
       cplx_rows_elem(e, J.kind == kTabCplxPair, (const float4*)J.tab, (const float2*)J.wt, J.bi,
-                     J.bk, J.mp, J.nu, J.wpc, (float4*)J.out, (float2*)J.wd);
+                     J.bk, J.mp, J.nu, J.wpc, (unsigned char*)J.out);
   }
 }
 
@@ -752,11 +764,11 @@ size_t metropolis_scratch_bytes(int n, int m, int cplx, int move, int nb) {
   for (int wpc = 1; wpc <= 2; ++wpc) {
     if (wpc == 2 && mp < 512) continue;
     const int nu = metro_nu(mp, 1, wpc);
-    if (nu) row = std::max(row, cplx_row_bytes(nu, wpc));
+    if (nu) row = std::max(row, cplx_row_stride(nu, wpc, mp));
   }
+  (void)f;
   const int64_t rows = move == NK_MOVE_FLIP ? n : nb;
   size_t bytes = (size_t)round_up((int64_t)(rows * row), 256);
-  if (move != NK_MOVE_FLIP) bytes += (size_t)round_up((int64_t)nb * mp * f, 256);
   // or the group kernel's rows (any of its unit-pair choices)
   size_t grow = 0;
   for (int pp = 1; pp <= 3; ++pp)
@@ -1048,7 +1060,6 @@ static nk_status plan_metropolis(const nk_rbm* r, const nk_chains* ch, int move,
   P->tab_elems = 0;
   char* sc = (char*)scratch;
   const int rows = move == NK_MOVE_FLIP ? r->n : nb;
-  const int64_t qbytes = round_up((int64_t)rows * (int64_t)cd_row, 256);
   if (!cplx) {
     if (move == NK_MOVE_FLIP) {
       A.cd = ws + L.tab;
@@ -1062,11 +1073,11 @@ static nk_status plan_metropolis(const nk_rbm* r, const nk_chains* ch, int move,
       P->tab_elems = (int64_t)nb * L.mp;
     }
   } else {
-    A.cd = sc;
-    A.wd = move == NK_MOVE_FLIP ? (const void*)(ws + L.wt) : (const void*)(sc + qbytes);
+    A.cd = sc;  // rows of cplx_row_stride bytes, increments included
+    A.wd = nullptr;
     J.kind = move == NK_MOVE_FLIP ? kTabCplxFlip : kTabCplxPair;
     J.out = sc;
-    J.wd = move == NK_MOVE_FLIP ? nullptr : (void*)(sc + qbytes);
+    J.wd = nullptr;
     P->tab_elems = (int64_t)rows * (nu / 2) * wpc * 32;
   }
   if (skip_tables) {  // tables of an earlier launch of the same call
@@ -1104,11 +1115,11 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
     else if (J.kind == kTabCplxFlip)
       cplx_rows_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(
           (const float4*)J.tab, (const float2*)J.wt, bi, bk, r->n, J.mp, J.nu, J.wpc,
-          (float4*)J.out, nullptr);
+          (unsigned char*)J.out);
     else
       cplx_rows_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(
           (const float4*)J.tab, (const float2*)J.wt, bi, bk, nb, J.mp, J.nu, J.wpc,
-          (float4*)J.out, (float2*)J.wd);
+          (unsigned char*)J.out);
     if (nk_status e = check_launch("nk_metropolis_sweep(tables)")) return e;
   }
   nk_status e;

@@ -104,15 +104,15 @@ def test_host_argument_validation(lib):
     # the W_i - W_k increments per bond
     assert lib.nk_metropolis_scratch_bytes(400, 1600, 0, 0, 800) == 0
     assert lib.nk_metropolis_scratch_bytes(400, 1600, 0, 1, 800) == 800 * 1600 * 12
-    # complex RBM: pair rows of 512 * NU * WPC bytes, sized for the larger of one
-    # warp per chain (NU = 64) and two (NU = 26), per site (flips) or bond
-    # (exchanges, plus complex increments), or the group kernel's rows of 48 bytes
-    # per unit pair, sized for its widest padding (3 pairs per thread: 288 threads,
-    # 864 pairs), whichever is larger
-    assert lib.nk_metropolis_scratch_bytes(400, 1600, 1, 0, 800) == max(400 * 512 * 64,
-                                                                        400 * 48 * 864)
+    # complex RBM: pair rows of 512 * NU * WPC bytes followed by the row's complex
+    # increments, sized for the larger of one warp per chain (NU = 64) and two
+    # (NU = 26), per site (flips) or bond (exchanges), or the group kernel's rows
+    # of 48 bytes per unit pair, sized for its widest padding (3 pairs per thread:
+    # 288 threads, 864 pairs), whichever is larger
+    assert lib.nk_metropolis_scratch_bytes(400, 1600, 1, 0, 800) == max(
+        400 * (512 * 64 + 1600 * 8), 400 * 48 * 864)
     assert lib.nk_metropolis_scratch_bytes(400, 1600, 1, 1, 800) == max(
-        800 * 512 * 64 + 800 * 1600 * 8, 800 * 48 * 864)
+        800 * (512 * 64 + 1600 * 8), 800 * 48 * 864)
     assert lib.nk_sr_step(C.byref(r), 8, 8, 8, None, 10, 3, 0.01, 0.01, 5, 0.0, 0, 256, 1 << 20,
                           8, None) == 2  # 10 samples do not split into 3 chains
     assert ch.counter == 0
