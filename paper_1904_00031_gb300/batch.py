@@ -145,8 +145,8 @@ class BatchedVmc:
     def launches_per_step(self) -> int:
         if self.fused:
             fields = len({v.w.is_complex for v in self.items})
-            tables = any(v.w.is_complex or v.w.move == "exchange" for v in self.items)
-            # sampling: tables (complex RBMs, exchange moves), one sweep launch per
+            tables = len(self.items) > 0
+            # sampling: move rows (one launch), one sweep launch per
             # kernel template, device counters (graph mode); up to 64 items per launch
             n = int(tables) + len({_metro_template(v.w) for v in self.items})
             n += 1 if self.use_graph else 0

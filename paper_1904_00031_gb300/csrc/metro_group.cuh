@@ -91,12 +91,12 @@ __global__ void group_rows_kernel(const float4* __restrict__ tab, const float2* 
 
 // The accept test of one lane (its own uniform; no shuffle), decided like
 // accept_test: a float pre-test with a 1e-5 relative margin, FP64 on near-ties.
-__device__ __forceinline__ bool accept_lane(float u32, float two_re, double u) {
+__device__ __forceinline__ bool accept_lane(float u32, float two_re, uint32_t uh, uint32_t ul) {
   if (two_re >= 0.f) return true;
   const float e32 = __expf(two_re);
   if (u32 < e32 * (1.f - 1e-5f) - 1e-37f) return true;
   if (u32 > e32 * (1.f + 1e-5f) + 1e-37f) return false;
-  return u < exp((double)two_re);
+  return uniform53(uh, ul) < exp((double)two_re);
 }
 
 // Threads of the group kernel with pp hidden-unit pairs per thread (a multiple
@@ -245,7 +245,7 @@ __device__ __forceinline__ void metropolis_group_body(const MetroArgs& A, const 
   uint32_t kphase = 0u;
   int my_i = 0, my_k = -1;  // site draws of step (32-block + lane)
   float my_da = 0.f;
-  double my_u = 0.0;        // accept draw of chain cl, step (4-block + lane % 4)
+  uint32_t my_uh = 0u, my_ul = 0u;  // accept draw of chain cl, step (4-block + lane % 4)
   float my_u32 = 0.f;
   for (int step = 0; step < total; ++step) {
     const int q32 = step & 31;
@@ -266,8 +266,9 @@ __device__ __forceinline__ void metropolis_group_body(const MetroArgs& A, const 
     if ((step & 3) == 0) {
       const uint64_t gs = ctr + (uint64_t)(step + (lane & 3));
       const u4 ua = philox_stream((uint32_t)(c0 + cl), gs, kTagAccept, A.seed);
-      my_u = uniform53(ua.x, ua.y);
-      my_u32 = (float)my_u;
+      my_uh = ua.x;
+      my_ul = ua.y;
+      my_u32 = uniform53_f(ua.x, ua.y);
     }
     const int i = __shfl_sync(FULL, my_i, q32);
     const int kk2 = __shfl_sync(FULL, my_k, q32);
@@ -359,7 +360,7 @@ __device__ __forceinline__ void metropolis_group_body(const MetroArgs& A, const 
         const float si = ((mi >> cl) & 1u) ? 1.f : -1.f;
         // visible term -2 s_i (a_i - a_k), in FP32 like the hidden-unit product
         const float two_re = 0.69314718055994531f * tot - 4.f * si * da;
-        acc = accept_lane(my_u32, beta * two_re, my_u);
+        acc = accept_lane(my_u32, beta * two_re, my_uh, my_ul);
       }
       const uint32_t bal = __ballot_sync(FULL, acc) >> (step & 3);
 #pragma unroll

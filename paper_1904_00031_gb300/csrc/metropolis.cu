@@ -42,10 +42,10 @@ struct MetroArgs {
   int8_t* samples;      // [nc * n_samples][n]
   uint64_t* n_acc;      // [nc] or null
   const double* a;      // master a (F64)
-  const void* cd;       // real: [rows][mp] T2 (cosh c, sinh c / s_i) per site (flip) or bond;
-                        // complex: [rows] pair rows of cplx_row_stride(NU, WPC, mp) bytes,
-                        // the theta increments included
-  const void* wd;       // real: [rows][mp] F : W_i (flip) or W_i - W_k (bond); complex: unused
+  const void* cd;       // [rows] rows per site (flip) or bond: real_row_stride(mp) or
+                        // cplx_row_stride(NU, WPC, mp) bytes (table block, theta
+                        // increments, header); group kernel: group_row_bytes(m2p)
+  const void* wd;       // unused
   const void* wt;       // [n][mp] F    : W transposed (initial theta)
   const void* b32;      // [mp] F
   // parallel tempering (0 / null: plain sampling): chain c is replica c % pt_R
@@ -56,18 +56,27 @@ struct MetroArgs {
   int m2p = 0;             // group kernel: unit pairs per table row (threads x pairs)
 };
 
+// The step's uniform as a float, from the bits uniform53 takes: within 2^-23
+// relative of uniform53(hi, lo) (hi >> 5 is exact below 2^24, rounded once above),
+// far inside the accept test's 1e-5 margin; FP64 is kept for near-ties.
+__device__ __forceinline__ float uniform53_f(uint32_t hi, uint32_t lo) {
+  return __fmaf_rn((float)(hi >> 5), 0x1p-27f, (float)(lo >> 6) * 0x1p-53f);
+}
+
 // Accept test U < exp(two_re), decided in FP64.  A float pre-test on
-// u32 = (float) U with a 1e-5 relative margin settles all but near-ties (the
-// per-step path then has no FP64 instruction, which is slow on this GPU); a
-// near-tie fetches the double U of the step from its lane and compares in FP64.
+// u32 ~ U with a 1e-5 relative margin settles all but near-ties (the per-step
+// path then has no FP64 instruction, which is slow on this GPU); a near-tie
+// fetches the bits of the step's U from its lane and compares in FP64.
 // Warp-uniform: every lane holds the same two_re and u32.
-__device__ __forceinline__ bool accept_test(float u32, float two_re, double my_u, int src_lane) {
+__device__ __forceinline__ bool accept_test(float u32, float two_re, uint32_t my_uh, uint32_t my_ul,
+                                            int src_lane) {
   if (two_re >= 0.f) return true;
   float e32 = __expf(two_re);
   if (u32 < e32 * (1.f - 1e-5f) - 1e-37f) return true;
   if (u32 > e32 * (1.f + 1e-5f) + 1e-37f) return false;
-  const double U = __shfl_sync(0xffffffffu, my_u, src_lane);
-  return U < exp((double)two_re);
+  const uint32_t hi = __shfl_sync(0xffffffffu, my_uh, src_lane);
+  const uint32_t lo = __shfl_sync(0xffffffffu, my_ul, src_lane);
+  return uniform53(hi, lo) < exp((double)two_re);
 }
 
 // A lane's share of log2 prod_j |r_j|^2, made finite before it is summed with
@@ -91,12 +100,13 @@ __device__ __forceinline__ int move_row(const MetroArgs& A, uint64_t ctr, uint32
 // barrier of the pair.  The columns of step t sit in ring slot t % R (R up to
 // kMaxRing, as many as shared memory holds).  The warps are not in lockstep:
 // each waits for its slot to be filled (full barrier) and releases it when done
-// (empty barrier, one arrival per warp), and the copy into a slot is issued
-// once every warp has released the slot's previous step, so chains may run up
-// to R - 1 steps apart and absorb the uneven work of accepted, rejected and
-// null proposals.  theta is kept in tensor memory (per-thread TMEM columns,
-// loaded and stored with tcgen05.ld / tcgen05.st), which leaves shared memory
-// to the ring.
+// (one count per warp in shared memory); the warp whose release completes the
+// count issues the slot's next copy (the step R on) at once, so chains may run
+// up to R - 1 steps apart and absorb the uneven work of accepted, rejected and
+// null proposals.  A row is one copy: the table block, the theta increments
+// and a 16-byte header holding a_i (- a_k) as a float.  theta is kept in tensor
+// memory (per-thread TMEM columns, loaded and stored with tcgen05.ld /
+// tcgen05.st), which leaves shared memory to the ring.
 constexpr int kMaxRing = 8;
 
 // Complex tables: a thread (half h, lane l) owns units j = 32 (h + WPC q) + l,
@@ -110,9 +120,12 @@ constexpr int kMaxRing = 8;
 __host__ __device__ constexpr size_t cplx_row_bytes(int nu, int wpc) {
   return (size_t)512 * nu * wpc;
 }
+constexpr int kRowHdr = 16;  // row header: a_i (- a_k) as a float, then padding
 __host__ __device__ constexpr size_t cplx_row_stride(int nu, int wpc, int mp) {
-  return cplx_row_bytes(nu, wpc) + (size_t)mp * 8;
+  return cplx_row_bytes(nu, wpc) + (size_t)mp * 8 + kRowHdr;
 }
+// Real rows: [mp] (cosh c, sinh c / s_i), [mp] increments, header.
+__host__ __device__ constexpr size_t real_row_stride(int mp) { return (size_t)mp * 12 + kRowHdr; }
 
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -174,6 +187,31 @@ __device__ __forceinline__ void theta_add(uint32_t tm, const typename RatioTypes
   }
 }
 
+// Complex RBMs, accepted move: for unit pairs Q0, Q0 + 1, Q0 + 2 (columns
+// 4 Q0 .. 4 Q0 + 11), load theta, run tupd(qp) for those pairs (the t update,
+// which does not read theta) while the load is in flight, then add m2s times
+// the increments and store; then the next three pairs.
+template <int Q0, int EP, int WPC, typename Fn>
+__device__ __forceinline__ void theta_t_update(uint32_t tm, const float2* wdc, float m2s, int h,
+                                               int lane, int mp, Fn&& tupd) {
+  if constexpr (Q0 < EP) {
+    constexpr int NQ = (EP - Q0) < 3 ? (EP - Q0) : 3;
+    float th[4 * NQ];
+    tmem_ld_cols<4 * NQ>(tm + 4 * Q0, th);
+#pragma unroll
+    for (int qp = Q0; qp < Q0 + NQ; ++qp) tupd(qp);
+    tmem_ld_wait();
+#pragma unroll
+    for (int e = 0; e < 4 * NQ; ++e) {
+      const int col = 4 * Q0 + e;
+      const int j = 32 * (h + WPC * (col / 2)) + lane;
+      if (j < mp) th[e] = fmaf(m2s, (col & 1) ? wdc[j].y : wdc[j].x, th[e]);
+    }
+    tmem_st_cols<4 * NQ>(tm + 4 * Q0, th);
+    theta_t_update<Q0 + NQ, EP, WPC>(tm, wdc, m2s, h, lane, mp, tupd);
+  }
+}
+
 // Read this thread's theta from TMEM in chunks of 16 columns and hand each unit
 // (index q, value) to f.
 template <bool CPLX, int TC, int C0, typename Fn>
@@ -204,8 +242,8 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
   extern __shared__ __align__(128) unsigned char smem[];
   const int mp = A.mp, n = A.n, G = A.G, R = A.ring;
   const size_t cd_row = CPLX ? cplx_row_bytes(NU, WPC) : (size_t)mp * sizeof(T2);
-  const size_t slot_bytes = cd_row + (size_t)mp * sizeof(F);
-  // ring slot k: the move's table row (cd_row bytes), then WD [mp] F
+  const size_t slot_bytes = cd_row + (size_t)mp * sizeof(F) + kRowHdr;  // one row
+  // ring slot k: the move's row: table block (cd_row bytes), increments [mp] F, header
   float* part = reinterpret_cast<float*>(smem + (size_t)R * slot_bytes);            // [2][G][WPC]
   uint64_t* full = reinterpret_cast<uint64_t*>(part + round_up(2 * G * WPC, 2));    // [kMaxRing]
   uint64_t* empty = full + kMaxRing;                                                 // [kMaxRing]
@@ -221,8 +259,6 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
   const bool active = (cw < G) && (c < A.nc);
   const uint32_t g = (uint32_t)bx;
   int8_t* sg = sgall + (size_t)(active ? w : 0) * n16;  // one copy per warp
-  const unsigned char* cdg = reinterpret_cast<const unsigned char*>(A.cd);
-  const F* wdg = reinterpret_cast<const F*>(A.wd);
   const F* wt = reinterpret_cast<const F*>(A.wt);
   const F* b32 = reinterpret_cast<const F*>(A.b32);
   auto jof = [&](int q) { return 32 * (h + WPC * q) + lane; };
@@ -230,7 +266,8 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
   if (tid == 0) {
     for (int k = 0; k < R; ++k) {
       mbar_init(&full[k], 1);
-      mbar_init(&empty[k], (uint32_t)(chains_here * WPC));
+      reinterpret_cast<int*>(empty)[k] = 0;              // releases of slot k
+      reinterpret_cast<int*>(empty)[kMaxRing + k] = 0;   // copies issued into slot k
     }
     mbar_fence_init();
   }
@@ -308,61 +345,70 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
   // inactive warps skip the steps (no CTA-wide barrier until the end)
   const int total = active ? (A.n_discard + A.n_samples) * n : 0;
   const uint32_t cd_bytes = (uint32_t)cd_row, wd_bytes = (uint32_t)(mp * sizeof(F));
-  auto issue = [&](int step) {
+  const uint32_t row_bytes = (uint32_t)slot_bytes;  // table block, increments, header
+  const unsigned char* rows = reinterpret_cast<const unsigned char*>(A.cd);
+  // per slot: releases of its current step, copies issued into it
+  int* rel = reinterpret_cast<int*>(empty);
+  int* iss = rel + kMaxRing;
+  const int nwarps = chains_here * WPC;  // every active warp releases every step's slot
+  auto issue = [&](int step, int row) {   // one thread
     const int k = step % R;
-    const int row = move_row(A, ctr, g, step);
-    unsigned char* sl = smem + (size_t)k * slot_bytes;
-    mbar_arrive_expect_tx(&full[k], cd_bytes + wd_bytes);
-    if constexpr (CPLX) {  // table block and increments of a row are contiguous
-      bulk_g2s(sl, cdg + (int64_t)row * slot_bytes, cd_bytes + wd_bytes, &full[k]);
-    } else {
-      bulk_g2s(sl, cdg + (int64_t)row * cd_row, cd_bytes, &full[k]);
-      bulk_g2s(sl + cd_bytes, wdg + (int64_t)row * mp, wd_bytes, &full[k]);
-    }
+    ++iss[k];
+    mbar_arrive_expect_tx(&full[k], row_bytes);
+    bulk_g2s(smem + (size_t)k * slot_bytes, rows + (int64_t)row * slot_bytes, row_bytes, &full[k]);
   };
   // inverse temperature of this chain (exactly 1 without tempering, so that the
   // accept test below is unchanged bit for bit)
   const float beta = A.pt_R > 0 ? 1.f - (float)(c % A.pt_R) / (float)A.pt_R : 1.f;
-  const bool producer = (tid == 0);
-  int issued = 0;  // steps whose columns have been requested (producer only)
-  if (producer) {
-    for (; issued < R && issued < total; ++issued) issue(issued);
+  if (tid == 0) {
+    // the staging writes above (generic proxy) before the copies (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int s = 0; s < R && s < total; ++s) issue(s, move_row(A, ctr, g, s));
   }
 
   uint64_t nacc = 0;
   bool timed_out = false;  // a bounded wait gave up: finish the loop without work
   int nn = 0;              // non-null steps so far (identical in the warps of a chain)
-  // per lane: the draws of step (block start + lane): proposed sites, accept
-  // uniform and a_i - a_k, fetched once per 32 steps and broadcast by shuffles
   int sweep_pos = 0, sweep_no = 0;  // step within the sweep, sweeps completed
   int kslot = 0;          // ring slot of the current step (step % R)
   uint32_t kphase = 0u;   // phase of its full barrier ((step / R) & 1)
-  int my_i = 0, my_k = -1;
-  double my_u = 0.0;          // FP64 uniform (near-ties only)
-  float my_u32 = 0.f, my_da = 0.f;
+  // per lane, drawn one 32-step block ahead: the row (site or bond) of step
+  // (block start + lane) and of the next block's step (for refills), the sites of
+  // the move (their loads land during the block before they are used), and the
+  // accept draw of step (block start + lane) as a float for the test and as bits
+  // (FP64 only on near-ties)
+  int row_cur = 0, row_nxt = 0, my_i = 0, my_k = -1, nx_i = 0, nx_k = -1;
+  uint32_t my_uh = 0u, my_ul = 0u;
+  float my_u32 = 0.f;
+  auto sites_of = [&](int row, int& si_, int& sk_) {
+    if (A.move == NK_MOVE_FLIP) {
+      si_ = row;
+      sk_ = -1;
+    } else {
+      si_ = A.bond_i[row];
+      sk_ = A.bond_k[row];
+    }
+  };
   for (int step = 0; step < total; ++step) {
     const int q32 = step & 31;
     if (q32 == 0) {
-      const uint64_t gs = ctr + (uint64_t)(step + lane);
-      u4 us = philox_stream(g, gs, kTagSite, A.seed);
-      const int idx = uniform_index(us.x, A.move == NK_MOVE_FLIP ? n : A.nb);
-      u4 ua = philox_stream((uint32_t)c, gs, kTagAccept, A.seed);
-      my_u = uniform53(ua.x, ua.y);
-      my_u32 = (float)my_u;
-      if (A.move == NK_MOVE_FLIP) {
-        my_i = idx;
-        my_k = -1;
-        my_da = (float)(CPLX ? A.a[2 * idx] : A.a[idx]);
-      } else {
-        my_i = A.bond_i[idx];
-        my_k = A.bond_k[idx];
-        my_da = (float)(CPLX ? A.a[2 * my_i] - A.a[2 * my_k] : A.a[my_i] - A.a[my_k]);
+      if (step == 0) {
+        row_nxt = move_row(A, ctr, g, lane);
+        sites_of(row_nxt, nx_i, nx_k);
       }
+      row_cur = row_nxt;
+      my_i = nx_i;
+      my_k = nx_k;
+      row_nxt = move_row(A, ctr, g, step + 32 + lane);
+      sites_of(row_nxt, nx_i, nx_k);
+      const u4 ua = philox_stream((uint32_t)c, ctr + (uint64_t)(step + lane), kTagAccept, A.seed);
+      my_uh = ua.x;
+      my_ul = ua.y;
+      my_u32 = uniform53_f(ua.x, ua.y);
     }
     const int i = __shfl_sync(0xffffffffu, my_i, q32);
     const int kk2 = __shfl_sync(0xffffffffu, my_k, q32);
     const float u32 = __shfl_sync(0xffffffffu, my_u32, q32);
-    const float da = __shfl_sync(0xffffffffu, my_da, q32);
     const int k = kslot;
     const T2* cd = reinterpret_cast<const T2*>(smem + (size_t)k * slot_bytes);
     const F* wdc = reinterpret_cast<const F*>(smem + (size_t)k * slot_bytes + cd_bytes);
@@ -436,20 +482,24 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
       }
       ++nn;
       // visible term -2 s_i a_i (- 2 s_k a_k) = -2 s_i (a_i - a_k) (s_k = -s_i),
-      // in FP32 like the hidden-unit product
+      // in FP32 like the hidden-unit product; a_i (- a_k) from the row's header
+      const float da = *reinterpret_cast<const float*>(smem + (size_t)k * slot_bytes + cd_bytes +
+                                                       wd_bytes);
       const float two_re = (CPLX ? 1.f : 2.f) * 0.69314718055994531f * l2 - 4.f * si * da;
-      if (!timed_out && accept_test(u32, beta * two_re, my_u, q32)) {
+      if (!timed_out && accept_test(u32, beta * two_re, my_uh, my_ul, q32)) {
         ++nacc;
         if constexpr (CPLX) {
+          // theta's columns of three unit pairs at a time are read before those
+          // pairs' t is updated, so that the tensor-memory loads complete under
+          // the tanh-addition arithmetic
           const float4* row4 = reinterpret_cast<const float4*>(smem + (size_t)k * slot_bytes);
-#pragma unroll
-          for (int qp = 0; qp < EP; ++qp) {
+          tmem_st_wait();  // the previous update's stores
+          theta_t_update<0, EP, WPC>(tmem_th, wdc, -2.f * si, h, lane, mp, [&](int qp) {
             const float4 q0 = row4[(qp * WPC + h) * 64 + lane];
             const float4 q1 = row4[(qp * WPC + h) * 64 + 32 + lane];
             t_add_pair(tx[qp], ty[qp], make_float2(q0.x, q0.y), make_float2(q0.z, q0.w),
                        make_float2(q1.x, q1.y), make_float2(q1.z, q1.w), si);
-          }
-          theta_add<true, WPC, TC, 0>(tmem_th, wdc, -2.f * si, h, lane, mp);
+          });
         } else {
 #pragma unroll
           for (int q = 0; q < E; ++q) {
@@ -469,26 +519,27 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
         }
       }
     }
+    // release slot k; the last warp to release it refills it with the step R on
+    // (its row drawn by this warp's lanes), so that no copy waits for a
+    // particular warp to come round
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[k]);  // this warp is done with slot k
-    if (producer && !timed_out) {
-      // refill slots whose previous step every warp has released; block only
-      // when this warp's own next step would otherwise have no data
-      while (issued < total && issued <= step + R) {
-        const int prev = issued - R;  // last step that used the slot
-        const uint32_t par = (uint32_t)((prev / R) & 1);
-        if (!mbar_try_wait(&empty[prev % R], par)) {
-          if (issued > step + 1) break;
-          if (!mbar_wait_bounded(&empty[prev % R], par)) {
-            timed_out = true;
-            break;
-          }
-        }
-        issue(issued);
-        ++issued;
+    bool last = false;
+    if (lane == 0) {
+      __threadfence_block();  // this warp's reads of the slot before the release
+      last = atomicAdd(&rel[k], 1) == nwarps - 1;
+      if (last) atomicExch(&rel[k], 0);
+    }
+    last = __shfl_sync(0xffffffffu, (int)last, 0) != 0;
+    if (last && !timed_out && step + R < total) {
+      const int tq = q32 + R;  // the refill's offset from this block's start (< 64)
+      const int rc = __shfl_sync(0xffffffffu, row_cur, tq & 31);
+      const int rn = __shfl_sync(0xffffffffu, row_nxt, tq & 31);
+      if (lane == 0) {
+        __threadfence_block();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(step + R, tq < 32 ? rc : rn);
       }
     }
-    if (w == 0) timed_out = __shfl_sync(0xffffffffu, (int)timed_out, 0) != 0;
     if (++sweep_pos == n) {  // the last step of a sweep
       sweep_pos = 0;
       const int sweep = sweep_no++;
@@ -543,10 +594,6 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
     }
   }
   if (timed_out && lane == 0) dev_status_set(1u << NK_ERR_TIMEOUT);
-  if (timed_out && producer) {
-    // let copies still in flight land before the CTA exits
-    for (int k = 0; k < R; ++k) mbar_wait_bounded(&full[k], 0, 1u << 20);
-  }
   if (active && h == 0) {
     for (int ii = lane; ii < n; ii += 32) A.sigma[(int64_t)c * n + ii] = sg[ii];
     if (A.n_acc && lane == 0) {
@@ -559,6 +606,13 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
   }
   tc_fence_before();
   __syncthreads();
+  if (tid == 0) {
+    // copies still in flight (a timed-out run) land before the CTA exits: the
+    // last copy issued into each slot
+    const int* iss = reinterpret_cast<const int*>(empty) + kMaxRing;
+    for (int k = 0; k < R; ++k)
+      if (iss[k] > 0) mbar_wait_bounded(&full[k], (uint32_t)((iss[k] - 1) & 1), 1u << 20);
+  }
   if (w == 0) {
     tc_fence_after();
     tmem_dealloc(*tslot, tcols);
@@ -593,40 +647,44 @@ __global__ void __launch_bounds__(512, 1) metropolis_batch_kernel(const __grid_c
 
 namespace nk {
 
-// Per-bond tables of an exchange move of a real RBM (s_k = -s_i):
-// cosh c = A_i A_k - B_i B_k, sinh c / s_i = B_i A_k - A_i B_k, increment W_i - W_k.
-// Element x of nb * mp.
-__device__ __forceinline__ void pair_table_real_elem(int64_t x, const float2* __restrict__ tab,
-                                                     const float* __restrict__ wt,
-                                                     const int32_t* __restrict__ bi,
-                                                     const int32_t* __restrict__ bk, int mp,
-                                                     float2* __restrict__ cd,
-                                                     float* __restrict__ wd) {
-  const int b = (int)(x / mp), j = (int)(x % mp);
-  const int i = bi[b], k = bk[b];
-  const float2 ti = tab[(int64_t)i * mp + j], tk = tab[(int64_t)k * mp + j];
-  cd[x] = make_float2(fmaf(-ti.y, tk.y, ti.x * tk.x), fmaf(-ti.x, tk.y, ti.y * tk.x));
-  wd[x] = wt[(int64_t)i * mp + j] - wt[(int64_t)k * mp + j];
+// Rows of a real RBM (layout of real_row_stride), one per site (flips: the
+// site's (cosh 2W_i, sinh 2W_i) and W_i) or bond (exchanges, s_k = -s_i:
+// cosh c = A_i A_k - B_i B_k, sinh c / s_i = B_i A_k - A_i B_k, increment
+// W_i - W_k), each with its header a_i (- a_k).  Element x of rows * mp.
+__device__ __forceinline__ void real_rows_elem(int64_t x, bool pair, const float2* __restrict__ tab,
+                                               const float* __restrict__ wt,
+                                               const int32_t* __restrict__ bi,
+                                               const int32_t* __restrict__ bk,
+                                               const double* __restrict__ a, int mp,
+                                               unsigned char* __restrict__ out) {
+  const int r = (int)(x / mp), j = (int)(x % mp);
+  unsigned char* base = out + (int64_t)r * real_row_stride(mp);
+  float2* cd = reinterpret_cast<float2*>(base);
+  float* wd = reinterpret_cast<float*>(base + (size_t)mp * 8);
+  const int i = pair ? bi[r] : r;
+  const float2 ti = tab[(int64_t)i * mp + j];
+  if (pair) {
+    const int k = bk[r];
+    const float2 tk = tab[(int64_t)k * mp + j];
+    cd[j] = make_float2(fmaf(-ti.y, tk.y, ti.x * tk.x), fmaf(-ti.x, tk.y, ti.y * tk.x));
+    wd[j] = wt[(int64_t)i * mp + j] - wt[(int64_t)k * mp + j];
+    if (j == 0) *reinterpret_cast<float*>(base + (size_t)mp * 12) = (float)(a[i] - a[k]);
+  } else {
+    cd[j] = ti;
+    wd[j] = wt[(int64_t)i * mp + j];
+    if (j == 0) *reinterpret_cast<float*>(base + (size_t)mp * 12) = (float)a[i];
+  }
 }
 
-__global__ void pair_tables_real_kernel(const float2* __restrict__ tab, const float* __restrict__ wt,
-                                        const int32_t* __restrict__ bi,
-                                        const int32_t* __restrict__ bk, int nb, int mp,
-                                        float2* __restrict__ cd, float* __restrict__ wd) {
-  const int64_t total = (int64_t)nb * mp;
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
-       x += (int64_t)gridDim.x * blockDim.x)
-    pair_table_real_elem(x, tab, wt, bi, bk, mp, cd, wd);
-}
-
-// Pair rows of a complex RBM (layout of cplx_row_bytes): one per site (flips,
-// C = A_i, D = B_i) or per bond (exchanges, s_k = -s_i: C = A_i A_k - B_i B_k,
-// D = B_i A_k - A_i B_k, and the increments W_i - W_k into wd).  Element x of
-// rows * (nu / 2) * wpc * 32.
+// Pair rows of a complex RBM (layout of cplx_row_stride): one per site (flips,
+// C = A_i, D = B_i, increments W_i) or per bond (exchanges, s_k = -s_i:
+// C = A_i A_k - B_i B_k, D = B_i A_k - A_i B_k, increments W_i - W_k), each with
+// its header Re a_i (- Re a_k).  Element x of rows * (nu / 2) * wpc * 32.
 __device__ __forceinline__ void cplx_rows_elem(int64_t x, bool pair, const float4* __restrict__ tab,
                                                const float2* __restrict__ wt,
                                                const int32_t* __restrict__ bi,
-                                               const int32_t* __restrict__ bk, int mp, int nu,
+                                               const int32_t* __restrict__ bk,
+                                               const double* __restrict__ a, int mp, int nu,
                                                int wpc, unsigned char* __restrict__ qout) {
   const int nblk = (nu / 2) * wpc;
   const int lane = (int)(x & 31);
@@ -635,6 +693,9 @@ __device__ __forceinline__ void cplx_rows_elem(int64_t x, bool pair, const float
   const int qp = blk / wpc, h = blk % wpc;
   unsigned char* base = qout + (int64_t)r * cplx_row_stride(nu, wpc, mp);
   float2* wd = reinterpret_cast<float2*>(base + cplx_row_bytes(nu, wpc));
+  if (blk == 0 && lane == 0)
+    *reinterpret_cast<float*>(base + cplx_row_bytes(nu, wpc) + (size_t)mp * 8) =
+        pair ? (float)(a[2 * bi[r]] - a[2 * bk[r]]) : (float)a[2 * r];
   float v[2][4];
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
@@ -669,20 +730,11 @@ __device__ __forceinline__ void cplx_rows_elem(int64_t x, bool pair, const float
   row[32 + lane] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
 }
 
-template <bool PAIR>
-__global__ void cplx_rows_kernel(const float4* __restrict__ tab, const float2* __restrict__ wt,
-                                 const int32_t* __restrict__ bi, const int32_t* __restrict__ bk,
-                                 int rows, int mp, int nu, int wpc, unsigned char* __restrict__ qout) {
-  const int64_t total = (int64_t)rows * (nu / 2) * wpc * 32;
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
-       x += (int64_t)gridDim.x * blockDim.x)
-    cplx_rows_elem(x, PAIR, tab, wt, bi, bk, mp, nu, wpc, qout);
-}
 
 // The table builds of many problems in one launch: job k owns elements
 // [start[k], start[k + 1]) of the concatenated index range.
 enum { kTabNone = 0, kTabRealPair = 1, kTabCplxFlip = 2, kTabCplxPair = 3, kTabGroupFlip = 4,
-       kTabGroupPair = 5 };
+       kTabGroupPair = 5, kTabRealFlip = 6 };
 struct TableJob {
   int kind, mp, nu, wpc;
   const void* tab;
@@ -692,6 +744,7 @@ struct TableJob {
   void* out;
   void* wd;
   int m = 0, m2p = 0;  // group rows
+  const double* a = nullptr;  // master visible biases (row headers)
 };
 struct TableBatch {
   int n;
@@ -710,15 +763,15 @@ __global__ void tables_batch_kernel(const __grid_constant__ TableBatch B) {
     }
     const TableJob& J = B.j[lo];
     const int64_t e = x - B.start[lo];
-    if (J.kind == kTabRealPair)
-      pair_table_real_elem(e, (const float2*)J.tab, (const float*)J.wt, J.bi, J.bk, J.mp,
-                           (float2*)J.out, (float*)J.wd);
+    if (J.kind == kTabRealPair || J.kind == kTabRealFlip)
+      real_rows_elem(e, J.kind == kTabRealPair, (const float2*)J.tab, (const float*)J.wt, J.bi,
+                     J.bk, J.a, J.mp, (unsigned char*)J.out);
     else if (J.kind == kTabGroupFlip || J.kind == kTabGroupPair)
       group_rows_elem(e, J.kind == kTabGroupPair, (const float4*)J.tab, (const float2*)J.wt, J.bi,
                       J.bk, J.m, J.mp, J.m2p, (float4*)J.out);
     else
       cplx_rows_elem(e, J.kind == kTabCplxPair, (const float4*)J.tab, (const float2*)J.wt, J.bi,
-                     J.bk, J.mp, J.nu, J.wpc, (unsigned char*)J.out);
+                     J.bk, J.a, J.mp, J.nu, J.wpc, (unsigned char*)J.out);
   }
 }
 
@@ -756,8 +809,9 @@ size_t metropolis_scratch_bytes(int n, int m, int cplx, int move, int nb) {
   const int mp = padded_m(m);
   const size_t f = cplx ? 8 : 4;
   if (!cplx) {
-    if (move == NK_MOVE_FLIP) return 0;
-    return (size_t)round_up((int64_t)nb * mp * 2 * f, 256) + (size_t)round_up((int64_t)nb * mp * f, 256);
+    (void)f;
+    const int64_t rows = move == NK_MOVE_FLIP ? n : nb;
+    return (size_t)round_up(rows * (int64_t)real_row_stride(mp), 256);
   }
   // the row layout depends on the warps per chain (group size): take the larger
   size_t row = 0;
@@ -1036,7 +1090,7 @@ static nk_status plan_metropolis(const nk_rbm* r, const nk_chains* ch, int move,
                 need);
   // ring depth: as many slots as fit next to the pair partials, barriers and
   // the per-warp sigma copies (theta lives in tensor memory)
-  const size_t slot = cd_row + (size_t)L.mp * f;
+  const size_t slot = cd_row + (size_t)L.mp * f + kRowHdr;
   const size_t rest = (size_t)round_up(2 * A.G * wpc, 2) * 4 + 2 * kMaxRing * 8 + 16 +
                       (size_t)A.G * wpc * round_up(r->n, 16);
   const size_t cap = 227 * 1024;
@@ -1056,28 +1110,18 @@ static nk_status plan_metropolis(const nk_rbm* r, const nk_chains* ch, int move,
   P->ctr_dev = ch->counter_dev;
   P->advance = (uint64_t)(n_discard + n_samples) * r->n;
   TableJob& J = P->tj;
-  J = TableJob{kTabNone, L.mp, nu, wpc, ws + L.tab, ws + L.wt, bi, bk, nullptr, nullptr};
-  P->tab_elems = 0;
-  char* sc = (char*)scratch;
+  J = TableJob{kTabNone, L.mp, nu, wpc, ws + L.tab, ws + L.wt, bi, bk, scratch, nullptr};
+  J.a = r->a;
   const int rows = move == NK_MOVE_FLIP ? r->n : nb;
+  // rows of real_row_stride / cplx_row_stride bytes in the scratch: table block,
+  // increments, header
+  A.cd = scratch;
+  A.wd = nullptr;
   if (!cplx) {
-    if (move == NK_MOVE_FLIP) {
-      A.cd = ws + L.tab;
-      A.wd = ws + L.wt;
-    } else {
-      A.cd = sc;
-      A.wd = sc + round_up((int64_t)nb * L.mp * 2 * f, 256);
-      J.kind = kTabRealPair;
-      J.out = sc;
-      J.wd = (void*)A.wd;
-      P->tab_elems = (int64_t)nb * L.mp;
-    }
+    J.kind = move == NK_MOVE_FLIP ? kTabRealFlip : kTabRealPair;
+    P->tab_elems = (int64_t)rows * L.mp;
   } else {
-    A.cd = sc;  // rows of cplx_row_stride bytes, increments included
-    A.wd = nullptr;
     J.kind = move == NK_MOVE_FLIP ? kTabCplxFlip : kTabCplxPair;
-    J.out = sc;
-    J.wd = nullptr;
     P->tab_elems = (int64_t)rows * (nu / 2) * wpc * 32;
   }
   if (skip_tables) {  // tables of an earlier launch of the same call
@@ -1096,30 +1140,15 @@ nk_status launch_metropolis(const nk_rbm* r, nk_chains* ch, int move, const int3
                                     n_acc, scratch, scratch_bytes, pt, &P))
     return e;
   if (dry) return NK_OK;  // every check passed; nothing is enqueued
-  const TableJob& J = P.tj;
-  if (J.kind != kTabNone && P.tab_elems > 0) {
+  if (P.tj.kind != kTabNone && P.tab_elems > 0) {
+    TableBatch TB;
+    TB.n = 1;
+    TB.start[0] = 0;
+    TB.start[1] = P.tab_elems;
+    TB.j[0] = P.tj;
     const int64_t blocks =
         std::max<int64_t>(1, std::min<int64_t>((P.tab_elems + 255) / 256, 152 * 16));
-    if (J.kind == kTabRealPair)
-      pair_tables_real_kernel<<<(unsigned)blocks, 256, 0, st>>>(
-          (const float2*)J.tab, (const float*)J.wt, bi, bk, nb, J.mp, (float2*)J.out,
-          (float*)J.wd);
-    else if (J.kind == kTabGroupFlip)
-      group_rows_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(
-          (const float4*)J.tab, (const float2*)J.wt, bi, bk, r->n, J.m, J.mp, J.m2p,
-          (float4*)J.out);
-    else if (J.kind == kTabGroupPair)
-      group_rows_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(
-          (const float4*)J.tab, (const float2*)J.wt, bi, bk, nb, J.m, J.mp, J.m2p,
-          (float4*)J.out);
-    else if (J.kind == kTabCplxFlip)
-      cplx_rows_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(
-          (const float4*)J.tab, (const float2*)J.wt, bi, bk, r->n, J.mp, J.nu, J.wpc,
-          (unsigned char*)J.out);
-    else
-      cplx_rows_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(
-          (const float4*)J.tab, (const float2*)J.wt, bi, bk, nb, J.mp, J.nu, J.wpc,
-          (unsigned char*)J.out);
+    tables_batch_kernel<<<(unsigned)blocks, 256, 0, st>>>(TB);
     if (nk_status e = check_launch("nk_metropolis_sweep(tables)")) return e;
   }
   nk_status e;

@@ -194,9 +194,9 @@ class VmcSr:
 
     # kernel launches per step (for reporting)
     def launches_per_step(self) -> int:
-        # move tables (exchanges; flips of complex RBMs), sweep; with tempering
-        # a sweep launch and an exchange launch per sweep (the tables once)
-        n = 1 + (1 if self.move == nk.NK_MOVE_EXCHANGE or self.w.is_complex else 0)
+        # move rows, sweep; with tempering a sweep launch and an exchange launch
+        # per sweep (the rows once)
+        n = 2
         sweeps = self.w.n_discard + self.w.samples_per_chain
         if self.replicas > 1:
             n += 2 * sweeps - 1

@@ -100,19 +100,19 @@ def test_host_argument_validation(lib):
     ch = nk._Chains(4, 4, 8, 1, 0)
     assert lib.nk_metropolis_sweep(C.byref(r), C.byref(ch), 1, None, None, 0, 1, 1, 8, None,
                                    None, 0, None) == 1
-    # real RBM: flips read the workspace tables; exchanges need (C, D) float2 and
-    # the W_i - W_k increments per bond
-    assert lib.nk_metropolis_scratch_bytes(400, 1600, 0, 0, 800) == 0
-    assert lib.nk_metropolis_scratch_bytes(400, 1600, 0, 1, 800) == 800 * 1600 * 12
+    # real RBM: one row per site (flips) or bond (exchanges): (C, D) float2 and
+    # the increment float per unit, then a 16-byte header (a_i - a_k)
+    assert lib.nk_metropolis_scratch_bytes(400, 1600, 0, 0, 800) == 400 * (1600 * 12 + 16)
+    assert lib.nk_metropolis_scratch_bytes(400, 1600, 0, 1, 800) == 800 * (1600 * 12 + 16)
     # complex RBM: pair rows of 512 * NU * WPC bytes followed by the row's complex
-    # increments, sized for the larger of one warp per chain (NU = 64) and two
-    # (NU = 26), per site (flips) or bond (exchanges), or the group kernel's rows
-    # of 48 bytes per unit pair, sized for its widest padding (3 pairs per thread:
-    # 288 threads, 864 pairs), whichever is larger
+    # increments and header, sized for the larger of one warp per chain (NU = 64)
+    # and two (NU = 26), per site (flips) or bond (exchanges), or the group
+    # kernel's rows of 48 bytes per unit pair, sized for its widest padding (3
+    # pairs per thread: 288 threads, 864 pairs), whichever is larger
     assert lib.nk_metropolis_scratch_bytes(400, 1600, 1, 0, 800) == max(
-        400 * (512 * 64 + 1600 * 8), 400 * 48 * 864)
+        400 * (512 * 64 + 1600 * 8 + 16), 400 * 48 * 864)
     assert lib.nk_metropolis_scratch_bytes(400, 1600, 1, 1, 800) == max(
-        800 * (512 * 64 + 1600 * 8), 800 * 48 * 864)
+        800 * (512 * 64 + 1600 * 8 + 16), 800 * 48 * 864)
     assert lib.nk_sr_step(C.byref(r), 8, 8, 8, None, 10, 3, 0.01, 0.01, 5, 0.0, 0, 256, 1 << 20,
                           8, None) == 2  # 10 samples do not split into 3 chains
     assert ch.counter == 0
