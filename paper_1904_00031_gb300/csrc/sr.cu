@@ -52,7 +52,7 @@ static bool adj_centres(int m, int cplx) {
 }
 // Elements per thread whose loads are issued together in the vector kernels
 // (a thread's elements are still visited, and summed, in grid-stride order).
-constexpr int kVecUnroll = 4;
+constexpr int kVecUnroll = 2;
 constexpr int kAdjBK = 16;
 
 // scalars in the scratch `scal` block
