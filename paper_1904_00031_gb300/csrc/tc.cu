@@ -280,6 +280,8 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
   uint64_t* tempty = tfull + 2;
   uint64_t* afull = tempty + 2;
   uint32_t* slot = reinterpret_cast<uint32_t*>(afull + 1);
+  // after the barriers (128 bytes): the epilogue warps' staging tiles, 4 KB each
+  float4* epi_stage = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(full) + 128);
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int64_t s0 = (int64_t)bx * 128;
 
@@ -389,6 +391,58 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
     // 16-byte loads when every row of T starts 16-B aligned (m even for complex,
     // m a multiple of 4 for real); the tile's tail and j = m are handled per element
     const bool vec = CPLX ? (A.m % 2 == 0) : (A.m % 4 == 0);
+    // ln psi / theta mode with 16-B aligned rows: each 16-unit chunk of theta (and
+    // tanh theta) goes through the warp's staging tile (32 rows, 16-B chunks
+    // XOR-swizzled by row, so that neither side has bank conflicts) and out as
+    // whole row segments: 4 rows of 128 B (complex) or 8 rows of 64 B (real) per
+    // store instruction instead of one 8- or 4-byte value in each of 32 rows
+    float4* stg = (A.mode == 1 && vec) ? epi_stage + q * 256 : nullptr;
+    auto stage_store_c = [&](float4* sb, const float (&xr)[16], const float (&xi)[16], float2* dst,
+                             int jc) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        sb[lane * 8 + (k ^ (lane & 7))] =
+            make_float4(xr[2 * k], xi[2 * k], xr[2 * k + 1], xi[2 * k + 1]);
+      __syncwarp();
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int f = it * 32 + lane, r = f >> 3, k = f & 7;
+        const float4 v = sb[r * 8 + (k ^ (r & 7))];
+        const int64_t sr = s0 + 32 * q + r;
+        const int j = jc + 2 * k;
+        if (sr < A.ns && j < A.m) {
+          float2* d = dst + sr * A.m + j;
+          if (j + 1 < A.m) *reinterpret_cast<float4*>(d) = v;
+          else *d = make_float2(v.x, v.y);
+        }
+      }
+      __syncwarp();
+    };
+    auto stage_store_r = [&](float4* sb, const float (&x)[16], float* dst, int jc) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        sb[lane * 4 + (k ^ ((lane >> 1) & 3))] =
+            make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
+      __syncwarp();
+#pragma unroll
+      for (int it = 0; it < 4; ++it) {
+        const int f = it * 32 + lane, r = f >> 2, k = f & 3;
+        const float4 v = sb[r * 4 + (k ^ ((r >> 1) & 3))];
+        const int64_t sr = s0 + 32 * q + r;
+        const int j = jc + 4 * k;
+        if (sr < A.ns && j < A.m) {
+          float* d = dst + sr * A.m + j;
+          if (j + 3 < A.m) {
+            *reinterpret_cast<float4*>(d) = v;
+          } else {
+            d[0] = v.x;
+            if (j + 1 < A.m) d[1] = v.y;
+            if (j + 2 < A.m) d[2] = v.z;
+          }
+        }
+      }
+      __syncwarp();
+    };
     auto load_t = [&](int jt) {
       const int j0 = jt * HJ;
       if (vec && live && j0 + HJ <= A.m) {
@@ -488,20 +542,39 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
               pr += t.x * ur[e] - t.y * ui[e];
               pi += t.x * ui[e] + t.y * ur[e];
             }
-          } else if (live) {
+          } else {
+            if (A.logpsi && live) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int j = j0 + c * 16 + e;
-              if (j < A.m) {
-                if (A.logpsi) {
+              for (int e = 0; e < 16; ++e) {
+                if (j0 + c * 16 + e < A.m) {
                   cf l = lncosh_c(cf{ur[e], ui[e]});
                   pr += l.x;
                   pi += l.y;
                 }
-                if (th) th[s * A.m + j] = make_float2(ur[e], ui[e]);
-                if (tt) {
-                  cf t = tanh_c(cf{ur[e], ui[e]});
-                  tt[s * A.m + j] = make_float2(t.x, t.y);
+              }
+            }
+            if (stg) {  // aligned rows: through the warp's staging tile
+              if (th) stage_store_c(stg, ur, ui, th, j0 + c * 16);
+              if (tt) {
+                float vr[16], vi[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                  const cf t = tanh_c(cf{ur[e], ui[e]});
+                  vr[e] = t.x;
+                  vi[e] = t.y;
+                }
+                stage_store_c(stg, vr, vi, tt, j0 + c * 16);
+              }
+            } else if (live) {
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                const int j = j0 + c * 16 + e;
+                if (j < A.m) {
+                  if (th) th[s * A.m + j] = make_float2(ur[e], ui[e]);
+                  if (tt) {
+                    cf t = tanh_c(cf{ur[e], ui[e]});
+                    tt[s * A.m + j] = make_float2(t.x, t.y);
+                  }
                 }
               }
             }
@@ -520,14 +593,28 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
           if (A.mode == 0) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) pr += (PREFETCH ? tp[c * 16 + e] : tc[e]) * u[e];
-          } else if (live) {
+          } else {
+            if (A.logpsi && live) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int j = j0 + c * 16 + e;
-              if (j < A.m) {
-                if (A.logpsi) pr += lncosh_f(u[e]);
-                if (th) th[s * A.m + j] = u[e];
-                if (tt) tt[s * A.m + j] = tanh_f(u[e]);
+              for (int e = 0; e < 16; ++e)
+                if (j0 + c * 16 + e < A.m) pr += lncosh_f(u[e]);
+            }
+            if (stg) {  // aligned rows: through the warp's staging tile
+              if (th) stage_store_r(stg, u, th, j0 + c * 16);
+              if (tt) {
+                float v[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) v[e] = tanh_f(u[e]);
+                stage_store_r(stg, v, tt, j0 + c * 16);
+              }
+            } else if (live) {
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                const int j = j0 + c * 16 + e;
+                if (j < A.m) {
+                  if (th) th[s * A.m + j] = u[e];
+                  if (tt) tt[s * A.m + j] = tanh_f(u[e]);
+                }
               }
             }
           }
@@ -622,7 +709,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 }
 
 static size_t fwd_smem_bytes(int na64, int stages = kFwdStages) {
-  return 1024 + (size_t)(na64 / 64) * 16384 + (size_t)stages * kStageB + 128;
+  // alignment slack, sigma' tile, stages, barriers, 4 epilogue staging tiles
+  return 1024 + (size_t)(na64 / 64) * 16384 + (size_t)stages * kStageB + 128 + 4 * 4096;
 }
 
 // One CTA per SM: when the last wave would be far from full, split the hidden
