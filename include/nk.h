@@ -188,9 +188,10 @@ nk_status nk_rbm_logpsi(const nk_rbm* rbm, const int8_t* sigma, int64_t ns, int3
 
 /* ---------------------------------------------------------------- sampling */
 
-/* Scratch bytes nk_metropolis_sweep needs: per-bond tables of exchange moves;
- * for complex RBMs also per-site tables of flips.  0 for flips of a real RBM
- * (NULL scratch is then fine). */
+/* Scratch bytes nk_metropolis_sweep needs: one move row per site (flips) or
+ * bond (exchanges), built at the start of every call: the move's table block,
+ * its theta increments and a 16-byte header (a_i - a_k), sized for the larger
+ * of the two sampler kernels' row layouts (nk_rbm.sampler).  Never 0. */
 size_t nk_metropolis_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int32_t move,
                                    int32_t n_bonds);
 
@@ -207,16 +208,16 @@ size_t nk_metropolis_scratch_bytes(int32_t n, int32_t m, int32_t is_complex, int
  * (relative) of a tie; decisions agree with an FP64 evaluation except where
  * |ln U - 2 Re(ln psi' - ln psi)| is below the FP32 error of the log-ratio (none
  * of the decisions with a margin of 1e-4 or more differed in the parity tests,
- * up to m = 1600).
+ * up to m = 1600).  For complex RBMs a factor |r_j|^2 that rounds to zero or
+ * below in FP32 makes the move's ratio zero (rejected).
  *   bond_i, bond_k  int32 [n_bonds] exchange bonds (ignored for FLIP; may be NULL)
  *   samples_out     int8 [nc * n_samples_per_chain][n], chain-major
  *                   (row c * n_samples_per_chain + s)
  *   n_accept_out    uint64 [nc] accepted proposals per chain in this call, or NULL.
  *                   UINT64_MAX marks a chain whose CTA gave up waiting for a
- *                   table copy (bounded wait; the call's results are then invalid)
+ *                   row copy (bounded wait; the call's results are then invalid)
  *   scratch         nk_metropolis_scratch_bytes(...) bytes, 256-B aligned
- *                   (move tables built at the start of the call); may be NULL
- *                   when that size is 0
+ *                   (move rows built at the start of the call); required
  * chains->sigma is updated in place and chains->counter advanced by
  * (n_discard + n_samples_per_chain) * n on success. */
 nk_status nk_metropolis_sweep(const nk_rbm* rbm, nk_chains* chains, int32_t move,
