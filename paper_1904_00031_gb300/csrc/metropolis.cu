@@ -4,15 +4,18 @@
 // One or two warps run one chain; a CTA runs one proposal group, whose chains
 // all propose the same site (bond) at a step.  Per proposal the ratio needs, for
 // every hidden unit j, the table column (cosh c_j, sinh c_j / s_i) of the move
-// and, on acceptance, its theta increment W_i (- W_k).  One thread streams each
-// step's columns into shared memory with 1-D TMA bulk copies through a ring
-// of slots, so the warps read every table value from shared memory once per
-// chain.
+// and, on acceptance, its theta increment W_i (- W_k).  Each step's row (table
+// block, increments and a header with a_i - a_k, built per call) reaches shared
+// memory by one 1-D TMA bulk copy into a ring of slots, issued by the warp that
+// releases the slot last, so the warps read every table value from shared
+// memory once per chain.  (metro_group.cuh holds the other form: one CTA per
+// group with the hidden units split over its threads.)
 //
 // Per chain: sigma lives in shared memory, theta in tensor memory (per-thread
 // TMEM columns), t = tanh(theta) in registers.  With C = cosh c and
-// D = sinh c / s_i, the factor of hidden unit j is r_j = C_j - s_i t_j D_j.  Real RBMs read (C, D) and multiply r_j.  Complex RBMs
-// need only |r_j|^2 for the accept test and read, per unit, the expanded form
+// D = sinh c / s_i, the factor of hidden unit j is r_j = C_j - s_i t_j D_j.  Real
+// RBMs read (C, D) and multiply r_j.  Complex RBMs need only |r_j|^2 for the
+// accept test and read, per unit, the expanded form
 //   |r|^2 = |C|^2 + |t|^2 |D|^2 - 2 s_i Re(t conj(C) D),
 // from per-call tables (|C|^2, |D|^2, conj(C) D) laid out so that one 16-byte
 // load gives a thread two of its units, evaluated with packed FP32 pair
@@ -20,8 +23,8 @@
 // t by the tanh addition formula t' = (t C - s_i D) / r, for complex RBMs from
 // the same tables: t' = (t |C|^2 + conj(t) |D|^2 - s_i (|t|^2 conj(E) + E)) / |r|^2
 // with E = conj(C) D.  t is recomputed exactly from theta after every sweep.
-// Philox draws are made 32 steps at a time, one step per lane, and broadcast by
-// shuffles.
+// Philox draws are made 32 steps at a time, one step per lane (the rows and
+// sites of the next block ahead of use), and broadcast by shuffles.
 #include "common.cuh"
 #include "internal.h"
 #include "ratio.cuh"
