@@ -159,14 +159,14 @@ __device__ __forceinline__ void pair_sync(int id, int nthreads) {
 
 constexpr int kThetaChunk = 13;  // TMEM columns per load / wait / store round trip
 
-// theta += m2s * increment for this thread's units, in chunks of kThetaChunk TMEM
-// columns (complex: column 2 q + 0/1 = Re/Im theta of unit q; real: column q).
-// The stores are not waited for here: the wait comes before the next read of
-// theta (the next accepted move, the end-of-sweep refresh, the kernel's end),
-// so that their latency overlaps the steps in between.
-template <bool CPLX, int WPC, int TC, int C0>
-__device__ __forceinline__ void theta_add(uint32_t tm, const typename RatioTypes<CPLX>::F* wdc,
-                                          float m2s, int h, int lane, int mp) {
+// Real RBMs, accepted move: theta += m2s * increment for this thread's units
+// (TMEM column q = theta of unit q), in chunks of kThetaChunk columns.  The
+// stores are not waited for here: the wait comes before the next read of theta
+// (the next accepted move, the end-of-sweep refresh, the kernel's end), so that
+// their latency overlaps the steps in between.
+template <int WPC, int TC, int C0>
+__device__ __forceinline__ void theta_add(uint32_t tm, const float* wdc, float m2s, int h, int lane,
+                                          int mp) {
   if constexpr (C0 == 0) tmem_st_wait();  // the previous update's stores
   if constexpr (C0 < TC) {
     constexpr int N = (TC - C0) < kThetaChunk ? (TC - C0) : kThetaChunk;
@@ -175,18 +175,11 @@ __device__ __forceinline__ void theta_add(uint32_t tm, const typename RatioTypes
     tmem_ld_wait();
 #pragma unroll
     for (int e = 0; e < N; ++e) {
-      const int col = C0 + e;
-      const int q = CPLX ? col / 2 : col;
-      const int j = 32 * (h + WPC * q) + lane;
-      if (j < mp) {
-        if constexpr (CPLX)
-          v[e] = fmaf(m2s, (col & 1) ? wdc[j].y : wdc[j].x, v[e]);
-        else
-          v[e] = fmaf(m2s, wdc[j], v[e]);
-      }
+      const int j = 32 * (h + WPC * (C0 + e)) + lane;
+      if (j < mp) v[e] = fmaf(m2s, wdc[j], v[e]);
     }
     tmem_st_cols<N>(tm + C0, v);
-    theta_add<CPLX, WPC, TC, C0 + kThetaChunk>(tm, wdc, m2s, h, lane, mp);
+    theta_add<WPC, TC, C0 + kThetaChunk>(tm, wdc, m2s, h, lane, mp);
   }
 }
 
@@ -513,7 +506,7 @@ __device__ __forceinline__ void metropolis_body(const MetroArgs& A, const int bx
               t[q] = __fdividef(fmaf(t[q], v.x, -si * v.y), r);
             }
           }
-          theta_add<false, WPC, TC, 0>(tmem_th, wdc, -2.f * si, h, lane, mp);
+          theta_add<WPC, TC, 0>(tmem_th, wdc, -2.f * si, h, lane, mp);
         }
         __syncwarp();
         if (lane == 0) {
