@@ -708,9 +708,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
   fwd_tc_body<CPLX, kFwdStages, true, SIG_TMA>(&tb, A, blockIdx.x, blockIdx.y, &sg);
 }
 
-static size_t fwd_smem_bytes(int na64, int stages = kFwdStages) {
-  // alignment slack, sigma' tile, stages, barriers, 4 epilogue staging tiles
-  return 1024 + (size_t)(na64 / 64) * 16384 + (size_t)stages * kStageB + 128 + 4 * 4096;
+// Alignment slack, sigma' tile, stages, barriers and, for the ln psi / theta
+// mode (mode 1), the epilogue warps' four 4 KB staging tiles: the SR forward
+// (mode 0) does not reserve them, which keeps two CTAs per SM on small problems.
+static size_t fwd_smem_bytes(int na64, int stages, bool staging) {
+  return 1024 + (size_t)(na64 / 64) * 16384 + (size_t)stages * kStageB + 128 +
+         (staging ? 4 * 4096 : 0);
 }
 
 // One CTA per SM: when the last wave would be far from full, split the hidden
@@ -734,7 +737,7 @@ nk_status launch_fwd_tc(const FwdTcArgs& A, const void* planes, cudaStream_t st)
   } else {
     smap = map;  // unused
   }
-  const size_t smem = fwd_smem_bytes(A.na64);
+  const size_t smem = fwd_smem_bytes(A.na64, kFwdStages, A.mode == 1);
   const int64_t blocks = (A.ns + 127) / 128;
   FwdTcArgs B = A;
   B.nseg = fwd_tc_nseg(A.ns, A.mt, A.mode, sig_tma);
@@ -809,7 +812,7 @@ nk_status launch_fwd_tc_fused(const FwdTcArgs* args, const void* const* planes, 
         B->a[B->n] = C;
         B->tiles[B->n] = (int)((A.ns + 127) / 128);
         B->start[B->n + 1] = B->start[B->n] + B->tiles[B->n] * C.nseg;
-        smem = std::max(smem, fwd_smem_bytes(A.na64));
+        smem = std::max(smem, fwd_smem_bytes(A.na64, kFwdStages, A.mode == 1));
         ++B->n;
       }
       u0 = u;
@@ -1244,7 +1247,9 @@ static unsigned vec_blocks(int64_t elems) {
 
 nk_status launch_fwd_tc_batch(const FwdBatch& P, int G, int max_tiles, int max_na64,
                               cudaStream_t st) {
-  const size_t smem = fwd_smem_bytes(max_na64, kFwdBatchStages);
+  bool staging = false;  // the SR forwards run mode 0; any ln psi item needs the tiles
+  for (int z = 0; z < G; ++z) staging = staging || P.a[z].mode == 1;
+  const size_t smem = fwd_smem_bytes(max_na64, kFwdBatchStages, staging);
   if (cudaFuncSetAttribute(fwd_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return fail(NK_ERR_CUDA, "fwd_tc_batch: shared memory attribute");
