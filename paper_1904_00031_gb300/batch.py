@@ -1,9 +1,13 @@
 """Many independent, unevenly sized VMC + SR problems advanced together.
 
-Every instance samples, evaluates ln psi and its local energies on a stream of
-its own (the streams fork from and join the caller's stream); the SR steps of
-all instances then run as one batch (nk_sr_step_batch: one launch of each
-kernel per group of up to 64 instances, instead of one per instance), on the tensor-core path when every instance shares the SR settings.
+By default (fused) the instances' sweeps run as one launch per Metropolis
+kernel template, each template's call on a stream of its own (forked from and
+joined back into the caller's stream, so that the templates overlap), then
+ln psi / theta and the local energies as one launch per field; otherwise every
+instance samples, evaluates ln psi and its local energies on a stream of its
+own.  The SR steps of all instances then run as one batch (nk_sr_step_batch:
+one launch of each kernel per group of up to 64 instances, instead of one per
+instance), on the tensor-core path when every instance shares the SR settings.
 The whole multi-instance iteration is captured once into a single CUDA graph,
 so each later iteration is one graph launch.
 """
@@ -58,6 +62,14 @@ class BatchedVmc:
                                 n_samples_per_chain=v.w.samples_per_chain, samples_out=v.samples,
                                 n_accept_out=v.n_acc, scratch=v.metro_scratch)
                            for v in self.items]
+        # one fused sweep call per kernel template, each on a stream of its own, so
+        # that the templates' launches (each covering only its own instances)
+        # overlap on the GPU instead of running one after another
+        groups = {}
+        for v, job in zip(self.items, self.sweep_jobs):
+            groups.setdefault(_metro_template(v.w), []).append(job)
+        self.sweep_groups = list(groups.values())
+        self.group_streams = [torch.cuda.Stream(device=device) for _ in self.sweep_groups]
         self.theta_jobs = [dict(rbm=v.rbm, sigma=v.samples, logpsi_out=None, theta_out=v.theta)
                            for v in self.items]
         self.eloc_jobs = [dict(rbm=v.rbm, op=v.op, sigma=v.samples, theta=v.theta,
@@ -80,9 +92,22 @@ class BatchedVmc:
     def n_samples(self) -> int:
         return sum(v.ns for v in self.items)
 
+    def _fork(self, fn, groups):
+        """fn(jobs, stream) for every group of jobs, each group on a stream of its
+        own forked from (and joined back into) the current stream."""
+        if len(groups) == 1:
+            fn(groups[0], None)
+            return
+        cur = torch.cuda.current_stream()
+        for jobs, st in zip(groups, self.group_streams):
+            st.wait_stream(cur)
+            fn(jobs, st)
+        for st in self.group_streams[:len(groups)]:
+            cur.wait_stream(st)
+
     def _eager_step(self):
         if self.fused:
-            nk.nk_batch_sweep(self.sweep_jobs)
+            self._fork(lambda j, st: nk.nk_batch_sweep(j, stream=st), self.sweep_groups)
             nk.nk_batch_logpsi(self.theta_jobs, prec=self.prec)
             nk.nk_batch_local_energy(self.eloc_jobs)
             if self.srb is not None:
@@ -145,11 +170,10 @@ class BatchedVmc:
     def launches_per_step(self) -> int:
         if self.fused:
             fields = len({v.w.is_complex for v in self.items})
-            tables = len(self.items) > 0
-            # sampling: move rows (one launch), one sweep launch per
-            # kernel template, device counters (graph mode); up to 64 items per launch
-            n = int(tables) + len({_metro_template(v.w) for v in self.items})
-            n += 1 if self.use_graph else 0
+            # sampling, per kernel template (one call each, on its own stream): the
+            # move rows, the sweep launch, the device counters (graph mode); up to
+            # 64 items per launch
+            n = len(self.sweep_groups) * (2 + (1 if self.use_graph else 0))
             n += fields            # theta
             n += 1 + fields        # move tables, local energies
         elif self.srb is None:
