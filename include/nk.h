@@ -465,9 +465,11 @@ nk_status nk_tune_shapes(nk_rbm* rbm, const void* op_dev, int32_t n_moves, const
  * nk_last_error) and nothing is enqueued.  Results are identical to the single
  * calls.  Items with a stream of their own are launched per item, in item
  * order; all the others run fused on `stream`: one launch of each kernel for
- * every group of items that share its template (sampling: the move-table
+ * every group of items that share its template (sampling: the move-row
  * builds of all items, one sweep launch per group of equal field, hidden units
- * per lane, warps per chain and group size, one device-counter launch; ln psi:
+ * per lane, warps per chain and group size -- for the one-CTA-per-group kernel
+ * (nk_rbm.sampler) equal unit pairs per thread and block size -- one
+ * device-counter launch; ln psi:
  * one launch per field; local energies: the move tables of all items, one
  * energy launch per field), each item running the arithmetic of its own call.
  * (With graph capture, the fused launches are single nodes.) */
