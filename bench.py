@@ -39,9 +39,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "bf16x2"])
     ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c3", "c4", "c5"])
-    ap.add_argument("--model", default="rbm", choices=["rbm", "symm"],
+    ap.add_argument("--model", default="rbm", choices=["rbm", "symm", "supervised", "ffnn"],
                     help="symm: the translation-symmetric RBM (alpha = m / n families) on the "
-                         "workload's lattice, SR in its tied parameters")
+                         "workload's lattice, SR in its tied parameters; supervised: overlap "
+                         "learning steps (c1: the paper's example shape, c5); ffnn: a two-layer "
+                         "ln cosh network's ln psi and gradient (c2, c5)")
     ap.add_argument("--graph", type=int, default=1, help="replay iterations as CUDA graphs")
     ap.add_argument("--profile-kernels", action="store_true",
                     help="small 20x20 J1-J2 case for ncu captures: one CTA per SM per kernel")
@@ -535,7 +537,9 @@ def run_gpu(args):
         "fp32_path_samples_per_s": None if fp32_arm is None else round(fp32_arm, 2),
         "fp32_arm": fp32_info, "same_accuracy": same_acc,
         "cg_iters": int(info["cg_iters"]), "cg_resid": info["cg_resid"],
-        "acceptance": round(info["acceptance"], 4), "energy": info["energy"],
+        "acceptance": round(info["acceptance"], 4),
+        "exchange_rate": (round(info["exchange_rate"], 4) if "exchange_rate" in info else None),
+        "energy": info["energy"],
         "energy_error_bar": info["error"],
         "nonnull_proposal_fraction": round(nonnull_frac, 4),
         "connected_per_sample": round(n_conn, 2), "moves": v.op.n_moves,
@@ -643,6 +647,245 @@ def run_gpu_batched(args):
     }
 
 
+# ---------------------------------------------------------------------- widened rows
+
+def _timed_calls(fn, steps, stream, flush=None) -> float:
+    """Mean ms of `steps` calls fn(k) (CUDA events on `stream`; the L2 flushed
+    before each call, outside the events, when `flush` is given)."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for k in range(steps):
+        if flush is not None:
+            flush.zero_()
+        evs[k][0].record(stream)
+        fn(k)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+# supervised learning shapes: (n, m, complex, target samples per step, the
+# target's perturbation: small enough that ln psi - ln target spreads by O(1)
+# over the samples, so that the overlap estimate rests on many of them)
+SUP_SHAPES = {
+    "c1": (10, 20, False, 400, 0.05),      # the paper's example: 10-site TFIM, 20 hidden units
+    "c5": (400, 1600, True, 65536, 0.003),  # the 20x20 shapes
+}
+
+
+def run_gpu_supervised(args):
+    """Supervised overlap learning (Sec. 2.2.3, Eq. 1): one nk_supervised_step per
+    step (ln psi of the target samples, loss, gradient, AdaMax).  The target is a
+    second RBM, the model's initial parameters perturbed by N(0, s^2), whose ln psi
+    is computed once on the device; the samples are random configurations (the
+    step's arithmetic does not depend on how they were drawn).  ln psi and the
+    backward are also timed alone."""
+    import torch
+
+    from paper_1904_00031_gb300 import nk
+    from paper_1904_00031_gb300 import workloads as W
+    from paper_1904_00031_gb300 import replicas as R
+
+    if args.workload not in SUP_SHAPES:
+        raise SystemExit("--model supervised runs --workload c1 (the paper's example shape) or c5")
+    world, rank, local = R.env_world()
+    R.init(world, "nccl")
+    torch.cuda.set_device(local)
+    nk.load_library()
+    n, m, cplx, ns, pert = SUP_SHAPES[args.workload]
+    prec_name = args.prec if args.prec != "auto" else "bf16x2"
+    prec = nk.NK_PREC_FP32 if prec_name == "fp32" else nk.NK_PREC_BF16X2
+    seed = R.replica_seed(1238, rank)
+    p = W.init_params(n, m, cplx, 0.01, seed)
+    rbm = nk.Rbm(n, m, cplx)
+    rbm.load(p.a, p.b, p.w)
+    pt = W.perturb_params(p, pert, seed + 1)
+    tgt = nk.Rbm(n, m, cplx)
+    tgt.load(pt.a, pt.b, pt.w)
+    sigma = torch.from_numpy(W.random_configs(ns, n, seed)).cuda()
+    log_t = nk.nk_rbm_logpsi(tgt, sigma, nk.NK_PREC_FP32)
+    pr = p.n_params * (2 if cplx else 1)
+    mom = torch.zeros(2 * pr, dtype=torch.float64, device="cuda")
+    info = torch.zeros(4, dtype=torch.float64, device="cuda")
+    scratch = nk.supervised_scratch(rbm, ns)
+    stream = torch.cuda.current_stream()
+    step_no = [0]
+
+    def step(_k, s=sigma, lt=log_t):
+        step_no[0] += 1
+        nk.nk_supervised_step(rbm, s, lt, prec=prec, lr=1e-3, step=step_no[0], moments=mom,
+                              scratch=scratch, info_out=info)
+
+    for k in range(args.warmup):
+        step(k)
+    loss0 = float(info[0].item())
+    R.barrier(world)
+    torch.cuda.synchronize()
+    # working set: sigma, ln psi, the backward's theta / T chunk and the parameters
+    small = ns * (n + 16) + min(ns, 16384) * m * (8 if cplx else 4) <= 129e6
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if small else None
+    clocks = ClockSampler(local)
+    ms = _timed_calls(step, args.steps, stream, flush)
+    clk = clocks.stop()
+    ms = R.max_over_ranks(ms, world, "cuda")
+    loss1 = float(info[0].item())
+    # the step's two contractions alone: ln psi of the samples, and the backward
+    # (theta recomputed per chunk, the adjoint) with an upstream vector g
+    lp_buf = torch.empty(ns, dtype=torch.complex128, device="cuda")
+    g = torch.full((ns,), 1.0 / ns, dtype=torch.complex128, device="cuda")
+    grad = torch.empty(p.n_params, dtype=torch.complex128 if cplx else torch.float64,
+                       device="cuda")
+    bscr = nk.backward_scratch(rbm, ns)
+    lp_ms = _timed_calls(lambda _k: nk.nk_rbm_logpsi(rbm, sigma, prec, logpsi_out=lp_buf),
+                         args.steps, stream, flush)
+    bk_ms = _timed_calls(lambda _k: nk.nk_rbm_logpsi_backward(rbm, sigma, g, prec, grad, bscr),
+                         args.steps, stream, flush)
+    # end to end: the batch (samples and ln target) from pinned host memory, the
+    # step, the info block back, every step
+    h_sig = sigma.cpu().pin_memory()
+    h_lt = log_t.cpu().pin_memory()
+    h_info = torch.empty(4, dtype=torch.float64).pin_memory()
+    d_sig = torch.empty_like(sigma)
+    d_lt = torch.empty_like(log_t)
+
+    def e2e(k):
+        d_sig.copy_(h_sig, non_blocking=True)
+        d_lt.copy_(h_lt, non_blocking=True)
+        step(k, d_sig, d_lt)
+        h_info.copy_(info, non_blocking=True)
+
+    R.barrier(world)
+    e2e_ms = R.max_over_ranks(_timed_calls(e2e, args.steps, stream), world, "cuda")
+    # algorithmic FLOPs per step: theta = W sigma' for ln psi and again in the
+    # backward, the adjoint contraction sum_s conj(O_s) g_s (complex W: 4 n m per
+    # sample each, real: 2 n m)
+    flops = 3.0 * ns * (4 if cplx else 2) * n * m
+    pk, src = peaks()
+    peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    chunks = (ns + 16383) // 16384
+    launches = 1 + 4 + chunks * (5 + (1 if chunks > 1 else 0)) + 1 + 1 + 2
+    achieved = flops / (ms / 1e3) / 1e12
+    return rank, {
+        "metric": "supervised overlap learning (Eq. 1 loss, gradient, AdaMax) target samples/s",
+        "value": round(R.aggregate_rate(ns, world, ms / 1e3), 2), "unit": "samples/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (random configurations; target = a perturbed RBM, ln psi on the device)",
+        "config": {"workload": f"supervised_{args.workload}", "n": n, "m": m, "complex": cplx,
+                   "samples_per_step": ns, "target_perturbation": pert, "prec": prec_name,
+                   "optimizer": "AdaMax lr 1e-3",
+                   "parallelism": f"replicas x{world}",
+                   "l2": ("L2 flushed before each timed step" if small else
+                          "inputs larger than L2")},
+        "steps_per_s": round(1e3 / ms, 3), "loss_first": round(loss0, 6),
+        "loss_last": round(loss1, 6),
+        "parts_ms": {"logpsi": round(lp_ms, 4), "backward": round(bk_ms, 4)},
+        "roofline": {"bound": "tensor" if prec == nk.NK_PREC_BF16X2 else "alu",
+                     "achieved": round(achieved, 3),
+                     "peak": peak if prec == nk.NK_PREC_BF16X2 else None,
+                     "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4) if prec == nk.NK_PREC_BF16X2 else None,
+                     "kernel": "whole step (ln psi, reductions, chunked backward, AdaMax)",
+                     "traffic": None,
+                     "peak_source": f"{src} bf16 dense TFLOP/s (sustained)"},
+        "e2e": {"value": round(R.aggregate_rate(ns, world, e2e_ms / 1e3), 2), "unit": "samples/s",
+                "h2d_bytes_per_step": int(h_sig.numel() + h_lt.numel() * 16),
+                "d2h_bytes_per_step": 32},
+        "gpu_launches": launches * args.steps, "clocks": clk,
+    }
+
+
+# FFNN shapes: (widths, complex, samples)
+FFNN_SHAPES = {
+    "c2": ([40, 80, 40], True, 16384),
+    "c5": ([400, 1600, 400], True, 65536),
+}
+
+
+def run_gpu_ffnn(args):
+    """Multi-layer ln cosh FFNN (Sec. 2.2.2): one step = nk_ffnn_logpsi and
+    nk_ffnn_backward (grad = sum_s conj(O_s) g_s for an upstream vector g) on a
+    batch of random configurations, CUDA-core FP32 contractions."""
+    import numpy as np
+    import torch
+
+    from paper_1904_00031_gb300 import nk
+    from paper_1904_00031_gb300 import workloads as W
+    from paper_1904_00031_gb300 import replicas as R
+
+    if args.workload not in FFNN_SHAPES:
+        raise SystemExit("--model ffnn runs --workload c2 or c5")
+    world, rank, local = R.env_world()
+    R.init(world, "nccl")
+    torch.cuda.set_device(local)
+    nk.load_library()
+    widths, cplx, ns = FFNN_SHAPES[args.workload]
+    seed = R.replica_seed(1239, rank)
+    net = nk.Ffnn(widths, cplx)
+    net.load(W.init_ffnn_params(widths, cplx, 0.01, seed))
+    sigma = torch.from_numpy(W.random_configs(ns, widths[0], seed)).cuda()
+    rng = np.random.default_rng(seed + 1)
+    g = torch.from_numpy(rng.normal(size=ns) + 1j * rng.normal(size=ns)).cuda() / ns
+    scratch = net.scratch(ns)
+    lp = torch.empty(ns, dtype=torch.complex128, device="cuda")
+    grad = torch.empty(net.n_params, dtype=torch.complex128 if cplx else torch.float64,
+                       device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def fwd(_k):
+        nk.nk_ffnn_logpsi(net, sigma, lp, scratch)
+
+    def bwd(_k):
+        nk.nk_ffnn_backward(net, sigma, g, grad, scratch)
+
+    def step(k):
+        fwd(k)
+        bwd(k)
+
+    for k in range(args.warmup):
+        step(k)
+    R.barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    ms = _timed_calls(step, args.steps, stream)
+    ms_f = _timed_calls(fwd, args.steps, stream)
+    ms_b = _timed_calls(bwd, args.steps, stream)
+    clk = clocks.stop()
+    ms = R.max_over_ranks(ms, world, "cuda")
+    alu = nk.nk_measure_alu_peaks()
+    peak = alu["fp32_fma_flops"] / 1e12
+    # algorithmic FLOPs (complex multiply-add 8, complex x real 4): forward
+    # h_l = W_l x_(l-1) + b_l; backward e_(l-1) = conj(tanh h) (e_l conj(W_l)) for
+    # l > 1 and grad W_l = e_l^T conj(x_(l-1)) (the backward's recomputed forward
+    # is not counted)
+    L = len(widths) - 1
+    per = [(4 if l == 1 else 8) * widths[l] * widths[l - 1] for l in range(1, L + 1)]
+    f_fl = float(ns) * sum(per)
+    b_fl = float(ns) * (sum(per) + sum(8 * widths[l] * widths[l - 1] for l in range(2, L + 1)))
+    ach = (f_fl + b_fl) / (ms / 1e3) / 1e12
+    launches = (L + 1) + 4 * L
+    big = ns * sum(widths[1:]) * 16 > 129e6
+    return rank, {
+        "metric": "multi-layer ln cosh FFNN ln psi + gradient, samples/s",
+        "value": round(R.aggregate_rate(ns, world, ms / 1e3), 2), "unit": "samples/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (random configurations, parameters N(0, 0.01^2), random upstream g)",
+        "config": {"workload": f"ffnn_{args.workload}", "widths": widths, "complex": cplx,
+                   "samples": ns, "parallelism": f"replicas x{world}",
+                   "l2": ("activations larger than L2" if big else
+                          "activations smaller than L2, not flushed")},
+        "forward_ms": round(ms_f, 4), "backward_ms": round(ms_b, 4),
+        "roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
+                     "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                     "kernel": "forward + backward (ffnn_fwd / wgrad / bwd kernels)",
+                     "traffic": None,
+                     "peak_source": "measured packed FP32 FMA rate (nk_measure_alu_peaks)"},
+        "gpu_launches": launches * args.steps, "clocks": clk,
+    }
+
+
 def main():
     args = parse()
     if args.oracle_sample:
@@ -710,6 +953,12 @@ def main():
                              "sample": f"{nc} chains x ({spc} samples + 1 burn-in sweep), one "
                                        f"full oracle VMC+SR iteration ({ncg} CG iterations), "
                                        f"{r['seconds']:.1f} s"}}
+    if args.model in ("supervised", "ffnn"):
+        rank, out = (run_gpu_supervised if args.model == "supervised" else run_gpu_ffnn)(args)
+        out["cpu_baseline"] = None
+        if rank == 0:
+            print(json.dumps(out))
+        return
     if args.workload == "c4" and args.model != "rbm":
         raise SystemExit("--model symm runs the single-instance workloads (c1, c2, c3, c5)")
     rank, out = run_gpu_batched(args) if args.workload == "c4" else run_gpu(args)

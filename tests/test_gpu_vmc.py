@@ -200,6 +200,48 @@ def test_graph_replay_equals_eager(mods, prec):
     assert b.chains.counter == a.chains.counter
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tempering_iteration_matches_oracle_heis12(mods, prec):
+    """The VMC iteration with the parallel-tempering sampler (ladders of 3
+    replicas, only the beta = 1 replica recorded) samples the same |psi|^2 as the
+    plain sampler, so its energies meet the criterion against the oracle's run of
+    the plain sampler on the same workload."""
+    nk, VmcSr = mods
+    g = json.load(open(os.path.join(GOLDEN, "vmc_heis12.json")))
+    w = workload_of("heis12")
+    w.lr = g["lr"]
+    p = W.init_params(w.n, w.m, w.is_complex, 0.01, w.seed)
+    v = VmcSr(w, p, prec=prec, replicas=3)
+    energies = []
+    for _ in range(len(g["energies"])):
+        v.step()
+        energies.append(v.info()["energy"])
+    _criterion(dict(g, name="heis12, tempering sampler"), energies)
+    inf = v.info()
+    assert 0.0 < inf["acceptance"] < 1.0
+    assert 0.0 < inf["exchange_rate"] <= 1.0
+
+
+def test_tempering_graph_replay_equals_eager(mods):
+    """With the tempering sampler a captured iteration also replays the eager
+    arithmetic bit for bit (the device counter advances once per sweep)."""
+    nk, VmcSr = mods
+    w = workload_of("heis12")
+    p = W.init_params(w.n, w.m, w.is_complex, 0.01, w.seed)
+    a = VmcSr(w, p, prec=nk.NK_PREC_BF16X2, graph=False, replicas=2)
+    b = VmcSr(w, p, prec=nk.NK_PREC_BF16X2, graph=True, replicas=2)
+    a.chains.counter_dev = None
+    for _ in range(4):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    for xa, xb in zip(a.rbm.params_numpy(), b.rbm.params_numpy()):
+        assert np.array_equal(xa, xb)
+    assert np.array_equal(a.chains.sigma.cpu().numpy(), b.chains.sigma.cpu().numpy())
+    assert np.array_equal(a.n_swap.cpu().numpy(), b.n_swap.cpu().numpy())
+    assert b.chains.counter == a.chains.counter
+
+
 def test_symmetric_rbm_heisenberg20(mods):
     """The same listing run with the translation-symmetric RBM (alpha = 1: one
     filter of 20 weights, 22 parameters instead of 440), SR in the tied space:
