@@ -527,22 +527,35 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
       if constexpr (CPLX) {
         float2* th = reinterpret_cast<float2*>(A.theta_out);
         float2* tt = reinterpret_cast<float2*>(A.t_out);
+        // SR forward: the chunk loop unrolled (the prefetched T' values sit in a
+        // register array indexed by chunk); ln psi / theta / tanh theta: one chunk
+        // per loop trip, so that the transcendental epilogue is inlined once
+        // instead of four times (the unrolled body overflowed the instruction
+        // cache); the summation order is the same either way
+        if (A.mode == 0) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          float2 tc[16];
-          if (!PREFETCH && A.mode == 0) load_chunk(jt, c, tc);
-          float ur[16], ui[16];
-          tmem_ld16(tb0 + c * 16, ur);
-          tmem_ld16(tb0 + 64 + c * 16, ui);
-          tmem_ld_wait();
-          if (A.mode == 0) {
+          for (int c = 0; c < 4; ++c) {
+            float2 tc[16];
+            if (!PREFETCH) load_chunk(jt, c, tc);
+            float ur[16], ui[16];
+            tmem_ld16(tb0 + c * 16, ur);
+            tmem_ld16(tb0 + 64 + c * 16, ui);
+            tmem_ld_wait();
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
               const float2 t = PREFETCH ? tp[c * 16 + e] : tc[e];
               pr += t.x * ur[e] - t.y * ui[e];
               pi += t.x * ui[e] + t.y * ur[e];
             }
-          } else {
+          }
+        }
+#pragma unroll 1
+        for (int c = 0; c < (A.mode == 0 ? 0 : 4); ++c) {
+          float ur[16], ui[16];
+          tmem_ld16(tb0 + c * 16, ur);
+          tmem_ld16(tb0 + 64 + c * 16, ui);
+          tmem_ld_wait();
+          {
             if (A.logpsi && live) {
 #pragma unroll
               for (int e = 0; e < 16; ++e) {
@@ -583,17 +596,24 @@ __device__ __forceinline__ void fwd_tc_body(const CUtensorMap* tbp, const FwdTcA
       } else {
         float* th = reinterpret_cast<float*>(A.theta_out);
         float* tt = reinterpret_cast<float*>(A.t_out);
+        if (A.mode == 0) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          float tc[16];
-          if (!PREFETCH && A.mode == 0) load_chunk(jt, c, tc);
+          for (int c = 0; c < 8; ++c) {
+            float tc[16];
+            if (!PREFETCH) load_chunk(jt, c, tc);
+            float u[16];
+            tmem_ld16(tb0 + c * 16, u);
+            tmem_ld_wait();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) pr += (PREFETCH ? tp[c * 16 + e] : tc[e]) * u[e];
+          }
+        }
+#pragma unroll 1
+        for (int c = 0; c < (A.mode == 0 ? 0 : 8); ++c) {
           float u[16];
           tmem_ld16(tb0 + c * 16, u);
           tmem_ld_wait();
-          if (A.mode == 0) {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) pr += (PREFETCH ? tp[c * 16 + e] : tc[e]) * u[e];
-          } else {
+          {
             if (A.logpsi && live) {
 #pragma unroll
               for (int e = 0; e < 16; ++e)
