@@ -286,7 +286,8 @@ size_t nk_local_energy_scratch_bytes(int32_t m, int32_t is_complex, int32_t n_mo
  *   eloc_out c128 [ns]
  *   t_out    F32 [ns][m] tanh(theta) (the factored log-derivatives), or NULL
  *   scratch  nk_local_energy_scratch_bytes(m, is_complex, n_moves) bytes, 256-B
- *            aligned (per-move ratio tables built by the call) */
+ *            aligned (built by the call: the per-move ratio tables, and per move and
+ *            spin pattern the FP64 factor mel x exp(-2 s_i a_i - 2 s_k a_k)) */
 nk_status nk_local_energy(const nk_rbm* rbm, const void* op_dev, int32_t n_moves,
                           const int8_t* sigma, const void* theta, int64_t ns, double* eloc_out,
                           void* t_out, void* scratch, size_t scratch_bytes, void* stream);

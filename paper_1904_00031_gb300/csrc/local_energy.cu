@@ -28,6 +28,7 @@ struct ElocArgs {
   const void* theta;   // [ns][m] F
   const char* op;      // compiled operator
   const double* a;     // master a
+  const double2* fac;  // [nm_pad][4] mel x exp(visible) per move and spin pattern (built per call)
   const void* tab;     // [n][mp] T2
   double* eloc;        // c128 [ns]
   void* t_out;         // [ns][m] F or null
@@ -112,15 +113,77 @@ __host__ __device__ inline int64_t move_table_elems(int cplx, int mp, int nm_pad
   return cplx ? (int64_t)mp * (nm_pad / kEBM) * 32 : (int64_t)mp * nm_pad;
 }
 
+// Byte offset of the factor table in the scratch: after the move table of
+// mp x nm_pad entries (T2: 16 bytes complex, 8 real).
+__host__ __device__ inline int64_t move_factor_offset(int cplx, int mp, int nm_pad) {
+  return ((int64_t)mp * nm_pad * (cplx ? 16 : 8) + 255) / 256 * 256;
+}
+
+// Element y = 4 mv + x of the factor table: mel(x) exp(-2 s_i a_i (- 2 s_k a_k)) of
+// move mv for the spin pattern x = 2 idx(s_i) + idx(s_k) (zero for a padding move
+// or a zero matrix element), in FP64: the per-move constant of every ratio.
+template <bool CPLX>
+__device__ __forceinline__ void move_factor_elem(int64_t y, const OpMove* __restrict__ mvs,
+                                                 const double* __restrict__ a, int nm,
+                                                 double2* out) {
+  const int mv = (int)(y >> 2), x = (int)(y & 3);
+  double cr = 0.0, ci = 0.0;
+  if (mv < nm) {
+    const double mr = mvs[mv].mel[x][0], mi = mvs[mv].mel[x][1];
+    if (mr != 0.0 || mi != 0.0) {
+      const double si = (x >> 1) ? -1.0 : 1.0, sk = (x & 1) ? -1.0 : 1.0;
+      const int i = mvs[mv].i, k = mvs[mv].k;
+      double vr, vi;
+      if (CPLX) {
+        vr = -2.0 * si * a[2 * i];
+        vi = -2.0 * si * a[2 * i + 1];
+        if (mvs[mv].two) {
+          vr += -2.0 * sk * a[2 * k];
+          vi += -2.0 * sk * a[2 * k + 1];
+        }
+      } else {
+        vr = -2.0 * si * a[i];
+        vi = 0.0;
+        if (mvs[mv].two) vr += -2.0 * sk * a[k];
+      }
+      const double ev = exp(vr), fr = ev * cos(vi), fi = ev * sin(vi);
+      cr = mr * fr - mi * fi;
+      ci = mr * fi + mi * fr;
+    }
+  }
+  out[y] = make_double2(cr, ci);
+}
+
+// Element x of a call's tables: the move table, then the factor table.
+template <bool CPLX>
+__device__ __forceinline__ void move_job_elem(int64_t x, const OpMove* __restrict__ mvs,
+                                              const void* __restrict__ tabv,
+                                              const double* __restrict__ a, int mp, int nm,
+                                              int nm_pad, void* outv) {
+  const int64_t te = move_table_elems(CPLX, mp, nm_pad);
+  if (x < te) {
+    move_table_elem<CPLX>(x, mvs, tabv, mp, nm, nm_pad, outv);
+  } else {
+    double2* fac = reinterpret_cast<double2*>(reinterpret_cast<char*>(outv) +
+                                              move_factor_offset(CPLX, mp, nm_pad));
+    move_factor_elem<CPLX>(x - te, mvs, a, nm, fac);
+  }
+}
+
+__host__ __device__ inline int64_t move_job_elems(int cplx, int mp, int nm_pad) {
+  return move_table_elems(cplx, mp, nm_pad) + (int64_t)nm_pad * 4;
+}
+
 template <bool CPLX>
 __global__ void move_tables_kernel(const char* __restrict__ op, const void* __restrict__ tabv,
-                                   int mp, int nm, int nm_pad, void* outv) {
+                                   const double* __restrict__ a, int mp, int nm, int nm_pad,
+                                   void* outv) {
   const OpDevHeader* H = reinterpret_cast<const OpDevHeader*>(op);
   const OpMove* mvs = reinterpret_cast<const OpMove*>(op + H->off_moves);
-  const int64_t total = move_table_elems(CPLX, mp, nm_pad);
+  const int64_t total = move_job_elems(CPLX, mp, nm_pad);
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
        x += (int64_t)gridDim.x * blockDim.x)
-    move_table_elem<CPLX>(x, mvs, tabv, mp, nm, nm_pad, outv);
+    move_job_elem<CPLX>(x, mvs, tabv, a, mp, nm, nm_pad, outv);
 }
 
 // The move tables of many problems in one launch (job k owns elements
@@ -130,6 +193,7 @@ struct MoveTableJob {
   int cplx, mp, nm, nm_pad;
   const char* op;
   const void* tab;
+  const double* a;
   void* out;
 };
 struct MoveTableBatch {
@@ -150,8 +214,10 @@ __global__ void move_tables_batch_kernel(const __grid_constant__ MoveTableBatch 
     const MoveTableJob& J = B.j[lo];
     const OpDevHeader* H = reinterpret_cast<const OpDevHeader*>(J.op);
     const OpMove* mvs = reinterpret_cast<const OpMove*>(J.op + H->off_moves);
-    if (J.cplx) move_table_elem<true>(x - B.start[lo], mvs, J.tab, J.mp, J.nm, J.nm_pad, J.out);
-    else move_table_elem<false>(x - B.start[lo], mvs, J.tab, J.mp, J.nm, J.nm_pad, J.out);
+    if (J.cplx)
+      move_job_elem<true>(x - B.start[lo], mvs, J.tab, J.a, J.mp, J.nm, J.nm_pad, J.out);
+    else
+      move_job_elem<false>(x - B.start[lo], mvs, J.tab, J.a, J.mp, J.nm, J.nm_pad, J.out);
   }
 }
 
@@ -319,34 +385,9 @@ __device__ __forceinline__ void local_energy_body(const CUtensorMap* mtab, const
         mvk[tid] = mv < nm ? mvs[mv].k : 0;
         mvtwo[tid] = mv < nm ? mvs[mv].two : -1;  // -1: padding move
       }
-      {
-        const int mm = tid >> 2, x = tid & 3, mv = mt0 + mm;
-        double cr = 0.0, ci = 0.0;
-        if (mv < nm) {
-          const double mr = mvs[mv].mel[x][0], mi = mvs[mv].mel[x][1];
-          if (mr != 0.0 || mi != 0.0) {
-            const double si = (x >> 1) ? -1.0 : 1.0, sk = (x & 1) ? -1.0 : 1.0;
-            const int i = mvs[mv].i, k = mvs[mv].k;
-            double vr, vi;
-            if (CPLX) {
-              vr = -2.0 * si * A.a[2 * i];
-              vi = -2.0 * si * A.a[2 * i + 1];
-              if (mvs[mv].two) {
-                vr += -2.0 * sk * A.a[2 * k];
-                vi += -2.0 * sk * A.a[2 * k + 1];
-              }
-            } else {
-              vr = -2.0 * si * A.a[i];
-              vi = 0.0;
-              if (mvs[mv].two) vr += -2.0 * sk * A.a[k];
-            }
-            const double ev = exp(vr), fr = ev * cos(vi), fi = ev * sin(vi);
-            cr = mr * fr - mi * fi;
-            ci = mr * fi + mi * fr;
-          }
-        }
-        cvs[mm * 4 + x] = make_double2(cr, ci);
-      }
+      // the tile's mel x exp(visible) factors, built once per call by the
+      // move-table launch (tile mt0 .. mt0 + 63 lies inside the padded table)
+      cvs[tid] = A.fac[(int64_t)mt0 * 4 + tid];
       __syncthreads();
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
@@ -576,7 +617,8 @@ __global__ void __launch_bounds__(256, 2) local_energy_batch(const __grid_consta
 
 size_t local_energy_scratch_bytes(int m, int cplx, int n_moves) {
   const int64_t nm_pad = round_up(std::max(n_moves, 1), kEBM);
-  return (size_t)round_up((int64_t)padded_m(m) * nm_pad * (cplx ? 16 : 8), 256);
+  // the move table, then the factor table (one double2 per move and spin pattern)
+  return (size_t)(move_factor_offset(cplx, padded_m(m), (int)nm_pad) + nm_pad * 4 * 16);
 }
 
 // Everything one local-energy call needs, before anything is enqueued.
@@ -615,8 +657,11 @@ static nk_status plan_local_energy(const nk_rbm* r, const void* op_dev, int n_mo
   P->cplx = cplx;
   const int nm_pad = (int)round_up(std::max(n_moves, 1), kEBM);
   memset(&P->map, 0, sizeof(P->map));
-  P->job = MoveTableJob{cplx ? 1 : 0, L.mp, n_moves, nm_pad, A.op, A.tab, scratch};
-  P->tab_elems = n_moves > 0 ? move_table_elems(cplx, L.mp, nm_pad) : 0;
+  P->job = MoveTableJob{cplx ? 1 : 0, L.mp, n_moves, nm_pad, A.op, A.tab, r->a, scratch};
+  P->tab_elems = n_moves > 0 ? move_job_elems(cplx, L.mp, nm_pad) : 0;
+  A.fac = n_moves > 0 ? reinterpret_cast<const double2*>(
+                            (const char*)scratch + move_factor_offset(cplx, L.mp, nm_pad))
+                      : nullptr;
   if (n_moves > 0) {
     const int fl = cplx ? 4 : 2;  // floats per table entry
     if (!make_map_f32(&P->map, scratch, L.mp, (int64_t)nm_pad * fl, (int64_t)nm_pad * fl * 4,
@@ -651,11 +696,11 @@ nk_status launch_local_energy(const nk_rbm* r, const void* op_dev, int n_moves,
   if (P.tab_elems > 0) {
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((P.tab_elems + 255) / 256, 152 * 8));
     if (P.cplx)
-      move_tables_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(A.op, A.tab, A.mp, n_moves,
+      move_tables_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(A.op, A.tab, A.a, A.mp, n_moves,
                                                                  P.job.nm_pad, scratch);
     else
-      move_tables_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(A.op, A.tab, A.mp, n_moves,
-                                                                  P.job.nm_pad, scratch);
+      move_tables_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(A.op, A.tab, A.a, A.mp,
+                                                                  n_moves, P.job.nm_pad, scratch);
     if (nk_status e = check_launch("nk_local_energy(move tables)")) return e;
   }
   if (A.nseg == 2 &&
