@@ -10,6 +10,7 @@ import bench
 from oracle import hamiltonian
 from paper_1904_00031_gb300 import workloads as W
 
+
 def brute_connected(op, n, zero_magnetisation):
     xs = hamiltonian.basis(n, zero_magnetisation)
     h = hamiltonian.sparse_h(op, xs).tocsc()
