@@ -57,6 +57,18 @@ def test_status_strings_and_sizes(lib):
     assert lib.nk_backward_scratch_bytes(400, 1600, 1, 65536) < 65536 * 1600 * 8
 
 
+@pytest.mark.parametrize("m, cplx, moves", [(1600, 1, 1600), (1600, 0, 1600), (20, 0, 10),
+                                            (80, 1, 40), (33, 1, 65), (400, 0, 1)])
+def test_local_energy_scratch_layout(lib, m, cplx, moves):
+    """The move table ([m rounded to 32][moves rounded to 64] entries of 16 B complex
+    or 8 B real, rounded to 256 B), then one FP64 complex factor per move and spin
+    pattern."""
+    mp = (m + 31) // 32 * 32
+    nm_pad = (moves + 63) // 64 * 64
+    table = (mp * nm_pad * (16 if cplx else 8) + 255) // 256 * 256
+    assert lib.nk_local_energy_scratch_bytes(m, cplx, moves) == table + nm_pad * 4 * 16
+
+
 def test_sr_batch_host_checks(lib):
     from paper_1904_00031_gb300 import nk
     assert lib.nk_sr_batch_desc_bytes(0) == 0
